@@ -1,0 +1,564 @@
+"""Seeded synthetic inputs for the granule-grid coupling substep.
+
+This module is shared by the tests, the benchmark and the smoke check. It
+holds NONE of the method's arithmetic: it only builds granule packings, fluid
+fields and parameter sets, and encodes granule positions in the canonical
+input format that both the CPU oracle and the CUDA library read exactly.
+
+Canonical input format (every field is exactly representable in FP32, so the
+FP64 oracle and the FP32 GPU path start from identical numbers):
+
+* ``cell``  int32 [N, 3]  contact-cell coordinates (cx, cy, cz)
+* ``q``     uint32 [N, 3] offset inside the contact cell, as a 30-bit
+  fixed-point fraction: x = origin + (cell + q / 2**30) * h_c
+* ``r``     float32 [N]   radius
+* ``v``     float32 [N, 3] velocity
+* fluid fields on the MAC grid, float32, x-fastest:
+  ``u`` (nx+1, ny, nz) on x-faces, ``vf`` (nx, ny+1, nz), ``wf`` (nx, ny, nz+1),
+  ``p`` and ``alpha_f`` at cell centres.
+
+Random numbers come from numpy's Philox counter-based generator keyed by
+(config seed, stream id), so every input is a pure function of its seed.
+
+Recipes follow the workload descriptions of the five configurations
+(plain 8k FP64 substep, 1M dam-break column, 8M polydisperse bed, 100k
+differentiable window, 16M scale sweep) plus small parity cases with real
+contacts.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import Optional
+
+import numpy as np
+
+FRAC_BITS = 30
+FRAC_ONE = 1 << FRAC_BITS
+# offsets closer than this (in 2**-30 cell units) to a contact-cell face are
+# nudged inwards so that floor() of the FP64 absolute position is unambiguous
+FRAC_GUARD = 1 << 10
+
+STREAM_POS, STREAM_RAD, STREAM_VEL, STREAM_FLUID, STREAM_TARGET, STREAM_MISC = range(6)
+
+
+def rng(seed: int, stream: int) -> np.random.Generator:
+    """Counter-based Philox stream keyed by (seed, stream)."""
+    return np.random.Generator(np.random.Philox(key=np.array([seed, stream], dtype=np.uint64)))
+
+
+@dataclasses.dataclass
+class Grid:
+    nx: int
+    ny: int
+    nz: int
+    dx: float
+    origin: tuple = (0.0, 0.0, 0.0)
+    k_contact: int = 1
+
+    @property
+    def h_c(self) -> float:
+        return self.dx / self.k_contact
+
+    @property
+    def nc(self) -> tuple:
+        return (self.nx * self.k_contact, self.ny * self.k_contact, self.nz * self.k_contact)
+
+    @property
+    def extent(self) -> np.ndarray:
+        return np.array([self.nx, self.ny, self.nz], dtype=np.float64) * self.dx
+
+
+@dataclasses.dataclass
+class Params:
+    rho_s: float = 2650.0
+    rho_f: float = 1000.0
+    k_n: float = 1.0e5
+    zeta: float = 0.3
+    kt_over_cn: float = 1.0
+    mu_fric: float = 0.5
+    c_drag: float = 0.22
+    g: tuple = (0.0, 0.0, -9.8)
+    dt_sub: float = 1.0e-5
+    dt_fluid: float = 1.0e-4
+    virtual_mass: int = 1
+    walls: int = 1
+
+
+@dataclasses.dataclass
+class Problem:
+    name: str
+    grid: Grid
+    params: Params
+    K: int
+    cell: np.ndarray
+    q: np.ndarray
+    r: np.ndarray
+    v: np.ndarray
+    u: np.ndarray
+    vf: np.ndarray
+    wf: np.ndarray
+    p: np.ndarray
+    alpha_f: np.ndarray
+    target: Optional[np.ndarray] = None
+    note: str = ""
+
+    @property
+    def n(self) -> int:
+        return int(self.r.shape[0])
+
+    def positions(self) -> np.ndarray:
+        """FP64 absolute positions decoded from the canonical encoding."""
+        return decode_positions(self.cell, self.q, self.grid)
+
+
+# --------------------------------------------------------------------------
+# position encoding
+# --------------------------------------------------------------------------
+
+def contact_k(dx: float, r_max: float) -> int:
+    """Contact cells per MAC cell: the largest k with dx / k >= 2 r_max."""
+    return max(1, int(math.floor(dx / (2.0 * r_max) * (1.0 - 1e-12))))
+
+
+def encode_positions(x: np.ndarray, grid: Grid):
+    """Absolute FP64 positions -> (cell int32[N,3], q uint32[N,3]).
+
+    The fraction is rounded to 30 bits and kept FRAC_GUARD away from the
+    cell faces."""
+    o = np.asarray(grid.origin, dtype=np.float64)
+    s = (np.asarray(x, dtype=np.float64) - o) / grid.h_c
+    c = np.floor(s).astype(np.int64)
+    nc = np.array(grid.nc, dtype=np.int64)
+    c = np.clip(c, 0, nc - 1)
+    f = s - c
+    q = np.rint(f * FRAC_ONE).astype(np.int64)
+    q = np.clip(q, FRAC_GUARD, FRAC_ONE - FRAC_GUARD)
+    return c.astype(np.int32), q.astype(np.uint32)
+
+
+def decode_positions(cell: np.ndarray, q: np.ndarray, grid: Grid) -> np.ndarray:
+    o = np.asarray(grid.origin, dtype=np.float64)
+    return o + (cell.astype(np.float64) + q.astype(np.float64) / FRAC_ONE) * grid.h_c
+
+
+# --------------------------------------------------------------------------
+# packings
+# --------------------------------------------------------------------------
+
+def cubic_lattice(counts, spacing, start):
+    ii, jj, kk = np.meshgrid(np.arange(counts[0]), np.arange(counts[1]), np.arange(counts[2]), indexing="ij")
+    pts = np.stack([ii.ravel(order="F"), jj.ravel(order="F"), kk.ravel(order="F")], axis=1).astype(np.float64)
+    return np.asarray(start, dtype=np.float64) + pts * spacing
+
+
+def fcc_fill(lo, hi, nn, n_max=None):
+    """FCC lattice points with nearest-neighbour distance nn inside the box
+    [lo, hi], filled layer by layer upwards in z (x fastest) until n_max
+    (all sites of the box when n_max is None)."""
+    a = nn * math.sqrt(2.0)
+    basis = np.array([[0, 0, 0], [0.5, 0.5, 0], [0.5, 0, 0.5], [0, 0.5, 0.5]]) * a
+    lo = np.asarray(lo, dtype=np.float64)
+    hi = np.asarray(hi, dtype=np.float64)
+    ncell = np.floor((hi - lo) / a + 1.0).astype(int) + 1
+    out = []
+    total = 0
+    for kz in range(ncell[2] * 2 + 2):
+        # atomic layers: even -> basis z=0, odd -> basis z=a/2
+        z_layer = lo[2] + (kz // 2) * a + (kz % 2) * 0.5 * a
+        if z_layer > hi[2]:
+            break
+        sel = basis[np.isclose(basis[:, 2], (kz % 2) * 0.5 * a)]
+        ii, jj = np.meshgrid(np.arange(ncell[0]), np.arange(ncell[1]), indexing="ij")
+        base = np.stack([ii.ravel(order="F") * a, jj.ravel(order="F") * a], axis=1)
+        for b in sel:
+            pts = np.empty((base.shape[0], 3))
+            pts[:, 0] = lo[0] + base[:, 0] + b[0]
+            pts[:, 1] = lo[1] + base[:, 1] + b[1]
+            pts[:, 2] = z_layer
+            keep = (pts[:, 0] <= hi[0]) & (pts[:, 1] <= hi[1])
+            pts = pts[keep]
+            # x fastest inside the layer
+            order = np.lexsort((pts[:, 0], pts[:, 1]))
+            out.append(pts[order])
+            total += pts.shape[0]
+        if n_max is not None and total >= n_max:
+            break
+    pts = np.concatenate(out, axis=0)
+    # stable order: by z, then y, then x
+    order = np.lexsort((pts[:, 0], pts[:, 1], pts[:, 2]))
+    pts = pts[order]
+    if n_max is None:
+        return pts
+    if pts.shape[0] < n_max:
+        raise ValueError(f"box holds only {pts.shape[0]} FCC sites, wanted {n_max}")
+    return pts[:n_max]
+
+
+# --------------------------------------------------------------------------
+# neighbour pairs (input validation only: the contact-band guard)
+# --------------------------------------------------------------------------
+
+def pairs_within(x: np.ndarray, r: np.ndarray, extra: float, chunk: int = 1 << 21):
+    """All pairs i<j with |x_i - x_j| < r_i + r_j + extra.
+
+    Returns (i, j, d). Binned search with bins of width 2 r_max + extra."""
+    n = x.shape[0]
+    if n < 2:
+        return np.zeros(0, np.int64), np.zeros(0, np.int64), np.zeros(0)
+    hb = 2.0 * float(r.max()) + extra
+    lo = x.min(axis=0)
+    b = np.floor((x - lo) / hb).astype(np.int64)
+    nb = b.max(axis=0) + 3
+    b += 1
+    lin = b[:, 0] + nb[0] * (b[:, 1] + nb[1] * b[:, 2])
+    order = np.argsort(lin, kind="stable")
+    lin_s = lin[order]
+    ub, first, cnt = np.unique(lin_s, return_index=True, return_counts=True)
+    I, J, D = [], [], []
+    offs = [(a, bb, c) for c in (-1, 0, 1) for bb in (-1, 0, 1) for a in (-1, 0, 1)]
+    for (ox, oy, oz) in offs:
+        q = lin + ox + nb[0] * (oy + nb[1] * oz)
+        pos = np.searchsorted(ub, q)
+        pos = np.minimum(pos, ub.shape[0] - 1)
+        hit = ub[pos] == q
+        idx = np.nonzero(hit)[0]
+        st = first[pos[idx]]
+        ct = cnt[pos[idx]]
+        for s0 in range(0, idx.shape[0], chunk):
+            ii = idx[s0:s0 + chunk]
+            ss = st[s0:s0 + chunk]
+            cc = ct[s0:s0 + chunk]
+            tot = int(cc.sum())
+            if tot == 0:
+                continue
+            rep_i = np.repeat(ii, cc)
+            base = np.repeat(ss - np.cumsum(cc) + cc, cc)
+            kk = base + np.arange(tot)
+            jj = order[kk]
+            m = rep_i < jj
+            rep_i = rep_i[m]
+            jj = jj[m]
+            d = np.linalg.norm(x[rep_i] - x[jj], axis=1)
+            keep = d < r[rep_i] + r[jj] + extra
+            I.append(rep_i[keep])
+            J.append(jj[keep])
+            D.append(d[keep])
+    if not I:
+        return np.zeros(0, np.int64), np.zeros(0, np.int64), np.zeros(0)
+    return np.concatenate(I), np.concatenate(J), np.concatenate(D)
+
+
+def band_pairs(x, r, band):
+    """Pairs whose gap |d - (r_i + r_j)| is below `band` (ambiguous contact predicate)."""
+    i, j, d = pairs_within(x, r, band)
+    m = np.abs(d - (r[i] + r[j])) < band
+    return i[m], j[m]
+
+
+def wall_band(x, r, grid: Grid, band):
+    o = np.asarray(grid.origin)
+    hi = o + grid.extent
+    gap_lo = x - o
+    gap_hi = hi - x
+    return np.nonzero(((np.abs(gap_lo - r[:, None]) < band) | (np.abs(gap_hi - r[:, None]) < band)).any(axis=1))[0]
+
+
+def _clear_band(x, r, grid, gen, jitter, band, max_iter=50):
+    """Re-jitter granules taking part in an ambiguous contact (pair or wall)."""
+    x0 = x.copy()
+    for _ in range(max_iter):
+        cell, q = encode_positions(x, grid)
+        xe = decode_positions(cell, q, grid)
+        i, j = band_pairs(xe, r.astype(np.float64), band)
+        w = wall_band(xe, r.astype(np.float64), grid, band)
+        bad = np.unique(np.concatenate([i, j, w]))
+        if bad.size == 0:
+            return x
+        x[bad] = x0[bad] + gen.uniform(-jitter, jitter, size=(bad.size, 3))
+    raise RuntimeError("could not clear the contact band")
+
+
+# --------------------------------------------------------------------------
+# fluid fields
+# --------------------------------------------------------------------------
+
+def face_coords(grid: Grid, comp: int):
+    """Sample coordinates of MAC component `comp` (0=u,1=v,2=w) as 1-D axes."""
+    n = [grid.nx, grid.ny, grid.nz]
+    axes = []
+    for a in range(3):
+        if a == comp:
+            axes.append(grid.origin[a] + np.arange(n[a] + 1) * grid.dx)
+        else:
+            axes.append(grid.origin[a] + (np.arange(n[a]) + 0.5) * grid.dx)
+    return axes
+
+
+def centre_coords(grid: Grid):
+    n = [grid.nx, grid.ny, grid.nz]
+    return [grid.origin[a] + (np.arange(n[a]) + 0.5) * grid.dx for a in range(3)]
+
+
+def _flat(arr3):
+    """(X, Y, Z) array -> x-fastest flat float32."""
+    return np.ascontiguousarray(np.transpose(arr3, (2, 1, 0))).ravel().astype(np.float32)
+
+
+def zero_wall_normal(u, vf, wf, grid):
+    """Solid walls: the wall-normal velocity on boundary faces is zero."""
+    nx, ny, nz = grid.nx, grid.ny, grid.nz
+    u3 = u.reshape(nz, ny, nx + 1)
+    u3[:, :, 0] = 0
+    u3[:, :, nx] = 0
+    v3 = vf.reshape(nz, ny + 1, nx)
+    v3[:, 0, :] = 0
+    v3[:, ny, :] = 0
+    w3 = wf.reshape(nz + 1, ny, nx)
+    w3[0] = 0
+    w3[nz] = 0
+    return u, vf, wf
+
+
+def uniform_noise_velocity(grid: Grid, gen, amp):
+    nx, ny, nz = grid.nx, grid.ny, grid.nz
+    u = gen.uniform(-amp, amp, size=(nx + 1) * ny * nz).astype(np.float32)
+    vf = gen.uniform(-amp, amp, size=nx * (ny + 1) * nz).astype(np.float32)
+    wf = gen.uniform(-amp, amp, size=nx * ny * (nz + 1)).astype(np.float32)
+    return zero_wall_normal(u, vf, wf, grid)
+
+
+def fourier_velocity(grid: Grid, gen, n_modes, kmax, scale_to, scale_kind="max"):
+    """Divergence-free sum of random Fourier modes a_m sin(k_m . x + phi_m),
+    a_m orthogonal to k_m, k_m = 2 pi (integer vector in 1..kmax).
+
+    Evaluated separably per mode: sin(A+B+C) expanded into products of 1-D
+    factors. Scaled so that the max (or RMS) speed over the cell centres
+    equals `scale_to`."""
+    L = grid.extent
+    ks = gen.integers(1, kmax + 1, size=(n_modes, 3)) * (2.0 * np.pi) / L
+    ks *= gen.choice([-1.0, 1.0], size=(n_modes, 3))
+    ph = gen.uniform(0, 2 * np.pi, size=n_modes)
+    amps = np.empty((n_modes, 3))
+    for m in range(n_modes):
+        a = gen.normal(size=3)
+        kh = ks[m] / np.linalg.norm(ks[m])
+        a -= a.dot(kh) * kh
+        amps[m] = a / np.linalg.norm(a)
+
+    def evaluate(axes, comp):
+        out = np.zeros((axes[0].size, axes[1].size, axes[2].size), dtype=np.float64)
+        for m in range(n_modes):
+            A = ks[m, 0] * axes[0] + ph[m]
+            B = ks[m, 1] * axes[1]
+            C = ks[m, 2] * axes[2]
+            sA, cA, sB, cB, sC, cC = np.sin(A), np.cos(A), np.sin(B), np.cos(B), np.sin(C), np.cos(C)
+            term = (np.einsum("i,j,k->ijk", sA, cB, cC) + np.einsum("i,j,k->ijk", cA, sB, cC)
+                    + np.einsum("i,j,k->ijk", cA, cB, sC) - np.einsum("i,j,k->ijk", sA, sB, sC))
+            out += amps[m, comp] * term
+        return out
+
+    cc = centre_coords(grid)
+    speed2 = sum(evaluate(cc, c) ** 2 for c in range(3))
+    s = scale_to / (np.sqrt(speed2.max()) if scale_kind == "max" else np.sqrt(speed2.mean()))
+    u = _flat(evaluate(face_coords(grid, 0), 0) * s)
+    vf = _flat(evaluate(face_coords(grid, 1), 1) * s)
+    wf = _flat(evaluate(face_coords(grid, 2), 2) * s)
+    return zero_wall_normal(u, vf, wf, grid)
+
+
+def shear_velocity(grid: Grid, rate):
+    """u_x = rate * z on x-faces, v = w = 0."""
+    ax = face_coords(grid, 0)
+    u3 = np.broadcast_to(rate * ax[2][None, None, :], (ax[0].size, ax[1].size, ax[2].size))
+    u = _flat(u3)
+    vf = np.zeros(grid.nx * (grid.ny + 1) * grid.nz, np.float32)
+    wf = np.zeros(grid.nx * grid.ny * (grid.nz + 1), np.float32)
+    return zero_wall_normal(u, vf, wf, grid)
+
+
+def hydrostatic_pressure(grid: Grid, rho_f, g=9.8):
+    """p = rho_f g (H - z) at cell centres, free surface at the top of the box."""
+    cc = centre_coords(grid)
+    H = grid.origin[2] + grid.nz * grid.dx
+    p3 = np.broadcast_to(rho_f * g * (H - cc[2])[None, None, :], (grid.nx, grid.ny, grid.nz))
+    return _flat(p3)
+
+
+def box_fluid_fraction(grid: Grid, lo, hi, phi):
+    """Given fluid fraction: 1 - phi in cells whose centre lies inside the
+    packing's bounding box [lo, hi], 1 elsewhere."""
+    cc = centre_coords(grid)
+    inside = [(cc[a] >= lo[a]) & (cc[a] <= hi[a]) for a in range(3)]
+    m = inside[0][:, None, None] & inside[1][None, :, None] & inside[2][None, None, :]
+    return _flat(np.where(m, 1.0 - phi, 1.0))
+
+
+# --------------------------------------------------------------------------
+# configurations
+# --------------------------------------------------------------------------
+
+def _finish(name, grid, params, K, x, r, v, u, vf, wf, p, af, target=None, note=""):
+    cell, q = encode_positions(x, grid)
+    return Problem(name=name, grid=grid, params=params, K=K, cell=cell, q=q,
+                   r=np.asarray(r, np.float32), v=np.asarray(v, np.float32),
+                   u=u, vf=vf, wf=wf, p=p, alpha_f=af, target=target, note=note)
+
+
+def plain_fp64(seed=1, n_side=20):
+    """8,000 monodisperse granules (r = 0.004) on a jittered simple-cubic
+    lattice (spacing 2.2 r, jitter U[-0.05 r, 0.05 r]^3) in the lower half of
+    a unit cube with a 32^3 MAC grid; fluid velocity iid U[-0.1, 0.1] on the
+    faces, hydrostatic pressure, 10 substeps of 1e-5 s."""
+    r0 = 0.004
+    grid = Grid(32, 32, 32, 1.0 / 32, k_contact=contact_k(1.0 / 32, r0))
+    spacing = 2.2 * r0
+    span = (n_side - 1) * spacing
+    start = np.array([0.5 - span / 2, 0.5 - span / 2, 1.1 * r0])
+    x = cubic_lattice((n_side,) * 3, spacing, start)
+    gen = rng(seed, STREAM_POS)
+    x = x + gen.uniform(-0.05 * r0, 0.05 * r0, size=x.shape)
+    n = x.shape[0]
+    r = np.full(n, r0, np.float32)
+    v = np.zeros((n, 3), np.float32)
+    u, vf, wf = uniform_noise_velocity(grid, rng(seed, STREAM_FLUID), 0.1)
+    params = Params(dt_sub=1e-5, dt_fluid=10 * 1e-5)
+    p = hydrostatic_pressure(grid, params.rho_f)
+    phi = (4.0 / 3.0 * np.pi * r0 ** 3) / spacing ** 3
+    af = box_fluid_fraction(grid, x.min(0) - r0, x.max(0) + r0, phi)
+    return _finish("plain_fp64_8k", grid, params, 10, x, r, v, u, vf, wf, p, af)
+
+
+def dam_break(seed=2, n=1_000_000):
+    """1,000,000 granules (r = 0.0015) on an FCC lattice at volume fraction
+    0.55 (nearest neighbour 2.208 r, jitter 0.05 r) filling the 0.3 x 1.0
+    footprint of a corner column upwards from the floor; 128^3 grid; smooth
+    divergence-free noise (8 modes, max speed 0.5 m/s); 100 substeps of 2e-5 s.
+
+    The column 0.3 x 1.0 x 0.5 at volume fraction 0.55 would hold about
+    5.8M granules, more than the 1M asked for, so the column is filled from
+    the floor until 1M granules are placed (height about 0.086)."""
+    r0 = 0.0015
+    dx = 1.0 / 128
+    grid = Grid(128, 128, 128, dx, k_contact=contact_k(dx, r0))
+    lo = np.array([1.1 * r0, 1.1 * r0, 1.1 * r0])
+    hi = np.array([0.3 - 1.1 * r0, 1.0 - 1.1 * r0, 0.5])
+    x = fcc_fill(lo, hi, 2.208 * r0, n)
+    gen = rng(seed, STREAM_POS)
+    x = x + gen.uniform(-0.05 * r0, 0.05 * r0, size=x.shape)
+    r = np.full(n, r0, np.float32)
+    v = np.zeros((n, 3), np.float32)
+    u, vf, wf = fourier_velocity(grid, rng(seed, STREAM_FLUID), 8, 4, 0.5, "max")
+    params = Params(dt_sub=2e-5, dt_fluid=100 * 2e-5)
+    p = hydrostatic_pressure(grid, params.rho_f)
+    af = box_fluid_fraction(grid, x.min(0) - r0, x.max(0) + r0, 0.55)
+    return _finish("dam_break_1m", grid, params, 100, x, r, v, u, vf, wf, p, af)
+
+
+def differentiable_window(seed=4, n=100_000, r0=0.002, grid_n=64):
+    """100,000 granules (r = 0.002) in a loose packing at volume fraction 0.3:
+    a simple-cubic lattice of spacing (V/0.3)^(1/3) with uniform jitter
+    +-0.2 r per coordinate, in a cube centred in x, y and resting on the
+    floor; initial velocities iid U[-0.01, 0.01]; 64^3 grid with smooth noise
+    (amplitude 0.1 m/s); 50 substeps of 2e-5 s; target cloud = initial
+    positions + N(0, (0.5 r)^2)."""
+    dx = 1.0 / grid_n
+    grid = Grid(grid_n, grid_n, grid_n, dx, k_contact=contact_k(dx, r0))
+    vol = 4.0 / 3.0 * np.pi * r0 ** 3
+    spacing = (vol / 0.3) ** (1.0 / 3.0)
+    side = int(math.ceil(n ** (1.0 / 3.0)))
+    x = cubic_lattice((side, side, side), spacing, (0.0, 0.0, 0.0))[:n]
+    span = (side - 1) * spacing
+    x[:, 0] += 0.5 - span / 2
+    x[:, 1] += 0.5 - span / 2
+    x[:, 2] += 1.25 * r0
+    gen = rng(seed, STREAM_POS)
+    x = x + gen.uniform(-0.2 * r0, 0.2 * r0, size=x.shape)
+    r = np.full(n, r0, np.float32)
+    v = rng(seed, STREAM_VEL).uniform(-0.01, 0.01, size=(n, 3)).astype(np.float32)
+    u, vf, wf = fourier_velocity(grid, rng(seed, STREAM_FLUID), 8, 4, 0.1, "max")
+    params = Params(dt_sub=2e-5, dt_fluid=50 * 2e-5)
+    p = hydrostatic_pressure(grid, params.rho_f)
+    af = box_fluid_fraction(grid, x.min(0) - r0, x.max(0) + r0, 0.3)
+    prob = _finish("diff_window_100k", grid, params, 50, x, r, v, u, vf, wf, p, af)
+    xe = prob.positions()
+    prob.target = xe + rng(seed, STREAM_TARGET).normal(0.0, 0.5 * r0, size=xe.shape)
+    return prob
+
+
+def dense_block(seed=11, n_side=(8, 8, 8), r0=0.004, nn_factor=1.98, jitter=0.01, grid_n=32,
+                poly=0.0, fluid_amp=0.1, K=10, dt=1e-5):
+    """Parity case with real contacts: an FCC block whose nearest-neighbour
+    distance is `nn_factor` * r (so neighbours overlap by about (2 - nn_factor)
+    r, i.e. 2% of r by default), jittered, standing on the floor next to the x = 0 wall, so that pair
+    forces, wall forces, Coulomb capping and the dashpot all take part.
+
+    Optional polydispersity: radii scaled by exp(poly * N(0,1)), clipped to
+    [0.5, 2] x r0 then capped so the contact cell still holds 2 r_max."""
+    nside = np.array(n_side)
+    nn = nn_factor * r0           # nearest-neighbour distance; overlap (2 - nn_factor) r
+    a = nn * math.sqrt(2.0)
+    lo = np.array([0.985 * r0, 0.25, 0.985 * r0])
+    hi = lo + (nside - 1) * a + 0.75 * a
+    x = fcc_fill(lo, hi, nn, None)
+    gen = rng(seed, STREAM_POS)
+    n = x.shape[0]
+    if poly > 0:
+        rr = r0 * np.exp(poly * rng(seed, STREAM_RAD).normal(size=n))
+        r = np.clip(rr, 0.5 * r0, 1.2 * r0)
+    else:
+        r = np.full(n, r0)
+    r = r.astype(np.float32)
+    dxg = 1.0 / grid_n
+    grid = Grid(grid_n, grid_n, grid_n, dxg, k_contact=contact_k(dxg, float(r.max())))
+    x = x + gen.uniform(-jitter * r0, jitter * r0, size=x.shape)
+    x = _clear_band(x, r.astype(np.float64), grid, gen, jitter * r0, 1e-5 * float(r.min()))
+    v = rng(seed, STREAM_VEL).uniform(-0.05, 0.05, size=(n, 3)).astype(np.float32)
+    u, vf, wf = uniform_noise_velocity(grid, rng(seed, STREAM_FLUID), fluid_amp)
+    params = Params(dt_sub=dt, dt_fluid=K * dt)
+    p = hydrostatic_pressure(grid, params.rho_f)
+    af = box_fluid_fraction(grid, x.min(0) - r0, x.max(0) + r0, 0.7)
+    return _finish("dense_block", grid, params, K, x, r, v, u, vf, wf, p, af)
+
+
+def random_cloud(seed=21, n=2000, r0=0.004, grid_n=16, fluid_amp=0.2, K=10, dt=1e-5, phi=0.35):
+    """Small random cloud with overlaps: a simple-cubic lattice at volume
+    fraction `phi` with uniform jitter of +-0.35 lattice spacings, after which
+    one granule of every pair closer than 1.9 r is dropped (overlaps stay
+    below 5% of r). The brute-force O(N^2) enumeration is cheap at this size."""
+    dxg = 1.0 / grid_n
+    grid = Grid(grid_n, grid_n, grid_n, dxg, k_contact=contact_k(dxg, r0))
+    gen = rng(seed, STREAM_POS)
+    spacing = (4 / 3 * np.pi * r0 ** 3 / phi) ** (1 / 3)
+    side = int(math.ceil((1.3 * n) ** (1 / 3)))
+    x = cubic_lattice((side, side, side), spacing, (0.3, 0.3, 1.05 * r0 + 0.35 * spacing))
+    x = x + gen.uniform(-0.35 * spacing, 0.35 * spacing, size=x.shape)
+    r = np.full(x.shape[0], r0)
+    while True:
+        i, j, d = pairs_within(x, r, 0.0)
+        bad = np.unique(i[d < 1.9 * r0])
+        if bad.size == 0:
+            break
+        x = np.delete(x, bad, axis=0)
+        r = r[: x.shape[0]]
+    x = x[:n]
+    n = x.shape[0]
+    r = np.full(n, r0, np.float32)
+    x = _clear_band(x, r.astype(np.float64), grid, gen, 0.01 * r0, 1e-5 * r0)
+    v = rng(seed, STREAM_VEL).uniform(-0.05, 0.05, size=(n, 3)).astype(np.float32)
+    u, vf, wf = uniform_noise_velocity(grid, rng(seed, STREAM_FLUID), fluid_amp)
+    params = Params(dt_sub=dt, dt_fluid=K * dt)
+    p = hydrostatic_pressure(grid, params.rho_f)
+    af = box_fluid_fraction(grid, x.min(0) - r0, x.max(0) + r0, 1.0 - phi)
+    return _finish("random_cloud", grid, params, K, x, r, v, u, vf, wf, p, af)
+
+
+def make(name: str, **kw) -> Problem:
+    table = {
+        "plain_fp64_8k": plain_fp64,
+        "dam_break_1m": dam_break,
+        "diff_window_100k": differentiable_window,
+        "dense_block": dense_block,
+        "random_cloud": random_cloud,
+    }
+    return table[name](**kw)

@@ -1,0 +1,641 @@
+/*
+ * gic_oracle.c -- plain, slow, single-threaded FP64 oracle for the per-substep
+ * granule-grid coupling of the Granule-In-Cell method (Tang et al., "The
+ * Granule-In-Cell Method for Simulating Sand-Water Mixtures", TOG 2025).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may call, link or
+ * load this file: only the test-suite, the smoke check and the benchmark's
+ * CPU-baseline leg use it.  It shares no code, header or constant with the
+ * CUDA library; it has its own parameter structs and reads the canonical
+ * input encoding itself.
+ *
+ * Everything is FP64 and uses ABSOLUTE positions.  Granules are kept in their
+ * original order; the cell sort is a separate function (or_sort) used only to
+ * check the GPU's sort, because ordering does not change what the substep
+ * computes.
+ *
+ * One substep follows Algorithm 2 (SandSubstep) of the paper, in its order:
+ *   CalCoupling   -> or_g2p        (Sec. 3.3 Eqs. 5a-5c, Sec. 5.2)
+ *   TransferCoupling -> or_p2g     (Sec. 5.2 "Exchange Momentum"; alpha_s of Sec. 5.1)
+ *   CollisionHandling -> or_contact (Sec. 3.1 contact law, Eq. k_n)
+ *   MoveParticle  -> or_integrate  (Sec. 5.2 Eq. "sand kine", symplectic Euler Sec. 4)
+ * The contact force only feeds MoveParticle, and the exchange force needs the
+ * granule's acceleration (virtual-mass term), so or_run evaluates contact and
+ * coupling first, integrates, then transfers; the values are identical to the
+ * paper's ordering because none of these steps reads another's output except
+ * MoveParticle and the transfer.
+ *
+ * Readings taken where the paper is silent or ambiguous (listed in full in the
+ * design notes of the repository):
+ *  - drag prefactor: F_d = c_drag * pi r^2 rho_f |dv| dv (c_drag = 0.22 default,
+ *    i.e. one half of the drag coefficient 0.44 of Sec. 6 "Parameters");
+ *  - normal force: linear spring k_n * overlap plus a dashpot -c_n v_n with
+ *    c_n = 2 zeta sqrt(k_n m_eff), not clamped at zero;
+ *  - tangential force: f_t = -k_t v_t with k_t = kt_over_cn * c_n, capped at
+ *    mu |F_n| (Sec. 3.1: tan(phi) = mu), memoryless;
+ *  - polydisperse radii generalise 2r to r_i + r_j;
+ *  - interpolation kernel N: trilinear tent on the MAC samples; a point beyond
+ *    the first/last sample takes the end sample's value (G2P), and P2G puts
+ *    the whole weight on that end sample (the transpose);
+ *  - grad p on an x-face i is (p_i - p_{i-1}) / dx, boundary faces copy the
+ *    adjacent interior face;
+ *  - dv_f/dt = g - grad p / rho_f (the F_s / (rho alpha_f) term of Eq.
+ *    momentum4 is unknown during the sand step and dropped);
+ *  - exchange force per granule f = F_p + F_d + m_a (a_f - a_s), scattered at
+ *    the substep's starting position, scaled by -dt'/dt;
+ *  - walls: the six box planes, infinite mass, at rest, same contact law.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_PI 3.14159265358979323846
+
+/* status bits reported by the oracle */
+#define OR_OUT_OF_DOMAIN 1u
+#define OR_COINCIDENT 2u
+#define OR_NONFINITE 4u
+
+typedef struct {
+  int nx, ny, nz; /* MAC cells per axis */
+  int k;          /* contact cells per MAC cell and axis: h_c = dx / k */
+  double dx;
+  double ox, oy, oz; /* domain origin; the domain is [o, o + n dx] */
+} or_grid;
+
+typedef struct {
+  double rho_s, rho_f, k_n, zeta, kt_over_cn, mu, c_drag;
+  double gx, gy, gz;
+  double dt;       /* sand substep dt' */
+  double dt_fluid; /* fluid step dt (exchange scale dt'/dt) */
+  int virtual_mass, walls;
+} or_params;
+
+/* ------------------------------------------------------------------------ */
+/* canonical input encoding                                                 */
+/* ------------------------------------------------------------------------ */
+
+/* x = origin + (cell + q / 2^30) * h_c */
+void or_decode(const or_grid* G, int64_t n, const int32_t* cell, const uint32_t* q, double* x) {
+  double hc = G->dx / G->k;
+  double o[3] = {G->ox, G->oy, G->oz};
+  for (int64_t i = 0; i < n; ++i)
+    for (int a = 0; a < 3; ++a)
+      x[3 * i + a] = o[a] + ((double)cell[3 * i + a] + (double)q[3 * i + a] / 1073741824.0) * hc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Morton cell sort (the neighbour search the method needs, Sec. 3.1:       */
+/* contacts only between granules closer than 2r)                           */
+/* ------------------------------------------------------------------------ */
+
+/* contact cell of each granule: floor((x - o) / h_c), clamped into the grid */
+void or_cells(const or_grid* G, int64_t n, const double* x, int32_t* c) {
+  double hc = G->dx / G->k;
+  double o[3] = {G->ox, G->oy, G->oz};
+  int nc[3] = {G->nx * G->k, G->ny * G->k, G->nz * G->k};
+  for (int64_t i = 0; i < n; ++i)
+    for (int a = 0; a < 3; ++a) {
+      double f = floor((x[3 * i + a] - o[a]) / hc);
+      int ci = !(f >= 0.0) ? 0 : (f > nc[a] - 1 ? nc[a] - 1 : (int)f); /* NaN -> 0 */
+      c[3 * i + a] = ci;
+    }
+}
+
+/* Morton key: bit b of x goes to bit 3b, of y to 3b+1, of z to 3b+2 */
+uint64_t or_morton(uint32_t ix, uint32_t iy, uint32_t iz) {
+  uint64_t key = 0;
+  for (int b = 0; b < 21; ++b) {
+    key |= (uint64_t)((ix >> b) & 1u) << (3 * b);
+    key |= (uint64_t)((iy >> b) & 1u) << (3 * b + 1);
+    key |= (uint64_t)((iz >> b) & 1u) << (3 * b + 2);
+  }
+  return key;
+}
+
+typedef struct {
+  uint64_t key;
+  int64_t idx;
+} or_keyidx;
+
+static int cmp_keyidx(const void* a, const void* b) {
+  const or_keyidx* x = (const or_keyidx*)a;
+  const or_keyidx* y = (const or_keyidx*)b;
+  if (x->key != y->key) return x->key < y->key ? -1 : 1;
+  if (x->idx != y->idx) return x->idx < y->idx ? -1 : 1;
+  return 0;
+}
+
+/* Stable sort of the granules by the Morton key of their contact cell.
+ * perm[k] = index (in the input order) of the k-th granule after sorting;
+ * ties keep input order.  keys[k] = key of that granule. */
+void or_sort(int64_t n, const int32_t* c, int64_t* perm, uint64_t* keys) {
+  or_keyidx* t = (or_keyidx*)malloc(sizeof(or_keyidx) * (size_t)(n > 0 ? n : 1));
+  for (int64_t i = 0; i < n; ++i) {
+    t[i].key = or_morton((uint32_t)c[3 * i], (uint32_t)c[3 * i + 1], (uint32_t)c[3 * i + 2]);
+    t[i].idx = i;
+  }
+  qsort(t, (size_t)n, sizeof(or_keyidx), cmp_keyidx);
+  for (int64_t i = 0; i < n; ++i) {
+    perm[i] = t[i].idx;
+    keys[i] = t[i].key;
+  }
+  free(t);
+}
+
+/* Run-length table of the sorted keys: one row (key, start, count) per
+ * occupied cell, in key order.  Returns the number of occupied cells. */
+int64_t or_cell_table(int64_t n, const uint64_t* keys, uint64_t* cell_key, int64_t* start, int64_t* count) {
+  int64_t m = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    if (i == 0 || keys[i] != keys[i - 1]) {
+      cell_key[m] = keys[i];
+      start[m] = i;
+      count[m] = 0;
+      ++m;
+    }
+    count[m - 1] += 1;
+  }
+  return m;
+}
+
+/* ------------------------------------------------------------------------ */
+/* DEM contact (Sec. 3.1, Eq. k_n, with the dashpot / tangential readings)  */
+/* ------------------------------------------------------------------------ */
+
+static double granule_volume(double r) { return 4.0 / 3.0 * OR_PI * r * r * r; }
+
+/* Force on granule i from partner j.  xij = x_i - x_j, vij = v_i - v_j.
+ * mj <= 0 marks a wall (infinite mass).  Returns 1 if in contact, 0 if not,
+ * -1 for coincident centres (skipped). */
+static int pair_force(const or_params* P, const double xij[3], const double vij[3], double ri, double rj,
+                      double mi, double mj, double F[3]) {
+  double d2 = xij[0] * xij[0] + xij[1] * xij[1] + xij[2] * xij[2];
+  double R = ri + rj;
+  if (!(d2 < R * R)) return 0;
+  double d = sqrt(d2);
+  if (d == 0.0) return -1;
+  double n[3] = {xij[0] / d, xij[1] / d, xij[2] / d};
+  double overlap = R - d;
+  double meff = mj > 0.0 ? mi * mj / (mi + mj) : mi;
+  double cn = 2.0 * P->zeta * sqrt(P->k_n * meff);
+  double vn = vij[0] * n[0] + vij[1] * n[1] + vij[2] * n[2];
+  double Fn = P->k_n * overlap - cn * vn; /* signed normal magnitude */
+  double vt[3] = {vij[0] - vn * n[0], vij[1] - vn * n[1], vij[2] - vn * n[2]};
+  double kt = P->kt_over_cn * cn;
+  double ft[3] = {-kt * vt[0], -kt * vt[1], -kt * vt[2]};
+  double ftn = sqrt(ft[0] * ft[0] + ft[1] * ft[1] + ft[2] * ft[2]);
+  double cap = P->mu * fabs(Fn);
+  double s = 1.0; /* F_t = min(|f_t|, cap) * f_t / |f_t| */
+  if (ftn > cap) s = cap / ftn;
+  for (int a = 0; a < 3; ++a) F[a] = Fn * n[a] + s * ft[a];
+  return 1;
+}
+
+/* wall contacts of one granule: the six planes of the box */
+static void wall_forces(const or_grid* G, const or_params* P, const double* x, const double* v, double r, double m,
+                        double F[3], uint32_t* status) {
+  double lo[3] = {G->ox, G->oy, G->oz};
+  int nn[3] = {G->nx, G->ny, G->nz};
+  for (int a = 0; a < 3; ++a) {
+    double hi = lo[a] + nn[a] * G->dx;
+    for (int side = 0; side < 2; ++side) {
+      double gap = side == 0 ? x[a] - lo[a] : hi - x[a];
+      if (gap >= r) continue;
+      if (gap <= 0.0) {
+        *status |= OR_OUT_OF_DOMAIN;
+        continue;
+      }
+      double xij[3] = {0, 0, 0};
+      xij[a] = side == 0 ? gap : -gap;
+      double f[3];
+      pair_force(P, xij, v, r, 0.0, m, 0.0, f);
+      for (int b = 0; b < 3; ++b) F[b] += f[b];
+    }
+  }
+}
+
+/* uniform bins of width >= 2 r_max for the oracle's own neighbour search */
+typedef struct {
+  int nb[3];
+  double hb, lo[3];
+  int64_t *head, *next; /* linked lists, ascending index within a bin */
+} or_bins;
+
+static void bins_build(or_bins* B, const or_grid* G, int64_t n, const double* x, const double* r) {
+  double rmax = 0;
+  for (int64_t i = 0; i < n; ++i) rmax = r[i] > rmax ? r[i] : rmax;
+  double L[3] = {G->nx * G->dx, G->ny * G->dx, G->nz * G->dx};
+  B->lo[0] = G->ox;
+  B->lo[1] = G->oy;
+  B->lo[2] = G->oz;
+  B->hb = 2.0 * rmax;
+  if (B->hb <= 0) B->hb = G->dx;
+  int64_t tot = 1;
+  for (int a = 0; a < 3; ++a) {
+    B->nb[a] = (int)floor(L[a] / B->hb); /* bin width L / nb >= 2 r_max */
+    if (B->nb[a] < 1) B->nb[a] = 1;
+    if (B->nb[a] > 2048) { /* coarse bins are still correct, only slower */
+      B->nb[a] = 2048;
+    }
+    tot *= B->nb[a];
+  }
+  B->head = (int64_t*)malloc(sizeof(int64_t) * (size_t)tot);
+  B->next = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+  for (int64_t b = 0; b < tot; ++b) B->head[b] = -1;
+  /* insert in descending order so each list is ascending */
+  for (int64_t i = n - 1; i >= 0; --i) {
+    int bi[3];
+    for (int a = 0; a < 3; ++a) {
+      double w = L[a] / B->nb[a];
+      double f = floor((x[3 * i + a] - B->lo[a]) / w);
+      bi[a] = !(f >= 0.0) ? 0 : (f >= B->nb[a] - 1 ? B->nb[a] - 1 : (int)f); /* NaN -> bin 0 */
+    }
+    int64_t lin = bi[0] + (int64_t)B->nb[0] * (bi[1] + (int64_t)B->nb[1] * bi[2]);
+    B->next[i] = B->head[lin];
+    B->head[lin] = i;
+  }
+}
+
+static void bins_free(or_bins* B) {
+  free(B->head);
+  free(B->next);
+}
+
+static void bin_of(const or_bins* B, const or_grid* G, const double* xi, int bi[3]) {
+  double L[3] = {G->nx * G->dx, G->ny * G->dx, G->nz * G->dx};
+  for (int a = 0; a < 3; ++a) {
+    double w = L[a] / B->nb[a];
+    double f = floor((xi[a] - B->lo[a]) / w);
+    bi[a] = !(f >= 0.0) ? 0 : (f >= B->nb[a] - 1 ? B->nb[a] - 1 : (int)f); /* NaN -> bin 0 */
+  }
+}
+
+/* Enumerate the contact pairs i < j (d_ij < r_i + r_j).  brute != 0: O(N^2)
+ * double loop; else the binned search.  Writes up to max_pairs pairs and
+ * returns the total count. */
+int64_t or_contact_pairs(const or_grid* G, int64_t n, const double* x, const double* r, int brute, int64_t max_pairs,
+                         int64_t* pairs) {
+  int64_t m = 0;
+  if (brute) {
+    for (int64_t i = 0; i < n; ++i)
+      for (int64_t j = i + 1; j < n; ++j) {
+        double d2 = 0;
+        for (int a = 0; a < 3; ++a) {
+          double t = x[3 * i + a] - x[3 * j + a];
+          d2 += t * t;
+        }
+        double R = r[i] + r[j];
+        if (d2 < R * R) {
+          if (m < max_pairs) {
+            pairs[2 * m] = i;
+            pairs[2 * m + 1] = j;
+          }
+          ++m;
+        }
+      }
+    return m;
+  }
+  or_bins B;
+  bins_build(&B, G, n, x, r);
+  for (int64_t i = 0; i < n; ++i) {
+    int bi[3];
+    bin_of(&B, G, x + 3 * i, bi);
+    for (int dz = -1; dz <= 1; ++dz)
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+          int b[3] = {bi[0] + dx, bi[1] + dy, bi[2] + dz};
+          if (b[0] < 0 || b[1] < 0 || b[2] < 0 || b[0] >= B.nb[0] || b[1] >= B.nb[1] || b[2] >= B.nb[2]) continue;
+          int64_t lin = b[0] + (int64_t)B.nb[0] * (b[1] + (int64_t)B.nb[1] * b[2]);
+          for (int64_t j = B.head[lin]; j >= 0; j = B.next[j]) {
+            if (j <= i) continue;
+            double d2 = 0;
+            for (int a = 0; a < 3; ++a) {
+              double t = x[3 * i + a] - x[3 * j + a];
+              d2 += t * t;
+            }
+            double R = r[i] + r[j];
+            if (d2 < R * R) {
+              if (m < max_pairs) {
+                pairs[2 * m] = i;
+                pairs[2 * m + 1] = j;
+              }
+              ++m;
+            }
+          }
+        }
+  }
+  bins_free(&B);
+  return m;
+}
+
+/* Contact force on every granule: sum of pair forces over all partners with
+ * d < r_i + r_j, plus the walls.  brute != 0 uses the O(N^2) loop. */
+void or_contact(const or_grid* G, const or_params* P, int64_t n, const double* x, const double* v, const double* r,
+                int brute, double* F, uint32_t* status) {
+  or_bins B;
+  if (!brute) bins_build(&B, G, n, x, r);
+  for (int64_t i = 0; i < n; ++i) {
+    double Fi[3] = {0, 0, 0};
+    double mi = P->rho_s * granule_volume(r[i]);
+    const double* xi = x + 3 * i;
+    const double* vi = v + 3 * i;
+    if (brute) {
+      for (int64_t j = 0; j < n; ++j) {
+        if (j == i) continue;
+        double xij[3], vij[3], f[3];
+        for (int a = 0; a < 3; ++a) {
+          xij[a] = xi[a] - x[3 * j + a];
+          vij[a] = vi[a] - v[3 * j + a];
+        }
+        int c = pair_force(P, xij, vij, r[i], r[j], mi, P->rho_s * granule_volume(r[j]), f);
+        if (c < 0) *status |= OR_COINCIDENT;
+        if (c > 0)
+          for (int a = 0; a < 3; ++a) Fi[a] += f[a];
+      }
+    } else {
+      int bi[3];
+      bin_of(&B, G, xi, bi);
+      for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+          for (int dx = -1; dx <= 1; ++dx) {
+            int b[3] = {bi[0] + dx, bi[1] + dy, bi[2] + dz};
+            if (b[0] < 0 || b[1] < 0 || b[2] < 0 || b[0] >= B.nb[0] || b[1] >= B.nb[1] || b[2] >= B.nb[2]) continue;
+            int64_t lin = b[0] + (int64_t)B.nb[0] * (b[1] + (int64_t)B.nb[1] * b[2]);
+            for (int64_t j = B.head[lin]; j >= 0; j = B.next[j]) {
+              if (j == i) continue;
+              double xij[3], vij[3], f[3];
+              for (int a = 0; a < 3; ++a) {
+                xij[a] = xi[a] - x[3 * j + a];
+                vij[a] = vi[a] - v[3 * j + a];
+              }
+              int c = pair_force(P, xij, vij, r[i], r[j], mi, P->rho_s * granule_volume(r[j]), f);
+              if (c < 0) *status |= OR_COINCIDENT;
+              if (c > 0)
+                for (int a = 0; a < 3; ++a) Fi[a] += f[a];
+            }
+          }
+    }
+    if (P->walls) wall_forces(G, P, xi, vi, r[i], mi, Fi, status);
+    for (int a = 0; a < 3; ++a) F[3 * i + a] = Fi[a];
+  }
+  if (!brute) bins_free(&B);
+}
+
+/* ------------------------------------------------------------------------ */
+/* interpolation kernel N (trilinear tent on MAC samples), Sec. 5.1 / 5.2   */
+/* ------------------------------------------------------------------------ */
+
+/* One axis: samples at (k + s) dx, k = 0..ns-1.  Lower sample i0 and the
+ * weight t of sample i0+1 (1 - t on i0).  A point beyond the first or last
+ * sample is clamped onto it. */
+static void axis_stencil(double xg, double s, int ns, int* i0, double* t) {
+  double f = xg - s;
+  if (!(f > 0.0)) { /* also NaN */
+    *i0 = 0;
+    *t = 0.0;
+    return;
+  }
+  if (f >= (double)(ns - 1)) {
+    *i0 = ns - 2;
+    *t = 1.0;
+    return;
+  }
+  double fl = floor(f);
+  *i0 = (int)fl;
+  *t = f - fl;
+}
+
+/* A sampled MAC field: ns samples per axis, sample offsets s (in cells). */
+typedef struct {
+  int ns[3];
+  double s[3];
+} or_layout;
+
+static or_layout layout_of(const or_grid* G, int comp) {
+  /* comp 0,1,2: u, v, w faces; 3: cell centres */
+  or_layout L;
+  int n[3] = {G->nx, G->ny, G->nz};
+  for (int a = 0; a < 3; ++a) {
+    L.ns[a] = n[a] + (a == comp ? 1 : 0);
+    L.s[a] = a == comp ? 0.0 : 0.5;
+  }
+  return L;
+}
+
+/* sample index (x fastest) */
+static int64_t sidx(const or_layout* L, int i, int j, int k) {
+  return i + (int64_t)L->ns[0] * (j + (int64_t)L->ns[1] * k);
+}
+
+/* weights of the 8 stencil samples of point x for layout L */
+typedef struct {
+  int i0[3];
+  double t[3];
+} or_stencil;
+
+static or_stencil stencil_at(const or_grid* G, const or_layout* L, const double* x) {
+  or_stencil S;
+  double o[3] = {G->ox, G->oy, G->oz};
+  for (int a = 0; a < 3; ++a) axis_stencil((x[a] - o[a]) / G->dx, L->s[a], L->ns[a], &S.i0[a], &S.t[a]);
+  return S;
+}
+
+static double corner_weight(const or_stencil* S, int a, int b, int c) {
+  double wx = a ? S->t[0] : 1.0 - S->t[0];
+  double wy = b ? S->t[1] : 1.0 - S->t[1];
+  double wz = c ? S->t[2] : 1.0 - S->t[2];
+  return wx * wy * wz;
+}
+
+/* Pressure gradient component `comp` on its face sample (i,j,k): (p_i - p_{i-1}) / dx
+ * along `comp`; boundary faces take the adjacent interior face's value. */
+static double grad_p_face(const or_grid* G, const double* p, int comp, int i, int j, int k) {
+  int idx[3] = {i, j, k};
+  int n[3] = {G->nx, G->ny, G->nz};
+  int c = idx[comp];
+  if (c < 1) c = 1;
+  if (c > n[comp] - 1) c = n[comp] - 1;
+  int hi[3] = {idx[0], idx[1], idx[2]};
+  int lo[3] = {idx[0], idx[1], idx[2]};
+  hi[comp] = c;
+  lo[comp] = c - 1;
+  int64_t ih = hi[0] + (int64_t)G->nx * (hi[1] + (int64_t)G->ny * hi[2]);
+  int64_t il = lo[0] + (int64_t)G->nx * (lo[1] + (int64_t)G->ny * lo[2]);
+  return (p[ih] - p[il]) / G->dx;
+}
+
+/* interpolate a plain sampled field */
+static double interp(const or_grid* G, const or_layout* L, const double* f, const double* x) {
+  or_stencil S = stencil_at(G, L, x);
+  double acc = 0.0;
+  for (int c = 0; c < 2; ++c)
+    for (int b = 0; b < 2; ++b)
+      for (int a = 0; a < 2; ++a)
+        acc += corner_weight(&S, a, b, c) * f[sidx(L, S.i0[0] + a, S.i0[1] + b, S.i0[2] + c)];
+  return acc;
+}
+
+/* interpolate grad p component comp (sampled on comp-faces) */
+static double interp_grad_p(const or_grid* G, const double* p, int comp, const double* x) {
+  or_layout L = layout_of(G, comp);
+  or_stencil S = stencil_at(G, &L, x);
+  double acc = 0.0;
+  for (int c = 0; c < 2; ++c)
+    for (int b = 0; b < 2; ++b)
+      for (int a = 0; a < 2; ++a)
+        acc += corner_weight(&S, a, b, c) * grad_p_face(G, p, comp, S.i0[0] + a, S.i0[1] + b, S.i0[2] + c);
+  return acc;
+}
+
+/* Public helper for tests: interpolate field `comp` (0..2 faces, 3 centres)
+ * at m points. */
+void or_interp(const or_grid* G, int comp, const double* f, int64_t m, const double* x, double* out) {
+  or_layout L = layout_of(G, comp);
+  for (int64_t i = 0; i < m; ++i) out[i] = interp(G, &L, f, x + 3 * i);
+}
+
+void or_interp_grad_p(const or_grid* G, const double* p, int64_t m, const double* x, double* out /*3m*/) {
+  for (int64_t i = 0; i < m; ++i)
+    for (int a = 0; a < 3; ++a) out[3 * i + a] = interp_grad_p(G, p, a, x + 3 * i);
+}
+
+/* ------------------------------------------------------------------------ */
+/* CalCoupling: G2P of fluid velocity, grad p and alpha_f (Sec. 3.3, 5.2)   */
+/* ------------------------------------------------------------------------ */
+
+/* F_fl = F_d + F_p,  F_p = -(4/3) pi r^3 grad p (Eq. gradient-force),
+ * F_d = c_drag pi r^2 rho_f |u_f - v| (u_f - v) (Eq. 5b with the drag reading),
+ * a_f = dv_f/dt = g - grad p / rho_f (Eq. momentum4 without the F_s term),
+ * alpha_f_p = alpha_f interpolated at the granule. */
+void or_g2p(const or_grid* G, const or_params* P, int64_t n, const double* x, const double* v, const double* r,
+            const double* u, const double* vf, const double* wf, const double* p, const double* af, double* F_fl,
+            double* a_f, double* alpha_f_p) {
+  or_layout Lu = layout_of(G, 0), Lv = layout_of(G, 1), Lw = layout_of(G, 2), Lc = layout_of(G, 3);
+  double g[3] = {P->gx, P->gy, P->gz};
+  for (int64_t i = 0; i < n; ++i) {
+    const double* xi = x + 3 * i;
+    double uf[3] = {interp(G, &Lu, u, xi), interp(G, &Lv, vf, xi), interp(G, &Lw, wf, xi)};
+    double gp[3];
+    for (int a = 0; a < 3; ++a) gp[a] = interp_grad_p(G, p, a, xi);
+    double V = granule_volume(r[i]);
+    double dv[3] = {uf[0] - v[3 * i], uf[1] - v[3 * i + 1], uf[2] - v[3 * i + 2]};
+    double sp = sqrt(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
+    double cd = P->c_drag * OR_PI * r[i] * r[i] * P->rho_f * sp;
+    for (int a = 0; a < 3; ++a) {
+      F_fl[3 * i + a] = cd * dv[a] - V * gp[a];
+      a_f[3 * i + a] = P->rho_f > 0.0 ? g[a] - gp[a] / P->rho_f : g[a];
+    }
+    alpha_f_p[i] = interp(G, &Lc, af, xi);
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* MoveParticle: virtual-mass symplectic Euler (Sec. 5.2 Eq. sand kine)     */
+/* ------------------------------------------------------------------------ */
+
+/* (m + m_a) a = m_a a_f + F_c + F_fl + m g,  m_a = (2/3) pi r^3 rho_f;
+ * v' = v + dt a;  x' = x + dt v';  exchange force f = F_fl + m_a (a_f - a). */
+void or_integrate(const or_grid* G, const or_params* P, int64_t n, const double* x, const double* v, const double* r,
+                  const double* F_c, const double* F_fl, const double* a_f, double* x_new, double* v_new, double* f_ex,
+                  uint32_t* status) {
+  double g[3] = {P->gx, P->gy, P->gz};
+  double lo[3] = {G->ox, G->oy, G->oz};
+  double hi[3] = {G->ox + G->nx * G->dx, G->oy + G->ny * G->dx, G->oz + G->nz * G->dx};
+  for (int64_t i = 0; i < n; ++i) {
+    double V = granule_volume(r[i]);
+    double m = P->rho_s * V;
+    double ma = P->virtual_mass ? 0.5 * P->rho_f * V : 0.0;
+    for (int a = 0; a < 3; ++a) {
+      double acc = (F_c[3 * i + a] + F_fl[3 * i + a] + m * g[a] + ma * a_f[3 * i + a]) / (m + ma);
+      double vn = v[3 * i + a] + P->dt * acc;
+      double xn = x[3 * i + a] + P->dt * vn;
+      v_new[3 * i + a] = vn;
+      x_new[3 * i + a] = xn;
+      f_ex[3 * i + a] = F_fl[3 * i + a] + ma * (a_f[3 * i + a] - acc);
+      if (!(xn >= lo[a] && xn < hi[a])) *status |= OR_OUT_OF_DOMAIN;
+      if (!isfinite(vn) || !isfinite(xn)) *status |= OR_NONFINITE;
+    }
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* TransferCoupling: P2G (Sec. 5.1 alpha_s, Sec. 5.2 exchange momentum)     */
+/* ------------------------------------------------------------------------ */
+
+/* alpha_s(c) = (1/dx^3) sum_i V_i N(x_new_i - x_c)       (written, cell centres)
+ * F_s(face) += -(dt'/dt) sum_i f_i N(x_old_i - x_face)   (accumulated, MAC faces)
+ * sums[0] = sum_c alpha_s(c) dx^3,  sums[1] = sum_i V_i */
+void or_p2g(const or_grid* G, const or_params* P, int64_t n, const double* x_old, const double* x_new, const double* r,
+            const double* f_ex, double* alpha_s, double* Fs_u, double* Fs_v, double* Fs_w, double* sums) {
+  or_layout Lc = layout_of(G, 3);
+  int64_t ncell = (int64_t)G->nx * G->ny * G->nz;
+  double dx3 = G->dx * G->dx * G->dx;
+  for (int64_t c = 0; c < ncell; ++c) alpha_s[c] = 0.0;
+  double* Fs[3] = {Fs_u, Fs_v, Fs_w};
+  double scale = -P->dt / P->dt_fluid;
+  double sumV = 0.0;
+  for (int64_t i = 0; i < n; ++i) {
+    double V = granule_volume(r[i]);
+    sumV += V;
+    or_stencil S = stencil_at(G, &Lc, x_new + 3 * i);
+    for (int c = 0; c < 2; ++c)
+      for (int b = 0; b < 2; ++b)
+        for (int a = 0; a < 2; ++a)
+          alpha_s[sidx(&Lc, S.i0[0] + a, S.i0[1] + b, S.i0[2] + c)] += V / dx3 * corner_weight(&S, a, b, c);
+    for (int comp = 0; comp < 3; ++comp) {
+      or_layout L = layout_of(G, comp);
+      or_stencil T = stencil_at(G, &L, x_old + 3 * i);
+      for (int c = 0; c < 2; ++c)
+        for (int b = 0; b < 2; ++b)
+          for (int a = 0; a < 2; ++a)
+            Fs[comp][sidx(&L, T.i0[0] + a, T.i0[1] + b, T.i0[2] + c)] +=
+                scale * f_ex[3 * i + comp] * corner_weight(&T, a, b, c);
+    }
+  }
+  double tot = 0.0;
+  for (int64_t c = 0; c < ncell; ++c) tot += alpha_s[c] * dx3;
+  sums[0] = tot;
+  sums[1] = sumV;
+}
+
+/* ------------------------------------------------------------------------ */
+/* SandSubstep loop (Algorithm 2), K substeps, state updated in place       */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  const double *u, *vf, *wf, *p, *af;
+} or_fluid;
+
+/* One substep.  Scratch arrays of 3n doubles: F_c, F_fl, a_f, f_ex, x_new,
+ * v_new; n doubles alpha_f_p. */
+static void substep(const or_grid* G, const or_params* P, const or_fluid* Fd, int64_t n, double* x, double* v,
+                    const double* r, double* alpha_s, double* Fs_u, double* Fs_v, double* Fs_w, double* sums,
+                    int brute, double* scratch, uint32_t* status) {
+  double* F_c = scratch;
+  double* F_fl = F_c + 3 * n;
+  double* a_f = F_fl + 3 * n;
+  double* f_ex = a_f + 3 * n;
+  double* x_new = f_ex + 3 * n;
+  double* v_new = x_new + 3 * n;
+  double* afp = v_new + 3 * n;
+  or_g2p(G, P, n, x, v, r, Fd->u, Fd->vf, Fd->wf, Fd->p, Fd->af, F_fl, a_f, afp);
+  or_contact(G, P, n, x, v, r, brute, F_c, status);
+  or_integrate(G, P, n, x, v, r, F_c, F_fl, a_f, x_new, v_new, f_ex, status);
+  or_p2g(G, P, n, x, x_new, r, f_ex, alpha_s, Fs_u, Fs_v, Fs_w, sums);
+  memcpy(x, x_new, sizeof(double) * 3 * (size_t)n);
+  memcpy(v, v_new, sizeof(double) * 3 * (size_t)n);
+}
+
+/* K substeps.  x, v (3n) updated in place; alpha_s is the last substep's;
+ * F_s accumulates over all K substeps (caller zeroes it); sums = last
+ * substep's conservation sums. */
+void or_run(const or_grid* G, const or_params* P, int64_t n, int K, double* x, double* v, const double* r,
+            const double* u, const double* vf, const double* wf, const double* p, const double* af, double* alpha_s,
+            double* Fs_u, double* Fs_v, double* Fs_w, double* sums, int brute, uint32_t* status) {
+  or_fluid Fd = {u, vf, wf, p, af};
+  double* scratch = (double*)malloc(sizeof(double) * (size_t)(19 * (n > 0 ? n : 1)));
+  for (int s = 0; s < K; ++s) substep(G, P, &Fd, n, x, v, r, alpha_s, Fs_u, Fs_v, Fs_w, sums, brute, scratch, status);
+  free(scratch);
+}
