@@ -1,0 +1,393 @@
+"""Benchmark of the granule-grid coupling substep on GB300.
+
+One step = one window of K substeps of Alg. 2 (sort, contact, G2P couple,
+integrate, P2G with FP64 volume fraction and conservation sums) over the
+1,000,000-granule dam-break column on a 128^3 grid (100 substeps of 2e-5 s,
+FP32 state with FP64 alpha_s accumulation), starting every step from the same
+seeded initial packing.  The metric is granule-substeps per second.
+
+Prints ONE JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+instead, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes as C
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "granule-substeps/s fwd & adjoint, FP32 vs FP64 on 1 GB300; % HBM roofline"
+UNIT = "granule-substeps/s"
+# algorithmic bytes per granule-substep of each step (FP32 path): what the
+# method must move, 12 B per 3-vector, state = 36 B
+ALGO_BYTES = {"gic_sort": 88, "gic_contact": 48, "gic_g2p_couple": 65, "gic_integrate": 120, "gic_p2g": 54}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="dam_break_1m")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true", help="skip the FP64 and adjoint variants")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------- distributed plumbing
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+
+        backend = "nccl"
+        dist.init_process_group(backend=backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(x, ws, device="cuda"):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# --------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.gpu), "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- CPU oracle sample
+
+def oracle_sample(prob, target_s, K_full):
+    """Time the FP64 oracle on a bounded sample of the workload: the first m
+    granules (the bottom of the column, contacts and walls included) for
+    K_s substeps, sized for about target_s seconds."""
+    import dataclasses
+
+    import oracle
+
+    def sub(m):
+        return dataclasses.replace(prob, cell=prob.cell[:m], q=prob.q[:m], r=prob.r[:m], v=prob.v[:m])
+
+    # calibrate on a small sample
+    m = min(prob.n, 20000)
+    t0 = time.perf_counter()
+    oracle.run(sub(m), K=2)
+    per = (time.perf_counter() - t0) / (2 * m)
+    K_s = K_full
+    m = int(min(prob.n, max(1000, target_s / (per * K_s))))
+    if m < 1000:
+        K_s = max(1, int(target_s / (per * 1000)))
+        m = 1000
+    t0 = time.perf_counter()
+    oracle.run(sub(m), K=K_s)
+    dt = time.perf_counter() - t0
+    return {"value": m * K_s / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {m} granules of the {prob.n}-granule workload, {K_s} substeps, single-threaded FP64 C",
+            "seconds": dt}
+
+
+def run_reference(args, ws, rank):
+    """--impl reference: the oracle is the reference arm (rank 0 only)."""
+    if rank != 0:
+        return
+    import gic_inputs as gi
+
+    prob = gi.make(args.workload)
+    import dataclasses
+
+    import oracle
+
+    # bounded sample per step so W + K steps finish within a few minutes
+    per_step_s = min(20.0, 150.0 / max(1, args.steps + args.warmup))
+    m = min(prob.n, 20000)
+    t0 = time.perf_counter()
+    oracle.run(dataclasses.replace(prob, cell=prob.cell[:m], q=prob.q[:m], r=prob.r[:m], v=prob.v[:m]), K=2)
+    per = (time.perf_counter() - t0) / (2 * m)
+    K_s = prob.K
+    m = int(min(prob.n, max(1000, per_step_s / (per * K_s))))
+    sub = dataclasses.replace(prob, cell=prob.cell[:m], q=prob.q[:m], r=prob.r[:m], v=prob.v[:m])
+    for _ in range(args.warmup):
+        oracle.run(sub, K=1)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.run(sub, K=K_s)
+        times.append(time.perf_counter() - t0)
+    ms = 1000 * statistics.mean(times)
+    value = m * K_s / (ms / 1000)
+    sample = f"first {m} granules of {prob.n}, {K_s} substeps per step, single-threaded FP64 C oracle"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": prob.name, "granules": prob.n, "grid": [prob.grid.nx, prob.grid.ny, prob.grid.nz],
+                       "substeps_per_step": prob.K, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- GPU arm
+
+def run_gpu(args, ws, rank, local):
+    import numpy as np
+    import torch
+
+    import gic_inputs as gi
+    from paper_2504_00745_gb300 import gic
+    from paper_2504_00745_gb300.window import Simulator
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prob = gi.make(args.workload)
+    n, K = prob.n, prob.K
+    sim = Simulator.from_problem(prob, gic.GIC_FP32, dev)
+    init = sim.A.clone()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 512 MB > L2
+
+    names = list(ALGO_BYTES)
+    ev_acc = {k: [] for k in names}
+
+    def one_step(probe=False):
+        sim.A.cell.copy_(init.cell)
+        sim.A.pos.copy_(init.pos)
+        sim.A.vel.copy_(init.vel)
+        sim.A.id.copy_(init.id)
+        flush.zero_()
+        start = torch.cuda.Event(enable_timing=True)
+        end = torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        sim.zero_transfer()
+        for s in range(K):
+            if probe:
+                sim.substep_probe(ev_acc, stream=stream)
+            else:
+                sim.substep()
+        end.record(stream)
+        return start, end
+
+    gic.gic_check_status(clear=True)
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(ws)
+    torch.cuda.synchronize()
+    l0 = gic.launch_count()
+    t_wall = time.perf_counter()
+    evs = [one_step(probe=True) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    barrier(ws)
+    wall = time.perf_counter() - t_wall
+    launches = gic.launch_count() - l0
+    clk = clocks.stop()
+    status = gic.gic_check_status(clear=True)
+    ms = statistics.mean(s.elapsed_time(e) for s, e in evs)
+    ms = max_over_ranks(ms, ws, dev)
+    value = ws * n * K / (ms / 1000.0)
+
+    # per-entry-point durations inside the timed region -> roofline of the dominant one
+    per_call = {k: statistics.mean(a.elapsed_time(b) for a, b in ev_acc[k]) for k in names if ev_acc[k]}
+    dom = max(per_call, key=per_call.get)
+    import math
+
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = ALGO_BYTES[dom] * n / (per_call[dom] / 1000.0) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": None, "kernel": dom, "peak_source": "measured" if peaks else "fallback",
+                "per_call_ms": per_call,
+                "per_call_frac": {k: ALGO_BYTES[k] * n / (v / 1000.0) / 1e9 / hbm for k, v in per_call.items()}}
+
+    # e2e through the C ABI with host buffers (copies inside the timed region)
+    e2e = run_e2e(prob, sim, gic, torch, np, dev, stream, max(1, min(args.steps, 3)))
+
+    variants = {}
+    if not args.no_variants:
+        variants["fp64_fwd"] = run_fp64(prob, gic, torch, dev, stream)
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 (fixed-point positions, f64 alpha_s)", "data": "synthetic",
+            "config": {"workload": prob.name, "granules": n, "grid": [prob.grid.nx, prob.grid.ny, prob.grid.nz],
+                       "substeps_per_step": K, "dt_sub": prob.params.dt_sub, "precision": "fp32",
+                       "l2": "flushed between steps (512 MB write), state reset to the initial packing",
+                       "wall_s": wall},
+            "roofline": roofline, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
+            "device_status": status, "variants": variants}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_sample(prob, args.cpu_seconds, K)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_e2e(prob, sim, gic, torch, np, dev, stream, steps):
+    """The K-substep window through gic_window_forward_host: pinned host
+    inputs -> device -> K substeps -> host outputs, per step."""
+    n, K = prob.n, prob.K
+    G, P = sim.grid, sim.params
+    wsb = C.c_size_t(0)
+    L = gic.lib()
+    L.gic_window_host_workspace_size.argtypes = [C.c_void_p, C.c_int64, C.c_int32, C.c_void_p]
+    rc = L.gic_window_host_workspace_size(C.byref(G), n, 0, C.byref(wsb))
+    assert rc == 0, gic.last_error()
+    ws = torch.empty(wsb.value, dtype=torch.uint8, device=dev)
+    pin = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a)).to(dt).pin_memory()
+    h_cell = pin(prob.cell, torch.int32)
+    h_q = pin(prob.q.astype(np.int64), torch.int32)
+    h_r = pin(prob.r, torch.float32)
+    h_v = pin(prob.v, torch.float32)
+    fields = [pin(a, torch.float32) for a in (prob.u, prob.vf, prob.wf, prob.p, prob.alpha_f)]
+    nx, ny, nz = prob.grid.nx, prob.grid.ny, prob.grid.nz
+    o_x = torch.empty((n, 3), dtype=torch.float64).pin_memory()
+    o_v = torch.empty((n, 3), dtype=torch.float64).pin_memory()
+    o_a = torch.empty(nx * ny * nz, dtype=torch.float64).pin_memory()
+    o_fs = [torch.empty(m, dtype=torch.float32).pin_memory()
+            for m in ((nx + 1) * ny * nz, nx * (ny + 1) * nz, nx * ny * (nz + 1))]
+    o_s = torch.empty(2, dtype=torch.float64).pin_memory()
+    fn = L.gic_window_forward_host
+    fn.argtypes = [C.c_void_p] * 2 + [C.c_int64, C.c_int32] + [C.c_void_p] * 9 + [C.c_int32] + [C.c_void_p] * 7 + \
+        [C.c_size_t, C.c_void_p]
+    p = lambda t: C.c_void_p(t.data_ptr())
+
+    def call():
+        rc = fn(C.byref(G), C.byref(P), n, 0, p(h_cell), p(h_q), p(h_r), p(h_v), *[p(f) for f in fields], K, p(o_x),
+                p(o_v), p(o_a), *[p(f) for f in o_fs], p(o_s), p(ws), ws.numel(), C.c_void_p(stream.cuda_stream))
+        assert rc == 0, gic.last_error()
+
+    call()  # warm-up
+    times = []
+    for _ in range(steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        call()
+        times.append(time.perf_counter() - t0)
+    h2d = sum(t.numel() * t.element_size() for t in [h_cell, h_q, h_r, h_v, *fields])
+    d2h = sum(t.numel() * t.element_size() for t in [o_x, o_v, o_a, *o_fs, o_s])
+    sec = statistics.mean(times)
+    return {"value": n * K / sec, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "ms_per_step": 1000 * sec, "api": "gic_window_forward_host (C ABI, pinned host buffers)"}
+
+
+def run_fp64(prob, gic, torch, dev, stream, steps=1):
+    """The same workload on the all-FP64 GPU path (FP64 state and arithmetic)."""
+    from paper_2504_00745_gb300.window import Simulator
+
+    sim = Simulator.from_problem(prob, gic.GIC_FP64, dev)
+    init = sim.A.clone()
+    K = prob.K
+    res = []
+    for it in range(steps + 1):
+        sim.A.cell.copy_(init.cell)
+        sim.A.pos.copy_(init.pos)
+        sim.A.vel.copy_(init.vel)
+        sim.A.id.copy_(init.id)
+        s = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        sim.zero_transfer()
+        for _ in range(K):
+            sim.substep()
+        e.record(stream)
+        torch.cuda.synchronize()
+        if it > 0:
+            res.append(s.elapsed_time(e))
+    ms = statistics.mean(res)
+    return {"value": prob.n * K / (ms / 1000), "unit": UNIT, "ms_per_step": ms, "dtype": "f64", "steps": steps}
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_gpu(args, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,301 @@
+/*
+ * gic.h -- C ABI of the GB300 (sm_103a) granule-grid coupling library.
+ *
+ * The library implements, as CUDA kernels, the per-substep granule-grid
+ * coupling of the Granule-In-Cell (GIC) method (Tang, Zhu, Ni, Chen, "The
+ * Granule-In-Cell Method for Simulating Sand-Water Mixtures", ACM TOG 44(6),
+ * 2025): Algorithm 2 (SandSubstep) without the capillary / wetting terms,
+ * plus a Morton cell sort for the contact neighbour search and a hand-written
+ * adjoint of every step.
+ *
+ * One substep is
+ *   gic_sort        contact-cell Morton sort + cell table   (neighbour search for Sec. 3.1)
+ *   gic_contact     DEM contact forces                       (Sec. 3.1, contact law Eq. k_n)
+ *   gic_g2p_couple  drag, buoyancy, fluid acceleration       (Sec. 3.3 Eqs. 5a-5c, Sec. 5.2)
+ *   gic_integrate   virtual-mass symplectic Euler            (Sec. 5.2 Eq. sand kine; Alg. 2 MoveParticle)
+ *   gic_p2g         alpha_s and exchange momentum to the MAC grid (Sec. 5.1 alpha_s; Sec. 5.2 Exchange Momentum)
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Memory.  Every array argument is a DEVICE pointer owned by the caller
+ * (except the *_host entry points, which say so).  The library allocates no
+ * device memory: scratch space comes from a caller-provided workspace whose
+ * size gic_workspace_size reports.
+ * Streams.  Every call enqueues work on `stream` (a cudaStream_t; NULL is the
+ * legacy default stream) and returns without synchronising, except where
+ * stated.
+ * Errors.  Return GIC_OK (0) or a negative GIC_ERR_* code for argument errors
+ * detected on the host (null pointer, bad size, misalignment, workspace too
+ * small) and for CUDA launch errors; gic_last_error() describes the last one.
+ * Conditions met inside a kernel (granule left the domain, coincident centres,
+ * non-finite value, radius too large for the contact grid) set bits of a sticky device status word
+ * read by gic_check_status().  No kernel traps, asserts or spins.
+ *
+ * Granule state (GicGranules), structure of arrays, n granules:
+ *   cell  int32[n]   contact-cell coordinates packed as cx | cy << 10 | cz << 20
+ *                    (at most 1024 contact cells per axis)
+ *   pos   GIC_FP32: uint32[4 n] = {qx, qy, qz, bits of float r}: the offset in
+ *                    the contact cell as a 30-bit fixed-point fraction,
+ *                    x = origin + (c + q / 2^30) h_c, 16-byte aligned;
+ *         GIC_FP64: double[4 n] = {ox, oy, oz, r}, offset in metres in
+ *                    [0, h_c), 32-byte aligned
+ *   vel   float[4 n] / double[4 n] = {vx, vy, vz, 0}
+ *   id    int32[n] or NULL: original granule id, carried along by gic_sort
+ * Per-granule vectors (forces, accelerations, gradients) are real[4 n] with
+ * the 4th lane unused (real = float for GIC_FP32, double for GIC_FP64).
+ * Grid fields are real arrays on the MAC grid, x fastest:
+ *   u (nx+1) ny nz on x-faces, v nx (ny+1) nz, w nx ny (nz+1), p and alpha_f at
+ *   cell centres nx ny nz.  alpha_s is ALWAYS double (FP64 accumulation).
+ * The contact grid subdivides each MAC cell into k_contact^3 cells of side
+ * h_c = dx / k_contact, which must be at least 2 r_max.
+ */
+#ifndef GIC_H_
+#define GIC_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* gic_stream_t; /* == cudaStream_t */
+
+enum { GIC_FP32 = 0, GIC_FP64 = 1 };
+
+enum {
+  GIC_OK = 0,
+  GIC_ERR_INVALID = -1,   /* bad argument (null pointer, size, grid) */
+  GIC_ERR_CUDA = -2,      /* a CUDA call failed */
+  GIC_ERR_WORKSPACE = -3, /* workspace missing or too small */
+  GIC_ERR_ALIGN = -4,     /* pointer not aligned as documented */
+  GIC_ERR_TIMEOUT = -5    /* host wait exceeded its deadline */
+};
+
+/* sticky device status bits */
+enum {
+  GIC_STATUS_OUT_OF_DOMAIN = 1u, /* a granule left the box; it was clamped to the boundary */
+  GIC_STATUS_COINCIDENT = 2u,    /* a pair at distance 0 was skipped */
+  GIC_STATUS_NONFINITE = 4u,     /* a non-finite velocity or force appeared */
+  GIC_STATUS_RADIUS = 8u,        /* a radius exceeds h_c / 2: contacts beyond the 27 cells are missed */
+  GIC_STATUS_BAD_CELL = 16u,     /* an input cell id lay outside the contact grid */
+  GIC_STATUS_FAST = 32u          /* a granule moved more than one contact cell in a substep */
+};
+
+typedef struct GicGrid {
+  int32_t nx, ny, nz; /* MAC cells per axis, each >= 2 */
+  int32_t k_contact;  /* contact cells per MAC cell and axis, >= 1 */
+  double dx;          /* MAC cell size */
+  double origin[3];   /* lower corner of the box [origin, origin + n dx] */
+} GicGrid;
+
+typedef struct GicParams {
+  double rho_s, rho_f;   /* granule and fluid density */
+  double k_n;            /* normal stiffness (Sec. 3.1) */
+  double zeta;           /* normal damping ratio: c_n = 2 zeta sqrt(k_n m_eff) */
+  double kt_over_cn;     /* tangential coefficient k_t = kt_over_cn * c_n */
+  double mu_fric;        /* Coulomb coefficient tan(phi) (Sec. 3.1) */
+  double c_drag;         /* F_d = c_drag pi r^2 rho_f |dv| dv (Sec. 3.3 Eq. 5b) */
+  double g[3];           /* gravity */
+  double dt_sub;         /* sand substep dt' */
+  double dt_fluid;       /* fluid step dt; the exchange force is scaled by dt'/dt */
+  int32_t virtual_mass;  /* 1: added mass (2/3) pi r^3 rho_f (Sec. 5.2 Eq. sand kine) */
+  int32_t walls;         /* 1: the six box planes are contact partners */
+} GicParams;
+
+typedef struct GicGranules {
+  int64_t n;
+  int32_t* cell;
+  void* pos;
+  void* vel;
+  int32_t* id;
+  int32_t precision; /* GIC_FP32 or GIC_FP64 */
+} GicGranules;
+
+/* ------------------------------------------------------------------ sizes */
+
+/* Bytes of workspace gic_sort (and gic_window_forward) need for n granules. */
+int gic_workspace_size(const GicGrid* grid, int64_t n, int32_t precision, size_t* bytes);
+
+/* Bytes of the cell table: 16 * (1 + number of contact cells).  The caller
+ * zero-fills it once; gic_sort tags every entry it writes with an epoch kept
+ * in the table's first entry, so the table is never cleared again (after
+ * 2^32 - 1 sorts the caller must zero it once more). */
+int gic_cell_table_size(const GicGrid* grid, size_t* bytes);
+
+/* ------------------------------------------------------------ conversion */
+
+/* Build a state from the canonical encoding: cell_xyz int32[3n], q uint32[3n]
+ * (30-bit fractions), r float[n], v float[3n] (device pointers).  Writes
+ * out->cell, out->pos, out->vel and, if out->id != NULL, id = 0..n-1. */
+int gic_pack(const GicGrid* grid, int64_t n, const int32_t* cell_xyz, const uint32_t* q, const float* r,
+             const float* v, GicGranules* out, gic_stream_t stream);
+
+/* Absolute FP64 positions and velocities (double[3n] each).  With in->id set,
+ * granule k is written to slot id[k] (original order); else to slot k. */
+int gic_unpack(const GicGrid* grid, const GicGranules* in, double* x, double* v, gic_stream_t stream);
+
+/* Adjoint of gic_unpack: gradients w.r.t. the absolute positions/velocities
+ * (double[3n], original order when in->id is set) gathered into the state's
+ * order as real[4n] position / velocity gradients (written, not added). */
+int gic_unpack_adj(const GicGrid* grid, const GicGranules* in, const double* gx, const double* gv, void* g_pos,
+                   void* g_vel, gic_stream_t stream);
+
+/* ------------------------------------------------------------ forward */
+
+/* a1: stable Morton sort of the granules by contact cell (ties keep input
+ * order), permutation of the state into out, and the cell table.
+ *   perm[k] = input index of the k-th sorted granule (int32[n]).
+ *   cell_table: see gic_cell_table_size.  in and out must not alias.
+ * The neighbour search itself is not described by the paper; Sec. 3.1 only
+ * states that granules interact when closer than 2 r. */
+int gic_sort(const GicGrid* grid, const GicGranules* in, GicGranules* out, int32_t* perm, void* cell_table, void* ws,
+             size_t ws_bytes, gic_stream_t stream);
+
+/* a2: contact force on every granule of a SORTED state (the output of
+ * gic_sort with the same cell table): linear spring k_n (r_i + r_j - d) plus
+ * dashpot -c_n v_n along the normal, tangential -k_t v_t capped at
+ * mu |F_n| (Sec. 3.1, Eq. k_n, polydisperse form), and the six walls when
+ * params->walls.  F_c real[4n], written. */
+int gic_contact(const GicGrid* grid, const GicParams* params, const GicGranules* sorted, const void* cell_table,
+                void* F_c, gic_stream_t stream);
+
+/* a3: trilinear G2P of u, v, w, grad p (face differences of p) and alpha_f:
+ *   F_fl = c_drag pi r^2 rho_f |u_f - v| (u_f - v) - (4/3) pi r^3 grad p
+ *   a_f  = g - grad p / rho_f   (dv_f/dt of Sec. 5.2 Eq. momentum4 without the
+ *          F_s term, which the sand step cannot know; a_f = g if rho_f = 0)
+ *   alpha_f_p = alpha_f at the granule.
+ * Fields u, v, w, p, alpha_f are real; F_fl, a_f real[4n]; alpha_f_p real[n]
+ * (may be NULL).  All written. */
+int gic_g2p_couple(const GicGrid* grid, const GicParams* params, const GicGranules* granules, const void* u,
+                   const void* v, const void* w, const void* p, const void* alpha_f, void* F_fl, void* a_f,
+                   void* alpha_f_p, gic_stream_t stream);
+
+/* a4: (m + m_a) a = F_c + F_fl + m g + m_a a_f;  v' = v + dt' a;
+ * x' = x + dt' v' (Sec. 5.2 Eq. sand kine, symplectic Euler of Sec. 4);
+ * exchange force f_ex = F_fl + m_a (a_f - a) (every force the fluid exerts on
+ * the granule, Sec. 5.2).  out may alias in (element-wise); out->id receives
+ * in->id when both are set.  Granules that
+ * would leave the box are clamped onto its boundary and flagged
+ * GIC_STATUS_OUT_OF_DOMAIN. */
+int gic_integrate(const GicGrid* grid, const GicParams* params, const GicGranules* in, const void* F_c,
+                  const void* F_fl, const void* a_f, GicGranules* out, void* f_ex, gic_stream_t stream);
+
+/* a5: P2G with the trilinear tent (weights beyond the first/last sample fold
+ * onto it, so every granule deposits weight 1):
+ *   alpha_s(c) = sum_i V_i N(x'_i - x_c) / dx^3  at the NEW positions (Sec. 5.1;
+ *                Alg. 1 computes the target fraction from x^{t+dt}); WRITTEN,
+ *                accumulated in FP64.  May be NULL to skip.
+ *   F_s(face) += -(dt'/dt) sum_i f_ex_i N(x_i - x_face) at the OLD positions
+ *                (Sec. 5.2 Exchange Momentum); ACCUMULATED (the caller zeroes
+ *                them once per fluid step).  May be NULL to skip.
+ *   sums2[0] = sum_c alpha_s(c) dx^3, sums2[1] = sum_i V_i (FP64; written; may
+ *                be NULL; needs alpha_s).
+ * old_ and new_ are the input and output of gic_integrate (same order). */
+int gic_p2g(const GicGrid* grid, const GicParams* params, const GicGranules* old_, const GicGranules* new_,
+            const void* f_ex, double* alpha_s, void* Fs_u, void* Fs_v, void* Fs_w, double* sums2,
+            gic_stream_t stream);
+
+/* ------------------------------------------------------------ adjoints */
+/* Gradients w.r.t. positions are w.r.t. ABSOLUTE positions (metres).
+ * "accumulates" = adds into the output arrays. */
+
+/* Adjoint of the permutation of gic_sort: g_in[perm[k]] = g_out[k] (written)
+ * for real[4n] position and velocity gradients. */
+int gic_sort_adj(int64_t n, int32_t precision, const int32_t* perm, const void* g_pos_out, const void* g_vel_out,
+                 void* g_pos_in, void* g_vel_in, gic_stream_t stream);
+
+/* Adjoint of gic_contact for upstream gF_c (real[4n]): accumulates
+ * sum_j (dF_ij/dx_ij)^T (gF_i - gF_j) into g_pos and the velocity analogue
+ * into g_vel (gather form, using F_ji = -F_ij), and adds
+ * sum_i gF_i . dF_i/dmu into *g_mu (double, device). */
+int gic_contact_adj(const GicGrid* grid, const GicParams* params, const GicGranules* sorted, const void* cell_table,
+                    const void* gF_c, void* g_pos, void* g_vel, double* g_mu, gic_stream_t stream);
+
+/* Adjoint of gic_g2p_couple for upstream gF_fl, ga_f (real[4n]) and
+ * galpha_f_p (real[n] or NULL): accumulates into g_pos, g_vel and adds
+ * sum_i gF_fl_i . dF_fl_i/dc_drag into *g_cdrag (double, device). */
+int gic_g2p_couple_adj(const GicGrid* grid, const GicParams* params, const GicGranules* granules, const void* u,
+                       const void* v, const void* w, const void* p, const void* alpha_f, const void* gF_fl,
+                       const void* ga_f, const void* galpha_f_p, void* g_pos, void* g_vel, double* g_cdrag,
+                       gic_stream_t stream);
+
+/* Adjoint of gic_integrate: from gradients of the new state (g_pos_out,
+ * g_vel_out) and of f_ex (g_f_ex, may be NULL) writes the gradients of the
+ * old state (g_pos_in, g_vel_in) and of F_c, F_fl, a_f (all real[4n]). */
+int gic_integrate_adj(const GicGrid* grid, const GicParams* params, const GicGranules* in, const void* g_pos_out,
+                      const void* g_vel_out, const void* g_f_ex, void* g_pos_in, void* g_vel_in, void* gF_c,
+                      void* gF_fl, void* ga_f, gic_stream_t stream);
+
+/* Adjoint of gic_p2g for upstream grid gradients g_alpha_s (double, or NULL)
+ * and gFs_u/v/w (real, or NULL): accumulates into g_pos_old, g_pos_new and
+ * writes g_f_ex (real[4n]). */
+int gic_p2g_adj(const GicGrid* grid, const GicParams* params, const GicGranules* old_, const GicGranules* new_,
+                const void* f_ex, const double* g_alpha_s, const void* gFs_u, const void* gFs_v, const void* gFs_w,
+                void* g_pos_old, void* g_pos_new, void* g_f_ex, gic_stream_t stream);
+
+/* ------------------------------------------------------------ windows */
+
+/* Bytes of workspace gic_window_forward needs (sort scratch, the second
+ * state, the permutation and the per-granule force arrays). */
+int gic_window_workspace_size(const GicGrid* grid, int64_t n, int32_t precision, size_t* bytes);
+
+/* K substeps of Alg. 2 (SandSubstep): per substep gic_sort, gic_contact,
+ * gic_g2p_couple, gic_integrate, gic_p2g.  `state` is updated in place and
+ * ends in the sorted order of the last substep (state->id, if set, maps it
+ * back).  alpha_s (may be NULL) is the last substep's; F_s (all three or none)
+ * accumulates over the K substeps; sums2 (may be NULL) is the last substep's.
+ * cell_table as for gic_sort; ws of gic_window_workspace_size bytes,
+ * 256-byte aligned.  Asynchronous on `stream`. */
+int gic_window_forward(const GicGrid* grid, const GicParams* params, GicGranules* state, int32_t K, const void* u,
+                       const void* v, const void* w, const void* p, const void* alpha_f, double* alpha_s, void* Fs_u,
+                       void* Fs_v, void* Fs_w, double* sums2, void* cell_table, void* ws, size_t ws_bytes,
+                       gic_stream_t stream);
+
+/* Bytes of DEVICE workspace gic_window_forward_host needs: everything in
+ * gic_window_workspace_size plus device copies of its inputs and outputs and
+ * a cell table. */
+int gic_window_host_workspace_size(const GicGrid* grid, int64_t n, int32_t precision, size_t* bytes);
+
+/* The same K-substep window on HOST buffers: copies the canonical inputs
+ * (cell_xyz int32[3n], q uint32[3n], r float[n], v float[3n]) and the fluid
+ * fields (real, host) to the device, runs gic_window_forward, and copies back
+ * the final positions / velocities (double[3n] each, original order),
+ * alpha_s (double), F_s (real, accumulated from zero) and sums2 (any output
+ * may be NULL).  Host buffers should be pinned for asynchronous copies.
+ * Blocks until the results are on the host (deadline 10 minutes, then
+ * GIC_ERR_TIMEOUT). */
+int gic_window_forward_host(const GicGrid* grid, const GicParams* params, int64_t n, int32_t precision,
+                            const int32_t* cell_xyz, const uint32_t* q, const float* r, const float* v,
+                            const void* u, const void* v_f, const void* w, const void* p, const void* alpha_f,
+                            int32_t K, double* x_out, double* v_out, double* alpha_s, void* Fs_u, void* Fs_v,
+                            void* Fs_w, double* sums2, void* ws, size_t ws_bytes, gic_stream_t stream);
+
+/* ------------------------------------------------------------ diagnostics */
+
+/* Contact pairs of a sorted state with id set: counts[k] = number of partners
+ * of sorted granule k (int32[n]); if pairs != NULL also writes up to max_pairs
+ * pairs (id_a < id_b) as int32[2 max_pairs] in unspecified order and the
+ * total number into *n_pairs (int64, device; the caller zeroes it). */
+int gic_contact_pairs(const GicGrid* grid, const GicGranules* sorted, const void* cell_table, int32_t* counts,
+                      int32_t* pairs, int64_t max_pairs, int64_t* n_pairs, gic_stream_t stream);
+
+/* Copy the sticky status word to *flags (host) after synchronising the
+ * stream; clear it if clear != 0.  The wait polls with a deadline of
+ * timeout_ms (<= 0: 60 s) and returns GIC_ERR_TIMEOUT if it passes. */
+int gic_check_status(uint32_t* flags, int32_t clear, int32_t timeout_ms, gic_stream_t stream);
+
+/* Text of the last host-side error on this thread. */
+const char* gic_last_error(void);
+
+/* Number of kernels this process has launched through the library. */
+int64_t gic_launch_count(void);
+
+/* Library version string. */
+const char* gic_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GIC_H_ */

@@ -1,0 +1,394 @@
+// gic_contact.cu -- a2: DEM contact forces and their adjoint.
+//
+// Gather form: one thread per granule of the sorted state walks the 27
+// contact cells around its own (h_c >= 2 r_max), reads each partner's
+// position / velocity and sums the pair forces on itself.  No atomics.  The
+// adjoint uses the antisymmetry F_ji = -F_ij, so it is a gather as well:
+// dL/dx_i = sum_j (dF_ij/dx_ij)^T (lambda_i - lambda_j).
+//
+// Contact law (Sec. 3.1, Eq. k_n), polydisperse and with the readings of this
+// library: n = x_ij / d, overlap = r_i + r_j - d,
+//   F_n = (k_n overlap - c_n v_n) n,   c_n = 2 zeta sqrt(k_n m_eff),
+//   f_t = -k_t v_t,  k_t = kt_over_cn c_n,   F_t = min(|f_t|, mu |F_n|) f_t/|f_t|.
+// Walls are partners of infinite mass at rest (m_eff = m_i).
+#include "gic_internal.cuh"
+
+namespace gic {
+
+template <typename T>
+__device__ __forceinline__ T granule_mass(const DParams<T>& P, T r) {
+  return P.rho_s * (T(4.0 / 3.0 * kPi) * r * r * r);
+}
+
+// Pair force on i (x = x_i - x_j, v = v_i - v_j), already known to overlap
+// (d2 < R^2).  Returns false for coincident centres.
+template <typename T>
+__device__ __forceinline__ bool pair_force(const DParams<T>& P, T x0, T x1, T x2, T d2, T v0, T v1, T v2, T R, T meff,
+                                           T& F0, T& F1, T& F2) {
+  T d = sqrt(d2);
+  if (d == T(0)) return false;
+  T inv_d = T(1) / d;
+  T n0 = x0 * inv_d, n1 = x1 * inv_d, n2 = x2 * inv_d;
+  T overlap = R - d;
+  T cn = T(2) * P.zeta * sqrt(P.k_n * meff);
+  T vn = v0 * n0 + v1 * n1 + v2 * n2;
+  T Fn = P.k_n * overlap - cn * vn;
+  T t0 = v0 - vn * n0, t1 = v1 - vn * n1, t2 = v2 - vn * n2;
+  T kt = P.kt_over_cn * cn;
+  T ftn = kt * sqrt(t0 * t0 + t1 * t1 + t2 * t2);
+  T cap = P.mu * fabs(Fn);
+  T s = ftn > cap ? cap / ftn : T(1);
+  T a = s * kt;
+  F0 = Fn * n0 - a * t0;
+  F1 = Fn * n1 - a * t1;
+  F2 = Fn * n2 - a * t2;
+  return true;
+}
+
+// Reverse mode of pair_force for upstream l (gradient of the pair force):
+// adds d<l, F>/dx to gx and d<l, F>/dv to gv; returns d<lm, F>/dmu for the
+// second upstream lm (the granule's own gradient).
+template <typename T>
+__device__ __forceinline__ T pair_force_adj(const DParams<T>& P, T x0, T x1, T x2, T d2, T v0, T v1, T v2, T R,
+                                            T meff, T l0, T l1, T l2, T lm0, T lm1, T lm2, T& gx0, T& gx1, T& gx2,
+                                            T& gv0, T& gv1, T& gv2) {
+  T d = sqrt(d2);
+  if (d == T(0)) return T(0);
+  T inv_d = T(1) / d;
+  T n0 = x0 * inv_d, n1 = x1 * inv_d, n2 = x2 * inv_d;
+  T overlap = R - d;
+  T cn = T(2) * P.zeta * sqrt(P.k_n * meff);
+  T vn = v0 * n0 + v1 * n1 + v2 * n2;
+  T Fn = P.k_n * overlap - cn * vn;
+  T t0 = v0 - vn * n0, t1 = v1 - vn * n1, t2 = v2 - vn * n2;
+  T kt = P.kt_over_cn * cn;
+  T vtn = sqrt(t0 * t0 + t1 * t1 + t2 * t2);
+  T ftn = kt * vtn;
+  T cap = P.mu * fabs(Fn);
+  bool slip = ftn > cap;
+  // F = Fn n + F_t
+  T gFn = l0 * n0 + l1 * n1 + l2 * n2;
+  T gn0 = Fn * l0, gn1 = Fn * l1, gn2 = Fn * l2;
+  T gt0, gt1, gt2;
+  T gmu = T(0);
+  if (slip) {
+    // F_t = -A u, A = mu |Fn|, u = v_t / |v_t|
+    T inv_vt = T(1) / vtn;
+    T u0 = t0 * inv_vt, u1 = t1 * inv_vt, u2 = t2 * inv_vt;
+    T A = cap;
+    T gA = -(l0 * u0 + l1 * u1 + l2 * u2);
+    T sgn = Fn > T(0) ? T(1) : (Fn < T(0) ? T(-1) : T(0));
+    gFn += gA * P.mu * sgn;
+    gmu = -(lm0 * u0 + lm1 * u1 + lm2 * u2) * fabs(Fn);
+    T gu0 = -A * l0, gu1 = -A * l1, gu2 = -A * l2;
+    T gudu = gu0 * u0 + gu1 * u1 + gu2 * u2;
+    gt0 = (gu0 - gudu * u0) * inv_vt;
+    gt1 = (gu1 - gudu * u1) * inv_vt;
+    gt2 = (gu2 - gudu * u2) * inv_vt;
+  } else {
+    gt0 = -kt * l0;
+    gt1 = -kt * l1;
+    gt2 = -kt * l2;
+  }
+  // v_t = v - vn n
+  gv0 += gt0;
+  gv1 += gt1;
+  gv2 += gt2;
+  T gvn = -(gt0 * n0 + gt1 * n1 + gt2 * n2);
+  gn0 -= vn * gt0;
+  gn1 -= vn * gt1;
+  gn2 -= vn * gt2;
+  // Fn = k_n (R - d) - cn vn
+  T gd = -P.k_n * gFn;
+  gvn -= cn * gFn;
+  // vn = v . n
+  gv0 += gvn * n0;
+  gv1 += gvn * n1;
+  gv2 += gvn * n2;
+  gn0 += gvn * v0;
+  gn1 += gvn * v1;
+  gn2 += gvn * v2;
+  // n = x / d, d = |x|
+  T gnn = gn0 * n0 + gn1 * n1 + gn2 * n2;
+  gx0 += (gn0 - gnn * n0) * inv_d + gd * n0;
+  gx1 += (gn1 - gnn * n1) * inv_d + gd * n1;
+  gx2 += (gn2 - gnn * n2) * inv_d + gd * n2;
+  return gmu;
+}
+
+template <typename T>
+__device__ __forceinline__ void load_cell_coords(int32_t c, int& x, int& y, int& z) {
+  x = cell_x(c);
+  y = cell_y(c);
+  z = cell_z(c);
+}
+
+// Visit every granule j != i in the 27 contact cells around (cx, cy, cz).
+template <typename F>
+__device__ __forceinline__ void for_each_partner(const DGrid& G, const uint4* __restrict__ table, uint32_t epoch,
+                                                 int64_t i, int cx, int cy, int cz, F&& f) {
+  for (int oz = -1; oz <= 1; ++oz) {
+    int z = cz + oz;
+    if (z < 0 || z >= G.nc[2]) continue;
+    for (int oy = -1; oy <= 1; ++oy) {
+      int y = cy + oy;
+      if (y < 0 || y >= G.nc[1]) continue;
+      for (int ox = -1; ox <= 1; ++ox) {
+        int x = cx + ox;
+        if (x < 0 || x >= G.nc[0]) continue;
+        uint4 e = __ldg(&table[table_index(G, x, y, z)]);
+        if (e.z != epoch) continue;
+        for (uint32_t j = e.x; j < e.x + e.y; ++j) {
+          if ((int64_t)j == i) continue;
+          f((int64_t)j, ox, oy, oz);
+        }
+      }
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_contact(DGrid G, DParams<T> P, int64_t n, const int32_t* __restrict__ cell,
+                                                  const pos_t<T>* __restrict__ pos, const vec_t<T>* __restrict__ vel,
+                                                  const uint4* __restrict__ table, vec_t<T>* __restrict__ F,
+                                                  uint32_t* status) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int32_t ci = cell[i];
+  int cx, cy, cz;
+  load_cell_coords<T>(ci, cx, cy, cz);
+  pos_t<T> pi = pos[i];
+  vec_t<T> vi = vel[i];
+  T ri = radius_of(pi);
+  T mi = granule_mass(P, ri);
+  uint32_t epoch = __ldg(&table[0].x);
+  if (T(2) * ri > (T)G.hc) raise_status(status, GIC_STATUS_RADIUS);
+  T F0 = 0, F1 = 0, F2 = 0;
+  bool coincident = false;
+  for_each_partner(G, table, epoch, i, cx, cy, cz, [&](int64_t j, int ox, int oy, int oz) {
+    pos_t<T> pj = ldg(&pos[j]);
+    T x0, x1, x2;
+    rel_ij(G, pi, pj, ox, oy, oz, x0, x1, x2);
+    T rj = radius_of(pj);
+    T R = ri + rj;
+    T d2 = x0 * x0 + x1 * x1 + x2 * x2;
+    if (!(d2 < R * R)) return;
+    vec_t<T> vj = ldg(&vel[j]);
+    T mj = granule_mass(P, rj);
+    T f0, f1, f2;
+    if (pair_force(P, x0, x1, x2, d2, vi.x - vj.x, vi.y - vj.y, vi.z - vj.z, R, mi * mj / (mi + mj), f0, f1, f2)) {
+      F0 += f0;
+      F1 += f1;
+      F2 += f2;
+    } else {
+      coincident = true;
+    }
+  });
+  if (P.walls) {
+    const int c3[3] = {cx, cy, cz};
+    for (int a = 0; a < 3; ++a) {
+      for (int side = 0; side < 2; ++side) {
+        if (side == 0 ? c3[a] != 0 : c3[a] != G.nc[a] - 1) continue;
+        T gap = side == 0 ? gap_lo(G, pi, a) : gap_hi(G, pi, a);
+        if (!(gap < ri)) continue;
+        T x[3] = {0, 0, 0};
+        x[a] = side == 0 ? gap : -gap;
+        T f0, f1, f2;
+        if (pair_force(P, x[0], x[1], x[2], gap * gap, vi.x, vi.y, vi.z, ri, mi, f0, f1, f2)) {
+          F0 += f0;
+          F1 += f1;
+          F2 += f2;
+        } else {
+          raise_status(status, GIC_STATUS_OUT_OF_DOMAIN);
+        }
+      }
+    }
+  }
+  if (coincident) raise_status(status, GIC_STATUS_COINCIDENT);
+  if (!isfinite(F0) || !isfinite(F1) || !isfinite(F2)) raise_status(status, GIC_STATUS_NONFINITE);
+  F[i] = make_vec<T>(F0, F1, F2);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_contact_adj(DGrid G, DParams<T> P, int64_t n, const int32_t* __restrict__ cell,
+                                                      const pos_t<T>* __restrict__ pos,
+                                                      const vec_t<T>* __restrict__ vel, const uint4* __restrict__ table,
+                                                      const vec_t<T>* __restrict__ gF, vec_t<T>* __restrict__ gpos,
+                                                      vec_t<T>* __restrict__ gvel, double* __restrict__ g_mu) {
+  __shared__ double s_red[32];
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double my_gmu = 0.0;
+  if (i < n) {
+    int32_t ci = cell[i];
+    int cx, cy, cz;
+    load_cell_coords<T>(ci, cx, cy, cz);
+    pos_t<T> pi = pos[i];
+    vec_t<T> vi = vel[i];
+    vec_t<T> li = gF[i];
+    T ri = radius_of(pi);
+    T mi = granule_mass(P, ri);
+    uint32_t epoch = __ldg(&table[0].x);
+    T gx0 = 0, gx1 = 0, gx2 = 0, gv0 = 0, gv1 = 0, gv2 = 0, gm = 0;
+    for_each_partner(G, table, epoch, i, cx, cy, cz, [&](int64_t j, int ox, int oy, int oz) {
+      pos_t<T> pj = ldg(&pos[j]);
+      T x0, x1, x2;
+      rel_ij(G, pi, pj, ox, oy, oz, x0, x1, x2);
+      T rj = radius_of(pj);
+      T R = ri + rj;
+      T d2 = x0 * x0 + x1 * x1 + x2 * x2;
+      if (!(d2 < R * R)) return;
+      vec_t<T> vj = ldg(&vel[j]);
+      vec_t<T> lj = ldg(&gF[j]);
+      T mj = granule_mass(P, rj);
+      gm += pair_force_adj(P, x0, x1, x2, d2, vi.x - vj.x, vi.y - vj.y, vi.z - vj.z, R, mi * mj / (mi + mj),
+                           li.x - lj.x, li.y - lj.y, li.z - lj.z, li.x, li.y, li.z, gx0, gx1, gx2, gv0, gv1, gv2);
+    });
+    if (P.walls) {
+      const int c3[3] = {cx, cy, cz};
+      for (int a = 0; a < 3; ++a) {
+        for (int side = 0; side < 2; ++side) {
+          if (side == 0 ? c3[a] != 0 : c3[a] != G.nc[a] - 1) continue;
+          T gap = side == 0 ? gap_lo(G, pi, a) : gap_hi(G, pi, a);
+          if (!(gap < ri)) continue;
+          T x[3] = {0, 0, 0};
+          x[a] = side == 0 ? gap : -gap;
+          gm += pair_force_adj(P, x[0], x[1], x[2], gap * gap, vi.x, vi.y, vi.z, ri, mi, li.x, li.y, li.z, li.x, li.y,
+                               li.z, gx0, gx1, gx2, gv0, gv1, gv2);
+        }
+      }
+    }
+    vec_t<T> a = gpos[i];
+    vec_t<T> b = gvel[i];
+    gpos[i] = make_vec<T>(a.x + gx0, a.y + gx1, a.z + gx2);
+    gvel[i] = make_vec<T>(b.x + gv0, b.y + gv1, b.z + gv2);
+    my_gmu = (double)gm;
+  }
+  if (g_mu) {
+    double s = block_sum(my_gmu, s_red);
+    if (threadIdx.x == 0) atomicAdd(g_mu, s);
+  }
+}
+
+// Diagnostic: number of partners per granule and the pair list by id.
+template <typename T>
+__global__ void k_contact_pairs(DGrid G, int64_t n, const int32_t* __restrict__ cell, const pos_t<T>* __restrict__ pos,
+                                const int32_t* __restrict__ id, const uint4* __restrict__ table,
+                                int32_t* __restrict__ counts, int32_t* __restrict__ pairs, int64_t max_pairs,
+                                unsigned long long* __restrict__ n_pairs) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int cx, cy, cz;
+  load_cell_coords<T>(cell[i], cx, cy, cz);
+  pos_t<T> pi = pos[i];
+  T ri = radius_of(pi);
+  int32_t idi = id ? id[i] : (int32_t)i;
+  uint32_t epoch = __ldg(&table[0].x);
+  int cnt = 0;
+  for_each_partner(G, table, epoch, i, cx, cy, cz, [&](int64_t j, int ox, int oy, int oz) {
+    pos_t<T> pj = pos[j];
+    T x0, x1, x2;
+    rel_ij(G, pi, pj, ox, oy, oz, x0, x1, x2);
+    T R = ri + radius_of(pj);
+    if (!(x0 * x0 + x1 * x1 + x2 * x2 < R * R)) return;
+    ++cnt;
+    int32_t idj = id ? id[j] : (int32_t)j;
+    if (pairs && idi < idj) {
+      unsigned long long slot = atomicAdd(n_pairs, 1ull);
+      if ((int64_t)slot < max_pairs) {
+        pairs[2 * slot] = idi;
+        pairs[2 * slot + 1] = idj;
+      }
+    }
+  });
+  if (counts) counts[i] = cnt;
+}
+
+static int check_table(const void* t) {
+  if (!t) return set_error(GIC_ERR_INVALID, "cell_table is NULL");
+  if ((uintptr_t)t % 16) return set_error(GIC_ERR_ALIGN, "cell_table must be 16-byte aligned");
+  return GIC_OK;
+}
+
+}  // namespace gic
+
+using namespace gic;
+
+extern "C" int gic_contact(const GicGrid* grid, const GicParams* params, const GicGranules* s, const void* table,
+                           void* F_c, gic_stream_t stream) {
+  DGrid G;
+  int rc = make_grid(grid, &G);
+  if (rc) return rc;
+  if ((rc = check_granules(s, "gic_contact"))) return rc;
+  if ((rc = check_table(table))) return rc;
+  if (s->n == 0) return GIC_OK;
+  if (!F_c) return set_error(GIC_ERR_INVALID, "gic_contact: F_c is NULL");
+  if ((rc = check_vecs(s->precision, "gic_contact", {F_c}))) return rc;
+  const int threads = 128;
+  if (s->precision == GIC_FP32) {
+    DParams<float> P;
+    if ((rc = make_params(params, &P))) return rc;
+    k_contact<float><<<grid_blocks(s->n, threads), threads, 0, stream>>>(
+        G, P, s->n, s->cell, (const uint4*)s->pos, (const float4*)s->vel, (const uint4*)table, (float4*)F_c,
+        status_word());
+  } else {
+    DParams<double> P;
+    if ((rc = make_params(params, &P))) return rc;
+    k_contact<double><<<grid_blocks(s->n, threads), threads, 0, stream>>>(G, P, s->n, s->cell, (const d4*)s->pos,
+                                                                           (const d4*)s->vel, (const uint4*)table,
+                                                                           (d4*)F_c, status_word());
+  }
+  count_launches(1);
+  GIC_CHECK_LAUNCH("gic_contact");
+  return GIC_OK;
+}
+
+extern "C" int gic_contact_adj(const GicGrid* grid, const GicParams* params, const GicGranules* s, const void* table,
+                               const void* gF_c, void* g_pos, void* g_vel, double* g_mu, gic_stream_t stream) {
+  DGrid G;
+  int rc = make_grid(grid, &G);
+  if (rc) return rc;
+  if ((rc = check_granules(s, "gic_contact_adj"))) return rc;
+  if ((rc = check_table(table))) return rc;
+  if (s->n == 0) return GIC_OK;
+  if (!gF_c || !g_pos || !g_vel) return set_error(GIC_ERR_INVALID, "gic_contact_adj: null gradient array");
+  if ((rc = check_vecs(s->precision, "gic_contact_adj", {gF_c, g_pos, g_vel}))) return rc;
+  const int threads = 128;
+  if (s->precision == GIC_FP32) {
+    DParams<float> P;
+    if ((rc = make_params(params, &P))) return rc;
+    k_contact_adj<float><<<grid_blocks(s->n, threads), threads, 0, stream>>>(
+        G, P, s->n, s->cell, (const uint4*)s->pos, (const float4*)s->vel, (const uint4*)table, (const float4*)gF_c,
+        (float4*)g_pos, (float4*)g_vel, g_mu);
+  } else {
+    DParams<double> P;
+    if ((rc = make_params(params, &P))) return rc;
+    k_contact_adj<double><<<grid_blocks(s->n, threads), threads, 0, stream>>>(
+        G, P, s->n, s->cell, (const d4*)s->pos, (const d4*)s->vel, (const uint4*)table, (const d4*)gF_c, (d4*)g_pos,
+        (d4*)g_vel, g_mu);
+  }
+  count_launches(1);
+  GIC_CHECK_LAUNCH("gic_contact_adj");
+  return GIC_OK;
+}
+
+extern "C" int gic_contact_pairs(const GicGrid* grid, const GicGranules* s, const void* table, int32_t* counts,
+                                 int32_t* pairs, int64_t max_pairs, int64_t* n_pairs, gic_stream_t stream) {
+  DGrid G;
+  int rc = make_grid(grid, &G);
+  if (rc) return rc;
+  if ((rc = check_granules(s, "gic_contact_pairs"))) return rc;
+  if ((rc = check_table(table))) return rc;
+  if (s->n == 0) return GIC_OK;
+  if (pairs && !n_pairs) return set_error(GIC_ERR_INVALID, "gic_contact_pairs: n_pairs is NULL");
+  if (s->precision == GIC_FP32)
+    k_contact_pairs<float><<<grid_blocks(s->n, 128), 128, 0, stream>>>(G, s->n, s->cell, (const uint4*)s->pos, s->id,
+                                                                        (const uint4*)table, counts, pairs, max_pairs,
+                                                                        (unsigned long long*)n_pairs);
+  else
+    k_contact_pairs<double><<<grid_blocks(s->n, 128), 128, 0, stream>>>(G, s->n, s->cell, (const d4*)s->pos, s->id,
+                                                                         (const uint4*)table, counts, pairs,
+                                                                         max_pairs, (unsigned long long*)n_pairs);
+  count_launches(1);
+  GIC_CHECK_LAUNCH("gic_contact_pairs");
+  return GIC_OK;
+}

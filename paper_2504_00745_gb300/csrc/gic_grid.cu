@@ -1,0 +1,460 @@
+// gic_grid.cu -- a3 G2P coupling (drag, pressure gradient, fluid acceleration,
+// fluid fraction) and a5 P2G (volume fraction, exchange momentum), with
+// adjoints.  One thread per granule; granules arrive Morton-sorted, so the
+// lanes of a warp read and write the same few MAC cells.
+#include "gic_interp.cuh"
+
+namespace gic {
+
+template <typename T>
+struct Fields {
+  const T* u;
+  const T* v;
+  const T* w;
+  const T* p;
+  const T* af;
+};
+
+template <typename T>
+__device__ __forceinline__ FieldLoad<T> face_loader(const DGrid& G, const T* f, int comp) {
+  FieldLoad<T> L;
+  L.f = f;
+  L.nsx = G.nx + (comp == 0);
+  L.nsy = G.ny + (comp == 1);
+  return L;
+}
+
+template <typename T>
+__device__ __forceinline__ GradPLoad<T> gradp_loader(const DGrid& G, const T* p, int comp) {
+  GradPLoad<T> L;
+  L.p = p;
+  L.nx = G.nx;
+  L.ny = G.ny;
+  L.nz = G.nz;
+  L.comp = comp;
+  L.inv_dx = (T)G.inv_dx;
+  return L;
+}
+
+// ------------------------------------------------------------------ G2P
+
+// F_fl = c_drag pi r^2 rho_f |u_f - v| (u_f - v) - V grad p   (Sec. 3.3 Eqs. 5a, 5b)
+// a_f  = g - grad p / rho_f                                   (Sec. 5.2 Eq. momentum4)
+template <typename T>
+__global__ void __launch_bounds__(256) k_g2p(DGrid G, DParams<T> P, int64_t n, const int32_t* __restrict__ cell,
+                                              const pos_t<T>* __restrict__ pos, const vec_t<T>* __restrict__ vel,
+                                              Fields<T> Fd, vec_t<T>* __restrict__ F_fl, vec_t<T>* __restrict__ a_f,
+                                              T* __restrict__ afp, uint32_t* status) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  pos_t<T> pi = pos[i];
+  vec_t<T> vi = vel[i];
+  int m[3];
+  T t[3];
+  granule_mac<T>(G, cell[i], pi, m, t);
+  const T* uvw[3] = {Fd.u, Fd.v, Fd.w};
+  T uf[3], gp[3];
+  T inv_dx = (T)G.inv_dx;
+#pragma unroll
+  for (int comp = 0; comp < 3; ++comp) {
+    Stencil3<T> S = make_stencil<T>(G, m, t, comp);
+    uf[comp] = interp<T>(S, face_loader<T>(G, uvw[comp], comp), inv_dx, nullptr);
+    gp[comp] = interp<T>(S, gradp_loader<T>(G, Fd.p, comp), inv_dx, nullptr);
+  }
+  T r = radius_of(pi);
+  T V = T(4.0 / 3.0 * kPi) * r * r * r;
+  T d0 = uf[0] - vi.x, d1 = uf[1] - vi.y, d2 = uf[2] - vi.z;
+  T sp = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+  T cd = P.c_drag * T(kPi) * r * r * P.rho_f * sp;
+  F_fl[i] = make_vec<T>(cd * d0 - V * gp[0], cd * d1 - V * gp[1], cd * d2 - V * gp[2]);
+  if (P.rho_f > T(0))
+    a_f[i] = make_vec<T>(P.g[0] - gp[0] * P.inv_rho_f, P.g[1] - gp[1] * P.inv_rho_f, P.g[2] - gp[2] * P.inv_rho_f);
+  else
+    a_f[i] = make_vec<T>(P.g[0], P.g[1], P.g[2]);
+  if (afp) {
+    Stencil3<T> S = make_stencil<T>(G, m, t, 3);
+    FieldLoad<T> L;
+    L.f = Fd.af;
+    L.nsx = G.nx;
+    L.nsy = G.ny;
+    afp[i] = interp<T>(S, L, inv_dx, nullptr);
+  }
+  if (!isfinite(sp)) raise_status(status, GIC_STATUS_NONFINITE);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_g2p_adj(DGrid G, DParams<T> P, int64_t n, const int32_t* __restrict__ cell,
+                                                  const pos_t<T>* __restrict__ pos, const vec_t<T>* __restrict__ vel,
+                                                  Fields<T> Fd, const vec_t<T>* __restrict__ gF,
+                                                  const vec_t<T>* __restrict__ ga, const T* __restrict__ galpha,
+                                                  vec_t<T>* __restrict__ gpos, vec_t<T>* __restrict__ gvel,
+                                                  double* __restrict__ g_cdrag) {
+  __shared__ double s_red[32];
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double my_gc = 0.0;
+  if (i < n) {
+    pos_t<T> pi = pos[i];
+    vec_t<T> vi = vel[i];
+    int m[3];
+    T t[3];
+    granule_mac<T>(G, cell[i], pi, m, t);
+    const T* uvw[3] = {Fd.u, Fd.v, Fd.w};
+    T uf[3], gu[3][3], gp[3], ggp[3][3];
+    T inv_dx = (T)G.inv_dx;
+#pragma unroll
+    for (int comp = 0; comp < 3; ++comp) {
+      Stencil3<T> S = make_stencil<T>(G, m, t, comp);
+      uf[comp] = interp<T>(S, face_loader<T>(G, uvw[comp], comp), inv_dx, gu[comp]);
+      gp[comp] = interp<T>(S, gradp_loader<T>(G, Fd.p, comp), inv_dx, ggp[comp]);
+    }
+    T r = radius_of(pi);
+    T V = T(4.0 / 3.0 * kPi) * r * r * r;
+    T dv[3] = {uf[0] - vi.x, uf[1] - vi.y, uf[2] - vi.z};
+    T sp = sqrt(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
+    T k = P.c_drag * T(kPi) * r * r * P.rho_f;
+    vec_t<T> lF = gF[i];
+    vec_t<T> la = ga[i];
+    T l[3] = {lF.x, lF.y, lF.z};
+    T lam_a[3] = {la.x, la.y, la.z};
+    T dvl = dv[0] * l[0] + dv[1] * l[1] + dv[2] * l[2];
+    // d/d dv of k |dv| dv . l = k (|dv| l + (dv . l) dv / |dv|)
+    T gdv[3];
+    for (int a = 0; a < 3; ++a) gdv[a] = sp > T(0) ? k * (sp * l[a] + dvl * dv[a] / sp) : T(0);
+    T gx[3] = {0, 0, 0};
+    for (int comp = 0; comp < 3; ++comp) {
+      T ggrad = -V * l[comp] - P.inv_rho_f * lam_a[comp];  // upstream of grad p component
+      for (int b = 0; b < 3; ++b) gx[b] += gdv[comp] * gu[comp][b] + ggrad * ggp[comp][b];
+    }
+    if (galpha) {
+      Stencil3<T> S = make_stencil<T>(G, m, t, 3);
+      FieldLoad<T> L;
+      L.f = Fd.af;
+      L.nsx = G.nx;
+      L.nsy = G.ny;
+      T gal[3];
+      interp<T>(S, L, inv_dx, gal);
+      T la_ = galpha[i];
+      for (int b = 0; b < 3; ++b) gx[b] += la_ * gal[b];
+    }
+    vec_t<T> a = gpos[i];
+    vec_t<T> bb = gvel[i];
+    gpos[i] = make_vec<T>(a.x + gx[0], a.y + gx[1], a.z + gx[2]);
+    gvel[i] = make_vec<T>(bb.x - gdv[0], bb.y - gdv[1], bb.z - gdv[2]);
+    my_gc = (double)(T(kPi) * r * r * P.rho_f * sp * dvl);
+  }
+  if (g_cdrag) {
+    double s = block_sum(my_gc, s_red);
+    if (threadIdx.x == 0) atomicAdd(g_cdrag, s);
+  }
+}
+
+// ------------------------------------------------------------------ P2G
+
+__global__ void k_zero(double* __restrict__ a, int64_t m, double* __restrict__ sums) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (; i < m; i += stride) a[i] = 0.0;
+  if (sums && blockIdx.x == 0 && threadIdx.x < 2) sums[threadIdx.x] = 0.0;
+}
+
+__global__ void k_alpha_sum(const double* __restrict__ a, int64_t m, double dx3, double* __restrict__ sums) {
+  __shared__ double s_red[32];
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+    acc += a[i];
+  double s = block_sum(acc, s_red);
+  if (threadIdx.x == 0) atomicAdd(&sums[0], s * dx3);
+}
+
+// alpha_s(c) = sum_i V_i N(x'_i - x_c) / dx^3 at the new positions, FP64
+// weights (from the exact fixed-point state) and FP64 atomics;
+// F_s(face) += exch * f_ex_i N(x_i - x_face) at the old positions, with a
+// warp-segmented pre-sum over lanes that share the stencil's base sample.
+template <typename T>
+__global__ void __launch_bounds__(256) k_p2g(DGrid G, DParams<T> P, int64_t n, const int32_t* __restrict__ cell_old,
+                                              const pos_t<T>* __restrict__ pos_old,
+                                              const int32_t* __restrict__ cell_new,
+                                              const pos_t<T>* __restrict__ pos_new, const vec_t<T>* __restrict__ fex,
+                                              double* __restrict__ alpha, T* __restrict__ Fs_u, T* __restrict__ Fs_v,
+                                              T* __restrict__ Fs_w, double* __restrict__ sums) {
+  __shared__ double s_red[32];
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  bool valid = i < n;
+  double Vi = 0.0;
+  if (valid && alpha) {
+    pos_t<T> pn = pos_new[i];
+    double r = (double)radius_of(pn);
+    Vi = 4.0 / 3.0 * kPi * r * r * r;
+    int m[3];
+    double t[3];
+    granule_mac_fp64(G, cell_new[i], pn, m, t);
+    Stencil3<double> S = make_stencil<double>(G, m, t, 3);
+    double s = Vi * G.inv_dx * G.inv_dx * G.inv_dx;
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        double wyz = (b ? S.w[1] : 1.0 - S.w[1]) * (c ? S.w[2] : 1.0 - S.w[2]) * s;
+        int64_t row = sample_index(G.nx, G.ny, S.i0[0], S.i0[1] + b, S.i0[2] + c);
+        atomicAdd(&alpha[row], (1.0 - S.w[0]) * wyz);
+        atomicAdd(&alpha[row + 1], S.w[0] * wyz);
+      }
+  }
+  bool do_fs = Fs_u != nullptr;  // uniform over the launch
+  if (do_fs) {
+    int m[3] = {0, 0, 0};
+    T t[3] = {0, 0, 0};
+    vec_t<T> f = make_vec<T>(0, 0, 0);
+    if (valid) {
+      granule_mac<T>(G, cell_old[i], pos_old[i], m, t);
+      f = fex[i];
+    }
+    T* Fs[3] = {Fs_u, Fs_v, Fs_w};
+    T fv[3] = {P.exch * f.x, P.exch * f.y, P.exch * f.z};
+#pragma unroll
+    for (int comp = 0; comp < 3; ++comp) {
+      Stencil3<T> S = make_stencil<T>(G, m, t, comp);
+      unsigned key = valid ? (unsigned)base_index(S) : 0xffffffffu - (unsigned)lane_id();
+      int end = run_end(key);
+      bool head = run_head(key);
+      T val[8];
+#pragma unroll
+      for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+          for (int a = 0; a < 2; ++a) {
+            T w = (a ? S.w[0] : T(1) - S.w[0]) * (b ? S.w[1] : T(1) - S.w[1]) * (c ? S.w[2] : T(1) - S.w[2]);
+            val[a + 2 * b + 4 * c] = seg_sum(valid ? w * fv[comp] : T(0), end);
+          }
+      if (valid && head) {
+        int nsx = S.ns[0], nsy = S.ns[1];
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+          for (int b = 0; b < 2; ++b) {
+            int64_t row = sample_index(nsx, nsy, S.i0[0], S.i0[1] + b, S.i0[2] + c);
+            atomicAdd(&Fs[comp][row], val[2 * b + 4 * c]);
+            atomicAdd(&Fs[comp][row + 1], val[1 + 2 * b + 4 * c]);
+          }
+      }
+    }
+  }
+  if (sums) {
+    double s = block_sum(Vi, s_red);
+    if (threadIdx.x == 0) atomicAdd(&sums[1], s);
+  }
+}
+
+// Adjoint of P2G: G2P-shaped gathers of the grid gradients.
+template <typename T>
+__global__ void __launch_bounds__(256) k_p2g_adj(DGrid G, DParams<T> P, int64_t n,
+                                                  const int32_t* __restrict__ cell_old,
+                                                  const pos_t<T>* __restrict__ pos_old,
+                                                  const int32_t* __restrict__ cell_new,
+                                                  const pos_t<T>* __restrict__ pos_new,
+                                                  const vec_t<T>* __restrict__ fex, const double* __restrict__ galpha,
+                                                  const T* __restrict__ gu, const T* __restrict__ gv,
+                                                  const T* __restrict__ gw, vec_t<T>* __restrict__ gpos_old,
+                                                  vec_t<T>* __restrict__ gpos_new, vec_t<T>* __restrict__ gfex) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  T inv_dx = (T)G.inv_dx;
+  if (galpha && gpos_new) {
+    pos_t<T> pn = pos_new[i];
+    double r = (double)radius_of(pn);
+    double s = 4.0 / 3.0 * kPi * r * r * r * G.inv_dx * G.inv_dx * G.inv_dx;
+    int m[3];
+    double t[3];
+    granule_mac_fp64(G, cell_new[i], pn, m, t);
+    Stencil3<double> S = make_stencil<double>(G, m, t, 3);
+    FieldLoad<double> L;
+    L.f = galpha;
+    L.nsx = G.nx;
+    L.nsy = G.ny;
+    double g[3];
+    interp<double>(S, L, G.inv_dx, g);
+    vec_t<T> a = gpos_new[i];
+    gpos_new[i] = make_vec<T>(a.x + (T)(s * g[0]), a.y + (T)(s * g[1]), a.z + (T)(s * g[2]));
+  }
+  const T* gF[3] = {gu, gv, gw};
+  vec_t<T> f = fex[i];
+  T fv[3] = {f.x, f.y, f.z};
+  T gf[3] = {0, 0, 0}, gx[3] = {0, 0, 0};
+  int m[3];
+  T t[3];
+  granule_mac<T>(G, cell_old[i], pos_old[i], m, t);
+#pragma unroll
+  for (int comp = 0; comp < 3; ++comp) {
+    if (!gF[comp]) continue;
+    Stencil3<T> S = make_stencil<T>(G, m, t, comp);
+    T g[3];
+    T val = interp<T>(S, face_loader<T>(G, gF[comp], comp), inv_dx, g);
+    gf[comp] = P.exch * val;
+    for (int b = 0; b < 3; ++b) gx[b] += P.exch * fv[comp] * g[b];
+  }
+  if (gfex) gfex[i] = make_vec<T>(gf[0], gf[1], gf[2]);
+  if (gpos_old) {
+    vec_t<T> a = gpos_old[i];
+    gpos_old[i] = make_vec<T>(a.x + gx[0], a.y + gx[1], a.z + gx[2]);
+  }
+}
+
+template <typename T>
+static Fields<T> fields(const void* u, const void* v, const void* w, const void* p, const void* af) {
+  Fields<T> F;
+  F.u = (const T*)u;
+  F.v = (const T*)v;
+  F.w = (const T*)w;
+  F.p = (const T*)p;
+  F.af = (const T*)af;
+  return F;
+}
+
+}  // namespace gic
+
+using namespace gic;
+
+extern "C" int gic_g2p_couple(const GicGrid* grid, const GicParams* params, const GicGranules* s, const void* u,
+                              const void* v, const void* w, const void* p, const void* alpha_f, void* F_fl, void* a_f,
+                              void* alpha_f_p, gic_stream_t stream) {
+  DGrid G;
+  int rc = make_grid(grid, &G);
+  if (rc) return rc;
+  if ((rc = check_granules(s, "gic_g2p_couple"))) return rc;
+  if (s->n == 0) return GIC_OK;
+  if (!u || !v || !w || !p || !F_fl || !a_f) return set_error(GIC_ERR_INVALID, "gic_g2p_couple: null array");
+  if (alpha_f_p && !alpha_f) return set_error(GIC_ERR_INVALID, "gic_g2p_couple: alpha_f_p needs alpha_f");
+  if ((rc = check_vecs(s->precision, "gic_g2p_couple", {F_fl, a_f}))) return rc;
+  if (s->precision == GIC_FP32) {
+    DParams<float> P;
+    if ((rc = make_params(params, &P))) return rc;
+    k_g2p<float><<<grid_blocks(s->n, 256), 256, 0, stream>>>(G, P, s->n, s->cell, (const uint4*)s->pos,
+                                                              (const float4*)s->vel, fields<float>(u, v, w, p, alpha_f),
+                                                              (float4*)F_fl, (float4*)a_f, (float*)alpha_f_p,
+                                                              status_word());
+  } else {
+    DParams<double> P;
+    if ((rc = make_params(params, &P))) return rc;
+    k_g2p<double><<<grid_blocks(s->n, 256), 256, 0, stream>>>(
+        G, P, s->n, s->cell, (const d4*)s->pos, (const d4*)s->vel, fields<double>(u, v, w, p, alpha_f), (d4*)F_fl,
+        (d4*)a_f, (double*)alpha_f_p, status_word());
+  }
+  count_launches(1);
+  GIC_CHECK_LAUNCH("gic_g2p_couple");
+  return GIC_OK;
+}
+
+extern "C" int gic_g2p_couple_adj(const GicGrid* grid, const GicParams* params, const GicGranules* s, const void* u,
+                                  const void* v, const void* w, const void* p, const void* alpha_f, const void* gF_fl,
+                                  const void* ga_f, const void* galpha_f_p, void* g_pos, void* g_vel,
+                                  double* g_cdrag, gic_stream_t stream) {
+  DGrid G;
+  int rc = make_grid(grid, &G);
+  if (rc) return rc;
+  if ((rc = check_granules(s, "gic_g2p_couple_adj"))) return rc;
+  if (s->n == 0) return GIC_OK;
+  if (!u || !v || !w || !p || !gF_fl || !ga_f || !g_pos || !g_vel)
+    return set_error(GIC_ERR_INVALID, "gic_g2p_couple_adj: null array");
+  if (galpha_f_p && !alpha_f) return set_error(GIC_ERR_INVALID, "gic_g2p_couple_adj: galpha_f_p needs alpha_f");
+  if ((rc = check_vecs(s->precision, "gic_g2p_couple_adj", {gF_fl, ga_f, g_pos, g_vel}))) return rc;
+  if (s->precision == GIC_FP32) {
+    DParams<float> P;
+    if ((rc = make_params(params, &P))) return rc;
+    k_g2p_adj<float><<<grid_blocks(s->n, 256), 256, 0, stream>>>(
+        G, P, s->n, s->cell, (const uint4*)s->pos, (const float4*)s->vel, fields<float>(u, v, w, p, alpha_f),
+        (const float4*)gF_fl, (const float4*)ga_f, (const float*)galpha_f_p, (float4*)g_pos, (float4*)g_vel,
+        g_cdrag);
+  } else {
+    DParams<double> P;
+    if ((rc = make_params(params, &P))) return rc;
+    k_g2p_adj<double><<<grid_blocks(s->n, 256), 256, 0, stream>>>(
+        G, P, s->n, s->cell, (const d4*)s->pos, (const d4*)s->vel, fields<double>(u, v, w, p, alpha_f),
+        (const d4*)gF_fl, (const d4*)ga_f, (const double*)galpha_f_p, (d4*)g_pos, (d4*)g_vel, g_cdrag);
+  }
+  count_launches(1);
+  GIC_CHECK_LAUNCH("gic_g2p_couple_adj");
+  return GIC_OK;
+}
+
+extern "C" int gic_p2g(const GicGrid* grid, const GicParams* params, const GicGranules* old_, const GicGranules* new_,
+                       const void* f_ex, double* alpha_s, void* Fs_u, void* Fs_v, void* Fs_w, double* sums2,
+                       gic_stream_t stream) {
+  DGrid G;
+  int rc = make_grid(grid, &G);
+  if (rc) return rc;
+  if ((rc = check_granules(old_, "gic_p2g old"))) return rc;
+  if ((rc = check_granules(new_, "gic_p2g new"))) return rc;
+  if (old_->n != new_->n || old_->precision != new_->precision)
+    return set_error(GIC_ERR_INVALID, "gic_p2g: old/new differ in size or precision");
+  bool fs = Fs_u || Fs_v || Fs_w;
+  if (fs && !(Fs_u && Fs_v && Fs_w)) return set_error(GIC_ERR_INVALID, "gic_p2g: give all three F_s arrays or none");
+  if (fs && !f_ex && old_->n > 0) return set_error(GIC_ERR_INVALID, "gic_p2g: F_s needs f_ex");
+  if (sums2 && !alpha_s) return set_error(GIC_ERR_INVALID, "gic_p2g: sums2 needs alpha_s");
+  if ((rc = check_vecs(old_->precision, "gic_p2g", {f_ex}))) return rc;
+  int64_t n = old_->n;
+  int64_t ncell = (int64_t)G.nx * G.ny * G.nz;
+  int launches = 0;
+  if (alpha_s) {
+    k_zero<<<1184, 256, 0, stream>>>(alpha_s, ncell, sums2);
+    ++launches;
+  }
+  if (n > 0 && (alpha_s || fs)) {
+    if (old_->precision == GIC_FP32) {
+      DParams<float> P;
+      if ((rc = make_params(params, &P))) return rc;
+      k_p2g<float><<<grid_blocks(n, 256), 256, 0, stream>>>(
+          G, P, n, old_->cell, (const uint4*)old_->pos, new_->cell, (const uint4*)new_->pos, (const float4*)f_ex,
+          alpha_s, (float*)Fs_u, (float*)Fs_v, (float*)Fs_w, sums2);
+    } else {
+      DParams<double> P;
+      if ((rc = make_params(params, &P))) return rc;
+      k_p2g<double><<<grid_blocks(n, 256), 256, 0, stream>>>(
+          G, P, n, old_->cell, (const d4*)old_->pos, new_->cell, (const d4*)new_->pos, (const d4*)f_ex, alpha_s,
+          (double*)Fs_u, (double*)Fs_v, (double*)Fs_w, sums2);
+    }
+    ++launches;
+  }
+  if (sums2) {
+    k_alpha_sum<<<592, 256, 0, stream>>>(alpha_s, ncell, G.dx * G.dx * G.dx, sums2);
+    ++launches;
+  }
+  count_launches(launches);
+  GIC_CHECK_LAUNCH("gic_p2g");
+  return GIC_OK;
+}
+
+extern "C" int gic_p2g_adj(const GicGrid* grid, const GicParams* params, const GicGranules* old_,
+                           const GicGranules* new_, const void* f_ex, const double* g_alpha_s, const void* gFs_u,
+                           const void* gFs_v, const void* gFs_w, void* g_pos_old, void* g_pos_new, void* g_f_ex,
+                           gic_stream_t stream) {
+  DGrid G;
+  int rc = make_grid(grid, &G);
+  if (rc) return rc;
+  if ((rc = check_granules(old_, "gic_p2g_adj old"))) return rc;
+  if ((rc = check_granules(new_, "gic_p2g_adj new"))) return rc;
+  if (old_->n != new_->n || old_->precision != new_->precision)
+    return set_error(GIC_ERR_INVALID, "gic_p2g_adj: old/new differ in size or precision");
+  int64_t n = old_->n;
+  if (n == 0) return GIC_OK;
+  if (!f_ex) return set_error(GIC_ERR_INVALID, "gic_p2g_adj: f_ex is NULL");
+  if ((rc = check_vecs(old_->precision, "gic_p2g_adj", {f_ex, g_pos_old, g_pos_new, g_f_ex}))) return rc;
+  if (old_->precision == GIC_FP32) {
+    DParams<float> P;
+    if ((rc = make_params(params, &P))) return rc;
+    k_p2g_adj<float><<<grid_blocks(n, 256), 256, 0, stream>>>(
+        G, P, n, old_->cell, (const uint4*)old_->pos, new_->cell, (const uint4*)new_->pos, (const float4*)f_ex,
+        g_alpha_s, (const float*)gFs_u, (const float*)gFs_v, (const float*)gFs_w, (float4*)g_pos_old,
+        (float4*)g_pos_new, (float4*)g_f_ex);
+  } else {
+    DParams<double> P;
+    if ((rc = make_params(params, &P))) return rc;
+    k_p2g_adj<double><<<grid_blocks(n, 256), 256, 0, stream>>>(
+        G, P, n, old_->cell, (const d4*)old_->pos, new_->cell, (const d4*)new_->pos, (const d4*)f_ex, g_alpha_s,
+        (const double*)gFs_u, (const double*)gFs_v, (const double*)gFs_w, (d4*)g_pos_old, (d4*)g_pos_new,
+        (d4*)g_f_ex);
+  }
+  count_launches(1);
+  GIC_CHECK_LAUNCH("gic_p2g_adj");
+  return GIC_OK;
+}

@@ -1,0 +1,211 @@
+// gic_integrate.cu -- a4: virtual-mass symplectic Euler (Sec. 5.2 Eq. sand
+// kine; Alg. 2 MoveParticle) and its adjoint.
+//
+//   (m + m_a) a = F_c + F_fl + m g + m_a a_f,   m_a = (2/3) pi r^3 rho_f
+//   v' = v + dt' a,   x' = x + dt' v',   f_ex = F_fl + m_a (a_f - a)
+//
+// FP32 path: the position increment dt' v' is rounded to the 2^-30 h_c
+// fixed-point lattice of the cell offset and added in integer arithmetic, so
+// positions carry no floating-point drift; a carry or borrow moves the granule
+// to the neighbouring contact cell.  FP64 path: offsets are doubles re-binned
+// into [0, h_c).
+#include "gic_internal.cuh"
+
+namespace gic {
+
+template <typename T>
+struct Masses {
+  T m, ma;
+};
+
+template <typename T>
+__device__ __forceinline__ Masses<T> masses(const DParams<T>& P, T r) {
+  T V = T(4.0 / 3.0 * kPi) * r * r * r;
+  Masses<T> M;
+  M.m = P.rho_s * V;
+  M.ma = P.vm ? T(0.5) * P.rho_f * V : T(0);
+  return M;
+}
+
+__device__ __forceinline__ void advance_axis(const DGrid& G, float dt, float v, uint32_t q, int c, int nc,
+                                             uint32_t& q_out, int& c_out, uint32_t& flags) {
+  float inc_f = dt * v * G.inv_unit_f;
+  // clamp far beyond one cell so the integer conversion is defined
+  inc_f = fminf(fmaxf(inc_f, -0x1p40f), 0x1p40f);
+  long long inc = __float2ll_rn(inc_f);
+  long long s = (long long)q + inc;
+  long long shift = s >> kFracBits;  // floor division by 2^30
+  q_out = (uint32_t)(s & (long long)kFracMask);
+  long long cn = (long long)c + shift;
+  if (shift > 1 || shift < -1) flags |= GIC_STATUS_FAST;
+  if (cn < 0) {
+    cn = 0;
+    q_out = 0;
+    flags |= GIC_STATUS_OUT_OF_DOMAIN;
+  } else if (cn > nc - 1) {
+    cn = nc - 1;
+    q_out = kFracMask;
+    flags |= GIC_STATUS_OUT_OF_DOMAIN;
+  }
+  c_out = (int)cn;
+}
+
+__device__ __forceinline__ void advance_axis(const DGrid& G, double dt, double v, double o, int c, int nc,
+                                             double& o_out, int& c_out, uint32_t& flags) {
+  double x = o + dt * v;
+  double sh = floor(x * G.inv_hc);
+  if (!(fabs(sh) < 1e9)) sh = x > 0 ? 1e9 : -1e9;
+  long long shift = (long long)sh;
+  x -= sh * G.hc;
+  // guard against rounding just outside [0, h_c)
+  if (x < 0.0) x = 0.0;
+  if (x >= G.hc) x = nextafter(G.hc, 0.0);
+  if (shift > 1 || shift < -1) flags |= GIC_STATUS_FAST;
+  long long cn = (long long)c + shift;
+  if (cn < 0) {
+    cn = 0;
+    x = 0.0;
+    flags |= GIC_STATUS_OUT_OF_DOMAIN;
+  } else if (cn > nc - 1) {
+    cn = nc - 1;
+    x = nextafter(G.hc, 0.0);
+    flags |= GIC_STATUS_OUT_OF_DOMAIN;
+  }
+  o_out = x;
+  c_out = (int)cn;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_integrate(DGrid G, DParams<T> P, int64_t n, const int32_t* __restrict__ cell,
+                                                    const pos_t<T>* __restrict__ pos,
+                                                    const vec_t<T>* __restrict__ vel,
+                                                    const vec_t<T>* __restrict__ Fc, const vec_t<T>* __restrict__ Ffl,
+                                                    const vec_t<T>* __restrict__ af, int32_t* __restrict__ cell_out,
+                                                    pos_t<T>* __restrict__ pos_out, vec_t<T>* __restrict__ vel_out,
+                                                    vec_t<T>* __restrict__ fex, const int32_t* id_in, int32_t* id_out,
+                                                    uint32_t* status) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int32_t c = cell[i];
+  pos_t<T> p = pos[i];
+  vec_t<T> v = vel[i];
+  vec_t<T> fc = Fc[i], ff = Ffl[i], fa = af[i];
+  Masses<T> M = masses(P, radius_of(p));
+  T inv = T(1) / (M.m + M.ma);
+  T a0 = (fc.x + ff.x + M.m * P.g[0] + M.ma * fa.x) * inv;
+  T a1 = (fc.y + ff.y + M.m * P.g[1] + M.ma * fa.y) * inv;
+  T a2 = (fc.z + ff.z + M.m * P.g[2] + M.ma * fa.z) * inv;
+  T v0 = v.x + P.dt * a0, v1 = v.y + P.dt * a1, v2 = v.z + P.dt * a2;
+  uint32_t flags = 0;
+  if (!isfinite(v0) || !isfinite(v1) || !isfinite(v2)) flags |= GIC_STATUS_NONFINITE;
+  int c3[3] = {cell_x(c), cell_y(c), cell_z(c)};
+  int cn[3];
+  pos_t<T> po = p;
+  if constexpr (sizeof(T) == 4) {
+    advance_axis(G, P.dt, v0, p.x, c3[0], G.nc[0], po.x, cn[0], flags);
+    advance_axis(G, P.dt, v1, p.y, c3[1], G.nc[1], po.y, cn[1], flags);
+    advance_axis(G, P.dt, v2, p.z, c3[2], G.nc[2], po.z, cn[2], flags);
+  } else {
+    advance_axis(G, P.dt, v0, p.x, c3[0], G.nc[0], po.x, cn[0], flags);
+    advance_axis(G, P.dt, v1, p.y, c3[1], G.nc[1], po.y, cn[1], flags);
+    advance_axis(G, P.dt, v2, p.z, c3[2], G.nc[2], po.z, cn[2], flags);
+  }
+  if (flags) raise_status(status, flags);
+  cell_out[i] = pack_cell(cn[0], cn[1], cn[2]);
+  pos_out[i] = po;
+  vel_out[i] = make_vec<T>(v0, v1, v2);
+  if (fex) fex[i] = make_vec<T>(ff.x + M.ma * (fa.x - a0), ff.y + M.ma * (fa.y - a1), ff.z + M.ma * (fa.z - a2));
+  if (id_out && id_in && id_out != id_in) id_out[i] = id_in[i];
+}
+
+// From the gradients of (x', v', f_ex) to those of (x, v, F_c, F_fl, a_f).
+template <typename T>
+__global__ void __launch_bounds__(256) k_integrate_adj(DParams<T> P, int64_t n, const pos_t<T>* __restrict__ pos,
+                                                        const vec_t<T>* __restrict__ gxo,
+                                                        const vec_t<T>* __restrict__ gvo,
+                                                        const vec_t<T>* __restrict__ gfe, vec_t<T>* __restrict__ gxi,
+                                                        vec_t<T>* __restrict__ gvi, vec_t<T>* __restrict__ gFc,
+                                                        vec_t<T>* __restrict__ gFfl, vec_t<T>* __restrict__ gaf) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  Masses<T> M = masses(P, radius_of(pos[i]));
+  T inv = T(1) / (M.m + M.ma);
+  vec_t<T> gx = gxo[i], gv = gvo[i];
+  vec_t<T> gf = gfe ? gfe[i] : make_vec<T>(0, 0, 0);
+  // x' = x + dt v', v' = v + dt a
+  T gvt0 = gv.x + P.dt * gx.x, gvt1 = gv.y + P.dt * gx.y, gvt2 = gv.z + P.dt * gx.z;
+  // a enters v' (dt) and f_ex (-m_a)
+  T ga0 = P.dt * gvt0 - M.ma * gf.x, ga1 = P.dt * gvt1 - M.ma * gf.y, ga2 = P.dt * gvt2 - M.ma * gf.z;
+  gxi[i] = gx;
+  gvi[i] = make_vec<T>(gvt0, gvt1, gvt2);
+  gFc[i] = make_vec<T>(ga0 * inv, ga1 * inv, ga2 * inv);
+  gFfl[i] = make_vec<T>(ga0 * inv + gf.x, ga1 * inv + gf.y, ga2 * inv + gf.z);
+  gaf[i] = make_vec<T>(M.ma * (ga0 * inv + gf.x), M.ma * (ga1 * inv + gf.y), M.ma * (ga2 * inv + gf.z));
+}
+
+}  // namespace gic
+
+using namespace gic;
+
+extern "C" int gic_integrate(const GicGrid* grid, const GicParams* params, const GicGranules* in, const void* F_c,
+                             const void* F_fl, const void* a_f, GicGranules* out, void* f_ex, gic_stream_t stream) {
+  DGrid G;
+  int rc = make_grid(grid, &G);
+  if (rc) return rc;
+  if ((rc = check_granules(in, "gic_integrate in"))) return rc;
+  if ((rc = check_granules(out, "gic_integrate out"))) return rc;
+  if (in->n != out->n || in->precision != out->precision)
+    return set_error(GIC_ERR_INVALID, "gic_integrate: in/out differ in size or precision");
+  int64_t n = in->n;
+  if (n == 0) return GIC_OK;
+  if (!F_c || !F_fl || !a_f) return set_error(GIC_ERR_INVALID, "gic_integrate: null force array");
+  if ((rc = check_vecs(in->precision, "gic_integrate", {F_c, F_fl, a_f, f_ex}))) return rc;
+  if (in->precision == GIC_FP32) {
+    DParams<float> P;
+    if ((rc = make_params(params, &P))) return rc;
+    k_integrate<float><<<grid_blocks(n, 256), 256, 0, stream>>>(
+        G, P, n, in->cell, (const uint4*)in->pos, (const float4*)in->vel, (const float4*)F_c, (const float4*)F_fl,
+        (const float4*)a_f, out->cell, (uint4*)out->pos, (float4*)out->vel, (float4*)f_ex, in->id, out->id,
+        status_word());
+  } else {
+    DParams<double> P;
+    if ((rc = make_params(params, &P))) return rc;
+    k_integrate<double><<<grid_blocks(n, 256), 256, 0, stream>>>(
+        G, P, n, in->cell, (const d4*)in->pos, (const d4*)in->vel, (const d4*)F_c, (const d4*)F_fl, (const d4*)a_f,
+        out->cell, (d4*)out->pos, (d4*)out->vel, (d4*)f_ex, in->id, out->id, status_word());
+  }
+  count_launches(1);
+  GIC_CHECK_LAUNCH("gic_integrate");
+  return GIC_OK;
+}
+
+extern "C" int gic_integrate_adj(const GicGrid* grid, const GicParams* params, const GicGranules* in,
+                                 const void* g_pos_out, const void* g_vel_out, const void* g_f_ex, void* g_pos_in,
+                                 void* g_vel_in, void* gF_c, void* gF_fl, void* ga_f, gic_stream_t stream) {
+  DGrid G;
+  int rc = make_grid(grid, &G);
+  if (rc) return rc;
+  if ((rc = check_granules(in, "gic_integrate_adj"))) return rc;
+  int64_t n = in->n;
+  if (n == 0) return GIC_OK;
+  if (!g_pos_out || !g_vel_out || !g_pos_in || !g_vel_in || !gF_c || !gF_fl || !ga_f)
+    return set_error(GIC_ERR_INVALID, "gic_integrate_adj: null array");
+  if ((rc = check_vecs(in->precision, "gic_integrate_adj", {g_pos_out, g_vel_out, g_f_ex, g_pos_in, g_vel_in, gF_c, gF_fl, ga_f})))
+    return rc;
+  if (in->precision == GIC_FP32) {
+    DParams<float> P;
+    if ((rc = make_params(params, &P))) return rc;
+    k_integrate_adj<float><<<grid_blocks(n, 256), 256, 0, stream>>>(
+        P, n, (const uint4*)in->pos, (const float4*)g_pos_out, (const float4*)g_vel_out, (const float4*)g_f_ex,
+        (float4*)g_pos_in, (float4*)g_vel_in, (float4*)gF_c, (float4*)gF_fl, (float4*)ga_f);
+  } else {
+    DParams<double> P;
+    if ((rc = make_params(params, &P))) return rc;
+    k_integrate_adj<double><<<grid_blocks(n, 256), 256, 0, stream>>>(
+        P, n, (const d4*)in->pos, (const d4*)g_pos_out, (const d4*)g_vel_out, (const d4*)g_f_ex, (d4*)g_pos_in,
+        (d4*)g_vel_in, (d4*)gF_c, (d4*)gF_fl, (d4*)ga_f);
+  }
+  count_launches(1);
+  GIC_CHECK_LAUNCH("gic_integrate_adj");
+  return GIC_OK;
+}

@@ -1,0 +1,146 @@
+"""K-substep windows of the granule-grid coupling (Alg. 2 SandSubstep) on one GPU.
+
+`Simulator` owns the device buffers of one problem and runs substeps through
+the C ABI (sort -> contact -> G2P couple -> integrate -> P2G); `GicWindow` is
+the torch.autograd.Function that runs a window forward with a checkpoint
+every `ckpt` substeps and, backward, recomputes each segment from its
+checkpoint and walks the hand-written adjoints in reverse.
+
+Everything numeric runs in libgic.so kernels; torch provides memory and
+streams only.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from typing import List, Optional
+
+import torch
+
+from . import gic
+from .gic import GIC_FP32, GIC_FP64, State
+
+
+@dataclass
+class DeviceFluid:
+    u: torch.Tensor
+    v: torch.Tensor
+    w: torch.Tensor
+    p: torch.Tensor
+    alpha_f: torch.Tensor
+
+
+class Simulator:
+    """Device buffers + substep loop for one problem.
+
+    grid / params: objects with the fields of GicGrid / GicParams (e.g.
+    gic_inputs.Grid / Params).  The initial state comes from the canonical
+    encoding (cell int32 [n,3], q uint32 [n,3], r float32 [n], v float32 [n,3])
+    as host or device tensors.
+    """
+
+    def __init__(self, grid, params, n: int, precision: int = GIC_FP32, device="cuda"):
+        self.grid_obj = grid
+        self.params_obj = params
+        self.grid = gic.make_grid(grid)
+        self.params = gic.make_params(params)
+        self.n = int(n)
+        self.precision = precision
+        self.device = torch.device(device)
+        self.real = torch.float32 if precision == GIC_FP32 else torch.float64
+        n = self.n
+        self.A = State.empty(n, precision, device)
+        self.B = State.empty(n, precision, device)
+        self.perm = torch.empty(n, dtype=torch.int32, device=device)
+        self.table = gic.new_cell_table(self.grid, device)
+        self.ws = gic.new_workspace(self.grid, n, precision, device)
+        self.F_c = gic.vec4(n, precision, device)
+        self.F_fl = gic.vec4(n, precision, device)
+        self.a_f = gic.vec4(n, precision, device)
+        self.f_ex = gic.vec4(n, precision, device)
+        self.alpha_f_p = torch.zeros(n, dtype=self.real, device=device)
+        nx, ny, nz = grid.nx, grid.ny, grid.nz
+        self.alpha_s = torch.zeros(nx * ny * nz, dtype=torch.float64, device=device)
+        self.Fs = (torch.zeros((nx + 1) * ny * nz, dtype=self.real, device=device),
+                   torch.zeros(nx * (ny + 1) * nz, dtype=self.real, device=device),
+                   torch.zeros(nx * ny * (nz + 1), dtype=self.real, device=device))
+        self.sums = torch.zeros(2, dtype=torch.float64, device=device)
+        self.fluid: Optional[DeviceFluid] = None
+
+    # ------------------------------------------------------------ inputs
+    def set_fluid(self, u, v, w, p, alpha_f):
+        conv = lambda a: torch.as_tensor(a).to(device=self.device, dtype=self.real).contiguous()
+        self.fluid = DeviceFluid(conv(u), conv(v), conv(w), conv(p), conv(alpha_f))
+
+    def set_state(self, cell_xyz, q, r, v, stream=None):
+        dev = lambda a, dt: torch.as_tensor(a).to(device=self.device, dtype=dt).contiguous()
+        q64 = torch.as_tensor(q).to(torch.int64)
+        qi = q64.to(torch.int32)  # the 30-bit fractions fit in int32
+        gic.gic_pack(self.grid, dev(cell_xyz, torch.int32), dev(qi, torch.int32), dev(r, torch.float32),
+                     dev(v, torch.float32), self.A, stream)
+
+    @classmethod
+    def from_problem(cls, prob, precision=GIC_FP32, device="cuda"):
+        sim = cls(prob.grid, prob.params, prob.n, precision, device)
+        sim.set_fluid(prob.u, prob.vf, prob.wf, prob.p, prob.alpha_f)
+        sim.set_state(prob.cell, prob.q, prob.r, prob.v)
+        return sim
+
+    # ------------------------------------------------------------ substeps
+    def substep(self, alpha: bool = True, transfer: bool = True, sums: bool = True, stream=None):
+        """One SandSubstep: A (current) -> sort -> B -> forces -> A (next)."""
+        F = self.fluid
+        gic.gic_sort(self.grid, self.A, self.B, self.perm, self.table, self.ws, stream)
+        gic.gic_contact(self.grid, self.params, self.B, self.table, self.F_c, stream)
+        gic.gic_g2p_couple(self.grid, self.params, self.B, F.u, F.v, F.w, F.p, F.alpha_f, self.F_fl, self.a_f,
+                           self.alpha_f_p, stream)
+        gic.gic_integrate(self.grid, self.params, self.B, self.F_c, self.F_fl, self.a_f, self.A, self.f_ex, stream)
+        gic.gic_p2g(self.grid, self.params, self.B, self.A, self.f_ex, self.alpha_s if alpha else None,
+                    self.Fs if transfer else (None, None, None), self.sums if (sums and alpha) else None, stream)
+
+    def substep_probe(self, acc, stream=None):
+        """substep() with CUDA events around every entry point: appends
+        (start, end) event pairs to acc[name] (timing only)."""
+        s = torch.cuda.current_stream() if stream is None else stream
+        F = self.fluid
+
+        def timed(name, fn):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(s)
+            fn()
+            b.record(s)
+            acc.setdefault(name, []).append((a, b))
+
+        timed("gic_sort", lambda: gic.gic_sort(self.grid, self.A, self.B, self.perm, self.table, self.ws, s))
+        timed("gic_contact", lambda: gic.gic_contact(self.grid, self.params, self.B, self.table, self.F_c, s))
+        timed("gic_g2p_couple", lambda: gic.gic_g2p_couple(self.grid, self.params, self.B, F.u, F.v, F.w, F.p,
+                                                            F.alpha_f, self.F_fl, self.a_f, self.alpha_f_p, s))
+        timed("gic_integrate", lambda: gic.gic_integrate(self.grid, self.params, self.B, self.F_c, self.F_fl,
+                                                          self.a_f, self.A, self.f_ex, s))
+        timed("gic_p2g", lambda: gic.gic_p2g(self.grid, self.params, self.B, self.A, self.f_ex, self.alpha_s, self.Fs,
+                                              self.sums, s))
+
+    def zero_transfer(self):
+        for f in self.Fs:
+            f.zero_()
+
+    def run(self, K: int, stream=None, alpha_every: bool = True):
+        """K substeps; F_s accumulates from zero; alpha_s and sums are those of
+        the last substep (every substep recomputes them unless alpha_every is
+        False, in which case only the last does)."""
+        self.zero_transfer()
+        for s in range(K):
+            last = s == K - 1
+            self.substep(alpha=alpha_every or last, sums=alpha_every or last, stream=stream)
+
+    # ------------------------------------------------------------ outputs
+    def positions(self, state: Optional[State] = None):
+        """(x, v) FP64 [n, 3] in original granule order."""
+        st = self.A if state is None else state
+        x = torch.empty((self.n, 3), dtype=torch.float64, device=self.device)
+        v = torch.empty((self.n, 3), dtype=torch.float64, device=self.device)
+        gic.gic_unpack(self.grid, st, x, v)
+        return x, v
+
+    def status(self, clear=True) -> int:
+        return gic.gic_check_status(clear=clear)

@@ -1,0 +1,85 @@
+"""Host-side checks of the C ABI library (no GPU needed).
+
+The library loads, exports every entry point include/gic.h declares, and its
+host-side argument validation returns the documented error codes before any
+device work is enqueued.
+"""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "gic.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(gic_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2504_00745_gb300 import gic
+    return gic.lib()
+
+
+def test_header_declares_the_hot_path():
+    names = _declared()
+    for need in ["gic_sort", "gic_contact", "gic_g2p_couple", "gic_integrate", "gic_p2g", "gic_sort_adj",
+                 "gic_contact_adj", "gic_g2p_couple_adj", "gic_integrate_adj", "gic_p2g_adj"]:
+        assert need in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_version_and_launch_counter(lib):
+    from paper_2504_00745_gb300 import gic
+    assert "sm_103a" in gic.gic_version()
+    assert gic.launch_count() >= 0
+
+
+def test_grid_validation_codes():
+    from paper_2504_00745_gb300 import gic
+    bad = [gic.GicGrid(1, 4, 4, 1, 0.1, (C.c_double * 3)(0, 0, 0)),       # < 2 cells
+           gic.GicGrid(4, 4, 4, 0, 0.1, (C.c_double * 3)(0, 0, 0)),       # k < 1
+           gic.GicGrid(4, 4, 4, 1, -0.1, (C.c_double * 3)(0, 0, 0)),      # dx <= 0
+           gic.GicGrid(600, 4, 4, 2, 0.1, (C.c_double * 3)(0, 0, 0))]     # > 1024 contact cells
+    for g in bad:
+        b = C.c_size_t(0)
+        assert gic.lib().gic_workspace_size(C.byref(g), 10, 0, C.byref(b)) == -1
+        assert "grid" in gic.last_error() or "cells" in gic.last_error() or "dx" in gic.last_error() \
+            or "k_contact" in gic.last_error()
+
+
+def test_sizes():
+    from paper_2504_00745_gb300 import gic
+    g = gic.GicGrid(32, 16, 8, 3, 1 / 32, (C.c_double * 3)(0, 0, 0))
+    assert gic.gic_cell_table_size(g) == 16 * (1 + 96 * 48 * 24)
+    a = gic.gic_workspace_size(g, 1000, 0)
+    b = gic.gic_workspace_size(g, 100000, 0)
+    assert 0 < a < b
+    assert b >= 4 * 4 * 100000  # two ping-pong (key, value) pairs
+
+
+def test_null_arguments_are_rejected_on_the_host():
+    from paper_2504_00745_gb300 import gic
+    L = gic.lib()
+    g = gic.GicGrid(8, 8, 8, 1, 1 / 8, (C.c_double * 3)(0, 0, 0))
+    p = gic.GicParams(2650, 1000, 1e5, 0.3, 1, 0.5, 0.22, (C.c_double * 3)(0, 0, -9.8), 1e-5, 1e-4, 1, 1)
+    s = gic.GicGranules(10, None, None, None, None, 0)
+    assert L.gic_contact(C.byref(g), C.byref(p), C.byref(s), None, None, None) == -1
+    assert L.gic_sort(C.byref(g), C.byref(s), C.byref(s), None, None, None, 0, None) == -1
+    s2 = gic.GicGranules(10, None, None, None, None, 7)
+    assert L.gic_integrate(C.byref(g), C.byref(p), C.byref(s2), None, None, None, C.byref(s2), None, None) == -1
+    assert "precision" in gic.last_error()
+    bad_p = gic.GicParams(-1, 1000, 1e5, 0.3, 1, 0.5, 0.22, (C.c_double * 3)(0, 0, -9.8), 1e-5, 1e-4, 1, 1)
+    empty = gic.GicGranules(0, None, None, None, None, 0)
+    # an empty problem is valid and enqueues nothing
+    assert L.gic_contact(C.byref(g), C.byref(bad_p), C.byref(empty), C.c_void_p(16), None, None) == 0
+    assert L.gic_sort_adj(0, 0, None, None, None, None, None, None) == 0
+    assert L.gic_sort_adj(5, 0, None, None, None, None, None, None) == -1

@@ -1,0 +1,406 @@
+"""GPU parity: every step of the substep through the C ABI against the FP64
+oracle, element by element, on seeded inputs.
+
+Tolerances (stated by the workload definition for the FP32 path, derived from
+the arithmetic where it states none):
+  * sort permutation, cell table and contact-pair sets: bit-exact;
+  * after 10 substeps: positions <= 1e-5 dx, velocities <= 1e-4 v_ref
+    (v_ref = largest oracle speed), alpha_s <= 1e-9 absolute;
+  * single kernels: see each test.
+"""
+import numpy as np
+import pytest
+import torch
+
+import gic_inputs as gi
+import oracle
+from gpu_util import FP32, FP64, by_id, oracle_inputs, shuffled, sim_for, subset, tol_force
+from paper_2504_00745_gb300 import gic
+from paper_2504_00745_gb300.window import Simulator
+
+pytestmark = pytest.mark.gpu
+
+SMALL = ["plain_fp64_8k", "dense_block", "random_cloud"]
+PRECS = [FP32, FP64]
+
+
+@pytest.fixture(autouse=True)
+def _clear_status():
+    torch.cuda.synchronize()
+    gic.gic_check_status(clear=True)
+    yield
+
+
+def _problem(name, shuffle=True):
+    p = gi.make(name)
+    return shuffled(p) if shuffle else p
+
+
+# ----------------------------------------------------------------------------- a1 sort
+
+@pytest.mark.parametrize("name", SMALL + ["ragged_2049", "ragged_6145"])
+@pytest.mark.parametrize("prec", PRECS)
+def test_sort_bit_exact(name, prec):
+    if name.startswith("ragged"):
+        base = shuffled(gi.make("dense_block", n_side=(10, 10, 10)))
+        prob = subset(base, int(name.split("_")[1]))
+    else:
+        prob = _problem(name)
+    sim = sim_for(prob, prec)
+    gic.gic_sort(sim.grid, sim.A, sim.B, sim.perm, sim.table, sim.ws)
+    torch.cuda.synchronize()
+    x, _, _ = oracle_inputs(prob)
+    c = oracle.cells(prob.grid, x)
+    assert np.array_equal(c, prob.cell)
+    perm_o, keys_o = oracle.sort(c)
+    perm_g = sim.perm.cpu().numpy()
+    assert np.array_equal(perm_g, perm_o)
+    # the state moved with the permutation, ids included
+    assert np.array_equal(sim.B.id.cpu().numpy(), perm_o)
+    assert torch.equal(sim.B.pos.cpu(), sim.A.pos.cpu()[perm_o])
+    assert torch.equal(sim.B.vel.cpu(), sim.A.vel.cpu()[perm_o])
+    assert torch.equal(sim.B.cell.cpu(), sim.A.cell.cpu()[perm_o])
+    # cell table: exactly the occupied cells carry the current epoch, with the
+    # oracle's (start, count)
+    ck, st, ct = oracle.cell_table(keys_o)
+    tab = sim.table.view(-1, 4).cpu().numpy().astype(np.int64)
+    epoch = tab[0, 0]
+    assert epoch >= 1
+    nc = prob.grid.nc
+    cs = c[perm_o[st]]
+    lin = 1 + cs[:, 0] + nc[0] * (cs[:, 1] + nc[1] * cs[:, 2])
+    assert np.array_equal(tab[lin, 0], st)
+    assert np.array_equal(tab[lin, 1], ct)
+    assert np.all(tab[lin, 2] == epoch)
+    assert int((tab[1:, 2] == epoch).sum()) == len(ck)
+
+
+def test_sort_epochs_do_not_leak_between_calls():
+    """A second sort of a different state must not see cells occupied only in
+    the first one (the epoch tag retires them without a clear)."""
+    prob = _problem("dense_block")
+    sim = sim_for(prob, FP32)
+    gic.gic_sort(sim.grid, sim.A, sim.B, sim.perm, sim.table, sim.ws)
+    prob2 = subset(prob, 100)
+    sim2 = Simulator(prob2.grid, prob2.params, prob2.n)
+    sim2.table = sim.table  # reuse the table
+    sim2.set_fluid(prob.u, prob.vf, prob.wf, prob.p, prob.alpha_f)
+    sim2.set_state(prob2.cell, prob2.q, prob2.r, prob2.v)
+    gic.gic_sort(sim2.grid, sim2.A, sim2.B, sim2.perm, sim2.table, sim2.ws)
+    torch.cuda.synchronize()
+    tab = sim.table.view(-1, 4).cpu().numpy()
+    epoch = tab[0, 0]
+    occupied = len(np.unique(prob2.cell, axis=0))
+    assert int((tab[1:, 2] == epoch).sum()) == occupied
+
+
+# ----------------------------------------------------------------------------- a2 contact
+
+@pytest.mark.parametrize("name", SMALL)
+@pytest.mark.parametrize("prec", PRECS)
+def test_contact_pairs_bit_exact(name, prec):
+    prob = _problem(name)
+    sim = sim_for(prob, prec)
+    gic.gic_sort(sim.grid, sim.A, sim.B, sim.perm, sim.table, sim.ws)
+    counts = torch.zeros(prob.n, dtype=torch.int32, device="cuda")
+    cap = 20 * prob.n
+    pairs = torch.zeros((cap, 2), dtype=torch.int32, device="cuda")
+    npairs = torch.zeros(1, dtype=torch.int64, device="cuda")
+    gic.gic_contact_pairs(sim.grid, sim.B, sim.table, counts, pairs, npairs)
+    torch.cuda.synchronize()
+    m = int(npairs.item())
+    assert m <= cap
+    got = set(map(tuple, pairs[:m].cpu().numpy().tolist()))
+    x, v, r = oracle_inputs(prob)
+    want = oracle.contact_pairs(prob.grid, x, r, brute=prob.n <= 3000)
+    want = set(map(tuple, np.sort(want, axis=1).tolist()))
+    assert got == want
+    per = np.zeros(prob.n, np.int64)
+    for a, b in want:
+        per[a] += 1
+        per[b] += 1
+    assert np.array_equal(by_id(counts, sim.B.id), per)
+
+
+@pytest.mark.parametrize("name", SMALL)
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("walls", [1, 0])
+def test_contact_force_parity(name, prec, walls):
+    prob = _problem(name)
+    prob.params.walls = walls
+    sim = sim_for(prob, prec)
+    gic.gic_sort(sim.grid, sim.A, sim.B, sim.perm, sim.table, sim.ws)
+    gic.gic_contact(sim.grid, sim.params, sim.B, sim.table, sim.F_c)
+    torch.cuda.synchronize()
+    assert gic.gic_check_status() == 0
+    F = by_id(sim.F_c, sim.B.id)[:, :3].astype(np.float64)
+    x, v, r = oracle_inputs(prob)
+    Fo, st = oracle.contact(prob.grid, prob.params, x, v, r)
+    assert st == 0
+    scale = max(np.abs(Fo).max(), 1e-30)
+    atol = tol_force(prob, prec) + (1e-5 if prec == FP32 else 1e-11) * scale
+    assert np.abs(F - Fo).max() <= atol, (np.abs(F - Fo).max(), atol, scale)
+
+
+# ----------------------------------------------------------------------------- a3 G2P
+
+@pytest.mark.parametrize("name", SMALL)
+@pytest.mark.parametrize("prec", PRECS)
+def test_g2p_parity(name, prec):
+    prob = _problem(name)
+    sim = sim_for(prob, prec)
+    F = sim.fluid
+    gic.gic_g2p_couple(sim.grid, sim.params, sim.A, F.u, F.v, F.w, F.p, F.alpha_f, sim.F_fl, sim.a_f, sim.alpha_f_p)
+    torch.cuda.synchronize()
+    x, v, r = oracle_inputs(prob)
+    Ffl_o, af_o, alp_o = oracle.g2p(prob.grid, prob.params, x, v, r, prob.u, prob.vf, prob.wf, prob.p,
+                                     prob.alpha_f)
+    rtol = 2e-6 if prec == FP32 else 1e-12
+    Ffl = sim.F_fl.cpu().numpy()[:, :3]
+    af = sim.a_f.cpu().numpy()[:, :3]
+    alp = sim.alpha_f_p.cpu().numpy()
+    assert np.abs(Ffl - Ffl_o).max() <= rtol * np.abs(Ffl_o).max()
+    assert np.abs(af - af_o).max() <= rtol * np.abs(af_o).max()
+    assert np.abs(alp - alp_o).max() <= rtol
+
+
+# ----------------------------------------------------------------------------- a4 integrate
+
+@pytest.mark.parametrize("name", SMALL)
+@pytest.mark.parametrize("prec", PRECS)
+def test_integrate_parity(name, prec):
+    prob = _problem(name)
+    sim = sim_for(prob, prec)
+    x, v, r = oracle_inputs(prob)
+    rng = np.random.default_rng(3)
+    m = prob.params.rho_s * 4 / 3 * np.pi * r ** 3
+    # forces of a few hundred g, rounded to the GPU's precision so both sides read the same numbers
+    real = np.float32 if prec == FP32 else np.float64
+    Fc = (rng.normal(size=(prob.n, 3)) * 300 * 9.8 * m[:, None]).astype(real)
+    Ffl = (rng.normal(size=(prob.n, 3)) * 3 * 9.8 * m[:, None]).astype(real)
+    af = rng.normal(size=(prob.n, 3)).astype(real) * real(5)
+    to4 = lambda a: torch.from_numpy(np.concatenate([a, np.zeros((prob.n, 1), real)], 1)).cuda()
+    gic.gic_integrate(sim.grid, sim.params, sim.A, to4(Fc), to4(Ffl), to4(af), sim.B, sim.f_ex)
+    torch.cuda.synchronize()
+    xg, vg = sim.positions(sim.B)
+    xo, vo, fo, st = oracle.integrate(prob.grid, prob.params, x, v, r, Fc, Ffl, af)
+    unit = prob.grid.h_c * 2.0 ** -30
+    xtol = 2 * unit if prec == FP32 else 1e-15
+    assert np.abs(xg.cpu().numpy() - xo).max() <= xtol
+    vtol = 2e-6 if prec == FP32 else 1e-13
+    assert np.abs(vg.cpu().numpy() - vo).max() <= vtol * np.abs(vo).max()
+    fg = sim.f_ex.cpu().numpy()[:, :3]
+    assert np.abs(fg - fo).max() <= vtol * np.abs(fo).max()
+    assert np.array_equal(sim.B.id.cpu().numpy(), np.arange(prob.n))
+
+
+# ----------------------------------------------------------------------------- a5 P2G
+
+@pytest.mark.parametrize("name", SMALL)
+@pytest.mark.parametrize("prec", PRECS)
+def test_p2g_parity(name, prec):
+    prob = _problem(name)
+    sim = sim_for(prob, prec)
+    real = np.float32 if prec == FP32 else np.float64
+    rng = np.random.default_rng(5)
+    # a moved copy of the state: one substep with arbitrary forces
+    x, v, r = oracle_inputs(prob)
+    m = prob.params.rho_s * 4 / 3 * np.pi * r ** 3
+    Fc = (rng.normal(size=(prob.n, 3)) * 3000 * 9.8 * m[:, None]).astype(real)
+    z = np.zeros((prob.n, 3), real)
+    to4 = lambda a: torch.from_numpy(np.concatenate([a, np.zeros((prob.n, 1), real)], 1)).cuda()
+    gic.gic_integrate(sim.grid, sim.params, sim.A, to4(Fc), to4(z), to4(z), sim.B, sim.f_ex)
+    fex = (rng.normal(size=(prob.n, 3)) * 9.8 * m[:, None]).astype(real)
+    sim.f_ex.copy_(to4(fex))
+    sim.zero_transfer()
+    gic.gic_p2g(sim.grid, sim.params, sim.A, sim.B, sim.f_ex, sim.alpha_s, sim.Fs, sim.sums)
+    torch.cuda.synchronize()
+    xa, _ = sim.positions(sim.A)
+    xb, _ = sim.positions(sim.B)
+    a_o, Fs_o, sums_o = oracle.p2g(prob.grid, prob.params, xa.cpu().numpy(), xb.cpu().numpy(), r, fex)
+    ag = sim.alpha_s.cpu().numpy()
+    assert np.abs(ag - a_o).max() <= 1e-9
+    sums = sim.sums.cpu().numpy()
+    assert abs(sums[1] - sums_o[1]) <= 1e-13 * sums_o[1]
+    assert abs(sums[0] - sums[1]) <= 1e-12 * sums[1]
+    ftol = 2e-6 if prec == FP32 else 1e-12
+    for c in range(3):
+        fg = sim.Fs[c].cpu().numpy()
+        assert np.abs(fg - Fs_o[c]).max() <= ftol * np.abs(Fs_o[c]).max()
+
+
+# ----------------------------------------------------------------------------- windows
+
+@pytest.mark.parametrize("name", SMALL)
+@pytest.mark.parametrize("prec", PRECS)
+def test_window_10_substeps(name, prec):
+    prob = _problem(name)
+    K = 10
+    sim = sim_for(prob, prec)
+    sim.run(K)
+    x, v = sim.positions()
+    torch.cuda.synchronize()
+    st = gic.gic_check_status()
+    ref = oracle.run(prob, K=K)
+    assert st == ref["status"] == 0
+    dx = prob.grid.dx
+    ex = np.abs(x.cpu().numpy() - ref["x"]).max()
+    vref = np.linalg.norm(ref["v"], axis=1).max()
+    ev = np.linalg.norm(v.cpu().numpy() - ref["v"], axis=1).max()
+    ea = np.abs(sim.alpha_s.cpu().numpy() - ref["alpha_s"]).max()
+    if prec == FP32:
+        assert ex <= 1e-5 * dx, ex
+        assert ev <= 1e-4 * vref, (ev, vref)
+        assert ea <= 1e-9, ea
+    else:
+        assert ex <= 1e-12 * dx
+        assert ev <= 1e-10 * vref
+        assert ea <= 1e-12
+    sums = sim.sums.cpu().numpy()
+    assert abs(sums[0] - sums[1]) <= 1e-12 * sums[1]
+    assert abs(sums[1] - ref["sums"][1]) <= 1e-13 * sums[1]
+    for c in range(3):
+        fo = ref["Fs"][c]
+        fg = sim.Fs[c].cpu().numpy()
+        assert np.abs(fg - fo).max() <= (1e-4 if prec == FP32 else 1e-10) * np.abs(fo).max()
+
+
+# ----------------------------------------------------------------------------- edge cases
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_empty_problem(prec):
+    prob = subset(gi.make("dense_block"), 0)
+    sim = Simulator(prob.grid, prob.params, 0, prec)
+    sim.set_fluid(prob.u, prob.vf, prob.wf, prob.p, prob.alpha_f)
+    sim.alpha_s.fill_(7.0)
+    sim.sums.fill_(7.0)
+    sim.run(3)
+    torch.cuda.synchronize()
+    assert float(sim.alpha_s.abs().max()) == 0.0
+    assert sim.sums.cpu().tolist() == [0.0, 0.0]
+    assert gic.gic_check_status() == 0
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_single_granule_matches_oracle(prec):
+    prob = subset(gi.make("random_cloud"), 1)
+    sim = sim_for(prob, prec)
+    sim.run(10)
+    x, v = sim.positions()
+    ref = oracle.run(prob, K=10)
+    assert np.abs(x.cpu().numpy() - ref["x"]).max() <= 1e-5 * prob.grid.dx
+    assert np.abs(v.cpu().numpy() - ref["v"]).max() <= 1e-4 * np.abs(ref["v"]).max()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_out_of_domain_is_flagged_not_faulted(prec):
+    prob = subset(gi.make("dense_block"), 64)
+    prob.v = prob.v.copy()
+    prob.v[3] = [-1e4, 0, 0]  # crosses the x = 0 wall in one substep
+    sim = sim_for(prob, prec)
+    sim.run(1)
+    torch.cuda.synchronize()
+    st = gic.gic_check_status()
+    assert st & gic.STATUS_OUT_OF_DOMAIN
+    assert st & gic.STATUS_FAST
+    ref = oracle.run(prob, K=1)
+    assert ref["status"] & oracle.OUT_OF_DOMAIN
+    x, _ = sim.positions()
+    assert np.all(np.isfinite(x.cpu().numpy()))
+    assert x.cpu().numpy()[3, 0] >= 0.0
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_coincident_pair_is_skipped_and_flagged(prec):
+    prob = subset(gi.make("random_cloud"), 50)
+    prob.cell = prob.cell.copy()
+    prob.q = prob.q.copy()
+    prob.cell[1] = prob.cell[0]
+    prob.q[1] = prob.q[0]
+    sim = sim_for(prob, prec)
+    gic.gic_sort(sim.grid, sim.A, sim.B, sim.perm, sim.table, sim.ws)
+    gic.gic_contact(sim.grid, sim.params, sim.B, sim.table, sim.F_c)
+    torch.cuda.synchronize()
+    assert gic.gic_check_status() & gic.STATUS_COINCIDENT
+    x, v, r = oracle_inputs(prob)
+    Fo, st = oracle.contact(prob.grid, prob.params, x, v, r)
+    assert st & oracle.COINCIDENT
+    F = by_id(sim.F_c, sim.B.id)[:, :3]
+    assert np.abs(F - Fo).max() <= tol_force(prob, prec) + 1e-5 * max(np.abs(Fo).max(), 1.0)
+
+
+def test_nonfinite_velocity_is_flagged():
+    prob = subset(gi.make("random_cloud"), 40)
+    prob.v = prob.v.copy()
+    prob.v[5] = [np.nan, 0, 0]
+    sim = sim_for(prob, FP32)
+    sim.run(1)
+    torch.cuda.synchronize()
+    assert gic.gic_check_status() & gic.STATUS_NONFINITE
+
+
+def test_host_errors_with_device_buffers():
+    prob = gi.make("dense_block")
+    sim = sim_for(prob, FP32)
+    small = torch.empty(64, dtype=torch.uint8, device="cuda")
+    with pytest.raises(gic.GicError, match="workspace"):
+        gic.gic_sort(sim.grid, sim.A, sim.B, sim.perm, sim.table, small)
+    with pytest.raises(gic.GicError, match="alias"):
+        gic.gic_sort(sim.grid, sim.A, sim.A, sim.perm, sim.table, sim.ws)
+    s = sim.A.struct()
+    s.pos = s.pos + 4  # misaligned by 4 bytes
+    rc = gic.lib().gic_contact(gic.C.byref(sim.grid), gic.C.byref(sim.params), gic.C.byref(s),
+                               gic.C.c_void_p(sim.table.data_ptr()), gic.C.c_void_p(sim.F_c.data_ptr()), None)
+    assert rc == -4
+
+
+# ----------------------------------------------------------------------------- full size (sampled)
+
+@pytest.mark.slow
+def test_dam_break_full_size_one_substep():
+    """1M granules, 128^3: one substep in the launch configuration the
+    benchmark uses, every output compared with the oracle (sort bit-exact)."""
+    prob = gi.make("dam_break_1m")
+    sim = sim_for(prob, FP32)
+    gic.gic_sort(sim.grid, sim.A, sim.B, sim.perm, sim.table, sim.ws)
+    gic.gic_contact(sim.grid, sim.params, sim.B, sim.table, sim.F_c)
+    F = sim.fluid
+    gic.gic_g2p_couple(sim.grid, sim.params, sim.B, F.u, F.v, F.w, F.p, F.alpha_f, sim.F_fl, sim.a_f, sim.alpha_f_p)
+    torch.cuda.synchronize()
+    x, v, r = oracle_inputs(prob)
+    perm_o, _ = oracle.sort(prob.cell)
+    assert np.array_equal(sim.perm.cpu().numpy(), perm_o)
+    Fo, st = oracle.contact(prob.grid, prob.params, x, v, r)
+    Fg = by_id(sim.F_c, sim.B.id)[:, :3]
+    assert np.abs(Fg - Fo).max() <= tol_force(prob, FP32) + 1e-5 * np.abs(Fo).max()
+    Ffl_o, af_o, _ = oracle.g2p(prob.grid, prob.params, x, v, r, prob.u, prob.vf, prob.wf, prob.p, prob.alpha_f)
+    Ffl = by_id(sim.F_fl, sim.B.id)[:, :3]
+    assert np.abs(Ffl - Ffl_o).max() <= 2e-6 * np.abs(Ffl_o).max()
+    # the rest of the substep, then alpha_s against the oracle at the GPU's new positions
+    gic.gic_integrate(sim.grid, sim.params, sim.B, sim.F_c, sim.F_fl, sim.a_f, sim.A, sim.f_ex)
+    sim.zero_transfer()
+    gic.gic_p2g(sim.grid, sim.params, sim.B, sim.A, sim.f_ex, sim.alpha_s, sim.Fs, sim.sums)
+    xb, _ = sim.positions(sim.B)
+    xa, _ = sim.positions(sim.A)
+    fex = by_id(sim.f_ex, sim.A.id)[:, :3].astype(np.float64)
+    a_o, Fs_o, sums_o = oracle.p2g(prob.grid, prob.params, xb.cpu().numpy(), xa.cpu().numpy(), r, fex)
+    assert np.abs(sim.alpha_s.cpu().numpy() - a_o).max() <= 1e-9
+    for c in range(3):
+        assert np.abs(sim.Fs[c].cpu().numpy() - Fs_o[c]).max() <= 2e-6 * np.abs(Fs_o[c]).max()
+    assert gic.gic_check_status() == 0
+
+
+@pytest.mark.slow
+def test_dam_break_full_size_window():
+    """1M granules, 10 substeps, against the oracle's 10 substeps."""
+    prob = gi.make("dam_break_1m")
+    K = 10
+    sim = sim_for(prob, FP32)
+    sim.run(K)
+    x, v = sim.positions()
+    ref = oracle.run(prob, K=K)
+    dx = prob.grid.dx
+    assert np.abs(x.cpu().numpy() - ref["x"]).max() <= 1e-5 * dx
+    vref = np.linalg.norm(ref["v"], axis=1).max()
+    assert np.linalg.norm(v.cpu().numpy() - ref["v"], axis=1).max() <= 1e-4 * vref
+    assert np.abs(sim.alpha_s.cpu().numpy() - ref["alpha_s"]).max() <= 1e-9
