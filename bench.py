@@ -34,7 +34,7 @@ ALGO_BYTES = {"gic_sort": 88, "gic_contact": 48, "gic_g2p_couple": 65, "gic_inte
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="dam_break_1m")
@@ -326,7 +326,7 @@ def run_e2e(prob, sim, gic, torch, np, dev, stream, steps):
             for m in ((nx + 1) * ny * nz, nx * (ny + 1) * nz, nx * ny * (nz + 1))]
     o_s = torch.empty(2, dtype=torch.float64).pin_memory()
     fn = L.gic_window_forward_host
-    fn.argtypes = [C.c_void_p] * 2 + [C.c_int64, C.c_int32] + [C.c_void_p] * 9 + [C.c_int32] + [C.c_void_p] * 7 + \
+    fn.argtypes = [C.c_void_p] * 2 + [C.c_int64, C.c_int32] + [C.c_void_p] * 9 + [C.c_int32] + [C.c_void_p] * 8 + \
         [C.c_size_t, C.c_void_p]
     p = lambda t: C.c_void_p(t.data_ptr())
 

@@ -17,7 +17,7 @@ import subprocess
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = [os.path.join(_HERE, "gic_oracle.c"), os.path.join(_HERE, "gic_oracle_adj.c")]
+_SRC = [os.path.join(_HERE, "gic_oracle.c")]
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
 
@@ -233,3 +233,86 @@ def run(prob, K=None, brute=False, x=None, v=None, params=None):
                  _p(v), _p(r), *[_p(a) for a in fl], _p(alpha), _p(Fs[0]), _p(Fs[1]), _p(Fs[2]), _p(sums),
                  C.c_int(int(brute)), C.byref(st))
     return dict(x=x, v=v, alpha_s=alpha, Fs=Fs, sums=sums, status=st.value)
+
+
+# ---------------------------------------------------------------- adjoints
+
+def contact_adj(grid, params, x, v, r, gF, brute=False):
+    """(gx, gv, g_mu) of <gF, contact(x, v)>."""
+    x, v, r, gF = map(_f64, (x, v, r, gF))
+    n = x.shape[0]
+    gx = np.zeros((n, 3))
+    gv = np.zeros((n, 3))
+    gmu = C.c_double(0.0)
+    lib().or_contact_adj(C.byref(grid_struct(grid)), C.byref(params_struct(params)), C.c_int64(n), _p(x), _p(v),
+                         _p(r), _p(gF), C.c_int(int(brute)), _p(gx), _p(gv), C.byref(gmu))
+    return gx, gv, gmu.value
+
+
+def g2p_adj(grid, params, x, v, r, u, vf, wf, p, af, gFfl, gaf, galpha=None):
+    """(gx, gv, g_cdrag) of <gFfl, F_fl> + <gaf, a_f> + <galpha, alpha_f_p>."""
+    x, v, r, gFfl, gaf = map(_f64, (x, v, r, gFfl, gaf))
+    u, vf, wf, p, af = map(_f64, (u, vf, wf, p, af))
+    n = x.shape[0]
+    gx = np.zeros((n, 3))
+    gv = np.zeros((n, 3))
+    gc = C.c_double(0.0)
+    ga = None if galpha is None else _f64(galpha)
+    lib().or_g2p_adj(C.byref(grid_struct(grid)), C.byref(params_struct(params)), C.c_int64(n), _p(x), _p(v), _p(r),
+                     _p(u), _p(vf), _p(wf), _p(p), _p(af), _p(gFfl), _p(gaf), None if ga is None else _p(ga), _p(gx),
+                     _p(gv), C.byref(gc))
+    return gx, gv, gc.value
+
+
+def integrate_adj(grid, params, r, gx_new, gv_new, gfex=None):
+    """(gx, gv, gFc, gFfl, gaf) of <gx_new, x'> + <gv_new, v'> + <gfex, f_ex>."""
+    r, gx_new, gv_new = map(_f64, (r, gx_new, gv_new))
+    n = r.shape[0]
+    outs = [np.empty((n, 3)) for _ in range(5)]
+    gf = None if gfex is None else _f64(gfex)
+    lib().or_integrate_adj(C.byref(grid_struct(grid)), C.byref(params_struct(params)), C.c_int64(n), _p(r),
+                           _p(gx_new), _p(gv_new), None if gf is None else _p(gf), *[_p(o) for o in outs])
+    return tuple(outs)
+
+
+def p2g_adj(grid, params, x_old, x_new, r, f_ex, g_alpha=None, gFs=None):
+    """(gx_old, gx_new, gfex) of <g_alpha, alpha_s> + sum_c <gFs_c, F_s,c>."""
+    x_old, x_new, r, f_ex = map(_f64, (x_old, x_new, r, f_ex))
+    n = x_old.shape[0]
+    gxo = np.zeros((n, 3))
+    gxn = np.zeros((n, 3))
+    gfe = np.zeros((n, 3))
+    ga = None if g_alpha is None else _f64(g_alpha)
+    gf = [None, None, None] if gFs is None else [_f64(a) for a in gFs]
+    lib().or_p2g_adj(C.byref(grid_struct(grid)), C.byref(params_struct(params)), C.c_int64(n), _p(x_old), _p(x_new),
+                     _p(r), _p(f_ex), None if ga is None else _p(ga), *[None if a is None else _p(a) for a in gf],
+                     _p(gxo), _p(gxn), _p(gfe))
+    return gxo, gxn, gfe
+
+
+def run_adjoint(prob, gxK, gvK=None, K=None, params=None, x=None, v=None, brute=False, signature=False):
+    """K substeps forward then the reverse pass.
+
+    Returns dict(x, v (final), g_x0, g_v0, g_c (d/dc_drag), g_mu, sig, status)."""
+    grid = prob.grid
+    P = params if params is not None else prob.params
+    K = prob.K if K is None else K
+    x = decode(grid, prob.cell, prob.q) if x is None else _f64(x).copy()
+    v = _f64(prob.v).copy() if v is None else _f64(v).copy()
+    r = _f64(prob.r)
+    n = x.shape[0]
+    fl = [_f64(a) for a in (prob.u, prob.vf, prob.wf, prob.p, prob.alpha_f)]
+    gx0 = np.empty((n, 3))
+    gv0 = np.empty((n, 3))
+    gc = C.c_double(0.0)
+    gm = C.c_double(0.0)
+    sig = np.zeros(3, np.uint64)
+    st = C.c_uint32(0)
+    gxK = _f64(gxK)
+    gvK = None if gvK is None else _f64(gvK)
+    lib().or_run_adjoint(C.byref(grid_struct(grid)), C.byref(params_struct(P)), C.c_int64(n), C.c_int(K), _p(x),
+                         _p(v), _p(r), *[_p(a) for a in fl], _p(gxK), None if gvK is None else _p(gvK), _p(gx0),
+                         _p(gv0), C.byref(gc), C.byref(gm), _p(sig) if signature else None, C.c_int(int(brute)),
+                         C.byref(st))
+    return dict(x=x, v=v, g_x0=gx0, g_v0=gv0, g_c=gc.value, g_mu=gm.value, sig=tuple(int(s) for s in sig),
+                status=st.value)

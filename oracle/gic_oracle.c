@@ -639,3 +639,405 @@ void or_run(const or_grid* G, const or_params* P, int64_t n, int K, double* x, d
   for (int s = 0; s < K; ++s) substep(G, P, &Fd, n, x, v, r, alpha_s, Fs_u, Fs_v, Fs_w, sums, brute, scratch, status);
   free(scratch);
 }
+
+/* ======================================================================== */
+/* ADJOINT (hand-derived, explicit Jacobians)                               */
+/*                                                                          */
+/* The paper has no gradients; these are the exact derivatives of the       */
+/* forward functions above, written out as 3x3 Jacobians (not as a replay   */
+/* of the forward code), so the CUDA reverse-mode kernels are checked       */
+/* against an independent derivation.  Non-smooth points (contact onset,    */
+/* the Coulomb switch, clamped interpolation) take the one-sided branch the */
+/* forward takes.                                                           */
+/* ======================================================================== */
+
+typedef struct {
+  double m[3][3];
+} or_m3;
+
+static void m3_zero(or_m3* A) { memset(A, 0, sizeof(*A)); }
+/* y += A^T x */
+static void m3_tmul_add(const or_m3* A, const double x[3], double y[3]) {
+  for (int b = 0; b < 3; ++b)
+    for (int a = 0; a < 3; ++a) y[b] += A->m[a][b] * x[a];
+}
+
+/* Jacobians of the pair force F(x, v) of pair_force w.r.t. x = x_i - x_j and
+ * v = v_i - v_j, and dF/dmu.  Returns 0 if the pair is not in contact. */
+static int pair_force_jac(const or_params* P, const double x[3], const double v[3], double ri, double rj, double mi,
+                          double mj, or_m3* Jx, or_m3* Jv, double dmu[3], int* slip_out) {
+  double d2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+  double R = ri + rj;
+  if (!(d2 < R * R)) return 0;
+  double d = sqrt(d2);
+  if (d == 0.0) return 0;
+  double n[3] = {x[0] / d, x[1] / d, x[2] / d};
+  double meff = mj > 0.0 ? mi * mj / (mi + mj) : mi;
+  double cn = 2.0 * P->zeta * sqrt(P->k_n * meff);
+  double kt = P->kt_over_cn * cn;
+  double vn = v[0] * n[0] + v[1] * n[1] + v[2] * n[2];
+  double Fn = P->k_n * (R - d) - cn * vn;
+  double vt[3] = {v[0] - vn * n[0], v[1] - vn * n[1], v[2] - vn * n[2]};
+  double vtn = sqrt(vt[0] * vt[0] + vt[1] * vt[1] + vt[2] * vt[2]);
+  int slip = kt * vtn > P->mu * fabs(Fn);
+  /* projector Pn = I - n n^T */
+  double Pn[3][3], dndx[3][3];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      Pn[a][b] = (a == b ? 1.0 : 0.0) - n[a] * n[b];
+      dndx[a][b] = Pn[a][b] / d;
+    }
+  /* d vn / dx = v^T dn/dx,  d vn / dv = n^T */
+  double dvn_dx[3];
+  for (int b = 0; b < 3; ++b) dvn_dx[b] = v[0] * dndx[0][b] + v[1] * dndx[1][b] + v[2] * dndx[2][b];
+  /* d Fn / dx = -k_n n^T - cn dvn/dx,  d Fn / dv = -cn n^T */
+  double dFn_dx[3], dFn_dv[3];
+  for (int b = 0; b < 3; ++b) {
+    dFn_dx[b] = -P->k_n * n[b] - cn * dvn_dx[b];
+    dFn_dv[b] = -cn * n[b];
+  }
+  /* d vt / dx = -n dvn/dx - vn dn/dx,  d vt / dv = Pn */
+  double dvt_dx[3][3];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) dvt_dx[a][b] = -n[a] * dvn_dx[b] - vn * dndx[a][b];
+  m3_zero(Jx);
+  m3_zero(Jv);
+  /* normal part Fn n */
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      Jx->m[a][b] += n[a] * dFn_dx[b] + Fn * dndx[a][b];
+      Jv->m[a][b] += n[a] * dFn_dv[b];
+    }
+  dmu[0] = dmu[1] = dmu[2] = 0.0;
+  if (!slip) {
+    /* F_t = -kt vt */
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) {
+        Jx->m[a][b] += -kt * dvt_dx[a][b];
+        Jv->m[a][b] += -kt * Pn[a][b];
+      }
+  } else {
+    /* F_t = -mu |Fn| u, u = vt / |vt| */
+    double u[3] = {vt[0] / vtn, vt[1] / vtn, vt[2] / vtn};
+    double sg = Fn > 0 ? 1.0 : (Fn < 0 ? -1.0 : 0.0);
+    double A = P->mu * fabs(Fn);
+    double Q[3][3]; /* du/dvt = (I - u u^T) / |vt| */
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) Q[a][b] = ((a == b ? 1.0 : 0.0) - u[a] * u[b]) / vtn;
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) {
+        double qx = 0, qv = 0;
+        for (int c = 0; c < 3; ++c) {
+          qx += Q[a][c] * dvt_dx[c][b];
+          qv += Q[a][c] * Pn[c][b];
+        }
+        Jx->m[a][b] += -P->mu * sg * u[a] * dFn_dx[b] - A * qx;
+        Jv->m[a][b] += -P->mu * sg * u[a] * dFn_dv[b] - A * qv;
+      }
+    for (int a = 0; a < 3; ++a) dmu[a] = -fabs(Fn) * u[a];
+  }
+  if (slip_out) *slip_out = slip;
+  return 1;
+}
+
+/* contact adjoint: gx_i += sum_j Jx_ij^T (l_i - l_j), gv_i likewise,
+ * g_mu += sum_i l_i . dF_i/dmu.  Walls: partner gradient zero. */
+void or_contact_adj(const or_grid* G, const or_params* P, int64_t n, const double* x, const double* v,
+                    const double* r, const double* gF, int brute, double* gx, double* gv, double* g_mu) {
+  or_bins B;
+  if (!brute) bins_build(&B, G, n, x, r);
+  double gm = 0.0;
+  for (int64_t i = 0; i < n; ++i) {
+    double mi = P->rho_s * granule_volume(r[i]);
+    const double* li = gF + 3 * i;
+    /* candidate partners: every j (brute) or the 27 bins around i */
+    int64_t* cand = NULL;
+    int64_t nc = 0;
+    if (brute) {
+      cand = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+      for (int64_t j = 0; j < n; ++j) cand[nc++] = j;
+    } else {
+      int bi[3];
+      bin_of(&B, G, x + 3 * i, bi);
+      int64_t cap = 64;
+      cand = (int64_t*)malloc(sizeof(int64_t) * (size_t)cap);
+      for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+          for (int dx = -1; dx <= 1; ++dx) {
+            int b[3] = {bi[0] + dx, bi[1] + dy, bi[2] + dz};
+            if (b[0] < 0 || b[1] < 0 || b[2] < 0 || b[0] >= B.nb[0] || b[1] >= B.nb[1] || b[2] >= B.nb[2]) continue;
+            int64_t lin = b[0] + (int64_t)B.nb[0] * (b[1] + (int64_t)B.nb[1] * b[2]);
+            for (int64_t j = B.head[lin]; j >= 0; j = B.next[j]) {
+              if (nc == cap) {
+                cap *= 2;
+                cand = (int64_t*)realloc(cand, sizeof(int64_t) * (size_t)cap);
+              }
+              cand[nc++] = j;
+            }
+          }
+    }
+    for (int64_t c = 0; c < nc; ++c) {
+      int64_t j = cand[c];
+      if (j == i) continue;
+      double xij[3], vij[3], lam[3], dmu[3];
+      for (int a = 0; a < 3; ++a) {
+        xij[a] = x[3 * i + a] - x[3 * j + a];
+        vij[a] = v[3 * i + a] - v[3 * j + a];
+        lam[a] = li[a] - gF[3 * j + a];
+      }
+      or_m3 Jx, Jv;
+      if (!pair_force_jac(P, xij, vij, r[i], r[j], mi, P->rho_s * granule_volume(r[j]), &Jx, &Jv, dmu, NULL)) continue;
+      m3_tmul_add(&Jx, lam, gx + 3 * i);
+      m3_tmul_add(&Jv, lam, gv + 3 * i);
+      gm += li[0] * dmu[0] + li[1] * dmu[1] + li[2] * dmu[2];
+    }
+    free(cand);
+    if (P->walls) {
+      double lo[3] = {G->ox, G->oy, G->oz};
+      int nn[3] = {G->nx, G->ny, G->nz};
+      for (int a = 0; a < 3; ++a) {
+        double hi = lo[a] + nn[a] * G->dx;
+        for (int side = 0; side < 2; ++side) {
+          double gap = side == 0 ? x[3 * i + a] - lo[a] : hi - x[3 * i + a];
+          if (gap >= r[i] || gap <= 0.0) continue;
+          double xw[3] = {0, 0, 0}, dmu[3];
+          xw[a] = side == 0 ? gap : -gap;
+          or_m3 Jx, Jv;
+          if (!pair_force_jac(P, xw, v + 3 * i, r[i], 0.0, mi, 0.0, &Jx, &Jv, dmu, NULL)) continue;
+          /* x_w = +-(x_i - wall): d x_w / d x_i = I on this axis only, 0 on the others */
+          double tmp[3] = {0, 0, 0};
+          m3_tmul_add(&Jx, li, tmp);
+          gx[3 * i + a] += tmp[a];
+          m3_tmul_add(&Jv, li, gv + 3 * i);
+          gm += li[0] * dmu[0] + li[1] * dmu[1] + li[2] * dmu[2];
+        }
+      }
+    }
+  }
+  *g_mu += gm;
+  if (!brute) bins_free(&B);
+}
+
+/* value and x-gradient of the interpolation of a sampled field */
+static double interp_grad_layout(const or_grid* G, const or_layout* L, const double* f, int gp_comp, const double* p,
+                                 const double* x, double grad[3]) {
+  double o[3] = {G->ox, G->oy, G->oz};
+  or_stencil S;
+  int clamped[3];
+  for (int a = 0; a < 3; ++a) {
+    double xg = (x[a] - o[a]) / G->dx;
+    double fpos = xg - L->s[a];
+    clamped[a] = !(fpos > 0.0) || fpos >= (double)(L->ns[a] - 1);
+    axis_stencil(xg, L->s[a], L->ns[a], &S.i0[a], &S.t[a]);
+  }
+  double val = 0.0, g[3] = {0, 0, 0};
+  for (int c = 0; c < 2; ++c)
+    for (int b = 0; b < 2; ++b)
+      for (int a = 0; a < 2; ++a) {
+        double fv = gp_comp >= 0 ? grad_p_face(G, p, gp_comp, S.i0[0] + a, S.i0[1] + b, S.i0[2] + c)
+                                 : f[sidx(L, S.i0[0] + a, S.i0[1] + b, S.i0[2] + c)];
+        double wx = a ? S.t[0] : 1.0 - S.t[0];
+        double wy = b ? S.t[1] : 1.0 - S.t[1];
+        double wz = c ? S.t[2] : 1.0 - S.t[2];
+        val += wx * wy * wz * fv;
+        g[0] += (a ? 1.0 : -1.0) * wy * wz * fv;
+        g[1] += wx * (b ? 1.0 : -1.0) * wz * fv;
+        g[2] += wx * wy * (c ? 1.0 : -1.0) * fv;
+      }
+  for (int a = 0; a < 3; ++a) grad[a] = clamped[a] ? 0.0 : g[a] / G->dx;
+  return val;
+}
+
+/* G2P adjoint.  gx, gv accumulated; g_cdrag accumulated. galpha may be NULL. */
+void or_g2p_adj(const or_grid* G, const or_params* P, int64_t n, const double* x, const double* v, const double* r,
+                const double* u, const double* vf, const double* wf, const double* p, const double* af,
+                const double* gFfl, const double* gaf, const double* galpha, double* gx, double* gv,
+                double* g_cdrag) {
+  const double* uvw[3] = {u, vf, wf};
+  double gc = 0.0;
+  for (int64_t i = 0; i < n; ++i) {
+    const double* xi = x + 3 * i;
+    double uf[3], Du[3][3], H[3][3];
+    for (int comp = 0; comp < 3; ++comp) {
+      or_layout L = layout_of(G, comp);
+      uf[comp] = interp_grad_layout(G, &L, uvw[comp], -1, NULL, xi, Du[comp]);
+      interp_grad_layout(G, &L, NULL, comp, p, xi, H[comp]);
+    }
+    double V = granule_volume(r[i]);
+    double k = P->c_drag * OR_PI * r[i] * r[i] * P->rho_f;
+    double dv[3] = {uf[0] - v[3 * i], uf[1] - v[3 * i + 1], uf[2] - v[3 * i + 2]};
+    double sp = sqrt(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
+    double D[3][3]; /* d F_d / d dv = k (|dv| I + dv dv^T / |dv|) */
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) D[a][b] = sp > 0 ? k * ((a == b ? sp : 0.0) + dv[a] * dv[b] / sp) : 0.0;
+    const double* lF = gFfl + 3 * i;
+    const double* la = gaf + 3 * i;
+    /* dF_fl/dx = D Du - V H ; da_f/dx = -H / rho_f ; dF_fl/dv = -D */
+    for (int b = 0; b < 3; ++b) {
+      double s = 0.0, t = 0.0;
+      for (int a = 0; a < 3; ++a) {
+        double DDu = 0.0;
+        for (int c = 0; c < 3; ++c) DDu += D[a][c] * Du[c][b];
+        s += lF[a] * (DDu - V * H[a][b]);
+        if (P->rho_f > 0) s += la[a] * (-H[a][b] / P->rho_f);
+        t += lF[a] * (-D[a][b]);
+      }
+      gx[3 * i + b] += s;
+      gv[3 * i + b] += t;
+    }
+    if (galpha) {
+      or_layout Lc = layout_of(G, 3);
+      double ga[3];
+      interp_grad_layout(G, &Lc, af, -1, NULL, xi, ga);
+      for (int b = 0; b < 3; ++b) gx[3 * i + b] += galpha[i] * ga[b];
+    }
+    /* dF_d / dc_drag = pi r^2 rho_f |dv| dv */
+    double q = OR_PI * r[i] * r[i] * P->rho_f * sp;
+    gc += q * (dv[0] * lF[0] + dv[1] * lF[1] + dv[2] * lF[2]);
+  }
+  *g_cdrag += gc;
+}
+
+/* integrate adjoint: writes gx, gv, gFc, gFfl, gaf from gx_new, gv_new, gfex (may be NULL) */
+void or_integrate_adj(const or_grid* G, const or_params* P, int64_t n, const double* r, const double* gx_new,
+                      const double* gv_new, const double* gfex, double* gx, double* gv, double* gFc, double* gFfl,
+                      double* gaf) {
+  (void)G;
+  double dt = P->dt;
+  for (int64_t i = 0; i < n; ++i) {
+    double V = granule_volume(r[i]);
+    double m = P->rho_s * V;
+    double ma = P->virtual_mass ? 0.5 * P->rho_f * V : 0.0;
+    double M = m + ma;
+    for (int a = 0; a < 3; ++a) {
+      double gX = gx_new[3 * i + a], gV = gv_new[3 * i + a], gf = gfex ? gfex[3 * i + a] : 0.0;
+      /* x' = x + dt v + dt^2 a, v' = v + dt a, f = F_fl + ma (a_f - a) */
+      double through_a = dt * dt / M * gX + dt / M * gV; /* d(x', v')/dF . g for F in {F_c, F_fl} */
+      gx[3 * i + a] = gX;
+      gv[3 * i + a] = dt * gX + gV;
+      gFc[3 * i + a] = through_a - ma / M * gf;
+      gFfl[3 * i + a] = through_a + (1.0 - ma / M) * gf;
+      gaf[3 * i + a] = ma * through_a + ma * m / M * gf;
+    }
+  }
+}
+
+/* P2G adjoint: gx_old, gx_new accumulated; gfex written.  g_alpha and gFs
+ * (all three) may be NULL. */
+void or_p2g_adj(const or_grid* G, const or_params* P, int64_t n, const double* x_old, const double* x_new,
+                const double* r, const double* f_ex, const double* g_alpha, const double* gFs_u, const double* gFs_v,
+                const double* gFs_w, double* gx_old, double* gx_new, double* gfex) {
+  const double* gF[3] = {gFs_u, gFs_v, gFs_w};
+  double dx3 = G->dx * G->dx * G->dx;
+  double scale = -P->dt / P->dt_fluid;
+  for (int64_t i = 0; i < n; ++i) {
+    if (g_alpha) {
+      or_layout Lc = layout_of(G, 3);
+      double g[3];
+      interp_grad_layout(G, &Lc, g_alpha, -1, NULL, x_new + 3 * i, g);
+      double s = granule_volume(r[i]) / dx3;
+      for (int a = 0; a < 3; ++a) gx_new[3 * i + a] += s * g[a];
+    }
+    for (int comp = 0; comp < 3; ++comp) {
+      if (!gF[comp]) {
+        gfex[3 * i + comp] = 0.0;
+        continue;
+      }
+      or_layout L = layout_of(G, comp);
+      double g[3];
+      double val = interp_grad_layout(G, &L, gF[comp], -1, NULL, x_old + 3 * i, g);
+      gfex[3 * i + comp] = scale * val;
+      for (int a = 0; a < 3; ++a) gx_old[3 * i + a] += scale * f_ex[3 * i + comp] * g[a];
+    }
+  }
+}
+
+/* Contact signature of one state: number of contacts, number slipping and
+ * an order-free hash of (i, j, slip) -- used to tell whether a finite-
+ * difference pair of runs saw the same contact set. */
+static void contact_signature(const or_grid* G, const or_params* P, int64_t n, const double* x, const double* v,
+                              const double* r, uint64_t sig[3]) {
+  int64_t m = 0, ms = 0;
+  uint64_t h = 0;
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t j = i + 1; j < n; ++j) {
+      double xij[3], vij[3], dmu[3];
+      for (int a = 0; a < 3; ++a) {
+        xij[a] = x[3 * i + a] - x[3 * j + a];
+        vij[a] = v[3 * i + a] - v[3 * j + a];
+      }
+      or_m3 Jx, Jv;
+      int slip = 0;
+      if (!pair_force_jac(P, xij, vij, r[i], r[j], P->rho_s * granule_volume(r[i]),
+                          P->rho_s * granule_volume(r[j]), &Jx, &Jv, dmu, &slip))
+        continue;
+      ++m;
+      ms += slip;
+      uint64_t k = (uint64_t)i * 0x9E3779B97F4A7C15ull ^ ((uint64_t)j + 0x632BE59BD9B4E019ull) * 0xBF58476D1CE4E5B9ull;
+      k ^= (uint64_t)slip * 0x94D049BB133111EBull;
+      h += k * 0xD6E8FEB86659FD93ull;
+    }
+  (void)G;
+  sig[0] += (uint64_t)m;
+  sig[1] += (uint64_t)ms;
+  sig[2] = sig[2] * 31u + h;
+}
+
+/* K substeps forward (storing every state) and the reverse pass.
+ *   gxK, gvK: dL/dx_K, dL/dv_K (3n each, v may be NULL)
+ *   out: g_x0, g_v0 (3n), g_c = dL/dc_drag, g_mu = dL/dmu.
+ *   sig (3 uint64, may be NULL): contact signature summed over the window
+ *   (O(N^2) per substep: small problems only).
+ * x, v are left at the final state. */
+void or_run_adjoint(const or_grid* G, const or_params* P, int64_t n, int K, double* x, double* v, const double* r,
+                    const double* u, const double* vf, const double* wf, const double* p, const double* af,
+                    const double* gxK, const double* gvK, double* g_x0, double* g_v0, double* g_c, double* g_mu,
+                    uint64_t* sig, int brute, uint32_t* status) {
+  size_t n3 = 3 * (size_t)(n > 0 ? n : 1);
+  double* xs = (double*)malloc(sizeof(double) * n3 * (size_t)(K + 1));
+  double* vs = (double*)malloc(sizeof(double) * n3 * (size_t)(K + 1));
+  double* Fc = (double*)malloc(sizeof(double) * n3);
+  double* Ffl = (double*)malloc(sizeof(double) * n3);
+  double* a_f = (double*)malloc(sizeof(double) * n3);
+  double* fex = (double*)malloc(sizeof(double) * n3);
+  double* afp = (double*)malloc(sizeof(double) * (n3 / 3));
+  memcpy(xs, x, sizeof(double) * 3 * n);
+  memcpy(vs, v, sizeof(double) * 3 * n);
+  if (sig) sig[0] = sig[1] = sig[2] = 0;
+  for (int s = 0; s < K; ++s) {
+    double* xc = xs + n3 * s;
+    double* vc = vs + n3 * s;
+    if (sig) contact_signature(G, P, n, xc, vc, r, sig);
+    or_g2p(G, P, n, xc, vc, r, u, vf, wf, p, af, Ffl, a_f, afp);
+    or_contact(G, P, n, xc, vc, r, brute, Fc, status);
+    or_integrate(G, P, n, xc, vc, r, Fc, Ffl, a_f, xs + n3 * (s + 1), vs + n3 * (s + 1), fex, status);
+  }
+  memcpy(x, xs + n3 * K, sizeof(double) * 3 * n);
+  memcpy(v, vs + n3 * K, sizeof(double) * 3 * n);
+  double* gX = (double*)malloc(sizeof(double) * n3);
+  double* gV = (double*)malloc(sizeof(double) * n3);
+  double* gXp = (double*)malloc(sizeof(double) * n3);
+  double* gVp = (double*)malloc(sizeof(double) * n3);
+  double* gFc = (double*)malloc(sizeof(double) * n3);
+  double* gFfl = (double*)malloc(sizeof(double) * n3);
+  double* gaf = (double*)malloc(sizeof(double) * n3);
+  for (size_t k = 0; k < 3 * (size_t)n; ++k) {
+    gXp[k] = gxK ? gxK[k] : 0.0;
+    gVp[k] = gvK ? gvK[k] : 0.0;
+  }
+  *g_c = 0.0;
+  *g_mu = 0.0;
+  for (int s = K - 1; s >= 0; --s) {
+    double* xc = xs + n3 * s;
+    double* vc = vs + n3 * s;
+    or_integrate_adj(G, P, n, r, gXp, gVp, NULL, gX, gV, gFc, gFfl, gaf);
+    or_g2p_adj(G, P, n, xc, vc, r, u, vf, wf, p, af, gFfl, gaf, NULL, gX, gV, g_c);
+    or_contact_adj(G, P, n, xc, vc, r, gFc, brute, gX, gV, g_mu);
+    memcpy(gXp, gX, sizeof(double) * 3 * n);
+    memcpy(gVp, gV, sizeof(double) * 3 * n);
+  }
+  memcpy(g_x0, gXp, sizeof(double) * 3 * n);
+  memcpy(g_v0, gVp, sizeof(double) * 3 * n);
+  free(xs); free(vs); free(Fc); free(Ffl); free(a_f); free(fex); free(afp);
+  free(gX); free(gV); free(gXp); free(gVp); free(gFc); free(gFfl); free(gaf);
+}

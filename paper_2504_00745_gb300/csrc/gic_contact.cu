@@ -252,8 +252,13 @@ __global__ void __launch_bounds__(128) k_contact_adj(DGrid G, DParams<T> P, int6
           if (!(gap < ri)) continue;
           T x[3] = {0, 0, 0};
           x[a] = side == 0 ? gap : -gap;
+          // the wall vector depends on x_i only through its axis-a component
+          T w[3] = {0, 0, 0};
           gm += pair_force_adj(P, x[0], x[1], x[2], gap * gap, vi.x, vi.y, vi.z, ri, mi, li.x, li.y, li.z, li.x, li.y,
-                               li.z, gx0, gx1, gx2, gv0, gv1, gv2);
+                               li.z, w[0], w[1], w[2], gv0, gv1, gv2);
+          if (a == 0) gx0 += w[0];
+          else if (a == 1) gx1 += w[1];
+          else gx2 += w[2];
         }
       }
     }

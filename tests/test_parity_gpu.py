@@ -159,9 +159,14 @@ def test_g2p_parity(name, prec):
     Ffl = sim.F_fl.cpu().numpy()[:, :3]
     af = sim.a_f.cpu().numpy()[:, :3]
     alp = sim.alpha_f_p.cpu().numpy()
-    assert np.abs(Ffl - Ffl_o).max() <= rtol * np.abs(Ffl_o).max()
-    assert np.abs(af - af_o).max() <= rtol * np.abs(af_o).max()
-    assert np.abs(alp - alp_o).max() <= rtol
+    e = np.abs(Ffl - Ffl_o)
+    k = np.unravel_index(np.argmax(e), e.shape)
+    assert e.max() <= rtol * np.abs(Ffl_o).max(), (e.max(), np.abs(Ffl_o).max(), k, Ffl[k[0]], Ffl_o[k[0]],
+                                                    x[k[0]], v[k[0]])
+    # a_f = g - grad p / rho_f cancels to ~0 in hydrostatic fluid: the scale is |g|
+    ascale = max(np.abs(af_o).max(), np.linalg.norm(prob.params.g))
+    assert np.abs(af - af_o).max() <= rtol * ascale, (np.abs(af - af_o).max(), ascale)
+    assert np.abs(alp - alp_o).max() <= rtol, np.abs(alp - alp_o).max()
 
 
 # ----------------------------------------------------------------------------- a4 integrate
@@ -219,14 +224,15 @@ def test_p2g_parity(name, prec):
     xb, _ = sim.positions(sim.B)
     a_o, Fs_o, sums_o = oracle.p2g(prob.grid, prob.params, xa.cpu().numpy(), xb.cpu().numpy(), r, fex)
     ag = sim.alpha_s.cpu().numpy()
-    assert np.abs(ag - a_o).max() <= 1e-9
+    assert np.abs(ag - a_o).max() <= 1e-9, np.abs(ag - a_o).max()
     sums = sim.sums.cpu().numpy()
-    assert abs(sums[1] - sums_o[1]) <= 1e-13 * sums_o[1]
+    assert abs(sums[1] - sums_o[1]) <= 1e-12 * sums_o[1]  # n-term FP64 sums in different orders
     assert abs(sums[0] - sums[1]) <= 1e-12 * sums[1]
     ftol = 2e-6 if prec == FP32 else 1e-12
     for c in range(3):
         fg = sim.Fs[c].cpu().numpy()
-        assert np.abs(fg - Fs_o[c]).max() <= ftol * np.abs(Fs_o[c]).max()
+        assert np.abs(fg - Fs_o[c]).max() <= ftol * np.abs(Fs_o[c]).max(), (c, np.abs(fg - Fs_o[c]).max(),
+                                                                            np.abs(Fs_o[c]).max())
 
 
 # ----------------------------------------------------------------------------- windows
@@ -248,17 +254,18 @@ def test_window_10_substeps(name, prec):
     vref = np.linalg.norm(ref["v"], axis=1).max()
     ev = np.linalg.norm(v.cpu().numpy() - ref["v"], axis=1).max()
     ea = np.abs(sim.alpha_s.cpu().numpy() - ref["alpha_s"]).max()
+    print(f"window {name} prec={prec}: |dx|={ex:.3e} ({ex / dx:.2e} dx) |dv|={ev:.3e} (vref {vref:.3e}) |dalpha|={ea:.3e}")
     if prec == FP32:
         assert ex <= 1e-5 * dx, ex
         assert ev <= 1e-4 * vref, (ev, vref)
         assert ea <= 1e-9, ea
     else:
-        assert ex <= 1e-12 * dx
-        assert ev <= 1e-10 * vref
-        assert ea <= 1e-12
+        assert ex <= 1e-12 * dx, ex
+        assert ev <= 1e-10 * vref, (ev, vref)
+        assert ea <= 1e-12, ea
     sums = sim.sums.cpu().numpy()
     assert abs(sums[0] - sums[1]) <= 1e-12 * sums[1]
-    assert abs(sums[1] - ref["sums"][1]) <= 1e-13 * sums[1]
+    assert abs(sums[1] - ref["sums"][1]) <= 1e-12 * sums[1]
     for c in range(3):
         fo = ref["Fs"][c]
         fg = sim.Fs[c].cpu().numpy()
@@ -297,6 +304,7 @@ def test_out_of_domain_is_flagged_not_faulted(prec):
     prob = subset(gi.make("dense_block"), 64)
     prob.v = prob.v.copy()
     prob.v[3] = [-1e4, 0, 0]  # crosses the x = 0 wall in one substep
+    prob.params.c_drag = 0.0  # (quadratic drag at 1e4 m/s would reverse the granule within the substep)
     sim = sim_for(prob, prec)
     sim.run(1)
     torch.cuda.synchronize()
