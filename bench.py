@@ -41,6 +41,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true", help="skip the FP64 and adjoint variants")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--profile-substeps", type=int, default=0,
+                    help="run this many substeps of the workload once, untimed, and exit (for ncu captures)")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"], help="precision of --profile-substeps")
     return ap.parse_args()
 
 
@@ -376,8 +379,29 @@ def run_fp64(prob, gic, torch, dev, stream, steps=1):
     return {"value": prob.n * K / (ms / 1000), "unit": UNIT, "ms_per_step": ms, "dtype": "f64", "steps": steps}
 
 
+def run_profile(args):
+    """N substeps of the workload, nothing else (the command ncu wraps)."""
+    import torch
+
+    import gic_inputs as gi
+    from paper_2504_00745_gb300 import gic
+    from paper_2504_00745_gb300.window import Simulator
+
+    prob = gi.make(args.workload)
+    prec = gic.GIC_FP32 if args.precision == "fp32" else gic.GIC_FP64
+    sim = Simulator.from_problem(prob, prec)
+    sim.run(args.profile_substeps)
+    torch.cuda.synchronize()
+    st = gic.gic_check_status()
+    print(json.dumps({"profile_substeps": args.profile_substeps, "workload": prob.name, "precision": args.precision,
+                      "device_status": st, "launches": gic.launch_count()}))
+
+
 def main():
     args = parse()
+    if args.profile_substeps > 0:
+        run_profile(args)
+        return
     ws, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, ws, rank)

@@ -88,6 +88,9 @@ int make_grid(const GicGrid* g, DGrid* G) {
   G->unit_f = (float)G->unit;
   G->inv_unit_f = (float)G->inv_unit;
   G->inv_k_f = (float)(1.0 / g->k_contact);
+  G->s_hi = (float)G->inv_unit;
+  G->s_lo = (float)(G->inv_unit - (double)G->s_hi);
+  G->s2_margin = (float)((double)G->s_hi * (double)G->s_hi * (1.0 + 4e-6));
   return GIC_OK;
 }
 

@@ -20,16 +20,14 @@ __device__ __forceinline__ T granule_mass(const DParams<T>& P, T r) {
   return P.rho_s * (T(4.0 / 3.0 * kPi) * r * r * r);
 }
 
-// Pair force on i (x = x_i - x_j, v = v_i - v_j), already known to overlap
-// (d2 < R^2).  Returns false for coincident centres.
+// Pair force on i (x = x_i - x_j, v = v_i - v_j) at distance d with
+// overlap = r_i + r_j - d > 0.  Returns false for coincident centres.
 template <typename T>
-__device__ __forceinline__ bool pair_force(const DParams<T>& P, T x0, T x1, T x2, T d2, T v0, T v1, T v2, T R, T meff,
-                                           T& F0, T& F1, T& F2) {
-  T d = sqrt(d2);
+__device__ __forceinline__ bool pair_force(const DParams<T>& P, T x0, T x1, T x2, T d, T overlap, T v0, T v1, T v2,
+                                           T meff, T& F0, T& F1, T& F2) {
   if (d == T(0)) return false;
   T inv_d = T(1) / d;
   T n0 = x0 * inv_d, n1 = x1 * inv_d, n2 = x2 * inv_d;
-  T overlap = R - d;
   T cn = T(2) * P.zeta * sqrt(P.k_n * meff);
   T vn = v0 * n0 + v1 * n1 + v2 * n2;
   T Fn = P.k_n * overlap - cn * vn;
@@ -49,14 +47,12 @@ __device__ __forceinline__ bool pair_force(const DParams<T>& P, T x0, T x1, T x2
 // adds d<l, F>/dx to gx and d<l, F>/dv to gv; returns d<lm, F>/dmu for the
 // second upstream lm (the granule's own gradient).
 template <typename T>
-__device__ __forceinline__ T pair_force_adj(const DParams<T>& P, T x0, T x1, T x2, T d2, T v0, T v1, T v2, T R,
+__device__ __forceinline__ T pair_force_adj(const DParams<T>& P, T x0, T x1, T x2, T d, T overlap, T v0, T v1, T v2,
                                             T meff, T l0, T l1, T l2, T lm0, T lm1, T lm2, T& gx0, T& gx1, T& gx2,
                                             T& gv0, T& gv1, T& gv2) {
-  T d = sqrt(d2);
   if (d == T(0)) return T(0);
   T inv_d = T(1) / d;
   T n0 = x0 * inv_d, n1 = x1 * inv_d, n2 = x2 * inv_d;
-  T overlap = R - d;
   T cn = T(2) * P.zeta * sqrt(P.k_n * meff);
   T vn = v0 * n0 + v1 * n1 + v2 * n2;
   T Fn = P.k_n * overlap - cn * vn;
@@ -116,6 +112,101 @@ __device__ __forceinline__ T pair_force_adj(const DParams<T>& P, T x0, T x1, T x
   return gmu;
 }
 
+// Contact geometry of a candidate pair: x_ij (metres), distance d and overlap
+// r_i + r_j - d.  Returns false if the pair does not overlap.
+template <typename T>
+struct PairGeom {
+  T x0, x1, x2, d, overlap;
+};
+
+// FP32 path.  The separation is an exact integer vector D in 2^-30 h_c units.
+// A float pre-test with a 4e-6 margin rejects most candidates; survivors get
+// the overlap to ~1e-7 of itself (not of d): R = (r_i + r_j) 2^30 / h_c as a
+// float pair (TwoSum / TwoProd), |D|^2 exact in 64-bit integers, d = sqrt with
+// one exact-residual correction, and R - d taken hi-to-hi (exact) plus the
+// low parts.  Plain FP32 would lose the overlap to cancellation (d ~ 100x
+// overlap in dense packings).
+__device__ __forceinline__ bool pair_geom(const DGrid& G, const uint4& pi, const uint4& pj, int ox, int oy, int oz,
+                                          float ri, float rj, PairGeom<float>& g) {
+  int Dx = (int)pi.x - (int)pj.x - ox * (int)kFracOne;
+  int Dy = (int)pi.y - (int)pj.y - oy * (int)kFracOne;
+  int Dz = (int)pi.z - (int)pj.z - oz * (int)kFracOne;
+  float fx = (float)Dx, fy = (float)Dy, fz = (float)Dz;
+  float d2f = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
+  float Rs = ri + rj;
+  if (!(d2f < Rs * Rs * G.s2_margin)) return false;
+  // R (2^-30 h_c units) as hi + lo
+  float Rh = ri + rj;
+  float bb = Rh - ri;
+  float Rl = (ri - (Rh - bb)) + (rj - bb);  // TwoSum error
+  float Ph = Rh * G.s_hi;
+  float Pl = fmaf(Rh, G.s_hi, -Ph) + fmaf(Rh, G.s_lo, Rl * G.s_hi);
+  // exact |D|^2 and a corrected square root
+  unsigned long long d2 = (unsigned long long)((long long)Dx * Dx) + (unsigned long long)((long long)Dy * Dy) +
+                          (unsigned long long)((long long)Dz * Dz);
+  float dh = sqrtf(__ull2float_rn(d2));
+  float ov;
+  if (dh >= 8388608.0f) {  // dh is an integer: the residual d2 - dh^2 is exact
+    unsigned long long di = (unsigned long long)dh;
+    long long res = (long long)(d2 - di * di);
+    float c = (float)res / (2.0f * dh);
+    ov = (Ph - dh) + (Pl - c);
+    dh += c;
+  } else {  // deep overlap (d < h_c / 128): relative precision is ample
+    ov = (Ph - dh) + Pl;
+  }
+  if (!(ov > 0.0f)) return false;
+  g.x0 = fx * G.unit_f;
+  g.x1 = fy * G.unit_f;
+  g.x2 = fz * G.unit_f;
+  g.d = dh * G.unit_f;
+  g.overlap = ov * G.unit_f;
+  return true;
+}
+
+__device__ __forceinline__ bool pair_geom(const DGrid& G, const d4& pi, const d4& pj, int ox, int oy, int oz,
+                                          double ri, double rj, PairGeom<double>& g) {
+  double x0, x1, x2;
+  rel_ij(G, pi, pj, ox, oy, oz, x0, x1, x2);
+  double d2 = x0 * x0 + x1 * x1 + x2 * x2;
+  double R = ri + rj;
+  if (!(d2 < R * R)) return false;
+  g.x0 = x0;
+  g.x1 = x1;
+  g.x2 = x2;
+  g.d = sqrt(d2);
+  g.overlap = R - g.d;
+  return true;
+}
+
+// Wall geometry: the granule's gap to the lower (side 0) or upper wall of
+// axis a when it sits in the first / last contact cell.  FP32: the gap is the
+// exact integer q (or 2^30 - q) and the overlap r 2^30/h_c - gap is formed
+// from the float pair of r 2^30 / h_c.
+__device__ __forceinline__ bool wall_geom(const DGrid& G, const uint4& p, int a, int side, float r, float& gap,
+                                          float& overlap) {
+  uint32_t q = pcomp(p, a);
+  long long gq = side == 0 ? (long long)q : (long long)kFracOne - (long long)q;
+  float Ph = r * G.s_hi;
+  float Pl = fmaf(r, G.s_hi, -Ph) + r * G.s_lo;
+  float ov;
+  if (Ph >= 16777216.0f)
+    ov = (float)((long long)Ph - gq) + Pl;  // Ph is an integer here
+  else
+    ov = (Ph - (float)gq) + Pl;
+  if (!(ov > 0.0f)) return false;
+  gap = (float)gq * G.unit_f;
+  overlap = ov * G.unit_f;
+  return true;
+}
+__device__ __forceinline__ bool wall_geom(const DGrid& G, const d4& p, int a, int side, double r, double& gap,
+                                          double& overlap) {
+  gap = side == 0 ? gap_lo(G, p, a) : gap_hi(G, p, a);
+  if (!(gap < r)) return false;
+  overlap = r - gap;
+  return true;
+}
+
 template <typename T>
 __device__ __forceinline__ void load_cell_coords(int32_t c, int& x, int& y, int& z) {
   x = cell_x(c);
@@ -167,16 +258,14 @@ __global__ void __launch_bounds__(128) k_contact(DGrid G, DParams<T> P, int64_t 
   bool coincident = false;
   for_each_partner(G, table, epoch, i, cx, cy, cz, [&](int64_t j, int ox, int oy, int oz) {
     pos_t<T> pj = ldg(&pos[j]);
-    T x0, x1, x2;
-    rel_ij(G, pi, pj, ox, oy, oz, x0, x1, x2);
     T rj = radius_of(pj);
-    T R = ri + rj;
-    T d2 = x0 * x0 + x1 * x1 + x2 * x2;
-    if (!(d2 < R * R)) return;
+    PairGeom<T> g;
+    if (!pair_geom(G, pi, pj, ox, oy, oz, ri, rj, g)) return;
     vec_t<T> vj = ldg(&vel[j]);
     T mj = granule_mass(P, rj);
     T f0, f1, f2;
-    if (pair_force(P, x0, x1, x2, d2, vi.x - vj.x, vi.y - vj.y, vi.z - vj.z, R, mi * mj / (mi + mj), f0, f1, f2)) {
+    if (pair_force(P, g.x0, g.x1, g.x2, g.d, g.overlap, vi.x - vj.x, vi.y - vj.y, vi.z - vj.z, mi * mj / (mi + mj), f0,
+                   f1, f2)) {
       F0 += f0;
       F1 += f1;
       F2 += f2;
@@ -189,12 +278,12 @@ __global__ void __launch_bounds__(128) k_contact(DGrid G, DParams<T> P, int64_t 
     for (int a = 0; a < 3; ++a) {
       for (int side = 0; side < 2; ++side) {
         if (side == 0 ? c3[a] != 0 : c3[a] != G.nc[a] - 1) continue;
-        T gap = side == 0 ? gap_lo(G, pi, a) : gap_hi(G, pi, a);
-        if (!(gap < ri)) continue;
+        T gap, ov;
+        if (!wall_geom(G, pi, a, side, ri, gap, ov)) continue;
         T x[3] = {0, 0, 0};
         x[a] = side == 0 ? gap : -gap;
         T f0, f1, f2;
-        if (pair_force(P, x[0], x[1], x[2], gap * gap, vi.x, vi.y, vi.z, ri, mi, f0, f1, f2)) {
+        if (pair_force(P, x[0], x[1], x[2], gap, ov, vi.x, vi.y, vi.z, mi, f0, f1, f2)) {
           F0 += f0;
           F1 += f1;
           F2 += f2;
@@ -231,31 +320,29 @@ __global__ void __launch_bounds__(128) k_contact_adj(DGrid G, DParams<T> P, int6
     T gx0 = 0, gx1 = 0, gx2 = 0, gv0 = 0, gv1 = 0, gv2 = 0, gm = 0;
     for_each_partner(G, table, epoch, i, cx, cy, cz, [&](int64_t j, int ox, int oy, int oz) {
       pos_t<T> pj = ldg(&pos[j]);
-      T x0, x1, x2;
-      rel_ij(G, pi, pj, ox, oy, oz, x0, x1, x2);
       T rj = radius_of(pj);
-      T R = ri + rj;
-      T d2 = x0 * x0 + x1 * x1 + x2 * x2;
-      if (!(d2 < R * R)) return;
+      PairGeom<T> g;
+      if (!pair_geom(G, pi, pj, ox, oy, oz, ri, rj, g)) return;
       vec_t<T> vj = ldg(&vel[j]);
       vec_t<T> lj = ldg(&gF[j]);
       T mj = granule_mass(P, rj);
-      gm += pair_force_adj(P, x0, x1, x2, d2, vi.x - vj.x, vi.y - vj.y, vi.z - vj.z, R, mi * mj / (mi + mj),
-                           li.x - lj.x, li.y - lj.y, li.z - lj.z, li.x, li.y, li.z, gx0, gx1, gx2, gv0, gv1, gv2);
+      gm += pair_force_adj(P, g.x0, g.x1, g.x2, g.d, g.overlap, vi.x - vj.x, vi.y - vj.y, vi.z - vj.z,
+                           mi * mj / (mi + mj), li.x - lj.x, li.y - lj.y, li.z - lj.z, li.x, li.y, li.z, gx0, gx1, gx2,
+                           gv0, gv1, gv2);
     });
     if (P.walls) {
       const int c3[3] = {cx, cy, cz};
       for (int a = 0; a < 3; ++a) {
         for (int side = 0; side < 2; ++side) {
           if (side == 0 ? c3[a] != 0 : c3[a] != G.nc[a] - 1) continue;
-          T gap = side == 0 ? gap_lo(G, pi, a) : gap_hi(G, pi, a);
-          if (!(gap < ri)) continue;
+          T gap, ov;
+          if (!wall_geom(G, pi, a, side, ri, gap, ov)) continue;
           T x[3] = {0, 0, 0};
           x[a] = side == 0 ? gap : -gap;
           // the wall vector depends on x_i only through its axis-a component
           T w[3] = {0, 0, 0};
-          gm += pair_force_adj(P, x[0], x[1], x[2], gap * gap, vi.x, vi.y, vi.z, ri, mi, li.x, li.y, li.z, li.x, li.y,
-                               li.z, w[0], w[1], w[2], gv0, gv1, gv2);
+          gm += pair_force_adj(P, x[0], x[1], x[2], gap, ov, vi.x, vi.y, vi.z, mi, li.x, li.y, li.z, li.x, li.y, li.z,
+                               w[0], w[1], w[2], gv0, gv1, gv2);
           if (a == 0) gx0 += w[0];
           else if (a == 1) gx1 += w[1];
           else gx2 += w[2];
@@ -291,10 +378,8 @@ __global__ void k_contact_pairs(DGrid G, int64_t n, const int32_t* __restrict__ 
   int cnt = 0;
   for_each_partner(G, table, epoch, i, cx, cy, cz, [&](int64_t j, int ox, int oy, int oz) {
     pos_t<T> pj = pos[j];
-    T x0, x1, x2;
-    rel_ij(G, pi, pj, ox, oy, oz, x0, x1, x2);
-    T R = ri + radius_of(pj);
-    if (!(x0 * x0 + x1 * x1 + x2 * x2 < R * R)) return;
+    PairGeom<T> g;
+    if (!pair_geom(G, pi, pj, ox, oy, oz, ri, radius_of(pj), g)) return;
     ++cnt;
     int32_t idj = id ? id[j] : (int32_t)j;
     if (pairs && idi < idj) {

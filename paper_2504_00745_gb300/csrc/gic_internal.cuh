@@ -50,6 +50,8 @@ struct DGrid {
   double unit, inv_unit;  // h_c 2^-30 and its inverse
   double inv_k_frac;      // 1 / (k 2^30)
   float dx_f, hc_f, inv_dx_f, inv_hc_f, unit_f, inv_unit_f, inv_k_f;
+  float s_hi, s_lo;  // 2^30 / h_c as an unevaluated float pair (hi + lo)
+  float s2_margin;   // s_hi^2 (1 + 4e-6): contact pre-test threshold factor
 };
 
 template <typename T>

@@ -144,3 +144,101 @@ class Simulator:
 
     def status(self, clear=True) -> int:
         return gic.gic_check_status(clear=clear)
+
+
+# ---------------------------------------------------------------------------
+# differentiable window
+# ---------------------------------------------------------------------------
+
+def _copy_state(dst: State, src: State):
+    dst.cell.copy_(src.cell)
+    dst.pos.copy_(src.pos)
+    dst.vel.copy_(src.vel)
+    if dst.id is not None and src.id is not None:
+        dst.id.copy_(src.id)
+
+
+class GicWindow(torch.autograd.Function):
+    """x_K = window(v0, c_drag, mu): K substeps from the simulator's initial
+    state with initial velocities v0 (FP64 [n, 3], original order), drag
+    coefficient c_drag and friction coefficient mu (0-d tensors).  Returns the
+    final absolute positions (FP64 [n, 3], original order).
+
+    Backward: the window is cut into segments of `ckpt` substeps; the state at
+    the start of each segment is kept from the forward pass, every segment is
+    recomputed from it in reverse order, and each substep's adjoint runs
+    gic_integrate_adj, gic_g2p_couple_adj, gic_contact_adj and gic_sort_adj.
+    """
+
+    @staticmethod
+    def forward(ctx, v0, c_drag, mu, sim: "Simulator", init: State, K: int, ckpt: int):
+        sim.params.c_drag = float(c_drag)
+        sim.params.mu_fric = float(mu)
+        _copy_state(sim.A, init)
+        vel = sim.A.vel
+        vel[:, :3] = v0.detach().to(vel.dtype)  # init is in original order (id = 0..n-1)
+        vel[:, 3] = 0
+        ckpts = []
+        for s in range(K):
+            if s % ckpt == 0:
+                ckpts.append(sim.A.clone())
+            sim.substep(alpha=False, transfer=False, sums=False)
+        x, _ = sim.positions()
+        ctx.sim, ctx.K, ctx.ckpt = sim, K, ckpt
+        ctx.ckpts = ckpts
+        ctx.final = sim.A.clone()
+        return x
+
+    @staticmethod
+    def backward(ctx, g_x):
+        sim, K, ckpt = ctx.sim, ctx.K, ctx.ckpt
+        n, prec = sim.n, sim.precision
+        dev = sim.device
+        g_pos = gic.vec4(n, prec, dev)
+        g_vel = gic.vec4(n, prec, dev)
+        gic.gic_unpack_adj(sim.grid, ctx.final, g_x.contiguous().to(torch.float64), None, g_pos, None)
+        g_pos_b = gic.vec4(n, prec, dev)
+        g_vel_b = gic.vec4(n, prec, dev)
+        gFc = gic.vec4(n, prec, dev)
+        gFfl = gic.vec4(n, prec, dev)
+        gaf = gic.vec4(n, prec, dev)
+        g_scalars = torch.zeros(2, dtype=torch.float64, device=dev)  # [c_drag, mu]
+        F = sim.fluid
+        n_seg = len(ctx.ckpts)
+        for m in reversed(range(n_seg)):
+            s0 = m * ckpt
+            s1 = min(K, s0 + ckpt)
+            # recompute the segment, keeping the state before every substep
+            _copy_state(sim.A, ctx.ckpts[m])
+            pre = []
+            for s in range(s0, s1):
+                pre.append(sim.A.clone())
+                if s < s1 - 1:
+                    sim.substep(alpha=False, transfer=False, sums=False)
+            for s in reversed(range(s0, s1)):
+                S = pre[s - s0]
+                gic.gic_sort(sim.grid, S, sim.B, sim.perm, sim.table, sim.ws)
+                gic.gic_integrate_adj(sim.grid, sim.params, sim.B, g_pos, g_vel, None, g_pos_b, g_vel_b, gFc, gFfl,
+                                      gaf)
+                gic.gic_g2p_couple_adj(sim.grid, sim.params, sim.B, F.u, F.v, F.w, F.p, F.alpha_f, gFfl, gaf, None,
+                                       g_pos_b, g_vel_b, g_scalars[0:1])
+                gic.gic_contact_adj(sim.grid, sim.params, sim.B, sim.table, gFc, g_pos_b, g_vel_b, g_scalars[1:2])
+                gic.gic_sort_adj(n, prec, sim.perm, g_pos_b, g_vel_b, g_pos, g_vel)
+        g_v0 = g_vel[:, :3].to(torch.float64)
+        return g_v0, g_scalars[0].clone(), g_scalars[1].clone(), None, None, None, None
+
+
+def window_loss_and_grads(prob, precision=GIC_FP32, K=None, ckpt=10, device="cuda"):
+    """Loss = mean |x_K - target|^2 of a problem with a target cloud, and its
+    gradients w.r.t. the initial velocities, c_drag and mu (FP64 tensors)."""
+    sim = Simulator.from_problem(prob, precision, device)
+    init = sim.A.clone()
+    K = prob.K if K is None else K
+    v0 = torch.tensor(prob.v, dtype=torch.float64, device=device, requires_grad=True)
+    c = torch.tensor(float(prob.params.c_drag), dtype=torch.float64, device=device, requires_grad=True)
+    mu = torch.tensor(float(prob.params.mu_fric), dtype=torch.float64, device=device, requires_grad=True)
+    x = GicWindow.apply(v0, c, mu, sim, init, K, ckpt)
+    target = torch.as_tensor(prob.target, dtype=torch.float64, device=device)
+    loss = ((x - target) ** 2).sum(dim=1).mean()
+    loss.backward()
+    return loss.detach(), v0.grad, c.grad, mu.grad, sim
