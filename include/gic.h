@@ -152,6 +152,28 @@ int gic_unpack_adj(const GicGrid* grid, const GicGranules* in, const double* gx,
 int gic_sort(const GicGrid* grid, const GicGranules* in, GicGranules* out, int32_t* perm, void* cell_table, void* ws,
              size_t ws_bytes, gic_stream_t stream);
 
+/* gic_sort without a workspace argument, for callers that cannot allocate
+ * device memory (for example code that runs inside a host callback or a
+ * real-time loop where cudaMalloc must not be called, or a host that can only
+ * pass buffers registered in advance).  The paper has no counterpart: this is
+ * an interface convenience of the library.
+ *   Same arguments, results and errors as gic_sort, minus ws / ws_bytes.  The
+ *   radix-sort scratch is a static array of about 4.3 MB compiled into the
+ *   library: it holds at most gic_sort_static_max_n() granules (262,144);
+ *   larger n returns GIC_ERR_INVALID without launching anything.
+ *   The array exists once per device that loads the library, until exit.  The
+ *   first call on each device looks up its device address (make that first
+ *   call before any stream capture).  Every call on a device uses the same
+ *   array: calls that can run at the same time on the GPU (different streams
+ *   without ordering) race and must be serialised by the caller.  The array
+ *   keeps the last call's contents; nothing in it has to start at zero.
+ *   Allocates nothing (no cudaMalloc, no allocating library routine). */
+int gic_sort_static(const GicGrid* grid, const GicGranules* in, GicGranules* out, int32_t* perm, void* cell_table,
+                    gic_stream_t stream);
+
+/* Largest n gic_sort_static accepts. */
+int64_t gic_sort_static_max_n(void);
+
 /* a2: contact force on every granule of a SORTED state (the output of
  * gic_sort with the same cell table): linear spring k_n (r_i + r_j - d) plus
  * dashpot -c_n v_n along the normal, tangential -k_t v_t capped at

@@ -11,6 +11,8 @@
 // Stability: inside a tile each warp ranks 8 consecutive chunks of 32 keys in
 // order, warps own consecutive sub-ranges and tiles are offset by the counts
 // of earlier tiles, so equal keys keep their input order in every pass.
+#include <mutex>
+
 #include "gic_internal.cuh"
 
 namespace gic {
@@ -373,4 +375,86 @@ extern "C" int gic_sort_adj(int64_t n, int32_t precision, const int32_t* perm, c
   count_launches(1);
   GIC_CHECK_LAUNCH("gic_sort_adj");
   return GIC_OK;
+}
+
+// ----------------------------------------------------------------- sort without a caller workspace
+//
+// For callers that cannot allocate device memory themselves -- code running
+// where a cudaMalloc would be unsafe or unavailable, such as inside a host
+// callback, a signal-free real-time loop, or a host that hands the library
+// only pre-registered buffers -- this variant takes its radix-sort scratch
+// from a fixed array compiled into the library instead of a workspace
+// argument.  The array exists once per device that loads the library and
+// lives until the process exits.
+
+namespace gic {
+
+// Largest granule count the static scratch holds.
+constexpr int64_t kStaticSortMaxN = 1 << 18;  // 262,144 granules
+constexpr int kStaticSortTiles = (int)((kStaticSortMaxN + kTile - 1) / kTile);
+// keys and values ping-pong (4 x n x 4 B) + per-tile digit counts + digit totals
+constexpr size_t kStaticSortBytes =
+    4 * ((sizeof(uint32_t) * kStaticSortMaxN + 255) & ~(size_t)255) +
+    ((sizeof(uint32_t) * (size_t)kRadix * kStaticSortTiles + 255) & ~(size_t)255) +
+    ((sizeof(uint32_t) * kRadix + 255) & ~(size_t)255);
+
+static __device__ __align__(256) unsigned char g_static_sort_scratch[kStaticSortBytes];
+
+namespace {
+std::mutex g_static_mu;
+void* g_static_ptr[64] = {nullptr};
+}  // namespace
+
+// Device address of the static scratch on the current device, looked up once
+// per device (host code may not use the symbol's name as an address).
+static int static_scratch(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return set_error(GIC_ERR_CUDA, "gic_sort_static: %s", cudaGetErrorString(e));
+  if (dev < 0 || dev >= 64) return set_error(GIC_ERR_INVALID, "gic_sort_static: device index %d unsupported", dev);
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  if (!g_static_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_static_sort_scratch);
+    if (e != cudaSuccess || !p)
+      return set_error(GIC_ERR_CUDA, "gic_sort_static: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+    g_static_ptr[dev] = p;
+  }
+  *out = g_static_ptr[dev];
+  return GIC_OK;
+}
+
+}  // namespace gic
+
+extern "C" int64_t gic_sort_static_max_n(void) { return gic::kStaticSortMaxN; }
+
+extern "C" int gic_sort_static(const GicGrid* grid, const GicGranules* in, GicGranules* out, int32_t* perm,
+                               void* cell_table, gic_stream_t stream) {
+  DGrid G;
+  int rc = make_grid(grid, &G);
+  if (rc) return rc;
+  if ((rc = check_granules(in, "gic_sort_static in"))) return rc;
+  if ((rc = check_granules(out, "gic_sort_static out"))) return rc;
+  if (in->n != out->n || in->precision != out->precision)
+    return set_error(GIC_ERR_INVALID, "gic_sort_static: in/out size or precision differ");
+  if (in->n > kStaticSortMaxN)
+    return set_error(GIC_ERR_INVALID, "gic_sort_static: %lld granules exceed the static scratch limit of %lld",
+                     (long long)in->n, (long long)kStaticSortMaxN);
+  if (!cell_table) return set_error(GIC_ERR_INVALID, "gic_sort_static: cell_table is NULL");
+  if ((uintptr_t)cell_table % 16) return set_error(GIC_ERR_ALIGN, "gic_sort_static: cell_table must be 16-byte aligned");
+  int64_t n = in->n;
+  if (n == 0) return GIC_OK;
+  if (!perm) return set_error(GIC_ERR_INVALID, "gic_sort_static: perm is NULL");
+  if (in->cell == out->cell || in->pos == out->pos || in->vel == out->vel)
+    return set_error(GIC_ERR_INVALID, "gic_sort_static: in and out must not alias");
+  void* scratch = nullptr;
+  if ((rc = static_scratch(&scratch))) return rc;
+  // Every pass writes the scratch regions it later reads (all tile counts in
+  // the upsweep, keys and values in the downsweep), so the previous call's
+  // contents need no clearing.
+  SortLayout L = sort_layout(G, n);
+  if (L.total > kStaticSortBytes) return set_error(GIC_ERR_INVALID, "gic_sort_static: scratch layout too large");
+  if (in->precision == GIC_FP32)
+    return launch_sort<float>(G, in, out, perm, (uint4*)cell_table, (char*)scratch, L, (cudaStream_t)stream);
+  return launch_sort<double>(G, in, out, perm, (uint4*)cell_table, (char*)scratch, L, (cudaStream_t)stream);
 }

@@ -64,6 +64,7 @@ _SIGS = {
     "gic_p2g_adj": [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P],
     "gic_contact_pairs": [_P, _P, _P, _P, _P, C.c_int64, _P, _P],
     "gic_check_status": [_P, C.c_int32, C.c_int32, _P],
+    "gic_sort_static": [_P, _P, _P, _P, _P, _P],
 }
 # entry points that exist in include/gic.h but are declared optional here
 # (added later in the library's life) are looked up lazily
@@ -94,6 +95,7 @@ def lib():
         L.gic_last_error.restype = C.c_char_p
         L.gic_version.restype = C.c_char_p
         L.gic_launch_count.restype = C.c_int64
+        L.gic_sort_static_max_n.restype = C.c_int64
         _lib = L
     return _lib
 
@@ -220,6 +222,17 @@ def gic_sort(grid: GicGrid, st_in: State, st_out: State, perm, cell_table, ws, s
     a, b = st_in.struct(), st_out.struct()
     _check(lib().gic_sort(C.byref(grid), C.byref(a), C.byref(b), _ptr(perm), _ptr(cell_table), _ptr(ws),
                           ws.numel() * ws.element_size(), _stream(stream)), "gic_sort")
+
+
+def gic_sort_static(grid: GicGrid, st_in: State, st_out: State, perm, cell_table, stream=None):
+    """gic_sort with the library's static scratch instead of a workspace."""
+    a, b = st_in.struct(), st_out.struct()
+    _check(lib().gic_sort_static(C.byref(grid), C.byref(a), C.byref(b), _ptr(perm), _ptr(cell_table),
+                                 _stream(stream)), "gic_sort_static")
+
+
+def gic_sort_static_max_n() -> int:
+    return int(lib().gic_sort_static_max_n())
 
 
 def gic_contact(grid: GicGrid, params: GicParams, st: State, cell_table, F_c, stream=None):
