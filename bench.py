@@ -288,6 +288,10 @@ def run_gpu(args, ws, rank, local):
     variants = {}
     if not args.no_variants:
         variants["fp64_fwd"] = run_fp64(prob, gic, torch, dev, stream)
+        for prec_name, prec in (("fp32", gic.GIC_FP32), ("fp64", gic.GIC_FP64)):
+            variants[f"{prec_name}_adjoint_dam_break"] = run_adjoint(prob, prec, torch, dev)
+            wprob = gi.make("diff_window_100k")
+            variants[f"{prec_name}_adjoint_diff_window"] = run_adjoint(wprob, prec, torch, dev)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -350,6 +354,45 @@ def run_e2e(prob, sim, gic, torch, np, dev, stream, steps):
     sec = statistics.mean(times)
     return {"value": n * K / sec, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
             "ms_per_step": 1000 * sec, "api": "gic_window_forward_host (C ABI, pinned host buffers)"}
+
+
+def run_adjoint(prob, prec, torch, dev, ckpt=10):
+    """Forward window + backward (recompute from checkpoints every `ckpt`
+    substeps + the adjoint kernels) of L = mean |x_K - target|^2, w.r.t. the
+    initial velocities, c_drag and mu.  Reported per granule-substep."""
+    import numpy as np
+
+    from paper_2504_00745_gb300.window import GicWindow, Simulator
+
+    if prob.target is None:
+        rng = np.random.default_rng(7)
+        prob.target = prob.positions() + rng.normal(0.0, 0.5 * float(prob.r.mean()), size=(prob.n, 3))
+    sim = Simulator.from_problem(prob, prec, dev)
+    init = sim.A.clone()
+    target = torch.as_tensor(prob.target, dtype=torch.float64, device=dev)
+    K = prob.K
+    res = []
+    for it in range(2):
+        v0 = torch.tensor(prob.v, dtype=torch.float64, device=dev, requires_grad=True)
+        c = torch.tensor(float(prob.params.c_drag), dtype=torch.float64, device=dev, requires_grad=True)
+        mu = torch.tensor(float(prob.params.mu_fric), dtype=torch.float64, device=dev, requires_grad=True)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        torch.cuda.synchronize()
+        e0.record()
+        x = GicWindow.apply(v0, c, mu, sim, init, K, ckpt)
+        loss = ((x - target) ** 2).sum(dim=1).mean()
+        e1.record()
+        loss.backward()
+        e2.record()
+        torch.cuda.synchronize()
+        if it > 0:
+            res.append((e0.elapsed_time(e1), e1.elapsed_time(e2)))
+    fwd_ms, bwd_ms = res[-1]
+    units = prob.n * K
+    return {"value": units / (bwd_ms / 1000), "unit": UNIT, "what": "backward incl. recompute",
+            "fwd_ms": fwd_ms, "bwd_ms": bwd_ms, "fwd_plus_bwd_value": units / ((fwd_ms + bwd_ms) / 1000),
+            "workload": prob.name, "granules": prob.n, "substeps": K, "ckpt_every": ckpt,
+            "dtype": "f32" if prec == 0 else "f64"}
 
 
 def run_fp64(prob, gic, torch, dev, stream, steps=1):

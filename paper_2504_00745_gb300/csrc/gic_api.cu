@@ -91,6 +91,15 @@ int make_grid(const GicGrid* g, DGrid* G) {
   G->s_hi = (float)G->inv_unit;
   G->s_lo = (float)(G->inv_unit - (double)G->s_hi);
   G->s2_margin = (float)((double)G->s_hi * (double)G->s_hi * (1.0 + 4e-6));
+  if (g->k_contact == 1) {
+    G->kinv64 = 0;
+  } else {
+    // ceil(2^64 / k) = floor((2^64 - 1) / k) + 1 for k not a power of two, exact otherwise
+    unsigned long long k = (unsigned long long)g->k_contact;
+    unsigned long long q = ~0ull / k;
+    G->kinv64 = q + 1;
+  }
+  G->vol_fx = 4.0 / 3.0 * kPi / (g->dx * g->dx * g->dx) * 9007199254740992.0;  // * 2^53
   return GIC_OK;
 }
 
@@ -129,6 +138,7 @@ int check_granules(const GicGranules* s, const char* what, bool need_id) {
   size_t al = s->precision == GIC_FP32 ? 16 : 32;
   if (((uintptr_t)s->pos % al) || ((uintptr_t)s->vel % al))
     return set_error(GIC_ERR_ALIGN, "%s: pos/vel must be %zu-byte aligned", what, al);
+  if ((uintptr_t)s->posf % 16) return set_error(GIC_ERR_ALIGN, "%s: posf must be 16-byte aligned", what);
   return GIC_OK;
 }
 

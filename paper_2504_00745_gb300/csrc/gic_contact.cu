@@ -120,21 +120,15 @@ struct PairGeom {
 };
 
 // FP32 path.  The separation is an exact integer vector D in 2^-30 h_c units.
-// A float pre-test with a 4e-6 margin rejects most candidates; survivors get
+// A float pre-test with a small margin rejects most candidates; survivors get
 // the overlap to ~1e-7 of itself (not of d): R = (r_i + r_j) 2^30 / h_c as a
 // float pair (TwoSum / TwoProd), |D|^2 exact in 64-bit integers, d = sqrt with
 // one exact-residual correction, and R - d taken hi-to-hi (exact) plus the
 // low parts.  Plain FP32 would lose the overlap to cancellation (d ~ 100x
 // overlap in dense packings).
-__device__ __forceinline__ bool pair_geom(const DGrid& G, const uint4& pi, const uint4& pj, int ox, int oy, int oz,
-                                          float ri, float rj, PairGeom<float>& g) {
-  int Dx = (int)pi.x - (int)pj.x - ox * (int)kFracOne;
-  int Dy = (int)pi.y - (int)pj.y - oy * (int)kFracOne;
-  int Dz = (int)pi.z - (int)pj.z - oz * (int)kFracOne;
-  float fx = (float)Dx, fy = (float)Dy, fz = (float)Dz;
-  float d2f = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
-  float Rs = ri + rj;
-  if (!(d2f < Rs * Rs * G.s2_margin)) return false;
+// Exact part for a candidate that passed a pre-test (D = integer separation).
+__device__ __forceinline__ bool pair_geom_exact(const DGrid& G, int Dx, int Dy, int Dz, float ri, float rj,
+                                                PairGeom<float>& g) {
   // R (2^-30 h_c units) as hi + lo
   float Rh = ri + rj;
   float bb = Rh - ri;
@@ -156,12 +150,30 @@ __device__ __forceinline__ bool pair_geom(const DGrid& G, const uint4& pi, const
     ov = (Ph - dh) + Pl;
   }
   if (!(ov > 0.0f)) return false;
-  g.x0 = fx * G.unit_f;
-  g.x1 = fy * G.unit_f;
-  g.x2 = fz * G.unit_f;
+  g.x0 = (float)Dx * G.unit_f;
+  g.x1 = (float)Dy * G.unit_f;
+  g.x2 = (float)Dz * G.unit_f;
   g.d = dh * G.unit_f;
   g.overlap = ov * G.unit_f;
   return true;
+}
+
+__device__ __forceinline__ void int_sep(const uint4& pi, const uint4& pj, int ox, int oy, int oz, int& Dx, int& Dy,
+                                        int& Dz) {
+  Dx = (int)pi.x - (int)pj.x - ox * (int)kFracOne;
+  Dy = (int)pi.y - (int)pj.y - oy * (int)kFracOne;
+  Dz = (int)pi.z - (int)pj.z - oz * (int)kFracOne;
+}
+
+__device__ __forceinline__ bool pair_geom(const DGrid& G, const uint4& pi, const uint4& pj, int ox, int oy, int oz,
+                                          float ri, float rj, PairGeom<float>& g) {
+  int Dx, Dy, Dz;
+  int_sep(pi, pj, ox, oy, oz, Dx, Dy, Dz);
+  float fx = (float)Dx, fy = (float)Dy, fz = (float)Dz;
+  float d2f = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
+  float Rs = ri + rj;
+  if (!(d2f < Rs * Rs * G.s2_margin)) return false;
+  return pair_geom_exact(G, Dx, Dy, Dz, ri, rj, g);
 }
 
 __device__ __forceinline__ bool pair_geom(const DGrid& G, const d4& pi, const d4& pj, int ox, int oy, int oz,
@@ -238,11 +250,82 @@ __device__ __forceinline__ void for_each_partner(const DGrid& G, const uint4* __
   }
 }
 
+// Visit every occupied contact cell of the 27 around (cx, cy, cz):
+// f(start, count, ox, oy, oz).
+template <typename F>
+__device__ __forceinline__ void for_each_cell(const DGrid& G, const uint4* __restrict__ table, uint32_t epoch, int cx,
+                                              int cy, int cz, F&& f) {
+  for (int oz = -1; oz <= 1; ++oz) {
+    int z = cz + oz;
+    if (z < 0 || z >= G.nc[2]) continue;
+    for (int oy = -1; oy <= 1; ++oy) {
+      int y = cy + oy;
+      if (y < 0 || y >= G.nc[1]) continue;
+      for (int ox = -1; ox <= 1; ++ox) {
+        int x = cx + ox;
+        if (x < 0 || x >= G.nc[0]) continue;
+        uint4 e = __ldg(&table[table_index(G, x, y, z)]);
+        if (e.z != epoch) continue;
+        f(e.x, e.y, ox, oy, oz);
+      }
+    }
+  }
+}
+
+// FP32 candidate loop on the float copy of the positions: per candidate only
+// float adds / FMAs and one compare; the exact integer geometry runs for
+// candidates within 1e-5 of contact.  f(j, ox, oy, oz, geometry).
+template <typename F>
+__device__ __forceinline__ void for_each_contact_f(const DGrid& G, const uint4* __restrict__ table, uint32_t epoch,
+                                                   int64_t i, int cx, int cy, int cz, const float4& fi,
+                                                   const uint4& pi, float ri, const float4* __restrict__ posf,
+                                                   const uint4* __restrict__ pos, F&& f) {
+  const float rci = ri * G.inv_hc_f;
+  const float m2 = 1.0f + 1e-5f;
+  for_each_cell(G, table, epoch, cx, cy, cz, [&](uint32_t start, uint32_t cnt, int ox, int oy, int oz) {
+    float ax = (float)ox - fi.x, ay = (float)oy - fi.y, az = (float)oz - fi.z;
+    for (uint32_t j = start; j < start + cnt; ++j) {
+      if ((int64_t)j == i) continue;
+      float4 fj = __ldg(&posf[j]);
+      float rx = ax + fj.x, ry = ay + fj.y, rz = az + fj.z;
+      float d2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+      float Rc = fmaf(fj.w, G.inv_hc_f, rci);
+      if (!(d2 < Rc * Rc * m2)) continue;
+      uint4 pj = __ldg(&pos[j]);
+      int Dx, Dy, Dz;
+      int_sep(pi, pj, ox, oy, oz, Dx, Dy, Dz);
+      PairGeom<float> g;
+      if (!pair_geom_exact(G, Dx, Dy, Dz, ri, fj.w, g)) continue;
+      f((int64_t)j, g);
+    }
+  });
+}
+
+// Every partner j of granule i in contact (overlap > 0), with its geometry:
+// f(j, g).  FP32 with a float position copy uses the float pre-test loop.
+template <typename T, typename F>
+__device__ __forceinline__ void for_each_contact(const DGrid& G, const uint4* __restrict__ table, uint32_t epoch,
+                                                 int64_t i, int cx, int cy, int cz, const pos_t<T>& pi, T ri,
+                                                 const pos_t<T>* __restrict__ pos, const float4* __restrict__ posf,
+                                                 F&& f) {
+  if constexpr (sizeof(T) == 4) {
+    if (posf) {
+      for_each_contact_f(G, table, epoch, i, cx, cy, cz, __ldg(&posf[i]), pi, ri, posf, pos, f);
+      return;
+    }
+  }
+  for_each_partner(G, table, epoch, i, cx, cy, cz, [&](int64_t j, int ox, int oy, int oz) {
+    pos_t<T> pj = ldg(&pos[j]);
+    PairGeom<T> g;
+    if (pair_geom(G, pi, pj, ox, oy, oz, ri, radius_of(pj), g)) f(j, g);
+  });
+}
+
 template <typename T>
 __global__ void __launch_bounds__(128) k_contact(DGrid G, DParams<T> P, int64_t n, const int32_t* __restrict__ cell,
-                                                  const pos_t<T>* __restrict__ pos, const vec_t<T>* __restrict__ vel,
-                                                  const uint4* __restrict__ table, vec_t<T>* __restrict__ F,
-                                                  uint32_t* status) {
+                                                  const pos_t<T>* __restrict__ pos, const float4* __restrict__ posf,
+                                                  const vec_t<T>* __restrict__ vel, const uint4* __restrict__ table,
+                                                  vec_t<T>* __restrict__ F, uint32_t* status) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   int32_t ci = cell[i];
@@ -256,13 +339,9 @@ __global__ void __launch_bounds__(128) k_contact(DGrid G, DParams<T> P, int64_t 
   if (T(2) * ri > (T)G.hc) raise_status(status, GIC_STATUS_RADIUS);
   T F0 = 0, F1 = 0, F2 = 0;
   bool coincident = false;
-  for_each_partner(G, table, epoch, i, cx, cy, cz, [&](int64_t j, int ox, int oy, int oz) {
-    pos_t<T> pj = ldg(&pos[j]);
-    T rj = radius_of(pj);
-    PairGeom<T> g;
-    if (!pair_geom(G, pi, pj, ox, oy, oz, ri, rj, g)) return;
+  for_each_contact<T>(G, table, epoch, i, cx, cy, cz, pi, ri, pos, posf, [&](int64_t j, const PairGeom<T>& g) {
     vec_t<T> vj = ldg(&vel[j]);
-    T mj = granule_mass(P, rj);
+    T mj = granule_mass(P, radius_of(ldg(&pos[j])));
     T f0, f1, f2;
     if (pair_force(P, g.x0, g.x1, g.x2, g.d, g.overlap, vi.x - vj.x, vi.y - vj.y, vi.z - vj.z, mi * mj / (mi + mj), f0,
                    f1, f2)) {
@@ -301,6 +380,7 @@ __global__ void __launch_bounds__(128) k_contact(DGrid G, DParams<T> P, int64_t 
 template <typename T>
 __global__ void __launch_bounds__(128) k_contact_adj(DGrid G, DParams<T> P, int64_t n, const int32_t* __restrict__ cell,
                                                       const pos_t<T>* __restrict__ pos,
+                                                      const float4* __restrict__ posf,
                                                       const vec_t<T>* __restrict__ vel, const uint4* __restrict__ table,
                                                       const vec_t<T>* __restrict__ gF, vec_t<T>* __restrict__ gpos,
                                                       vec_t<T>* __restrict__ gvel, double* __restrict__ g_mu) {
@@ -318,14 +398,10 @@ __global__ void __launch_bounds__(128) k_contact_adj(DGrid G, DParams<T> P, int6
     T mi = granule_mass(P, ri);
     uint32_t epoch = __ldg(&table[0].x);
     T gx0 = 0, gx1 = 0, gx2 = 0, gv0 = 0, gv1 = 0, gv2 = 0, gm = 0;
-    for_each_partner(G, table, epoch, i, cx, cy, cz, [&](int64_t j, int ox, int oy, int oz) {
-      pos_t<T> pj = ldg(&pos[j]);
-      T rj = radius_of(pj);
-      PairGeom<T> g;
-      if (!pair_geom(G, pi, pj, ox, oy, oz, ri, rj, g)) return;
+    for_each_contact<T>(G, table, epoch, i, cx, cy, cz, pi, ri, pos, posf, [&](int64_t j, const PairGeom<T>& g) {
       vec_t<T> vj = ldg(&vel[j]);
       vec_t<T> lj = ldg(&gF[j]);
-      T mj = granule_mass(P, rj);
+      T mj = granule_mass(P, radius_of(ldg(&pos[j])));
       gm += pair_force_adj(P, g.x0, g.x1, g.x2, g.d, g.overlap, vi.x - vj.x, vi.y - vj.y, vi.z - vj.z,
                            mi * mj / (mi + mj), li.x - lj.x, li.y - lj.y, li.z - lj.z, li.x, li.y, li.z, gx0, gx1, gx2,
                            gv0, gv1, gv2);
@@ -364,7 +440,7 @@ __global__ void __launch_bounds__(128) k_contact_adj(DGrid G, DParams<T> P, int6
 // Diagnostic: number of partners per granule and the pair list by id.
 template <typename T>
 __global__ void k_contact_pairs(DGrid G, int64_t n, const int32_t* __restrict__ cell, const pos_t<T>* __restrict__ pos,
-                                const int32_t* __restrict__ id, const uint4* __restrict__ table,
+                                const float4* __restrict__ posf, const int32_t* __restrict__ id, const uint4* __restrict__ table,
                                 int32_t* __restrict__ counts, int32_t* __restrict__ pairs, int64_t max_pairs,
                                 unsigned long long* __restrict__ n_pairs) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -376,10 +452,7 @@ __global__ void k_contact_pairs(DGrid G, int64_t n, const int32_t* __restrict__ 
   int32_t idi = id ? id[i] : (int32_t)i;
   uint32_t epoch = __ldg(&table[0].x);
   int cnt = 0;
-  for_each_partner(G, table, epoch, i, cx, cy, cz, [&](int64_t j, int ox, int oy, int oz) {
-    pos_t<T> pj = pos[j];
-    PairGeom<T> g;
-    if (!pair_geom(G, pi, pj, ox, oy, oz, ri, radius_of(pj), g)) return;
+  for_each_contact<T>(G, table, epoch, i, cx, cy, cz, pi, ri, pos, posf, [&](int64_t j, const PairGeom<T>&) {
     ++cnt;
     int32_t idj = id ? id[j] : (int32_t)j;
     if (pairs && idi < idj) {
@@ -418,14 +491,14 @@ extern "C" int gic_contact(const GicGrid* grid, const GicParams* params, const G
     DParams<float> P;
     if ((rc = make_params(params, &P))) return rc;
     k_contact<float><<<grid_blocks(s->n, threads), threads, 0, stream>>>(
-        G, P, s->n, s->cell, (const uint4*)s->pos, (const float4*)s->vel, (const uint4*)table, (float4*)F_c,
-        status_word());
+        G, P, s->n, s->cell, (const uint4*)s->pos, (const float4*)s->posf, (const float4*)s->vel,
+        (const uint4*)table, (float4*)F_c, status_word());
   } else {
     DParams<double> P;
     if ((rc = make_params(params, &P))) return rc;
-    k_contact<double><<<grid_blocks(s->n, threads), threads, 0, stream>>>(G, P, s->n, s->cell, (const d4*)s->pos,
-                                                                           (const d4*)s->vel, (const uint4*)table,
-                                                                           (d4*)F_c, status_word());
+    k_contact<double><<<grid_blocks(s->n, threads), threads, 0, stream>>>(
+        G, P, s->n, s->cell, (const d4*)s->pos, nullptr, (const d4*)s->vel, (const uint4*)table, (d4*)F_c,
+        status_word());
   }
   count_launches(1);
   GIC_CHECK_LAUNCH("gic_contact");
@@ -447,14 +520,14 @@ extern "C" int gic_contact_adj(const GicGrid* grid, const GicParams* params, con
     DParams<float> P;
     if ((rc = make_params(params, &P))) return rc;
     k_contact_adj<float><<<grid_blocks(s->n, threads), threads, 0, stream>>>(
-        G, P, s->n, s->cell, (const uint4*)s->pos, (const float4*)s->vel, (const uint4*)table, (const float4*)gF_c,
-        (float4*)g_pos, (float4*)g_vel, g_mu);
+        G, P, s->n, s->cell, (const uint4*)s->pos, (const float4*)s->posf, (const float4*)s->vel, (const uint4*)table,
+        (const float4*)gF_c, (float4*)g_pos, (float4*)g_vel, g_mu);
   } else {
     DParams<double> P;
     if ((rc = make_params(params, &P))) return rc;
     k_contact_adj<double><<<grid_blocks(s->n, threads), threads, 0, stream>>>(
-        G, P, s->n, s->cell, (const d4*)s->pos, (const d4*)s->vel, (const uint4*)table, (const d4*)gF_c, (d4*)g_pos,
-        (d4*)g_vel, g_mu);
+        G, P, s->n, s->cell, (const d4*)s->pos, nullptr, (const d4*)s->vel, (const uint4*)table, (const d4*)gF_c,
+        (d4*)g_pos, (d4*)g_vel, g_mu);
   }
   count_launches(1);
   GIC_CHECK_LAUNCH("gic_contact_adj");
@@ -471,11 +544,13 @@ extern "C" int gic_contact_pairs(const GicGrid* grid, const GicGranules* s, cons
   if (s->n == 0) return GIC_OK;
   if (pairs && !n_pairs) return set_error(GIC_ERR_INVALID, "gic_contact_pairs: n_pairs is NULL");
   if (s->precision == GIC_FP32)
-    k_contact_pairs<float><<<grid_blocks(s->n, 128), 128, 0, stream>>>(G, s->n, s->cell, (const uint4*)s->pos, s->id,
+    k_contact_pairs<float><<<grid_blocks(s->n, 128), 128, 0, stream>>>(G, s->n, s->cell, (const uint4*)s->pos,
+                                                                        (const float4*)s->posf, s->id,
                                                                         (const uint4*)table, counts, pairs, max_pairs,
                                                                         (unsigned long long*)n_pairs);
   else
-    k_contact_pairs<double><<<grid_blocks(s->n, 128), 128, 0, stream>>>(G, s->n, s->cell, (const d4*)s->pos, s->id,
+    k_contact_pairs<double><<<grid_blocks(s->n, 128), 128, 0, stream>>>(G, s->n, s->cell, (const d4*)s->pos, nullptr,
+                                                                         s->id,
                                                                          (const uint4*)table, counts, pairs,
                                                                          max_pairs, (unsigned long long*)n_pairs);
   count_launches(1);

@@ -166,6 +166,107 @@ __global__ void k_alpha_sum(const double* __restrict__ a, int64_t m, double dx3,
   if (threadIdx.x == 0) atomicAdd(&sums[0], s * dx3);
 }
 
+// ---- FP32 path: exact fixed-point volume fraction ----
+//
+// alpha_s is accumulated as a 64-bit integer in units of 2^-53: per granule
+// the volume fraction S = V / dx^3 is rounded once to 2^-53, the tent weights
+// come from the 30-bit fixed-point position as 31-bit integers (the eighth
+// corner takes the remainder, so every granule deposits exactly S up to the
+// final truncations), and integer atomics make the sum independent of the
+// order of arrival -- bitwise reproducible.  k_alpha_finish turns the
+// integers into doubles in place.
+
+constexpr uint32_t kW1 = 1u << 31;  // weight 1.0
+constexpr double kAlphaUnit = 1.0 / 9007199254740992.0;  // 2^-53
+
+// Centred-stencil weights of one axis from the contact coordinate c and the
+// fixed-point offset q: lower sample i0 and integer weights (w0, w1), w0 + w1 = 2^31.
+__device__ __forceinline__ void fixed_axis(const DGrid& G, int c, uint32_t q, int n, int& i0, uint32_t& w1) {
+  int m = mac_of(G, c);
+  unsigned long long N = ((unsigned long long)(c - m * G.k) << kFracBits) | q;  // offset in 2^-30 h_c
+  // P = round(N * 2 / k): the offset inside the MAC cell in units of 2^-31 dx
+  unsigned long long P;
+  if (G.k == 1)
+    P = N << 1;
+  else
+    P = (__umul64hi(N << 2, G.kinv64) + 1ull) >> 1;
+  uint32_t p = (uint32_t)P;  // < 2^31
+  if (p >= (1u << 30)) {
+    i0 = m;
+    w1 = p - (1u << 30);
+  } else {
+    i0 = m - 1;
+    w1 = p + (1u << 30);
+  }
+  if (i0 < 0) {
+    i0 = 0;
+    w1 = 0;
+  } else if (i0 > n - 2) {
+    i0 = n - 2;
+    w1 = kW1;
+  }
+}
+
+__device__ __forceinline__ uint32_t wmul(uint32_t a, uint32_t b) {
+  return (uint32_t)(((unsigned long long)a * b + (1ull << 30)) >> 31);
+}
+
+// (S * w) >> 31 for S < 2^54, |w| <= 2^31 (w may be slightly negative for the remainder corner)
+__device__ __forceinline__ long long wscale(unsigned long long S, long long w) {
+  if (w >= 0) return (long long)__umul64hi(S << 1, (unsigned long long)w << 32);
+  return -(long long)__umul64hi(S << 1, (unsigned long long)(-w) << 32);
+}
+
+__device__ __forceinline__ void scatter_alpha_fixed(const DGrid& G, int32_t cell, const uint4& p,
+                                                    unsigned long long* __restrict__ acc, double& Vi) {
+  double r = (double)__uint_as_float(p.w);
+  double r3 = r * r * r;
+  Vi = 4.0 / 3.0 * kPi * r3;
+  unsigned long long S = (unsigned long long)__double2ll_rn(G.vol_fx * r3);
+  int c3[3] = {cell_x(cell), cell_y(cell), cell_z(cell)};
+  const int n[3] = {G.nx, G.ny, G.nz};
+  int i0[3];
+  uint32_t w1[3], w0[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    fixed_axis(G, c3[a], pcomp(p, a), n[a], i0[a], w1[a]);
+    w0[a] = kW1 - w1[a];
+  }
+  long long w[8];
+  long long sum7 = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    int a = k & 1, b = (k >> 1) & 1, cz = (k >> 2) & 1;
+    uint32_t wxy = wmul(a ? w1[0] : w0[0], b ? w1[1] : w0[1]);
+    w[k] = (long long)wmul(wxy, cz ? w1[2] : w0[2]);
+    if (k < 7) sum7 += w[k];
+  }
+  w[7] = (long long)kW1 - sum7;  // exact partition of unity
+  int64_t base = sample_index(G.nx, G.ny, i0[0], i0[1], i0[2]);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    int a = k & 1, b = (k >> 1) & 1, cz = (k >> 2) & 1;
+    long long v = wscale(S, w[k]);
+    if (v) atomicAdd(&acc[base + a + (int64_t)G.nx * (b + (int64_t)G.ny * cz)], (unsigned long long)v);
+  }
+}
+
+// In place: 64-bit fixed-point alpha_s -> double, and sum_c alpha_s dx^3.
+__global__ void k_alpha_finish(double* __restrict__ a, int64_t m, double dx3, double* __restrict__ sums) {
+  __shared__ double s_red[32];
+  double acc = 0.0;
+  long long* ai = reinterpret_cast<long long*>(a);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    double v = (double)ai[i] * kAlphaUnit;
+    a[i] = v;
+    acc += v;
+  }
+  if (sums) {
+    double s = block_sum(acc, s_red);
+    if (threadIdx.x == 0) atomicAdd(&sums[0], s * dx3);
+  }
+}
+
 // alpha_s(c) = sum_i V_i N(x'_i - x_c) / dx^3 at the new positions, FP64
 // weights (from the exact fixed-point state) and FP64 atomics;
 // F_s(face) += exch * f_ex_i N(x_i - x_face) at the old positions, with a
@@ -181,7 +282,9 @@ __global__ void __launch_bounds__(256) k_p2g(DGrid G, DParams<T> P, int64_t n, c
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   bool valid = i < n;
   double Vi = 0.0;
-  if (valid && alpha) {
+  if constexpr (sizeof(T) == 4) {
+    if (valid && alpha) scatter_alpha_fixed(G, cell_new[i], pos_new[i], (unsigned long long*)alpha, Vi);
+  } else if (valid && alpha) {
     pos_t<T> pn = pos_new[i];
     double r = (double)radius_of(pn);
     Vi = 4.0 / 3.0 * kPi * r * r * r;
@@ -415,7 +518,11 @@ extern "C" int gic_p2g(const GicGrid* grid, const GicParams* params, const GicGr
     }
     ++launches;
   }
-  if (sums2) {
+  if (alpha_s && old_->precision == GIC_FP32) {
+    // the FP32 path accumulated 64-bit fixed point: convert in place (and sum)
+    k_alpha_finish<<<1184, 256, 0, stream>>>(alpha_s, ncell, G.dx * G.dx * G.dx, sums2);
+    ++launches;
+  } else if (sums2) {
     k_alpha_sum<<<592, 256, 0, stream>>>(alpha_s, ncell, G.dx * G.dx * G.dx, sums2);
     ++launches;
   }

@@ -52,6 +52,8 @@ struct DGrid {
   float dx_f, hc_f, inv_dx_f, inv_hc_f, unit_f, inv_unit_f, inv_k_f;
   float s_hi, s_lo;  // 2^30 / h_c as an unevaluated float pair (hi + lo)
   float s2_margin;   // s_hi^2 (1 + 4e-6): contact pre-test threshold factor
+  unsigned long long kinv64;  // ceil(2^64 / k) for k > 1 (fixed-point division by k), 0 for k = 1
+  double vol_fx;              // (4/3) pi / dx^3 * 2^53: granule volume fraction in 2^-53 units per r^3
 };
 
 template <typename T>

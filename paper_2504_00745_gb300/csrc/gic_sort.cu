@@ -138,6 +138,7 @@ struct ScatterState {
   void* out_vel;
   int32_t* out_id;
   int32_t* perm;
+  float4* out_posf;  // FP32 path: float copy of the sorted positions, or NULL
 };
 
 // Rank every key of the tile stably and scatter.  Not-last passes write
@@ -222,7 +223,13 @@ __global__ void __launch_bounds__(kSortThreads) k_downsweep(int64_t n, int shift
       uint32_t src = r_val[c];
       S.perm[pos] = (int32_t)src;
       S.out_cell[pos] = S.in_cell[src];
-      ((pos_t<T>*)S.out_pos)[pos] = ((const pos_t<T>*)S.in_pos)[src];
+      pos_t<T> p = ((const pos_t<T>*)S.in_pos)[src];
+      ((pos_t<T>*)S.out_pos)[pos] = p;
+      if constexpr (sizeof(T) == 4) {
+        if (S.out_posf)
+          S.out_posf[pos] = make_float4((float)p.x * 0x1p-30f, (float)p.y * 0x1p-30f, (float)p.z * 0x1p-30f,
+                                        __uint_as_float(p.w));
+      }
       ((vec_t<T>*)S.out_vel)[pos] = ((const vec_t<T>*)S.in_vel)[src];
       if (S.out_id) S.out_id[pos] = S.in_id ? S.in_id[src] : (int32_t)src;
     }
@@ -258,7 +265,8 @@ static int launch_sort(const DGrid& G, const GicGranules* in, GicGranules* out, 
   uint32_t* vals_b = (uint32_t*)(ws + L.off_vals_b);
   uint32_t* counts = (uint32_t*)(ws + L.off_counts);
   uint32_t* totals = (uint32_t*)(ws + L.off_totals);
-  ScatterState S{in->cell, in->pos, in->vel, in->id, out->cell, out->pos, out->vel, out->id, perm};
+  ScatterState S{in->cell, in->pos,  in->vel, in->id, out->cell,
+                 out->pos, out->vel, out->id, perm, sizeof(T) == 4 ? (float4*)out->posf : nullptr};
   const uint32_t* kin = nullptr;
   const uint32_t* vin = nullptr;
   uint32_t* kout = keys_a;

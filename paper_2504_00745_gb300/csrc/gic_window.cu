@@ -29,8 +29,8 @@ static int window_layout(const GicGrid* grid, int64_t n, int32_t precision, Wind
   L->sort_ws = al(ws);
   L->off_sort = off;
   off += L->sort_ws;
-  L->off_state_b = off;  // cell, pos, vel, id of the second state
-  off += al(4 * nn) + vec + vec + al(4 * nn);
+  L->off_state_b = off;  // cell, pos, vel, id of the second state (+ float positions, FP32)
+  off += al(4 * nn) + vec + vec + al(4 * nn) + (precision == GIC_FP32 ? al(16 * nn) : 0);
   L->off_perm = off;
   off += al(4 * nn);
   L->off_fc = off;
@@ -89,6 +89,7 @@ static GicGranules state_at(char* base, int64_t n, int32_t precision) {
   s.vel = base + al(4 * nn) + vec;
   s.id = (int32_t*)(base + al(4 * nn) + 2 * vec);
   s.precision = precision;
+  s.posf = nullptr;
   return s;
 }
 
@@ -130,6 +131,10 @@ extern "C" int gic_window_forward(const GicGrid* grid, const GicParams* params, 
   char* base = (char*)ws;
   GicGranules B = state_at(base + L.off_state_b, state->n, state->precision);
   if (!state->id) B.id = nullptr;
+  if (state->precision == GIC_FP32) {
+    size_t nn = (size_t)(state->n > 0 ? state->n : 1);
+    B.posf = (float*)(base + L.off_state_b + al(4 * nn) + 2 * al(16 * nn) + al(4 * nn));
+  }
   int32_t* perm = (int32_t*)(base + L.off_perm);
   void* Fc = base + L.off_fc;
   void* Ffl = base + L.off_ffl;

@@ -42,7 +42,7 @@ class GicParams(C.Structure):
 
 class GicGranules(C.Structure):
     _fields_ = [("n", C.c_int64), ("cell", C.c_void_p), ("pos", C.c_void_p), ("vel", C.c_void_p), ("id", C.c_void_p),
-                ("precision", C.c_int32)]
+                ("precision", C.c_int32), ("posf", C.c_void_p)]
 
 
 _P = C.c_void_p
@@ -145,6 +145,7 @@ class State:
     vel: torch.Tensor   # float32 / float64 [n, 4]
     id: Optional[torch.Tensor]  # int32 [n] or None
     precision: int
+    posf: Optional[torch.Tensor] = None  # FP32 path: float32 [n, 4] copy written by gic_sort, or None
 
     @property
     def n(self) -> int:
@@ -155,20 +156,24 @@ class State:
         return torch.float32 if self.precision == GIC_FP32 else torch.float64
 
     @staticmethod
-    def empty(n: int, precision: int, device="cuda", with_id=True) -> "State":
+    def empty(n: int, precision: int, device="cuda", with_id=True, with_posf=False) -> "State":
         real = torch.float32 if precision == GIC_FP32 else torch.float64
         pos_dtype = torch.int32 if precision == GIC_FP32 else torch.float64
+        posf = torch.empty((n, 4), dtype=torch.float32, device=device) if (with_posf and precision == GIC_FP32) \
+            else None
         return State(torch.empty(n, dtype=torch.int32, device=device),
                      torch.empty((n, 4), dtype=pos_dtype, device=device),
                      torch.zeros((n, 4), dtype=real, device=device),
-                     torch.empty(n, dtype=torch.int32, device=device) if with_id else None, precision)
+                     torch.empty(n, dtype=torch.int32, device=device) if with_id else None, precision, posf)
 
     def struct(self) -> GicGranules:
-        return GicGranules(self.n, _ptr(self.cell), _ptr(self.pos), _ptr(self.vel), _ptr(self.id), self.precision)
+        return GicGranules(self.n, _ptr(self.cell), _ptr(self.pos), _ptr(self.vel), _ptr(self.id), self.precision,
+                           _ptr(self.posf))
 
     def clone(self) -> "State":
         return State(self.cell.clone(), self.pos.clone(), self.vel.clone(),
-                     None if self.id is None else self.id.clone(), self.precision)
+                     None if self.id is None else self.id.clone(), self.precision,
+                     None if self.posf is None else self.posf.clone())
 
 
 def vec4(n: int, precision: int, device="cuda") -> torch.Tensor:

@@ -49,7 +49,7 @@ class Simulator:
         self.real = torch.float32 if precision == GIC_FP32 else torch.float64
         n = self.n
         self.A = State.empty(n, precision, device)
-        self.B = State.empty(n, precision, device)
+        self.B = State.empty(n, precision, device, with_posf=True)  # sorted state: float position copy (FP32)
         self.perm = torch.empty(n, dtype=torch.int32, device=device)
         self.table = gic.new_cell_table(self.grid, device)
         self.ws = gic.new_workspace(self.grid, n, precision, device)
