@@ -100,6 +100,8 @@ int make_grid(const GicGrid* g, DGrid* G) {
     G->kinv64 = q + 1;
   }
   G->vol_fx = 4.0 / 3.0 * kPi / (g->dx * g->dx * g->dx) * 9007199254740992.0;  // * 2^53
+  G->vol_fx_hi = (float)G->vol_fx;
+  G->vol_fx_lo = (float)(G->vol_fx - (double)G->vol_fx_hi);
   return GIC_OK;
 }
 

@@ -377,6 +377,227 @@ __global__ void __launch_bounds__(128) k_contact(DGrid G, DParams<T> P, int64_t 
   F[i] = make_vec<T>(F0, F1, F2);
 }
 
+// ----------------------------------------------------------------- staged FP32 contact
+//
+// One CTA = 128 consecutive granules of the Morton-sorted state: a compact
+// blob of contact cells.  The CTA stages the cell-table entries of the
+// blob's bounding box (+1 cell halo) and the float positions of every
+// granule in those cells in shared memory, then each thread walks its 27
+// neighbour cells there.  A CTA whose box or granule count exceeds the
+// shared-memory budget (a Morton range that jumps across the domain) takes
+// the global-memory path instead; the results are identical.
+
+constexpr int kTileThreads = 128;
+constexpr int kTileMaxCells = 512;
+constexpr int kTileMaxGranules = 1152;
+
+__device__ __forceinline__ void add_pair_force(const DParams<float>& P, const PairGeom<float>& g, const float4& vi,
+                                               const float4& vj, float mi, float mj, float& F0, float& F1, float& F2,
+                                               bool& coincident) {
+  float f0, f1, f2;
+  if (pair_force(P, g.x0, g.x1, g.x2, g.d, g.overlap, vi.x - vj.x, vi.y - vj.y, vi.z - vj.z, mi * mj / (mi + mj), f0,
+                 f1, f2)) {
+    F0 += f0;
+    F1 += f1;
+    F2 += f2;
+  } else {
+    coincident = true;
+  }
+}
+
+__global__ void __launch_bounds__(kTileThreads) k_contact_tile(DGrid G, DParams<float> P, int64_t n,
+                                                               const int32_t* __restrict__ cell,
+                                                               const uint4* __restrict__ pos,
+                                                               const float4* __restrict__ posf,
+                                                               const float4* __restrict__ vel,
+                                                               const uint4* __restrict__ table,
+                                                               float4* __restrict__ F, uint32_t* status) {
+  __shared__ int s_lo[3], s_hi[3];
+  __shared__ uint32_t s_start[kTileMaxCells];
+  __shared__ uint32_t s_cnt[kTileMaxCells];
+  __shared__ uint32_t s_off[kTileMaxCells + 1];
+  __shared__ float4 s_pf[kTileMaxGranules];
+  __shared__ uint32_t s_wsum[kTileThreads / 32];
+  __shared__ int s_mode;  // 0: staged, 1: global fallback
+
+  const int64_t i = blockIdx.x * (int64_t)kTileThreads + threadIdx.x;
+  const bool valid = i < n;
+  const uint32_t epoch = __ldg(&table[0].x);
+  int cx = 0, cy = 0, cz = 0;
+  if (threadIdx.x < 3) {
+    s_lo[threadIdx.x] = 1 << 30;
+    s_hi[threadIdx.x] = -1;
+  }
+  __syncthreads();
+  if (valid) {
+    int32_t ci = cell[i];
+    cx = cell_x(ci);
+    cy = cell_y(ci);
+    cz = cell_z(ci);
+    atomicMin(&s_lo[0], cx);
+    atomicMin(&s_lo[1], cy);
+    atomicMin(&s_lo[2], cz);
+    atomicMax(&s_hi[0], cx);
+    atomicMax(&s_hi[1], cy);
+    atomicMax(&s_hi[2], cz);
+  }
+  __syncthreads();
+  // bounding box with a one-cell halo, clipped to the grid
+  const int bx0 = max(s_lo[0] - 1, 0), by0 = max(s_lo[1] - 1, 0), bz0 = max(s_lo[2] - 1, 0);
+  const int bx = min(s_hi[0] + 1, G.nc[0] - 1) - bx0 + 1;
+  const int by = min(s_hi[1] + 1, G.nc[1] - 1) - by0 + 1;
+  const int bz = min(s_hi[2] + 1, G.nc[2] - 1) - bz0 + 1;
+  const int ncell = bx * by * bz;
+  if (threadIdx.x == 0) s_mode = (ncell > kTileMaxCells || s_hi[0] < 0) ? 1 : 0;
+  __syncthreads();
+  if (s_mode == 0) {
+    // stage the table entries of the box
+    // box index -> coordinates with float reciprocals (exact for these small integers)
+    const float ibx = 1.0f / (float)bx, ibxy = 1.0f / (float)(bx * by);
+    for (int b = threadIdx.x; b < ncell; b += kTileThreads) {
+      int z = (int)(((float)b + 0.5f) * ibxy);
+      int rem = b - z * bx * by;
+      int y = (int)(((float)rem + 0.5f) * ibx);
+      int x = bx0 + rem - y * bx;
+      y += by0;
+      z += bz0;
+      uint4 e = __ldg(&table[table_index(G, x, y, z)]);
+      bool ok = e.z == epoch;
+      s_start[b] = ok ? e.x : 0u;
+      s_cnt[b] = ok ? e.y : 0u;
+    }
+    __syncthreads();
+    // exclusive scan of the counts (ncell <= 512: 4 per thread)
+    {
+      const int per = (kTileMaxCells + kTileThreads - 1) / kTileThreads;
+      uint32_t loc[per];
+      uint32_t sum = 0;
+#pragma unroll
+      for (int k = 0; k < per; ++k) {
+        int b = threadIdx.x * per + k;
+        loc[k] = b < ncell ? s_cnt[b] : 0u;
+        sum += loc[k];
+      }
+      uint32_t incl = sum;
+      for (int off = 1; off < 32; off <<= 1) {
+        uint32_t o = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane_id() >= off) incl += o;
+      }
+      if (lane_id() == 31) s_wsum[threadIdx.x >> 5] = incl;
+      __syncthreads();
+      uint32_t base = 0;
+      for (int w = 0; w < (threadIdx.x >> 5); ++w) base += s_wsum[w];
+      uint32_t run = base + incl - sum;
+#pragma unroll
+      for (int k = 0; k < per; ++k) {
+        int b = threadIdx.x * per + k;
+        if (b < kTileMaxCells) s_off[b] = run;
+        run += loc[k];
+      }
+      if (threadIdx.x == kTileThreads - 1) s_off[kTileMaxCells] = run;
+    }
+    __syncthreads();
+    const uint32_t total = s_off[kTileMaxCells];
+    if (total > (uint32_t)kTileMaxGranules) {
+      if (threadIdx.x == 0) s_mode = 1;
+    } else {
+      // stage the float positions: slot t belongs to cell b with s_off[b] <= t < s_off[b + 1]
+      for (uint32_t t = threadIdx.x; t < total; t += kTileThreads) {
+        int lo = 0, hi = ncell - 1;  // last b with s_off[b] <= t
+        while (lo < hi) {
+          int mid = (lo + hi + 1) >> 1;
+          if (s_off[mid] <= t) lo = mid;
+          else hi = mid - 1;
+        }
+        // position in units of contact cells relative to the box corner: the three
+        // cells of an x-row are consecutive slots, and no cell offset is needed
+        float4 p = __ldg(&posf[s_start[lo] + (t - s_off[lo])]);
+        int lz = (int)(((float)lo + 0.5f) * ibxy);
+        int rem = lo - lz * bx * by;
+        int ly = (int)(((float)rem + 0.5f) * ibx);
+        int lx = rem - ly * bx;
+        s_pf[t] = make_float4((float)lx + p.x, (float)ly + p.y, (float)lz + p.z, p.w);
+      }
+    }
+    __syncthreads();
+  }
+  if (!valid) return;
+  const uint4 pi = pos[i];
+  const float4 vi = vel[i];
+  const float ri = __uint_as_float(pi.w);
+  const float mi = granule_mass(P, ri);
+  if (2.0f * ri > G.hc_f) raise_status(status, GIC_STATUS_RADIUS);
+  float F0 = 0.f, F1 = 0.f, F2 = 0.f;
+  bool coincident = false;
+  if (s_mode == 0) {
+    const int lx = cx - bx0, ly = cy - by0, lz = cz - bz0;
+    const float4 fi0 = __ldg(&posf[i]);
+    const float xi = (float)lx + fi0.x, yi = (float)ly + fi0.y, zi = (float)lz + fi0.z;
+    const float rci = ri * G.inv_hc_f;
+    // box coordinates reach 2^6 cells: their float rounding (< 1e-5 cell) stays inside this margin
+    const float m2 = 1.0f + 1e-4f;
+    const int xa = max(lx - 1, 0), xb = min(lx + 1, bx - 1);
+    // own slot (excluded): own cell's first slot + rank inside the cell
+    const int bown = lx + bx * (ly + by * lz);
+    const uint32_t tself = s_off[bown] + (uint32_t)(i - (int64_t)s_start[bown]);
+    for (int oz = -1; oz <= 1; ++oz) {
+      int z = lz + oz;
+      if (z < 0 || z >= bz) continue;
+      for (int oy = -1; oy <= 1; ++oy) {
+        int y = ly + oy;
+        if (y < 0 || y >= by) continue;
+        int row = bx * (y + by * z);
+        uint32_t t0 = s_off[row + xa], t1 = s_off[row + xb + 1];
+        for (uint32_t t = t0; t < t1; ++t) {
+          float4 fj = s_pf[t];
+          float rx = fj.x - xi, ry = fj.y - yi, rz = fj.z - zi;
+          float d2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+          float Rc = fmaf(fj.w, G.inv_hc_f, rci);
+          if (!(d2 < Rc * Rc * m2) || t == tself) continue;
+          // contact candidate: locate j and its cell offset, then the exact geometry
+          int bj = row + xa;
+          while (s_off[bj + 1] <= t) ++bj;
+          uint32_t j = s_start[bj] + (t - s_off[bj]);
+          int ox = (bj - row) - lx;
+          uint4 pj = __ldg(&pos[j]);
+          int Dx, Dy, Dz;
+          int_sep(pi, pj, ox, oy, oz, Dx, Dy, Dz);
+          PairGeom<float> g;
+          if (!pair_geom_exact(G, Dx, Dy, Dz, ri, fj.w, g)) continue;
+          add_pair_force(P, g, vi, __ldg(&vel[j]), mi, granule_mass(P, fj.w), F0, F1, F2, coincident);
+        }
+      }
+    }
+  } else {
+    for_each_contact<float>(G, table, epoch, i, cx, cy, cz, pi, ri, pos, posf, [&](int64_t j, const PairGeom<float>& g) {
+      add_pair_force(P, g, vi, __ldg(&vel[j]), mi, granule_mass(P, radius_of(__ldg(&pos[j]))), F0, F1, F2, coincident);
+    });
+  }
+  if (P.walls) {
+    const int c3[3] = {cx, cy, cz};
+    for (int a = 0; a < 3; ++a) {
+      for (int side = 0; side < 2; ++side) {
+        if (side == 0 ? c3[a] != 0 : c3[a] != G.nc[a] - 1) continue;
+        float gap, ov;
+        if (!wall_geom(G, pi, a, side, ri, gap, ov)) continue;
+        float x[3] = {0, 0, 0};
+        x[a] = side == 0 ? gap : -gap;
+        float f0, f1, f2;
+        if (pair_force(P, x[0], x[1], x[2], gap, ov, vi.x, vi.y, vi.z, mi, f0, f1, f2)) {
+          F0 += f0;
+          F1 += f1;
+          F2 += f2;
+        } else {
+          raise_status(status, GIC_STATUS_OUT_OF_DOMAIN);
+        }
+      }
+    }
+  }
+  if (coincident) raise_status(status, GIC_STATUS_COINCIDENT);
+  if (!isfinite(F0) || !isfinite(F1) || !isfinite(F2)) raise_status(status, GIC_STATUS_NONFINITE);
+  F[i] = make_float4(F0, F1, F2, 0.f);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(128) k_contact_adj(DGrid G, DParams<T> P, int64_t n, const int32_t* __restrict__ cell,
                                                       const pos_t<T>* __restrict__ pos,
@@ -490,9 +711,14 @@ extern "C" int gic_contact(const GicGrid* grid, const GicParams* params, const G
   if (s->precision == GIC_FP32) {
     DParams<float> P;
     if ((rc = make_params(params, &P))) return rc;
-    k_contact<float><<<grid_blocks(s->n, threads), threads, 0, stream>>>(
-        G, P, s->n, s->cell, (const uint4*)s->pos, (const float4*)s->posf, (const float4*)s->vel,
-        (const uint4*)table, (float4*)F_c, status_word());
+    if (s->posf)
+      k_contact_tile<<<grid_blocks(s->n, kTileThreads), kTileThreads, 0, stream>>>(
+          G, P, s->n, s->cell, (const uint4*)s->pos, (const float4*)s->posf, (const float4*)s->vel,
+          (const uint4*)table, (float4*)F_c, status_word());
+    else
+      k_contact<float><<<grid_blocks(s->n, threads), threads, 0, stream>>>(
+          G, P, s->n, s->cell, (const uint4*)s->pos, nullptr, (const float4*)s->vel, (const uint4*)table,
+          (float4*)F_c, status_word());
   } else {
     DParams<double> P;
     if ((rc = make_params(params, &P))) return rc;

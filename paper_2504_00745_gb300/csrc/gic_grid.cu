@@ -41,7 +41,7 @@ __device__ __forceinline__ GradPLoad<T> gradp_loader(const DGrid& G, const T* p,
 // F_fl = c_drag pi r^2 rho_f |u_f - v| (u_f - v) - V grad p   (Sec. 3.3 Eqs. 5a, 5b)
 // a_f  = g - grad p / rho_f                                   (Sec. 5.2 Eq. momentum4)
 template <typename T>
-__global__ void __launch_bounds__(256) k_g2p(DGrid G, DParams<T> P, int64_t n, const int32_t* __restrict__ cell,
+__global__ void __launch_bounds__(256, 4) k_g2p(DGrid G, DParams<T> P, int64_t n, const int32_t* __restrict__ cell,
                                               const pos_t<T>* __restrict__ pos, const vec_t<T>* __restrict__ vel,
                                               Fields<T> Fd, vec_t<T>* __restrict__ F_fl, vec_t<T>* __restrict__ a_f,
                                               T* __restrict__ afp, uint32_t* status) {
@@ -207,6 +207,29 @@ __device__ __forceinline__ void fixed_axis(const DGrid& G, int c, uint32_t q, in
   }
 }
 
+// An integer-valued float (|v| >= 2^23) as int64, exactly, with integer ops.
+__device__ __forceinline__ long long float_int_to_ll(float v) {
+  uint32_t b = __float_as_uint(v);
+  int e = (int)((b >> 23) & 0xffu) - 127 - 23;
+  long long m = (long long)((b & 0x7fffffu) | 0x800000u);
+  long long r = e >= 0 ? (m << e) : (m >> (-e));
+  return (b >> 31) ? -r : r;
+}
+
+// S = V / dx^3 in 2^-53 units for radius r, rounded, in FP32 double-float
+// arithmetic (r^3 exact to ~2^-46, the constant as a float pair): the FP64
+// pipe of this GPU is 1/64 of the FP32 rate.
+__device__ __forceinline__ unsigned long long volume_fixed(const DGrid& G, float r) {
+  float r2h = r * r;
+  float r2l = fmaf(r, r, -r2h);
+  float r3h = r2h * r;
+  float r3l = fmaf(r2h, r, -r3h) + r2l * r;
+  float sh = r3h * G.vol_fx_hi;
+  float sl = fmaf(r3h, G.vol_fx_hi, -sh) + fmaf(r3h, G.vol_fx_lo, r3l * G.vol_fx_hi);
+  long long a = fabsf(sh) >= 8388608.0f ? float_int_to_ll(sh) : (long long)__float2ll_rn(sh);
+  return (unsigned long long)(a + __float2ll_rn(sl));
+}
+
 __device__ __forceinline__ uint32_t wmul(uint32_t a, uint32_t b) {
   return (uint32_t)(((unsigned long long)a * b + (1ull << 30)) >> 31);
 }
@@ -217,58 +240,8 @@ __device__ __forceinline__ long long wscale(unsigned long long S, long long w) {
   return -(long long)__umul64hi(S << 1, (unsigned long long)(-w) << 32);
 }
 
-__device__ __forceinline__ void scatter_alpha_fixed(const DGrid& G, int32_t cell, const uint4& p,
-                                                    unsigned long long* __restrict__ acc, double& Vi) {
-  double r = (double)__uint_as_float(p.w);
-  double r3 = r * r * r;
-  Vi = 4.0 / 3.0 * kPi * r3;
-  unsigned long long S = (unsigned long long)__double2ll_rn(G.vol_fx * r3);
-  int c3[3] = {cell_x(cell), cell_y(cell), cell_z(cell)};
-  const int n[3] = {G.nx, G.ny, G.nz};
-  int i0[3];
-  uint32_t w1[3], w0[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    fixed_axis(G, c3[a], pcomp(p, a), n[a], i0[a], w1[a]);
-    w0[a] = kW1 - w1[a];
-  }
-  long long w[8];
-  long long sum7 = 0;
-#pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    int a = k & 1, b = (k >> 1) & 1, cz = (k >> 2) & 1;
-    uint32_t wxy = wmul(a ? w1[0] : w0[0], b ? w1[1] : w0[1]);
-    w[k] = (long long)wmul(wxy, cz ? w1[2] : w0[2]);
-    if (k < 7) sum7 += w[k];
-  }
-  w[7] = (long long)kW1 - sum7;  // exact partition of unity
-  int64_t base = sample_index(G.nx, G.ny, i0[0], i0[1], i0[2]);
-#pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    int a = k & 1, b = (k >> 1) & 1, cz = (k >> 2) & 1;
-    long long v = wscale(S, w[k]);
-    if (v) atomicAdd(&acc[base + a + (int64_t)G.nx * (b + (int64_t)G.ny * cz)], (unsigned long long)v);
-  }
-}
-
-// In place: 64-bit fixed-point alpha_s -> double, and sum_c alpha_s dx^3.
-__global__ void k_alpha_finish(double* __restrict__ a, int64_t m, double dx3, double* __restrict__ sums) {
-  __shared__ double s_red[32];
-  double acc = 0.0;
-  long long* ai = reinterpret_cast<long long*>(a);
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
-    double v = (double)ai[i] * kAlphaUnit;
-    a[i] = v;
-    acc += v;
-  }
-  if (sums) {
-    double s = block_sum(acc, s_red);
-    if (threadIdx.x == 0) atomicAdd(&sums[0], s * dx3);
-  }
-}
-
-// alpha_s(c) = sum_i V_i N(x'_i - x_c) / dx^3 at the new positions, FP64
-// weights (from the exact fixed-point state) and FP64 atomics;
+// FP64 path: alpha_s(c) = sum_i V_i N(x'_i - x_c) / dx^3 at the new positions, FP64
+// weights and FP64 atomics;
 // F_s(face) += exch * f_ex_i N(x_i - x_face) at the old positions, with a
 // warp-segmented pre-sum over lanes that share the stencil's base sample.
 template <typename T>
@@ -282,9 +255,7 @@ __global__ void __launch_bounds__(256) k_p2g(DGrid G, DParams<T> P, int64_t n, c
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   bool valid = i < n;
   double Vi = 0.0;
-  if constexpr (sizeof(T) == 4) {
-    if (valid && alpha) scatter_alpha_fixed(G, cell_new[i], pos_new[i], (unsigned long long*)alpha, Vi);
-  } else if (valid && alpha) {
+  if (valid && alpha) {
     pos_t<T> pn = pos_new[i];
     double r = (double)radius_of(pn);
     Vi = 4.0 / 3.0 * kPi * r * r * r;
@@ -346,6 +317,160 @@ __global__ void __launch_bounds__(256) k_p2g(DGrid G, DParams<T> P, int64_t n, c
   if (sums) {
     double s = block_sum(Vi, s_red);
     if (threadIdx.x == 0) atomicAdd(&sums[1], s);
+  }
+}
+
+// ---- FP32 path scatter ----
+//
+// One thread per granule (Morton order).  alpha_s: the eight 64-bit fixed-
+// point contributions go straight to global integer atomics (exact, order-
+// free); their warp total is added to an integer running sum, so
+// sum_c alpha_s(c) is exact.  F_s: lanes whose stencils share a base sample
+// form runs (Morton order keeps them adjacent); a segmented suffix sum with
+// only as many shuffle steps as the longest run of the warp needs leaves each
+// run's total in its head lane, which alone issues the eight float atomics.
+
+__device__ __forceinline__ float seg_sum_steps(float v, int end, int steps) {
+  int lane = lane_id();
+  int off = 1;
+  for (int s = 0; s < steps; ++s, off <<= 1) {
+    float o = __shfl_down_sync(0xffffffffu, v, off);
+    if (lane + off <= end) v += o;
+  }
+  return v;
+}
+
+// v * 2^e2 rounded to double with integer operations only (the FP64 pipe is
+// the slowest unit of this GPU)
+__device__ __forceinline__ double i64_scaled_to_double(long long v, int e2) {
+  if (v == 0) return 0.0;
+  unsigned long long sign = v < 0 ? (1ull << 63) : 0ull;
+  unsigned long long a = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
+  int msb = 63 - __clzll(a);
+  unsigned long long m;
+  if (msb > 52) {
+    int sh = msb - 52;
+    unsigned long long rem = a & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+    m = a >> sh;
+    if (rem > half || (rem == half && (m & 1ull))) {
+      ++m;
+      if (m == (1ull << 53)) {
+        m >>= 1;
+        ++msb;
+      }
+    }
+  } else {
+    m = a << (52 - msb);
+  }
+  unsigned long long e = (unsigned long long)(msb + e2 + 1023);
+  return __longlong_as_double((long long)(sign | (e << 52) | (m & ((1ull << 52) - 1ull))));
+}
+
+__global__ void __launch_bounds__(256) k_p2g_f32(DGrid G, DParams<float> P, int64_t n,
+                                                 const int32_t* __restrict__ cell_old,
+                                                 const uint4* __restrict__ pos_old,
+                                                 const int32_t* __restrict__ cell_new,
+                                                 const uint4* __restrict__ pos_new, const float4* __restrict__ fex,
+                                                 double* __restrict__ alpha, float* __restrict__ Fs_u,
+                                                 float* __restrict__ Fs_v, float* __restrict__ Fs_w,
+                                                 double* __restrict__ sums) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const bool valid = i < n;
+  long long Si = 0;  // this granule's volume fraction in 2^-53 units
+  long long deposited = 0;
+  if (valid && alpha) {
+    uint4 pn = pos_new[i];
+    int32_t cn = cell_new[i];
+    unsigned long long S = volume_fixed(G, __uint_as_float(pn.w));
+    Si = (long long)S;
+    int c3[3] = {cell_x(cn), cell_y(cn), cell_z(cn)};
+    const int nn[3] = {G.nx, G.ny, G.nz};
+    int i0[3];
+    uint32_t w1[3], w0[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      fixed_axis(G, c3[a], pcomp(pn, a), nn[a], i0[a], w1[a]);
+      w0[a] = kW1 - w1[a];
+    }
+    long long w[8];
+    long long sum7 = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      int a = k & 1, b = (k >> 1) & 1, cz = (k >> 2) & 1;
+      uint32_t wxy = wmul(a ? w1[0] : w0[0], b ? w1[1] : w0[1]);
+      w[k] = (long long)wmul(wxy, cz ? w1[2] : w0[2]);
+      if (k < 7) sum7 += w[k];
+    }
+    w[7] = (long long)kW1 - sum7;  // exact partition of unity
+    unsigned long long* acc = (unsigned long long*)alpha;
+    int64_t base = sample_index(G.nx, G.ny, i0[0], i0[1], i0[2]);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      int a = k & 1, b = (k >> 1) & 1, cz = (k >> 2) & 1;
+      long long v = wscale(S, w[k]);
+      deposited += v;
+      if (v) atomicAdd(&acc[base + a + (int64_t)G.nx * (b + (int64_t)G.ny * cz)], (unsigned long long)v);
+    }
+  }
+  if (Fs_u) {  // uniform over the launch
+    int m[3] = {0, 0, 0};
+    float t[3] = {0.f, 0.f, 0.f};
+    float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (valid) {
+      granule_mac<float>(G, cell_old[i], pos_old[i], m, t);
+      f = fex[i];
+    }
+    float* Fs[3] = {Fs_u, Fs_v, Fs_w};
+    const float fv[3] = {P.exch * f.x, P.exch * f.y, P.exch * f.z};
+#pragma unroll
+    for (int comp = 0; comp < 3; ++comp) {
+      Stencil3<float> S = make_stencil<float>(G, m, t, comp);
+      unsigned key = valid ? (unsigned)base_index(S) : 0xffffffffu - (unsigned)lane_id();
+      int end = run_end(key);
+      bool head = run_head(key);
+      int len = __reduce_max_sync(0xffffffffu, (unsigned)(head ? end - lane_id() + 1 : 1));
+      int steps = 32 - __clz(len - 1);  // ceil(log2(len))
+      float val[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        int a = k & 1, b = (k >> 1) & 1, cz = (k >> 2) & 1;
+        float wgt = (a ? S.w[0] : 1.f - S.w[0]) * (b ? S.w[1] : 1.f - S.w[1]) * (cz ? S.w[2] : 1.f - S.w[2]);
+        val[k] = seg_sum_steps(valid ? wgt * fv[comp] : 0.f, end, steps);
+      }
+      if (valid && head) {
+        int nsx = S.ns[0], nsy = S.ns[1];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          int a = k & 1, b = (k >> 1) & 1, cz = (k >> 2) & 1;
+          atomicAdd(&Fs[comp][sample_index(nsx, nsy, S.i0[0] + a, S.i0[1] + b, S.i0[2] + cz)], val[k]);
+        }
+      }
+    }
+  }
+  if (sums) {  // exact integer warp totals of sum_i V_i / dx^3 and of the deposits
+    long long v = Si, d = deposited;
+    for (int off = 16; off > 0; off >>= 1) {
+      v += __shfl_down_sync(0xffffffffu, v, off);
+      d += __shfl_down_sync(0xffffffffu, d, off);
+    }
+    if (lane_id() == 0) {
+      if (d != 0) atomicAdd((unsigned long long*)&sums[0], (unsigned long long)d);
+      if (v != 0) atomicAdd((unsigned long long*)&sums[1], (unsigned long long)v);
+    }
+  }
+}
+
+// In place: 64-bit fixed-point alpha_s -> double; sums[0] and sums[1] (integer
+// totals of the deposits and of V_i / dx^3) -> sum_c alpha_s dx^3, sum_i V_i.
+__global__ void k_alpha_finish_f32(double* __restrict__ a, int64_t m, double dx3, double* __restrict__ sums) {
+  long long* ai = reinterpret_cast<long long*>(a);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+    a[i] = i64_scaled_to_double(ai[i], -53);
+  if (sums && blockIdx.x == 0 && threadIdx.x == 0) {  // both sums were accumulated as 2^-53 integers
+    long long tot = *reinterpret_cast<long long*>(&sums[0]);
+    long long vol = *reinterpret_cast<long long*>(&sums[1]);
+    sums[0] = i64_scaled_to_double(tot, -53) * dx3;
+    sums[1] = i64_scaled_to_double(vol, -53) * dx3;
   }
 }
 
@@ -506,7 +631,7 @@ extern "C" int gic_p2g(const GicGrid* grid, const GicParams* params, const GicGr
     if (old_->precision == GIC_FP32) {
       DParams<float> P;
       if ((rc = make_params(params, &P))) return rc;
-      k_p2g<float><<<grid_blocks(n, 256), 256, 0, stream>>>(
+      k_p2g_f32<<<grid_blocks(n, 256), 256, 0, stream>>>(
           G, P, n, old_->cell, (const uint4*)old_->pos, new_->cell, (const uint4*)new_->pos, (const float4*)f_ex,
           alpha_s, (float*)Fs_u, (float*)Fs_v, (float*)Fs_w, sums2);
     } else {
@@ -519,8 +644,8 @@ extern "C" int gic_p2g(const GicGrid* grid, const GicParams* params, const GicGr
     ++launches;
   }
   if (alpha_s && old_->precision == GIC_FP32) {
-    // the FP32 path accumulated 64-bit fixed point: convert in place (and sum)
-    k_alpha_finish<<<1184, 256, 0, stream>>>(alpha_s, ncell, G.dx * G.dx * G.dx, sums2);
+    // the FP32 path accumulated 64-bit fixed point: convert in place
+    k_alpha_finish_f32<<<1184, 256, 0, stream>>>(alpha_s, ncell, G.dx * G.dx * G.dx, sums2);
     ++launches;
   } else if (sums2) {
     k_alpha_sum<<<592, 256, 0, stream>>>(alpha_s, ncell, G.dx * G.dx * G.dx, sums2);

@@ -54,6 +54,7 @@ struct DGrid {
   float s2_margin;   // s_hi^2 (1 + 4e-6): contact pre-test threshold factor
   unsigned long long kinv64;  // ceil(2^64 / k) for k > 1 (fixed-point division by k), 0 for k = 1
   double vol_fx;              // (4/3) pi / dx^3 * 2^53: granule volume fraction in 2^-53 units per r^3
+  float vol_fx_hi, vol_fx_lo;  // the same as an unevaluated float pair
 };
 
 template <typename T>

@@ -8,7 +8,7 @@
 // permutation, so there is no separate gather pass.  A final kernel writes the
 // epoch-tagged cell table {start, count, epoch} of the occupied cells.
 //
-// Stability: inside a tile each warp ranks 8 consecutive chunks of 32 keys in
+// Stability: inside a tile each warp ranks 4 consecutive chunks of 32 keys in
 // order, warps own consecutive sub-ranges and tiles are offset by the counts
 // of earlier tiles, so equal keys keep their input order in every pass.
 #include <mutex>
@@ -19,8 +19,8 @@ namespace gic {
 
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
-constexpr int kChunksPerWarp = 8;
-constexpr int kTile = kSortThreads * kChunksPerWarp;  // 2048 keys per CTA
+constexpr int kChunksPerWarp = 4;
+constexpr int kTile = kSortThreads * kChunksPerWarp;  // 1024 keys per CTA
 constexpr int kRadix = 256;
 
 struct SortLayout {
@@ -217,35 +217,39 @@ __global__ void __launch_bounds__(kSortThreads) k_downsweep(int64_t n, int shift
     uint32_t d = digit_of(r_key[c], shift);
     uint32_t pos = s_base[d] + s_warp_hist[warp][d] + r_rank[c];
     keys_out[pos] = r_key[c];
-    if (!kLast) {
+    if (!kLast)
       vals_out[pos] = r_val[c];
-    } else {
-      uint32_t src = r_val[c];
-      S.perm[pos] = (int32_t)src;
-      S.out_cell[pos] = S.in_cell[src];
-      pos_t<T> p = ((const pos_t<T>*)S.in_pos)[src];
-      ((pos_t<T>*)S.out_pos)[pos] = p;
-      if constexpr (sizeof(T) == 4) {
-        if (S.out_posf)
-          S.out_posf[pos] = make_float4((float)p.x * 0x1p-30f, (float)p.y * 0x1p-30f, (float)p.z * 0x1p-30f,
-                                        __uint_as_float(p.w));
-      }
-      ((vec_t<T>*)S.out_vel)[pos] = ((const vec_t<T>*)S.in_vel)[src];
-      if (S.out_id) S.out_id[pos] = S.in_id ? S.in_id[src] : (int32_t)src;
-    }
+    else
+      S.perm[pos] = (int32_t)r_val[c];
   }
 }
 
-// One entry per occupied cell: {start, count, epoch, 0} at 1 + linear index.
-__global__ void k_cell_table(DGrid G, int64_t n, const uint32_t* __restrict__ keys, const int32_t* __restrict__ cell,
-                             uint4* __restrict__ table, uint32_t* status) {
+// Gather the state into sorted order (out[k] = in[perm[k]]: perm is close to
+// the identity because the input is the previous substep's sorted order, so
+// the reads are nearly coalesced) and write the cell table entry
+// {start, count, epoch, 0} of every occupied cell at 1 + its linear index.
+template <typename T>
+__global__ void __launch_bounds__(256) k_permute_table(DGrid G, int64_t n, const uint32_t* __restrict__ keys,
+                                                       const int32_t* __restrict__ perm, ScatterState S,
+                                                       uint4* __restrict__ table, uint32_t* status) {
   int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= n) return;
+  int32_t src = perm[k];
+  int32_t c = S.in_cell[src];
+  pos_t<T> p = ((const pos_t<T>*)S.in_pos)[src];
+  S.out_cell[k] = c;
+  ((pos_t<T>*)S.out_pos)[k] = p;
+  ((vec_t<T>*)S.out_vel)[k] = ((const vec_t<T>*)S.in_vel)[src];
+  if (S.out_id) S.out_id[k] = S.in_id ? S.in_id[src] : src;
+  if constexpr (sizeof(T) == 4) {
+    if (S.out_posf)
+      S.out_posf[k] = make_float4((float)p.x * 0x1p-30f, (float)p.y * 0x1p-30f, (float)p.z * 0x1p-30f,
+                                  __uint_as_float(p.w));
+  }
   uint32_t key = keys[k];
   if (k > 0 && keys[k - 1] == key) return;
   int64_t e = k + 1;
   while (e < n && keys[e] == key) ++e;
-  int32_t c = cell[k];
   int x = cell_x(c), y = cell_y(c), z = cell_z(c);
   if (x >= G.nc[0] || y >= G.nc[1] || z >= G.nc[2]) {
     raise_status(status, GIC_STATUS_BAD_CELL);
@@ -299,7 +303,7 @@ static int launch_sort(const DGrid& G, const GicGranules* in, GicGranules* out, 
     vout = (vout == vals_a) ? vals_b : vals_a;
   }
   // kin now holds the sorted keys
-  k_cell_table<<<grid_blocks(n, 256), 256, 0, st>>>(G, n, kin, out->cell, table, status_word());
+  k_permute_table<T><<<grid_blocks(n, 256), 256, 0, st>>>(G, n, kin, perm, S, table, status_word());
   launches += 1;
   count_launches(launches);
   GIC_CHECK_LAUNCH("gic_sort");
