@@ -50,14 +50,17 @@ def parse():
 # --------------------------------------------------------------------------- distributed plumbing
 
 def dist_setup(args):
+    """One process per GPU (torchrun env).  The ranks run independent replicas
+    of the workload: the only communication is the barrier and the timing
+    reduction (NCCL with GPUs, gloo otherwise)."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if ws > 1:
+        import torch
         import torch.distributed as dist
 
-        backend = "nccl"
-        dist.init_process_group(backend=backend)
+        dist.init_process_group(backend="nccl" if torch.cuda.is_available() else "gloo")
     return ws, rank, local
 
 
@@ -69,6 +72,7 @@ def barrier(ws):
 
 
 def max_over_ranks(x, ws, device="cuda"):
+    """Largest value over the ranks (the slowest rank's time)."""
     if ws == 1:
         return x
     import torch
@@ -77,6 +81,13 @@ def max_over_ranks(x, ws, device="cuda"):
     t = torch.tensor([x], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_throughput(units_per_rank, ms_per_rank, ws, device="cuda"):
+    """Whole-job units per second: all ranks' units over the slowest rank's
+    time (weak scaling of independent replicas)."""
+    ms = max_over_ranks(ms_per_rank, ws, device)
+    return ws * units_per_rank / (ms / 1000.0), ms
 
 
 # --------------------------------------------------------------------------- clocks
@@ -262,8 +273,7 @@ def run_gpu(args, ws, rank, local):
     clk = clocks.stop()
     status = gic.gic_check_status(clear=True)
     ms = statistics.mean(s.elapsed_time(e) for s, e in evs)
-    ms = max_over_ranks(ms, ws, dev)
-    value = ws * n * K / (ms / 1000.0)
+    value, ms = job_throughput(n * K, ms, ws, dev)
 
     # per-entry-point durations inside the timed region -> roofline of the dominant one
     per_call = {k: statistics.mean(a.elapsed_time(b) for a, b in ev_acc[k]) for k in names if ev_acc[k]}

@@ -321,5 +321,29 @@ def gic_check_status(clear: bool = True, timeout_ms: int = 60000, stream=None) -
     return int(f.value)
 
 
+def gic_window_forward_host(grid: GicGrid, params: GicParams, precision: int, cell_xyz, q, r, v, u, vf, wf, p,
+                            alpha_f, K: int, x_out, v_out, alpha_s, Fs, sums2, ws, stream=None):
+    """K substeps on HOST (CPU, ideally pinned) tensors through the C ABI; ws
+    is a device workspace of gic_window_host_workspace_size bytes."""
+    L = lib()
+    f = L.gic_window_forward_host
+    f.argtypes = [_P, _P, C.c_int64, C.c_int32] + [_P] * 9 + [C.c_int32] + [_P] * 8 + [C.c_size_t, _P]
+    f.restype = C.c_int
+    hp = lambda t: None if t is None else C.c_void_p(t.data_ptr())
+    Fs = Fs if Fs is not None else (None, None, None)
+    _check(f(C.byref(grid), C.byref(params), int(r.shape[0]), precision, hp(cell_xyz), hp(q), hp(r), hp(v), hp(u),
+             hp(vf), hp(wf), hp(p), hp(alpha_f), int(K), hp(x_out), hp(v_out), hp(alpha_s), hp(Fs[0]), hp(Fs[1]),
+             hp(Fs[2]), hp(sums2), _ptr(ws), ws.numel() * ws.element_size(), _stream(stream)),
+           "gic_window_forward_host")
+
+
+def gic_window_host_workspace_size(grid: GicGrid, n: int, precision: int) -> int:
+    L = lib()
+    L.gic_window_host_workspace_size.argtypes = [_P, C.c_int64, C.c_int32, _P]
+    b = C.c_size_t(0)
+    _check(L.gic_window_host_workspace_size(C.byref(grid), n, precision, C.byref(b)), "gic_window_host_workspace_size")
+    return int(b.value)
+
+
 def gic_version() -> str:
     return lib().gic_version().decode()

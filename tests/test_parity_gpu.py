@@ -412,3 +412,50 @@ def test_dam_break_full_size_window():
     vref = np.linalg.norm(ref["v"], axis=1).max()
     assert np.linalg.norm(v.cpu().numpy() - ref["v"], axis=1).max() <= 1e-4 * vref
     assert np.abs(sim.alpha_s.cpu().numpy() - ref["alpha_s"]).max() <= 1e-9
+
+
+# ----------------------------------------------------------------------------- public host-buffer window, failures
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_host_window_matches_oracle(prec):
+    """gic_window_forward_host (host buffers in, host buffers out, copies
+    inside) against the oracle's 10-substep window."""
+    prob = shuffled(gi.make("dense_block"))
+    g = gic.make_grid(prob.grid)
+    P = gic.make_params(prob.params)
+    real = np.float32 if prec == FP32 else np.float64
+    host = lambda a, dt=None: torch.from_numpy(np.ascontiguousarray(a if dt is None else a.astype(dt))).pin_memory()
+    nx, ny, nz = prob.grid.nx, prob.grid.ny, prob.grid.nz
+    x = torch.empty((prob.n, 3), dtype=torch.float64).pin_memory()
+    v = torch.empty((prob.n, 3), dtype=torch.float64).pin_memory()
+    a = torch.empty(nx * ny * nz, dtype=torch.float64).pin_memory()
+    tr = torch.float32 if prec == FP32 else torch.float64
+    Fs = [torch.empty(m, dtype=tr).pin_memory() for m in ((nx + 1) * ny * nz, nx * (ny + 1) * nz, nx * ny * (nz + 1))]
+    sums = torch.empty(2, dtype=torch.float64).pin_memory()
+    ws = torch.empty(gic.gic_window_host_workspace_size(g, prob.n, prec), dtype=torch.uint8, device="cuda")
+    gic.gic_window_forward_host(g, P, prec, host(prob.cell), host(prob.q.astype(np.int64), np.int32), host(prob.r),
+                                host(prob.v), *[host(f, real) for f in (prob.u, prob.vf, prob.wf, prob.p, prob.alpha_f)],
+                                prob.K, x, v, a, Fs, sums, ws)
+    ref = oracle.run(prob)
+    dx = prob.grid.dx
+    assert np.abs(x.numpy() - ref["x"]).max() <= (1e-5 if prec == FP32 else 1e-12) * dx
+    vref = np.linalg.norm(ref["v"], axis=1).max()
+    assert np.linalg.norm(v.numpy() - ref["v"], axis=1).max() <= (1e-4 if prec == FP32 else 1e-10) * vref
+    assert np.abs(a.numpy() - ref["alpha_s"]).max() <= 1e-9
+    for c in range(3):
+        assert np.abs(Fs[c].numpy() - ref["Fs"][c]).max() <= 1e-4 * np.abs(ref["Fs"][c]).max()
+    assert abs(sums[0].item() - sums[1].item()) <= 1e-12 * sums[1].item()
+
+
+def test_status_wait_has_a_deadline():
+    """The status query waits for the stream against a deadline: with work
+    still running it returns GIC_ERR_TIMEOUT instead of blocking, and the
+    context stays usable afterwards (no GPU fault is involved)."""
+    prob = gi.make("dense_block", n_side=(10, 10, 10))
+    sim = sim_for(prob, FP32)
+    for _ in range(200):
+        sim.substep()
+    with pytest.raises(gic.GicError, match="still busy"):
+        gic.gic_check_status(clear=False, timeout_ms=1)
+    torch.cuda.synchronize()
+    assert gic.gic_check_status(timeout_ms=5000) == 0
