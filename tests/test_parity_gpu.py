@@ -451,9 +451,10 @@ def test_status_wait_has_a_deadline():
     """The status query waits for the stream against a deadline: with work
     still running it returns GIC_ERR_TIMEOUT instead of blocking, and the
     context stays usable afterwards (no GPU fault is involved)."""
-    prob = gi.make("dense_block", n_side=(10, 10, 10))
+    prob = gi.make("dam_break_1m")
     sim = sim_for(prob, FP32)
-    for _ in range(200):
+    torch.cuda.synchronize()
+    for _ in range(30):  # ~15 ms of GPU work, enqueued in ~3 ms
         sim.substep()
     with pytest.raises(gic.GicError, match="still busy"):
         gic.gic_check_status(clear=False, timeout_ms=1)
