@@ -28,6 +28,7 @@ contacts.
 from __future__ import annotations
 
 import dataclasses
+import functools
 import math
 from typing import Optional
 
@@ -330,40 +331,47 @@ def uniform_noise_velocity(grid: Grid, gen, amp):
 
 def fourier_velocity(grid: Grid, gen, n_modes, kmax, scale_to, scale_kind="max"):
     """Divergence-free sum of random Fourier modes a_m sin(k_m . x + phi_m),
-    a_m orthogonal to k_m, k_m = 2 pi (integer vector in 1..kmax).
+    a_m orthogonal to k_m, k_m = 2 pi (integer vector in +-{1..kmax}) / L.
 
-    Evaluated separably per mode: sin(A+B+C) expanded into products of 1-D
-    factors. Scaled so that the max (or RMS) speed over the cell centres
-    equals `scale_to`."""
-    L = grid.extent
-    ks = gen.integers(1, kmax + 1, size=(n_modes, 3)) * (2.0 * np.pi) / L
-    ks *= gen.choice([-1.0, 1.0], size=(n_modes, 3))
+    Each component is evaluated on its MAC samples with one inverse FFT (the
+    modes are periodic on the box, the half-cell staggering is a phase
+    shift); scaled so that the max (or RMS) speed over the cell centres
+    equals `scale_to`.  Requires a cubic grid."""
+    import scipy.fft as sfft
+
+    N = grid.nx
+    if not (grid.ny == N and grid.nz == N):
+        raise ValueError("fourier_velocity needs a cubic grid")
+    nvec = gen.integers(1, kmax + 1, size=(n_modes, 3)) * gen.choice([-1, 1], size=(n_modes, 3))
     ph = gen.uniform(0, 2 * np.pi, size=n_modes)
     amps = np.empty((n_modes, 3))
     for m in range(n_modes):
         a = gen.normal(size=3)
-        kh = ks[m] / np.linalg.norm(ks[m])
+        kh = nvec[m] / np.linalg.norm(nvec[m])
         a -= a.dot(kh) * kh
         amps[m] = a / np.linalg.norm(a)
 
-    def evaluate(axes, comp):
-        out = np.zeros((axes[0].size, axes[1].size, axes[2].size), dtype=np.float64)
+    def evaluate(comp, shift):
+        # samples at (i + shift_a) dx; field = Im(sum_m c_m exp(2 pi i n_m . x / L))
+        Y = np.zeros((N, N, N), dtype=np.complex128)
         for m in range(n_modes):
-            A = ks[m, 0] * axes[0] + ph[m]
-            B = ks[m, 1] * axes[1]
-            C = ks[m, 2] * axes[2]
-            sA, cA, sB, cB, sC, cC = np.sin(A), np.cos(A), np.sin(B), np.cos(B), np.sin(C), np.cos(C)
-            term = (np.einsum("i,j,k->ijk", sA, cB, cC) + np.einsum("i,j,k->ijk", cA, sB, cC)
-                    + np.einsum("i,j,k->ijk", cA, cB, sC) - np.einsum("i,j,k->ijk", sA, sB, sC))
-            out += amps[m, comp] * term
-        return out
+            c = amps[m, comp] * np.exp(1j * ph[m]) * np.exp(2j * np.pi * np.dot(nvec[m], shift) / N)
+            Y[tuple(int(v) % N for v in nvec[m])] += c * N ** 3
+        X = sfft.ifftn(Y, workers=-1).imag  # [i, j, k] = x, y, z
+        return X
 
-    cc = centre_coords(grid)
-    speed2 = sum(evaluate(cc, c) ** 2 for c in range(3))
-    s = scale_to / (np.sqrt(speed2.max()) if scale_kind == "max" else np.sqrt(speed2.mean()))
-    u = _flat(evaluate(face_coords(grid, 0), 0) * s)
-    vf = _flat(evaluate(face_coords(grid, 1), 1) * s)
-    wf = _flat(evaluate(face_coords(grid, 2), 2) * s)
+    centre = np.array([0.5, 0.5, 0.5])
+    speed2 = sum(evaluate(c, centre) ** 2 for c in range(3))
+    s_ = scale_to / (np.sqrt(speed2.max()) if scale_kind == "max" else np.sqrt(speed2.mean()))
+    out = []
+    for comp in range(3):
+        shift = centre.copy()
+        shift[comp] = 0.0
+        X = evaluate(comp, shift) * s_
+        # the face axis has N + 1 samples; the last equals the first (periodic modes)
+        X = np.concatenate([X, np.take(X, [0], axis=comp)], axis=comp)
+        out.append(_flat(X))
+    u, vf, wf = out
     return zero_wall_normal(u, vf, wf, grid)
 
 
@@ -553,6 +561,190 @@ def random_cloud(seed=21, n=2000, r0=0.004, grid_n=16, fluid_amp=0.2, K=10, dt=1
     return _finish("random_cloud", grid, params, K, x, r, v, u, vf, wf, p, af)
 
 
+def _fcc_neighbour_table():
+    """For each FCC basis atom b and each of the 12 nearest-neighbour vectors:
+    (cell offset, neighbour basis index), in units of the cubic cell."""
+    basis = np.array([[0, 0, 0], [0.5, 0.5, 0], [0.5, 0, 0.5], [0, 0.5, 0.5]])
+    dirs = []
+    for a in range(3):
+        for b in range(a + 1, 3):
+            for sa in (-0.5, 0.5):
+                for sb in (-0.5, 0.5):
+                    d = np.zeros(3)
+                    d[a], d[b] = sa, sb
+                    dirs.append(d)
+    table = np.zeros((4, 12, 4), dtype=np.int64)
+    for bi in range(4):
+        for k, d in enumerate(dirs):
+            q = basis[bi] + d
+            cell = np.floor(q + 1e-9).astype(np.int64)
+            frac = q - cell
+            bj = int(np.argmin(np.abs(basis - frac).sum(1)))
+            table[bi, k, :3] = cell
+            table[bi, k, 3] = bj
+    return basis, table
+
+
+def _periodic_pairs(pos, reach, L):
+    """Index pairs (i < j) closer than `reach` with x, y periodic of period
+    L[0], L[1] (z open), and their minimum-image separations."""
+    from scipy.spatial import cKDTree
+
+    p = pos.copy()
+    p[:, 0] %= L[0]
+    p[:, 1] %= L[1]
+    z0 = p[:, 2].min()
+    p[:, 2] -= z0
+    tree = cKDTree(p, boxsize=[L[0], L[1], 2.0 * (p[:, 2].max() + reach) + 1.0])
+    P = tree.query_pairs(reach, output_type="ndarray")
+    I, J = P[:, 0], P[:, 1]
+    d = pos[I] - pos[J]
+    d[:, 0] -= np.round(d[:, 0] / L[0]) * L[0]
+    d[:, 1] -= np.round(d[:, 1] / L[1]) * L[1]
+    return I, J, d
+
+
+def _settle_tile(pos, rr, L, iters, push, skin, relax, tol):
+    """Settle a periodic tile: `iters` rounds of averaged Jacobi overlap
+    removal (each overlapping pair split by inverse volume, a granule moves by
+    1.5 x the mean of its corrections), each round after a downward shift of
+    `push` (decreasing to zero), with the floor at z = r; then up to `relax`
+    rounds without the push, until no overlap exceeds `tol`.  Neighbour pairs
+    are re-found whenever a granule has moved 0.4 `skin` since the last
+    search."""
+    m = len(rr)
+    w = 1.0 / rr ** 3
+    ref = None
+    for it in range(iters + relax):
+        if ref is None or np.abs(pos - ref).max() > 0.4 * skin:
+            I, J, _ = _periodic_pairs(pos, 2 * rr.max() + skin, L)
+            ref = pos.copy()
+        d = pos[I] - pos[J]
+        d[:, 0] -= np.round(d[:, 0] / L[0]) * L[0]
+        d[:, 1] -= np.round(d[:, 1] / L[1]) * L[1]
+        dist = np.linalg.norm(d, axis=1)
+        ov = rr[I] + rr[J] - dist
+        k = ov > 0
+        if it >= iters and not (ov > tol).any():
+            break
+        Ik, Jk = I[k], J[k]
+        nrm = d[k] / dist[k][:, None] * ov[k][:, None]
+        fi = (w[Ik] / (w[Ik] + w[Jk]))[:, None]
+        disp = np.zeros_like(pos)
+        cnt = np.zeros(m)
+        np.add.at(disp, Ik, nrm * fi)
+        np.add.at(disp, Jk, -nrm * (1 - fi))
+        np.add.at(cnt, Ik, 1)
+        np.add.at(cnt, Jk, 1)
+        pos += 1.5 * disp / np.maximum(cnt, 1)[:, None]
+        if it < iters:
+            pos[:, 2] -= push * (1 - it / iters)
+        pos[:, 2] = np.maximum(pos[:, 2], rr)
+    return pos
+
+
+@functools.lru_cache(maxsize=2)
+def _bed_tile(seed, tile_cells, iters, relax):
+    """The settled periodic tile of the polydisperse bed: positions, radii,
+    periods and (neighbours, contacts, packing fraction, height)."""
+    med = 8e-4
+    gen = rng(seed, STREAM_POS)
+    a = 2.35 * med * math.sqrt(2.0)
+    cx, cy, cz = tile_cells
+    basis, _ = _fcc_neighbour_table()
+    ii, jj, kk, bb = np.meshgrid(np.arange(cx), np.arange(cy), np.arange(cz), np.arange(4), indexing="ij")
+    m = ii.size
+    pos = (np.stack([ii.ravel(), jj.ravel(), kk.ravel()], 1) + basis[bb.ravel()]) * a
+    pos[:, 2] += med
+    pos += gen.uniform(-0.02 * med, 0.02 * med, size=pos.shape)
+    rr = np.clip(med * np.exp(0.25 * rng(seed, STREAM_RAD).normal(size=m)), 0.5 * med, 2.0 * med)
+    L = (cx * a, cy * a)
+    tol = 0.01 * rr.min()
+    pos = _settle_tile(pos, rr, L, iters, 0.004 * med, 0.3 * med, relax, tol)
+    for _ in range(50):
+        I, J, d = _periodic_pairs(pos, 2 * rr.max(), L)
+        excess = rr[I] + rr[J] - np.linalg.norm(d, axis=1) - tol
+        bad = excess > 0
+        if not bad.any():
+            break
+        big = np.where(rr[I] >= rr[J], I, J)[bad]
+        shrink = np.zeros(m)
+        np.maximum.at(shrink, big, excess[bad] * (1 + 1e-9) + 1e-12)
+        rr = rr - shrink
+    else:
+        raise RuntimeError("bed overlap capping did not converge")
+    pos[:, 0] %= L[0]
+    pos[:, 1] %= L[1]
+    I, J, d = _periodic_pairs(pos, 2 * rr.max() + 0.02 * med, L)
+    gap = np.linalg.norm(d, axis=1) - rr[I] - rr[J]
+    nbr = 2.0 * np.count_nonzero(gap < 0.02 * med) / m
+    con = 2.0 * np.count_nonzero(gap < 0) / m
+    height = pos[:, 2].max() + med
+    phi = (4.0 / 3.0 * np.pi * rr ** 3).sum() / (L[0] * L[1] * height)
+    return pos, rr, L, (nbr, con, phi, height)
+
+
+def polydisperse_bed(seed=3, n=8_000_000, tile_cells=(12, 12, 15), iters=300, relax=1500):
+    """8,000,000 granules with lognormal radii (median 8e-4, sigma_log 0.25,
+    clipped to [0.5, 2] x median) in a settled-bed layout on a 256^3 grid,
+    under the shear flow u_x = 0.8 z; 50 substeps of 1e-5.
+
+    Layout: a tile periodic in x and y, started as an FCC lattice whose
+    nearest-neighbour spacing (2.35 x median, jitter 0.02 x median) holds the
+    lognormal volumes at a packing fraction near 0.6, settled by `iters`
+    rounds of overlap removal under a decreasing downward push and up to
+    `relax` more without it; where a pair still overlaps by more than 1% of
+    the smallest radius, the larger granule is shrunk by the excess.  Copies of the tile placed side by side over the
+    floor meet with the same neighbour structure; the bed is those copies
+    until n granules.  The tile's neighbour statistics (neighbours within
+    r_i + r_j + 0.02 x median, contacts, packing fraction) go in `note`."""
+    med = 8e-4
+    dx = 1.0 / 256
+    grid = Grid(256, 256, 256, dx, k_contact=contact_k(dx, 2 * med))
+    pos, rr, L, (nbr, con, phi, height) = _bed_tile(seed, tuple(tile_cells), iters, relax)
+    m = len(rr)
+    # replicate the tile over the floor
+    nx_t, ny_t = int(np.floor((1.0 - 4 * med) / L[0])), int(np.floor((1.0 - 4 * med) / L[1]))
+    reps = int(math.ceil(n / m))
+    if reps > nx_t * ny_t:
+        raise ValueError("bed tile does not fit the box floor")
+    off = np.array([(2 * med + ix * L[0], 2 * med + iy * L[1], 0.0) for iy in range(ny_t) for ix in range(nx_t)][:reps])
+    x = (pos[None, :, :] + off[:, None, :]).reshape(-1, 3)[:n]
+    r = np.tile(rr, reps)[:n].astype(np.float32)
+    v = np.zeros((n, 3), np.float32)
+    u, vf, wf = shear_velocity(grid, 0.8)
+    params = Params(dt_sub=1e-5, dt_fluid=50 * 1e-5)
+    p = hydrostatic_pressure(grid, params.rho_f)
+    af = box_fluid_fraction(grid, x.min(0) - med, x.max(0) + med, 0.6)
+    prob = _finish("polydisperse_bed_8m", grid, params, 50, x, r, v, u, vf, wf, p, af)
+    prob.note = (f"tile of {m} granules, {reps} copies; radii {r.min() / med:.2f}-{r.max() / med:.2f} x median; "
+                 f"{nbr:.2f} neighbours and {con:.2f} contacts per granule; packing {phi:.3f}, height {height:.4f}")
+    return prob
+
+
+def scale_sweep(seed=5, n=16_000_000, grid_n=384):
+    """16,000,000 granules (r = 6e-4) on an FCC lattice at volume fraction 0.6
+    (nearest neighbour 2.145 r, jitter 0.05 r) as a full-footprint slab from
+    the floor (height about 0.024) on a 384^3 grid; 32 divergence-free Fourier
+    modes (k in 2 pi {1..8}^3) scaled to an RMS speed of 1 m/s; 20 substeps of
+    1e-5.  The jitter leaves a few small initial overlaps."""
+    r0 = 6e-4
+    dx = 1.0 / grid_n
+    grid = Grid(grid_n, grid_n, grid_n, dx, k_contact=contact_k(dx, r0))
+    lo = np.array([1.1 * r0, 1.1 * r0, 1.1 * r0])
+    hi = np.array([1.0 - 1.1 * r0, 1.0 - 1.1 * r0, 0.5])
+    x = fcc_fill(lo, hi, 2.145 * r0, n)
+    gen = rng(seed, STREAM_POS)
+    x = x + gen.uniform(-0.05 * r0, 0.05 * r0, size=x.shape)
+    r = np.full(n, r0, np.float32)
+    v = np.zeros((n, 3), np.float32)
+    u, vf, wf = fourier_velocity(grid, rng(seed, STREAM_FLUID), 32, 8, 1.0, "rms")
+    params = Params(dt_sub=1e-5, dt_fluid=20 * 1e-5)
+    p = hydrostatic_pressure(grid, params.rho_f)
+    af = box_fluid_fraction(grid, x.min(0) - r0, x.max(0) + r0, 0.6)
+    return _finish("scale_sweep_16m", grid, params, 20, x, r, v, u, vf, wf, p, af)
+
+
 def make(name: str, **kw) -> Problem:
     table = {
         "plain_fp64_8k": plain_fp64,
@@ -560,5 +752,7 @@ def make(name: str, **kw) -> Problem:
         "diff_window_100k": differentiable_window,
         "dense_block": dense_block,
         "random_cloud": random_cloud,
+        "polydisperse_bed_8m": polydisperse_bed,
+        "scale_sweep_16m": scale_sweep,
     }
     return table[name](**kw)
