@@ -297,11 +297,18 @@ def run_gpu(args, ws, rank, local):
 
     variants = {}
     if not args.no_variants:
-        variants["fp64_fwd"] = run_fp64(prob, gic, torch, dev, stream)
+        variants["fp64_fwd"] = run_fwd(prob, gic.GIC_FP64, gic, torch, dev, stream)
         for prec_name, prec in (("fp32", gic.GIC_FP32), ("fp64", gic.GIC_FP64)):
             variants[f"{prec_name}_adjoint_dam_break"] = run_adjoint(prob, prec, torch, dev)
             wprob = gi.make("diff_window_100k")
             variants[f"{prec_name}_adjoint_diff_window"] = run_adjoint(wprob, prec, torch, dev)
+        del sim, init, flush
+        torch.cuda.empty_cache()
+        for wname in ("polydisperse_bed_8m", "scale_sweep_16m"):
+            wp = gi.make(wname)
+            for prec_name, prec in (("fp32", gic.GIC_FP32), ("fp64", gic.GIC_FP64)):
+                variants[f"{prec_name}_fwd_{wname}"] = run_fwd(wp, prec, gic, torch, dev, stream)
+            del wp
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -405,31 +412,56 @@ def run_adjoint(prob, prec, torch, dev, ckpt=10):
             "dtype": "f32" if prec == 0 else "f64"}
 
 
-def run_fp64(prob, gic, torch, dev, stream, steps=1):
-    """The same workload on the all-FP64 GPU path (FP64 state and arithmetic)."""
+def run_fwd(prob, prec, gic, torch, dev, stream, steps=2, warmup=1):
+    """The forward window of a workload on one precision path, `warmup`
+    untimed and `steps` timed windows, each from the initial packing after a
+    512 MB L2 flush; per-entry-point mean durations from events around each
+    call."""
     from paper_2504_00745_gb300.window import Simulator
 
-    sim = Simulator.from_problem(prob, gic.GIC_FP64, dev)
+    sim = Simulator.from_problem(prob, prec, dev)
     init = sim.A.clone()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     K = prob.K
     res = []
-    for it in range(steps + 1):
+    ev_acc = {k: [] for k in ALGO_BYTES}
+    gic.gic_check_status(clear=True)
+    for it in range(warmup + steps):
         sim.A.cell.copy_(init.cell)
         sim.A.pos.copy_(init.pos)
         sim.A.vel.copy_(init.vel)
         sim.A.id.copy_(init.id)
+        flush.zero_()
         s = torch.cuda.Event(enable_timing=True)
         e = torch.cuda.Event(enable_timing=True)
         s.record(stream)
         sim.zero_transfer()
         for _ in range(K):
-            sim.substep()
+            if it >= warmup:
+                sim.substep_probe(ev_acc, stream=stream)
+            else:
+                sim.substep()
         e.record(stream)
         torch.cuda.synchronize()
-        if it > 0:
+        if it >= warmup:
             res.append(s.elapsed_time(e))
+        elif gic.gic_check_status(clear=False):
+            # granules left the domain or crossed cells too fast: the timing
+            # would not be of this workload
+            out = {"skipped": f"device status {gic.gic_check_status(clear=True)} after the warm-up window",
+                   "workload": prob.name, "dtype": "f32" if prec == 0 else "f64"}
+            del sim, init, flush
+            torch.cuda.empty_cache()
+            return out
+    status = gic.gic_check_status(clear=True)
     ms = statistics.mean(res)
-    return {"value": prob.n * K / (ms / 1000), "unit": UNIT, "ms_per_step": ms, "dtype": "f64", "steps": steps}
+    per_call = {k: statistics.mean(a.elapsed_time(b) for a, b in v) for k, v in ev_acc.items() if v}
+    out = {"value": prob.n * K / (ms / 1000), "unit": UNIT, "ms_per_step": ms, "dtype": "f32" if prec == 0 else "f64",
+           "workload": prob.name, "granules": prob.n, "substeps": K, "steps": steps, "per_call_ms": per_call,
+           "device_status": status}
+    del sim, init, flush
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_profile(args):

@@ -216,30 +216,54 @@ static void wall_forces(const or_grid* G, const or_params* P, const double* x, c
   }
 }
 
-/* uniform bins of width >= 2 r_max for the oracle's own neighbour search */
+/* uniform bins of width >= 2 r_max over the granules' bounding box, for the
+ * oracle's own neighbour search (granules outside the box, or NaN, clamp to
+ * an edge bin: still correct, only slower) */
 typedef struct {
   int nb[3];
-  double hb, lo[3];
+  double w[3], lo[3];
   int64_t *head, *next; /* linked lists, ascending index within a bin */
 } or_bins;
+
+static void bin_of(const or_bins* B, const double* xi, int bi[3]) {
+  for (int a = 0; a < 3; ++a) {
+    double f = floor((xi[a] - B->lo[a]) / B->w[a]);
+    bi[a] = !(f >= 0.0) ? 0 : (f >= B->nb[a] - 1 ? B->nb[a] - 1 : (int)f); /* NaN -> bin 0 */
+  }
+}
 
 static void bins_build(or_bins* B, const or_grid* G, int64_t n, const double* x, const double* r) {
   double rmax = 0;
   for (int64_t i = 0; i < n; ++i) rmax = r[i] > rmax ? r[i] : rmax;
-  double L[3] = {G->nx * G->dx, G->ny * G->dx, G->nz * G->dx};
-  B->lo[0] = G->ox;
-  B->lo[1] = G->oy;
-  B->lo[2] = G->oz;
-  B->hb = 2.0 * rmax;
-  if (B->hb <= 0) B->hb = G->dx;
+  double hb = 2.0 * rmax;
+  if (!(hb > 0)) hb = G->dx;
+  double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (int64_t i = 0; i < n; ++i)
+    for (int a = 0; a < 3; ++a) {
+      double t = x[3 * i + a];
+      if (t < lo[a]) lo[a] = t; /* false for NaN */
+      if (t > hi[a]) hi[a] = t;
+    }
   int64_t tot = 1;
   for (int a = 0; a < 3; ++a) {
-    B->nb[a] = (int)floor(L[a] / B->hb); /* bin width L / nb >= 2 r_max */
-    if (B->nb[a] < 1) B->nb[a] = 1;
-    if (B->nb[a] > 2048) { /* coarse bins are still correct, only slower */
-      B->nb[a] = 2048;
+    if (!(hi[a] >= lo[a]) || !isfinite(hi[a] - lo[a])) { /* no finite coordinate */
+      lo[a] = 0.0;
+      hi[a] = 0.0;
     }
+    double ext = hi[a] - lo[a];
+    B->nb[a] = ext > hb ? (int)fmin(floor(ext / hb), 2048.0) : 1; /* bin width ext / nb >= 2 r_max */
     tot *= B->nb[a];
+  }
+  while (tot > 16 * n + 4096) { /* sparse clouds: coarser bins, still >= 2 r_max */
+    tot = 1;
+    for (int a = 0; a < 3; ++a) {
+      B->nb[a] = B->nb[a] > 1 ? B->nb[a] / 2 : 1;
+      tot *= B->nb[a];
+    }
+  }
+  for (int a = 0; a < 3; ++a) {
+    B->lo[a] = lo[a];
+    B->w[a] = B->nb[a] > 1 ? (hi[a] - lo[a]) / B->nb[a] : INFINITY;
   }
   B->head = (int64_t*)malloc(sizeof(int64_t) * (size_t)tot);
   B->next = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
@@ -247,11 +271,7 @@ static void bins_build(or_bins* B, const or_grid* G, int64_t n, const double* x,
   /* insert in descending order so each list is ascending */
   for (int64_t i = n - 1; i >= 0; --i) {
     int bi[3];
-    for (int a = 0; a < 3; ++a) {
-      double w = L[a] / B->nb[a];
-      double f = floor((x[3 * i + a] - B->lo[a]) / w);
-      bi[a] = !(f >= 0.0) ? 0 : (f >= B->nb[a] - 1 ? B->nb[a] - 1 : (int)f); /* NaN -> bin 0 */
-    }
+    bin_of(B, x + 3 * i, bi);
     int64_t lin = bi[0] + (int64_t)B->nb[0] * (bi[1] + (int64_t)B->nb[1] * bi[2]);
     B->next[i] = B->head[lin];
     B->head[lin] = i;
@@ -261,15 +281,6 @@ static void bins_build(or_bins* B, const or_grid* G, int64_t n, const double* x,
 static void bins_free(or_bins* B) {
   free(B->head);
   free(B->next);
-}
-
-static void bin_of(const or_bins* B, const or_grid* G, const double* xi, int bi[3]) {
-  double L[3] = {G->nx * G->dx, G->ny * G->dx, G->nz * G->dx};
-  for (int a = 0; a < 3; ++a) {
-    double w = L[a] / B->nb[a];
-    double f = floor((xi[a] - B->lo[a]) / w);
-    bi[a] = !(f >= 0.0) ? 0 : (f >= B->nb[a] - 1 ? B->nb[a] - 1 : (int)f); /* NaN -> bin 0 */
-  }
 }
 
 /* Enumerate the contact pairs i < j (d_ij < r_i + r_j).  brute != 0: O(N^2)
@@ -301,7 +312,7 @@ int64_t or_contact_pairs(const or_grid* G, int64_t n, const double* x, const dou
   bins_build(&B, G, n, x, r);
   for (int64_t i = 0; i < n; ++i) {
     int bi[3];
-    bin_of(&B, G, x + 3 * i, bi);
+    bin_of(&B, x + 3 * i, bi);
     for (int dz = -1; dz <= 1; ++dz)
       for (int dy = -1; dy <= 1; ++dy)
         for (int dx = -1; dx <= 1; ++dx) {
@@ -356,7 +367,7 @@ void or_contact(const or_grid* G, const or_params* P, int64_t n, const double* x
       }
     } else {
       int bi[3];
-      bin_of(&B, G, xi, bi);
+      bin_of(&B, xi, bi);
       for (int dz = -1; dz <= 1; ++dz)
         for (int dy = -1; dy <= 1; ++dy)
           for (int dx = -1; dx <= 1; ++dx) {
@@ -758,7 +769,7 @@ void or_contact_adj(const or_grid* G, const or_params* P, int64_t n, const doubl
       for (int64_t j = 0; j < n; ++j) cand[nc++] = j;
     } else {
       int bi[3];
-      bin_of(&B, G, x + 3 * i, bi);
+      bin_of(&B, x + 3 * i, bi);
       int64_t cap = 64;
       cand = (int64_t*)malloc(sizeof(int64_t) * (size_t)cap);
       for (int dz = -1; dz <= 1; ++dz)

@@ -169,12 +169,13 @@ __global__ void k_alpha_sum(const double* __restrict__ a, int64_t m, double dx3,
 // ---- FP32 path: exact fixed-point volume fraction ----
 //
 // alpha_s is accumulated as a 64-bit integer in units of 2^-53: per granule
-// the volume fraction S = V / dx^3 is rounded once to 2^-53, the tent weights
-// come from the 30-bit fixed-point position as 31-bit integers (the eighth
-// corner takes the remainder, so every granule deposits exactly S up to the
-// final truncations), and integer atomics make the sum independent of the
-// order of arrival -- bitwise reproducible.  k_alpha_finish turns the
-// integers into doubles in place.
+// the volume fraction S = V / dx^3 is rounded once to 2^-53; the per-axis
+// tent weights come from the 30-bit fixed-point position as 31-bit integers
+// (exact when the contact cell is the MAC cell), their product is kept to
+// 2^-62, each corner's deposit S w is truncated to 2^-53 and the eighth
+// corner takes the rest, so every granule deposits exactly S; integer atomics
+// make the sum independent of the order of arrival -- bitwise reproducible.
+// k_alpha_finish turns the integers into doubles in place.
 
 constexpr uint32_t kW1 = 1u << 31;  // weight 1.0
 constexpr double kAlphaUnit = 1.0 / 9007199254740992.0;  // 2^-53
@@ -230,14 +231,19 @@ __device__ __forceinline__ unsigned long long volume_fixed(const DGrid& G, float
   return (unsigned long long)(a + __float2ll_rn(sl));
 }
 
-__device__ __forceinline__ uint32_t wmul(uint32_t a, uint32_t b) {
-  return (uint32_t)(((unsigned long long)a * b + (1ull << 30)) >> 31);
+// w_xy w_z in 2^-62 units, rounded: w_xy = w_x w_y exactly (<= 2^62, 2^-62
+// units), w_z <= 2^31 in 2^-31 units; (hi:lo) >> 31 of the 93-bit product.
+__device__ __forceinline__ unsigned long long w3_62(unsigned long long wxy, uint32_t wz) {
+  unsigned long long lo = wxy * (unsigned long long)wz;
+  unsigned long long hi = __umul64hi(wxy, (unsigned long long)wz);
+  return ((hi << 33) | (lo >> 31)) + ((lo >> 30) & 1ull);
 }
 
-// (S * w) >> 31 for S < 2^54, |w| <= 2^31 (w may be slightly negative for the remainder corner)
-__device__ __forceinline__ long long wscale(unsigned long long S, long long w) {
-  if (w >= 0) return (long long)__umul64hi(S << 1, (unsigned long long)w << 32);
-  return -(long long)__umul64hi(S << 1, (unsigned long long)(-w) << 32);
+// floor(S w / 2^62) for S < 2^54, w <= 2^62
+__device__ __forceinline__ long long scale62(unsigned long long S, unsigned long long w) {
+  unsigned long long lo = S * w;
+  unsigned long long hi = __umul64hi(S, w);
+  return (long long)((hi << 2) | (lo >> 62));
 }
 
 // FP64 path: alpha_s(c) = sum_i V_i N(x'_i - x_c) / dx^3 at the new positions, FP64
@@ -392,24 +398,28 @@ __global__ void __launch_bounds__(256) k_p2g_f32(DGrid G, DParams<float> P, int6
       fixed_axis(G, c3[a], pcomp(pn, a), nn[a], i0[a], w1[a]);
       w0[a] = kW1 - w1[a];
     }
-    long long w[8];
+    // the 3-D tent weight to 2^-62, the deposit S w truncated to 2^-53; the
+    // eighth corner takes S minus the other seven, so the granule deposits
+    // exactly S
+    unsigned long long wxy[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      wxy[k] = (unsigned long long)((k & 1) ? w1[0] : w0[0]) * (unsigned long long)((k & 2) ? w1[1] : w0[1]);
+    long long v[8];
     long long sum7 = 0;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      int a = k & 1, b = (k >> 1) & 1, cz = (k >> 2) & 1;
-      uint32_t wxy = wmul(a ? w1[0] : w0[0], b ? w1[1] : w0[1]);
-      w[k] = (long long)wmul(wxy, cz ? w1[2] : w0[2]);
-      if (k < 7) sum7 += w[k];
+    for (int k = 0; k < 7; ++k) {
+      v[k] = scale62(S, w3_62(wxy[k & 3], (k & 4) ? w1[2] : w0[2]));
+      sum7 += v[k];
     }
-    w[7] = (long long)kW1 - sum7;  // exact partition of unity
+    v[7] = (long long)S - sum7;
+    deposited = (long long)S;
     unsigned long long* acc = (unsigned long long*)alpha;
     int64_t base = sample_index(G.nx, G.ny, i0[0], i0[1], i0[2]);
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
       int a = k & 1, b = (k >> 1) & 1, cz = (k >> 2) & 1;
-      long long v = wscale(S, w[k]);
-      deposited += v;
-      if (v) atomicAdd(&acc[base + a + (int64_t)G.nx * (b + (int64_t)G.ny * cz)], (unsigned long long)v);
+      if (v[k]) atomicAdd(&acc[base + a + (int64_t)G.nx * (b + (int64_t)G.ny * cz)], (unsigned long long)v[k]);
     }
   }
   if (Fs_u) {  // uniform over the launch

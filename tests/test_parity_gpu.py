@@ -8,6 +8,8 @@ the arithmetic where it states none):
     (v_ref = largest oracle speed), alpha_s <= 1e-9 absolute;
   * single kernels: see each test.
 """
+import dataclasses
+
 import numpy as np
 import pytest
 import torch
@@ -412,6 +414,156 @@ def test_dam_break_full_size_window():
     vref = np.linalg.norm(ref["v"], axis=1).max()
     assert np.linalg.norm(v.cpu().numpy() - ref["v"], axis=1).max() <= 1e-4 * vref
     assert np.abs(sim.alpha_s.cpu().numpy() - ref["alpha_s"]).max() <= 1e-9
+
+
+def _sub_box(prob, x, n_target, halo):
+    """A box over the full bed height, centred in x, y, holding about
+    n_target granules: (granules within the box grown by `halo`, granules in
+    the box itself, box low corner, box high corner)."""
+    lo_all, hi_all = x.min(0), x.max(0)
+    area = (hi_all[0] - lo_all[0]) * (hi_all[1] - lo_all[1])
+    w = np.sqrt(area * n_target / prob.n)
+    c = 0.5 * (lo_all[:2] + hi_all[:2])
+    lo = np.array([c[0] - w / 2, c[1] - w / 2, -1.0])
+    hi = np.array([c[0] + w / 2, c[1] + w / 2, 2.0])
+    inside = lambda pad: np.all((x >= lo - pad) & (x < hi + pad), axis=1)
+    return np.nonzero(inside(halo))[0], np.nonzero(inside(0.0))[0], lo, hi
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name", ["polydisperse_bed_8m", "scale_sweep_16m"])
+@pytest.mark.parametrize("prec", PRECS)
+def test_full_size_sampled_one_substep(name, prec):
+    """8M granules on 256^3 (lognormal radii) and 16M on 384^3: one substep
+    in the benchmark's launch configuration.  The permutation is compared in
+    full (bit-exact) and the cell table on every occupied cell; contact, G2P,
+    alpha_s and F_s on a 100k-granule box, against the oracle run on the box
+    grown by a halo: a granule's force depends only on granules within
+    2 r_max, and a cell's alpha_s and F_s only on granules within
+    r_max + 2 dx of it, so the box's interior is exact."""
+    prob = gi.make(name)
+    sim = sim_for(prob, prec)
+    gic.gic_sort(sim.grid, sim.A, sim.B, sim.perm, sim.table, sim.ws)
+    gic.gic_contact(sim.grid, sim.params, sim.B, sim.table, sim.F_c)
+    F = sim.fluid
+    gic.gic_g2p_couple(sim.grid, sim.params, sim.B, F.u, F.v, F.w, F.p, F.alpha_f, sim.F_fl, sim.a_f, sim.alpha_f_p)
+    torch.cuda.synchronize()
+    assert gic.gic_check_status() == 0
+    perm_o, keys_o = oracle.sort(prob.cell)
+    assert np.array_equal(sim.perm.cpu().numpy(), perm_o)
+    ck, st, ct = oracle.cell_table(keys_o)
+    tab = sim.table.view(-1, 4)
+    epoch = int(tab[0, 0].item())
+    nc = prob.grid.nc
+    cs = prob.cell[perm_o[st]].astype(np.int64)
+    lin = torch.from_numpy(1 + cs[:, 0] + nc[0] * (cs[:, 1] + nc[1] * cs[:, 2])).cuda()
+    rows = tab[lin].cpu().numpy().astype(np.int64)
+    assert np.array_equal(rows[:, 0], st) and np.array_equal(rows[:, 1], ct) and np.all(rows[:, 2] == epoch)
+    assert int((tab[1:, 2] == epoch).sum().item()) == len(ck)
+
+    x, v, r = oracle_inputs(prob)
+    r_max = float(r.max())
+    dx = prob.grid.dx
+    halo = 2 * r_max + 2 * dx
+    box, core, lo, hi = _sub_box(prob, x, 100_000, halo)
+    assert len(core) > 50_000
+    Fo, _ = oracle.contact(prob.grid, prob.params, x[box], v[box], r[box])
+    in_core = np.isin(box, core)
+    Fg = by_id(sim.F_c, sim.B.id)[:, :3][box]
+    err = np.abs(Fg - Fo)[in_core].max()
+    scale = np.abs(Fo[in_core]).max()
+    assert err <= (tol_force(prob, FP32) + 1e-5 * scale if prec == FP32 else 1e-9 * scale)  # 0 when no contacts
+    Ffl_o, af_o, afp_o = oracle.g2p(prob.grid, prob.params, x[box], v[box], r[box], prob.u, prob.vf, prob.wf, prob.p,
+                                    prob.alpha_f)
+    rel = 2e-6 if prec == FP32 else 1e-12
+    Ffl = by_id(sim.F_fl, sim.B.id)[:, :3][box]
+    assert np.abs(Ffl - Ffl_o).max() <= rel * np.abs(Ffl_o).max()
+    af = by_id(sim.a_f, sim.B.id)[:, :3][box]
+    assert np.abs(af - af_o).max() <= rel * 9.8
+
+    gic.gic_integrate(sim.grid, sim.params, sim.B, sim.F_c, sim.F_fl, sim.a_f, sim.A, sim.f_ex)
+    sim.zero_transfer()
+    gic.gic_p2g(sim.grid, sim.params, sim.B, sim.A, sim.f_ex, sim.alpha_s, sim.Fs, sim.sums)
+    torch.cuda.synchronize()
+    xb, _ = sim.positions(sim.B)
+    xa, _ = sim.positions(sim.A)
+    xb = xb.cpu().numpy()[box]
+    xa = xa.cpu().numpy()[box]
+    fex = by_id(sim.f_ex, sim.A.id)[:, :3].astype(np.float64)[box]
+    a_o, Fs_o, _ = oracle.p2g(prob.grid, prob.params, xb, xa, r[box], fex)
+    g = prob.grid
+    pad = r_max + 3 * dx
+
+    org = np.asarray(g.origin, dtype=np.float64)
+
+    def interior(sx, sy, sz, off):
+        # grids are stored x fastest: index = i + sx (j + sy k)
+        cx = org[0] + (np.arange(sx) + off[0]) * dx
+        cy = org[1] + (np.arange(sy) + off[1]) * dx
+        mx = (cx >= lo[0] + pad) & (cx < hi[0] - pad)
+        my = (cy >= lo[1] + pad) & (cy < hi[1] - pad)
+        return np.broadcast_to(my[None, :, None] & mx[None, None, :], (sz, sy, sx)).ravel()
+
+    cells = interior(g.nx, g.ny, g.nz, np.full(3, 0.5))
+    a_g = sim.alpha_s.cpu().numpy()
+    assert np.count_nonzero(a_o[cells]) > 1000
+    assert np.abs(a_g[cells] - a_o[cells]).max() <= 1e-9
+    dims = ((g.nx + 1, g.ny, g.nz), (g.nx, g.ny + 1, g.nz), (g.nx, g.ny, g.nz + 1))
+    for c in range(3):
+        off = np.full(3, 0.5)
+        off[c] = 0.0
+        faces = interior(*dims[c], off)
+        got = sim.Fs[c].cpu().numpy()[faces]
+        want = Fs_o[c][faces]
+        assert np.abs(got - want).max() <= (2e-6 if prec == FP32 else 1e-12) * np.abs(want).max()
+    assert gic.gic_check_status() == 0
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name,K", [("scale_sweep_16m", 20), ("polydisperse_bed_8m", 10)])
+@pytest.mark.parametrize("prec", PRECS)
+def test_full_size_subregion_window(name, K, prec):
+    """16M granules on 384^3 (its full 20 substeps) and the 8M-granule bed on
+    256^3 (10 substeps) on the GPU, against the oracle's substeps on a
+    100k-granule box grown by a halo of K (2 r_max + v_max dt) + 2 dx:
+    contacts carry information at most 2 r_max per substep and a granule
+    moves at most v_max dt, so the granules that start in the box, and the
+    alpha_s cells whose stencils stay inside it, see exactly the oracle's
+    inputs."""
+    prob = gi.make(name)
+    sim = sim_for(prob, prec)
+    sim.run(K)
+    torch.cuda.synchronize()
+    assert gic.gic_check_status() == 0
+    xg, vg = sim.positions()
+    x, v, r = oracle_inputs(prob)
+    r_max = float(r.max())
+    dx = prob.grid.dx
+    v_max = 2.0 * max(np.abs(a).max() for a in (prob.u, prob.vf, prob.wf)) + 1.0
+    halo = K * (2 * r_max + v_max * prob.params.dt_sub) + 2 * dx
+    box, core, lo, hi = _sub_box(prob, x, 100_000, halo)
+    sub = dataclasses.replace(prob, cell=prob.cell[box].copy(), q=prob.q[box].copy(), r=prob.r[box].copy(),
+                              v=prob.v[box].copy())
+    ref = oracle.run(sub, K=K)
+    in_core = np.isin(box, core)
+    xg = xg.cpu().numpy()[box][in_core]
+    vg = vg.cpu().numpy()[box][in_core]
+    assert np.abs(xg - ref["x"][in_core]).max() <= (1e-5 if prec == FP32 else 1e-12) * dx
+    vref = np.linalg.norm(ref["v"], axis=1).max()
+    # FP64: both sides form the overlap r_i + r_j - d from coordinates of
+    # ~0.5 m (ulp 1e-16 m) against overlaps of ~1e-6 m, so a stiff contact
+    # network moves velocities by ~K dt k_n 1e-16 / m_min ~ 1e-11 m/s
+    assert np.linalg.norm(vg - ref["v"][in_core], axis=1).max() <= (1e-4 if prec == FP32 else 1e-9) * vref
+    g = prob.grid
+    pad = r_max + 3 * dx + K * v_max * prob.params.dt_sub
+    cx = g.origin[0] + (np.arange(g.nx) + 0.5) * dx
+    cy = g.origin[1] + (np.arange(g.ny) + 0.5) * dx
+    mx = (cx >= lo[0] + pad) & (cx < hi[0] - pad)
+    my = (cy >= lo[1] + pad) & (cy < hi[1] - pad)
+    cells = np.broadcast_to(my[None, :, None] & mx[None, None, :], (g.nz, g.ny, g.nx)).ravel()
+    a_o = ref["alpha_s"][cells]
+    assert np.count_nonzero(a_o) > 1000
+    assert np.abs(sim.alpha_s.cpu().numpy()[cells] - a_o).max() <= 1e-9
 
 
 # ----------------------------------------------------------------------------- public host-buffer window, failures
