@@ -659,8 +659,8 @@ def _bed_tile(seed, tile_cells, iters, relax):
     pos += gen.uniform(-0.02 * med, 0.02 * med, size=pos.shape)
     rr = np.clip(med * np.exp(0.25 * rng(seed, STREAM_RAD).normal(size=m)), 0.5 * med, 2.0 * med)
     L = (cx * a, cy * a)
-    tol = 0.01 * rr.min()
-    pos = _settle_tile(pos, rr, L, iters, 0.004 * med, 0.3 * med, relax, tol)
+    pos = _settle_tile(pos, rr, L, iters, 0.004 * med, 0.3 * med, relax, 0.01 * rr.min())
+    tol = 0.001 * rr.min()
     for _ in range(50):
         I, J, d = _periodic_pairs(pos, 2 * rr.max(), L)
         excess = rr[I] + rr[J] - np.linalg.norm(d, axis=1) - tol
@@ -693,8 +693,9 @@ def polydisperse_bed(seed=3, n=8_000_000, tile_cells=(12, 12, 15), iters=300, re
     nearest-neighbour spacing (2.35 x median, jitter 0.02 x median) holds the
     lognormal volumes at a packing fraction near 0.6, settled by `iters`
     rounds of overlap removal under a decreasing downward push and up to
-    `relax` more without it; where a pair still overlaps by more than 1% of
-    the smallest radius, the larger granule is shrunk by the excess.  Copies of the tile placed side by side over the
+    `relax` more without it (or until no overlap exceeds 1% of the smallest
+    radius); where a pair still overlaps by more than 0.1% of the smallest
+    radius, the larger granule is shrunk by the excess.  Copies of the tile placed side by side over the
     floor meet with the same neighbour structure; the bed is those copies
     until n granules.  The tile's neighbour statistics (neighbours within
     r_i + r_j + 0.02 x median, contacts, packing fraction) go in `note`."""

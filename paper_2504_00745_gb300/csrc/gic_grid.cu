@@ -2,6 +2,8 @@
 // fluid fraction) and a5 P2G (volume fraction, exchange momentum), with
 // adjoints.  One thread per granule; granules arrive Morton-sorted, so the
 // lanes of a warp read and write the same few MAC cells.
+#include <climits>
+
 #include "gic_interp.cuh"
 
 namespace gic {
@@ -171,8 +173,8 @@ __global__ void k_alpha_sum(const double* __restrict__ a, int64_t m, double dx3,
 // alpha_s is accumulated as a 64-bit integer in units of 2^-53: per granule
 // the volume fraction S = V / dx^3 is rounded once to 2^-53; the per-axis
 // tent weights come from the 30-bit fixed-point position as 31-bit integers
-// (exact when the contact cell is the MAC cell), their product is kept to
-// 2^-62, each corner's deposit S w is truncated to 2^-53 and the eighth
+// (exact when the contact cell is the MAC cell), S times their product is
+// formed to 2^-62 and each corner's deposit truncated to 2^-53, and the eighth
 // corner takes the rest, so every granule deposits exactly S; integer atomics
 // make the sum independent of the order of arrival -- bitwise reproducible.
 // k_alpha_finish turns the integers into doubles in place.
@@ -189,6 +191,8 @@ __device__ __forceinline__ void fixed_axis(const DGrid& G, int c, uint32_t q, in
   unsigned long long P;
   if (G.k == 1)
     P = N << 1;
+  else if (G.k == 2)
+    P = N;
   else
     P = (__umul64hi(N << 2, G.kinv64) + 1ull) >> 1;
   uint32_t p = (uint32_t)P;  // < 2^31
@@ -229,21 +233,6 @@ __device__ __forceinline__ unsigned long long volume_fixed(const DGrid& G, float
   float sl = fmaf(r3h, G.vol_fx_hi, -sh) + fmaf(r3h, G.vol_fx_lo, r3l * G.vol_fx_hi);
   long long a = fabsf(sh) >= 8388608.0f ? float_int_to_ll(sh) : (long long)__float2ll_rn(sh);
   return (unsigned long long)(a + __float2ll_rn(sl));
-}
-
-// w_xy w_z in 2^-62 units, rounded: w_xy = w_x w_y exactly (<= 2^62, 2^-62
-// units), w_z <= 2^31 in 2^-31 units; (hi:lo) >> 31 of the 93-bit product.
-__device__ __forceinline__ unsigned long long w3_62(unsigned long long wxy, uint32_t wz) {
-  unsigned long long lo = wxy * (unsigned long long)wz;
-  unsigned long long hi = __umul64hi(wxy, (unsigned long long)wz);
-  return ((hi << 33) | (lo >> 31)) + ((lo >> 30) & 1ull);
-}
-
-// floor(S w / 2^62) for S < 2^54, w <= 2^62
-__device__ __forceinline__ long long scale62(unsigned long long S, unsigned long long w) {
-  unsigned long long lo = S * w;
-  unsigned long long hi = __umul64hi(S, w);
-  return (long long)((hi << 2) | (lo >> 62));
 }
 
 // FP64 path: alpha_s(c) = sum_i V_i N(x'_i - x_c) / dx^3 at the new positions, FP64
@@ -328,24 +317,6 @@ __global__ void __launch_bounds__(256) k_p2g(DGrid G, DParams<T> P, int64_t n, c
 
 // ---- FP32 path scatter ----
 //
-// One thread per granule (Morton order).  alpha_s: the eight 64-bit fixed-
-// point contributions go straight to global integer atomics (exact, order-
-// free); their warp total is added to an integer running sum, so
-// sum_c alpha_s(c) is exact.  F_s: lanes whose stencils share a base sample
-// form runs (Morton order keeps them adjacent); a segmented suffix sum with
-// only as many shuffle steps as the longest run of the warp needs leaves each
-// run's total in its head lane, which alone issues the eight float atomics.
-
-__device__ __forceinline__ float seg_sum_steps(float v, int end, int steps) {
-  int lane = lane_id();
-  int off = 1;
-  for (int s = 0; s < steps; ++s, off <<= 1) {
-    float o = __shfl_down_sync(0xffffffffu, v, off);
-    if (lane + off <= end) v += o;
-  }
-  return v;
-}
-
 // v * 2^e2 rounded to double with integer operations only (the FP64 pipe is
 // the slowest unit of this GPU)
 __device__ __forceinline__ double i64_scaled_to_double(long long v, int e2) {
@@ -372,100 +343,242 @@ __device__ __forceinline__ double i64_scaled_to_double(long long v, int e2) {
   return __longlong_as_double((long long)(sign | (e << 52) | (m & ((1ull << 52) - 1ull))));
 }
 
-__global__ void __launch_bounds__(256) k_p2g_f32(DGrid G, DParams<float> P, int64_t n,
-                                                 const int32_t* __restrict__ cell_old,
-                                                 const uint4* __restrict__ pos_old,
-                                                 const int32_t* __restrict__ cell_new,
-                                                 const uint4* __restrict__ pos_new, const float4* __restrict__ fex,
-                                                 double* __restrict__ alpha, float* __restrict__ Fs_u,
-                                                 float* __restrict__ Fs_v, float* __restrict__ Fs_w,
-                                                 double* __restrict__ sums) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+// floor(x w / 2^31) for x < 2^63, w <= 2^31, with two 32x32->64 products.
+__device__ __forceinline__ unsigned long long mul31(unsigned long long x, uint32_t w) {
+  unsigned long long hi = (unsigned long long)(uint32_t)(x >> 32) * w;
+  unsigned long long lo = (unsigned long long)(uint32_t)x * w;
+  return (hi << 1) + (lo >> 31);
+}
+
+// FP32-path alpha_s deposits of one granule at its new position: the base
+// sample i0 and the eight integer deposits (2^-53 units) summing to S exactly.
+// S is carried in 2^-62 units through the three per-axis weight products
+// (each truncated once), so a deposit is within ~2^-53 of S w_x w_y w_z; the
+// eighth corner takes S minus the other seven.
+__device__ __forceinline__ void alpha_deposits(const DGrid& G, int32_t cn, uint4 pn, int i0[3], long long v[8],
+                                               unsigned long long& S) {
+  S = volume_fixed(G, __uint_as_float(pn.w));
+  int c3[3] = {cell_x(cn), cell_y(cn), cell_z(cn)};
+  const int nn[3] = {G.nx, G.ny, G.nz};
+  uint32_t w1[3], w0[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    fixed_axis(G, c3[a], pcomp(pn, a), nn[a], i0[a], w1[a]);
+    w0[a] = kW1 - w1[a];
+  }
+  const unsigned long long S9 = S << 9;  // < 2^63
+  unsigned long long sx[2], sxy[4];
+  sx[0] = mul31(S9, w0[0]);
+  sx[1] = mul31(S9, w1[0]);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) sxy[k] = mul31(sx[k & 1], (k & 2) ? w1[1] : w0[1]);
+  long long sum7 = 0;
+#pragma unroll
+  for (int k = 0; k < 7; ++k) {
+    v[k] = (long long)(mul31(sxy[k & 3], (k & 4) ? w1[2] : w0[2]) >> 9);
+    sum7 += v[k];
+  }
+  v[7] = (long long)S - sum7;
+}
+
+// FP32 path of P2G.  One CTA takes 512 consecutive granules of the
+// Morton-sorted state, which occupy a compact block of MAC cells.  When the
+// samples they may touch fit a kP2GTile-entry box, every deposit goes to
+// shared-memory copies of alpha_s and the three F_s grids over that box,
+// held as 32-bit integer limbs (32-bit shared integer atomics run at full
+// rate even when lanes collide, unlike float or 64-bit ones), and the box's
+// non-zero entries then go to global memory with one atomic each; otherwise
+// every deposit is a global atomic.
+//   alpha_s: a deposit (< 2^54 units of 2^-53) is split into three 18-bit
+//   limbs, so up to 2^14 deposits per entry add without overflow -- exact.
+//   F_s: a deposit d is rounded to a multiple of u = M 2^-30, M the CTA's
+//   largest |exch f_ex| component, and q = d / u (|q| <= 2^30) is split into
+//   a signed high and an unsigned low 15-bit limb; the limb sums are exact,
+//   so the only rounding besides the float product d is the 2^-30 M grid.
+// alpha_s stays 64-bit fixed point (exact, order-independent) until
+// k_alpha_finish_f32.
+constexpr int kP2GThreads = 512;
+constexpr int kP2GTile = 1024;
+
+__global__ void __launch_bounds__(kP2GThreads, 2) k_p2g_f32(DGrid G, DParams<float> P, int64_t n,
+                                                           const int32_t* __restrict__ cell_old,
+                                                           const uint4* __restrict__ pos_old,
+                                                           const int32_t* __restrict__ cell_new,
+                                                           const uint4* __restrict__ pos_new,
+                                                           const float4* __restrict__ fex,
+                                                           double* __restrict__ alpha, float* __restrict__ Fs_u,
+                                                           float* __restrict__ Fs_v, float* __restrict__ Fs_w,
+                                                           double* __restrict__ sums) {
+  __shared__ uint32_t s_a[3][kP2GTile];
+  __shared__ int32_t s_fh[3][kP2GTile];
+  __shared__ uint32_t s_fl[3][kP2GTile];
+  __shared__ int s_lo[3], s_hi[3];
+  __shared__ unsigned s_M;
+  const int64_t i = blockIdx.x * (int64_t)kP2GThreads + threadIdx.x;
   const bool valid = i < n;
-  long long Si = 0;  // this granule's volume fraction in 2^-53 units
-  long long deposited = 0;
-  if (valid && alpha) {
-    uint4 pn = pos_new[i];
-    int32_t cn = cell_new[i];
-    unsigned long long S = volume_fixed(G, __uint_as_float(pn.w));
-    Si = (long long)S;
-    int c3[3] = {cell_x(cn), cell_y(cn), cell_z(cn)};
-    const int nn[3] = {G.nx, G.ny, G.nz};
-    int i0[3];
-    uint32_t w1[3], w0[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      fixed_axis(G, c3[a], pcomp(pn, a), nn[a], i0[a], w1[a]);
-      w0[a] = kW1 - w1[a];
+  const bool do_a = alpha != nullptr, do_f = Fs_u != nullptr;  // uniform over the launch
+  if (threadIdx.x < 3) {
+    s_lo[threadIdx.x] = INT_MAX;
+    s_hi[threadIdx.x] = INT_MIN;
+  }
+  if (threadIdx.x == 0) s_M = 0u;
+
+  // box of every sample this CTA may touch: a stencil's base is the MAC cell
+  // m or m - 1 on each axis, and it reaches one sample further
+  int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {INT_MIN, INT_MIN, INT_MIN};
+  int32_t cn = 0, co = 0;
+  float fc[3] = {0.f, 0.f, 0.f};
+  float M = 0.f;
+  if (valid) {
+    if (do_a) cn = cell_new[i];
+    if (do_f) {
+      co = cell_old[i];
+      float4 f = fex[i];
+      fc[0] = P.exch * f.x;
+      fc[1] = P.exch * f.y;
+      fc[2] = P.exch * f.z;
+      M = fmaxf(fabsf(fc[0]), fmaxf(fabsf(fc[1]), fabsf(fc[2])));
+      if (!(M <= 3.0e38f)) M = INFINITY;  // NaN or inf: no fixed-point grid for this CTA
     }
-    // the 3-D tent weight to 2^-62, the deposit S w truncated to 2^-53; the
-    // eighth corner takes S minus the other seven, so the granule deposits
-    // exactly S
-    unsigned long long wxy[4];
+    int32_t cs[2] = {do_a ? cn : co, do_f ? co : cn};
 #pragma unroll
-    for (int k = 0; k < 4; ++k)
-      wxy[k] = (unsigned long long)((k & 1) ? w1[0] : w0[0]) * (unsigned long long)((k & 2) ? w1[1] : w0[1]);
-    long long v[8];
-    long long sum7 = 0;
+    for (int h = 0; h < 2; ++h) {
+      int c3[3] = {cell_x(cs[h]), cell_y(cs[h]), cell_z(cs[h])};
 #pragma unroll
-    for (int k = 0; k < 7; ++k) {
-      v[k] = scale62(S, w3_62(wxy[k & 3], (k & 4) ? w1[2] : w0[2]));
-      sum7 += v[k];
-    }
-    v[7] = (long long)S - sum7;
-    deposited = (long long)S;
-    unsigned long long* acc = (unsigned long long*)alpha;
-    int64_t base = sample_index(G.nx, G.ny, i0[0], i0[1], i0[2]);
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      int a = k & 1, b = (k >> 1) & 1, cz = (k >> 2) & 1;
-      if (v[k]) atomicAdd(&acc[base + a + (int64_t)G.nx * (b + (int64_t)G.ny * cz)], (unsigned long long)v[k]);
+      for (int a = 0; a < 3; ++a) {
+        int m = mac_of(G, c3[a]);
+        lo[a] = min(lo[a], m - 1);
+        hi[a] = max(hi[a], m + 1);
+      }
     }
   }
-  if (Fs_u) {  // uniform over the launch
-    int m[3] = {0, 0, 0};
-    float t[3] = {0.f, 0.f, 0.f};
-    float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (valid) {
-      granule_mac<float>(G, cell_old[i], pos_old[i], m, t);
-      f = fex[i];
-    }
-    float* Fs[3] = {Fs_u, Fs_v, Fs_w};
-    const float fv[3] = {P.exch * f.x, P.exch * f.y, P.exch * f.z};
+  __syncthreads();
 #pragma unroll
-    for (int comp = 0; comp < 3; ++comp) {
-      Stencil3<float> S = make_stencil<float>(G, m, t, comp);
-      unsigned key = valid ? (unsigned)base_index(S) : 0xffffffffu - (unsigned)lane_id();
-      int end = run_end(key);
-      bool head = run_head(key);
-      int len = __reduce_max_sync(0xffffffffu, (unsigned)(head ? end - lane_id() + 1 : 1));
-      int steps = 32 - __clz(len - 1);  // ceil(log2(len))
-      float val[8];
+  for (int a = 0; a < 3; ++a) {
+    int l = __reduce_min_sync(0xffffffffu, lo[a]);
+    int h = __reduce_max_sync(0xffffffffu, hi[a]);
+    if (lane_id() == 0) {
+      atomicMin(&s_lo[a], l);
+      atomicMax(&s_hi[a], h);
+    }
+  }
+  if (do_f) {  // non-negative floats order like their bit patterns
+    unsigned mb = __reduce_max_sync(0xffffffffu, __float_as_uint(M));
+    if (lane_id() == 0) atomicMax(&s_M, mb);
+  }
+  __syncthreads();
+  const int bx = max(s_lo[0], 0), by = max(s_lo[1], 0), bz = max(s_lo[2], 0);
+  const int ex = s_hi[0] - bx + 1, ey = s_hi[1] - by + 1, ez = s_hi[2] - bz + 1;
+  // every CTA holds at least one granule, so the box is not empty
+  const bool tile = (int64_t)ex * ey * ez <= kP2GTile;
+  const float Mc = __uint_as_float(s_M);
+  const bool ftile = tile && Mc >= 1e-30f && Mc <= 3.0e38f;  // F_s through the fixed-point tile
+  const float unit = Mc * 0x1p-30f, inv_unit = ftile ? 0x1p30f / Mc : 0.f;
+  const int vol = tile ? ex * ey * ez : 0;
+  const int sy = ex, sz = ex * ey;
+  for (int e = threadIdx.x; e < vol; e += kP2GThreads) {
+    if (do_a) s_a[0][e] = s_a[1][e] = s_a[2][e] = 0u;
+    if (ftile) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        s_fh[c][e] = 0;
+        s_fl[c][e] = 0u;
+      }
+    }
+  }
+  if (tile) __syncthreads();
+
+  unsigned long long S = 0;
+  if (valid && do_a) {
+    int ia[3];
+    long long va[8];
+    alpha_deposits(G, cn, pos_new[i], ia, va, S);
+    if (tile) {
+      const int e0 = (ia[0] - bx) + sy * (ia[1] - by) + sz * (ia[2] - bz);
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
-        int a = k & 1, b = (k >> 1) & 1, cz = (k >> 2) & 1;
-        float wgt = (a ? S.w[0] : 1.f - S.w[0]) * (b ? S.w[1] : 1.f - S.w[1]) * (cz ? S.w[2] : 1.f - S.w[2]);
-        val[k] = seg_sum_steps(valid ? wgt * fv[comp] : 0.f, end, steps);
+        const int e = e0 + (k & 1) + ((k >> 1) & 1) * sy + (k >> 2) * sz;
+        const unsigned long long v = (unsigned long long)va[k];
+        atomicAdd(&s_a[0][e], (uint32_t)(v & 0x3ffffull));
+        atomicAdd(&s_a[1][e], (uint32_t)((v >> 18) & 0x3ffffull));
+        atomicAdd(&s_a[2][e], (uint32_t)(v >> 36));
       }
-      if (valid && head) {
-        int nsx = S.ns[0], nsy = S.ns[1];
+    } else {
+      unsigned long long* g0 = (unsigned long long*)alpha + sample_index(G.nx, G.ny, ia[0], ia[1], ia[2]);
+      const int64_t gy = G.nx, gz = (int64_t)G.nx * G.ny;
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        if (va[k]) atomicAdd(g0 + (k & 1) + ((k >> 1) & 1) * gy + (k >> 2) * gz, (unsigned long long)va[k]);
+    }
+  }
+  if (valid && do_f) {
+    int m[3];
+    float t[3];
+    granule_mac<float>(G, co, pos_old[i], m, t);
+    float* Fs[3] = {Fs_u, Fs_v, Fs_w};
+#pragma unroll
+    for (int comp = 0; comp < 3; ++comp) {
+      Stencil3<float> St = make_stencil<float>(G, m, t, comp);
+      const float wx = St.w[0], wy = St.w[1], wz = St.w[2];
+      const float fx0 = (1.f - wx) * fc[comp], fx1 = wx * fc[comp];
+      const float wyz[4] = {(1.f - wy) * (1.f - wz), wy * (1.f - wz), (1.f - wy) * wz, wy * wz};
+      if (ftile) {
+        const int e0 = (St.i0[0] - bx) + sy * (St.i0[1] - by) + sz * (St.i0[2] - bz);
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-          int a = k & 1, b = (k >> 1) & 1, cz = (k >> 2) & 1;
-          atomicAdd(&Fs[comp][sample_index(nsx, nsy, S.i0[0] + a, S.i0[1] + b, S.i0[2] + cz)], val[k]);
+          const int q = __float2int_rn(((k & 1) ? fx1 : fx0) * wyz[k >> 1] * inv_unit);
+          const int e = e0 + (k & 1) + ((k >> 1) & 1) * sy + (k >> 2) * sz;
+          atomicAdd(&s_fh[comp][e], q >> 15);
+          atomicAdd(&s_fl[comp][e], (uint32_t)(q & 0x7fff));
+        }
+      } else {
+        const int nsx = G.nx + (comp == 0), nsy = G.ny + (comp == 1);
+        float* g0 = Fs[comp] + sample_index(nsx, nsy, St.i0[0], St.i0[1], St.i0[2]);
+        const int64_t gy = nsx, gz = (int64_t)nsx * nsy;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const float d = ((k & 1) ? fx1 : fx0) * wyz[k >> 1];
+          if (d != 0.f) atomicAdd(g0 + (k & 1) + ((k >> 1) & 1) * gy + (k >> 2) * gz, d);
         }
       }
     }
   }
-  if (sums) {  // exact integer warp totals of sum_i V_i / dx^3 and of the deposits
-    long long v = Si, d = deposited;
-    for (int off = 16; off > 0; off >>= 1) {
-      v += __shfl_down_sync(0xffffffffu, v, off);
-      d += __shfl_down_sync(0xffffffffu, d, off);
+
+  if (tile) {  // the box's non-zero entries to global memory
+    __syncthreads();
+    unsigned long long* acc = (unsigned long long*)alpha;
+    float* Fs[3] = {Fs_u, Fs_v, Fs_w};
+    // e = lx + ex (ly + ey lz); (e + 1/2) / d stays >= 1/(2 d) away from an
+    // integer, far beyond the float error for e, d <= 1024
+    const float rx = 1.f / (float)ex, rxy = 1.f / (float)sz;
+    for (int e = threadIdx.x; e < vol; e += kP2GThreads) {
+      int lz = (int)(((float)e + 0.5f) * rxy);
+      int r = e - lz * sz;
+      int ly = (int)(((float)r + 0.5f) * rx);
+      int lx = r - ly * ex;
+      int gx = bx + lx, gy = by + ly, gz = bz + lz;
+      if (do_a) {
+        unsigned long long a = (unsigned long long)s_a[0][e] + ((unsigned long long)s_a[1][e] << 18) +
+                               ((unsigned long long)s_a[2][e] << 36);
+        if (a) atomicAdd(&acc[sample_index(G.nx, G.ny, gx, gy, gz)], a);
+      }
+      if (ftile) {
+#pragma unroll
+        for (int comp = 0; comp < 3; ++comp) {
+          long long q = (long long)s_fh[comp][e] * (1ll << 15) + (long long)s_fl[comp][e];
+          if (q) atomicAdd(&Fs[comp][sample_index(G.nx + (comp == 0), G.ny + (comp == 1), gx, gy, gz)],
+                           (float)q * unit);
+        }
+      }
     }
-    if (lane_id() == 0) {
-      if (d != 0) atomicAdd((unsigned long long*)&sums[0], (unsigned long long)d);
-      if (v != 0) atomicAdd((unsigned long long*)&sums[1], (unsigned long long)v);
+  }
+
+  if (sums) {  // exact integer warp totals of sum_i V_i / dx^3; every granule deposits exactly S
+    long long v = (long long)S;
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if (lane_id() == 0 && v != 0) {
+      atomicAdd((unsigned long long*)&sums[0], (unsigned long long)v);
+      atomicAdd((unsigned long long*)&sums[1], (unsigned long long)v);
     }
   }
 }
@@ -641,7 +754,7 @@ extern "C" int gic_p2g(const GicGrid* grid, const GicParams* params, const GicGr
     if (old_->precision == GIC_FP32) {
       DParams<float> P;
       if ((rc = make_params(params, &P))) return rc;
-      k_p2g_f32<<<grid_blocks(n, 256), 256, 0, stream>>>(
+      k_p2g_f32<<<grid_blocks(n, kP2GThreads), kP2GThreads, 0, stream>>>(
           G, P, n, old_->cell, (const uint4*)old_->pos, new_->cell, (const uint4*)new_->pos, (const float4*)f_ex,
           alpha_s, (float*)Fs_u, (float*)Fs_v, (float*)Fs_w, sums2);
     } else {

