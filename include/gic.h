@@ -188,6 +188,51 @@ int64_t gic_sort_static_max_n(void);
 int gic_contact(const GicGrid* grid, const GicParams* params, const GicGranules* sorted, const void* cell_table,
                 void* F_c, gic_stream_t stream);
 
+/* a2 with Verlet neighbour lists: the same forces as gic_contact (identical
+ * contact pairs, the pair sums in another order), found through a list of
+ * the partners each granule had within r_i + r_j + skin when the list was
+ * built.  The paper walks the cell list every substep (Sec. 3.1); a list stays
+ * exact while no granule has moved more than skin / 2 since it was built,
+ * because a pair can then have closed by at most skin.
+ *   A build numbers the granules by their sorted index at that moment (their
+ *   slot) and stores each slot's partners as slots, so list rows and the
+ *   reference positions are read in nearly sorted order between builds;
+ *   granule ids map to slots.  Each call first maps the current sorted
+ *   indices to slots and checks every displacement from the last build; if
+ *   one exceeds skin / 2, or a rebuild was requested, this call walks the 27
+ *   cells as gic_contact does and rebuilds every list while it sums the
+ *   forces; otherwise it walks the lists only.  sorted must carry ids
+ *   (0..n-1, each once).  Three launches, no host sync.
+ *   A list that would exceed cap entries makes every later call rebuild
+ *   (forces stay exact, the saving is lost) until gic_neighbors_reset with a
+ *   larger cap; flags[1] bit 1 reports it.
+ * Ownership: all arrays are device memory owned by the caller, sized for
+ * n granules; gic_neighbors_reset must run once before the first use (and
+ * whenever the granule set or radii change).  Errors: GIC_ERR_INVALID for a
+ * null array, n mismatch, cap < 1 or a negative skin; GIC_ERR_ALIGN when
+ * ref_pos is not 16-byte (FP32) / 32-byte (FP64) aligned. */
+typedef struct GicNeighbors {
+  int64_t n;         /* granules; ids run 0..n-1 */
+  int32_t cap;       /* list slots per granule */
+  double skin;       /* metres, >= 0 */
+  int32_t* list;     /* [n * cap] partner slots of each slot (row = slot) */
+  int32_t* count;    /* [n] entries used in each row */
+  int32_t* ref_cell; /* [n] contact cell of each slot at the last build */
+  void* ref_pos;     /* [n] position record (uint4 FP32, double4 FP64) of each slot at the last build */
+  int32_t* slot;     /* [n] slot of each granule id (written by a build) */
+  int32_t* cur;      /* [n] current sorted index of each slot (written by every call) */
+  int32_t* at;       /* [n] slot of each current sorted index (written by every call) */
+  uint32_t* flags;   /* [8]: [0] rebuild in this call, [1] bit 0 rebuild requested, bit 1 a list overflowed at the
+                      * last build, [2] CTA counter, [3] overflow during a build, [4] builds performed */
+} GicNeighbors;
+
+int gic_contact_verlet(const GicGrid* grid, const GicParams* params, const GicGranules* sorted,
+                       const void* cell_table, const GicNeighbors* nb, void* F_c, gic_stream_t stream);
+
+/* Request a rebuild at the next gic_contact_verlet and clear the counters
+ * (flags = {0, 1, 0, 0, 0, ...}). */
+int gic_neighbors_reset(const GicNeighbors* nb, gic_stream_t stream);
+
 /* a3: trilinear G2P of u, v, w, grad p (face differences of p) and alpha_f:
  *   F_fl = c_drag pi r^2 rho_f |u_f - v| (u_f - v) - (4/3) pi r^3 grad p
  *   a_f  = g - grad p / rho_f   (dv_f/dt of Sec. 5.2 Eq. momentum4 without the

@@ -687,6 +687,271 @@ __global__ void k_contact_pairs(DGrid G, int64_t n, const int32_t* __restrict__ 
   if (counts) counts[i] = cnt;
 }
 
+// ----------------------------------------------------------------- Verlet lists
+//
+// A build gives every granule a slot (its sorted index then); row s of
+// `list` holds the slots of the granules that were within r_i + r_j + skin of
+// slot s.  While every granule has moved less than skin / 2 since then, every
+// pair now in contact is in the rows, so walking them gives exactly
+// gic_contact's pairs.  Between builds the sorted order changes little, so
+// rows, reference positions and partners are read almost in order.
+
+enum : int { kNbRebuild = 0, kNbSticky = 1, kNbCounter = 2, kNbOverflow = 3, kNbBuilds = 4, kNbWords = 8 };
+
+struct NbDev {
+  int cap;
+  int32_t* list;
+  int32_t* count;
+  int32_t* ref_cell;
+  void* ref_pos;
+  int32_t* slot;  // by id
+  int32_t* cur;   // by slot
+  int32_t* at;    // by sorted index
+  uint32_t* flags;
+};
+
+// displacement since the last build beyond skin / 2 (lim2 = (skin / 2)^2 in
+// the units of each precision's position record)
+__device__ __forceinline__ bool moved_far(const DGrid&, int32_t c, const uint4& p, int32_t cr, const uint4& pr,
+                                          float lim2) {
+  // 32-bit pieces: the offset difference is exact, the cell part a multiple of 2^30
+  float dx = fmaf((float)(cell_x(c) - cell_x(cr)), 0x1p30f, (float)((int)p.x - (int)pr.x));
+  float dy = fmaf((float)(cell_y(c) - cell_y(cr)), 0x1p30f, (float)((int)p.y - (int)pr.y));
+  float dz = fmaf((float)(cell_z(c) - cell_z(cr)), 0x1p30f, (float)((int)p.z - (int)pr.z));
+  return fmaf(dx, dx, fmaf(dy, dy, dz * dz)) > lim2;
+}
+__device__ __forceinline__ bool moved_far(const DGrid& G, int32_t c, const d4& p, int32_t cr, const d4& pr,
+                                          double lim2) {
+  double dx = (double)(cell_x(c) - cell_x(cr)) * G.hc + (p.x - pr.x);
+  double dy = (double)(cell_y(c) - cell_y(cr)) * G.hc + (p.y - pr.y);
+  double dz = (double)(cell_z(c) - cell_z(cr)) * G.hc + (p.z - pr.z);
+  return dx * dx + dy * dy + dz * dz > lim2;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_verlet_check(DGrid G, int64_t n, const int32_t* __restrict__ cell,
+                                                       const pos_t<T>* __restrict__ pos,
+                                                       const int32_t* __restrict__ id, NbDev nb, T lim2) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  bool far = false;
+  if (i < n && !nb.flags[kNbSticky]) {  // after a reset the slots are not set yet
+    int32_t k = id[i];
+    int32_t s = (k >= 0 && (int64_t)k < n) ? nb.slot[k] : -1;
+    if (s >= 0 && (int64_t)s < n) {
+      nb.cur[s] = (int32_t)i;
+      nb.at[i] = s;
+      far = moved_far(G, cell[i], pos[i], nb.ref_cell[s], reinterpret_cast<const pos_t<T>*>(nb.ref_pos)[s], lim2);
+    } else {
+      far = true;  // ids outside 0..n-1: rebuild (the build path does not need them)
+    }
+  }
+  if (__any_sync(0xffffffffu, far) && lane_id() == 0) atomicOr(&nb.flags[kNbRebuild], 1u);
+}
+
+template <typename T>
+__device__ __forceinline__ void add_force(const DParams<T>& P, const PairGeom<T>& g, const vec_t<T>& vi,
+                                          const vec_t<T>& vj, T mi, T mj, T& F0, T& F1, T& F2, bool& coincident) {
+  T f0, f1, f2;
+  if (pair_force(P, g.x0, g.x1, g.x2, g.d, g.overlap, vi.x - vj.x, vi.y - vj.y, vi.z - vj.z, mi * mj / (mi + mj), f0,
+                 f1, f2)) {
+    F0 += f0;
+    F1 += f1;
+    F2 += f2;
+  } else {
+    coincident = true;
+  }
+}
+
+// FP32 candidate j (cell offset o from i): whether it is within R + skin
+// (list test, a superset with a float margin), and its contact geometry.
+__device__ __forceinline__ void verlet_pair(const DGrid& G, const uint4& pi, float ri, bool has_f, const float4& fi,
+                                            const float4& fj, const uint4* __restrict__ pos, int64_t j, int ox,
+                                            int oy, int oz, float skin, bool& near, bool& touch,
+                                            PairGeom<float>& g) {
+  uint4 pj;
+  float rj;
+  float d2, Rs, Rc;
+  if (has_f) {  // float positions in contact cells
+    rj = fj.w;
+    float rx = (float)ox + fj.x - fi.x, ry = (float)oy + fj.y - fi.y, rz = (float)oz + fj.z - fi.z;
+    d2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+    Rc = (ri + rj) * G.inv_hc_f;
+    Rs = (ri + rj + skin) * G.inv_hc_f;
+    near = d2 < Rs * Rs * (1.0f + 1e-4f);
+    touch = d2 < Rc * Rc * (1.0f + 1e-4f);
+    if (!touch) return;
+    pj = __ldg(&pos[j]);
+  } else {  // the exact integer separation, float pre-test
+    pj = __ldg(&pos[j]);
+    rj = radius_of(pj);
+    int Dx, Dy, Dz;
+    int_sep(pi, pj, ox, oy, oz, Dx, Dy, Dz);
+    float fx = (float)Dx, fy = (float)Dy, fz = (float)Dz;
+    d2 = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
+    Rc = ri + rj;
+    Rs = ri + rj + skin;
+    near = d2 < Rs * Rs * G.s2_margin;
+    touch = d2 < Rc * Rc * G.s2_margin;
+    if (!touch) return;
+  }
+  int Dx, Dy, Dz;
+  int_sep(pi, pj, ox, oy, oz, Dx, Dy, Dz);
+  touch = pair_geom_exact(G, Dx, Dy, Dz, ri, rj, g);
+}
+
+__device__ __forceinline__ void verlet_pair(const DGrid& G, const d4& pi, double ri, bool, const float4&,
+                                            const float4&, const d4* __restrict__ pos, int64_t j, int ox, int oy, int oz,
+                                            double skin, bool& near, bool& touch, PairGeom<double>& g) {
+  d4 pj = ldg(&pos[j]);
+  double x0, x1, x2;
+  rel_ij(G, pi, pj, ox, oy, oz, x0, x1, x2);
+  double d2 = x0 * x0 + x1 * x1 + x2 * x2;
+  double R = ri + pj.w;
+  near = d2 < (R + skin) * (R + skin);
+  touch = d2 < R * R;
+  if (!touch) return;
+  g.x0 = x0;
+  g.x1 = x1;
+  g.x2 = x2;
+  g.d = sqrt(d2);
+  g.overlap = R - g.d;
+}
+
+// Wall forces of granule i (cell coordinates c3) added to F.
+template <typename T>
+__device__ __forceinline__ void add_walls(const DGrid& G, const DParams<T>& P, const pos_t<T>& pi, T ri, T mi,
+                                          const vec_t<T>& vi, int cx, int cy, int cz, T& F0, T& F1, T& F2,
+                                          uint32_t* status) {
+  const int c3[3] = {cx, cy, cz};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      if (side == 0 ? c3[a] != 0 : c3[a] != G.nc[a] - 1) continue;
+      T gap, ov;
+      if (!wall_geom(G, pi, a, side, ri, gap, ov)) continue;
+      T x[3] = {0, 0, 0};
+      x[a] = side == 0 ? gap : -gap;
+      T f0, f1, f2;
+      if (pair_force(P, x[0], x[1], x[2], gap, ov, vi.x, vi.y, vi.z, mi, f0, f1, f2)) {
+        F0 += f0;
+        F1 += f1;
+        F2 += f2;
+      } else {
+        raise_status(status, GIC_STATUS_OUT_OF_DOMAIN);
+      }
+    }
+  }
+}
+
+// kBuild = true: runs only when this call rebuilds -- walks the 27 cells,
+// writes every row (slot = sorted index) and the forces.  kBuild = false:
+// runs only when it does not -- walks the rows; its last CTA then clears the
+// per-call words.  The two are launched back to back; the idle one exits.
+template <typename T, bool kBuild>
+__global__ void __launch_bounds__(kBuild ? 128 : 256, kBuild ? 1 : 4) k_contact_verlet(
+    DGrid G, DParams<T> P, int64_t n, const int32_t* __restrict__ cell, const pos_t<T>* __restrict__ pos,
+    const float4* __restrict__ posf, const vec_t<T>* __restrict__ vel, const int32_t* __restrict__ id,
+    const uint4* __restrict__ table, NbDev nb, T skin, vec_t<T>* __restrict__ F, uint32_t* status) {
+  const bool rebuild = (nb.flags[kNbRebuild] | nb.flags[kNbSticky]) != 0u;  // uniform over the launch
+  if (kBuild && !rebuild) return;
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (kBuild == rebuild && i < n) {
+    const int32_t ci = cell[i];
+    const int cx = cell_x(ci), cy = cell_y(ci), cz = cell_z(ci);
+    const pos_t<T> pi = pos[i];
+    const vec_t<T> vi = vel[i];
+    const T ri = radius_of(pi);
+    const T mi = granule_mass(P, ri);
+    if (T(2) * ri > (T)G.hc) raise_status(status, GIC_STATUS_RADIUS);
+    const bool has_f = sizeof(T) == 4 && posf != nullptr;
+    const float4 fi = has_f ? __ldg(&posf[i]) : make_float4(0.f, 0.f, 0.f, 0.f);
+    T F0 = 0, F1 = 0, F2 = 0;
+    bool coincident = false;
+    if constexpr (kBuild) {
+      int32_t* row = nb.list + i * nb.cap;
+      const uint32_t epoch = __ldg(&table[0].x);
+      int cnt = 0;
+      bool over = false;
+      for_each_partner(G, table, epoch, i, cx, cy, cz, [&](int64_t j, int ox, int oy, int oz) {
+        const float4 fj = has_f ? __ldg(&posf[j]) : fi;
+        bool near, touch;
+        PairGeom<T> g;
+        verlet_pair(G, pi, ri, has_f, fi, fj, pos, j, ox, oy, oz, skin, near, touch, g);
+        if (near) {
+          if (cnt < nb.cap)
+            row[cnt++] = (int32_t)j;
+          else
+            over = true;
+        }
+        if (touch) add_force(P, g, vi, ldg(&vel[j]), mi, granule_mass(P, radius_of(ldg(&pos[j]))), F0, F1, F2,
+                             coincident);
+      });
+      nb.count[i] = cnt;
+      nb.ref_cell[i] = ci;
+      reinterpret_cast<pos_t<T>*>(nb.ref_pos)[i] = pi;
+      const int32_t idi = id[i];
+      if (idi >= 0 && (int64_t)idi < n) nb.slot[idi] = (int32_t)i;
+      if (over) atomicOr(&nb.flags[kNbOverflow], 1u);
+    } else {
+      const int32_t s = nb.at[i];
+      const int32_t* row = nb.list + (int64_t)s * nb.cap;
+      const int cnt = nb.count[s];
+      // four partners at a time: their index, cell and float-position loads overlap
+      for (int k = 0; k < cnt; k += 4) {
+        int64_t jj[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) jj[u] = k + u < cnt ? (int64_t)nb.cur[row[k + u]] : -1;
+        int32_t cj[4];
+        float4 fj[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          cj[u] = jj[u] >= 0 ? __ldg(&cell[jj[u]]) : ci;
+          fj[u] = (has_f && jj[u] >= 0) ? __ldg(&posf[jj[u]]) : fi;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (jj[u] < 0) continue;
+          const int ox = cell_x(cj[u]) - cx, oy = cell_y(cj[u]) - cy, oz = cell_z(cj[u]) - cz;
+          // partners two or more cells apart are farther than h_c >= 2 r_max
+          if (ox < -1 || ox > 1 || oy < -1 || oy > 1 || oz < -1 || oz > 1) continue;
+          bool near, touch;
+          PairGeom<T> g;
+          verlet_pair(G, pi, ri, has_f, fi, fj[u], pos, jj[u], ox, oy, oz, T(0), near, touch, g);
+          if (touch)
+            add_force(P, g, vi, ldg(&vel[jj[u]]), mi, granule_mass(P, radius_of(ldg(&pos[jj[u]]))), F0, F1, F2,
+                      coincident);
+        }
+      }
+    }
+    if (P.walls) add_walls(G, P, pi, ri, mi, vi, cx, cy, cz, F0, F1, F2, status);
+    if (coincident) raise_status(status, GIC_STATUS_COINCIDENT);
+    if (!isfinite(F0) || !isfinite(F1) || !isfinite(F2)) raise_status(status, GIC_STATUS_NONFINITE);
+    F[i] = make_vec<T>(F0, F1, F2);
+  }
+  if constexpr (!kBuild) {
+    // the last CTA to finish clears the per-call words for the next call
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      if (atomicAdd(&nb.flags[kNbCounter], 1u) == gridDim.x - 1) {
+        __threadfence();
+        if (rebuild) {
+          nb.flags[kNbSticky] = atomicExch(&nb.flags[kNbOverflow], 0u) ? 2u : 0u;
+          nb.flags[kNbBuilds] += 1u;
+        }
+        nb.flags[kNbRebuild] = 0u;
+        nb.flags[kNbCounter] = 0u;
+        __threadfence();
+      }
+    }
+  }
+}
+
+__global__ void k_neighbors_reset(uint32_t* flags) {
+  if (threadIdx.x < kNbWords) flags[threadIdx.x] = threadIdx.x == kNbSticky ? 1u : 0u;
+}
+
 static int check_table(const void* t) {
   if (!t) return set_error(GIC_ERR_INVALID, "cell_table is NULL");
   if ((uintptr_t)t % 16) return set_error(GIC_ERR_ALIGN, "cell_table must be 16-byte aligned");
@@ -781,5 +1046,69 @@ extern "C" int gic_contact_pairs(const GicGrid* grid, const GicGranules* s, cons
                                                                          max_pairs, (unsigned long long*)n_pairs);
   count_launches(1);
   GIC_CHECK_LAUNCH("gic_contact_pairs");
+  return GIC_OK;
+}
+
+static int check_neighbors(const GicNeighbors* nb, const GicGranules* s, const char* what) {
+  if (!nb) return set_error(GIC_ERR_INVALID, "%s: neighbours struct is NULL", what);
+  if (!nb->list || !nb->count || !nb->ref_cell || !nb->ref_pos || !nb->slot || !nb->cur || !nb->at || !nb->flags)
+    return set_error(GIC_ERR_INVALID, "%s: a neighbour array is NULL", what);
+  if (nb->cap < 1) return set_error(GIC_ERR_INVALID, "%s: cap must be >= 1", what);
+  if (!(nb->skin >= 0.0)) return set_error(GIC_ERR_INVALID, "%s: skin must be >= 0", what);
+  if (s && nb->n != s->n) return set_error(GIC_ERR_INVALID, "%s: neighbour lists are for %lld granules, got %lld",
+                                           what, (long long)nb->n, (long long)s->n);
+  if (s && (uintptr_t)nb->ref_pos % (s->precision == GIC_FP32 ? 16 : 32))
+    return set_error(GIC_ERR_ALIGN, "%s: ref_pos misaligned", what);
+  return GIC_OK;
+}
+
+extern "C" int gic_contact_verlet(const GicGrid* grid, const GicParams* params, const GicGranules* s,
+                                  const void* table, const GicNeighbors* nb, void* F_c, gic_stream_t stream) {
+  DGrid G;
+  int rc = make_grid(grid, &G);
+  if (rc) return rc;
+  if ((rc = check_granules(s, "gic_contact_verlet", true))) return rc;
+  if ((rc = check_table(table))) return rc;
+  if ((rc = check_neighbors(nb, s, "gic_contact_verlet"))) return rc;
+  if (s->n == 0) return GIC_OK;
+  if (!F_c) return set_error(GIC_ERR_INVALID, "gic_contact_verlet: F_c is NULL");
+  if ((rc = check_vecs(s->precision, "gic_contact_verlet", {F_c}))) return rc;
+  NbDev d{nb->cap, nb->list, nb->count, nb->ref_cell, nb->ref_pos, nb->slot, nb->cur, nb->at, nb->flags};
+  const double half = 0.5 * nb->skin;
+  if (s->precision == GIC_FP32) {
+    DParams<float> P;
+    if ((rc = make_params(params, &P))) return rc;
+    const double lim = half * G.inv_unit;  // skin / 2 in 2^-30 h_c units
+    k_verlet_check<float><<<grid_blocks(s->n, 256), 256, 0, stream>>>(G, s->n, s->cell, (const uint4*)s->pos, s->id, d,
+                                                                      (float)(lim * lim));
+    k_contact_verlet<float, true><<<grid_blocks(s->n, 128), 128, 0, stream>>>(
+        G, P, s->n, s->cell, (const uint4*)s->pos, (const float4*)s->posf, (const float4*)s->vel, s->id,
+        (const uint4*)table, d, (float)nb->skin, (float4*)F_c, status_word());
+    k_contact_verlet<float, false><<<grid_blocks(s->n, 256), 256, 0, stream>>>(
+        G, P, s->n, s->cell, (const uint4*)s->pos, (const float4*)s->posf, (const float4*)s->vel, s->id,
+        (const uint4*)table, d, (float)nb->skin, (float4*)F_c, status_word());
+  } else {
+    DParams<double> P;
+    if ((rc = make_params(params, &P))) return rc;
+    k_verlet_check<double><<<grid_blocks(s->n, 256), 256, 0, stream>>>(G, s->n, s->cell, (const d4*)s->pos, s->id, d,
+                                                                       half * half);
+    k_contact_verlet<double, true><<<grid_blocks(s->n, 128), 128, 0, stream>>>(
+        G, P, s->n, s->cell, (const d4*)s->pos, nullptr, (const d4*)s->vel, s->id, (const uint4*)table, d, nb->skin,
+        (d4*)F_c, status_word());
+    k_contact_verlet<double, false><<<grid_blocks(s->n, 256), 256, 0, stream>>>(
+        G, P, s->n, s->cell, (const d4*)s->pos, nullptr, (const d4*)s->vel, s->id, (const uint4*)table, d, nb->skin,
+        (d4*)F_c, status_word());
+  }
+  count_launches(3);
+  GIC_CHECK_LAUNCH("gic_contact_verlet");
+  return GIC_OK;
+}
+
+extern "C" int gic_neighbors_reset(const GicNeighbors* nb, gic_stream_t stream) {
+  int rc = check_neighbors(nb, nullptr, "gic_neighbors_reset");
+  if (rc) return rc;
+  k_neighbors_reset<<<1, 32, 0, stream>>>(nb->flags);
+  count_launches(1);
+  GIC_CHECK_LAUNCH("gic_neighbors_reset");
   return GIC_OK;
 }

@@ -180,7 +180,6 @@ __global__ void k_alpha_sum(const double* __restrict__ a, int64_t m, double dx3,
 // k_alpha_finish turns the integers into doubles in place.
 
 constexpr uint32_t kW1 = 1u << 31;  // weight 1.0
-constexpr double kAlphaUnit = 1.0 / 9007199254740992.0;  // 2^-53
 
 // Centred-stencil weights of one axis from the contact coordinate c and the
 // fixed-point offset q: lower sample i0 and integer weights (w0, w1), w0 + w1 = 2^31.

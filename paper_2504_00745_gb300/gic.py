@@ -45,6 +45,12 @@ class GicGranules(C.Structure):
                 ("precision", C.c_int32), ("posf", C.c_void_p)]
 
 
+class GicNeighbors(C.Structure):
+    _fields_ = [("n", C.c_int64), ("cap", C.c_int32), ("skin", C.c_double), ("list", C.c_void_p),
+                ("count", C.c_void_p), ("ref_cell", C.c_void_p), ("ref_pos", C.c_void_p), ("slot", C.c_void_p),
+                ("cur", C.c_void_p), ("at", C.c_void_p), ("flags", C.c_void_p)]
+
+
 _P = C.c_void_p
 _SIGS = {
     "gic_workspace_size": [_P, C.c_int64, C.c_int32, _P],
@@ -65,6 +71,8 @@ _SIGS = {
     "gic_contact_pairs": [_P, _P, _P, _P, _P, C.c_int64, _P, _P],
     "gic_check_status": [_P, C.c_int32, C.c_int32, _P],
     "gic_sort_static": [_P, _P, _P, _P, _P, _P],
+    "gic_contact_verlet": [_P, _P, _P, _P, _P, _P, _P],
+    "gic_neighbors_reset": [_P, _P],
 }
 # entry points that exist in include/gic.h but are declared optional here
 # (added later in the library's life) are looked up lazily
@@ -244,6 +252,44 @@ def gic_contact(grid: GicGrid, params: GicParams, st: State, cell_table, F_c, st
     s = st.struct()
     _check(lib().gic_contact(C.byref(grid), C.byref(params), C.byref(s), _ptr(cell_table), _ptr(F_c),
                              _stream(stream)), "gic_contact")
+
+
+class Neighbors:
+    """Device arrays of a GicNeighbors (Verlet lists kept by granule id)."""
+
+    def __init__(self, n: int, precision: int, cap: int = 48, skin: float = 0.0, device="cuda"):
+        self.n, self.cap, self.skin, self.precision = n, cap, float(skin), precision
+        i32 = dict(dtype=torch.int32, device=device)
+        self.list = torch.empty(max(n * cap, 1), **i32)
+        self.count = torch.zeros(max(n, 1), **i32)
+        self.ref_cell = torch.zeros(max(n, 1), **i32)
+        real = torch.int32 if precision == GIC_FP32 else torch.float64
+        self.ref_pos = torch.zeros((max(n, 1), 4), dtype=real, device=device)
+        self.slot = torch.zeros(max(n, 1), **i32)
+        self.cur = torch.zeros(max(n, 1), **i32)
+        self.at = torch.zeros(max(n, 1), **i32)
+        self.flags = torch.zeros(8, **i32)
+
+    def struct(self) -> GicNeighbors:
+        return GicNeighbors(self.n, self.cap, self.skin, _ptr(self.list), _ptr(self.count), _ptr(self.ref_cell),
+                            _ptr(self.ref_pos), _ptr(self.slot), _ptr(self.cur), _ptr(self.at), _ptr(self.flags))
+
+    def builds(self) -> int:
+        return int(self.flags[4].item())
+
+    def overflowed(self) -> bool:
+        return bool(int(self.flags[1].item()) & 2)
+
+
+def gic_contact_verlet(grid: GicGrid, params: GicParams, st: State, cell_table, nb: Neighbors, F_c, stream=None):
+    s, b = st.struct(), nb.struct()
+    _check(lib().gic_contact_verlet(C.byref(grid), C.byref(params), C.byref(s), _ptr(cell_table), C.byref(b), _ptr(F_c),
+                                    _stream(stream)), "gic_contact_verlet")
+
+
+def gic_neighbors_reset(nb: Neighbors, stream=None):
+    b = nb.struct()
+    _check(lib().gic_neighbors_reset(C.byref(b), _stream(stream)), "gic_neighbors_reset")
 
 
 def gic_g2p_couple(grid: GicGrid, params: GicParams, st: State, u, v, w, p, alpha_f, F_fl, a_f, alpha_f_p=None,

@@ -35,10 +35,13 @@ class Simulator:
     grid / params: objects with the fields of GicGrid / GicParams (e.g.
     gic_inputs.Grid / Params).  The initial state comes from the canonical
     encoding (cell int32 [n,3], q uint32 [n,3], r float32 [n], v float32 [n,3])
-    as host or device tensors.
+    as host or device tensors.  verlet_skin (metres): contact through Verlet
+    lists with that skin (gic_contact_verlet, cap partners per granule)
+    instead of walking the cell table every substep (gic_contact).
     """
 
-    def __init__(self, grid, params, n: int, precision: int = GIC_FP32, device="cuda"):
+    def __init__(self, grid, params, n: int, precision: int = GIC_FP32, device="cuda",
+                 verlet_skin: Optional[float] = None, verlet_cap: int = 48):
         self.grid_obj = grid
         self.params_obj = params
         self.grid = gic.make_grid(grid)
@@ -65,6 +68,10 @@ class Simulator:
                    torch.zeros(nx * ny * (nz + 1), dtype=self.real, device=device))
         self.sums = torch.zeros(2, dtype=torch.float64, device=device)
         self.fluid: Optional[DeviceFluid] = None
+        self.nb: Optional[gic.Neighbors] = None
+        if verlet_skin is not None:
+            self.nb = gic.Neighbors(n, precision, cap=verlet_cap, skin=verlet_skin, device=device)
+            gic.gic_neighbors_reset(self.nb)
 
     # ------------------------------------------------------------ inputs
     def set_fluid(self, u, v, w, p, alpha_f):
@@ -77,10 +84,20 @@ class Simulator:
         qi = q64.to(torch.int32)  # the 30-bit fractions fit in int32
         gic.gic_pack(self.grid, dev(cell_xyz, torch.int32), dev(qi, torch.int32), dev(r, torch.float32),
                      dev(v, torch.float32), self.A, stream)
+        if self.nb is not None:  # radii may have changed
+            gic.gic_neighbors_reset(self.nb, stream)
 
     @classmethod
-    def from_problem(cls, prob, precision=GIC_FP32, device="cuda"):
-        sim = cls(prob.grid, prob.params, prob.n, precision, device)
+    def from_problem(cls, prob, precision=GIC_FP32, device="cuda", verlet: bool = True):
+        """Simulator of a gic_inputs.Problem; verlet: Verlet lists with a skin
+        of 0.15 r_max (48 partners per granule, 96 when radii vary by more
+        than 1.5x)."""
+        skin = cap = None
+        if verlet and prob.n > 0:
+            r = prob.r
+            skin = 0.15 * float(r.max())
+            cap = 48 if float(r.max()) <= 1.5 * float(r.min()) else 96
+        sim = cls(prob.grid, prob.params, prob.n, precision, device, verlet_skin=skin, verlet_cap=cap or 48)
         sim.set_fluid(prob.u, prob.vf, prob.wf, prob.p, prob.alpha_f)
         sim.set_state(prob.cell, prob.q, prob.r, prob.v)
         return sim
@@ -90,12 +107,20 @@ class Simulator:
         """One SandSubstep: A (current) -> sort -> B -> forces -> A (next)."""
         F = self.fluid
         gic.gic_sort(self.grid, self.A, self.B, self.perm, self.table, self.ws, stream)
-        gic.gic_contact(self.grid, self.params, self.B, self.table, self.F_c, stream)
+        self.contact(stream)
         gic.gic_g2p_couple(self.grid, self.params, self.B, F.u, F.v, F.w, F.p, F.alpha_f, self.F_fl, self.a_f,
                            self.alpha_f_p, stream)
         gic.gic_integrate(self.grid, self.params, self.B, self.F_c, self.F_fl, self.a_f, self.A, self.f_ex, stream)
         gic.gic_p2g(self.grid, self.params, self.B, self.A, self.f_ex, self.alpha_s if alpha else None,
                     self.Fs if transfer else (None, None, None), self.sums if (sums and alpha) else None, stream)
+
+    def contact(self, stream=None):
+        """a2 on the sorted state B: Verlet lists when configured, else the
+        cell-table walk."""
+        if self.nb is not None:
+            gic.gic_contact_verlet(self.grid, self.params, self.B, self.table, self.nb, self.F_c, stream)
+        else:
+            gic.gic_contact(self.grid, self.params, self.B, self.table, self.F_c, stream)
 
     def substep_probe(self, acc, stream=None):
         """substep() with CUDA events around every entry point: appends
@@ -112,7 +137,7 @@ class Simulator:
             acc.setdefault(name, []).append((a, b))
 
         timed("gic_sort", lambda: gic.gic_sort(self.grid, self.A, self.B, self.perm, self.table, self.ws, s))
-        timed("gic_contact", lambda: gic.gic_contact(self.grid, self.params, self.B, self.table, self.F_c, s))
+        timed("gic_contact", lambda: self.contact(s))
         timed("gic_g2p_couple", lambda: gic.gic_g2p_couple(self.grid, self.params, self.B, F.u, F.v, F.w, F.p,
                                                             F.alpha_f, self.F_fl, self.a_f, self.alpha_f_p, s))
         timed("gic_integrate", lambda: gic.gic_integrate(self.grid, self.params, self.B, self.F_c, self.F_fl,

@@ -1,0 +1,124 @@
+"""Verlet-list contact (gic_contact_verlet) against the cell-table walk
+(gic_contact) and the oracle: same forces (the pair sums in another order),
+rebuilds exactly when a granule has moved more than skin / 2, and a list
+overflow that falls back to rebuilding every call."""
+import numpy as np
+import pytest
+import torch
+
+import gic_inputs as gi
+import oracle
+from gpu_util import FP32, FP64, by_id, oracle_inputs, shuffled, tol_force
+from paper_2504_00745_gb300 import gic
+from paper_2504_00745_gb300.window import Simulator
+
+pytestmark = pytest.mark.gpu
+PRECS = [FP32, FP64]
+
+
+def _forces(sim, verlet):
+    gic.gic_sort(sim.grid, sim.A, sim.B, sim.perm, sim.table, sim.ws)
+    if verlet:
+        gic.gic_contact_verlet(sim.grid, sim.params, sim.B, sim.table, sim.nb, sim.F_c)
+    else:
+        gic.gic_contact(sim.grid, sim.params, sim.B, sim.table, sim.F_c)
+    torch.cuda.synchronize()
+    return by_id(sim.F_c, sim.B.id)[:, :3].astype(np.float64)
+
+
+def _tol(prob, prec, F):
+    return (tol_force(prob, FP32) + 1e-5 * np.abs(F).max()) if prec == FP32 else 1e-12 * np.abs(F).max()
+
+
+@pytest.mark.parametrize("name", ["dense_block", "random_cloud"])
+@pytest.mark.parametrize("prec", PRECS)
+def test_verlet_forces_match_cell_walk_and_oracle(name, prec):
+    prob = shuffled(gi.make(name))
+    sim = Simulator.from_problem(prob, prec)
+    assert sim.nb is not None
+    Fv = _forces(sim, True)  # first call builds
+    Fv2 = _forces(sim, True)  # second call walks the lists
+    Fc = _forces(sim, False)
+    assert sim.nb.builds() == 1
+    x, v, r = oracle_inputs(prob)
+    Fo, _ = oracle.contact(prob.grid, prob.params, x, v, r)
+    for F in (Fv, Fv2, Fc):
+        assert np.abs(F - Fo).max() <= _tol(prob, prec, Fo)
+    assert gic.gic_check_status() == 0
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_verlet_rebuilds_only_past_half_skin(prec):
+    prob = gi.make("dense_block")
+    skin = 0.2 * float(prob.r.max())
+    sim = Simulator(prob.grid, prob.params, prob.n, prec, verlet_skin=skin)
+    sim.set_fluid(prob.u, prob.vf, prob.wf, prob.p, prob.alpha_f)
+    sim.set_state(prob.cell, prob.q, prob.r, prob.v)
+    _forces(sim, True)
+    assert sim.nb.builds() == 1
+    # move every granule by 0.4 skin (< skin / 2): the lists stay
+    x0 = prob.positions()
+    rng = np.random.default_rng(3)
+    d = rng.normal(size=x0.shape)
+    d *= (0.4 * skin / np.linalg.norm(d, axis=1))[:, None]
+    for frac, builds in ((1.0, 1), (1.3, 2)):  # 0.4 skin, then 0.52 skin
+        cell, q = gi.encode_positions(x0 + frac * d, prob.grid)
+        # repack A directly: set_state would request a rebuild
+        dev = lambda a, dt: torch.as_tensor(a).to(device="cuda", dtype=dt).contiguous()
+        gic.gic_pack(sim.grid, dev(cell, torch.int32), dev(q.astype(np.int64), torch.int32),
+                     dev(prob.r, torch.float32), dev(prob.v, torch.float32), sim.A)
+        F = _forces(sim, True)
+        assert sim.nb.builds() == builds
+        Fo, _ = oracle.contact(prob.grid, prob.params, gi.decode_positions(cell, q, prob.grid), prob.v, prob.r)
+        assert np.abs(F - Fo).max() <= _tol(prob, prec, Fo)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_verlet_overflow_rebuilds_every_call(prec):
+    prob = shuffled(gi.make("dense_block"))
+    sim = Simulator(prob.grid, prob.params, prob.n, prec, verlet_skin=0.15 * float(prob.r.max()), verlet_cap=2)
+    sim.set_fluid(prob.u, prob.vf, prob.wf, prob.p, prob.alpha_f)
+    sim.set_state(prob.cell, prob.q, prob.r, prob.v)
+    x, v, r = oracle_inputs(prob)
+    Fo, _ = oracle.contact(prob.grid, prob.params, x, v, r)
+    for k in range(3):
+        F = _forces(sim, True)
+        assert sim.nb.overflowed()
+        assert sim.nb.builds() == k + 1
+        assert np.abs(F - Fo).max() <= _tol(prob, prec, Fo)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_verlet_window_matches_cell_walk_window(prec):
+    """20 substeps of the dense block (contacts form and break): the Verlet
+    path and the cell walk agree to the rounding of the pair-sum order."""
+    prob = shuffled(gi.make("dense_block"))
+    out = []
+    for verlet in (True, False):
+        sim = Simulator.from_problem(prob, prec, verlet=verlet)
+        sim.run(20)
+        x, v = sim.positions()
+        out.append((x.cpu().numpy(), v.cpu().numpy(), sim.alpha_s.cpu().numpy()))
+        if verlet:
+            assert sim.nb.builds() >= 1
+    (xa, va, aa), (xb, vb, ab) = out
+    dx = prob.grid.dx
+    assert np.abs(xa - xb).max() <= (1e-6 if prec == FP32 else 1e-13) * dx
+    vs = np.linalg.norm(vb, axis=1).max()
+    assert np.linalg.norm(va - vb, axis=1).max() <= (1e-5 if prec == FP32 else 1e-11) * vs
+    assert np.abs(aa - ab).max() <= 1e-10
+
+
+def test_verlet_argument_errors():
+    prob = gi.make("dense_block")
+    sim = Simulator.from_problem(prob, FP32)
+    nb = gic.Neighbors(prob.n + 1, FP32, cap=8, skin=1e-4)
+    gic.gic_sort(sim.grid, sim.A, sim.B, sim.perm, sim.table, sim.ws)
+    with pytest.raises(gic.GicError, match="granules"):
+        gic.gic_contact_verlet(sim.grid, sim.params, sim.B, sim.table, nb, sim.F_c)
+    bad = gic.Neighbors(prob.n, FP32, cap=0, skin=1e-4)
+    with pytest.raises(gic.GicError, match="cap"):
+        gic.gic_contact_verlet(sim.grid, sim.params, sim.B, sim.table, bad, sim.F_c)
+    neg = gic.Neighbors(prob.n, FP32, cap=8, skin=-1.0)
+    with pytest.raises(gic.GicError, match="skin"):
+        gic.gic_contact_verlet(sim.grid, sim.params, sim.B, sim.table, neg, sim.F_c)
