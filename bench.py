@@ -27,8 +27,17 @@ sys.path.insert(0, ROOT)
 METRIC = "granule-substeps/s fwd & adjoint, FP32 vs FP64 on 1 GB300; % HBM roofline"
 UNIT = "granule-substeps/s"
 # algorithmic bytes per granule-substep of each step (FP32 path): what the
-# method must move, 12 B per 3-vector, state = 36 B
-ALGO_BYTES = {"gic_sort": 88, "gic_contact": 48, "gic_g2p_couple": 65, "gic_integrate": 120, "gic_p2g": 54}
+# method must move, 12 B per 3-vector, state = 36 B.  P2G scatters F_s from
+# the old positions every substep (cell + pos 20 B, f_ex 12 B) and alpha_s
+# from the new ones once per fluid step (20 B more on the last substep).
+ALGO_BYTES = {"gic_sort": 88, "gic_contact": 48, "gic_g2p_couple": 65, "gic_integrate": 120, "gic_p2g": 32}
+P2G_ALPHA_BYTES = 20
+
+
+def algo_bytes(name, K):
+    """Algorithmic bytes per granule of one call of `name`, averaged over a
+    K-substep window."""
+    return ALGO_BYTES[name] + (P2G_ALPHA_BYTES / K if name == "gic_p2g" else 0.0)
 
 
 def parse():
@@ -247,11 +256,12 @@ def run_gpu(args, ws, rank, local):
         end = torch.cuda.Event(enable_timing=True)
         start.record(stream)
         sim.zero_transfer()
-        for s in range(K):
+        for s in range(K):  # alpha_s at the final positions only (Alg. 1), F_s every substep (Alg. 2)
+            last = s == K - 1
             if probe:
-                sim.substep_probe(ev_acc, stream=stream)
+                sim.substep_probe(ev_acc, stream=stream, alpha=last)
             else:
-                sim.substep()
+                sim.substep(alpha=last, sums=last)
         end.record(stream)
         return start, end
 
@@ -286,11 +296,12 @@ def run_gpu(args, ws, rank, local):
     except Exception:
         pass
     hbm = float(peaks.get("hbm_gbs", 6800.0))
-    achieved = ALGO_BYTES[dom] * n / (per_call[dom] / 1000.0) / 1e9
+    achieved = algo_bytes(dom, K) * n / (per_call[dom] / 1000.0) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": None, "kernel": dom, "peak_source": "measured" if peaks else "fallback",
                 "per_call_ms": per_call,
-                "per_call_frac": {k: ALGO_BYTES[k] * n / (v / 1000.0) / 1e9 / hbm for k, v in per_call.items()}}
+                "per_call_frac": {k: algo_bytes(k, K) * n / (v / 1000.0) / 1e9 / hbm for k, v in per_call.items()},
+                "algo_bytes_per_granule": {k: algo_bytes(k, K) for k in per_call}}
 
     # e2e through the C ABI with host buffers (copies inside the timed region)
     e2e = run_e2e(prob, sim, gic, torch, np, dev, stream, max(1, min(args.steps, 3)))
@@ -315,6 +326,8 @@ def run_gpu(args, ws, rank, local):
             "vs_baseline": None, "dtype": "f32 (fixed-point positions, f64 alpha_s)", "data": "synthetic",
             "config": {"workload": prob.name, "granules": n, "grid": [prob.grid.nx, prob.grid.ny, prob.grid.nz],
                        "substeps_per_step": K, "dt_sub": prob.params.dt_sub, "precision": "fp32",
+                       "schedule": "one fluid step: K substeps of sort, contact (Verlet lists, skin 0.15 r_max), "
+                                   "G2P couple, integrate, P2G of F_s; alpha_s and sums at the final positions",
                        "l2": "flushed between steps (512 MB write), state reset to the initial packing",
                        "wall_s": wall},
             "roofline": roofline, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
@@ -436,11 +449,12 @@ def run_fwd(prob, prec, gic, torch, dev, stream, steps=2, warmup=1):
         e = torch.cuda.Event(enable_timing=True)
         s.record(stream)
         sim.zero_transfer()
-        for _ in range(K):
+        for k in range(K):
+            last = k == K - 1
             if it >= warmup:
-                sim.substep_probe(ev_acc, stream=stream)
+                sim.substep_probe(ev_acc, stream=stream, alpha=last)
             else:
-                sim.substep()
+                sim.substep(alpha=last, sums=last)
         e.record(stream)
         torch.cuda.synchronize()
         if it >= warmup:

@@ -313,11 +313,14 @@ int gic_p2g_adj(const GicGrid* grid, const GicParams* params, const GicGranules*
  * state, the permutation and the per-granule force arrays). */
 int gic_window_workspace_size(const GicGrid* grid, int64_t n, int32_t precision, size_t* bytes);
 
-/* K substeps of Alg. 2 (SandSubstep): per substep gic_sort, gic_contact,
- * gic_g2p_couple, gic_integrate, gic_p2g.  `state` is updated in place and
- * ends in the sorted order of the last substep (state->id, if set, maps it
- * back).  alpha_s (may be NULL) is the last substep's; F_s (all three or none)
- * accumulates over the K substeps; sums2 (may be NULL) is the last substep's.
+/* K substeps of Alg. 2 (SandSubstep): per substep gic_sort, contact,
+ * gic_g2p_couple, gic_integrate, gic_p2g.  Contact is gic_contact_verlet
+ * (skin 0.075 h_c, 64 partners per granule, lists in the workspace) when
+ * state->id is set, else gic_contact.  `state` is updated in place and ends
+ * in the sorted order of the last substep (state->id, if set, maps it back).
+ * alpha_s (may be NULL) is computed once, at the final positions (Alg. 1
+ * CalTargetFraction); F_s (all three or none) accumulates over the K
+ * substeps; sums2 (may be NULL) goes with alpha_s.
  * cell_table as for gic_sort; ws of gic_window_workspace_size bytes,
  * 256-byte aligned.  Asynchronous on `stream`. */
 int gic_window_forward(const GicGrid* grid, const GicParams* params, GicGranules* state, int32_t K, const void* u,

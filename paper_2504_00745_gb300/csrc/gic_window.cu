@@ -8,8 +8,10 @@
 
 namespace gic {
 
+constexpr int kWindowNbCap = 64;  // Verlet partners per granule in the window's lists
+
 struct WindowLayout {
-  size_t sort_ws, off_sort, off_state_b, off_perm, off_fc, off_ffl, off_af, off_fex, total;
+  size_t sort_ws, off_sort, off_state_b, off_perm, off_fc, off_ffl, off_af, off_fex, off_nb, total;
   // host variant only: device copies of inputs and outputs
   size_t off_cxyz, off_q, off_r, off_v, off_fields, off_alpha, off_fs, off_sums, off_x, off_vout, off_state_a,
       off_table, host_total;
@@ -41,6 +43,8 @@ static int window_layout(const GicGrid* grid, int64_t n, int32_t precision, Wind
   off += vec;
   L->off_fex = off;
   off += vec;
+  L->off_nb = off;  // Verlet lists: list, count, ref_cell, ref_pos, slot, cur, at, flags
+  off += al(4 * nn * kWindowNbCap) + 5 * al(4 * nn) + al(4 * real * nn) + al(32);
   L->total = off;
   // host variant
   const GicGrid& g = *grid;
@@ -140,13 +144,44 @@ extern "C" int gic_window_forward(const GicGrid* grid, const GicParams* params, 
   void* Ffl = base + L.off_ffl;
   void* af = base + L.off_af;
   void* fex = base + L.off_fex;
+  // Verlet lists (skin 0.15 h_c / 2, an upper bound of 0.15 r_max) when the state carries ids
+  GicNeighbors nb;
+  const bool verlet = state->id != nullptr && state->n > 0;
+  if (verlet) {
+    size_t nn = (size_t)state->n;
+    size_t real = state->precision == GIC_FP32 ? 4 : 8;
+    char* q = base + L.off_nb;
+    nb.n = state->n;
+    nb.cap = kWindowNbCap;
+    nb.skin = 0.075 * grid->dx / grid->k_contact;
+    nb.list = (int32_t*)q;
+    q += al(4 * nn * kWindowNbCap);
+    nb.count = (int32_t*)q;
+    q += al(4 * nn);
+    nb.ref_cell = (int32_t*)q;
+    q += al(4 * nn);
+    nb.ref_pos = q;
+    q += al(4 * real * nn);
+    nb.slot = (int32_t*)q;
+    q += al(4 * nn);
+    nb.cur = (int32_t*)q;
+    q += al(4 * nn);
+    nb.at = (int32_t*)q;
+    q += al(4 * nn);
+    nb.flags = (uint32_t*)q;
+    if ((rc = gic_neighbors_reset(&nb, stream))) return rc;
+  }
+  // alpha_s once, at the final positions (Alg. 1 CalTargetFraction); F_s every substep (Alg. 2)
   for (int s = 0; s < K; ++s) {
     bool last = s == K - 1;
     if ((rc = gic_sort(grid, state, &B, perm, cell_table, base + L.off_sort, L.sort_ws, stream))) return rc;
-    if ((rc = gic_contact(grid, params, &B, cell_table, Fc, stream))) return rc;
+    rc = verlet ? gic_contact_verlet(grid, params, &B, cell_table, &nb, Fc, stream)
+                : gic_contact(grid, params, &B, cell_table, Fc, stream);
+    if (rc) return rc;
     if ((rc = gic_g2p_couple(grid, params, &B, u, v, w, p, alpha_f, Ffl, af, nullptr, stream))) return rc;
     if ((rc = gic_integrate(grid, params, &B, Fc, Ffl, af, state, fex, stream))) return rc;
-    if ((rc = gic_p2g(grid, params, &B, state, fex, alpha_s, Fs_u, Fs_v, Fs_w, last ? sums2 : nullptr, stream)))
+    if ((rc = gic_p2g(grid, params, &B, state, fex, last ? alpha_s : nullptr, Fs_u, Fs_v, Fs_w,
+                      last ? sums2 : nullptr, stream)))
       return rc;
   }
   return GIC_OK;

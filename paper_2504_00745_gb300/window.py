@@ -122,7 +122,7 @@ class Simulator:
         else:
             gic.gic_contact(self.grid, self.params, self.B, self.table, self.F_c, stream)
 
-    def substep_probe(self, acc, stream=None):
+    def substep_probe(self, acc, stream=None, alpha: bool = True):
         """substep() with CUDA events around every entry point: appends
         (start, end) event pairs to acc[name] (timing only)."""
         s = torch.cuda.current_stream() if stream is None else stream
@@ -142,17 +142,18 @@ class Simulator:
                                                             F.alpha_f, self.F_fl, self.a_f, self.alpha_f_p, s))
         timed("gic_integrate", lambda: gic.gic_integrate(self.grid, self.params, self.B, self.F_c, self.F_fl,
                                                           self.a_f, self.A, self.f_ex, s))
-        timed("gic_p2g", lambda: gic.gic_p2g(self.grid, self.params, self.B, self.A, self.f_ex, self.alpha_s, self.Fs,
-                                              self.sums, s))
+        timed("gic_p2g", lambda: gic.gic_p2g(self.grid, self.params, self.B, self.A, self.f_ex,
+                                              self.alpha_s if alpha else None, self.Fs,
+                                              self.sums if alpha else None, s))
 
     def zero_transfer(self):
         for f in self.Fs:
             f.zero_()
 
-    def run(self, K: int, stream=None, alpha_every: bool = True):
-        """K substeps; F_s accumulates from zero; alpha_s and sums are those of
-        the last substep (every substep recomputes them unless alpha_every is
-        False, in which case only the last does)."""
+    def run(self, K: int, stream=None, alpha_every: bool = False):
+        """K substeps (one fluid step); F_s accumulates from zero over them
+        (Alg. 2); alpha_s and sums are computed at the final positions only
+        (Alg. 1 CalTargetFraction), or after every substep if alpha_every."""
         self.zero_transfer()
         for s in range(K):
             last = s == K - 1
