@@ -30,14 +30,17 @@ UNIT = "granule-substeps/s"
 # method must move, 12 B per 3-vector, state = 36 B.  P2G scatters F_s from
 # the old positions every substep (cell + pos 20 B, f_ex 12 B) and alpha_s
 # from the new ones once per fluid step (20 B more on the last substep).
-ALGO_BYTES = {"gic_sort": 88, "gic_contact": 48, "gic_g2p_couple": 65, "gic_integrate": 120, "gic_p2g": 32}
+# The fused substep (contact, G2P, integrate, P2G after the sort) reads the
+# sorted state and writes the next one: 36 + 36 B.
+ALGO_BYTES = {"gic_sort": 88, "gic_contact": 48, "gic_g2p_couple": 65, "gic_integrate": 120, "gic_p2g": 32,
+              "gic_substep": 72}
 P2G_ALPHA_BYTES = 20
 
 
 def algo_bytes(name, K):
     """Algorithmic bytes per granule of one call of `name`, averaged over a
     K-substep window."""
-    return ALGO_BYTES[name] + (P2G_ALPHA_BYTES / K if name == "gic_p2g" else 0.0)
+    return ALGO_BYTES[name] + (P2G_ALPHA_BYTES / K if name in ("gic_p2g", "gic_substep") else 0.0)
 
 
 def parse():

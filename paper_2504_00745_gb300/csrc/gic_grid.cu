@@ -2,41 +2,9 @@
 // fluid fraction) and a5 P2G (volume fraction, exchange momentum), with
 // adjoints.  One thread per granule; granules arrive Morton-sorted, so the
 // lanes of a warp read and write the same few MAC cells.
-#include <climits>
-
-#include "gic_interp.cuh"
+#include "gic_grid.cuh"
 
 namespace gic {
-
-template <typename T>
-struct Fields {
-  const T* u;
-  const T* v;
-  const T* w;
-  const T* p;
-  const T* af;
-};
-
-template <typename T>
-__device__ __forceinline__ FieldLoad<T> face_loader(const DGrid& G, const T* f, int comp) {
-  FieldLoad<T> L;
-  L.f = f;
-  L.nsx = G.nx + (comp == 0);
-  L.nsy = G.ny + (comp == 1);
-  return L;
-}
-
-template <typename T>
-__device__ __forceinline__ GradPLoad<T> gradp_loader(const DGrid& G, const T* p, int comp) {
-  GradPLoad<T> L;
-  L.p = p;
-  L.nx = G.nx;
-  L.ny = G.ny;
-  L.nz = G.nz;
-  L.comp = comp;
-  L.inv_dx = (T)G.inv_dx;
-  return L;
-}
 
 // ------------------------------------------------------------------ G2P
 
@@ -50,36 +18,21 @@ __global__ void __launch_bounds__(256, 4) k_g2p(DGrid G, DParams<T> P, int64_t n
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   pos_t<T> pi = pos[i];
-  vec_t<T> vi = vel[i];
-  int m[3];
-  T t[3];
-  granule_mac<T>(G, cell[i], pi, m, t);
-  const T* uvw[3] = {Fd.u, Fd.v, Fd.w};
-  T uf[3], gp[3];
-  T inv_dx = (T)G.inv_dx;
-#pragma unroll
-  for (int comp = 0; comp < 3; ++comp) {
-    Stencil3<T> S = make_stencil<T>(G, m, t, comp);
-    uf[comp] = interp<T>(S, face_loader<T>(G, uvw[comp], comp), inv_dx, nullptr);
-    gp[comp] = interp<T>(S, gradp_loader<T>(G, Fd.p, comp), inv_dx, nullptr);
-  }
-  T r = radius_of(pi);
-  T V = T(4.0 / 3.0 * kPi) * r * r * r;
-  T d0 = uf[0] - vi.x, d1 = uf[1] - vi.y, d2 = uf[2] - vi.z;
-  T sp = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
-  T cd = P.c_drag * T(kPi) * r * r * P.rho_f * sp;
-  F_fl[i] = make_vec<T>(cd * d0 - V * gp[0], cd * d1 - V * gp[1], cd * d2 - V * gp[2]);
-  if (P.rho_f > T(0))
-    a_f[i] = make_vec<T>(P.g[0] - gp[0] * P.inv_rho_f, P.g[1] - gp[1] * P.inv_rho_f, P.g[2] - gp[2] * P.inv_rho_f);
-  else
-    a_f[i] = make_vec<T>(P.g[0], P.g[1], P.g[2]);
+  int32_t ci = cell[i];
+  T F[3], a[3];
+  T sp = g2p_granule(G, P, Fd, ci, pi, vel[i], F, a);
+  F_fl[i] = make_vec<T>(F[0], F[1], F[2]);
+  a_f[i] = make_vec<T>(a[0], a[1], a[2]);
   if (afp) {
+    int m[3];
+    T t[3];
+    granule_mac<T>(G, ci, pi, m, t);
     Stencil3<T> S = make_stencil<T>(G, m, t, 3);
     FieldLoad<T> L;
     L.f = Fd.af;
     L.nsx = G.nx;
     L.nsy = G.ny;
-    afp[i] = interp<T>(S, L, inv_dx, nullptr);
+    afp[i] = interp<T>(S, L, (T)G.inv_dx, nullptr);
   }
   if (!isfinite(sp)) raise_status(status, GIC_STATUS_NONFINITE);
 }
@@ -166,72 +119,6 @@ __global__ void k_alpha_sum(const double* __restrict__ a, int64_t m, double dx3,
     acc += a[i];
   double s = block_sum(acc, s_red);
   if (threadIdx.x == 0) atomicAdd(&sums[0], s * dx3);
-}
-
-// ---- FP32 path: exact fixed-point volume fraction ----
-//
-// alpha_s is accumulated as a 64-bit integer in units of 2^-53: per granule
-// the volume fraction S = V / dx^3 is rounded once to 2^-53; the per-axis
-// tent weights come from the 30-bit fixed-point position as 31-bit integers
-// (exact when the contact cell is the MAC cell), S times their product is
-// formed to 2^-62 and each corner's deposit truncated to 2^-53, and the eighth
-// corner takes the rest, so every granule deposits exactly S; integer atomics
-// make the sum independent of the order of arrival -- bitwise reproducible.
-// k_alpha_finish turns the integers into doubles in place.
-
-constexpr uint32_t kW1 = 1u << 31;  // weight 1.0
-
-// Centred-stencil weights of one axis from the contact coordinate c and the
-// fixed-point offset q: lower sample i0 and integer weights (w0, w1), w0 + w1 = 2^31.
-__device__ __forceinline__ void fixed_axis(const DGrid& G, int c, uint32_t q, int n, int& i0, uint32_t& w1) {
-  int m = mac_of(G, c);
-  unsigned long long N = ((unsigned long long)(c - m * G.k) << kFracBits) | q;  // offset in 2^-30 h_c
-  // P = round(N * 2 / k): the offset inside the MAC cell in units of 2^-31 dx
-  unsigned long long P;
-  if (G.k == 1)
-    P = N << 1;
-  else if (G.k == 2)
-    P = N;
-  else
-    P = (__umul64hi(N << 2, G.kinv64) + 1ull) >> 1;
-  uint32_t p = (uint32_t)P;  // < 2^31
-  if (p >= (1u << 30)) {
-    i0 = m;
-    w1 = p - (1u << 30);
-  } else {
-    i0 = m - 1;
-    w1 = p + (1u << 30);
-  }
-  if (i0 < 0) {
-    i0 = 0;
-    w1 = 0;
-  } else if (i0 > n - 2) {
-    i0 = n - 2;
-    w1 = kW1;
-  }
-}
-
-// An integer-valued float (|v| >= 2^23) as int64, exactly, with integer ops.
-__device__ __forceinline__ long long float_int_to_ll(float v) {
-  uint32_t b = __float_as_uint(v);
-  int e = (int)((b >> 23) & 0xffu) - 127 - 23;
-  long long m = (long long)((b & 0x7fffffu) | 0x800000u);
-  long long r = e >= 0 ? (m << e) : (m >> (-e));
-  return (b >> 31) ? -r : r;
-}
-
-// S = V / dx^3 in 2^-53 units for radius r, rounded, in FP32 double-float
-// arithmetic (r^3 exact to ~2^-46, the constant as a float pair): the FP64
-// pipe of this GPU is 1/64 of the FP32 rate.
-__device__ __forceinline__ unsigned long long volume_fixed(const DGrid& G, float r) {
-  float r2h = r * r;
-  float r2l = fmaf(r, r, -r2h);
-  float r3h = r2h * r;
-  float r3l = fmaf(r2h, r, -r3h) + r2l * r;
-  float sh = r3h * G.vol_fx_hi;
-  float sl = fmaf(r3h, G.vol_fx_hi, -sh) + fmaf(r3h, G.vol_fx_lo, r3l * G.vol_fx_hi);
-  long long a = fabsf(sh) >= 8388608.0f ? float_int_to_ll(sh) : (long long)__float2ll_rn(sh);
-  return (unsigned long long)(a + __float2ll_rn(sl));
 }
 
 // FP64 path: alpha_s(c) = sum_i V_i N(x'_i - x_c) / dx^3 at the new positions, FP64
@@ -342,62 +229,7 @@ __device__ __forceinline__ double i64_scaled_to_double(long long v, int e2) {
   return __longlong_as_double((long long)(sign | (e << 52) | (m & ((1ull << 52) - 1ull))));
 }
 
-// floor(x w / 2^31) for x < 2^63, w <= 2^31, with two 32x32->64 products.
-__device__ __forceinline__ unsigned long long mul31(unsigned long long x, uint32_t w) {
-  unsigned long long hi = (unsigned long long)(uint32_t)(x >> 32) * w;
-  unsigned long long lo = (unsigned long long)(uint32_t)x * w;
-  return (hi << 1) + (lo >> 31);
-}
-
-// FP32-path alpha_s deposits of one granule at its new position: the base
-// sample i0 and the eight integer deposits (2^-53 units) summing to S exactly.
-// S is carried in 2^-62 units through the three per-axis weight products
-// (each truncated once), so a deposit is within ~2^-53 of S w_x w_y w_z; the
-// eighth corner takes S minus the other seven.
-__device__ __forceinline__ void alpha_deposits(const DGrid& G, int32_t cn, uint4 pn, int i0[3], long long v[8],
-                                               unsigned long long& S) {
-  S = volume_fixed(G, __uint_as_float(pn.w));
-  int c3[3] = {cell_x(cn), cell_y(cn), cell_z(cn)};
-  const int nn[3] = {G.nx, G.ny, G.nz};
-  uint32_t w1[3], w0[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    fixed_axis(G, c3[a], pcomp(pn, a), nn[a], i0[a], w1[a]);
-    w0[a] = kW1 - w1[a];
-  }
-  const unsigned long long S9 = S << 9;  // < 2^63
-  unsigned long long sx[2], sxy[4];
-  sx[0] = mul31(S9, w0[0]);
-  sx[1] = mul31(S9, w1[0]);
-#pragma unroll
-  for (int k = 0; k < 4; ++k) sxy[k] = mul31(sx[k & 1], (k & 2) ? w1[1] : w0[1]);
-  long long sum7 = 0;
-#pragma unroll
-  for (int k = 0; k < 7; ++k) {
-    v[k] = (long long)(mul31(sxy[k & 3], (k & 4) ? w1[2] : w0[2]) >> 9);
-    sum7 += v[k];
-  }
-  v[7] = (long long)S - sum7;
-}
-
-// FP32 path of P2G.  One CTA takes 512 consecutive granules of the
-// Morton-sorted state, which occupy a compact block of MAC cells.  When the
-// samples they may touch fit a kP2GTile-entry box, every deposit goes to
-// shared-memory copies of alpha_s and the three F_s grids over that box,
-// held as 32-bit integer limbs (32-bit shared integer atomics run at full
-// rate even when lanes collide, unlike float or 64-bit ones), and the box's
-// non-zero entries then go to global memory with one atomic each; otherwise
-// every deposit is a global atomic.
-//   alpha_s: a deposit (< 2^54 units of 2^-53) is split into three 18-bit
-//   limbs, so up to 2^14 deposits per entry add without overflow -- exact.
-//   F_s: a deposit d is rounded to a multiple of u = M 2^-30, M the CTA's
-//   largest |exch f_ex| component, and q = d / u (|q| <= 2^30) is split into
-//   a signed high and an unsigned low 15-bit limb; the limb sums are exact,
-//   so the only rounding besides the float product d is the 2^-30 M grid.
-// alpha_s stays 64-bit fixed point (exact, order-independent) until
-// k_alpha_finish_f32.
 constexpr int kP2GThreads = 512;
-constexpr int kP2GTile = 1024;
 
 __global__ void __launch_bounds__(kP2GThreads, 2) k_p2g_f32(DGrid G, DParams<float> P, int64_t n,
                                                            const int32_t* __restrict__ cell_old,
@@ -408,178 +240,48 @@ __global__ void __launch_bounds__(kP2GThreads, 2) k_p2g_f32(DGrid G, DParams<flo
                                                            double* __restrict__ alpha, float* __restrict__ Fs_u,
                                                            float* __restrict__ Fs_v, float* __restrict__ Fs_w,
                                                            double* __restrict__ sums) {
-  __shared__ uint32_t s_a[3][kP2GTile];
-  __shared__ int32_t s_fh[3][kP2GTile];
-  __shared__ uint32_t s_fl[3][kP2GTile];
-  __shared__ int s_lo[3], s_hi[3];
-  __shared__ unsigned s_M;
+  __shared__ P2GShared sh;
   const int64_t i = blockIdx.x * (int64_t)kP2GThreads + threadIdx.x;
   const bool valid = i < n;
   const bool do_a = alpha != nullptr, do_f = Fs_u != nullptr;  // uniform over the launch
-  if (threadIdx.x < 3) {
-    s_lo[threadIdx.x] = INT_MAX;
-    s_hi[threadIdx.x] = INT_MIN;
-  }
-  if (threadIdx.x == 0) s_M = 0u;
-
-  // box of every sample this CTA may touch: a stencil's base is the MAC cell
-  // m or m - 1 on each axis, and it reaches one sample further
-  int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {INT_MIN, INT_MIN, INT_MIN};
+  p2g_box_init(sh);
+  P2GExtent ext;
   int32_t cn = 0, co = 0;
   float fc[3] = {0.f, 0.f, 0.f};
-  float M = 0.f;
   if (valid) {
-    if (do_a) cn = cell_new[i];
+    if (do_a) {
+      cn = cell_new[i];
+      ext.add_cell(G, cn);
+    }
     if (do_f) {
       co = cell_old[i];
+      ext.add_cell(G, co);
       float4 f = fex[i];
       fc[0] = P.exch * f.x;
       fc[1] = P.exch * f.y;
       fc[2] = P.exch * f.z;
-      M = fmaxf(fabsf(fc[0]), fmaxf(fabsf(fc[1]), fabsf(fc[2])));
-      if (!(M <= 3.0e38f)) M = INFINITY;  // NaN or inf: no fixed-point grid for this CTA
-    }
-    int32_t cs[2] = {do_a ? cn : co, do_f ? co : cn};
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      int c3[3] = {cell_x(cs[h]), cell_y(cs[h]), cell_z(cs[h])};
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        int m = mac_of(G, c3[a]);
-        lo[a] = min(lo[a], m - 1);
-        hi[a] = max(hi[a], m + 1);
-      }
+      ext.add_force(fc);
     }
   }
-  __syncthreads();
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    int l = __reduce_min_sync(0xffffffffu, lo[a]);
-    int h = __reduce_max_sync(0xffffffffu, hi[a]);
-    if (lane_id() == 0) {
-      atomicMin(&s_lo[a], l);
-      atomicMax(&s_hi[a], h);
-    }
-  }
-  if (do_f) {  // non-negative floats order like their bit patterns
-    unsigned mb = __reduce_max_sync(0xffffffffu, __float_as_uint(M));
-    if (lane_id() == 0) atomicMax(&s_M, mb);
-  }
-  __syncthreads();
-  const int bx = max(s_lo[0], 0), by = max(s_lo[1], 0), bz = max(s_lo[2], 0);
-  const int ex = s_hi[0] - bx + 1, ey = s_hi[1] - by + 1, ez = s_hi[2] - bz + 1;
-  // every CTA holds at least one granule, so the box is not empty
-  const bool tile = (int64_t)ex * ey * ez <= kP2GTile;
-  const float Mc = __uint_as_float(s_M);
-  const bool ftile = tile && Mc >= 1e-30f && Mc <= 3.0e38f;  // F_s through the fixed-point tile
-  const float unit = Mc * 0x1p-30f, inv_unit = ftile ? 0x1p30f / Mc : 0.f;
-  const int vol = tile ? ex * ey * ez : 0;
-  const int sy = ex, sz = ex * ey;
-  for (int e = threadIdx.x; e < vol; e += kP2GThreads) {
-    if (do_a) s_a[0][e] = s_a[1][e] = s_a[2][e] = 0u;
-    if (ftile) {
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        s_fh[c][e] = 0;
-        s_fl[c][e] = 0u;
-      }
-    }
-  }
-  if (tile) __syncthreads();
-
+  const P2GBox B = p2g_box(sh, ext, do_a, do_f);
+  float* Fs[3] = {Fs_u, Fs_v, Fs_w};
   unsigned long long S = 0;
   if (valid && do_a) {
     int ia[3];
     long long va[8];
     alpha_deposits(G, cn, pos_new[i], ia, va, S);
-    if (tile) {
-      const int e0 = (ia[0] - bx) + sy * (ia[1] - by) + sz * (ia[2] - bz);
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const int e = e0 + (k & 1) + ((k >> 1) & 1) * sy + (k >> 2) * sz;
-        const unsigned long long v = (unsigned long long)va[k];
-        atomicAdd(&s_a[0][e], (uint32_t)(v & 0x3ffffull));
-        atomicAdd(&s_a[1][e], (uint32_t)((v >> 18) & 0x3ffffull));
-        atomicAdd(&s_a[2][e], (uint32_t)(v >> 36));
-      }
-    } else {
-      unsigned long long* g0 = (unsigned long long*)alpha + sample_index(G.nx, G.ny, ia[0], ia[1], ia[2]);
-      const int64_t gy = G.nx, gz = (int64_t)G.nx * G.ny;
-#pragma unroll
-      for (int k = 0; k < 8; ++k)
-        if (va[k]) atomicAdd(g0 + (k & 1) + ((k >> 1) & 1) * gy + (k >> 2) * gz, (unsigned long long)va[k]);
-    }
+    p2g_add_alpha(sh, B, G, (unsigned long long*)alpha, ia, va);
   }
   if (valid && do_f) {
     int m[3];
     float t[3];
     granule_mac<float>(G, co, pos_old[i], m, t);
-    float* Fs[3] = {Fs_u, Fs_v, Fs_w};
 #pragma unroll
-    for (int comp = 0; comp < 3; ++comp) {
-      Stencil3<float> St = make_stencil<float>(G, m, t, comp);
-      const float wx = St.w[0], wy = St.w[1], wz = St.w[2];
-      const float fx0 = (1.f - wx) * fc[comp], fx1 = wx * fc[comp];
-      const float wyz[4] = {(1.f - wy) * (1.f - wz), wy * (1.f - wz), (1.f - wy) * wz, wy * wz};
-      if (ftile) {
-        const int e0 = (St.i0[0] - bx) + sy * (St.i0[1] - by) + sz * (St.i0[2] - bz);
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          const int q = __float2int_rn(((k & 1) ? fx1 : fx0) * wyz[k >> 1] * inv_unit);
-          const int e = e0 + (k & 1) + ((k >> 1) & 1) * sy + (k >> 2) * sz;
-          atomicAdd(&s_fh[comp][e], q >> 15);
-          atomicAdd(&s_fl[comp][e], (uint32_t)(q & 0x7fff));
-        }
-      } else {
-        const int nsx = G.nx + (comp == 0), nsy = G.ny + (comp == 1);
-        float* g0 = Fs[comp] + sample_index(nsx, nsy, St.i0[0], St.i0[1], St.i0[2]);
-        const int64_t gy = nsx, gz = (int64_t)nsx * nsy;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          const float d = ((k & 1) ? fx1 : fx0) * wyz[k >> 1];
-          if (d != 0.f) atomicAdd(g0 + (k & 1) + ((k >> 1) & 1) * gy + (k >> 2) * gz, d);
-        }
-      }
-    }
+    for (int comp = 0; comp < 3; ++comp) p2g_add_face(sh, B, G, Fs[comp], comp, make_stencil<float>(G, m, t, comp),
+                                                      fc[comp]);
   }
-
-  if (tile) {  // the box's non-zero entries to global memory
-    __syncthreads();
-    unsigned long long* acc = (unsigned long long*)alpha;
-    float* Fs[3] = {Fs_u, Fs_v, Fs_w};
-    // e = lx + ex (ly + ey lz); (e + 1/2) / d stays >= 1/(2 d) away from an
-    // integer, far beyond the float error for e, d <= 1024
-    const float rx = 1.f / (float)ex, rxy = 1.f / (float)sz;
-    for (int e = threadIdx.x; e < vol; e += kP2GThreads) {
-      int lz = (int)(((float)e + 0.5f) * rxy);
-      int r = e - lz * sz;
-      int ly = (int)(((float)r + 0.5f) * rx);
-      int lx = r - ly * ex;
-      int gx = bx + lx, gy = by + ly, gz = bz + lz;
-      if (do_a) {
-        unsigned long long a = (unsigned long long)s_a[0][e] + ((unsigned long long)s_a[1][e] << 18) +
-                               ((unsigned long long)s_a[2][e] << 36);
-        if (a) atomicAdd(&acc[sample_index(G.nx, G.ny, gx, gy, gz)], a);
-      }
-      if (ftile) {
-#pragma unroll
-        for (int comp = 0; comp < 3; ++comp) {
-          long long q = (long long)s_fh[comp][e] * (1ll << 15) + (long long)s_fl[comp][e];
-          if (q) atomicAdd(&Fs[comp][sample_index(G.nx + (comp == 0), G.ny + (comp == 1), gx, gy, gz)],
-                           (float)q * unit);
-        }
-      }
-    }
-  }
-
-  if (sums) {  // exact integer warp totals of sum_i V_i / dx^3; every granule deposits exactly S
-    long long v = (long long)S;
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-    if (lane_id() == 0 && v != 0) {
-      atomicAdd((unsigned long long*)&sums[0], (unsigned long long)v);
-      atomicAdd((unsigned long long*)&sums[1], (unsigned long long)v);
-    }
-  }
+  p2g_flush(sh, B, G, (unsigned long long*)alpha, Fs, kP2GThreads);
+  if (sums) p2g_sums(sums, (long long)S);
 }
 
 // In place: 64-bit fixed-point alpha_s -> double; sums[0] and sums[1] (integer
@@ -650,15 +352,23 @@ __global__ void __launch_bounds__(256) k_p2g_adj(DGrid G, DParams<T> P, int64_t 
   }
 }
 
-template <typename T>
-static Fields<T> fields(const void* u, const void* v, const void* w, const void* p, const void* af) {
-  Fields<T> F;
-  F.u = (const T*)u;
-  F.v = (const T*)v;
-  F.w = (const T*)w;
-  F.p = (const T*)p;
-  F.af = (const T*)af;
-  return F;
+// alpha_s accumulation around a P2G pass: zero the grid (and sums) before,
+// then convert (FP32 fixed point -> double) or sum (FP64) after.
+int alpha_begin(double* alpha_s, int64_t ncell, double* sums2, cudaStream_t stream) {
+  k_zero<<<1184, 256, 0, stream>>>(alpha_s, ncell, sums2);
+  count_launches(1);
+  return GIC_OK;
+}
+
+int alpha_end(const DGrid& G, int32_t precision, double* alpha_s, int64_t ncell, double* sums2, cudaStream_t stream) {
+  if (precision == GIC_FP32) {
+    k_alpha_finish_f32<<<1184, 256, 0, stream>>>(alpha_s, ncell, G.dx * G.dx * G.dx, sums2);
+    count_launches(1);
+  } else if (sums2) {
+    k_alpha_sum<<<592, 256, 0, stream>>>(alpha_s, ncell, G.dx * G.dx * G.dx, sums2);
+    count_launches(1);
+  }
+  return GIC_OK;
 }
 
 }  // namespace gic

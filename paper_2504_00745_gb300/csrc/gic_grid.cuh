@@ -1,0 +1,397 @@
+// gic_grid.cuh -- device side of a3 (G2P coupling) and a5 (P2G), shared by
+// the grid kernels and the fused substep.
+#pragma once
+
+#include <climits>
+
+#include "gic_interp.cuh"
+
+namespace gic {
+
+template <typename T>
+struct Fields {
+  const T* u;
+  const T* v;
+  const T* w;
+  const T* p;
+  const T* af;
+};
+
+template <typename T>
+__device__ __forceinline__ FieldLoad<T> face_loader(const DGrid& G, const T* f, int comp) {
+  FieldLoad<T> L;
+  L.f = f;
+  L.nsx = G.nx + (comp == 0);
+  L.nsy = G.ny + (comp == 1);
+  return L;
+}
+
+template <typename T>
+__device__ __forceinline__ GradPLoad<T> gradp_loader(const DGrid& G, const T* p, int comp) {
+  GradPLoad<T> L;
+  L.p = p;
+  L.nx = G.nx;
+  L.ny = G.ny;
+  L.nz = G.nz;
+  L.comp = comp;
+  L.inv_dx = (T)G.inv_dx;
+  return L;
+}
+
+// G2P coupling of one granule at (cell, p) with velocity v (Sec. 3.3 Eqs. 5a,
+// 5b; Sec. 5.2 Eq. momentum4): F_fl = c_drag pi r^2 rho_f |u_f - v| (u_f - v)
+// - V grad p and a_f = g - grad p / rho_f.  Returns |u_f - v|.
+template <typename T>
+__device__ __forceinline__ T g2p_granule(const DGrid& G, const DParams<T>& P, const Fields<T>& Fd, int32_t cell,
+                                         const pos_t<T>& pi, const vec_t<T>& vi, T F[3], T a[3]) {
+  int m[3];
+  T t[3];
+  granule_mac<T>(G, cell, pi, m, t);
+  const T* uvw[3] = {Fd.u, Fd.v, Fd.w};
+  T uf[3], gp[3];
+  T inv_dx = (T)G.inv_dx;
+#pragma unroll
+  for (int comp = 0; comp < 3; ++comp) {
+    Stencil3<T> S = make_stencil<T>(G, m, t, comp);
+    uf[comp] = interp<T>(S, face_loader<T>(G, uvw[comp], comp), inv_dx, nullptr);
+    gp[comp] = interp<T>(S, gradp_loader<T>(G, Fd.p, comp), inv_dx, nullptr);
+  }
+  T r = radius_of(pi);
+  T V = T(4.0 / 3.0 * kPi) * r * r * r;
+  T d0 = uf[0] - vi.x, d1 = uf[1] - vi.y, d2 = uf[2] - vi.z;
+  T sp = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+  T cd = P.c_drag * T(kPi) * r * r * P.rho_f * sp;
+  F[0] = cd * d0 - V * gp[0];
+  F[1] = cd * d1 - V * gp[1];
+  F[2] = cd * d2 - V * gp[2];
+  if (P.rho_f > T(0)) {
+    a[0] = P.g[0] - gp[0] * P.inv_rho_f;
+    a[1] = P.g[1] - gp[1] * P.inv_rho_f;
+    a[2] = P.g[2] - gp[2] * P.inv_rho_f;
+  } else {
+    a[0] = P.g[0];
+    a[1] = P.g[1];
+    a[2] = P.g[2];
+  }
+  return sp;
+}
+
+// ---- FP32 path: exact fixed-point volume fraction ----
+//
+// alpha_s is accumulated as a 64-bit integer in units of 2^-53: per granule
+// the volume fraction S = V / dx^3 is rounded once to 2^-53; the per-axis
+// tent weights come from the 30-bit fixed-point position as 31-bit integers
+// (exact when the contact cell is the MAC cell), S times their product is
+// formed to 2^-62 and each corner's deposit truncated to 2^-53, and the eighth
+// corner takes the rest, so every granule deposits exactly S; integer atomics
+// make the sum independent of the order of arrival -- bitwise reproducible.
+// k_alpha_finish turns the integers into doubles in place.
+
+constexpr uint32_t kW1 = 1u << 31;  // weight 1.0
+
+// Centred-stencil weights of one axis from the contact coordinate c and the
+// fixed-point offset q: lower sample i0 and integer weights (w0, w1), w0 + w1 = 2^31.
+__device__ __forceinline__ void fixed_axis(const DGrid& G, int c, uint32_t q, int n, int& i0, uint32_t& w1) {
+  int m = mac_of(G, c);
+  unsigned long long N = ((unsigned long long)(c - m * G.k) << kFracBits) | q;  // offset in 2^-30 h_c
+  // P = round(N * 2 / k): the offset inside the MAC cell in units of 2^-31 dx
+  unsigned long long P;
+  if (G.k == 1)
+    P = N << 1;
+  else if (G.k == 2)
+    P = N;
+  else
+    P = (__umul64hi(N << 2, G.kinv64) + 1ull) >> 1;
+  uint32_t p = (uint32_t)P;  // < 2^31
+  if (p >= (1u << 30)) {
+    i0 = m;
+    w1 = p - (1u << 30);
+  } else {
+    i0 = m - 1;
+    w1 = p + (1u << 30);
+  }
+  if (i0 < 0) {
+    i0 = 0;
+    w1 = 0;
+  } else if (i0 > n - 2) {
+    i0 = n - 2;
+    w1 = kW1;
+  }
+}
+
+// An integer-valued float (|v| >= 2^23) as int64, exactly, with integer ops.
+__device__ __forceinline__ long long float_int_to_ll(float v) {
+  uint32_t b = __float_as_uint(v);
+  int e = (int)((b >> 23) & 0xffu) - 127 - 23;
+  long long m = (long long)((b & 0x7fffffu) | 0x800000u);
+  long long r = e >= 0 ? (m << e) : (m >> (-e));
+  return (b >> 31) ? -r : r;
+}
+
+// S = V / dx^3 in 2^-53 units for radius r, rounded, in FP32 double-float
+// arithmetic (r^3 exact to ~2^-46, the constant as a float pair): the FP64
+// pipe of this GPU is 1/64 of the FP32 rate.
+__device__ __forceinline__ unsigned long long volume_fixed(const DGrid& G, float r) {
+  float r2h = r * r;
+  float r2l = fmaf(r, r, -r2h);
+  float r3h = r2h * r;
+  float r3l = fmaf(r2h, r, -r3h) + r2l * r;
+  float sh = r3h * G.vol_fx_hi;
+  float sl = fmaf(r3h, G.vol_fx_hi, -sh) + fmaf(r3h, G.vol_fx_lo, r3l * G.vol_fx_hi);
+  long long a = fabsf(sh) >= 8388608.0f ? float_int_to_ll(sh) : (long long)__float2ll_rn(sh);
+  return (unsigned long long)(a + __float2ll_rn(sl));
+}
+
+// floor(x w / 2^31) for x < 2^63, w <= 2^31, with two 32x32->64 products.
+__device__ __forceinline__ unsigned long long mul31(unsigned long long x, uint32_t w) {
+  unsigned long long hi = (unsigned long long)(uint32_t)(x >> 32) * w;
+  unsigned long long lo = (unsigned long long)(uint32_t)x * w;
+  return (hi << 1) + (lo >> 31);
+}
+
+// FP32-path alpha_s deposits of one granule at its new position: the base
+// sample i0 and the eight integer deposits (2^-53 units) summing to S exactly.
+// S is carried in 2^-62 units through the three per-axis weight products
+// (each truncated once), so a deposit is within ~2^-53 of S w_x w_y w_z; the
+// eighth corner takes S minus the other seven.
+__device__ __forceinline__ void alpha_deposits(const DGrid& G, int32_t cn, uint4 pn, int i0[3], long long v[8],
+                                               unsigned long long& S) {
+  S = volume_fixed(G, __uint_as_float(pn.w));
+  int c3[3] = {cell_x(cn), cell_y(cn), cell_z(cn)};
+  const int nn[3] = {G.nx, G.ny, G.nz};
+  uint32_t w1[3], w0[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    fixed_axis(G, c3[a], pcomp(pn, a), nn[a], i0[a], w1[a]);
+    w0[a] = kW1 - w1[a];
+  }
+  const unsigned long long S9 = S << 9;  // < 2^63
+  unsigned long long sx[2], sxy[4];
+  sx[0] = mul31(S9, w0[0]);
+  sx[1] = mul31(S9, w1[0]);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) sxy[k] = mul31(sx[k & 1], (k & 2) ? w1[1] : w0[1]);
+  long long sum7 = 0;
+#pragma unroll
+  for (int k = 0; k < 7; ++k) {
+    v[k] = (long long)(mul31(sxy[k & 3], (k & 4) ? w1[2] : w0[2]) >> 9);
+    sum7 += v[k];
+  }
+  v[7] = (long long)S - sum7;
+}
+
+// FP32 path of P2G.  One CTA takes 512 consecutive granules of the
+// Morton-sorted state, which occupy a compact block of MAC cells.  When the
+// samples they may touch fit a kP2GTile-entry box, every deposit goes to
+// shared-memory copies of alpha_s and the three F_s grids over that box,
+// held as 32-bit integer limbs (32-bit shared integer atomics run at full
+// rate even when lanes collide, unlike float or 64-bit ones), and the box's
+// non-zero entries then go to global memory with one atomic each; otherwise
+// every deposit is a global atomic.
+//   alpha_s: a deposit (< 2^54 units of 2^-53) is split into three 18-bit
+//   limbs, so up to 2^14 deposits per entry add without overflow -- exact.
+//   F_s: a deposit d is rounded to a multiple of u = M 2^-30, M the CTA's
+//   largest |exch f_ex| component, and q = d / u (|q| <= 2^30) is split into
+//   a signed high and an unsigned low 15-bit limb; the limb sums are exact,
+//   so the only rounding besides the float product d is the 2^-30 M grid.
+// alpha_s stays 64-bit fixed point (exact, order-independent) until
+// k_alpha_finish_f32.
+constexpr int kP2GTile = 1024;
+
+// Shared-memory copies of alpha_s and the three F_s grids over one CTA's box.
+struct P2GShared {
+  uint32_t a[3][kP2GTile];
+  int32_t fh[3][kP2GTile];
+  uint32_t fl[3][kP2GTile];
+  int lo[3], hi[3];
+  unsigned M;
+};
+
+// One thread's contribution to its CTA's box and fixed-point scale.
+struct P2GExtent {
+  int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {INT_MIN, INT_MIN, INT_MIN};
+  float M = 0.f;
+  // a stencil's base is the MAC cell m or m - 1 on each axis, and it reaches one sample further
+  __device__ __forceinline__ void add_cell(const DGrid& G, int32_t c) {
+    const int c3[3] = {cell_x(c), cell_y(c), cell_z(c)};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      int m = mac_of(G, c3[a]);
+      lo[a] = min(lo[a], m - 1);
+      hi[a] = max(hi[a], m + 1);
+    }
+  }
+  __device__ __forceinline__ void add_force(const float fc[3]) {
+    float m = fmaxf(fabsf(fc[0]), fmaxf(fabsf(fc[1]), fabsf(fc[2])));
+    M = fmaxf(M, m <= 3.0e38f ? m : INFINITY);  // NaN or inf: no fixed-point grid for this CTA
+  }
+};
+
+struct P2GBox {
+  bool tile, ftile;     // deposits go to the shared box (alpha_s; F_s)
+  bool do_a, do_f;      // alpha_s / F_s requested
+  int b[3], ex, sy, sz, vol;
+  float unit, inv_unit;  // F_s fixed-point unit M 2^-30 and its inverse
+};
+
+__device__ __forceinline__ void p2g_box_init(P2GShared& sh) {
+  if (threadIdx.x < 3) {
+    sh.lo[threadIdx.x] = INT_MAX;
+    sh.hi[threadIdx.x] = INT_MIN;
+  }
+  if (threadIdx.x == 0) sh.M = 0u;
+}
+
+// CTA-wide: reduce the extents, decide the tile and zero it.  Every thread
+// of the CTA must call it (it synchronises the CTA).
+__device__ __forceinline__ P2GBox p2g_box(P2GShared& sh, const P2GExtent& ext, bool do_a, bool do_f) {
+  __syncthreads();
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    int l = __reduce_min_sync(0xffffffffu, ext.lo[a]);
+    int h = __reduce_max_sync(0xffffffffu, ext.hi[a]);
+    if (lane_id() == 0) {
+      atomicMin(&sh.lo[a], l);
+      atomicMax(&sh.hi[a], h);
+    }
+  }
+  if (do_f) {  // non-negative floats order like their bit patterns
+    unsigned mb = __reduce_max_sync(0xffffffffu, __float_as_uint(ext.M));
+    if (lane_id() == 0) atomicMax(&sh.M, mb);
+  }
+  __syncthreads();
+  P2GBox B;
+  B.do_a = do_a;
+  B.do_f = do_f;
+  B.b[0] = max(sh.lo[0], 0);
+  B.b[1] = max(sh.lo[1], 0);
+  B.b[2] = max(sh.lo[2], 0);
+  const int ex = sh.hi[0] - B.b[0] + 1, ey = sh.hi[1] - B.b[1] + 1, ez = sh.hi[2] - B.b[2] + 1;
+  // a CTA without granules has lo > hi
+  B.tile = ex > 0 && ey > 0 && ez > 0 && (int64_t)ex * ey * ez <= kP2GTile;
+  const float Mc = __uint_as_float(sh.M);
+  B.ftile = B.tile && do_f && Mc >= 1e-30f && Mc <= 3.0e38f;
+  B.unit = Mc * 0x1p-30f;
+  B.inv_unit = B.ftile ? 0x1p30f / Mc : 0.f;
+  B.vol = B.tile ? ex * ey * ez : 0;
+  B.ex = ex;
+  B.sy = ex;
+  B.sz = ex * ey;
+  for (int e = threadIdx.x; e < B.vol; e += blockDim.x) {
+    if (do_a) sh.a[0][e] = sh.a[1][e] = sh.a[2][e] = 0u;
+    if (B.ftile) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        sh.fh[c][e] = 0;
+        sh.fl[c][e] = 0u;
+      }
+    }
+  }
+  if (B.tile) __syncthreads();
+  return B;
+}
+
+__device__ __forceinline__ void p2g_add_alpha(P2GShared& sh, const P2GBox& B, const DGrid& G,
+                                              unsigned long long* acc, const int ia[3], const long long va[8]) {
+  if (B.tile) {
+    const int e0 = (ia[0] - B.b[0]) + B.sy * (ia[1] - B.b[1]) + B.sz * (ia[2] - B.b[2]);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int e = e0 + (k & 1) + ((k >> 1) & 1) * B.sy + (k >> 2) * B.sz;
+      const unsigned long long v = (unsigned long long)va[k];
+      atomicAdd(&sh.a[0][e], (uint32_t)(v & 0x3ffffull));
+      atomicAdd(&sh.a[1][e], (uint32_t)((v >> 18) & 0x3ffffull));
+      atomicAdd(&sh.a[2][e], (uint32_t)(v >> 36));
+    }
+  } else {
+    unsigned long long* g0 = acc + sample_index(G.nx, G.ny, ia[0], ia[1], ia[2]);
+    const int64_t gy = G.nx, gz = (int64_t)G.nx * G.ny;
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if (va[k]) atomicAdd(g0 + (k & 1) + ((k >> 1) & 1) * gy + (k >> 2) * gz, (unsigned long long)va[k]);
+  }
+}
+
+// F_s deposit of one granule on face grid comp: the eight stencil weights
+// times fc (= exch f_ex component).
+__device__ __forceinline__ void p2g_add_face(P2GShared& sh, const P2GBox& B, const DGrid& G, float* Fs, int comp,
+                                             const Stencil3<float>& St, float fc) {
+  const float wx = St.w[0], wy = St.w[1], wz = St.w[2];
+  const float fx0 = (1.f - wx) * fc, fx1 = wx * fc;
+  const float wyz[4] = {(1.f - wy) * (1.f - wz), wy * (1.f - wz), (1.f - wy) * wz, wy * wz};
+  if (B.ftile) {
+    const int e0 = (St.i0[0] - B.b[0]) + B.sy * (St.i0[1] - B.b[1]) + B.sz * (St.i0[2] - B.b[2]);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int q = __float2int_rn(((k & 1) ? fx1 : fx0) * wyz[k >> 1] * B.inv_unit);
+      const int e = e0 + (k & 1) + ((k >> 1) & 1) * B.sy + (k >> 2) * B.sz;
+      atomicAdd(&sh.fh[comp][e], q >> 15);
+      atomicAdd(&sh.fl[comp][e], (uint32_t)(q & 0x7fff));
+    }
+  } else {
+    const int nsx = G.nx + (comp == 0), nsy = G.ny + (comp == 1);
+    float* g0 = Fs + sample_index(nsx, nsy, St.i0[0], St.i0[1], St.i0[2]);
+    const int64_t gy = nsx, gz = (int64_t)nsx * nsy;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const float d = ((k & 1) ? fx1 : fx0) * wyz[k >> 1];
+      if (d != 0.f) atomicAdd(g0 + (k & 1) + ((k >> 1) & 1) * gy + (k >> 2) * gz, d);
+    }
+  }
+}
+
+// CTA-wide: the box's non-zero entries to global memory (one atomic each).
+__device__ __forceinline__ void p2g_flush(P2GShared& sh, const P2GBox& B, const DGrid& G, unsigned long long* acc,
+                                          float* const Fs[3], int threads) {
+  if (!B.tile) return;
+  __syncthreads();
+  // e = lx + ex (ly + ey lz); (e + 1/2) / d stays >= 1/(2 d) away from an
+  // integer, far beyond the float error for e, d <= 1024
+  const float rx = 1.f / (float)B.ex, rxy = 1.f / (float)B.sz;
+  for (int e = threadIdx.x; e < B.vol; e += threads) {
+    int lz = (int)(((float)e + 0.5f) * rxy);
+    int r = e - lz * B.sz;
+    int ly = (int)(((float)r + 0.5f) * rx);
+    int lx = r - ly * B.ex;
+    int gx = B.b[0] + lx, gy = B.b[1] + ly, gz = B.b[2] + lz;
+    if (B.do_a) {
+      unsigned long long a = (unsigned long long)sh.a[0][e] + ((unsigned long long)sh.a[1][e] << 18) +
+                             ((unsigned long long)sh.a[2][e] << 36);
+      if (a) atomicAdd(&acc[sample_index(G.nx, G.ny, gx, gy, gz)], a);
+    }
+    if (B.ftile) {
+#pragma unroll
+      for (int comp = 0; comp < 3; ++comp) {
+        long long q = (long long)sh.fh[comp][e] * (1ll << 15) + (long long)sh.fl[comp][e];
+        if (q) atomicAdd(&Fs[comp][sample_index(G.nx + (comp == 0), G.ny + (comp == 1), gx, gy, gz)],
+                         (float)q * B.unit);
+      }
+    }
+  }
+}
+
+// Exact integer warp totals of sum_i V_i / dx^3 into both sums (every granule
+// deposits exactly its S).
+__device__ __forceinline__ void p2g_sums(double* sums, long long v) {
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  if (lane_id() == 0 && v != 0) {
+    atomicAdd((unsigned long long*)&sums[0], (unsigned long long)v);
+    atomicAdd((unsigned long long*)&sums[1], (unsigned long long)v);
+  }
+}
+
+template <typename T>
+inline Fields<T> fields(const void* u, const void* v, const void* w, const void* p, const void* af) {
+  Fields<T> F;
+  F.u = (const T*)u;
+  F.v = (const T*)v;
+  F.w = (const T*)w;
+  F.p = (const T*)p;
+  F.af = (const T*)af;
+  return F;
+}
+
+int alpha_begin(double* alpha_s, int64_t ncell, double* sums2, cudaStream_t stream);
+int alpha_end(const DGrid& G, int32_t precision, double* alpha_s, int64_t ncell, double* sums2, cudaStream_t stream);
+
+}  // namespace gic

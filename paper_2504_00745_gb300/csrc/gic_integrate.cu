@@ -9,71 +9,9 @@
 // positions carry no floating-point drift; a carry or borrow moves the granule
 // to the neighbouring contact cell.  FP64 path: offsets are doubles re-binned
 // into [0, h_c).
-#include "gic_internal.cuh"
+#include "gic_integrate.cuh"
 
 namespace gic {
-
-template <typename T>
-struct Masses {
-  T m, ma;
-};
-
-template <typename T>
-__device__ __forceinline__ Masses<T> masses(const DParams<T>& P, T r) {
-  T V = T(4.0 / 3.0 * kPi) * r * r * r;
-  Masses<T> M;
-  M.m = P.rho_s * V;
-  M.ma = P.vm ? T(0.5) * P.rho_f * V : T(0);
-  return M;
-}
-
-__device__ __forceinline__ void advance_axis(const DGrid& G, float dt, float v, uint32_t q, int c, int nc,
-                                             uint32_t& q_out, int& c_out, uint32_t& flags) {
-  float inc_f = dt * v * G.inv_unit_f;
-  // clamp far beyond one cell so the integer conversion is defined
-  inc_f = fminf(fmaxf(inc_f, -0x1p40f), 0x1p40f);
-  long long inc = __float2ll_rn(inc_f);
-  long long s = (long long)q + inc;
-  long long shift = s >> kFracBits;  // floor division by 2^30
-  q_out = (uint32_t)(s & (long long)kFracMask);
-  long long cn = (long long)c + shift;
-  if (shift > 1 || shift < -1) flags |= GIC_STATUS_FAST;
-  if (cn < 0) {
-    cn = 0;
-    q_out = 0;
-    flags |= GIC_STATUS_OUT_OF_DOMAIN;
-  } else if (cn > nc - 1) {
-    cn = nc - 1;
-    q_out = kFracMask;
-    flags |= GIC_STATUS_OUT_OF_DOMAIN;
-  }
-  c_out = (int)cn;
-}
-
-__device__ __forceinline__ void advance_axis(const DGrid& G, double dt, double v, double o, int c, int nc,
-                                             double& o_out, int& c_out, uint32_t& flags) {
-  double x = o + dt * v;
-  double sh = floor(x * G.inv_hc);
-  if (!(fabs(sh) < 1e9)) sh = x > 0 ? 1e9 : -1e9;
-  long long shift = (long long)sh;
-  x -= sh * G.hc;
-  // guard against rounding just outside [0, h_c)
-  if (x < 0.0) x = 0.0;
-  if (x >= G.hc) x = nextafter(G.hc, 0.0);
-  if (shift > 1 || shift < -1) flags |= GIC_STATUS_FAST;
-  long long cn = (long long)c + shift;
-  if (cn < 0) {
-    cn = 0;
-    x = 0.0;
-    flags |= GIC_STATUS_OUT_OF_DOMAIN;
-  } else if (cn > nc - 1) {
-    cn = nc - 1;
-    x = nextafter(G.hc, 0.0);
-    flags |= GIC_STATUS_OUT_OF_DOMAIN;
-  }
-  o_out = x;
-  c_out = (int)cn;
-}
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_integrate(DGrid G, DParams<T> P, int64_t n, const int32_t* __restrict__ cell,
@@ -86,35 +24,19 @@ __global__ void __launch_bounds__(256) k_integrate(DGrid G, DParams<T> P, int64_
                                                     uint32_t* status) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
-  int32_t c = cell[i];
-  pos_t<T> p = pos[i];
-  vec_t<T> v = vel[i];
   vec_t<T> fc = Fc[i], ff = Ffl[i], fa = af[i];
-  Masses<T> M = masses(P, radius_of(p));
-  T inv = T(1) / (M.m + M.ma);
-  T a0 = (fc.x + ff.x + M.m * P.g[0] + M.ma * fa.x) * inv;
-  T a1 = (fc.y + ff.y + M.m * P.g[1] + M.ma * fa.y) * inv;
-  T a2 = (fc.z + ff.z + M.m * P.g[2] + M.ma * fa.z) * inv;
-  T v0 = v.x + P.dt * a0, v1 = v.y + P.dt * a1, v2 = v.z + P.dt * a2;
+  int32_t co;
+  pos_t<T> po;
+  vec_t<T> vo;
+  T e0, e1, e2;
   uint32_t flags = 0;
-  if (!isfinite(v0) || !isfinite(v1) || !isfinite(v2)) flags |= GIC_STATUS_NONFINITE;
-  int c3[3] = {cell_x(c), cell_y(c), cell_z(c)};
-  int cn[3];
-  pos_t<T> po = p;
-  if constexpr (sizeof(T) == 4) {
-    advance_axis(G, P.dt, v0, p.x, c3[0], G.nc[0], po.x, cn[0], flags);
-    advance_axis(G, P.dt, v1, p.y, c3[1], G.nc[1], po.y, cn[1], flags);
-    advance_axis(G, P.dt, v2, p.z, c3[2], G.nc[2], po.z, cn[2], flags);
-  } else {
-    advance_axis(G, P.dt, v0, p.x, c3[0], G.nc[0], po.x, cn[0], flags);
-    advance_axis(G, P.dt, v1, p.y, c3[1], G.nc[1], po.y, cn[1], flags);
-    advance_axis(G, P.dt, v2, p.z, c3[2], G.nc[2], po.z, cn[2], flags);
-  }
+  integrate_granule(G, P, cell[i], pos[i], vel[i], fc.x, fc.y, fc.z, ff.x, ff.y, ff.z, fa.x, fa.y, fa.z, co, po, vo,
+                    e0, e1, e2, flags);
   if (flags) raise_status(status, flags);
-  cell_out[i] = pack_cell(cn[0], cn[1], cn[2]);
+  cell_out[i] = co;
   pos_out[i] = po;
-  vel_out[i] = make_vec<T>(v0, v1, v2);
-  if (fex) fex[i] = make_vec<T>(ff.x + M.ma * (fa.x - a0), ff.y + M.ma * (fa.y - a1), ff.z + M.ma * (fa.z - a2));
+  vel_out[i] = vo;
+  if (fex) fex[i] = make_vec<T>(e0, e1, e2);
   if (id_out && id_in && id_out != id_in) id_out[i] = id_in[i];
 }
 

@@ -37,11 +37,12 @@ class Simulator:
     encoding (cell int32 [n,3], q uint32 [n,3], r float32 [n], v float32 [n,3])
     as host or device tensors.  verlet_skin (metres): contact through Verlet
     lists with that skin (gic_contact_verlet, cap partners per granule)
-    instead of walking the cell table every substep (gic_contact).
+    instead of walking the cell table every substep (gic_contact); with
+    lists and fused, everything after the sort runs as gic_substep.
     """
 
     def __init__(self, grid, params, n: int, precision: int = GIC_FP32, device="cuda",
-                 verlet_skin: Optional[float] = None, verlet_cap: int = 48):
+                 verlet_skin: Optional[float] = None, verlet_cap: int = 48, fused: bool = True):
         self.grid_obj = grid
         self.params_obj = params
         self.grid = gic.make_grid(grid)
@@ -69,6 +70,7 @@ class Simulator:
         self.sums = torch.zeros(2, dtype=torch.float64, device=device)
         self.fluid: Optional[DeviceFluid] = None
         self.nb: Optional[gic.Neighbors] = None
+        self.fused = fused
         if verlet_skin is not None:
             self.nb = gic.Neighbors(n, precision, cap=verlet_cap, skin=verlet_skin, device=device)
             gic.gic_neighbors_reset(self.nb)
@@ -88,7 +90,7 @@ class Simulator:
             gic.gic_neighbors_reset(self.nb, stream)
 
     @classmethod
-    def from_problem(cls, prob, precision=GIC_FP32, device="cuda", verlet: bool = True):
+    def from_problem(cls, prob, precision=GIC_FP32, device="cuda", verlet: bool = True, fused: bool = True):
         """Simulator of a gic_inputs.Problem; verlet: Verlet lists with a skin
         of 0.15 r_max (48 partners per granule, 96 when radii vary by more
         than 1.5x)."""
@@ -97,7 +99,8 @@ class Simulator:
             r = prob.r
             skin = 0.15 * float(r.max())
             cap = 48 if float(r.max()) <= 1.5 * float(r.min()) else 96
-        sim = cls(prob.grid, prob.params, prob.n, precision, device, verlet_skin=skin, verlet_cap=cap or 48)
+        sim = cls(prob.grid, prob.params, prob.n, precision, device, verlet_skin=skin, verlet_cap=cap or 48,
+                  fused=fused)
         sim.set_fluid(prob.u, prob.vf, prob.wf, prob.p, prob.alpha_f)
         sim.set_state(prob.cell, prob.q, prob.r, prob.v)
         return sim
@@ -107,12 +110,22 @@ class Simulator:
         """One SandSubstep: A (current) -> sort -> B -> forces -> A (next)."""
         F = self.fluid
         gic.gic_sort(self.grid, self.A, self.B, self.perm, self.table, self.ws, stream)
+        if self.nb is not None and self.fused:
+            self.fused_rest(alpha, transfer, sums, stream)
+            return
         self.contact(stream)
         gic.gic_g2p_couple(self.grid, self.params, self.B, F.u, F.v, F.w, F.p, F.alpha_f, self.F_fl, self.a_f,
                            self.alpha_f_p, stream)
         gic.gic_integrate(self.grid, self.params, self.B, self.F_c, self.F_fl, self.a_f, self.A, self.f_ex, stream)
         gic.gic_p2g(self.grid, self.params, self.B, self.A, self.f_ex, self.alpha_s if alpha else None,
                     self.Fs if transfer else (None, None, None), self.sums if (sums and alpha) else None, stream)
+
+    def fused_rest(self, alpha: bool, transfer: bool, sums: bool, stream=None):
+        """Everything after the sort as one gic_substep: B -> A."""
+        F = self.fluid
+        gic.gic_substep(self.grid, self.params, self.B, self.table, self.nb, F.u, F.v, F.w, F.p, F.alpha_f, self.A,
+                        self.F_c, None, self.alpha_s if alpha else None,
+                        self.Fs if transfer else (None, None, None), self.sums if (sums and alpha) else None, stream)
 
     def contact(self, stream=None):
         """a2 on the sorted state B: Verlet lists when configured, else the
@@ -137,6 +150,9 @@ class Simulator:
             acc.setdefault(name, []).append((a, b))
 
         timed("gic_sort", lambda: gic.gic_sort(self.grid, self.A, self.B, self.perm, self.table, self.ws, s))
+        if self.nb is not None and self.fused:
+            timed("gic_substep", lambda: self.fused_rest(alpha, True, alpha, s))
+            return
         timed("gic_contact", lambda: self.contact(s))
         timed("gic_g2p_couple", lambda: gic.gic_g2p_couple(self.grid, self.params, self.B, F.u, F.v, F.w, F.p,
                                                             F.alpha_f, self.F_fl, self.a_f, self.alpha_f_p, s))

@@ -122,3 +122,46 @@ def test_verlet_argument_errors():
     neg = gic.Neighbors(prob.n, FP32, cap=8, skin=-1.0)
     with pytest.raises(gic.GicError, match="skin"):
         gic.gic_contact_verlet(sim.grid, sim.params, sim.B, sim.table, neg, sim.F_c)
+
+
+@pytest.mark.parametrize("name", ["dense_block", "random_cloud"])
+@pytest.mark.parametrize("prec", PRECS)
+def test_fused_substep_matches_separate_calls(name, prec):
+    """gic_substep (contact + G2P + integrate + P2G in one pass) against the
+    separate entry points on the same Verlet lists: the same state after 20
+    substeps (the same arithmetic in the same order: bit-identical positions
+    and velocities), alpha_s identical, F_s to the rounding of its
+    fixed-point tile (FP32) or of the atomics' order (FP64)."""
+    prob = shuffled(gi.make(name))
+    out = []
+    for fused in (True, False):
+        sim = Simulator.from_problem(prob, prec, fused=fused)
+        sim.run(20)
+        torch.cuda.synchronize()
+        assert gic.gic_check_status() == 0
+        x, v = sim.positions()
+        out.append((x.cpu().numpy(), v.cpu().numpy(), sim.alpha_s.cpu().numpy(), [f.cpu().numpy() for f in sim.Fs],
+                    sim.sums.cpu().numpy()))
+    (xa, va, aa, Fa, sa), (xb, vb, ab, Fb, sb) = out
+    assert np.array_equal(xa, xb)
+    assert np.array_equal(va, vb)
+    assert np.array_equal(aa, ab) if prec == FP32 else np.abs(aa - ab).max() <= 1e-15
+    for fa, fb in zip(Fa, Fb):
+        assert np.abs(fa - fb).max() <= (1e-6 if prec == FP32 else 1e-12) * max(np.abs(fb).max(), 1e-300)
+    assert np.allclose(sa, sb, rtol=1e-12, atol=0)
+
+
+def test_fused_substep_argument_errors():
+    prob = gi.make("dense_block")
+    sim = Simulator.from_problem(prob, FP32)
+    F = sim.fluid
+    gic.gic_sort(sim.grid, sim.A, sim.B, sim.perm, sim.table, sim.ws)
+    with pytest.raises(gic.GicError, match="null fluid"):
+        gic.gic_substep(sim.grid, sim.params, sim.B, sim.table, sim.nb, None, F.v, F.w, F.p, F.alpha_f, sim.A,
+                        sim.F_c)
+    with pytest.raises(gic.GicError, match="all three"):
+        gic.gic_substep(sim.grid, sim.params, sim.B, sim.table, sim.nb, F.u, F.v, F.w, F.p, F.alpha_f, sim.A,
+                        sim.F_c, Fs=(sim.Fs[0], None, None))
+    with pytest.raises(gic.GicError, match="sums2 needs alpha_s"):
+        gic.gic_substep(sim.grid, sim.params, sim.B, sim.table, sim.nb, F.u, F.v, F.w, F.p, F.alpha_f, sim.A,
+                        sim.F_c, sums2=sim.sums)
