@@ -229,6 +229,14 @@ typedef struct GicNeighbors {
 int gic_contact_verlet(const GicGrid* grid, const GicParams* params, const GicGranules* sorted,
                        const void* cell_table, const GicNeighbors* nb, void* F_c, gic_stream_t stream);
 
+/* gic_contact_adj through the Verlet lists nb: the same gradients (the pair
+ * sums in another order).  The lists are checked, and rebuilt when needed,
+ * exactly as by gic_contact_verlet (the build's forces go to the scratch
+ * F_c, real[4n]).  Accumulates into g_pos, g_vel and *g_mu. */
+int gic_contact_verlet_adj(const GicGrid* grid, const GicParams* params, const GicGranules* sorted,
+                           const void* cell_table, const GicNeighbors* nb, void* F_c, const void* gF_c, void* g_pos,
+                           void* g_vel, double* g_mu, gic_stream_t stream);
+
 /* One substep after the sort, fused (Alg. 2 body): contact through the
  * Verlet lists nb (exactly gic_contact_verlet's forces), the G2P coupling
  * (gic_g2p_couple), the integration (gic_integrate) from `sorted` into
@@ -331,10 +339,10 @@ int gic_p2g_adj(const GicGrid* grid, const GicParams* params, const GicGranules*
  * state, the permutation and the per-granule force arrays). */
 int gic_window_workspace_size(const GicGrid* grid, int64_t n, int32_t precision, size_t* bytes);
 
-/* K substeps of Alg. 2 (SandSubstep): per substep gic_sort, contact,
- * gic_g2p_couple, gic_integrate, gic_p2g.  Contact is gic_contact_verlet
- * (skin 0.075 h_c, 64 partners per granule, lists in the workspace) when
- * state->id is set, else gic_contact.  `state` is updated in place and ends
+/* K substeps of Alg. 2 (SandSubstep): per substep gic_sort, then gic_substep
+ * (Verlet lists with skin 0.075 h_c and 64 partners per granule, kept in the
+ * workspace) when state->id is set, else gic_contact, gic_g2p_couple,
+ * gic_integrate and gic_p2g.  `state` is updated in place and ends
  * in the sorted order of the last substep (state->id, if set, maps it back).
  * alpha_s (may be NULL) is computed once, at the final positions (Alg. 1
  * CalTargetFraction); F_s (all three or none) accumulates over the K

@@ -292,13 +292,18 @@ __global__ void __launch_bounds__(kTileThreads) k_contact_tile(DGrid G, DParams<
   F[i] = make_float4(F0, F1, F2, 0.f);
 }
 
-template <typename T>
+// kList: walk the Verlet rows (nb) instead of the 27 cells; the last CTA
+// then clears the per-call Verlet words.
+template <typename T, bool kList>
 __global__ void __launch_bounds__(128) k_contact_adj(DGrid G, DParams<T> P, int64_t n, const int32_t* __restrict__ cell,
                                                       const pos_t<T>* __restrict__ pos,
                                                       const float4* __restrict__ posf,
                                                       const vec_t<T>* __restrict__ vel, const uint4* __restrict__ table,
                                                       const vec_t<T>* __restrict__ gF, vec_t<T>* __restrict__ gpos,
-                                                      vec_t<T>* __restrict__ gvel, double* __restrict__ g_mu) {
+                                                      vec_t<T>* __restrict__ gvel, double* __restrict__ g_mu,
+                                                      NbDev nb) {
+  bool rebuilt = false;
+  if constexpr (kList) rebuilt = (nb.flags[kNbRebuild] | nb.flags[kNbSticky]) != 0u;
   __shared__ double s_red[32];
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   double my_gmu = 0.0;
@@ -311,16 +316,23 @@ __global__ void __launch_bounds__(128) k_contact_adj(DGrid G, DParams<T> P, int6
     vec_t<T> li = gF[i];
     T ri = radius_of(pi);
     T mi = granule_mass(P, ri);
-    uint32_t epoch = __ldg(&table[0].x);
     T gx0 = 0, gx1 = 0, gx2 = 0, gv0 = 0, gv1 = 0, gv2 = 0, gm = 0;
-    for_each_contact<T>(G, table, epoch, i, cx, cy, cz, pi, ri, pos, posf, [&](int64_t j, const PairGeom<T>& g) {
+    auto pair = [&](int64_t j, const PairGeom<T>& g) {
       vec_t<T> vj = ldg(&vel[j]);
       vec_t<T> lj = ldg(&gF[j]);
       T mj = granule_mass(P, radius_of(ldg(&pos[j])));
       gm += pair_force_adj(P, g.x0, g.x1, g.x2, g.d, g.overlap, vi.x - vj.x, vi.y - vj.y, vi.z - vj.z,
                            mi * mj / (mi + mj), li.x - lj.x, li.y - lj.y, li.z - lj.z, li.x, li.y, li.z, gx0, gx1, gx2,
                            gv0, gv1, gv2);
-    });
+    };
+    if constexpr (kList) {
+      const bool has_f = sizeof(T) == 4 && posf != nullptr;
+      const float4 fi = has_f ? __ldg(&posf[i]) : make_float4(0.f, 0.f, 0.f, 0.f);
+      for_each_list_contact<T>(G, nb, i, cx, cy, cz, ci, pi, ri, has_f, fi, cell, pos, posf, pair);
+    } else {
+      uint32_t epoch = __ldg(&table[0].x);
+      for_each_contact<T>(G, table, epoch, i, cx, cy, cz, pi, ri, pos, posf, pair);
+    }
     if (P.walls) {
       const int c3[3] = {cx, cy, cz};
       for (int a = 0; a < 3; ++a) {
@@ -350,6 +362,7 @@ __global__ void __launch_bounds__(128) k_contact_adj(DGrid G, DParams<T> P, int6
     double s = block_sum(my_gmu, s_red);
     if (threadIdx.x == 0) atomicAdd(g_mu, s);
   }
+  if constexpr (kList) verlet_call_done(nb, rebuilt);
 }
 
 // Diagnostic: number of partners per granule and the pair list by id.
@@ -445,6 +458,8 @@ __global__ void __launch_bounds__(kBuild ? 128 : 256, kBuild ? 1 : 4) k_contact_
                              coincident);
       });
       nb.count[i] = cnt;
+      nb.at[i] = (int32_t)i;  // after a build, slot = sorted index
+      nb.cur[i] = (int32_t)i;
       nb.ref_cell[i] = ci;
       reinterpret_cast<pos_t<T>*>(nb.ref_pos)[i] = pi;
       const int32_t idi = id[i];
@@ -524,15 +539,15 @@ extern "C" int gic_contact_adj(const GicGrid* grid, const GicParams* params, con
   if (s->precision == GIC_FP32) {
     DParams<float> P;
     if ((rc = make_params(params, &P))) return rc;
-    k_contact_adj<float><<<grid_blocks(s->n, threads), threads, 0, stream>>>(
+    k_contact_adj<float, false><<<grid_blocks(s->n, threads), threads, 0, stream>>>(
         G, P, s->n, s->cell, (const uint4*)s->pos, (const float4*)s->posf, (const float4*)s->vel, (const uint4*)table,
-        (const float4*)gF_c, (float4*)g_pos, (float4*)g_vel, g_mu);
+        (const float4*)gF_c, (float4*)g_pos, (float4*)g_vel, g_mu, NbDev{});
   } else {
     DParams<double> P;
     if ((rc = make_params(params, &P))) return rc;
-    k_contact_adj<double><<<grid_blocks(s->n, threads), threads, 0, stream>>>(
+    k_contact_adj<double, false><<<grid_blocks(s->n, threads), threads, 0, stream>>>(
         G, P, s->n, s->cell, (const d4*)s->pos, nullptr, (const d4*)s->vel, (const uint4*)table, (const d4*)gF_c,
-        (d4*)g_pos, (d4*)g_vel, g_mu);
+        (d4*)g_pos, (d4*)g_vel, g_mu, NbDev{});
   }
   count_launches(1);
   GIC_CHECK_LAUNCH("gic_contact_adj");
@@ -646,5 +661,37 @@ extern "C" int gic_neighbors_reset(const GicNeighbors* nb, gic_stream_t stream) 
   k_neighbors_reset<<<1, 32, 0, stream>>>(nb->flags);
   count_launches(1);
   GIC_CHECK_LAUNCH("gic_neighbors_reset");
+  return GIC_OK;
+}
+
+extern "C" int gic_contact_verlet_adj(const GicGrid* grid, const GicParams* params, const GicGranules* s,
+                                      const void* table, const GicNeighbors* nb, void* F_c, const void* gF_c,
+                                      void* g_pos, void* g_vel, double* g_mu, gic_stream_t stream) {
+  DGrid G;
+  int rc = make_grid(grid, &G);
+  if (rc) return rc;
+  if ((rc = check_granules(s, "gic_contact_verlet_adj", true))) return rc;
+  if (s->n > 0 && (!gF_c || !g_pos || !g_vel))
+    return set_error(GIC_ERR_INVALID, "gic_contact_verlet_adj: null gradient array");
+  if ((rc = check_vecs(s->precision, "gic_contact_verlet_adj", {gF_c, g_pos, g_vel}))) return rc;
+  NbDev d;
+  if ((rc = verlet_prelude(G, params, s, table, nb, F_c, stream, "gic_contact_verlet_adj", &d))) return rc;
+  if (s->n == 0) return GIC_OK;
+  const int threads = 128;
+  if (s->precision == GIC_FP32) {
+    DParams<float> P;
+    make_params(params, &P);
+    k_contact_adj<float, true><<<grid_blocks(s->n, threads), threads, 0, stream>>>(
+        G, P, s->n, s->cell, (const uint4*)s->pos, (const float4*)s->posf, (const float4*)s->vel, (const uint4*)table,
+        (const float4*)gF_c, (float4*)g_pos, (float4*)g_vel, g_mu, d);
+  } else {
+    DParams<double> P;
+    make_params(params, &P);
+    k_contact_adj<double, true><<<grid_blocks(s->n, threads), threads, 0, stream>>>(
+        G, P, s->n, s->cell, (const d4*)s->pos, nullptr, (const d4*)s->vel, (const uint4*)table, (const d4*)gF_c,
+        (d4*)g_pos, (d4*)g_vel, g_mu, d);
+  }
+  count_launches(1);
+  GIC_CHECK_LAUNCH("gic_contact_verlet_adj");
   return GIC_OK;
 }

@@ -477,16 +477,15 @@ __device__ __forceinline__ void verlet_call_done(const NbDev& nb, bool rebuild) 
   }
 }
 
-// Forces of the partners in granule i's Verlet row (slot at[i]): the list
-// walk of gic_contact_verlet, four partners at a time so that their index,
-// cell and float-position loads overlap.
-template <typename T>
-__device__ __forceinline__ void verlet_list_force(const DGrid& G, const DParams<T>& P, const NbDev& nb, int64_t i,
-                                                  int cx, int cy, int cz, int32_t ci, const pos_t<T>& pi, T ri, T mi,
-                                                  const vec_t<T>& vi, bool has_f, const float4& fi,
-                                                  const int32_t* __restrict__ cell, const pos_t<T>* __restrict__ pos,
-                                                  const float4* __restrict__ posf, const vec_t<T>* __restrict__ vel,
-                                                  T& F0, T& F1, T& F2, bool& coincident) {
+// Every partner j of granule i in its Verlet row (slot at[i]) that is in
+// contact, with the geometry: f(j, g).  Four partners at a time, so that
+// their index, cell and float-position loads overlap.
+template <typename T, typename F>
+__device__ __forceinline__ void for_each_list_contact(const DGrid& G, const NbDev& nb, int64_t i, int cx, int cy,
+                                                      int cz, int32_t ci, const pos_t<T>& pi, T ri, bool has_f,
+                                                      const float4& fi, const int32_t* __restrict__ cell,
+                                                      const pos_t<T>* __restrict__ pos,
+                                                      const float4* __restrict__ posf, F&& f) {
   const int32_t s = nb.at[i];
   const int32_t* row = nb.list + (int64_t)s * nb.cap;
   const int cnt = nb.count[s];
@@ -510,11 +509,25 @@ __device__ __forceinline__ void verlet_list_force(const DGrid& G, const DParams<
       bool near, touch;
       PairGeom<T> g;
       verlet_pair(G, pi, ri, has_f, fi, fj[u], pos, jj[u], ox, oy, oz, T(0), near, touch, g);
-      if (touch)
-        add_force(P, g, vi, ldg(&vel[jj[u]]), mi, granule_mass(P, radius_of(ldg(&pos[jj[u]]))), F0, F1, F2,
-                  coincident);
+      if (touch) f(jj[u], g);
     }
   }
+}
+
+// Forces of the partners in granule i's Verlet row (the list walk of
+// gic_contact_verlet).
+template <typename T>
+__device__ __forceinline__ void verlet_list_force(const DGrid& G, const DParams<T>& P, const NbDev& nb, int64_t i,
+                                                  int cx, int cy, int cz, int32_t ci, const pos_t<T>& pi, T ri, T mi,
+                                                  const vec_t<T>& vi, bool has_f, const float4& fi,
+                                                  const int32_t* __restrict__ cell, const pos_t<T>* __restrict__ pos,
+                                                  const float4* __restrict__ posf, const vec_t<T>* __restrict__ vel,
+                                                  T& F0, T& F1, T& F2, bool& coincident) {
+  for_each_list_contact<T>(G, nb, i, cx, cy, cz, ci, pi, ri, has_f, fi, cell, pos, posf,
+                           [&](int64_t j, const PairGeom<T>& g) {
+                             add_force(P, g, vi, ldg(&vel[j]), mi, granule_mass(P, radius_of(ldg(&pos[j]))), F0, F1,
+                                       F2, coincident);
+                           });
 }
 
 }  // namespace gic

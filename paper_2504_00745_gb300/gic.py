@@ -74,6 +74,7 @@ _SIGS = {
     "gic_contact_verlet": [_P, _P, _P, _P, _P, _P, _P],
     "gic_neighbors_reset": [_P, _P],
     "gic_substep": [_P] * 19,
+    "gic_contact_verlet_adj": [_P] * 11,
 }
 # entry points that exist in include/gic.h but are declared optional here
 # (added later in the library's life) are looked up lazily
@@ -295,6 +296,14 @@ def gic_substep(grid: GicGrid, params: GicParams, sorted_: State, cell_table, nb
                              _ptr(v), _ptr(w), _ptr(p), _ptr(alpha_f), C.byref(t), _ptr(F_c), _ptr(f_ex),
                              _ptr(alpha_s), _ptr(Fs[0]), _ptr(Fs[1]), _ptr(Fs[2]), _ptr(sums2), _stream(stream)),
            "gic_substep")
+
+
+def gic_contact_verlet_adj(grid, params, st: State, cell_table, nb: Neighbors, F_c, gF_c, g_pos, g_vel, g_mu,
+                           stream=None):
+    s, b = st.struct(), nb.struct()
+    _check(lib().gic_contact_verlet_adj(C.byref(grid), C.byref(params), C.byref(s), _ptr(cell_table), C.byref(b),
+                                        _ptr(F_c), _ptr(gF_c), _ptr(g_pos), _ptr(g_vel), _ptr(g_mu),
+                                        _stream(stream)), "gic_contact_verlet_adj")
 
 
 def gic_neighbors_reset(nb: Neighbors, stream=None):

@@ -209,7 +209,8 @@ class GicWindow(torch.autograd.Function):
     Backward: the window is cut into segments of `ckpt` substeps; the state at
     the start of each segment is kept from the forward pass, every segment is
     recomputed from it in reverse order, and each substep's adjoint runs
-    gic_integrate_adj, gic_g2p_couple_adj, gic_contact_adj and gic_sort_adj.
+    gic_integrate_adj, gic_g2p_couple_adj, gic_contact_adj (through the
+    Verlet lists when the simulator has them) and gic_sort_adj.
     """
 
     @staticmethod
@@ -264,7 +265,12 @@ class GicWindow(torch.autograd.Function):
                                       gaf)
                 gic.gic_g2p_couple_adj(sim.grid, sim.params, sim.B, F.u, F.v, F.w, F.p, F.alpha_f, gFfl, gaf, None,
                                        g_pos_b, g_vel_b, g_scalars[0:1])
-                gic.gic_contact_adj(sim.grid, sim.params, sim.B, sim.table, gFc, g_pos_b, g_vel_b, g_scalars[1:2])
+                if sim.nb is not None:
+                    gic.gic_contact_verlet_adj(sim.grid, sim.params, sim.B, sim.table, sim.nb, sim.F_c, gFc, g_pos_b,
+                                               g_vel_b, g_scalars[1:2])
+                else:
+                    gic.gic_contact_adj(sim.grid, sim.params, sim.B, sim.table, gFc, g_pos_b, g_vel_b,
+                                        g_scalars[1:2])
                 gic.gic_sort_adj(n, prec, sim.perm, g_pos_b, g_vel_b, g_pos, g_vel)
         g_v0 = g_vel[:, :3].to(torch.float64)
         return g_v0, g_scalars[0].clone(), g_scalars[1].clone(), None, None, None, None

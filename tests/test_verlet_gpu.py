@@ -165,3 +165,34 @@ def test_fused_substep_argument_errors():
     with pytest.raises(gic.GicError, match="sums2 needs alpha_s"):
         gic.gic_substep(sim.grid, sim.params, sim.B, sim.table, sim.nb, F.u, F.v, F.w, F.p, F.alpha_f, sim.A,
                         sim.F_c, sums2=sim.sums)
+
+
+@pytest.mark.parametrize("name", ["dense_block", "random_cloud"])
+@pytest.mark.parametrize("prec", PRECS)
+def test_verlet_adjoint_matches_cell_walk(name, prec):
+    """gic_contact_verlet_adj against gic_contact_adj on the same state and
+    upstream gradient: first call builds the lists, second walks them."""
+    prob = shuffled(gi.make(name))
+    sim = Simulator.from_problem(prob, prec)
+    gic.gic_sort(sim.grid, sim.A, sim.B, sim.perm, sim.table, sim.ws)
+    rng = np.random.default_rng(11)
+    real = np.float32 if prec == FP32 else np.float64
+    lam = np.concatenate([rng.normal(size=(prob.n, 3)), np.zeros((prob.n, 1))], 1).astype(real)
+    gF = torch.from_numpy(lam).cuda()
+    out = []
+    for verlet in (True, True, False):
+        gp, gv = gic.vec4(prob.n, prec), gic.vec4(prob.n, prec)
+        gmu = torch.zeros(1, dtype=torch.float64, device="cuda")
+        if verlet:
+            gic.gic_contact_verlet_adj(sim.grid, sim.params, sim.B, sim.table, sim.nb, sim.F_c, gF, gp, gv, gmu)
+        else:
+            gic.gic_contact_adj(sim.grid, sim.params, sim.B, sim.table, gF, gp, gv, gmu)
+        torch.cuda.synchronize()
+        out.append((gp.cpu().numpy()[:, :3], gv.cpu().numpy()[:, :3], float(gmu.item())))
+    assert sim.nb.builds() == 1
+    ref = out[2]
+    tol = 1e-5 if prec == FP32 else 1e-12
+    for gp, gv, gm in out[:2]:
+        assert np.abs(gp - ref[0]).max() <= tol * np.abs(ref[0]).max()
+        assert np.abs(gv - ref[1]).max() <= tol * np.abs(ref[1]).max()
+        assert abs(gm - ref[2]) <= tol * abs(ref[2]) + 1e-30
