@@ -238,22 +238,23 @@ int gic_contact_verlet_adj(const GicGrid* grid, const GicParams* params, const G
                            void* g_vel, double* g_mu, gic_stream_t stream);
 
 /* One substep after the sort, fused (Alg. 2 body): contact through the
- * Verlet lists nb (exactly gic_contact_verlet's forces), the G2P coupling
- * (gic_g2p_couple), the integration (gic_integrate) from `sorted` into
- * `next`, and the P2G scatter (gic_p2g with old = sorted, new = next), in one
- * pass that keeps the per-granule forces in registers.  The paper runs these
- * as the steps of one substep (Alg. 2); fusing them is this library's.
+ * Verlet lists nb (exactly gic_contact_verlet's forces; on a substep that
+ * rebuilds the lists the 27-cell walk that builds them gives the forces),
+ * the G2P coupling (gic_g2p_couple), the integration (gic_integrate) from
+ * `sorted` into `next`, and the P2G scatter (gic_p2g with old = sorted,
+ * new = next), in one pass that keeps the per-granule forces in registers.
+ * The paper runs these as the steps of one substep (Alg. 2); fusing them is
+ * this library's.
  *   sorted: the output of gic_sort (ids required); next: written (cell, pos,
- *   vel, id).  F_c: real[4n] device scratch (the forces of a list build).
- *   f_ex: real[4n] or NULL, written.  alpha_s (or NULL), F_s (all three or
- *   none) and sums2 as for gic_p2g: alpha_s and sums2 are written, F_s
- *   accumulates.  Fluid fields as for gic_g2p_couple.  Errors as for the
- *   calls it fuses (sorted and next must match in size and precision).  Three
- *   to five launches, no host sync. */
+ *   vel, id).  f_ex: real[4n] or NULL, written.  alpha_s (or NULL), F_s (all
+ *   three or none) and sums2 as for gic_p2g: alpha_s and sums2 are written,
+ *   F_s accumulates.  Fluid fields as for gic_g2p_couple.  Errors as for the
+ *   calls it fuses (sorted and next must match in size and precision).  Two
+ *   to four launches, no host sync. */
 int gic_substep(const GicGrid* grid, const GicParams* params, const GicGranules* sorted, const void* cell_table,
                 const GicNeighbors* nb, const void* u, const void* v, const void* w, const void* p,
-                const void* alpha_f, GicGranules* next, void* F_c, void* f_ex, double* alpha_s, void* Fs_u,
-                void* Fs_v, void* Fs_w, double* sums2, gic_stream_t stream);
+                const void* alpha_f, GicGranules* next, void* f_ex, double* alpha_s, void* Fs_u, void* Fs_v,
+                void* Fs_w, double* sums2, gic_stream_t stream);
 
 /* Request a rebuild at the next gic_contact_verlet and clear the counters
  * (flags = {0, 1, 0, 0, 0, ...}). */

@@ -425,8 +425,11 @@ __global__ void __launch_bounds__(kBuild ? 128 : 256, kBuild ? 1 : 4) k_contact_
     const uint4* __restrict__ table, NbDev nb, T skin, vec_t<T>* __restrict__ F, uint32_t* status) {
   const bool rebuild = (nb.flags[kNbRebuild] | nb.flags[kNbSticky]) != 0u;  // uniform over the launch
   if (kBuild && !rebuild) return;
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (kBuild == rebuild && i < n) {
+  // the build runs on a capped grid (grid-stride), so that its idle launch on
+  // the substeps that keep their lists is one short wave; the list walk has
+  // one thread per granule
+  const int64_t stride = kBuild ? (int64_t)gridDim.x * blockDim.x : n;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; kBuild == rebuild && i < n; i += stride) {
     const int32_t ci = cell[i];
     const int cx = cell_x(ci), cy = cell_y(ci), cz = cell_z(ci);
     const pos_t<T> pi = pos[i];
@@ -439,32 +442,8 @@ __global__ void __launch_bounds__(kBuild ? 128 : 256, kBuild ? 1 : 4) k_contact_
     T F0 = 0, F1 = 0, F2 = 0;
     bool coincident = false;
     if constexpr (kBuild) {
-      int32_t* row = nb.list + i * nb.cap;
-      const uint32_t epoch = __ldg(&table[0].x);
-      int cnt = 0;
-      bool over = false;
-      for_each_partner(G, table, epoch, i, cx, cy, cz, [&](int64_t j, int ox, int oy, int oz) {
-        const float4 fj = has_f ? __ldg(&posf[j]) : fi;
-        bool near, touch;
-        PairGeom<T> g;
-        verlet_pair(G, pi, ri, has_f, fi, fj, pos, j, ox, oy, oz, skin, near, touch, g);
-        if (near) {
-          if (cnt < nb.cap)
-            row[cnt++] = (int32_t)j;
-          else
-            over = true;
-        }
-        if (touch) add_force(P, g, vi, ldg(&vel[j]), mi, granule_mass(P, radius_of(ldg(&pos[j]))), F0, F1, F2,
-                             coincident);
-      });
-      nb.count[i] = cnt;
-      nb.at[i] = (int32_t)i;  // after a build, slot = sorted index
-      nb.cur[i] = (int32_t)i;
-      nb.ref_cell[i] = ci;
-      reinterpret_cast<pos_t<T>*>(nb.ref_pos)[i] = pi;
-      const int32_t idi = id[i];
-      if (idi >= 0 && (int64_t)idi < n) nb.slot[idi] = (int32_t)i;
-      if (over) atomicOr(&nb.flags[kNbOverflow], 1u);
+      verlet_build_granule(G, P, nb, table, n, i, cx, cy, cz, ci, pi, ri, mi, vi, has_f, fi, skin, id, pos, posf, vel,
+                           F0, F1, F2, coincident);
     } else {
       verlet_list_force(G, P, nb, i, cx, cy, cz, ci, pi, ri, mi, vi, has_f, fi, cell, pos, posf, vel, F0, F1, F2,
                         coincident);
@@ -593,12 +572,19 @@ static int check_neighbors(const GicNeighbors* nb, const GicGranules* s, const c
 
 namespace gic {
 
+// Grid of the list build: at most 2048 CTAs of 128 (grid-stride beyond).
+static unsigned build_blocks(int64_t n) {
+  unsigned b = grid_blocks(n, 128);
+  return b < 2048u ? b : 2048u;
+}
+
 int verlet_prelude(const DGrid& G, const GicParams* params, const GicGranules* s, const void* table,
-                   const GicNeighbors* nb, void* F_c, cudaStream_t stream, const char* what, NbDev* out) {
+                   const GicNeighbors* nb, void* F_c, cudaStream_t stream, const char* what, NbDev* out,
+                   bool launch_build) {
   int rc;
   if ((rc = check_table(table))) return rc;
   if ((rc = check_neighbors(nb, s, what))) return rc;
-  if (!F_c) return set_error(GIC_ERR_INVALID, "%s: F_c is NULL", what);
+  if (launch_build && !F_c) return set_error(GIC_ERR_INVALID, "%s: F_c is NULL", what);
   if ((rc = check_vecs(s->precision, what, {F_c}))) return rc;
   NbDev d{nb->cap, nb->list, nb->count, nb->ref_cell, nb->ref_pos, nb->slot, nb->cur, nb->at, nb->flags};
   *out = d;
@@ -610,7 +596,8 @@ int verlet_prelude(const DGrid& G, const GicParams* params, const GicGranules* s
     const double lim = half * G.inv_unit;  // skin / 2 in 2^-30 h_c units
     k_verlet_check<float><<<grid_blocks(s->n, 256), 256, 0, stream>>>(G, s->n, s->cell, (const uint4*)s->pos, s->id, d,
                                                                       (float)(lim * lim));
-    k_contact_verlet<float, true><<<grid_blocks(s->n, 128), 128, 0, stream>>>(
+    if (launch_build)
+    k_contact_verlet<float, true><<<build_blocks(s->n), 128, 0, stream>>>(
         G, P, s->n, s->cell, (const uint4*)s->pos, (const float4*)s->posf, (const float4*)s->vel, s->id,
         (const uint4*)table, d, (float)nb->skin, (float4*)F_c, status_word());
   } else {
@@ -618,11 +605,12 @@ int verlet_prelude(const DGrid& G, const GicParams* params, const GicGranules* s
     if ((rc = make_params(params, &P))) return rc;
     k_verlet_check<double><<<grid_blocks(s->n, 256), 256, 0, stream>>>(G, s->n, s->cell, (const d4*)s->pos, s->id, d,
                                                                        half * half);
-    k_contact_verlet<double, true><<<grid_blocks(s->n, 128), 128, 0, stream>>>(
+    if (launch_build)
+    k_contact_verlet<double, true><<<build_blocks(s->n), 128, 0, stream>>>(
         G, P, s->n, s->cell, (const d4*)s->pos, nullptr, (const d4*)s->vel, s->id, (const uint4*)table, d, nb->skin,
         (d4*)F_c, status_word());
   }
-  count_launches(2);
+  count_launches(launch_build ? 2 : 1);
   return GIC_OK;
 }
 
@@ -635,7 +623,7 @@ extern "C" int gic_contact_verlet(const GicGrid* grid, const GicParams* params, 
   if (rc) return rc;
   if ((rc = check_granules(s, "gic_contact_verlet", true))) return rc;
   NbDev d;
-  if ((rc = verlet_prelude(G, params, s, table, nb, F_c, stream, "gic_contact_verlet", &d))) return rc;
+  if ((rc = verlet_prelude(G, params, s, table, nb, F_c, stream, "gic_contact_verlet", &d, true))) return rc;
   if (s->n == 0) return GIC_OK;
   if (s->precision == GIC_FP32) {
     DParams<float> P;
@@ -675,7 +663,7 @@ extern "C" int gic_contact_verlet_adj(const GicGrid* grid, const GicParams* para
     return set_error(GIC_ERR_INVALID, "gic_contact_verlet_adj: null gradient array");
   if ((rc = check_vecs(s->precision, "gic_contact_verlet_adj", {gF_c, g_pos, g_vel}))) return rc;
   NbDev d;
-  if ((rc = verlet_prelude(G, params, s, table, nb, F_c, stream, "gic_contact_verlet_adj", &d))) return rc;
+  if ((rc = verlet_prelude(G, params, s, table, nb, F_c, stream, "gic_contact_verlet_adj", &d, true))) return rc;
   if (s->n == 0) return GIC_OK;
   const int threads = 128;
   if (s->precision == GIC_FP32) {

@@ -452,10 +452,49 @@ __device__ __forceinline__ void add_walls(const DGrid& G, const DParams<T>& P, c
 }
 
 // Host side of a Verlet call up to the list walk: argument checks, the
-// displacement check and the build launch (F_c holds the build's forces when
-// it ran).  Fills the device view of the lists.
+// displacement check and (launch_build) the build launch, after which F_c
+// holds the build's forces when it ran.  Fills the device view of the lists.
 int verlet_prelude(const DGrid& G, const GicParams* params, const GicGranules* s, const void* table,
-                   const GicNeighbors* nb, void* F_c, cudaStream_t stream, const char* what, NbDev* out);
+                   const GicNeighbors* nb, void* F_c, cudaStream_t stream, const char* what, NbDev* out,
+                   bool launch_build);
+
+// The list build of granule i (cell walk with the pre-test radius r_i + r_j
+// + skin; slot = sorted index) and its contact forces, walls excluded.
+template <typename T>
+__device__ __forceinline__ void verlet_build_granule(const DGrid& G, const DParams<T>& P, const NbDev& nb,
+                                                     const uint4* __restrict__ table, int64_t n, int64_t i,
+                                                     int cx, int cy, int cz, int32_t ci, const pos_t<T>& pi, T ri,
+                                                     T mi, const vec_t<T>& vi, bool has_f, const float4& fi, T skin,
+                                                     const int32_t* __restrict__ id, const pos_t<T>* __restrict__ pos,
+                                                     const float4* __restrict__ posf,
+                                                     const vec_t<T>* __restrict__ vel, T& F0, T& F1, T& F2,
+                                                     bool& coincident) {
+  int32_t* row = nb.list + i * nb.cap;
+  const uint32_t epoch = __ldg(&table[0].x);
+  int cnt = 0;
+  bool over = false;
+  for_each_partner(G, table, epoch, i, cx, cy, cz, [&](int64_t j, int ox, int oy, int oz) {
+    const float4 fj = has_f ? __ldg(&posf[j]) : fi;
+    bool near, touch;
+    PairGeom<T> g;
+    verlet_pair(G, pi, ri, has_f, fi, fj, pos, j, ox, oy, oz, skin, near, touch, g);
+    if (near) {
+      if (cnt < nb.cap)
+        row[cnt++] = (int32_t)j;
+      else
+        over = true;
+    }
+    if (touch) add_force(P, g, vi, ldg(&vel[j]), mi, granule_mass(P, radius_of(ldg(&pos[j]))), F0, F1, F2, coincident);
+  });
+  nb.count[i] = cnt;
+  nb.at[i] = (int32_t)i;  // after a build, slot = sorted index
+  nb.cur[i] = (int32_t)i;
+  nb.ref_cell[i] = ci;
+  reinterpret_cast<pos_t<T>*>(nb.ref_pos)[i] = pi;
+  const int32_t idi = id[i];
+  if (idi >= 0 && (int64_t)idi < n) nb.slot[idi] = (int32_t)i;
+  if (over) atomicOr(&nb.flags[kNbOverflow], 1u);
+}
 
 // Called by every thread of the last launch of a Verlet call: the last CTA
 // to finish clears the per-call words (after a build: records an overflow

@@ -1,6 +1,6 @@
 // gic_substep.cu -- one SandSubstep (Alg. 2) after the sort, fused into one
 // pass over the sorted state: contact forces from the Verlet lists (or, on a
-// substep that rebuilt them, from the build launch), the G2P coupling
+// substep that rebuilds them, from the 27-cell walk that builds them), the G2P coupling
 // (Sec. 3.3), the virtual-mass integration (Sec. 5.2) into the next state,
 // and the P2G scatter of F_s at the old positions and, when asked, of
 // alpha_s at the new ones.  The per-granule force arrays of the separate
@@ -17,7 +17,7 @@ template <typename T>
 __global__ void __launch_bounds__(kSubstepThreads, sizeof(T) == 4 ? 4 : 2) k_substep(
     DGrid G, DParams<T> P, int64_t n, const int32_t* __restrict__ cell, const pos_t<T>* __restrict__ pos,
     const float4* __restrict__ posf, const vec_t<T>* __restrict__ vel, const int32_t* __restrict__ id, NbDev nb,
-    const vec_t<T>* __restrict__ Fc_built, Fields<T> Fd, int32_t* __restrict__ cell_out, pos_t<T>* __restrict__ pos_out,
+    const uint4* __restrict__ table, T skin, Fields<T> Fd, int32_t* __restrict__ cell_out, pos_t<T>* __restrict__ pos_out,
     vec_t<T>* __restrict__ vel_out, int32_t* __restrict__ id_out, vec_t<T>* __restrict__ fex_out,
     double* __restrict__ alpha, T* __restrict__ Fs_u, T* __restrict__ Fs_v, T* __restrict__ Fs_w,
     double* __restrict__ sums, uint32_t* status) {
@@ -42,17 +42,16 @@ __global__ void __launch_bounds__(kSubstepThreads, sizeof(T) == 4 ? 4 : 2) k_sub
     // a2: contact
     T F0 = 0, F1 = 0, F2 = 0;
     bool coincident = false;
-    if (rebuild) {
-      const vec_t<T> f = Fc_built[i];
-      F0 = f.x;
-      F1 = f.y;
-      F2 = f.z;
-    } else {
+    {
       const int cx = cell_x(ci), cy = cell_y(ci), cz = cell_z(ci);
       const bool has_f = sizeof(T) == 4 && posf != nullptr;
       const float4 fi = has_f ? __ldg(&posf[i]) : make_float4(0.f, 0.f, 0.f, 0.f);
-      verlet_list_force(G, P, nb, i, cx, cy, cz, ci, pi, ri, mi, vi, has_f, fi, cell, pos, posf, vel, F0, F1, F2,
-                        coincident);
+      if (rebuild)  // this substep rebuilds the lists: walk the 27 cells
+        verlet_build_granule(G, P, nb, table, n, i, cx, cy, cz, ci, pi, ri, mi, vi, has_f, fi, skin, id, pos, posf,
+                             vel, F0, F1, F2, coincident);
+      else
+        verlet_list_force(G, P, nb, i, cx, cy, cz, ci, pi, ri, mi, vi, has_f, fi, cell, pos, posf, vel, F0, F1, F2,
+                          coincident);
       if (P.walls) add_walls(G, P, pi, ri, mi, vi, cx, cy, cz, F0, F1, F2, status);
       if (coincident) flags |= GIC_STATUS_COINCIDENT;
       if (!isfinite(F0) || !isfinite(F1) || !isfinite(F2)) flags |= GIC_STATUS_NONFINITE;
@@ -161,8 +160,7 @@ using namespace gic;
 
 extern "C" int gic_substep(const GicGrid* grid, const GicParams* params, const GicGranules* sorted,
                            const void* cell_table, const GicNeighbors* nb, const void* u, const void* v,
-                           const void* w, const void* p, const void* alpha_f, GicGranules* next, void* F_c,
-                           void* f_ex, double* alpha_s, void* Fs_u, void* Fs_v, void* Fs_w, double* sums2,
+                           const void* w, const void* p, const void* alpha_f, GicGranules* next, void* f_ex, double* alpha_s, void* Fs_u, void* Fs_v, void* Fs_w, double* sums2,
                            gic_stream_t stream) {
   DGrid G;
   int rc = make_grid(grid, &G);
@@ -178,7 +176,7 @@ extern "C" int gic_substep(const GicGrid* grid, const GicParams* params, const G
   if (sums2 && !alpha_s) return set_error(GIC_ERR_INVALID, "gic_substep: sums2 needs alpha_s");
   if ((rc = check_vecs(s->precision, "gic_substep", {f_ex}))) return rc;
   NbDev d;
-  if ((rc = verlet_prelude(G, params, s, cell_table, nb, F_c, stream, "gic_substep", &d))) return rc;
+  if ((rc = verlet_prelude(G, params, s, cell_table, nb, nullptr, stream, "gic_substep", &d, false))) return rc;
   const int64_t ncell = (int64_t)G.nx * G.ny * G.nz;
   if (alpha_s) alpha_begin(alpha_s, ncell, sums2, stream);
   if (s->n > 0) {
@@ -188,14 +186,14 @@ extern "C" int gic_substep(const GicGrid* grid, const GicParams* params, const G
       if ((rc = make_params(params, &P))) return rc;
       k_substep<float><<<blocks, kSubstepThreads, 0, stream>>>(
           G, P, s->n, s->cell, (const uint4*)s->pos, (const float4*)s->posf, (const float4*)s->vel, s->id, d,
-          (const float4*)F_c, fields<float>(u, v, w, p, alpha_f), next->cell, (uint4*)next->pos, (float4*)next->vel,
+          (const uint4*)cell_table, (float)nb->skin, fields<float>(u, v, w, p, alpha_f), next->cell, (uint4*)next->pos, (float4*)next->vel,
           next->id, (float4*)f_ex, alpha_s, (float*)Fs_u, (float*)Fs_v, (float*)Fs_w, sums2, status_word());
     } else {
       DParams<double> P;
       if ((rc = make_params(params, &P))) return rc;
       k_substep<double><<<blocks, kSubstepThreads, 0, stream>>>(
-          G, P, s->n, s->cell, (const d4*)s->pos, nullptr, (const d4*)s->vel, s->id, d, (const d4*)F_c,
-          fields<double>(u, v, w, p, alpha_f), next->cell, (d4*)next->pos, (d4*)next->vel, next->id, (d4*)f_ex,
+          G, P, s->n, s->cell, (const d4*)s->pos, nullptr, (const d4*)s->vel, s->id, d, (const uint4*)cell_table,
+          nb->skin, fields<double>(u, v, w, p, alpha_f), next->cell, (d4*)next->pos, (d4*)next->vel, next->id, (d4*)f_ex,
           alpha_s, (double*)Fs_u, (double*)Fs_v, (double*)Fs_w, sums2, status_word());
     }
     count_launches(1);

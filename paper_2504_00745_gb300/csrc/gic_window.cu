@@ -176,7 +176,7 @@ extern "C" int gic_window_forward(const GicGrid* grid, const GicParams* params, 
     bool last = s == K - 1;
     if ((rc = gic_sort(grid, state, &B, perm, cell_table, base + L.off_sort, L.sort_ws, stream))) return rc;
     if (verlet) {  // the rest of the substep fused
-      if ((rc = gic_substep(grid, params, &B, cell_table, &nb, u, v, w, p, alpha_f, state, Fc, nullptr,
+      if ((rc = gic_substep(grid, params, &B, cell_table, &nb, u, v, w, p, alpha_f, state, nullptr,
                             last ? alpha_s : nullptr, Fs_u, Fs_v, Fs_w, last ? sums2 : nullptr, stream)))
         return rc;
       continue;

@@ -73,7 +73,7 @@ _SIGS = {
     "gic_sort_static": [_P, _P, _P, _P, _P, _P],
     "gic_contact_verlet": [_P, _P, _P, _P, _P, _P, _P],
     "gic_neighbors_reset": [_P, _P],
-    "gic_substep": [_P] * 19,
+    "gic_substep": [_P] * 18,
     "gic_contact_verlet_adj": [_P] * 11,
 }
 # entry points that exist in include/gic.h but are declared optional here
@@ -290,10 +290,10 @@ def gic_contact_verlet(grid: GicGrid, params: GicParams, st: State, cell_table, 
 
 
 def gic_substep(grid: GicGrid, params: GicParams, sorted_: State, cell_table, nb: Neighbors, u, v, w, p, alpha_f,
-                next_: State, F_c, f_ex=None, alpha_s=None, Fs=(None, None, None), sums2=None, stream=None):
+                next_: State, f_ex=None, alpha_s=None, Fs=(None, None, None), sums2=None, stream=None):
     s, t, b = sorted_.struct(), next_.struct(), nb.struct()
     _check(lib().gic_substep(C.byref(grid), C.byref(params), C.byref(s), _ptr(cell_table), C.byref(b), _ptr(u),
-                             _ptr(v), _ptr(w), _ptr(p), _ptr(alpha_f), C.byref(t), _ptr(F_c), _ptr(f_ex),
+                             _ptr(v), _ptr(w), _ptr(p), _ptr(alpha_f), C.byref(t), _ptr(f_ex),
                              _ptr(alpha_s), _ptr(Fs[0]), _ptr(Fs[1]), _ptr(Fs[2]), _ptr(sums2), _stream(stream)),
            "gic_substep")
 

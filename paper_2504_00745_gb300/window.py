@@ -124,7 +124,7 @@ class Simulator:
         """Everything after the sort as one gic_substep: B -> A."""
         F = self.fluid
         gic.gic_substep(self.grid, self.params, self.B, self.table, self.nb, F.u, F.v, F.w, F.p, F.alpha_f, self.A,
-                        self.F_c, None, self.alpha_s if alpha else None,
+                        None, self.alpha_s if alpha else None,
                         self.Fs if transfer else (None, None, None), self.sums if (sums and alpha) else None, stream)
 
     def contact(self, stream=None):

@@ -145,7 +145,8 @@ def test_fused_substep_matches_separate_calls(name, prec):
     (xa, va, aa, Fa, sa), (xb, vb, ab, Fb, sb) = out
     assert np.array_equal(xa, xb)
     assert np.array_equal(va, vb)
-    assert np.array_equal(aa, ab) if prec == FP32 else np.abs(aa - ab).max() <= 1e-15
+    # FP32: exact integer accumulation; FP64: double atomics in another order (<= ~200 terms of <= 0.3)
+    assert np.array_equal(aa, ab) if prec == FP32 else np.abs(aa - ab).max() <= 1e-13
     for fa, fb in zip(Fa, Fb):
         assert np.abs(fa - fb).max() <= (1e-6 if prec == FP32 else 1e-12) * max(np.abs(fb).max(), 1e-300)
     assert np.allclose(sa, sb, rtol=1e-12, atol=0)
@@ -157,14 +158,13 @@ def test_fused_substep_argument_errors():
     F = sim.fluid
     gic.gic_sort(sim.grid, sim.A, sim.B, sim.perm, sim.table, sim.ws)
     with pytest.raises(gic.GicError, match="null fluid"):
-        gic.gic_substep(sim.grid, sim.params, sim.B, sim.table, sim.nb, None, F.v, F.w, F.p, F.alpha_f, sim.A,
-                        sim.F_c)
+        gic.gic_substep(sim.grid, sim.params, sim.B, sim.table, sim.nb, None, F.v, F.w, F.p, F.alpha_f, sim.A)
     with pytest.raises(gic.GicError, match="all three"):
         gic.gic_substep(sim.grid, sim.params, sim.B, sim.table, sim.nb, F.u, F.v, F.w, F.p, F.alpha_f, sim.A,
-                        sim.F_c, Fs=(sim.Fs[0], None, None))
+                        Fs=(sim.Fs[0], None, None))
     with pytest.raises(gic.GicError, match="sums2 needs alpha_s"):
         gic.gic_substep(sim.grid, sim.params, sim.B, sim.table, sim.nb, F.u, F.v, F.w, F.p, F.alpha_f, sim.A,
-                        sim.F_c, sums2=sim.sums)
+                        sums2=sim.sums)
 
 
 @pytest.mark.parametrize("name", ["dense_block", "random_cloud"])
