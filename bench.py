@@ -35,6 +35,10 @@ UNIT = "granule-substeps/s"
 ALGO_BYTES = {"gic_sort": 88, "gic_contact": 48, "gic_g2p_couple": 65, "gic_integrate": 120, "gic_p2g": 32,
               "gic_substep": 72}
 P2G_ALPHA_BYTES = 20
+# DRAM bytes (read + write) of one launch of the dominant entry point's main
+# kernel (k_substep for gic_substep), from an ncu capture of the current
+# kernel on the same workload (a list-walk substep; ncu flushes the caches)
+NCU_TRAFFIC = {("dam_break_1m", "gic_substep"): 174.19e6}
 
 
 def algo_bytes(name, K):
@@ -301,7 +305,8 @@ def run_gpu(args, ws, rank, local):
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     achieved = algo_bytes(dom, K) * n / (per_call[dom] / 1000.0) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": None, "kernel": dom, "peak_source": "measured" if peaks else "fallback",
+                "traffic": NCU_TRAFFIC.get((prob.name, dom)), "kernel": dom,
+                "peak_source": "measured" if peaks else "fallback",
                 "per_call_ms": per_call,
                 "per_call_frac": {k: algo_bytes(k, K) * n / (v / 1000.0) / 1e9 / hbm for k, v in per_call.items()},
                 "algo_bytes_per_granule": {k: algo_bytes(k, K) for k in per_call}}
