@@ -33,7 +33,7 @@ UNIT = "granule-substeps/s"
 # The fused substep (contact, G2P, integrate, P2G after the sort) reads the
 # sorted state and writes the next one: 36 + 36 B.
 ALGO_BYTES = {"gic_sort": 88, "gic_contact": 48, "gic_g2p_couple": 65, "gic_integrate": 120, "gic_p2g": 32,
-              "gic_substep": 72}
+              "gic_substep": 72, "gic_step": 72}
 P2G_ALPHA_BYTES = 20
 # DRAM bytes (read + write) of one launch of the dominant entry point's main
 # kernel (k_substep for gic_substep), from an ncu capture of the current
@@ -44,7 +44,7 @@ NCU_TRAFFIC = {("dam_break_1m", "gic_substep"): 174.19e6}
 def algo_bytes(name, K):
     """Algorithmic bytes per granule of one call of `name`, averaged over a
     K-substep window."""
-    return ALGO_BYTES[name] + (P2G_ALPHA_BYTES / K if name in ("gic_p2g", "gic_substep") else 0.0)
+    return ALGO_BYTES[name] + (P2G_ALPHA_BYTES / K if name in ("gic_p2g", "gic_substep", "gic_step") else 0.0)
 
 
 def parse():

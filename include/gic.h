@@ -256,6 +256,21 @@ int gic_substep(const GicGrid* grid, const GicParams* params, const GicGranules*
                 const void* alpha_f, GicGranules* next, void* f_ex, double* alpha_s, void* Fs_u, void* Fs_v,
                 void* Fs_w, double* sums2, gic_stream_t stream);
 
+/* One whole substep (Alg. 2 body with the sort in front) on a state kept
+ * with Verlet lists: the displacement check of `state` against the lists,
+ * then the sort of `state` into `sorted` ONLY when the lists are rebuilt in
+ * this call (otherwise `sorted` is a copy in the current order, perm the
+ * identity and the cell table keeps the last sort's entries), then
+ * gic_substep from `sorted` back into `state`.  Between list builds the
+ * neighbour search needs no sort, and the granules stay in the last sort's
+ * (Morton) order.  The decision stays on the device: eleven to fourteen
+ * launches, no host sync.  Arguments as for gic_sort and gic_substep
+ * (state and sorted must carry ids); perm is written every call. */
+int gic_step(const GicGrid* grid, const GicParams* params, GicGranules* state, GicGranules* sorted, int32_t* perm,
+             void* cell_table, void* ws, size_t ws_bytes, const GicNeighbors* nb, const void* u, const void* v,
+             const void* w, const void* p, const void* alpha_f, double* alpha_s, void* Fs_u, void* Fs_v, void* Fs_w,
+             double* sums2, gic_stream_t stream);
+
 /* Request a rebuild at the next gic_contact_verlet and clear the counters
  * (flags = {0, 1, 0, 0, 0, ...}). */
 int gic_neighbors_reset(const GicNeighbors* nb, gic_stream_t stream);
@@ -340,11 +355,12 @@ int gic_p2g_adj(const GicGrid* grid, const GicParams* params, const GicGranules*
  * state, the permutation and the per-granule force arrays). */
 int gic_window_workspace_size(const GicGrid* grid, int64_t n, int32_t precision, size_t* bytes);
 
-/* K substeps of Alg. 2 (SandSubstep): per substep gic_sort, then gic_substep
- * (Verlet lists with skin 0.075 h_c and 64 partners per granule, kept in the
- * workspace) when state->id is set, else gic_contact, gic_g2p_couple,
- * gic_integrate and gic_p2g.  `state` is updated in place and ends
- * in the sorted order of the last substep (state->id, if set, maps it back).
+/* K substeps of Alg. 2 (SandSubstep): per substep gic_step (Verlet lists
+ * with skin 0.075 h_c and 64 partners per granule, kept in the workspace; the
+ * sort runs on list rebuilds) when state->id is set, else gic_sort,
+ * gic_contact, gic_g2p_couple, gic_integrate and gic_p2g.  `state` is
+ * updated in place and ends in the order of the last sort (state->id, if
+ * set, maps it back).
  * alpha_s (may be NULL) is computed once, at the final positions (Alg. 1
  * CalTargetFraction); F_s (all three or none) accumulates over the K
  * substeps; sums2 (may be NULL) goes with alpha_s.

@@ -394,21 +394,52 @@ __global__ void k_contact_pairs(DGrid G, int64_t n, const int32_t* __restrict__ 
   if (counts) counts[i] = cnt;
 }
 
+// Optional copy of the checked state into a second state (same order), for a
+// caller whose sort may be skipped: cell, position record, velocity, id, the
+// FP32 float positions and an identity permutation.
+template <typename T>
+struct StateCopy {
+  const vec_t<T>* vel;
+  int32_t* cell_out;
+  pos_t<T>* pos_out;
+  vec_t<T>* vel_out;
+  int32_t* id_out;
+  float4* posf_out;
+  int32_t* perm_out;
+};
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_verlet_check(DGrid G, int64_t n, const int32_t* __restrict__ cell,
                                                        const pos_t<T>* __restrict__ pos,
-                                                       const int32_t* __restrict__ id, NbDev nb, T lim2) {
+                                                       const int32_t* __restrict__ id, NbDev nb, T lim2,
+                                                       StateCopy<T> cp) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   bool far = false;
-  if (i < n && !nb.flags[kNbSticky]) {  // after a reset the slots are not set yet
-    int32_t k = id[i];
-    int32_t s = (k >= 0 && (int64_t)k < n) ? nb.slot[k] : -1;
-    if (s >= 0 && (int64_t)s < n) {
-      nb.cur[s] = (int32_t)i;
-      nb.at[i] = s;
-      far = moved_far(G, cell[i], pos[i], nb.ref_cell[s], reinterpret_cast<const pos_t<T>*>(nb.ref_pos)[s], lim2);
-    } else {
-      far = true;  // ids outside 0..n-1: rebuild (the build path does not need them)
+  if (i < n) {
+    const int32_t c = cell[i];
+    const pos_t<T> p = pos[i];
+    const int32_t k = id[i];
+    if (!nb.flags[kNbSticky]) {  // after a reset the slots are not set yet
+      int32_t s = (k >= 0 && (int64_t)k < n) ? nb.slot[k] : -1;
+      if (s >= 0 && (int64_t)s < n) {
+        nb.cur[s] = (int32_t)i;
+        nb.at[i] = s;
+        far = moved_far(G, c, p, nb.ref_cell[s], reinterpret_cast<const pos_t<T>*>(nb.ref_pos)[s], lim2);
+      } else {
+        far = true;  // ids outside 0..n-1: rebuild (the build path does not need them)
+      }
+    }
+    if (cp.cell_out) {
+      cp.cell_out[i] = c;
+      cp.pos_out[i] = p;
+      cp.vel_out[i] = cp.vel[i];
+      cp.id_out[i] = k;
+      cp.perm_out[i] = (int32_t)i;
+      if constexpr (sizeof(T) == 4) {
+        if (cp.posf_out)
+          cp.posf_out[i] = make_float4((float)p.x * 0x1p-30f, (float)p.y * 0x1p-30f, (float)p.z * 0x1p-30f,
+                                       __uint_as_float(p.w));
+      }
     }
   }
   if (__any_sync(0xffffffffu, far) && lane_id() == 0) atomicOr(&nb.flags[kNbRebuild], 1u);
@@ -578,39 +609,59 @@ static unsigned build_blocks(int64_t n) {
   return b < 2048u ? b : 2048u;
 }
 
+int verlet_check(const DGrid& G, const GicGranules* s, const void* table, const GicNeighbors* nb,
+                 cudaStream_t stream, const char* what, NbDev* out, GicGranules* copy_to, int32_t* perm) {
+  int rc;
+  if ((rc = check_table(table))) return rc;
+  if ((rc = check_neighbors(nb, s, what))) return rc;
+  NbDev d{nb->cap, nb->list, nb->count, nb->ref_cell, nb->ref_pos, nb->slot, nb->cur, nb->at, nb->flags};
+  *out = d;
+  if (s->n == 0) return GIC_OK;
+  if (copy_to && (!perm || !copy_to->id)) return set_error(GIC_ERR_INVALID, "%s: copy needs ids and perm", what);
+  const double half = 0.5 * nb->skin;
+  if (s->precision == GIC_FP32) {
+    const double lim = half * G.inv_unit;  // skin / 2 in 2^-30 h_c units
+    StateCopy<float> cp{};
+    if (copy_to)
+      cp = StateCopy<float>{(const float4*)s->vel, copy_to->cell, (uint4*)copy_to->pos, (float4*)copy_to->vel,
+                            copy_to->id, (float4*)copy_to->posf, perm};
+    k_verlet_check<float><<<grid_blocks(s->n, 256), 256, 0, stream>>>(G, s->n, s->cell, (const uint4*)s->pos, s->id, d,
+                                                                      (float)(lim * lim), cp);
+  } else {
+    StateCopy<double> cp{};
+    if (copy_to)
+      cp = StateCopy<double>{(const d4*)s->vel, copy_to->cell, (d4*)copy_to->pos, (d4*)copy_to->vel, copy_to->id,
+                             nullptr, perm};
+    k_verlet_check<double><<<grid_blocks(s->n, 256), 256, 0, stream>>>(G, s->n, s->cell, (const d4*)s->pos, s->id, d,
+                                                                       half * half, cp);
+  }
+  count_launches(1);
+  return GIC_OK;
+}
+
 int verlet_prelude(const DGrid& G, const GicParams* params, const GicGranules* s, const void* table,
                    const GicNeighbors* nb, void* F_c, cudaStream_t stream, const char* what, NbDev* out,
                    bool launch_build) {
   int rc;
-  if ((rc = check_table(table))) return rc;
-  if ((rc = check_neighbors(nb, s, what))) return rc;
   if (launch_build && !F_c) return set_error(GIC_ERR_INVALID, "%s: F_c is NULL", what);
   if ((rc = check_vecs(s->precision, what, {F_c}))) return rc;
-  NbDev d{nb->cap, nb->list, nb->count, nb->ref_cell, nb->ref_pos, nb->slot, nb->cur, nb->at, nb->flags};
-  *out = d;
-  if (s->n == 0) return GIC_OK;
-  const double half = 0.5 * nb->skin;
+  if ((rc = verlet_check(G, s, table, nb, stream, what, out, nullptr, nullptr))) return rc;
+  if (s->n == 0 || !launch_build) return GIC_OK;
+  const NbDev d = *out;
   if (s->precision == GIC_FP32) {
     DParams<float> P;
     if ((rc = make_params(params, &P))) return rc;
-    const double lim = half * G.inv_unit;  // skin / 2 in 2^-30 h_c units
-    k_verlet_check<float><<<grid_blocks(s->n, 256), 256, 0, stream>>>(G, s->n, s->cell, (const uint4*)s->pos, s->id, d,
-                                                                      (float)(lim * lim));
-    if (launch_build)
     k_contact_verlet<float, true><<<build_blocks(s->n), 128, 0, stream>>>(
         G, P, s->n, s->cell, (const uint4*)s->pos, (const float4*)s->posf, (const float4*)s->vel, s->id,
         (const uint4*)table, d, (float)nb->skin, (float4*)F_c, status_word());
   } else {
     DParams<double> P;
     if ((rc = make_params(params, &P))) return rc;
-    k_verlet_check<double><<<grid_blocks(s->n, 256), 256, 0, stream>>>(G, s->n, s->cell, (const d4*)s->pos, s->id, d,
-                                                                       half * half);
-    if (launch_build)
     k_contact_verlet<double, true><<<build_blocks(s->n), 128, 0, stream>>>(
         G, P, s->n, s->cell, (const d4*)s->pos, nullptr, (const d4*)s->vel, s->id, (const uint4*)table, d, nb->skin,
         (d4*)F_c, status_word());
   }
-  count_launches(launch_build ? 2 : 1);
+  count_launches(1);
   return GIC_OK;
 }
 

@@ -457,6 +457,11 @@ __device__ __forceinline__ void add_walls(const DGrid& G, const DParams<T>& P, c
 int verlet_prelude(const DGrid& G, const GicParams* params, const GicGranules* s, const void* table,
                    const GicNeighbors* nb, void* F_c, cudaStream_t stream, const char* what, NbDev* out,
                    bool launch_build);
+// The displacement check alone (maps the state's ids to slots, sets the
+// rebuild word); with copy_to, it also copies the state into copy_to in the
+// same order and writes the identity into perm.
+int verlet_check(const DGrid& G, const GicGranules* s, const void* table, const GicNeighbors* nb,
+                 cudaStream_t stream, const char* what, NbDev* out, GicGranules* copy_to, int32_t* perm);
 
 // The list build of granule i (cell walk with the pre-test radius r_i + r_j
 // + skin; slot = sorted index) and its contact forces, walls excluded.

@@ -71,6 +71,9 @@ int make_grid(const GicGrid* g, DGrid* out);
 template <typename T>
 int make_params(const GicParams* p, DParams<T>* out);
 int check_granules(const GicGranules* s, const char* what, bool need_id = false);
+// gic_sort gated by two device words (see gic_sort.cu)
+int sort_gated(const GicGrid* grid, const GicGranules* in, GicGranules* out, int32_t* perm, void* cell_table, void* ws,
+               size_t ws_bytes, const uint32_t* gate, cudaStream_t stream);
 // per-granule vectors are real[4n]: 16-byte (FP32) / 32-byte (FP64) aligned
 int check_vecs(int32_t precision, const char* what, std::initializer_list<const void*> ptrs);
 

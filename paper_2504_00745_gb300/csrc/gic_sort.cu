@@ -22,6 +22,9 @@ constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kChunksPerWarp = 4;
 constexpr int kTile = kSortThreads * kChunksPerWarp;  // 1024 keys per CTA
 constexpr int kRadix = 256;
+// upsweep / downsweep CTAs loop over tiles: at most this many CTAs, so that a
+// gated launch that exits at once costs a short wave
+constexpr int kMaxSortCtas = 304;
 
 struct SortLayout {
   int64_t n;
@@ -68,34 +71,46 @@ static SortLayout sort_layout(const DGrid& G, int64_t n) {
 
 __device__ __forceinline__ uint32_t digit_of(uint32_t key, int shift) { return (key >> shift) & (kRadix - 1); }
 
+// A gated sort runs only when gate[0] | gate[1] != 0 (a Verlet-list rebuild in
+// this call); otherwise every kernel exits at once (the caller has copied the
+// state in its current order; the cell table keeps the last sort's entries).
+// gate == NULL: always sort.
+__device__ __forceinline__ bool sort_skipped(const uint32_t* gate) { return gate && (gate[0] | gate[1]) == 0u; }
+
 // Per-tile digit histogram.  counts[d * tiles + tile].
 template <bool kFirst>
 __global__ void __launch_bounds__(kSortThreads) k_upsweep(int64_t n, int shift, const int32_t* __restrict__ cell,
                                                           const uint32_t* __restrict__ keys,
-                                                          uint32_t* __restrict__ counts, int tiles) {
+                                                          uint32_t* __restrict__ counts, int tiles,
+                                                          const uint32_t* gate) {
+  if (sort_skipped(gate)) return;
   __shared__ uint32_t s_hist[kRadix];
-  s_hist[threadIdx.x] = 0;
-  __syncthreads();
   int warp = threadIdx.x >> 5, lane = lane_id();
-  int64_t base = (int64_t)blockIdx.x * kTile + warp * (32 * kChunksPerWarp);
+  for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    s_hist[threadIdx.x] = 0;
+    __syncthreads();
+    int64_t base = (int64_t)tile * kTile + warp * (32 * kChunksPerWarp);
 #pragma unroll
-  for (int c = 0; c < kChunksPerWarp; ++c) {
-    int64_t idx = base + c * 32 + lane;
-    bool valid = idx < n;
-    uint32_t key = 0;
-    if (valid) key = kFirst ? morton_of_cell(cell[idx]) : keys[idx];
-    uint32_t d = valid ? digit_of(key, shift) : 0xffffffffu;
-    unsigned peers = __match_any_sync(0xffffffffu, d);
-    if (valid && (peers & lanemask_lt()) == 0) atomicAdd(&s_hist[d], (uint32_t)__popc(peers));
+    for (int c = 0; c < kChunksPerWarp; ++c) {
+      int64_t idx = base + c * 32 + lane;
+      bool valid = idx < n;
+      uint32_t key = 0;
+      if (valid) key = kFirst ? morton_of_cell(cell[idx]) : keys[idx];
+      uint32_t d = valid ? digit_of(key, shift) : 0xffffffffu;
+      unsigned peers = __match_any_sync(0xffffffffu, d);
+      if (valid && (peers & lanemask_lt()) == 0) atomicAdd(&s_hist[d], (uint32_t)__popc(peers));
+    }
+    __syncthreads();
+    counts[(int64_t)threadIdx.x * tiles + tile] = s_hist[threadIdx.x];
   }
-  __syncthreads();
-  counts[(int64_t)threadIdx.x * tiles + blockIdx.x] = s_hist[threadIdx.x];
 }
 
 // Exclusive scan over tiles for one digit per CTA; totals[d] = count of digit d.
 // CTA 0 of the first pass also advances the cell-table epoch.
 __global__ void __launch_bounds__(kSortThreads) k_scan_tiles(uint32_t* __restrict__ counts, int tiles,
-                                                             uint32_t* __restrict__ totals, uint4* table_head) {
+                                                             uint32_t* __restrict__ totals, uint4* table_head,
+                                                             const uint32_t* gate) {
+  if (sort_skipped(gate)) return;
   __shared__ uint32_t s_warp[kSortWarps];
   __shared__ uint32_t s_carry;
   int d = blockIdx.x;
@@ -151,11 +166,14 @@ __global__ void __launch_bounds__(kSortThreads) k_downsweep(int64_t n, int shift
                                                             uint32_t* __restrict__ vals_out,
                                                             const uint32_t* __restrict__ counts,
                                                             const uint32_t* __restrict__ totals, int tiles,
-                                                            ScatterState S) {
+                                                            ScatterState S, const uint32_t* gate) {
+  if (sort_skipped(gate)) return;
   __shared__ uint32_t s_warp_hist[kSortWarps][kRadix];
   __shared__ uint32_t s_base[kRadix];
   __shared__ uint32_t s_scan[kSortWarps];
   int warp = threadIdx.x >> 5, lane = lane_id();
+  for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+  __syncthreads();  // the previous tile's reads of the shared arrays are done
   for (int w = 0; w < kSortWarps; ++w) s_warp_hist[w][threadIdx.x] = 0;
   // digit base = (exclusive scan of totals)[d] + (scanned count of earlier tiles)[d]
   {
@@ -169,12 +187,12 @@ __global__ void __launch_bounds__(kSortThreads) k_downsweep(int64_t n, int shift
     __syncthreads();
     uint32_t wsum = 0;
     for (int w = 0; w < warp; ++w) wsum += s_scan[w];
-    s_base[threadIdx.x] = wsum + incl - t + counts[(int64_t)threadIdx.x * tiles + blockIdx.x];
+    s_base[threadIdx.x] = wsum + incl - t + counts[(int64_t)threadIdx.x * tiles + tile];
   }
   __syncthreads();
 
   uint32_t r_key[kChunksPerWarp], r_val[kChunksPerWarp], r_rank[kChunksPerWarp];
-  int64_t base = (int64_t)blockIdx.x * kTile + warp * (32 * kChunksPerWarp);
+  int64_t base = (int64_t)tile * kTile + warp * (32 * kChunksPerWarp);
 #pragma unroll
   for (int c = 0; c < kChunksPerWarp; ++c) {
     int64_t idx = base + c * 32 + lane;
@@ -222,6 +240,7 @@ __global__ void __launch_bounds__(kSortThreads) k_downsweep(int64_t n, int shift
     else
       S.perm[pos] = (int32_t)r_val[c];
   }
+  }
 }
 
 // Gather the state into sorted order (out[k] = in[perm[k]]: perm is close to
@@ -230,10 +249,12 @@ __global__ void __launch_bounds__(kSortThreads) k_downsweep(int64_t n, int shift
 // {start, count, epoch, 0} of every occupied cell at 1 + its linear index.
 template <typename T>
 __global__ void __launch_bounds__(256) k_permute_table(DGrid G, int64_t n, const uint32_t* __restrict__ keys,
-                                                       const int32_t* __restrict__ perm, ScatterState S,
-                                                       uint4* __restrict__ table, uint32_t* status) {
+                                                       int32_t* __restrict__ perm, ScatterState S,
+                                                       uint4* __restrict__ table, uint32_t* status,
+                                                       const uint32_t* gate) {
   int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= n) return;
+  if (sort_skipped(gate)) return;  // the caller copied the state in its current order
   int32_t src = perm[k];
   int32_t c = S.in_cell[src];
   pos_t<T> p = ((const pos_t<T>*)S.in_pos)[src];
@@ -261,7 +282,7 @@ __global__ void __launch_bounds__(256) k_permute_table(DGrid G, int64_t n, const
 
 template <typename T>
 static int launch_sort(const DGrid& G, const GicGranules* in, GicGranules* out, int32_t* perm, uint4* table,
-                       char* ws, const SortLayout& L, cudaStream_t st) {
+                       char* ws, const SortLayout& L, cudaStream_t st, const uint32_t* gate = nullptr) {
   int64_t n = in->n;
   uint32_t* keys_a = (uint32_t*)(ws + L.off_keys_a);
   uint32_t* vals_a = (uint32_t*)(ws + L.off_vals_a);
@@ -276,26 +297,27 @@ static int launch_sort(const DGrid& G, const GicGranules* in, GicGranules* out, 
   uint32_t* kout = keys_a;
   uint32_t* vout = vals_a;
   int launches = 0;
+  const int grid_ctas = L.tiles < kMaxSortCtas ? L.tiles : kMaxSortCtas;
   for (int p = 0; p < L.passes; ++p) {
     int shift = 8 * p;
     bool first = p == 0, last = p == L.passes - 1;
     if (first)
-      k_upsweep<true><<<L.tiles, kSortThreads, 0, st>>>(n, shift, in->cell, nullptr, counts, L.tiles);
+      k_upsweep<true><<<grid_ctas, kSortThreads, 0, st>>>(n, shift, in->cell, nullptr, counts, L.tiles, gate);
     else
-      k_upsweep<false><<<L.tiles, kSortThreads, 0, st>>>(n, shift, nullptr, kin, counts, L.tiles);
-    k_scan_tiles<<<kRadix, kSortThreads, 0, st>>>(counts, L.tiles, totals, first ? table : nullptr);
+      k_upsweep<false><<<grid_ctas, kSortThreads, 0, st>>>(n, shift, nullptr, kin, counts, L.tiles, gate);
+    k_scan_tiles<<<kRadix, kSortThreads, 0, st>>>(counts, L.tiles, totals, first ? table : nullptr, gate);
     if (first && last)
-      k_downsweep<true, true, T><<<L.tiles, kSortThreads, 0, st>>>(n, shift, kin, vin, kout, vout, counts, totals,
-                                                                    L.tiles, S);
+      k_downsweep<true, true, T><<<grid_ctas, kSortThreads, 0, st>>>(n, shift, kin, vin, kout, vout, counts, totals,
+                                                                    L.tiles, S, gate);
     else if (first)
-      k_downsweep<true, false, T><<<L.tiles, kSortThreads, 0, st>>>(n, shift, kin, vin, kout, vout, counts, totals,
-                                                                     L.tiles, S);
+      k_downsweep<true, false, T><<<grid_ctas, kSortThreads, 0, st>>>(n, shift, kin, vin, kout, vout, counts, totals,
+                                                                     L.tiles, S, gate);
     else if (last)
-      k_downsweep<false, true, T><<<L.tiles, kSortThreads, 0, st>>>(n, shift, kin, vin, kout, vout, counts, totals,
-                                                                     L.tiles, S);
+      k_downsweep<false, true, T><<<grid_ctas, kSortThreads, 0, st>>>(n, shift, kin, vin, kout, vout, counts, totals,
+                                                                     L.tiles, S, gate);
     else
-      k_downsweep<false, false, T><<<L.tiles, kSortThreads, 0, st>>>(n, shift, kin, vin, kout, vout, counts, totals,
-                                                                      L.tiles, S);
+      k_downsweep<false, false, T><<<grid_ctas, kSortThreads, 0, st>>>(n, shift, kin, vin, kout, vout, counts, totals,
+                                                                      L.tiles, S, gate);
     launches += 3;
     kin = kout;
     vin = vout;
@@ -303,7 +325,7 @@ static int launch_sort(const DGrid& G, const GicGranules* in, GicGranules* out, 
     vout = (vout == vals_a) ? vals_b : vals_a;
   }
   // kin now holds the sorted keys
-  k_permute_table<T><<<grid_blocks(n, 256), 256, 0, st>>>(G, n, kin, perm, S, table, status_word());
+  k_permute_table<T><<<grid_blocks(n, 256), 256, 0, st>>>(G, n, kin, perm, S, table, status_word(), gate);
   launches += 1;
   count_launches(launches);
   GIC_CHECK_LAUNCH("gic_sort");
@@ -349,6 +371,35 @@ extern "C" int gic_sort(const GicGrid* grid, const GicGranules* in, GicGranules*
     return launch_sort<float>(G, in, out, perm, (uint4*)cell_table, (char*)ws, L, (cudaStream_t)stream);
   return launch_sort<double>(G, in, out, perm, (uint4*)cell_table, (char*)ws, L, (cudaStream_t)stream);
 }
+
+namespace gic {
+
+int sort_gated(const GicGrid* grid, const GicGranules* in, GicGranules* out, int32_t* perm, void* cell_table, void* ws,
+               size_t ws_bytes, const uint32_t* gate, cudaStream_t stream) {
+  DGrid G;
+  int rc = make_grid(grid, &G);
+  if (rc) return rc;
+  if ((rc = check_granules(in, "gic_step state"))) return rc;
+  if ((rc = check_granules(out, "gic_step sorted"))) return rc;
+  if (in->n != out->n || in->precision != out->precision)
+    return set_error(GIC_ERR_INVALID, "gic_step: state/sorted size or precision differ");
+  if (!cell_table) return set_error(GIC_ERR_INVALID, "gic_step: cell_table is NULL");
+  if ((uintptr_t)cell_table % 16) return set_error(GIC_ERR_ALIGN, "gic_step: cell_table must be 16-byte aligned");
+  int64_t n = in->n;
+  if (n == 0) return GIC_OK;
+  if (!perm) return set_error(GIC_ERR_INVALID, "gic_step: perm is NULL");
+  if (in->cell == out->cell || in->pos == out->pos || in->vel == out->vel)
+    return set_error(GIC_ERR_INVALID, "gic_step: state and sorted must not alias");
+  SortLayout L = sort_layout(G, n);
+  if (!ws || ws_bytes < L.total)
+    return set_error(GIC_ERR_WORKSPACE, "gic_step: workspace of %zu bytes needed, %zu given", L.total, ws_bytes);
+  if ((uintptr_t)ws % 256) return set_error(GIC_ERR_ALIGN, "gic_step: workspace must be 256-byte aligned");
+  if (in->precision == GIC_FP32)
+    return launch_sort<float>(G, in, out, perm, (uint4*)cell_table, (char*)ws, L, stream, gate);
+  return launch_sort<double>(G, in, out, perm, (uint4*)cell_table, (char*)ws, L, stream, gate);
+}
+
+}  // namespace gic
 
 // ----------------------------------------------------------------- adjoint
 

@@ -202,3 +202,57 @@ extern "C" int gic_substep(const GicGrid* grid, const GicParams* params, const G
   GIC_CHECK_LAUNCH("gic_substep");
   return GIC_OK;
 }
+
+extern "C" int gic_step(const GicGrid* grid, const GicParams* params, GicGranules* state, GicGranules* sorted,
+                        int32_t* perm, void* cell_table, void* ws, size_t ws_bytes, const GicNeighbors* nb,
+                        const void* u, const void* v, const void* w, const void* p, const void* alpha_f,
+                        double* alpha_s, void* Fs_u, void* Fs_v, void* Fs_w, double* sums2, gic_stream_t stream) {
+  DGrid G;
+  int rc = make_grid(grid, &G);
+  if (rc) return rc;
+  if ((rc = check_granules(state, "gic_step state", true))) return rc;
+  if ((rc = check_granules(sorted, "gic_step sorted", true))) return rc;
+  if (sorted->n != state->n || sorted->precision != state->precision)
+    return set_error(GIC_ERR_INVALID, "gic_step: state/sorted size or precision differ");
+  if (state->cell == sorted->cell || state->pos == sorted->pos || state->vel == sorted->vel ||
+      state->id == sorted->id)
+    return set_error(GIC_ERR_INVALID, "gic_step: state and sorted must not alias");
+  if (state->n > 0 && !perm) return set_error(GIC_ERR_INVALID, "gic_step: perm is NULL");
+  // 1. displacements of the current state against the lists (sets the rebuild
+  //    word), and the state copied into `sorted` in its current order
+  NbDev d;
+  if ((rc = verlet_check(G, state, cell_table, nb, stream, "gic_step", &d, sorted, perm))) return rc;
+  // 2. the sort over that copy, only when the lists are rebuilt
+  if ((rc = sort_gated(grid, state, sorted, perm, cell_table, ws, ws_bytes, nb->flags, stream))) return rc;
+  // 3. the fused rest of the substep, sorted -> state
+  const GicGranules* s = sorted;
+  if (!u || !v || !w || !p || !alpha_f) return set_error(GIC_ERR_INVALID, "gic_step: null fluid field");
+  bool fs = Fs_u || Fs_v || Fs_w;
+  if (fs && !(Fs_u && Fs_v && Fs_w)) return set_error(GIC_ERR_INVALID, "gic_step: give all three F_s arrays or none");
+  if (sums2 && !alpha_s) return set_error(GIC_ERR_INVALID, "gic_step: sums2 needs alpha_s");
+  const int64_t ncell = (int64_t)G.nx * G.ny * G.nz;
+  if (alpha_s) alpha_begin(alpha_s, ncell, sums2, stream);
+  if (s->n > 0) {
+    const unsigned blocks = grid_blocks(s->n, kSubstepThreads);
+    if (s->precision == GIC_FP32) {
+      DParams<float> P;
+      if ((rc = make_params(params, &P))) return rc;
+      k_substep<float><<<blocks, kSubstepThreads, 0, stream>>>(
+          G, P, s->n, s->cell, (const uint4*)s->pos, (const float4*)s->posf, (const float4*)s->vel, s->id, d,
+          (const uint4*)cell_table, (float)nb->skin, fields<float>(u, v, w, p, alpha_f), state->cell,
+          (uint4*)state->pos, (float4*)state->vel, state->id, nullptr, alpha_s, (float*)Fs_u, (float*)Fs_v,
+          (float*)Fs_w, sums2, status_word());
+    } else {
+      DParams<double> P;
+      if ((rc = make_params(params, &P))) return rc;
+      k_substep<double><<<blocks, kSubstepThreads, 0, stream>>>(
+          G, P, s->n, s->cell, (const d4*)s->pos, nullptr, (const d4*)s->vel, s->id, d, (const uint4*)cell_table,
+          nb->skin, fields<double>(u, v, w, p, alpha_f), state->cell, (d4*)state->pos, (d4*)state->vel, state->id,
+          nullptr, alpha_s, (double*)Fs_u, (double*)Fs_v, (double*)Fs_w, sums2, status_word());
+    }
+    count_launches(1);
+  }
+  if (alpha_s) alpha_end(G, s->precision, alpha_s, ncell, sums2, stream);
+  GIC_CHECK_LAUNCH("gic_step");
+  return GIC_OK;
+}

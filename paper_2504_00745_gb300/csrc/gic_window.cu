@@ -174,13 +174,13 @@ extern "C" int gic_window_forward(const GicGrid* grid, const GicParams* params, 
   // alpha_s once, at the final positions (Alg. 1 CalTargetFraction); F_s every substep (Alg. 2)
   for (int s = 0; s < K; ++s) {
     bool last = s == K - 1;
-    if ((rc = gic_sort(grid, state, &B, perm, cell_table, base + L.off_sort, L.sort_ws, stream))) return rc;
-    if (verlet) {  // the rest of the substep fused
-      if ((rc = gic_substep(grid, params, &B, cell_table, &nb, u, v, w, p, alpha_f, state, nullptr,
-                            last ? alpha_s : nullptr, Fs_u, Fs_v, Fs_w, last ? sums2 : nullptr, stream)))
+    if (verlet) {  // sort only on list rebuilds, the rest of the substep fused
+      if ((rc = gic_step(grid, params, state, &B, perm, cell_table, base + L.off_sort, L.sort_ws, &nb, u, v, w, p,
+                         alpha_f, last ? alpha_s : nullptr, Fs_u, Fs_v, Fs_w, last ? sums2 : nullptr, stream)))
         return rc;
       continue;
     }
+    if ((rc = gic_sort(grid, state, &B, perm, cell_table, base + L.off_sort, L.sort_ws, stream))) return rc;
     if ((rc = gic_contact(grid, params, &B, cell_table, Fc, stream))) return rc;
     if ((rc = gic_g2p_couple(grid, params, &B, u, v, w, p, alpha_f, Ffl, af, nullptr, stream))) return rc;
     if ((rc = gic_integrate(grid, params, &B, Fc, Ffl, af, state, fex, stream))) return rc;

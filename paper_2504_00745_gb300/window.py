@@ -38,7 +38,8 @@ class Simulator:
     as host or device tensors.  verlet_skin (metres): contact through Verlet
     lists with that skin (gic_contact_verlet, cap partners per granule)
     instead of walking the cell table every substep (gic_contact); with
-    lists and fused, everything after the sort runs as gic_substep.
+    lists and fused, a substep is one gic_step (sort only on list rebuilds,
+    then the fused gic_substep).
     """
 
     def __init__(self, grid, params, n: int, precision: int = GIC_FP32, device="cuda",
@@ -106,9 +107,19 @@ class Simulator:
         return sim
 
     # ------------------------------------------------------------ substeps
-    def substep(self, alpha: bool = True, transfer: bool = True, sums: bool = True, stream=None):
-        """One SandSubstep: A (current) -> sort -> B -> forces -> A (next)."""
+    def substep(self, alpha: bool = True, transfer: bool = True, sums: bool = True, stream=None,
+                sort_every: bool = False):
+        """One SandSubstep: A (current) -> sort -> B -> forces -> A (next).
+        With Verlet lists and the fused path the sort runs only when the
+        lists are rebuilt, unless sort_every (then B is the sorted A every
+        substep, as the adjoint's recomputation needs)."""
         F = self.fluid
+        if self.nb is not None and self.fused and not sort_every:  # sorts only when the lists are rebuilt
+            gic.gic_step(self.grid, self.params, self.A, self.B, self.perm, self.table, self.ws, self.nb, F.u, F.v,
+                         F.w, F.p, F.alpha_f, self.alpha_s if alpha else None,
+                         self.Fs if transfer else (None, None, None), self.sums if (sums and alpha) else None,
+                         stream)
+            return
         gic.gic_sort(self.grid, self.A, self.B, self.perm, self.table, self.ws, stream)
         if self.nb is not None and self.fused:
             self.fused_rest(alpha, transfer, sums, stream)
@@ -149,10 +160,13 @@ class Simulator:
             b.record(s)
             acc.setdefault(name, []).append((a, b))
 
-        timed("gic_sort", lambda: gic.gic_sort(self.grid, self.A, self.B, self.perm, self.table, self.ws, s))
         if self.nb is not None and self.fused:
-            timed("gic_substep", lambda: self.fused_rest(alpha, True, alpha, s))
+            timed("gic_step", lambda: gic.gic_step(self.grid, self.params, self.A, self.B, self.perm, self.table,
+                                                   self.ws, self.nb, F.u, F.v, F.w, F.p, F.alpha_f,
+                                                   self.alpha_s if alpha else None, self.Fs,
+                                                   self.sums if alpha else None, s))
             return
+        timed("gic_sort", lambda: gic.gic_sort(self.grid, self.A, self.B, self.perm, self.table, self.ws, s))
         timed("gic_contact", lambda: self.contact(s))
         timed("gic_g2p_couple", lambda: gic.gic_g2p_couple(self.grid, self.params, self.B, F.u, F.v, F.w, F.p,
                                                             F.alpha_f, self.F_fl, self.a_f, self.alpha_f_p, s))
@@ -208,7 +222,9 @@ class GicWindow(torch.autograd.Function):
 
     Backward: the window is cut into segments of `ckpt` substeps; the state at
     the start of each segment is kept from the forward pass, every segment is
-    recomputed from it in reverse order, and each substep's adjoint runs
+    recomputed from it in reverse order (forward and recomputation sort every
+    substep, so each substep's sorted order is the one its adjoint re-sorts
+    to), and each substep's adjoint runs
     gic_integrate_adj, gic_g2p_couple_adj, gic_contact_adj (through the
     Verlet lists when the simulator has them) and gic_sort_adj.
     """
@@ -225,7 +241,7 @@ class GicWindow(torch.autograd.Function):
         for s in range(K):
             if s % ckpt == 0:
                 ckpts.append(sim.A.clone())
-            sim.substep(alpha=False, transfer=False, sums=False)
+            sim.substep(alpha=False, transfer=False, sums=False, sort_every=True)
         x, _ = sim.positions()
         ctx.sim, ctx.K, ctx.ckpt = sim, K, ckpt
         ctx.ckpts = ckpts
@@ -257,7 +273,7 @@ class GicWindow(torch.autograd.Function):
             for s in range(s0, s1):
                 pre.append(sim.A.clone())
                 if s < s1 - 1:
-                    sim.substep(alpha=False, transfer=False, sums=False)
+                    sim.substep(alpha=False, transfer=False, sums=False, sort_every=True)
             for s in reversed(range(s0, s1)):
                 S = pre[s - s0]
                 gic.gic_sort(sim.grid, S, sim.B, sim.perm, sim.table, sim.ws)
