@@ -257,15 +257,23 @@ int gic_substep(const GicGrid* grid, const GicParams* params, const GicGranules*
                 void* Fs_w, double* sums2, gic_stream_t stream);
 
 /* One whole substep (Alg. 2 body with the sort in front) on a state kept
- * with Verlet lists: the displacement check of `state` against the lists,
- * then the sort of `state` into `sorted` ONLY when the lists are rebuilt in
- * this call (otherwise `sorted` is a copy in the current order, perm the
- * identity and the cell table keeps the last sort's entries), then
- * gic_substep from `sorted` back into `state`.  Between list builds the
- * neighbour search needs no sort, and the granules stay in the last sort's
- * (Morton) order.  The decision stays on the device: eleven to fourteen
- * launches, no host sync.  Arguments as for gic_sort and gic_substep
- * (state and sorted must carry ids); perm is written every call. */
+ * with Verlet lists: the displacement check of `state` against the lists
+ * (which also copies `state` into `sorted` in its current order and writes
+ * the identity into perm), then the sort of `state` into `sorted` ONLY when
+ * the lists are rebuilt in this call (otherwise the cell table keeps the
+ * last sort's entries), then gic_substep from `sorted` back into `state`.
+ * Between list builds the neighbour search needs no sort, and the granules
+ * stay in the last sort's (Morton) order.
+ *   The call runs as a CUDA graph whose sort is the body of a conditional
+ *   node set on the device by the check, so a substep without a rebuild
+ *   launches no sort kernel and nothing waits on the host.  The first call
+ *   with a given configuration (every argument's value, the params and the
+ *   structs' contents) builds and instantiates the graph; up to four
+ *   configurations stay cached (least recently used replaced).  The graph
+ *   bakes in the pointers: buffers must stay allocated while calls with
+ *   them may come.  Arguments as for gic_sort and gic_substep (state and
+ *   sorted must carry ids); errors as for those calls, plus GIC_ERR_CUDA if
+ *   a graph cannot be built. */
 int gic_step(const GicGrid* grid, const GicParams* params, GicGranules* state, GicGranules* sorted, int32_t* perm,
              void* cell_table, void* ws, size_t ws_bytes, const GicNeighbors* nb, const void* u, const void* v,
              const void* w, const void* p, const void* alpha_f, double* alpha_s, void* Fs_u, void* Fs_v, void* Fs_w,

@@ -30,7 +30,13 @@ int set_error(int code, const char* fmt, ...) {
   return code;
 }
 
-void count_launches(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+// Launches made while a graph is being captured are not executions: the
+// graph launches count their kernels themselves.
+thread_local bool g_capturing = false;
+void count_launches(int64_t k) {
+  if (!g_capturing) g_launches.fetch_add(k, std::memory_order_relaxed);
+}
+void set_capturing(bool on) { g_capturing = on; }
 
 // Poll the stream against a deadline instead of blocking forever.
 int wait_stream(cudaStream_t stream, int64_t timeout_ms, const char* what) {

@@ -31,6 +31,7 @@ struct alignas(32) d4 {
 // error reporting (thread-local text) and launch accounting
 int set_error(int code, const char* fmt, ...);
 void count_launches(int64_t k);
+void set_capturing(bool on);
 int wait_stream(cudaStream_t stream, int64_t timeout_ms, const char* what);
 uint32_t* status_word();  // device address of the sticky status word (current device)
 

@@ -22,8 +22,8 @@ constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kChunksPerWarp = 4;
 constexpr int kTile = kSortThreads * kChunksPerWarp;  // 1024 keys per CTA
 constexpr int kRadix = 256;
-// upsweep / downsweep CTAs loop over tiles: at most this many CTAs, so that a
-// gated launch that exits at once costs a short wave
+// upsweep / downsweep CTAs loop over tiles; a gated sort uses at most this
+// many CTAs, so that a launch that exits at once costs a short wave
 constexpr int kMaxSortCtas = 304;
 
 struct SortLayout {
@@ -297,7 +297,7 @@ static int launch_sort(const DGrid& G, const GicGranules* in, GicGranules* out, 
   uint32_t* kout = keys_a;
   uint32_t* vout = vals_a;
   int launches = 0;
-  const int grid_ctas = L.tiles < kMaxSortCtas ? L.tiles : kMaxSortCtas;
+  const int grid_ctas = (gate && L.tiles > kMaxSortCtas) ? kMaxSortCtas : L.tiles;
   for (int p = 0; p < L.passes; ++p) {
     int shift = 8 * p;
     bool first = p == 0, last = p == L.passes - 1;

@@ -5,6 +5,10 @@
 // and the P2G scatter of F_s at the old positions and, when asked, of
 // alpha_s at the new ones.  The per-granule force arrays of the separate
 // entry points (F_c, F_fl, a_f, f_ex) never leave registers.
+#include <string.h>
+
+#include <mutex>
+
 #include "gic_contact.cuh"
 #include "gic_grid.cuh"
 #include "gic_integrate.cuh"
@@ -158,9 +162,54 @@ __global__ void __launch_bounds__(kSubstepThreads, sizeof(T) == 4 ? 4 : 2) k_sub
 
 using namespace gic;
 
+namespace gic {
+
+// [zero alpha_s] -> k_substep (sorted -> next) -> [alpha_s out]; counts its
+// launches into *launches.
+static int substep_launch(const DGrid& G, const GicParams* params, const GicGranules* s, const void* cell_table,
+                          const GicNeighbors* nb, const NbDev& d, const void* u, const void* v, const void* w,
+                          const void* p, const void* alpha_f, GicGranules* next, void* f_ex, double* alpha_s,
+                          void* Fs_u, void* Fs_v, void* Fs_w, double* sums2, cudaStream_t stream, int* launches) {
+  int rc;
+  const int64_t ncell = (int64_t)G.nx * G.ny * G.nz;
+  if (alpha_s) {
+    alpha_begin(alpha_s, ncell, sums2, stream);
+    ++*launches;
+  }
+  if (s->n > 0) {
+    const unsigned blocks = grid_blocks(s->n, kSubstepThreads);
+    if (s->precision == GIC_FP32) {
+      DParams<float> P;
+      if ((rc = make_params(params, &P))) return rc;
+      k_substep<float><<<blocks, kSubstepThreads, 0, stream>>>(
+          G, P, s->n, s->cell, (const uint4*)s->pos, (const float4*)s->posf, (const float4*)s->vel, s->id, d,
+          (const uint4*)cell_table, (float)nb->skin, fields<float>(u, v, w, p, alpha_f), next->cell,
+          (uint4*)next->pos, (float4*)next->vel, next->id, (float4*)f_ex, alpha_s, (float*)Fs_u, (float*)Fs_v,
+          (float*)Fs_w, sums2, status_word());
+    } else {
+      DParams<double> P;
+      if ((rc = make_params(params, &P))) return rc;
+      k_substep<double><<<blocks, kSubstepThreads, 0, stream>>>(
+          G, P, s->n, s->cell, (const d4*)s->pos, nullptr, (const d4*)s->vel, s->id, d, (const uint4*)cell_table,
+          nb->skin, fields<double>(u, v, w, p, alpha_f), next->cell, (d4*)next->pos, (d4*)next->vel, next->id,
+          (d4*)f_ex, alpha_s, (double*)Fs_u, (double*)Fs_v, (double*)Fs_w, sums2, status_word());
+    }
+    count_launches(1);
+    ++*launches;
+  }
+  if (alpha_s) {
+    alpha_end(G, s->precision, alpha_s, ncell, sums2, stream);
+    ++*launches;
+  }
+  return GIC_OK;
+}
+
+}  // namespace gic
+
 extern "C" int gic_substep(const GicGrid* grid, const GicParams* params, const GicGranules* sorted,
                            const void* cell_table, const GicNeighbors* nb, const void* u, const void* v,
-                           const void* w, const void* p, const void* alpha_f, GicGranules* next, void* f_ex, double* alpha_s, void* Fs_u, void* Fs_v, void* Fs_w, double* sums2,
+                           const void* w, const void* p, const void* alpha_f, GicGranules* next, void* f_ex,
+                           double* alpha_s, void* Fs_u, void* Fs_v, void* Fs_w, double* sums2,
                            gic_stream_t stream) {
   DGrid G;
   int rc = make_grid(grid, &G);
@@ -177,31 +226,162 @@ extern "C" int gic_substep(const GicGrid* grid, const GicParams* params, const G
   if ((rc = check_vecs(s->precision, "gic_substep", {f_ex}))) return rc;
   NbDev d;
   if ((rc = verlet_prelude(G, params, s, cell_table, nb, nullptr, stream, "gic_substep", &d, false))) return rc;
-  const int64_t ncell = (int64_t)G.nx * G.ny * G.nz;
-  if (alpha_s) alpha_begin(alpha_s, ncell, sums2, stream);
-  if (s->n > 0) {
-    const unsigned blocks = grid_blocks(s->n, kSubstepThreads);
-    if (s->precision == GIC_FP32) {
-      DParams<float> P;
-      if ((rc = make_params(params, &P))) return rc;
-      k_substep<float><<<blocks, kSubstepThreads, 0, stream>>>(
-          G, P, s->n, s->cell, (const uint4*)s->pos, (const float4*)s->posf, (const float4*)s->vel, s->id, d,
-          (const uint4*)cell_table, (float)nb->skin, fields<float>(u, v, w, p, alpha_f), next->cell, (uint4*)next->pos, (float4*)next->vel,
-          next->id, (float4*)f_ex, alpha_s, (float*)Fs_u, (float*)Fs_v, (float*)Fs_w, sums2, status_word());
-    } else {
-      DParams<double> P;
-      if ((rc = make_params(params, &P))) return rc;
-      k_substep<double><<<blocks, kSubstepThreads, 0, stream>>>(
-          G, P, s->n, s->cell, (const d4*)s->pos, nullptr, (const d4*)s->vel, s->id, d, (const uint4*)cell_table,
-          nb->skin, fields<double>(u, v, w, p, alpha_f), next->cell, (d4*)next->pos, (d4*)next->vel, next->id, (d4*)f_ex,
-          alpha_s, (double*)Fs_u, (double*)Fs_v, (double*)Fs_w, sums2, status_word());
-    }
-    count_launches(1);
-  }
-  if (alpha_s) alpha_end(G, s->precision, alpha_s, ncell, sums2, stream);
+  int launches = 0;
+  if ((rc = substep_launch(G, params, s, cell_table, nb, d, u, v, w, p, alpha_f, next, f_ex, alpha_s, Fs_u, Fs_v, Fs_w,
+                           sums2, (cudaStream_t)stream, &launches)))
+    return rc;
   GIC_CHECK_LAUNCH("gic_substep");
   return GIC_OK;
 }
+
+namespace gic {
+
+// Sets the graph's conditional (run the sort) from the Verlet words.
+__global__ void k_step_decide(const uint32_t* flags, cudaGraphConditionalHandle h) {
+  cudaGraphSetConditional(h, (flags[kNbRebuild] | flags[kNbSticky]) != 0u ? 1u : 0u);
+}
+
+// Everything a gic_step graph depends on; a call with the same bytes reuses
+// the instantiated graph.
+struct StepKey {
+  GicGrid grid;
+  GicParams params;
+  GicGranules state, sorted;
+  GicNeighbors nb;
+  const void* ptr[13];
+  size_t ws_bytes;
+};
+
+struct StepGraph {
+  bool used = false;
+  uint64_t last = 0;
+  StepKey key;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int launches = 0;  // kernels every launch runs (the sort's are not counted)
+};
+
+constexpr int kStepGraphs = 4;
+static StepGraph g_step_graphs[kStepGraphs];
+static uint64_t g_step_clock = 0;
+static std::mutex g_step_mu;
+
+static bool same_key(const StepKey& a, const StepKey& b) { return memcmp(&a, &b, sizeof(StepKey)) == 0; }
+
+static void store_key(StepKey& k, const GicGrid* grid, const GicParams* params, const GicGranules* state,
+                      const GicGranules* sorted, const GicNeighbors* nb, const void* const ptr[13], size_t ws_bytes) {
+  memset(&k, 0, sizeof(k));  // padding bytes take part in the comparison
+  memcpy(&k.grid, grid, sizeof(GicGrid));
+  memcpy(&k.params, params, sizeof(GicParams));
+  memcpy(&k.state, state, sizeof(GicGranules));
+  memcpy(&k.sorted, sorted, sizeof(GicGranules));
+  memcpy(&k.nb, nb, sizeof(GicNeighbors));
+  for (int i = 0; i < 13; ++i) k.ptr[i] = ptr[i];
+  k.ws_bytes = ws_bytes;
+}
+
+// Builds the graph of one gic_step configuration:
+//   check (+ copy) -> decide -> IF rebuild: sort -> [zero alpha] -> k_substep -> [alpha out]
+static int build_step_graph(StepGraph& sg, const DGrid& G, const GicGrid* grid, const GicParams* params,
+                            GicGranules* state, GicGranules* sorted, int32_t* perm, void* cell_table, void* ws,
+                            size_t ws_bytes, const GicNeighbors* nb, const void* u, const void* v, const void* w,
+                            const void* p, const void* alpha_f, double* alpha_s, void* Fs_u, void* Fs_v, void* Fs_w,
+                            double* sums2) {
+  int rc = GIC_OK;
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ex = nullptr;
+  cudaStream_t cs = nullptr;
+  cudaGraph_t got = nullptr;
+  cudaGraphConditionalHandle h;
+  NbDev d;
+  int launches = 0;
+  status_word();  // resolve the device address before capturing
+  if (cudaGraphCreate(&g, 0) != cudaSuccess) return set_error(GIC_ERR_CUDA, "gic_step: cudaGraphCreate failed");
+  if (cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    cudaGraphDestroy(g);
+    return set_error(GIC_ERR_CUDA, "gic_step: graph setup failed");
+  }
+  set_capturing(true);
+  do {
+    // 1. displacement check of `state` with its copy into `sorted`, then the decision
+    if (cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+      rc = set_error(GIC_ERR_CUDA, "gic_step: graph capture failed");
+      break;
+    }
+    rc = verlet_check(G, state, cell_table, nb, cs, "gic_step", &d, sorted, perm);
+    if (rc == GIC_OK) k_step_decide<<<1, 1, 0, cs>>>(nb->flags, h);
+    if (cudaStreamEndCapture(cs, &got) != cudaSuccess && rc == GIC_OK)
+      rc = set_error(GIC_ERR_CUDA, "gic_step: graph capture failed");
+    if (rc) break;
+    launches += 2;
+    size_t nn = 0;
+    cudaGraphNode_t nodes[4];
+    if (cudaGraphGetNodes(g, nullptr, &nn) != cudaSuccess || nn > 4 || nn == 0 ||
+        cudaGraphGetNodes(g, nodes, &nn) != cudaSuccess) {
+      rc = set_error(GIC_ERR_CUDA, "gic_step: unexpected graph");
+      break;
+    }
+    cudaGraphNode_t decide = nullptr;
+    for (size_t k = 0; k < nn; ++k) {
+      cudaKernelNodeParams kp;
+      if (cudaGraphKernelNodeGetParams(nodes[k], &kp) == cudaSuccess && kp.func == (void*)k_step_decide)
+        decide = nodes[k];
+    }
+    if (!decide) {
+      rc = set_error(GIC_ERR_CUDA, "gic_step: decision node not found");
+      break;
+    }
+    // 2. the sort, as the body of an IF node
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeIf;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cond;
+    if (cudaGraphAddNode(&cond, g, &decide, nullptr, 1, &cp) != cudaSuccess) {
+      rc = set_error(GIC_ERR_CUDA, "gic_step: conditional node failed");
+      break;
+    }
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    if (cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+      rc = set_error(GIC_ERR_CUDA, "gic_step: graph capture failed");
+      break;
+    }
+    rc = sort_gated(grid, state, sorted, perm, cell_table, ws, ws_bytes, nullptr, cs);
+    if (cudaStreamEndCapture(cs, &got) != cudaSuccess && rc == GIC_OK)
+      rc = set_error(GIC_ERR_CUDA, "gic_step: graph capture failed");
+    if (rc) break;
+    // 3. the fused rest of the substep, sorted -> state
+    if (cudaStreamBeginCaptureToGraph(cs, g, &cond, nullptr, 1, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+      rc = set_error(GIC_ERR_CUDA, "gic_step: graph capture failed");
+      break;
+    }
+    rc = substep_launch(G, params, sorted, cell_table, nb, d, u, v, w, p, alpha_f, state, nullptr, alpha_s, Fs_u, Fs_v,
+                        Fs_w, sums2, cs, &launches);
+    if (cudaStreamEndCapture(cs, &got) != cudaSuccess && rc == GIC_OK)
+      rc = set_error(GIC_ERR_CUDA, "gic_step: graph capture failed");
+    if (rc) break;
+    if (cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) {
+      rc = set_error(GIC_ERR_CUDA, "gic_step: graph instantiation failed");
+      break;
+    }
+  } while (false);
+  set_capturing(false);
+  cudaStreamDestroy(cs);
+  if (rc) {
+    cudaGetLastError();
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  sg.graph = g;
+  sg.exec = ex;
+  sg.launches = launches;
+  return GIC_OK;
+}
+
+}  // namespace gic
 
 extern "C" int gic_step(const GicGrid* grid, const GicParams* params, GicGranules* state, GicGranules* sorted,
                         int32_t* perm, void* cell_table, void* ws, size_t ws_bytes, const GicNeighbors* nb,
@@ -210,6 +390,7 @@ extern "C" int gic_step(const GicGrid* grid, const GicParams* params, GicGranule
   DGrid G;
   int rc = make_grid(grid, &G);
   if (rc) return rc;
+  if (!params) return set_error(GIC_ERR_INVALID, "gic_step: params is NULL");
   if ((rc = check_granules(state, "gic_step state", true))) return rc;
   if ((rc = check_granules(sorted, "gic_step sorted", true))) return rc;
   if (sorted->n != state->n || sorted->precision != state->precision)
@@ -218,41 +399,52 @@ extern "C" int gic_step(const GicGrid* grid, const GicParams* params, GicGranule
       state->id == sorted->id)
     return set_error(GIC_ERR_INVALID, "gic_step: state and sorted must not alias");
   if (state->n > 0 && !perm) return set_error(GIC_ERR_INVALID, "gic_step: perm is NULL");
-  // 1. displacements of the current state against the lists (sets the rebuild
-  //    word), and the state copied into `sorted` in its current order
-  NbDev d;
-  if ((rc = verlet_check(G, state, cell_table, nb, stream, "gic_step", &d, sorted, perm))) return rc;
-  // 2. the sort over that copy, only when the lists are rebuilt
-  if ((rc = sort_gated(grid, state, sorted, perm, cell_table, ws, ws_bytes, nb->flags, stream))) return rc;
-  // 3. the fused rest of the substep, sorted -> state
-  const GicGranules* s = sorted;
   if (!u || !v || !w || !p || !alpha_f) return set_error(GIC_ERR_INVALID, "gic_step: null fluid field");
   bool fs = Fs_u || Fs_v || Fs_w;
   if (fs && !(Fs_u && Fs_v && Fs_w)) return set_error(GIC_ERR_INVALID, "gic_step: give all three F_s arrays or none");
   if (sums2 && !alpha_s) return set_error(GIC_ERR_INVALID, "gic_step: sums2 needs alpha_s");
-  const int64_t ncell = (int64_t)G.nx * G.ny * G.nz;
-  if (alpha_s) alpha_begin(alpha_s, ncell, sums2, stream);
-  if (s->n > 0) {
-    const unsigned blocks = grid_blocks(s->n, kSubstepThreads);
-    if (s->precision == GIC_FP32) {
-      DParams<float> P;
-      if ((rc = make_params(params, &P))) return rc;
-      k_substep<float><<<blocks, kSubstepThreads, 0, stream>>>(
-          G, P, s->n, s->cell, (const uint4*)s->pos, (const float4*)s->posf, (const float4*)s->vel, s->id, d,
-          (const uint4*)cell_table, (float)nb->skin, fields<float>(u, v, w, p, alpha_f), state->cell,
-          (uint4*)state->pos, (float4*)state->vel, state->id, nullptr, alpha_s, (float*)Fs_u, (float*)Fs_v,
-          (float*)Fs_w, sums2, status_word());
-    } else {
-      DParams<double> P;
-      if ((rc = make_params(params, &P))) return rc;
-      k_substep<double><<<blocks, kSubstepThreads, 0, stream>>>(
-          G, P, s->n, s->cell, (const d4*)s->pos, nullptr, (const d4*)s->vel, s->id, d, (const uint4*)cell_table,
-          nb->skin, fields<double>(u, v, w, p, alpha_f), state->cell, (d4*)state->pos, (d4*)state->vel, state->id,
-          nullptr, alpha_s, (double*)Fs_u, (double*)Fs_v, (double*)Fs_w, sums2, status_word());
-    }
-    count_launches(1);
+  if (!nb) return set_error(GIC_ERR_INVALID, "gic_step: neighbours struct is NULL");
+  if (!cell_table) return set_error(GIC_ERR_INVALID, "gic_step: cell_table is NULL");
+  if (state->n == 0) return GIC_OK;
+  {  // arguments of the sort, checked before they are baked into a graph
+    size_t need = 0;
+    if ((rc = gic_workspace_size(grid, state->n, state->precision, &need))) return rc;
+    if (!ws || ws_bytes < need)
+      return set_error(GIC_ERR_WORKSPACE, "gic_step: workspace of %zu bytes needed, %zu given", need, ws_bytes);
+    if ((uintptr_t)ws % 256) return set_error(GIC_ERR_ALIGN, "gic_step: workspace must be 256-byte aligned");
+    if ((uintptr_t)cell_table % 16) return set_error(GIC_ERR_ALIGN, "gic_step: cell_table must be 16-byte aligned");
   }
-  if (alpha_s) alpha_end(G, s->precision, alpha_s, ncell, sums2, stream);
-  GIC_CHECK_LAUNCH("gic_step");
+  const void* ptr[13] = {perm, cell_table, ws, u, v, w, p, alpha_f, alpha_s, Fs_u, Fs_v, Fs_w, sums2};
+  StepKey key;
+  store_key(key, grid, params, state, sorted, nb, ptr, ws_bytes);
+  std::lock_guard<std::mutex> lock(g_step_mu);
+  StepGraph* hit = nullptr;
+  for (auto& sg : g_step_graphs)
+    if (sg.used && same_key(sg.key, key)) hit = &sg;
+  if (!hit) {
+    StepGraph* slot = &g_step_graphs[0];
+    for (auto& sg : g_step_graphs) {
+      if (!sg.used) {
+        slot = &sg;
+        break;
+      }
+      if (sg.last < slot->last) slot = &sg;
+    }
+    if (slot->used) {
+      cudaGraphExecDestroy(slot->exec);
+      cudaGraphDestroy(slot->graph);
+      slot->used = false;
+    }
+    if ((rc = build_step_graph(*slot, G, grid, params, state, sorted, perm, cell_table, ws, ws_bytes, nb, u, v, w, p,
+                               alpha_f, alpha_s, Fs_u, Fs_v, Fs_w, sums2)))
+      return rc;
+    memcpy(&slot->key, &key, sizeof(StepKey));
+    slot->used = true;
+    hit = slot;
+  }
+  hit->last = ++g_step_clock;
+  cudaError_t e = cudaGraphLaunch(hit->exec, (cudaStream_t)stream);
+  if (e != cudaSuccess) return set_error(GIC_ERR_CUDA, "gic_step: cudaGraphLaunch: %s", cudaGetErrorString(e));
+  count_launches(hit->launches);
   return GIC_OK;
 }

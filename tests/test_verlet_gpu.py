@@ -196,3 +196,30 @@ def test_verlet_adjoint_matches_cell_walk(name, prec):
         assert np.abs(gp - ref[0]).max() <= tol * np.abs(ref[0]).max()
         assert np.abs(gv - ref[1]).max() <= tol * np.abs(ref[1]).max()
         assert abs(gm - ref[2]) <= tol * abs(ref[2]) + 1e-30
+
+
+def test_step_graphs_per_configuration():
+    """gic_step caches one graph per configuration: two simulators (and a
+    change of a parameter) interleaved give the same states as each run
+    alone."""
+    pa = shuffled(gi.make("dense_block"))
+    pb = gi.make("random_cloud")
+    alone = []
+    for prob in (pa, pb):
+        sim = Simulator.from_problem(prob, FP32)
+        sim.run(12)
+        alone.append(sim.positions()[0].cpu().numpy())
+    sa = Simulator.from_problem(pa, FP32)
+    sb = Simulator.from_problem(pb, FP32)
+    for k in range(12):
+        sa.substep(alpha=(k == 11), sums=(k == 11))
+        sb.substep(alpha=(k == 11), sums=(k == 11))
+    torch.cuda.synchronize()
+    assert np.array_equal(sa.positions()[0].cpu().numpy(), alone[0])
+    assert np.array_equal(sb.positions()[0].cpu().numpy(), alone[1])
+    # a different drag coefficient is a different configuration
+    sc = Simulator.from_problem(pa, FP32)
+    sc.params.c_drag = 2 * float(pa.params.c_drag)
+    sc.run(12)
+    assert not np.array_equal(sc.positions()[0].cpu().numpy(), alone[0])
+    assert gic.gic_check_status() == 0
