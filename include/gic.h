@@ -350,6 +350,27 @@ int gic_integrate_adj(const GicGrid* grid, const GicParams* params, const GicGra
                       const void* g_vel_out, const void* g_f_ex, void* g_pos_in, void* g_vel_in, void* gF_c,
                       void* gF_fl, void* ga_f, gic_stream_t stream);
 
+/* Adjoint of gic_substep's granule outputs, fused into one pass over the
+ * sorted state: from the gradients of the next state (g_pos_out, g_vel_out,
+ * in the sorted order) and of f_ex (g_f_ex, may be NULL) to those of the
+ * sorted state's positions and velocities, i.e. gic_integrate_adj,
+ * gic_g2p_couple_adj and gic_contact_verlet_adj in one kernel, each
+ * partner's F_c gradient formed again from its own upstream gradients.
+ * With perm (gic_sort's, or the identity gic_step writes when it does not
+ * sort) the results go to g_pos_in[perm[k]], g_vel_in[perm[k]] (the
+ * gic_sort_adj scatter, i.e. the order before the sort); with perm NULL to
+ * index k.  g_pos_in, g_vel_in (real[4n]) are WRITTEN; *g_cdrag and *g_mu
+ * (double, device) are accumulated.  The lists are checked, and rebuilt in
+ * the same kernel when needed, as by gic_substep (a rebuild needs the cell
+ * table of `sorted`).  The grid outputs (alpha_s, F_s) have their own
+ * adjoint, gic_p2g_adj, whose g_f_ex and position gradients the caller
+ * adds in.  One to two launches, no host sync. */
+int gic_substep_adj(const GicGrid* grid, const GicParams* params, const GicGranules* sorted, const int32_t* perm,
+                    const void* cell_table, const GicNeighbors* nb, const void* u, const void* v, const void* w,
+                    const void* p, const void* alpha_f, const void* g_pos_out, const void* g_vel_out,
+                    const void* g_f_ex, void* g_pos_in, void* g_vel_in, double* g_cdrag, double* g_mu,
+                    gic_stream_t stream);
+
 /* Adjoint of gic_p2g for upstream grid gradients g_alpha_s (double, or NULL)
  * and gFs_u/v/w (real, or NULL): accumulates into g_pos_old, g_pos_new and
  * writes g_f_ex (real[4n]). */

@@ -333,25 +333,8 @@ __global__ void __launch_bounds__(128) k_contact_adj(DGrid G, DParams<T> P, int6
       uint32_t epoch = __ldg(&table[0].x);
       for_each_contact<T>(G, table, epoch, i, cx, cy, cz, pi, ri, pos, posf, pair);
     }
-    if (P.walls) {
-      const int c3[3] = {cx, cy, cz};
-      for (int a = 0; a < 3; ++a) {
-        for (int side = 0; side < 2; ++side) {
-          if (side == 0 ? c3[a] != 0 : c3[a] != G.nc[a] - 1) continue;
-          T gap, ov;
-          if (!wall_geom(G, pi, a, side, ri, gap, ov)) continue;
-          T x[3] = {0, 0, 0};
-          x[a] = side == 0 ? gap : -gap;
-          // the wall vector depends on x_i only through its axis-a component
-          T w[3] = {0, 0, 0};
-          gm += pair_force_adj(P, x[0], x[1], x[2], gap, ov, vi.x, vi.y, vi.z, mi, li.x, li.y, li.z, li.x, li.y, li.z,
-                               w[0], w[1], w[2], gv0, gv1, gv2);
-          if (a == 0) gx0 += w[0];
-          else if (a == 1) gx1 += w[1];
-          else gx2 += w[2];
-        }
-      }
-    }
+    if (P.walls)
+      gm += add_walls_adj(G, P, pi, ri, mi, vi, cx, cy, cz, li.x, li.y, li.z, gx0, gx1, gx2, gv0, gv1, gv2);
     vec_t<T> a = gpos[i];
     vec_t<T> b = gvel[i];
     gpos[i] = make_vec<T>(a.x + gx0, a.y + gx1, a.z + gx2);

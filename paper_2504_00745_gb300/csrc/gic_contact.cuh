@@ -451,6 +451,35 @@ __device__ __forceinline__ void add_walls(const DGrid& G, const DParams<T>& P, c
   }
 }
 
+// The walls' part of the contact adjoint of granule i (upstream l = its own
+// force gradient): adds to gx, gv and returns the mu part.  A wall vector
+// depends on x_i only through its axis-a component.
+template <typename T>
+__device__ __forceinline__ T add_walls_adj(const DGrid& G, const DParams<T>& P, const pos_t<T>& pi, T ri, T mi,
+                                           const vec_t<T>& vi, int cx, int cy, int cz, T l0, T l1, T l2, T& gx0,
+                                           T& gx1, T& gx2, T& gv0, T& gv1, T& gv2) {
+  const int c3[3] = {cx, cy, cz};
+  T gm = T(0);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      if (side == 0 ? c3[a] != 0 : c3[a] != G.nc[a] - 1) continue;
+      T gap, ov;
+      if (!wall_geom(G, pi, a, side, ri, gap, ov)) continue;
+      T x[3] = {0, 0, 0};
+      x[a] = side == 0 ? gap : -gap;
+      T w[3] = {0, 0, 0};
+      gm += pair_force_adj(P, x[0], x[1], x[2], gap, ov, vi.x, vi.y, vi.z, mi, l0, l1, l2, l0, l1, l2, w[0], w[1],
+                           w[2], gv0, gv1, gv2);
+      if (a == 0) gx0 += w[0];
+      else if (a == 1) gx1 += w[1];
+      else gx2 += w[2];
+    }
+  }
+  return gm;
+}
+
 // Host side of a Verlet call up to the list walk: argument checks, the
 // displacement check and (launch_build) the build launch, after which F_c
 // holds the build's forces when it ran.  Fills the device view of the lists.
@@ -463,17 +492,15 @@ int verlet_prelude(const DGrid& G, const GicParams* params, const GicGranules* s
 int verlet_check(const DGrid& G, const GicGranules* s, const void* table, const GicNeighbors* nb,
                  cudaStream_t stream, const char* what, NbDev* out, GicGranules* copy_to, int32_t* perm);
 
-// The list build of granule i (cell walk with the pre-test radius r_i + r_j
-// + skin; slot = sorted index) and its contact forces, walls excluded.
-template <typename T>
-__device__ __forceinline__ void verlet_build_granule(const DGrid& G, const DParams<T>& P, const NbDev& nb,
-                                                     const uint4* __restrict__ table, int64_t n, int64_t i,
-                                                     int cx, int cy, int cz, int32_t ci, const pos_t<T>& pi, T ri,
-                                                     T mi, const vec_t<T>& vi, bool has_f, const float4& fi, T skin,
-                                                     const int32_t* __restrict__ id, const pos_t<T>* __restrict__ pos,
-                                                     const float4* __restrict__ posf,
-                                                     const vec_t<T>* __restrict__ vel, T& F0, T& F1, T& F2,
-                                                     bool& coincident) {
+// The list build of granule i: walks the 27 cells with the pre-test radius
+// r_i + r_j + skin, writes row i (slot = sorted index) and its reference
+// entries, and hands every partner in contact to f(j, g).
+template <typename T, typename F>
+__device__ __forceinline__ void verlet_build_row(const DGrid& G, const NbDev& nb, const uint4* __restrict__ table,
+                                                 int64_t n, int64_t i, int cx, int cy, int cz, int32_t ci,
+                                                 const pos_t<T>& pi, T ri, bool has_f, const float4& fi, T skin,
+                                                 const int32_t* __restrict__ id, const pos_t<T>* __restrict__ pos,
+                                                 const float4* __restrict__ posf, F&& f) {
   int32_t* row = nb.list + i * nb.cap;
   const uint32_t epoch = __ldg(&table[0].x);
   int cnt = 0;
@@ -489,7 +516,7 @@ __device__ __forceinline__ void verlet_build_granule(const DGrid& G, const DPara
       else
         over = true;
     }
-    if (touch) add_force(P, g, vi, ldg(&vel[j]), mi, granule_mass(P, radius_of(ldg(&pos[j]))), F0, F1, F2, coincident);
+    if (touch) f(j, g);
   });
   nb.count[i] = cnt;
   nb.at[i] = (int32_t)i;  // after a build, slot = sorted index
@@ -499,6 +526,23 @@ __device__ __forceinline__ void verlet_build_granule(const DGrid& G, const DPara
   const int32_t idi = id[i];
   if (idi >= 0 && (int64_t)idi < n) nb.slot[idi] = (int32_t)i;
   if (over) atomicOr(&nb.flags[kNbOverflow], 1u);
+}
+
+// The list build of granule i and its contact forces, walls excluded.
+template <typename T>
+__device__ __forceinline__ void verlet_build_granule(const DGrid& G, const DParams<T>& P, const NbDev& nb,
+                                                     const uint4* __restrict__ table, int64_t n, int64_t i,
+                                                     int cx, int cy, int cz, int32_t ci, const pos_t<T>& pi, T ri,
+                                                     T mi, const vec_t<T>& vi, bool has_f, const float4& fi, T skin,
+                                                     const int32_t* __restrict__ id, const pos_t<T>* __restrict__ pos,
+                                                     const float4* __restrict__ posf,
+                                                     const vec_t<T>* __restrict__ vel, T& F0, T& F1, T& F2,
+                                                     bool& coincident) {
+  verlet_build_row<T>(G, nb, table, n, i, cx, cy, cz, ci, pi, ri, has_f, fi, skin, id, pos, posf,
+                      [&](int64_t j, const PairGeom<T>& g) {
+                        add_force(P, g, vi, ldg(&vel[j]), mi, granule_mass(P, radius_of(ldg(&pos[j]))), F0, F1, F2,
+                                  coincident);
+                      });
 }
 
 // Called by every thread of the last launch of a Verlet call: the last CTA

@@ -48,38 +48,16 @@ __global__ void __launch_bounds__(256) k_g2p_adj(DGrid G, DParams<T> P, int64_t 
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   double my_gc = 0.0;
   if (i < n) {
-    pos_t<T> pi = pos[i];
-    vec_t<T> vi = vel[i];
+    const pos_t<T> pi = pos[i];
+    const vec_t<T> vi = vel[i];
+    const vec_t<T> lF = gF[i];
+    const vec_t<T> la = ga[i];
+    const T l[3] = {lF.x, lF.y, lF.z};
+    const T lam_a[3] = {la.x, la.y, la.z};
     int m[3];
-    T t[3];
-    granule_mac<T>(G, cell[i], pi, m, t);
-    const T* uvw[3] = {Fd.u, Fd.v, Fd.w};
-    T uf[3], gu[3][3], gp[3], ggp[3][3];
-    T inv_dx = (T)G.inv_dx;
-#pragma unroll
-    for (int comp = 0; comp < 3; ++comp) {
-      Stencil3<T> S = make_stencil<T>(G, m, t, comp);
-      uf[comp] = interp<T>(S, face_loader<T>(G, uvw[comp], comp), inv_dx, gu[comp]);
-      gp[comp] = interp<T>(S, gradp_loader<T>(G, Fd.p, comp), inv_dx, ggp[comp]);
-    }
-    T r = radius_of(pi);
-    T V = T(4.0 / 3.0 * kPi) * r * r * r;
-    T dv[3] = {uf[0] - vi.x, uf[1] - vi.y, uf[2] - vi.z};
-    T sp = sqrt(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
-    T k = P.c_drag * T(kPi) * r * r * P.rho_f;
-    vec_t<T> lF = gF[i];
-    vec_t<T> la = ga[i];
-    T l[3] = {lF.x, lF.y, lF.z};
-    T lam_a[3] = {la.x, la.y, la.z};
-    T dvl = dv[0] * l[0] + dv[1] * l[1] + dv[2] * l[2];
-    // d/d dv of k |dv| dv . l = k (|dv| l + (dv . l) dv / |dv|)
-    T gdv[3];
-    for (int a = 0; a < 3; ++a) gdv[a] = sp > T(0) ? k * (sp * l[a] + dvl * dv[a] / sp) : T(0);
-    T gx[3] = {0, 0, 0};
-    for (int comp = 0; comp < 3; ++comp) {
-      T ggrad = -V * l[comp] - P.inv_rho_f * lam_a[comp];  // upstream of grad p component
-      for (int b = 0; b < 3; ++b) gx[b] += gdv[comp] * gu[comp][b] + ggrad * ggp[comp][b];
-    }
+    T t[3], gx[3] = {0, 0, 0}, gdv[3];
+    const T gc = g2p_adj_granule<T>(G, P, Fd, cell[i], pi, vi, l, lam_a, gx, gdv, m, t);
+    const T inv_dx = (T)G.inv_dx;
     if (galpha) {
       Stencil3<T> S = make_stencil<T>(G, m, t, 3);
       FieldLoad<T> L;
@@ -95,7 +73,7 @@ __global__ void __launch_bounds__(256) k_g2p_adj(DGrid G, DParams<T> P, int64_t 
     vec_t<T> bb = gvel[i];
     gpos[i] = make_vec<T>(a.x + gx[0], a.y + gx[1], a.z + gx[2]);
     gvel[i] = make_vec<T>(bb.x - gdv[0], bb.y - gdv[1], bb.z - gdv[2]);
-    my_gc = (double)(T(kPi) * r * r * P.rho_f * sp * dvl);
+    my_gc = (double)gc;
   }
   if (g_cdrag) {
     double s = block_sum(my_gc, s_red);

@@ -76,6 +76,42 @@ __device__ __forceinline__ T g2p_granule(const DGrid& G, const DParams<T>& P, co
   return sp;
 }
 
+// Adjoint of g2p_granule for upstream gradients l (of F_fl) and la (of
+// a_f): adds their gradient w.r.t. the position to gx, writes in gdv the one
+// w.r.t. the slip u_f - v (so the velocity's is -gdv) and returns the c_drag
+// gradient.  m, t: the granule's MAC cell and offsets, for further stencils.
+template <typename T>
+__device__ __forceinline__ T g2p_adj_granule(const DGrid& G, const DParams<T>& P, const Fields<T>& Fd, int32_t cell,
+                                             const pos_t<T>& pi, const vec_t<T>& vi, const T l[3], const T la[3],
+                                             T gx[3], T gdv[3], int m[3], T t[3]) {
+  granule_mac<T>(G, cell, pi, m, t);
+  const T* uvw[3] = {Fd.u, Fd.v, Fd.w};
+  T uf[3], gu[3][3], ggp[3][3];
+  const T inv_dx = (T)G.inv_dx;
+#pragma unroll
+  for (int comp = 0; comp < 3; ++comp) {
+    Stencil3<T> S = make_stencil<T>(G, m, t, comp);
+    uf[comp] = interp<T>(S, face_loader<T>(G, uvw[comp], comp), inv_dx, gu[comp]);
+    interp<T>(S, gradp_loader<T>(G, Fd.p, comp), inv_dx, ggp[comp]);
+  }
+  const T r = radius_of(pi);
+  const T V = T(4.0 / 3.0 * kPi) * r * r * r;
+  const T dv[3] = {uf[0] - vi.x, uf[1] - vi.y, uf[2] - vi.z};
+  const T sp = sqrt(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
+  const T k = P.c_drag * T(kPi) * r * r * P.rho_f;
+  const T dvl = dv[0] * l[0] + dv[1] * l[1] + dv[2] * l[2];
+  // d/d dv of k |dv| dv . l = k (|dv| l + (dv . l) dv / |dv|)
+#pragma unroll
+  for (int a = 0; a < 3; ++a) gdv[a] = sp > T(0) ? k * (sp * l[a] + dvl * dv[a] / sp) : T(0);
+#pragma unroll
+  for (int comp = 0; comp < 3; ++comp) {
+    const T ggrad = -V * l[comp] - P.inv_rho_f * la[comp];  // upstream of grad p component
+#pragma unroll
+    for (int b = 0; b < 3; ++b) gx[b] += gdv[comp] * gu[comp][b] + ggrad * ggp[comp][b];
+  }
+  return T(kPi) * r * r * P.rho_f * sp * dvl;
+}
+
 // ---- FP32 path: exact fixed-point volume fraction ----
 //
 // alpha_s is accumulated as a 64-bit integer in units of 2^-53: per granule

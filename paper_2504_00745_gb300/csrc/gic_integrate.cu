@@ -50,19 +50,14 @@ __global__ void __launch_bounds__(256) k_integrate_adj(DParams<T> P, int64_t n, 
                                                         vec_t<T>* __restrict__ gFfl, vec_t<T>* __restrict__ gaf) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
-  Masses<T> M = masses(P, radius_of(pos[i]));
-  T inv = T(1) / (M.m + M.ma);
-  vec_t<T> gx = gxo[i], gv = gvo[i];
-  vec_t<T> gf = gfe ? gfe[i] : make_vec<T>(0, 0, 0);
-  // x' = x + dt v', v' = v + dt a
-  T gvt0 = gv.x + P.dt * gx.x, gvt1 = gv.y + P.dt * gx.y, gvt2 = gv.z + P.dt * gx.z;
-  // a enters v' (dt) and f_ex (-m_a)
-  T ga0 = P.dt * gvt0 - M.ma * gf.x, ga1 = P.dt * gvt1 - M.ma * gf.y, ga2 = P.dt * gvt2 - M.ma * gf.z;
+  const vec_t<T> gx = gxo[i];
+  const IntegrateAdj<T> o =
+      integrate_adj_granule(P, radius_of(pos[i]), gx, gvo[i], gfe ? gfe[i] : make_vec<T>(0, 0, 0));
   gxi[i] = gx;
-  gvi[i] = make_vec<T>(gvt0, gvt1, gvt2);
-  gFc[i] = make_vec<T>(ga0 * inv, ga1 * inv, ga2 * inv);
-  gFfl[i] = make_vec<T>(ga0 * inv + gf.x, ga1 * inv + gf.y, ga2 * inv + gf.z);
-  gaf[i] = make_vec<T>(M.ma * (ga0 * inv + gf.x), M.ma * (ga1 * inv + gf.y), M.ma * (ga2 * inv + gf.z));
+  gvi[i] = make_vec<T>(o.gvt[0], o.gvt[1], o.gvt[2]);
+  gFc[i] = make_vec<T>(o.gFc[0], o.gFc[1], o.gFc[2]);
+  gFfl[i] = make_vec<T>(o.gFfl[0], o.gFfl[1], o.gFfl[2]);
+  gaf[i] = make_vec<T>(o.gaf[0], o.gaf[1], o.gaf[2]);
 }
 
 }  // namespace gic

@@ -96,4 +96,31 @@ __device__ __forceinline__ void integrate_granule(const DGrid& G, const DParams<
   fe2 = ff2 + M.ma * (fa2 - a2);
 }
 
+// Adjoint of integrate_granule: from the gradients gx, gv, gf of (x', v',
+// f_ex) of a granule of radius r to those of v (gvt; x's is gx itself), F_c,
+// F_fl and a_f.  x' = x + dt v', v' = v + dt a, a = (F_c + F_fl + m g +
+// m_a a_f) / (m + m_a), f_ex = F_fl + m_a (a_f - a).
+template <typename T>
+struct IntegrateAdj {
+  T gvt[3], gFc[3], gFfl[3], gaf[3];
+};
+
+template <typename T>
+__device__ __forceinline__ IntegrateAdj<T> integrate_adj_granule(const DParams<T>& P, T r, const vec_t<T>& gx,
+                                                                 const vec_t<T>& gv, const vec_t<T>& gf) {
+  const Masses<T> M = masses(P, r);
+  const T inv = T(1) / (M.m + M.ma);
+  IntegrateAdj<T> o;
+  const T x[3] = {gx.x, gx.y, gx.z}, v[3] = {gv.x, gv.y, gv.z}, f[3] = {gf.x, gf.y, gf.z};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    o.gvt[a] = v[a] + P.dt * x[a];
+    const T ga = P.dt * o.gvt[a] - M.ma * f[a];  // a enters v' (dt) and f_ex (-m_a)
+    o.gFc[a] = ga * inv;
+    o.gFfl[a] = ga * inv + f[a];
+    o.gaf[a] = M.ma * (ga * inv + f[a]);
+  }
+  return o;
+}
+
 }  // namespace gic

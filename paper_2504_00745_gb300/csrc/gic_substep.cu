@@ -158,6 +158,85 @@ __global__ void __launch_bounds__(kSubstepThreads, sizeof(T) == 4 ? 4 : 2) k_sub
   verlet_call_done(nb, rebuild);
 }
 
+constexpr int kSubstepAdjThreads = 128;
+
+// Adjoint of k_substep's granule outputs (next position, velocity, f_ex) for
+// one granule of the sorted state: the integration's adjoint gives the
+// granule's own F_c, F_fl and a_f gradients, the G2P adjoint adds its
+// position and velocity parts, and the contact adjoint walks the granule's
+// Verlet row (or the 27 cells, writing the row, on a substep that rebuilds
+// it), forming each partner's F_c gradient from the partner's upstream
+// gradients.  Writes the result through perm (the sort's scatter).
+template <typename T>
+__global__ void __launch_bounds__(kSubstepAdjThreads, sizeof(T) == 4 ? 3 : 1) k_substep_adj(
+    DGrid G, DParams<T> P, int64_t n, const int32_t* __restrict__ cell, const pos_t<T>* __restrict__ pos,
+    const float4* __restrict__ posf, const vec_t<T>* __restrict__ vel, const int32_t* __restrict__ id, NbDev nb,
+    const uint4* __restrict__ table, T skin, Fields<T> Fd, const vec_t<T>* __restrict__ gxo,
+    const vec_t<T>* __restrict__ gvo, const vec_t<T>* __restrict__ gfe, const int32_t* __restrict__ perm,
+    vec_t<T>* __restrict__ gxi, vec_t<T>* __restrict__ gvi, double* __restrict__ g_cdrag,
+    double* __restrict__ g_mu) {
+  __shared__ double s_red[32];
+  const bool rebuild = (nb.flags[kNbRebuild] | nb.flags[kNbSticky]) != 0u;  // uniform over the launch
+  const int64_t i = blockIdx.x * (int64_t)kSubstepAdjThreads + threadIdx.x;
+  double my_gc = 0.0, my_gmu = 0.0;
+  if (i < n) {
+    const int32_t ci = cell[i];
+    const pos_t<T> pi = pos[i];
+    const vec_t<T> vi = vel[i];
+    const T ri = radius_of(pi);
+    const T mi = granule_mass(P, ri);
+    const vec_t<T> zero = make_vec<T>(0, 0, 0);
+    // a4: x' = x + dt v', v' = v + dt a
+    const vec_t<T> gxi_ = gxo[i];
+    const IntegrateAdj<T> o = integrate_adj_granule(P, ri, gxi_, gvo[i], gfe ? gfe[i] : zero);
+    T gx[3] = {gxi_.x, gxi_.y, gxi_.z};
+    T gv[3] = {o.gvt[0], o.gvt[1], o.gvt[2]};
+    // a3: F_fl and a_f at the granule
+    {
+      int m[3];
+      T t[3], gdv[3];
+      my_gc = (double)g2p_adj_granule<T>(G, P, Fd, ci, pi, vi, o.gFfl, o.gaf, gx, gdv, m, t);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) gv[a] -= gdv[a];
+    }
+    // a2: contact pairs (F_ji = -F_ij) and walls
+    const T l0 = o.gFc[0], l1 = o.gFc[1], l2 = o.gFc[2];
+    T gm = T(0);
+    auto pair = [&](int64_t j, const PairGeom<T>& g) {
+      const vec_t<T> vj = ldg(&vel[j]);
+      const T rj = radius_of(ldg(&pos[j]));
+      const IntegrateAdj<T> oj =
+          integrate_adj_granule(P, rj, ldg(&gxo[j]), ldg(&gvo[j]), gfe ? ldg(&gfe[j]) : zero);
+      const T mj = granule_mass(P, rj);
+      gm += pair_force_adj(P, g.x0, g.x1, g.x2, g.d, g.overlap, vi.x - vj.x, vi.y - vj.y, vi.z - vj.z,
+                           mi * mj / (mi + mj), l0 - oj.gFc[0], l1 - oj.gFc[1], l2 - oj.gFc[2], l0, l1, l2, gx[0],
+                           gx[1], gx[2], gv[0], gv[1], gv[2]);
+    };
+    const int cx = cell_x(ci), cy = cell_y(ci), cz = cell_z(ci);
+    const bool has_f = sizeof(T) == 4 && posf != nullptr;
+    const float4 fi = has_f ? __ldg(&posf[i]) : make_float4(0.f, 0.f, 0.f, 0.f);
+    if (rebuild)
+      verlet_build_row<T>(G, nb, table, n, i, cx, cy, cz, ci, pi, ri, has_f, fi, skin, id, pos, posf, pair);
+    else
+      for_each_list_contact<T>(G, nb, i, cx, cy, cz, ci, pi, ri, has_f, fi, cell, pos, posf, pair);
+    if (P.walls)
+      gm += add_walls_adj(G, P, pi, ri, mi, vi, cx, cy, cz, l0, l1, l2, gx[0], gx[1], gx[2], gv[0], gv[1], gv[2]);
+    my_gmu = (double)gm;
+    const int64_t out = perm ? (int64_t)perm[i] : i;
+    gxi[out] = make_vec<T>(gx[0], gx[1], gx[2]);
+    gvi[out] = make_vec<T>(gv[0], gv[1], gv[2]);
+  }
+  if (g_cdrag) {
+    const double sc = block_sum(my_gc, s_red);
+    if (threadIdx.x == 0) atomicAdd(g_cdrag, sc);
+  }
+  if (g_mu) {
+    const double sm = block_sum(my_gmu, s_red);
+    if (threadIdx.x == 0) atomicAdd(g_mu, sm);
+  }
+  verlet_call_done(nb, rebuild);
+}
+
 }  // namespace gic
 
 using namespace gic;
@@ -446,5 +525,50 @@ extern "C" int gic_step(const GicGrid* grid, const GicParams* params, GicGranule
   cudaError_t e = cudaGraphLaunch(hit->exec, (cudaStream_t)stream);
   if (e != cudaSuccess) return set_error(GIC_ERR_CUDA, "gic_step: cudaGraphLaunch: %s", cudaGetErrorString(e));
   count_launches(hit->launches);
+  return GIC_OK;
+}
+
+extern "C" int gic_substep_adj(const GicGrid* grid, const GicParams* params, const GicGranules* sorted,
+                               const int32_t* perm, const void* cell_table, const GicNeighbors* nb, const void* u,
+                               const void* v, const void* w, const void* p, const void* alpha_f,
+                               const void* g_pos_out, const void* g_vel_out, const void* g_f_ex, void* g_pos_in,
+                               void* g_vel_in, double* g_cdrag, double* g_mu, gic_stream_t stream) {
+  DGrid G;
+  int rc = make_grid(grid, &G);
+  if (rc) return rc;
+  const GicGranules* s = sorted;
+  if ((rc = check_granules(s, "gic_substep_adj sorted", true))) return rc;
+  if (!u || !v || !w || !p || !alpha_f) return set_error(GIC_ERR_INVALID, "gic_substep_adj: null fluid field");
+  if (!g_pos_out || !g_vel_out || !g_pos_in || !g_vel_in)
+    return set_error(GIC_ERR_INVALID, "gic_substep_adj: null gradient array");
+  if ((rc = check_vecs(s->precision, "gic_substep_adj", {g_pos_out, g_vel_out, g_f_ex, g_pos_in, g_vel_in})))
+    return rc;
+  // partners read the upstream gradients while others are written
+  const void* ins[3] = {g_pos_out, g_vel_out, g_f_ex};
+  for (const void* q : ins)
+    if (q && (q == g_pos_in || q == g_vel_in))
+      return set_error(GIC_ERR_INVALID, "gic_substep_adj: an output aliases an input gradient");
+  if (g_pos_in == g_vel_in) return set_error(GIC_ERR_INVALID, "gic_substep_adj: g_pos_in aliases g_vel_in");
+  NbDev d;
+  if ((rc = verlet_prelude(G, params, s, cell_table, nb, nullptr, stream, "gic_substep_adj", &d, false))) return rc;
+  if (s->n == 0) return GIC_OK;
+  const unsigned blocks = grid_blocks(s->n, kSubstepAdjThreads);
+  if (s->precision == GIC_FP32) {
+    DParams<float> P;
+    if ((rc = make_params(params, &P))) return rc;
+    k_substep_adj<float><<<blocks, kSubstepAdjThreads, 0, stream>>>(
+        G, P, s->n, s->cell, (const uint4*)s->pos, (const float4*)s->posf, (const float4*)s->vel, s->id, d,
+        (const uint4*)cell_table, (float)nb->skin, fields<float>(u, v, w, p, alpha_f), (const float4*)g_pos_out,
+        (const float4*)g_vel_out, (const float4*)g_f_ex, perm, (float4*)g_pos_in, (float4*)g_vel_in, g_cdrag, g_mu);
+  } else {
+    DParams<double> P;
+    if ((rc = make_params(params, &P))) return rc;
+    k_substep_adj<double><<<blocks, kSubstepAdjThreads, 0, stream>>>(
+        G, P, s->n, s->cell, (const d4*)s->pos, nullptr, (const d4*)s->vel, s->id, d, (const uint4*)cell_table,
+        nb->skin, fields<double>(u, v, w, p, alpha_f), (const d4*)g_pos_out, (const d4*)g_vel_out,
+        (const d4*)g_f_ex, perm, (d4*)g_pos_in, (d4*)g_vel_in, g_cdrag, g_mu);
+  }
+  count_launches(1);
+  GIC_CHECK_LAUNCH("gic_substep_adj");
   return GIC_OK;
 }

@@ -75,6 +75,7 @@ _SIGS = {
     "gic_neighbors_reset": [_P, _P],
     "gic_substep": [_P] * 18,
     "gic_contact_verlet_adj": [_P] * 11,
+    "gic_substep_adj": [_P] * 19,
     "gic_step": [_P, _P, _P, _P, _P, _P, _P, C.c_size_t, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P],
 }
 # entry points that exist in include/gic.h but are declared optional here
@@ -305,6 +306,15 @@ def gic_contact_verlet_adj(grid, params, st: State, cell_table, nb: Neighbors, F
     _check(lib().gic_contact_verlet_adj(C.byref(grid), C.byref(params), C.byref(s), _ptr(cell_table), C.byref(b),
                                         _ptr(F_c), _ptr(gF_c), _ptr(g_pos), _ptr(g_vel), _ptr(g_mu),
                                         _stream(stream)), "gic_contact_verlet_adj")
+
+
+def gic_substep_adj(grid: GicGrid, params: GicParams, sorted_: State, perm, cell_table, nb: Neighbors, u, v, w, p,
+                    alpha_f, g_pos_out, g_vel_out, g_f_ex, g_pos_in, g_vel_in, g_cdrag=None, g_mu=None, stream=None):
+    s, b = sorted_.struct(), nb.struct()
+    _check(lib().gic_substep_adj(C.byref(grid), C.byref(params), C.byref(s), _ptr(perm), _ptr(cell_table),
+                                 C.byref(b), _ptr(u), _ptr(v), _ptr(w), _ptr(p), _ptr(alpha_f), _ptr(g_pos_out),
+                                 _ptr(g_vel_out), _ptr(g_f_ex), _ptr(g_pos_in), _ptr(g_vel_in), _ptr(g_cdrag),
+                                 _ptr(g_mu), _stream(stream)), "gic_substep_adj")
 
 
 def gic_step(grid: GicGrid, params: GicParams, state: State, sorted_: State, perm, cell_table, ws, nb: Neighbors,

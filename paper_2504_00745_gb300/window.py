@@ -91,15 +91,18 @@ class Simulator:
             gic.gic_neighbors_reset(self.nb, stream)
 
     @classmethod
-    def from_problem(cls, prob, precision=GIC_FP32, device="cuda", verlet: bool = True, fused: bool = True):
+    def from_problem(cls, prob, precision=GIC_FP32, device="cuda", verlet: bool = True, fused: bool = True,
+                     skin: Optional[float] = None):
         """Simulator of a gic_inputs.Problem; verlet: Verlet lists with a skin
-        of 0.15 r_max (48 partners per granule, 96 when radii vary by more
-        than 1.5x)."""
-        skin = cap = None
+        of 0.15 r_max unless given (48 partners per granule, 96 when radii
+        vary by more than 1.5x)."""
+        cap = None
         if verlet and prob.n > 0:
             r = prob.r
-            skin = 0.15 * float(r.max())
+            skin = 0.15 * float(r.max()) if skin is None else float(skin)
             cap = 48 if float(r.max()) <= 1.5 * float(r.min()) else 96
+        else:
+            skin = None
         sim = cls(prob.grid, prob.params, prob.n, precision, device, verlet_skin=skin, verlet_cap=cap or 48,
                   fused=fused)
         sim.set_fluid(prob.u, prob.vf, prob.wf, prob.p, prob.alpha_f)
@@ -221,12 +224,24 @@ class GicWindow(torch.autograd.Function):
     final absolute positions (FP64 [n, 3], original order).
 
     Backward: the window is cut into segments of `ckpt` substeps; the state at
-    the start of each segment is kept from the forward pass, every segment is
-    recomputed from it in reverse order (forward and recomputation sort every
-    substep, so each substep's sorted order is the one its adjoint re-sorts
-    to), and each substep's adjoint runs
-    gic_integrate_adj, gic_g2p_couple_adj, gic_contact_adj (through the
-    Verlet lists when the simulator has them) and gic_sort_adj.
+    the start of each segment is kept from the forward pass and every segment
+    is recomputed from it, in reverse order.
+
+    With Verlet lists and the fused path, forward and recomputation run
+    gic_step (the sort only on list rebuilds).  The window opens with a list
+    build, and every checkpoint also keeps the lists as they stand (a new
+    copy only after a build), so the recomputation from it repeats the
+    forward pass exactly.  The recomputation keeps, per substep, the state
+    the substep acted on (sorted or in the previous order) and its
+    permutation, and notes which substeps rebuilt the lists; going back, the
+    lists each substep used are restored (from the checkpoint, or by sort +
+    build from the state of the substep that built them) and each substep's
+    adjoint is one gic_substep_adj.
+
+    Otherwise forward and recomputation sort every substep, and each
+    substep's adjoint re-sorts its state and runs gic_integrate_adj,
+    gic_g2p_couple_adj, gic_contact_adj (through the Verlet lists when the
+    simulator has them) and gic_sort_adj.
     """
 
     @staticmethod
@@ -237,65 +252,155 @@ class GicWindow(torch.autograd.Function):
         vel = sim.A.vel
         vel[:, :3] = v0.detach().to(vel.dtype)  # init is in original order (id = 0..n-1)
         vel[:, 3] = 0
-        ckpts = []
+        stepped = sim.nb is not None and sim.fused
+        if stepped:  # the lists left by earlier calls do not enter the result
+            gic.gic_neighbors_reset(sim.nb)
+        ckpts, lists = [], []
         for s in range(K):
             if s % ckpt == 0:
                 ckpts.append(sim.A.clone())
-            sim.substep(alpha=False, transfer=False, sums=False, sort_every=True)
+                if stepped:
+                    lists.append(_lists_snapshot(sim.nb, lists[-1] if lists else None))
+            sim.substep(alpha=False, transfer=False, sums=False, sort_every=not stepped)
         x, _ = sim.positions()
-        ctx.sim, ctx.K, ctx.ckpt = sim, K, ckpt
-        ctx.ckpts = ckpts
+        ctx.sim, ctx.K, ctx.ckpt, ctx.stepped = sim, K, ckpt, stepped
+        ctx.ckpts, ctx.lists = ckpts, lists
         ctx.final = sim.A.clone()
         return x
 
     @staticmethod
     def backward(ctx, g_x):
-        sim, K, ckpt = ctx.sim, ctx.K, ctx.ckpt
-        n, prec = sim.n, sim.precision
-        dev = sim.device
+        sim = ctx.sim
+        n, prec, dev = sim.n, sim.precision, sim.device
         g_pos = gic.vec4(n, prec, dev)
         g_vel = gic.vec4(n, prec, dev)
         gic.gic_unpack_adj(sim.grid, ctx.final, g_x.contiguous().to(torch.float64), None, g_pos, None)
-        g_pos_b = gic.vec4(n, prec, dev)
-        g_vel_b = gic.vec4(n, prec, dev)
-        gFc = gic.vec4(n, prec, dev)
-        gFfl = gic.vec4(n, prec, dev)
-        gaf = gic.vec4(n, prec, dev)
         g_scalars = torch.zeros(2, dtype=torch.float64, device=dev)  # [c_drag, mu]
-        F = sim.fluid
-        n_seg = len(ctx.ckpts)
-        for m in reversed(range(n_seg)):
-            s0 = m * ckpt
-            s1 = min(K, s0 + ckpt)
-            # recompute the segment, keeping the state before every substep
-            _copy_state(sim.A, ctx.ckpts[m])
-            pre = []
-            for s in range(s0, s1):
-                pre.append(sim.A.clone())
-                if s < s1 - 1:
-                    sim.substep(alpha=False, transfer=False, sums=False, sort_every=True)
-            for s in reversed(range(s0, s1)):
-                S = pre[s - s0]
-                gic.gic_sort(sim.grid, S, sim.B, sim.perm, sim.table, sim.ws)
-                gic.gic_integrate_adj(sim.grid, sim.params, sim.B, g_pos, g_vel, None, g_pos_b, g_vel_b, gFc, gFfl,
-                                      gaf)
-                gic.gic_g2p_couple_adj(sim.grid, sim.params, sim.B, F.u, F.v, F.w, F.p, F.alpha_f, gFfl, gaf, None,
-                                       g_pos_b, g_vel_b, g_scalars[0:1])
-                if sim.nb is not None:
-                    gic.gic_contact_verlet_adj(sim.grid, sim.params, sim.B, sim.table, sim.nb, sim.F_c, gFc, g_pos_b,
-                                               g_vel_b, g_scalars[1:2])
-                else:
-                    gic.gic_contact_adj(sim.grid, sim.params, sim.B, sim.table, gFc, g_pos_b, g_vel_b,
-                                        g_scalars[1:2])
-                gic.gic_sort_adj(n, prec, sim.perm, g_pos_b, g_vel_b, g_pos, g_vel)
+        if ctx.stepped:
+            g_vel = _backward_stepped(ctx, g_pos, g_vel, g_scalars)
+        else:
+            g_vel = _backward_sorted(ctx, g_pos, g_vel, g_scalars)
         g_v0 = g_vel[:, :3].to(torch.float64)
         return g_v0, g_scalars[0].clone(), g_scalars[1].clone(), None, None, None, None
 
 
-def window_loss_and_grads(prob, precision=GIC_FP32, K=None, ckpt=10, device="cuda"):
+def _segments(K: int, ckpt: int):
+    """(s0, s1) of every checkpoint segment, last first."""
+    return [(m * ckpt, min(K, (m + 1) * ckpt)) for m in reversed(range((K + ckpt - 1) // ckpt))]
+
+
+_NB_ARRAYS = ("list", "count", "ref_cell", "ref_pos", "slot")
+
+
+def _lists_snapshot(nb: gic.Neighbors, last: Optional[dict]) -> dict:
+    """The Verlet lists as they stand: the words and, unless a build is
+    pending, the rows and reference entries (`cur` and `at` follow from them
+    at the next check).  Returns `last` again when no build has run since it
+    was taken."""
+    flags = nb.flags.clone()
+    f = flags.tolist()
+    pending = bool(f[1])
+    if last is not None and not pending and not last["pending"] and last["builds"] == f[4]:
+        return last
+    snap = {"flags": flags, "builds": f[4], "pending": pending}
+    if not pending:
+        for a in _NB_ARRAYS:
+            snap[a] = getattr(nb, a).clone()
+    return snap
+
+
+def _lists_restore(nb: gic.Neighbors, snap: dict):
+    nb.flags.copy_(snap["flags"])
+    if not snap["pending"]:
+        for a in _NB_ARRAYS:
+            getattr(nb, a).copy_(snap[a])
+
+
+def _backward_stepped(ctx, g_pos, g_vel, g_scalars):
+    sim, nb, F = ctx.sim, ctx.sim.nb, ctx.sim.fluid
+    n, prec, dev = sim.n, sim.precision, sim.device
+    g_pos_n = gic.vec4(n, prec, dev)
+    g_vel_n = gic.vec4(n, prec, dev)
+    log = torch.zeros(ctx.ckpt + 1, dtype=torch.int32, device=dev)
+    ends, expected = [], []
+    for m, (s0, s1) in zip(reversed(range(len(ctx.ckpts))), _segments(ctx.K, ctx.ckpt)):
+        L = s1 - s0
+        # recompute the segment, keeping every substep's (sorted) state and permutation
+        _copy_state(sim.A, ctx.ckpts[m])
+        _lists_restore(nb, ctx.lists[m])
+        log[0:1].copy_(nb.flags[4:5])
+        states, perms = [], []
+        for k in range(L):
+            sim.substep(alpha=False, transfer=False, sums=False)
+            states.append(sim.B.clone())
+            perms.append(sim.perm.clone())
+            log[k + 1:k + 2].copy_(nb.flags[4:5])  # list builds so far
+        counts = log[:L + 1].tolist()
+        built = [counts[k + 1] != counts[k] for k in range(L)]
+        # the substep whose build made the lists substep k walked (-1: the checkpoint's)
+        last_build = [max([j for j in range(k + 1) if built[j]], default=-1) for k in range(L)]
+        lists_of, count_now = last_build[L - 1], counts[L]
+        for k in reversed(range(L)):
+            b = last_build[k]
+            if b != lists_of:
+                if b < 0:
+                    _lists_restore(nb, ctx.lists[m])
+                    count_now = ctx.lists[m]["builds"]
+                else:  # the lists built from states[b]: sort it for its cell table, build
+                    gic.gic_sort(sim.grid, states[b], sim.B, sim.perm, sim.table, sim.ws)
+                    gic.gic_neighbors_reset(nb)
+                    gic.gic_contact_verlet(sim.grid, sim.params, sim.B, sim.table, nb, sim.F_c)
+                    count_now = 1  # a reset clears the build count
+                lists_of = b
+            gic.gic_substep_adj(sim.grid, sim.params, states[k], perms[k], sim.table, nb, F.u, F.v, F.w, F.p,
+                                F.alpha_f, g_pos, g_vel, None, g_pos_n, g_vel_n, g_scalars[0:1], g_scalars[1:2])
+            g_pos, g_pos_n = g_pos_n, g_pos
+            g_vel, g_vel_n = g_vel_n, g_vel
+        ends.append(nb.flags[4:5].clone())
+        expected.append(count_now)
+    # every adjoint walked the lists its forward substep used: no build of its own
+    got = torch.cat(ends).tolist()
+    if got != expected:
+        raise RuntimeError(f"Verlet lists were rebuilt inside the adjoint (builds {got}, expected {expected})")
+    return g_vel
+
+
+def _backward_sorted(ctx, g_pos, g_vel, g_scalars):
+    sim, K, ckpt, F = ctx.sim, ctx.K, ctx.ckpt, ctx.sim.fluid
+    n, prec, dev = sim.n, sim.precision, sim.device
+    g_pos_b = gic.vec4(n, prec, dev)
+    g_vel_b = gic.vec4(n, prec, dev)
+    gFc = gic.vec4(n, prec, dev)
+    gFfl = gic.vec4(n, prec, dev)
+    gaf = gic.vec4(n, prec, dev)
+    for m, (s0, s1) in zip(reversed(range(len(ctx.ckpts))), _segments(K, ckpt)):
+        # recompute the segment, keeping the state before every substep
+        _copy_state(sim.A, ctx.ckpts[m])
+        pre = []
+        for s in range(s0, s1):
+            pre.append(sim.A.clone())
+            if s < s1 - 1:
+                sim.substep(alpha=False, transfer=False, sums=False, sort_every=True)
+        for s in reversed(range(s0, s1)):
+            S = pre[s - s0]
+            gic.gic_sort(sim.grid, S, sim.B, sim.perm, sim.table, sim.ws)
+            gic.gic_integrate_adj(sim.grid, sim.params, sim.B, g_pos, g_vel, None, g_pos_b, g_vel_b, gFc, gFfl, gaf)
+            gic.gic_g2p_couple_adj(sim.grid, sim.params, sim.B, F.u, F.v, F.w, F.p, F.alpha_f, gFfl, gaf, None,
+                                   g_pos_b, g_vel_b, g_scalars[0:1])
+            if sim.nb is not None:
+                gic.gic_contact_verlet_adj(sim.grid, sim.params, sim.B, sim.table, sim.nb, sim.F_c, gFc, g_pos_b,
+                                           g_vel_b, g_scalars[1:2])
+            else:
+                gic.gic_contact_adj(sim.grid, sim.params, sim.B, sim.table, gFc, g_pos_b, g_vel_b, g_scalars[1:2])
+            gic.gic_sort_adj(n, prec, sim.perm, g_pos_b, g_vel_b, g_pos, g_vel)
+    return g_vel
+
+
+def window_loss_and_grads(prob, precision=GIC_FP32, K=None, ckpt=10, device="cuda", **sim_kw):
     """Loss = mean |x_K - target|^2 of a problem with a target cloud, and its
-    gradients w.r.t. the initial velocities, c_drag and mu (FP64 tensors)."""
-    sim = Simulator.from_problem(prob, precision, device)
+    gradients w.r.t. the initial velocities, c_drag and mu (FP64 tensors).
+    sim_kw go to Simulator.from_problem."""
+    sim = Simulator.from_problem(prob, precision, device, **sim_kw)
     init = sim.A.clone()
     K = prob.K if K is None else K
     v0 = torch.tensor(prob.v, dtype=torch.float64, device=device, requires_grad=True)

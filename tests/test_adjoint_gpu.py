@@ -127,6 +127,62 @@ def test_p2g_adjoint_kernel(prec):
     assert _rel(gfe.cpu().numpy()[:, :3], wf) < tol
 
 
+@pytest.mark.parametrize("name", ["dense_block", "random_cloud"])
+@pytest.mark.parametrize("prec", PRECS)
+def test_substep_adjoint_matches_oracle(name, prec):
+    """gic_substep_adj (the integrate, G2P and contact adjoints in one pass,
+    scattered through the sort's permutation) against the oracle's
+    integrate_adj, g2p_adj and contact_adj composed by hand, on a call that
+    builds the Verlet lists and on one that walks them."""
+    prob = shuffled(gi.make(name))
+    sim = sim_for(prob, prec)
+    gic.gic_sort(sim.grid, sim.A, sim.B, sim.perm, sim.table, sim.ws)
+    rng = np.random.default_rng(6)
+    gX, gV, gFe = (rng.normal(size=(prob.n, 3)) for _ in range(3))
+    ids = sim.B.id.cpu().numpy()  # sorted index -> id
+    x, v, r = oracle_inputs(prob)
+    gxi, gvi, gFc, gFfl, gaf = oracle.integrate_adj(prob.grid, prob.params, r, gX, gV, gFe)
+    gxo, gvo, gc_o = oracle.g2p_adj(prob.grid, prob.params, x, v, r, prob.u, prob.vf, prob.wf, prob.p, prob.alpha_f,
+                                    gFfl, gaf, np.zeros(prob.n))
+    gxc, gvc, gmu_o = oracle.contact_adj(prob.grid, prob.params, x, v, r, gFc)
+    want_x, want_v = gxi + gxo + gxc, gvi + gvo + gvc
+    F = sim.fluid
+    tol = 2e-4 if prec == FP32 else 1e-9
+    for _ in range(2):
+        gp, gv = gic.vec4(prob.n, prec), gic.vec4(prob.n, prec)
+        gs = torch.zeros(2, dtype=torch.float64, device="cuda")
+        gic.gic_substep_adj(sim.grid, sim.params, sim.B, sim.perm, sim.table, sim.nb, F.u, F.v, F.w, F.p, F.alpha_f,
+                            _t4(gX[ids], prec), _t4(gV[ids], prec), _t4(gFe[ids], prec), gp, gv, gs[0:1], gs[1:2])
+        torch.cuda.synchronize()
+        assert gic.gic_check_status() == 0
+        assert _rel(by_id(gp, sim.A.id)[:, :3], want_x) < tol
+        assert _rel(by_id(gv, sim.A.id)[:, :3], want_v) < tol
+        assert abs(float(gs[0]) - gc_o) <= tol * abs(gc_o)
+        assert abs(float(gs[1]) - gmu_o) <= tol * abs(gmu_o)
+    assert sim.nb.builds() == 1
+
+
+def test_substep_adjoint_argument_errors():
+    prob = gi.make("dense_block")
+    sim = sim_for(prob, FP32)
+    gic.gic_sort(sim.grid, sim.A, sim.B, sim.perm, sim.table, sim.ws)
+    F = sim.fluid
+    g = [gic.vec4(prob.n, FP32) for _ in range(4)]
+
+    def call(u, gpo, gvo, gpi, gvi):
+        gic.gic_substep_adj(sim.grid, sim.params, sim.B, sim.perm, sim.table, sim.nb, u, F.v, F.w, F.p, F.alpha_f,
+                            gpo, gvo, None, gpi, gvi)
+
+    with pytest.raises(gic.GicError, match="aliases an input"):
+        call(F.u, g[0], g[1], g[0], g[3])
+    with pytest.raises(gic.GicError, match="g_pos_in aliases g_vel_in"):
+        call(F.u, g[0], g[1], g[2], g[2])
+    with pytest.raises(gic.GicError, match="null gradient"):
+        call(F.u, g[0], None, g[2], g[3])
+    with pytest.raises(gic.GicError, match="null fluid"):
+        call(None, g[0], g[1], g[2], g[3])
+
+
 def _window_case(kind):
     if kind == "contacts":
         prob = gi.make("dense_block", n_side=(4, 4, 4))
@@ -156,6 +212,35 @@ def test_window_gradients_match_oracle_adjoint(kind, ckpt, prec):
         assert abs(float(gmu) - adj["g_mu"]) <= tol * abs(adj["g_mu"])
     else:
         assert abs(float(gmu) - adj["g_mu"]) <= tol * max(abs(adj["g_mu"]), 1e-3 * abs(adj["g_c"]))
+
+
+@pytest.mark.parametrize("path", ["rebuild_every_substep", "rebuild_inside_segments", "sorted_every_substep"])
+@pytest.mark.parametrize("prec", PRECS)
+def test_window_gradient_paths(path, prec):
+    """The window's backward passes against the oracle's adjoint: with a skin
+    so thin that every substep rebuilds the Verlet lists (going back restores
+    another build's lists before every substep), with one that rebuilds in
+    the middle of checkpoint segments (the substeps before it walk the lists
+    kept with the checkpoint; the granules fall about 5e-5 m in the first
+    five substeps), and without the fused path (every substep sorted,
+    separate adjoint kernels)."""
+    prob = _window_case("contacts")
+    kw = {"rebuild_every_substep": dict(skin=1e-12), "rebuild_inside_segments": dict(skin=8e-5),
+          "sorted_every_substep": dict(fused=False)}[path]
+    if path != "sorted_every_substep":
+        sim = Simulator.from_problem(prob, prec, **kw)
+        sim.run(prob.K)
+        # builds at every substep; or at substeps 0 and 5 (and maybe 8 or 9)
+        assert sim.nb.builds() == prob.K if path == "rebuild_every_substep" else sim.nb.builds() in (2, 3)
+    loss, gv0, gc, gmu, _ = window_loss_and_grads(prob, prec, ckpt=4, **kw)
+    torch.cuda.synchronize()
+    assert gic.gic_check_status() == 0
+    out = oracle.run(prob)
+    adj = oracle.run_adjoint(prob, 2 * (out["x"] - prob.target) / prob.n)
+    tol = 1e-3 if prec == FP32 else 1e-8
+    assert _rel(gv0.cpu().numpy(), adj["g_v0"]) < tol
+    assert abs(float(gc) - adj["g_c"]) <= tol * abs(adj["g_c"])
+    assert abs(float(gmu) - adj["g_mu"]) <= tol * abs(adj["g_mu"])
 
 
 def test_window_gradients_match_gpu_fd():
