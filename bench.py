@@ -35,10 +35,11 @@ UNIT = "granule-substeps/s"
 ALGO_BYTES = {"gic_sort": 88, "gic_contact": 48, "gic_g2p_couple": 65, "gic_integrate": 120, "gic_p2g": 32,
               "gic_substep": 72, "gic_step": 72}
 P2G_ALPHA_BYTES = 20
-# DRAM bytes (read + write) of one launch of the dominant entry point's main
-# kernel (k_substep for gic_substep), from an ncu capture of the current
-# kernel on the same workload (a list-walk substep; ncu flushes the caches)
-NCU_TRAFFIC = {("dam_break_1m", "gic_substep"): 174.19e6}
+# DRAM bytes (read + write) of one call of the dominant entry point on a
+# substep that keeps its lists (gic_step: k_verlet_check + k_substep), from
+# an ncu capture of the current kernels on the same workload (ncu flushes
+# the caches before each launch)
+NCU_TRAFFIC = {}
 
 
 def algo_bytes(name, K):
@@ -60,6 +61,11 @@ def parse():
     ap.add_argument("--profile-substeps", type=int, default=0,
                     help="run this many substeps of the workload once, untimed, and exit (for ncu captures)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"], help="precision of --profile-substeps")
+    ap.add_argument("--profile-window", action="store_true",
+                    help="with --profile-substeps: the differentiable window (forward + backward) instead")
+    ap.add_argument("--profile-direct", action="store_true",
+                    help="with --profile-substeps: gic_sort + gic_substep every substep (no CUDA graph), so that "
+                         "a profiler sees each kernel")
     return ap.parse_args()
 
 
@@ -254,10 +260,7 @@ def run_gpu(args, ws, rank, local):
     ev_acc = {k: [] for k in names}
 
     def one_step(probe=False):
-        sim.A.cell.copy_(init.cell)
-        sim.A.pos.copy_(init.pos)
-        sim.A.vel.copy_(init.vel)
-        sim.A.id.copy_(init.id)
+        sim.load_state(init)  # the window's first substep builds the lists
         flush.zero_()
         start = torch.cuda.Event(enable_timing=True)
         end = torch.cuda.Event(enable_timing=True)
@@ -448,10 +451,7 @@ def run_fwd(prob, prec, gic, torch, dev, stream, steps=2, warmup=1):
     ev_acc = {k: [] for k in ALGO_BYTES}
     gic.gic_check_status(clear=True)
     for it in range(warmup + steps):
-        sim.A.cell.copy_(init.cell)
-        sim.A.pos.copy_(init.pos)
-        sim.A.vel.copy_(init.vel)
-        sim.A.id.copy_(init.id)
+        sim.load_state(init)  # the window's first substep builds the lists
         flush.zero_()
         s = torch.cuda.Event(enable_timing=True)
         e = torch.cuda.Event(enable_timing=True)
@@ -487,17 +487,29 @@ def run_fwd(prob, prec, gic, torch, dev, stream, steps=2, warmup=1):
 
 
 def run_profile(args):
-    """N substeps of the workload, nothing else (the command ncu wraps)."""
+    """N substeps of the workload, nothing else (the command ncu wraps); with
+    --profile-window the loss gradient of an N-substep window instead."""
+    import numpy as np
     import torch
 
     import gic_inputs as gi
     from paper_2504_00745_gb300 import gic
-    from paper_2504_00745_gb300.window import Simulator
+    from paper_2504_00745_gb300.window import GicWindow, Simulator
 
     prob = gi.make(args.workload)
     prec = gic.GIC_FP32 if args.precision == "fp32" else gic.GIC_FP64
     sim = Simulator.from_problem(prob, prec)
-    sim.run(args.profile_substeps)
+    if args.profile_window:
+        rng = np.random.default_rng(7)
+        target = torch.as_tensor(prob.positions() + rng.normal(0.0, 0.5 * float(prob.r.mean()), size=(prob.n, 3)),
+                                 device=sim.device)
+        v0 = torch.tensor(prob.v, dtype=torch.float64, device=sim.device, requires_grad=True)
+        c = torch.tensor(float(prob.params.c_drag), dtype=torch.float64, device=sim.device, requires_grad=True)
+        mu = torch.tensor(float(prob.params.mu_fric), dtype=torch.float64, device=sim.device, requires_grad=True)
+        x = GicWindow.apply(v0, c, mu, sim, sim.A.clone(), args.profile_substeps, 10)
+        ((x - target) ** 2).sum(dim=1).mean().backward()
+    else:
+        sim.run(args.profile_substeps, sort_every=args.profile_direct)
     torch.cuda.synchronize()
     st = gic.gic_check_status()
     print(json.dumps({"profile_substeps": args.profile_substeps, "workload": prob.name, "precision": args.precision,

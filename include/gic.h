@@ -223,7 +223,8 @@ typedef struct GicNeighbors {
   int32_t* cur;      /* [n] current sorted index of each slot (written by every call) */
   int32_t* at;       /* [n] slot of each current sorted index (written by every call) */
   uint32_t* flags;   /* [8]: [0] rebuild in this call, [1] bit 0 rebuild requested, bit 1 a list overflowed at the
-                      * last build, [2] CTA counter, [3] overflow during a build, [4] builds performed */
+                      * last build, [2] CTA counter, [3] overflow during a build, [4] builds performed, [5] a
+                      * granule written by the last substep kernel is beyond skin / 2 (read by gic_step) */
 } GicNeighbors;
 
 int gic_contact_verlet(const GicGrid* grid, const GicParams* params, const GicGranules* sorted,
@@ -257,27 +258,34 @@ int gic_substep(const GicGrid* grid, const GicParams* params, const GicGranules*
                 void* Fs_w, double* sums2, gic_stream_t stream);
 
 /* One whole substep (Alg. 2 body with the sort in front) on a state kept
- * with Verlet lists: the displacement check of `state` against the lists
- * (which also copies `state` into `sorted` in its current order and writes
- * the identity into perm), then the sort of `state` into `sorted` ONLY when
- * the lists are rebuilt in this call (otherwise the cell table keeps the
- * last sort's entries), then gic_substep from `sorted` back into `state`.
- * Between list builds the neighbour search needs no sort, and the granules
- * stay in the last sort's (Morton) order.
- *   The call runs as a CUDA graph whose sort is the body of a conditional
- *   node set on the device by the check, so a substep without a rebuild
- *   launches no sort kernel and nothing waits on the host.  The first call
- *   with a given configuration (every argument's value, the params and the
- *   structs' contents) builds and instantiates the graph; up to four
- *   configurations stay cached (least recently used replaced).  The graph
- *   bakes in the pointers: buffers must stay allocated while calls with
- *   them may come.  Arguments as for gic_sort and gic_substep (state and
- *   sorted must carry ids); errors as for those calls, plus GIC_ERR_CUDA if
- *   a graph cannot be built. */
-int gic_step(const GicGrid* grid, const GicParams* params, GicGranules* state, GicGranules* sorted, int32_t* perm,
-             void* cell_table, void* ws, size_t ws_bytes, const GicNeighbors* nb, const void* u, const void* v,
-             const void* w, const void* p, const void* alpha_f, double* alpha_s, void* Fs_u, void* Fs_v, void* Fs_w,
-             double* sums2, gic_stream_t stream);
+ * with Verlet lists, from `state` into `next` (state is not written).
+ * When the lists are rebuilt in this call, `state` is first sorted into
+ * `sorted` (perm, cell table as gic_sort) and the substep runs from there,
+ * building the lists; otherwise the substep runs from `state` itself and
+ * `next` keeps its order (the last sort's Morton order).  The rebuild is
+ * decided on the device: the previous gic_step on these lists tests every
+ * granule it writes against skin / 2 of its reference position, and
+ * gic_neighbors_reset forces one.  So, between calls on the same lists,
+ * `state` must be the previous call's `next`, unchanged; after anything else
+ * (a new state, another entry point on these lists) call gic_neighbors_reset.
+ * The caller swaps state and next between calls.
+ *   FP32: `next` receives float positions (posf, if set) for the next
+ *   call's contact pre-tests, read from `state` (if set) when no sort runs.
+ *   The call runs as a CUDA graph: a one-thread decision kernel sets the
+ *   conditionals of two branches (sort + substep, or substep alone), so a
+ *   substep without a rebuild launches only the decision and the substep
+ *   kernel and nothing waits on the host.  The first call with a given
+ *   configuration (every argument's value, the params and the structs'
+ *   contents) builds and instantiates the graph; up to eight configurations
+ *   stay cached (least recently used replaced).  The graph bakes in the
+ *   pointers: buffers must stay allocated while calls with them may come.
+ *   Arguments as for gic_sort and gic_substep (state, next and sorted must
+ *   carry ids and share no array); errors as for those calls, plus
+ *   GIC_ERR_CUDA if a graph cannot be built. */
+int gic_step(const GicGrid* grid, const GicParams* params, const GicGranules* state, GicGranules* next,
+             GicGranules* sorted, int32_t* perm, void* cell_table, void* ws, size_t ws_bytes, const GicNeighbors* nb,
+             const void* u, const void* v, const void* w, const void* p, const void* alpha_f, double* alpha_s,
+             void* Fs_u, void* Fs_v, void* Fs_w, double* sums2, gic_stream_t stream);
 
 /* Request a rebuild at the next gic_contact_verlet and clear the counters
  * (flags = {0, 1, 0, 0, 0, ...}). */
@@ -380,8 +388,9 @@ int gic_p2g_adj(const GicGrid* grid, const GicParams* params, const GicGranules*
 
 /* ------------------------------------------------------------ windows */
 
-/* Bytes of workspace gic_window_forward needs (sort scratch, the second
- * state, the permutation and the per-granule force arrays). */
+/* Bytes of workspace gic_window_forward needs (sort scratch, the sorted
+ * state and the two states gic_step alternates between, the permutation,
+ * the per-granule force arrays and the Verlet lists). */
 int gic_window_workspace_size(const GicGrid* grid, int64_t n, int32_t precision, size_t* bytes);
 
 /* K substeps of Alg. 2 (SandSubstep): per substep gic_step (Verlet lists

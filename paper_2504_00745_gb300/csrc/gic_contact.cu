@@ -592,12 +592,28 @@ static unsigned build_blocks(int64_t n) {
   return b < 2048u ? b : 2048u;
 }
 
+NbDev nb_dev(const DGrid& G, const GicNeighbors* nb, bool ident) {
+  const double half = 0.5 * nb->skin;
+  const double lim = half * G.inv_unit;  // skin / 2 in 2^-30 h_c units
+  return NbDev{nb->cap, nb->list, nb->count, nb->ref_cell, nb->ref_pos, nb->slot, nb->cur, nb->at, nb->flags,
+               ident ? 1 : 0, (float)(lim * lim), half * half};
+}
+
+int verlet_view(const DGrid& G, const GicGranules* s, const void* table, const GicNeighbors* nb, const char* what,
+                bool ident, NbDev* out) {
+  int rc;
+  if ((rc = check_table(table))) return rc;
+  if ((rc = check_neighbors(nb, s, what))) return rc;
+  *out = nb_dev(G, nb, ident);
+  return GIC_OK;
+}
+
 int verlet_check(const DGrid& G, const GicGranules* s, const void* table, const GicNeighbors* nb,
                  cudaStream_t stream, const char* what, NbDev* out, GicGranules* copy_to, int32_t* perm) {
   int rc;
   if ((rc = check_table(table))) return rc;
   if ((rc = check_neighbors(nb, s, what))) return rc;
-  NbDev d{nb->cap, nb->list, nb->count, nb->ref_cell, nb->ref_pos, nb->slot, nb->cur, nb->at, nb->flags};
+  const NbDev d = nb_dev(G, nb, false);
   *out = d;
   if (s->n == 0) return GIC_OK;
   if (copy_to && (!perm || !copy_to->id)) return set_error(GIC_ERR_INVALID, "%s: copy needs ids and perm", what);

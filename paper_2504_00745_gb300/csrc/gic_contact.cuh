@@ -321,9 +321,27 @@ __device__ __forceinline__ void for_each_contact(const DGrid& G, const uint4* __
 // slot s.  While every granule has moved less than skin / 2 since then, every
 // pair now in contact is in the rows, so walking them gives exactly
 // gic_contact's pairs.  Between builds the sorted order changes little, so
-// rows, reference positions and partners are read almost in order.
+// rows, reference positions and partners are read almost in order.  When the
+// state is still in the order of the build (gic_step keeps it so between
+// builds) slots are indices, and the walk skips the slot maps (ident).
+//
+// Flag words: kNbRebuild -- this call rebuilds (set by the displacement
+// check before the call, or by gic_step's decision); kNbSticky -- bit 0 a
+// rebuild was requested, bit 1 a row overflowed at the last build (rebuild
+// every call); kNbCounter -- CTAs done; kNbOverflow -- overflow during this
+// build; kNbBuilds -- builds so far; kNbNext -- a granule written by a
+// k_substep is beyond skin / 2 of its reference (gic_step's next call
+// rebuilds; gic_step consumes the word).
 
-enum : int { kNbRebuild = 0, kNbSticky = 1, kNbCounter = 2, kNbOverflow = 3, kNbBuilds = 4, kNbWords = 8 };
+enum : int {
+  kNbRebuild = 0,
+  kNbSticky = 1,
+  kNbCounter = 2,
+  kNbOverflow = 3,
+  kNbBuilds = 4,
+  kNbNext = 5,
+  kNbWords = 8
+};
 
 struct NbDev {
   int cap;
@@ -335,7 +353,13 @@ struct NbDev {
   int32_t* cur;   // by slot
   int32_t* at;    // by sorted index
   uint32_t* flags;
+  int ident;      // the state is in the order of the last build: slot = index
+  float lim2_f;   // (skin / 2)^2 in (2^-30 h_c)^2, FP32 positions
+  double lim2_d;  // (skin / 2)^2 in m^2, FP64 positions
 };
+
+__device__ __forceinline__ float nb_lim2(const NbDev& nb, float) { return nb.lim2_f; }
+__device__ __forceinline__ double nb_lim2(const NbDev& nb, double) { return nb.lim2_d; }
 
 // displacement since the last build beyond skin / 2 (lim2 = (skin / 2)^2 in
 // the units of each precision's position record)
@@ -486,6 +510,11 @@ __device__ __forceinline__ T add_walls_adj(const DGrid& G, const DParams<T>& P, 
 int verlet_prelude(const DGrid& G, const GicParams* params, const GicGranules* s, const void* table,
                    const GicNeighbors* nb, void* F_c, cudaStream_t stream, const char* what, NbDev* out,
                    bool launch_build);
+// The device view of the lists (ident: the state is in the build's order);
+// verlet_view also checks the arguments, and launches nothing.
+NbDev nb_dev(const DGrid& G, const GicNeighbors* nb, bool ident);
+int verlet_view(const DGrid& G, const GicGranules* s, const void* table, const GicNeighbors* nb, const char* what,
+                bool ident, NbDev* out);
 // The displacement check alone (maps the state's ids to slots, sets the
 // rebuild word); with copy_to, it also copies the state into copy_to in the
 // same order and writes the identity into perm.
@@ -574,13 +603,14 @@ __device__ __forceinline__ void for_each_list_contact(const DGrid& G, const NbDe
                                                       const float4& fi, const int32_t* __restrict__ cell,
                                                       const pos_t<T>* __restrict__ pos,
                                                       const float4* __restrict__ posf, F&& f) {
-  const int32_t s = nb.at[i];
+  const int32_t s = nb.ident ? (int32_t)i : nb.at[i];
   const int32_t* row = nb.list + (int64_t)s * nb.cap;
   const int cnt = nb.count[s];
   for (int k = 0; k < cnt; k += 4) {
     int64_t jj[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) jj[u] = k + u < cnt ? (int64_t)nb.cur[row[k + u]] : -1;
+    for (int u = 0; u < 4; ++u)
+      jj[u] = k + u < cnt ? (int64_t)(nb.ident ? row[k + u] : nb.cur[row[k + u]]) : -1;
     int32_t cj[4];
     float4 fj[4];
 #pragma unroll

@@ -330,4 +330,28 @@ __device__ __forceinline__ T block_sum(T v, T* smem /* >= 32 */) {
   return r;  // valid in thread 0
 }
 
+// Block sums of two values in one pass (one barrier); the results are valid
+// in thread 0, and smem (>= 64 doubles) is free again after the next barrier.
+__device__ __forceinline__ void block_sum2(double& a, double& b, double* smem) {
+  for (int off = 16; off > 0; off >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, off);
+    b += __shfl_down_sync(0xffffffffu, b, off);
+  }
+  const int w = threadIdx.x >> 5;
+  if (lane_id() == 0) {
+    smem[w] = a;
+    smem[32 + w] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int nw = (blockDim.x + 31) >> 5;
+    a = threadIdx.x < nw ? smem[threadIdx.x] : 0.0;
+    b = threadIdx.x < nw ? smem[32 + threadIdx.x] : 0.0;
+    for (int off = 16; off > 0; off >>= 1) {
+      a += __shfl_down_sync(0xffffffffu, a, off);
+      b += __shfl_down_sync(0xffffffffu, b, off);
+    }
+  }
+}
+
 }  // namespace gic

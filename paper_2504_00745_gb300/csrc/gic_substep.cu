@@ -22,9 +22,9 @@ __global__ void __launch_bounds__(kSubstepThreads, sizeof(T) == 4 ? 4 : 2) k_sub
     DGrid G, DParams<T> P, int64_t n, const int32_t* __restrict__ cell, const pos_t<T>* __restrict__ pos,
     const float4* __restrict__ posf, const vec_t<T>* __restrict__ vel, const int32_t* __restrict__ id, NbDev nb,
     const uint4* __restrict__ table, T skin, Fields<T> Fd, int32_t* __restrict__ cell_out, pos_t<T>* __restrict__ pos_out,
-    vec_t<T>* __restrict__ vel_out, int32_t* __restrict__ id_out, vec_t<T>* __restrict__ fex_out,
-    double* __restrict__ alpha, T* __restrict__ Fs_u, T* __restrict__ Fs_v, T* __restrict__ Fs_w,
-    double* __restrict__ sums, uint32_t* status) {
+    vec_t<T>* __restrict__ vel_out, int32_t* __restrict__ id_out, float4* __restrict__ posf_out,
+    vec_t<T>* __restrict__ fex_out, double* __restrict__ alpha, T* __restrict__ Fs_u, T* __restrict__ Fs_v,
+    T* __restrict__ Fs_w, double* __restrict__ sums, uint32_t* status) {
   __shared__ P2GShared sh;  // FP32 path only
   const bool rebuild = (nb.flags[kNbRebuild] | nb.flags[kNbSticky]) != 0u;  // uniform over the launch
   const bool do_a = alpha != nullptr, do_f = Fs_u != nullptr;
@@ -35,6 +35,7 @@ __global__ void __launch_bounds__(kSubstepThreads, sizeof(T) == 4 ? 4 : 2) k_sub
   int32_t ci = 0, co = 0;
   pos_t<T> pi{}, po{};
   T fe[3] = {T(0), T(0), T(0)};
+  bool far = false;
   if (valid) {
     ci = cell[i];
     pi = pos[i];
@@ -73,8 +74,23 @@ __global__ void __launch_bounds__(kSubstepThreads, sizeof(T) == 4 ? 4 : 2) k_sub
     pos_out[i] = po;
     vel_out[i] = vo;
     if (id_out && id) id_out[i] = id[i];
+    if constexpr (sizeof(T) == 4) {
+      if (posf_out)
+        posf_out[i] = make_float4((float)po.x * 0x1p-30f, (float)po.y * 0x1p-30f, (float)po.z * 0x1p-30f,
+                                  __uint_as_float(po.w));
+    }
     if (fex_out) fex_out[i] = make_vec<T>(fe[0], fe[1], fe[2]);
+    // the next call's displacement test, on the positions just written
+    // (after a build this call's positions are the reference)
+    if (rebuild) {
+      far = moved_far(G, co, po, ci, pi, nb_lim2(nb, T(0)));
+    } else {
+      const int32_t sl = nb.ident ? (int32_t)i : nb.at[i];
+      far = moved_far(G, co, po, nb.ref_cell[sl], reinterpret_cast<const pos_t<T>*>(nb.ref_pos)[sl],
+                      nb_lim2(nb, T(0)));
+    }
   }
+  if (__any_sync(0xffffffffu, far) && lane_id() == 0) atomicOr(&nb.flags[kNbNext], 1u);
 
   // a5: P2G
   if constexpr (sizeof(T) == 4) {
@@ -168,14 +184,14 @@ constexpr int kSubstepAdjThreads = 128;
 // it), forming each partner's F_c gradient from the partner's upstream
 // gradients.  Writes the result through perm (the sort's scatter).
 template <typename T>
-__global__ void __launch_bounds__(kSubstepAdjThreads, sizeof(T) == 4 ? 3 : 1) k_substep_adj(
+__global__ void __launch_bounds__(kSubstepAdjThreads, sizeof(T) == 4 ? 6 : 3) k_substep_adj(
     DGrid G, DParams<T> P, int64_t n, const int32_t* __restrict__ cell, const pos_t<T>* __restrict__ pos,
     const float4* __restrict__ posf, const vec_t<T>* __restrict__ vel, const int32_t* __restrict__ id, NbDev nb,
     const uint4* __restrict__ table, T skin, Fields<T> Fd, const vec_t<T>* __restrict__ gxo,
     const vec_t<T>* __restrict__ gvo, const vec_t<T>* __restrict__ gfe, const int32_t* __restrict__ perm,
     vec_t<T>* __restrict__ gxi, vec_t<T>* __restrict__ gvi, double* __restrict__ g_cdrag,
     double* __restrict__ g_mu) {
-  __shared__ double s_red[32];
+  __shared__ double s_red[64];
   const bool rebuild = (nb.flags[kNbRebuild] | nb.flags[kNbSticky]) != 0u;  // uniform over the launch
   const int64_t i = blockIdx.x * (int64_t)kSubstepAdjThreads + threadIdx.x;
   double my_gc = 0.0, my_gmu = 0.0;
@@ -226,15 +242,14 @@ __global__ void __launch_bounds__(kSubstepAdjThreads, sizeof(T) == 4 ? 3 : 1) k_
     gxi[out] = make_vec<T>(gx[0], gx[1], gx[2]);
     gvi[out] = make_vec<T>(gv[0], gv[1], gv[2]);
   }
-  if (g_cdrag) {
-    const double sc = block_sum(my_gc, s_red);
-    if (threadIdx.x == 0) atomicAdd(g_cdrag, sc);
+  if (g_cdrag || g_mu) {
+    block_sum2(my_gc, my_gmu, s_red);
+    if (threadIdx.x == 0) {
+      if (g_cdrag) atomicAdd(g_cdrag, my_gc);
+      if (g_mu) atomicAdd(g_mu, my_gmu);
+    }
   }
-  if (g_mu) {
-    const double sm = block_sum(my_gmu, s_red);
-    if (threadIdx.x == 0) atomicAdd(g_mu, sm);
-  }
-  verlet_call_done(nb, rebuild);
+  verlet_call_done(nb, rebuild);  // its barrier also frees s_red
 }
 
 }  // namespace gic
@@ -263,15 +278,15 @@ static int substep_launch(const DGrid& G, const GicParams* params, const GicGran
       k_substep<float><<<blocks, kSubstepThreads, 0, stream>>>(
           G, P, s->n, s->cell, (const uint4*)s->pos, (const float4*)s->posf, (const float4*)s->vel, s->id, d,
           (const uint4*)cell_table, (float)nb->skin, fields<float>(u, v, w, p, alpha_f), next->cell,
-          (uint4*)next->pos, (float4*)next->vel, next->id, (float4*)f_ex, alpha_s, (float*)Fs_u, (float*)Fs_v,
-          (float*)Fs_w, sums2, status_word());
+          (uint4*)next->pos, (float4*)next->vel, next->id, (float4*)next->posf, (float4*)f_ex, alpha_s,
+          (float*)Fs_u, (float*)Fs_v, (float*)Fs_w, sums2, status_word());
     } else {
       DParams<double> P;
       if ((rc = make_params(params, &P))) return rc;
       k_substep<double><<<blocks, kSubstepThreads, 0, stream>>>(
           G, P, s->n, s->cell, (const d4*)s->pos, nullptr, (const d4*)s->vel, s->id, d, (const uint4*)cell_table,
           nb->skin, fields<double>(u, v, w, p, alpha_f), next->cell, (d4*)next->pos, (d4*)next->vel, next->id,
-          (d4*)f_ex, alpha_s, (double*)Fs_u, (double*)Fs_v, (double*)Fs_w, sums2, status_word());
+          nullptr, (d4*)f_ex, alpha_s, (double*)Fs_u, (double*)Fs_v, (double*)Fs_w, sums2, status_word());
     }
     count_launches(1);
     ++*launches;
@@ -315,9 +330,15 @@ extern "C" int gic_substep(const GicGrid* grid, const GicParams* params, const G
 
 namespace gic {
 
-// Sets the graph's conditional (run the sort) from the Verlet words.
-__global__ void k_step_decide(const uint32_t* flags, cudaGraphConditionalHandle h) {
-  cudaGraphSetConditional(h, (flags[kNbRebuild] | flags[kNbSticky]) != 0u ? 1u : 0u);
+// gic_step's decision: this call rebuilds the lists (and sorts) when the
+// previous call's k_substep left a granule beyond skin / 2 of its reference,
+// or a rebuild was requested.  Sets the two branches' conditionals.
+__global__ void k_step_decide(uint32_t* flags, cudaGraphConditionalHandle rebuild, cudaGraphConditionalHandle keep) {
+  const unsigned r = (flags[kNbNext] | flags[kNbSticky]) != 0u ? 1u : 0u;
+  flags[kNbRebuild] = r;
+  flags[kNbNext] = 0u;
+  cudaGraphSetConditional(rebuild, r);
+  cudaGraphSetConditional(keep, 1u - r);
 }
 
 // Everything a gic_step graph depends on; a call with the same bytes reuses
@@ -325,7 +346,7 @@ __global__ void k_step_decide(const uint32_t* flags, cudaGraphConditionalHandle 
 struct StepKey {
   GicGrid grid;
   GicParams params;
-  GicGranules state, sorted;
+  GicGranules state, next, sorted;
   GicNeighbors nb;
   const void* ptr[13];
   size_t ws_bytes;
@@ -340,7 +361,7 @@ struct StepGraph {
   int launches = 0;  // kernels every launch runs (the sort's are not counted)
 };
 
-constexpr int kStepGraphs = 4;
+constexpr int kStepGraphs = 8;
 static StepGraph g_step_graphs[kStepGraphs];
 static uint64_t g_step_clock = 0;
 static std::mutex g_step_mu;
@@ -348,35 +369,59 @@ static std::mutex g_step_mu;
 static bool same_key(const StepKey& a, const StepKey& b) { return memcmp(&a, &b, sizeof(StepKey)) == 0; }
 
 static void store_key(StepKey& k, const GicGrid* grid, const GicParams* params, const GicGranules* state,
-                      const GicGranules* sorted, const GicNeighbors* nb, const void* const ptr[13], size_t ws_bytes) {
+                      const GicGranules* next, const GicGranules* sorted, const GicNeighbors* nb,
+                      const void* const ptr[13], size_t ws_bytes) {
   memset(&k, 0, sizeof(k));  // padding bytes take part in the comparison
   memcpy(&k.grid, grid, sizeof(GicGrid));
   memcpy(&k.params, params, sizeof(GicParams));
   memcpy(&k.state, state, sizeof(GicGranules));
+  memcpy(&k.next, next, sizeof(GicGranules));
   memcpy(&k.sorted, sorted, sizeof(GicGranules));
   memcpy(&k.nb, nb, sizeof(GicNeighbors));
   for (int i = 0; i < 13; ++i) k.ptr[i] = ptr[i];
   k.ws_bytes = ws_bytes;
 }
 
+// Adds an IF node on `dep` with handle h and captures fill(stream) into its body.
+template <typename Fill>
+static int add_branch(cudaGraph_t g, cudaGraphNode_t dep, cudaGraphConditionalHandle h, cudaStream_t cs, Fill&& fill) {
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeIf;
+  cp.conditional.size = 1;
+  cudaGraphNode_t cond;
+  if (cudaGraphAddNode(&cond, g, &dep, nullptr, 1, &cp) != cudaSuccess)
+    return set_error(GIC_ERR_CUDA, "gic_step: conditional node failed");
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  cudaGraph_t got = nullptr;
+  if (cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) != cudaSuccess)
+    return set_error(GIC_ERR_CUDA, "gic_step: graph capture failed");
+  int rc = fill(cs);
+  if (cudaStreamEndCapture(cs, &got) != cudaSuccess && rc == GIC_OK)
+    rc = set_error(GIC_ERR_CUDA, "gic_step: graph capture failed");
+  return rc;
+}
+
 // Builds the graph of one gic_step configuration:
-//   check (+ copy) -> decide -> IF rebuild: sort -> [zero alpha] -> k_substep -> [alpha out]
+//   decide -> IF rebuild: sort (state -> sorted) -> [zero alpha] -> k_substep (sorted -> next) -> [alpha out]
+//          -> IF keep:    [zero alpha] -> k_substep (state -> next) -> [alpha out]
 static int build_step_graph(StepGraph& sg, const DGrid& G, const GicGrid* grid, const GicParams* params,
-                            GicGranules* state, GicGranules* sorted, int32_t* perm, void* cell_table, void* ws,
-                            size_t ws_bytes, const GicNeighbors* nb, const void* u, const void* v, const void* w,
-                            const void* p, const void* alpha_f, double* alpha_s, void* Fs_u, void* Fs_v, void* Fs_w,
-                            double* sums2) {
+                            const GicGranules* state, GicGranules* next, GicGranules* sorted, int32_t* perm,
+                            void* cell_table, void* ws, size_t ws_bytes, const GicNeighbors* nb, const NbDev& d,
+                            const void* u, const void* v, const void* w, const void* p, const void* alpha_f,
+                            double* alpha_s, void* Fs_u, void* Fs_v, void* Fs_w, double* sums2) {
   int rc = GIC_OK;
   cudaGraph_t g = nullptr;
   cudaGraphExec_t ex = nullptr;
   cudaStream_t cs = nullptr;
   cudaGraph_t got = nullptr;
-  cudaGraphConditionalHandle h;
-  NbDev d;
+  cudaGraphConditionalHandle h_rebuild, h_keep;
   int launches = 0;
   status_word();  // resolve the device address before capturing
   if (cudaGraphCreate(&g, 0) != cudaSuccess) return set_error(GIC_ERR_CUDA, "gic_step: cudaGraphCreate failed");
-  if (cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault) != cudaSuccess ||
+  if (cudaGraphConditionalHandleCreate(&h_rebuild, g, 0, cudaGraphCondAssignDefault) != cudaSuccess ||
+      cudaGraphConditionalHandleCreate(&h_keep, g, 0, cudaGraphCondAssignDefault) != cudaSuccess ||
       cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
     cudaGraphDestroy(g);
@@ -384,63 +429,38 @@ static int build_step_graph(StepGraph& sg, const DGrid& G, const GicGrid* grid, 
   }
   set_capturing(true);
   do {
-    // 1. displacement check of `state` with its copy into `sorted`, then the decision
+    // 1. the decision
     if (cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
       rc = set_error(GIC_ERR_CUDA, "gic_step: graph capture failed");
       break;
     }
-    rc = verlet_check(G, state, cell_table, nb, cs, "gic_step", &d, sorted, perm);
-    if (rc == GIC_OK) k_step_decide<<<1, 1, 0, cs>>>(nb->flags, h);
-    if (cudaStreamEndCapture(cs, &got) != cudaSuccess && rc == GIC_OK)
+    k_step_decide<<<1, 1, 0, cs>>>(nb->flags, h_rebuild, h_keep);
+    if (cudaStreamEndCapture(cs, &got) != cudaSuccess) {
       rc = set_error(GIC_ERR_CUDA, "gic_step: graph capture failed");
-    if (rc) break;
-    launches += 2;
+      break;
+    }
+    launches += 1;
     size_t nn = 0;
-    cudaGraphNode_t nodes[4];
-    if (cudaGraphGetNodes(g, nullptr, &nn) != cudaSuccess || nn > 4 || nn == 0 ||
-        cudaGraphGetNodes(g, nodes, &nn) != cudaSuccess) {
+    cudaGraphNode_t decide = nullptr;
+    if (cudaGraphGetNodes(g, nullptr, &nn) != cudaSuccess || nn != 1 || cudaGraphGetNodes(g, &decide, &nn) != cudaSuccess) {
       rc = set_error(GIC_ERR_CUDA, "gic_step: unexpected graph");
       break;
     }
-    cudaGraphNode_t decide = nullptr;
-    for (size_t k = 0; k < nn; ++k) {
-      cudaKernelNodeParams kp;
-      if (cudaGraphKernelNodeGetParams(nodes[k], &kp) == cudaSuccess && kp.func == (void*)k_step_decide)
-        decide = nodes[k];
-    }
-    if (!decide) {
-      rc = set_error(GIC_ERR_CUDA, "gic_step: decision node not found");
-      break;
-    }
-    // 2. the sort, as the body of an IF node
-    cudaGraphNodeParams cp = {};
-    cp.type = cudaGraphNodeTypeConditional;
-    cp.conditional.handle = h;
-    cp.conditional.type = cudaGraphCondTypeIf;
-    cp.conditional.size = 1;
-    cudaGraphNode_t cond;
-    if (cudaGraphAddNode(&cond, g, &decide, nullptr, 1, &cp) != cudaSuccess) {
-      rc = set_error(GIC_ERR_CUDA, "gic_step: conditional node failed");
-      break;
-    }
-    cudaGraph_t body = cp.conditional.phGraph_out[0];
-    if (cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
-      rc = set_error(GIC_ERR_CUDA, "gic_step: graph capture failed");
-      break;
-    }
-    rc = sort_gated(grid, state, sorted, perm, cell_table, ws, ws_bytes, nullptr, cs);
-    if (cudaStreamEndCapture(cs, &got) != cudaSuccess && rc == GIC_OK)
-      rc = set_error(GIC_ERR_CUDA, "gic_step: graph capture failed");
+    // 2. the branch that rebuilds: sort, then the substep from the sorted state (its launches not counted)
+    int uncounted = 0;
+    rc = add_branch(g, decide, h_rebuild, cs, [&](cudaStream_t st) {
+      int r = sort_gated(grid, state, sorted, perm, cell_table, ws, ws_bytes, nullptr, st);
+      if (r == GIC_OK)
+        r = substep_launch(G, params, sorted, cell_table, nb, d, u, v, w, p, alpha_f, next, nullptr, alpha_s, Fs_u,
+                           Fs_v, Fs_w, sums2, st, &uncounted);
+      return r;
+    });
     if (rc) break;
-    // 3. the fused rest of the substep, sorted -> state
-    if (cudaStreamBeginCaptureToGraph(cs, g, &cond, nullptr, 1, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
-      rc = set_error(GIC_ERR_CUDA, "gic_step: graph capture failed");
-      break;
-    }
-    rc = substep_launch(G, params, sorted, cell_table, nb, d, u, v, w, p, alpha_f, state, nullptr, alpha_s, Fs_u, Fs_v,
-                        Fs_w, sums2, cs, &launches);
-    if (cudaStreamEndCapture(cs, &got) != cudaSuccess && rc == GIC_OK)
-      rc = set_error(GIC_ERR_CUDA, "gic_step: graph capture failed");
+    // 3. the branch that keeps the lists: the substep straight from the state
+    rc = add_branch(g, decide, h_keep, cs, [&](cudaStream_t st) {
+      return substep_launch(G, params, state, cell_table, nb, d, u, v, w, p, alpha_f, next, nullptr, alpha_s, Fs_u,
+                            Fs_v, Fs_w, sums2, st, &launches);
+    });
     if (rc) break;
     if (cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) {
       rc = set_error(GIC_ERR_CUDA, "gic_step: graph instantiation failed");
@@ -462,28 +482,36 @@ static int build_step_graph(StepGraph& sg, const DGrid& G, const GicGrid* grid, 
 
 }  // namespace gic
 
-extern "C" int gic_step(const GicGrid* grid, const GicParams* params, GicGranules* state, GicGranules* sorted,
-                        int32_t* perm, void* cell_table, void* ws, size_t ws_bytes, const GicNeighbors* nb,
-                        const void* u, const void* v, const void* w, const void* p, const void* alpha_f,
-                        double* alpha_s, void* Fs_u, void* Fs_v, void* Fs_w, double* sums2, gic_stream_t stream) {
+static bool share_array(const GicGranules* a, const GicGranules* b) {
+  return a->cell == b->cell || a->pos == b->pos || a->vel == b->vel || a->id == b->id ||
+         (a->posf && a->posf == b->posf);
+}
+
+extern "C" int gic_step(const GicGrid* grid, const GicParams* params, const GicGranules* state, GicGranules* next,
+                        GicGranules* sorted, int32_t* perm, void* cell_table, void* ws, size_t ws_bytes,
+                        const GicNeighbors* nb, const void* u, const void* v, const void* w, const void* p,
+                        const void* alpha_f, double* alpha_s, void* Fs_u, void* Fs_v, void* Fs_w, double* sums2,
+                        gic_stream_t stream) {
   DGrid G;
   int rc = make_grid(grid, &G);
   if (rc) return rc;
   if (!params) return set_error(GIC_ERR_INVALID, "gic_step: params is NULL");
   if ((rc = check_granules(state, "gic_step state", true))) return rc;
+  if ((rc = check_granules(next, "gic_step next", true))) return rc;
   if ((rc = check_granules(sorted, "gic_step sorted", true))) return rc;
-  if (sorted->n != state->n || sorted->precision != state->precision)
-    return set_error(GIC_ERR_INVALID, "gic_step: state/sorted size or precision differ");
-  if (state->cell == sorted->cell || state->pos == sorted->pos || state->vel == sorted->vel ||
-      state->id == sorted->id)
-    return set_error(GIC_ERR_INVALID, "gic_step: state and sorted must not alias");
+  if (next->n != state->n || next->precision != state->precision || sorted->n != state->n ||
+      sorted->precision != state->precision)
+    return set_error(GIC_ERR_INVALID, "gic_step: state/next/sorted size or precision differ");
+  if (share_array(state, next) || share_array(state, sorted) || share_array(next, sorted))
+    return set_error(GIC_ERR_INVALID, "gic_step: state, next and sorted must not share arrays");
   if (state->n > 0 && !perm) return set_error(GIC_ERR_INVALID, "gic_step: perm is NULL");
   if (!u || !v || !w || !p || !alpha_f) return set_error(GIC_ERR_INVALID, "gic_step: null fluid field");
   bool fs = Fs_u || Fs_v || Fs_w;
   if (fs && !(Fs_u && Fs_v && Fs_w)) return set_error(GIC_ERR_INVALID, "gic_step: give all three F_s arrays or none");
   if (sums2 && !alpha_s) return set_error(GIC_ERR_INVALID, "gic_step: sums2 needs alpha_s");
   if (!nb) return set_error(GIC_ERR_INVALID, "gic_step: neighbours struct is NULL");
-  if (!cell_table) return set_error(GIC_ERR_INVALID, "gic_step: cell_table is NULL");
+  NbDev d;
+  if ((rc = verlet_view(G, state, cell_table, nb, "gic_step", true, &d))) return rc;
   if (state->n == 0) return GIC_OK;
   {  // arguments of the sort, checked before they are baked into a graph
     size_t need = 0;
@@ -491,11 +519,10 @@ extern "C" int gic_step(const GicGrid* grid, const GicParams* params, GicGranule
     if (!ws || ws_bytes < need)
       return set_error(GIC_ERR_WORKSPACE, "gic_step: workspace of %zu bytes needed, %zu given", need, ws_bytes);
     if ((uintptr_t)ws % 256) return set_error(GIC_ERR_ALIGN, "gic_step: workspace must be 256-byte aligned");
-    if ((uintptr_t)cell_table % 16) return set_error(GIC_ERR_ALIGN, "gic_step: cell_table must be 16-byte aligned");
   }
   const void* ptr[13] = {perm, cell_table, ws, u, v, w, p, alpha_f, alpha_s, Fs_u, Fs_v, Fs_w, sums2};
   StepKey key;
-  store_key(key, grid, params, state, sorted, nb, ptr, ws_bytes);
+  store_key(key, grid, params, state, next, sorted, nb, ptr, ws_bytes);
   std::lock_guard<std::mutex> lock(g_step_mu);
   StepGraph* hit = nullptr;
   for (auto& sg : g_step_graphs)
@@ -514,8 +541,8 @@ extern "C" int gic_step(const GicGrid* grid, const GicParams* params, GicGranule
       cudaGraphDestroy(slot->graph);
       slot->used = false;
     }
-    if ((rc = build_step_graph(*slot, G, grid, params, state, sorted, perm, cell_table, ws, ws_bytes, nb, u, v, w, p,
-                               alpha_f, alpha_s, Fs_u, Fs_v, Fs_w, sums2)))
+    if ((rc = build_step_graph(*slot, G, grid, params, state, next, sorted, perm, cell_table, ws, ws_bytes, nb, d, u,
+                               v, w, p, alpha_f, alpha_s, Fs_u, Fs_v, Fs_w, sums2)))
       return rc;
     memcpy(&slot->key, &key, sizeof(StepKey));
     slot->used = true;

@@ -11,7 +11,7 @@ namespace gic {
 constexpr int kWindowNbCap = 64;  // Verlet partners per granule in the window's lists
 
 struct WindowLayout {
-  size_t sort_ws, off_sort, off_state_b, off_perm, off_fc, off_ffl, off_af, off_fex, off_nb, total;
+  size_t sort_ws, off_sort, state_bytes, off_state_b, off_perm, off_fc, off_ffl, off_af, off_fex, off_nb, total;
   // host variant only: device copies of inputs and outputs
   size_t off_cxyz, off_q, off_r, off_v, off_fields, off_alpha, off_fs, off_sums, off_x, off_vout, off_state_a,
       off_table, host_total;
@@ -31,8 +31,11 @@ static int window_layout(const GicGrid* grid, int64_t n, int32_t precision, Wind
   L->sort_ws = al(ws);
   L->off_sort = off;
   off += L->sort_ws;
-  L->off_state_b = off;  // cell, pos, vel, id of the second state (+ float positions, FP32)
-  off += al(4 * nn) + vec + vec + al(4 * nn) + (precision == GIC_FP32 ? al(16 * nn) : 0);
+  // three states: the sorted one and the two that gic_step alternates between; each cell, pos, vel, id (+ float
+  // positions, FP32)
+  L->state_bytes = al(4 * nn) + vec + vec + al(4 * nn) + (precision == GIC_FP32 ? al(16 * nn) : 0);
+  L->off_state_b = off;
+  off += 3 * L->state_bytes;
   L->off_perm = off;
   off += al(4 * nn);
   L->off_fc = off;
@@ -133,12 +136,16 @@ extern "C" int gic_window_forward(const GicGrid* grid, const GicParams* params, 
                      ws_bytes);
   if ((uintptr_t)ws % 256) return set_error(GIC_ERR_ALIGN, "gic_window_forward: workspace must be 256-byte aligned");
   char* base = (char*)ws;
-  GicGranules B = state_at(base + L.off_state_b, state->n, state->precision);
-  if (!state->id) B.id = nullptr;
-  if (state->precision == GIC_FP32) {
-    size_t nn = (size_t)(state->n > 0 ? state->n : 1);
-    B.posf = (float*)(base + L.off_state_b + al(4 * nn) + 2 * al(16 * nn) + al(4 * nn));
+  GicGranules S[3];  // S[0] sorted, S[1] and S[2] the states gic_step alternates between
+  for (int k = 0; k < 3; ++k) {
+    S[k] = state_at(base + L.off_state_b + k * L.state_bytes, state->n, state->precision);
+    if (!state->id) S[k].id = nullptr;
+    if (state->precision == GIC_FP32) {
+      size_t nn = (size_t)(state->n > 0 ? state->n : 1);
+      S[k].posf = (float*)(base + L.off_state_b + k * L.state_bytes + al(4 * nn) + 2 * al(16 * nn) + al(4 * nn));
+    }
   }
+  GicGranules& B = S[0];
   int32_t* perm = (int32_t*)(base + L.off_perm);
   void* Fc = base + L.off_fc;
   void* Ffl = base + L.off_ffl;
@@ -172,12 +179,15 @@ extern "C" int gic_window_forward(const GicGrid* grid, const GicParams* params, 
     if ((rc = gic_neighbors_reset(&nb, stream))) return rc;
   }
   // alpha_s once, at the final positions (Alg. 1 CalTargetFraction); F_s every substep (Alg. 2)
+  const GicGranules* cur = state;  // the lists were just reset: the first gic_step sorts `state`
   for (int s = 0; s < K; ++s) {
     bool last = s == K - 1;
     if (verlet) {  // sort only on list rebuilds, the rest of the substep fused
-      if ((rc = gic_step(grid, params, state, &B, perm, cell_table, base + L.off_sort, L.sort_ws, &nb, u, v, w, p,
+      GicGranules* nxt = cur == &S[1] ? &S[2] : &S[1];
+      if ((rc = gic_step(grid, params, cur, nxt, &B, perm, cell_table, base + L.off_sort, L.sort_ws, &nb, u, v, w, p,
                          alpha_f, last ? alpha_s : nullptr, Fs_u, Fs_v, Fs_w, last ? sums2 : nullptr, stream)))
         return rc;
+      cur = nxt;
       continue;
     }
     if ((rc = gic_sort(grid, state, &B, perm, cell_table, base + L.off_sort, L.sort_ws, stream))) return rc;
@@ -187,6 +197,18 @@ extern "C" int gic_window_forward(const GicGrid* grid, const GicParams* params, 
     if ((rc = gic_p2g(grid, params, &B, state, fex, last ? alpha_s : nullptr, Fs_u, Fs_v, Fs_w,
                       last ? sums2 : nullptr, stream)))
       return rc;
+  }
+  if (cur != state) {  // the result back into the caller's state
+    const size_t n = (size_t)state->n, real = state->precision == GIC_FP32 ? 4 : 8;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(state->cell, cur->cell, 4 * n, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(state->pos, cur->pos, 4 * real * n, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(state->vel, cur->vel, 4 * real * n, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(state->id, cur->id, 4 * n, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+      return set_error(GIC_ERR_CUDA, "gic_window_forward: copy of the result failed");
+    if (state->posf && cur->posf &&
+        cudaMemcpyAsync(state->posf, cur->posf, 16 * n, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+      return set_error(GIC_ERR_CUDA, "gic_window_forward: copy of the result failed");
   }
   return GIC_OK;
 }

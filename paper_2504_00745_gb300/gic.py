@@ -76,7 +76,7 @@ _SIGS = {
     "gic_substep": [_P] * 18,
     "gic_contact_verlet_adj": [_P] * 11,
     "gic_substep_adj": [_P] * 19,
-    "gic_step": [_P, _P, _P, _P, _P, _P, _P, C.c_size_t, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P],
+    "gic_step": [_P, _P, _P, _P, _P, _P, _P, _P, C.c_size_t, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P],
 }
 # entry points that exist in include/gic.h but are declared optional here
 # (added later in the library's life) are looked up lazily
@@ -317,13 +317,13 @@ def gic_substep_adj(grid: GicGrid, params: GicParams, sorted_: State, perm, cell
                                  _ptr(g_mu), _stream(stream)), "gic_substep_adj")
 
 
-def gic_step(grid: GicGrid, params: GicParams, state: State, sorted_: State, perm, cell_table, ws, nb: Neighbors,
-             u, v, w, p, alpha_f, alpha_s=None, Fs=(None, None, None), sums2=None, stream=None):
-    a, s, b = state.struct(), sorted_.struct(), nb.struct()
-    _check(lib().gic_step(C.byref(grid), C.byref(params), C.byref(a), C.byref(s), _ptr(perm), _ptr(cell_table),
-                          _ptr(ws), ws.numel() * ws.element_size(), C.byref(b), _ptr(u), _ptr(v), _ptr(w), _ptr(p),
-                          _ptr(alpha_f), _ptr(alpha_s), _ptr(Fs[0]), _ptr(Fs[1]), _ptr(Fs[2]), _ptr(sums2),
-                          _stream(stream)), "gic_step")
+def gic_step(grid: GicGrid, params: GicParams, state: State, next_: State, sorted_: State, perm, cell_table, ws,
+             nb: Neighbors, u, v, w, p, alpha_f, alpha_s=None, Fs=(None, None, None), sums2=None, stream=None):
+    a, t, s, b = state.struct(), next_.struct(), sorted_.struct(), nb.struct()
+    _check(lib().gic_step(C.byref(grid), C.byref(params), C.byref(a), C.byref(t), C.byref(s), _ptr(perm),
+                          _ptr(cell_table), _ptr(ws), ws.numel() * ws.element_size(), C.byref(b), _ptr(u), _ptr(v),
+                          _ptr(w), _ptr(p), _ptr(alpha_f), _ptr(alpha_s), _ptr(Fs[0]), _ptr(Fs[1]), _ptr(Fs[2]),
+                          _ptr(sums2), _stream(stream)), "gic_step")
 
 
 def gic_neighbors_reset(nb: Neighbors, stream=None):

@@ -38,8 +38,11 @@ class Simulator:
     as host or device tensors.  verlet_skin (metres): contact through Verlet
     lists with that skin (gic_contact_verlet, cap partners per granule)
     instead of walking the cell table every substep (gic_contact); with
-    lists and fused, a substep is one gic_step (sort only on list rebuilds,
-    then the fused gic_substep).
+    lists and fused, a substep is one gic_step from A into A2 (sort into B
+    only on list rebuilds, then the fused substep), after which A and A2
+    swap: A is always the current state.  A state written into A from
+    outside goes through load_state (or set_state), which makes the next
+    gic_step rebuild the lists.
     """
 
     def __init__(self, grid, params, n: int, precision: int = GIC_FP32, device="cuda",
@@ -53,8 +56,10 @@ class Simulator:
         self.device = torch.device(device)
         self.real = torch.float32 if precision == GIC_FP32 else torch.float64
         n = self.n
-        self.A = State.empty(n, precision, device)
-        self.B = State.empty(n, precision, device, with_posf=True)  # sorted state: float position copy (FP32)
+        # FP32 states carry the float position copy that the contact pre-tests read
+        self.A = State.empty(n, precision, device, with_posf=True)
+        self.A2 = State.empty(n, precision, device, with_posf=True)  # gic_step's next state
+        self.B = State.empty(n, precision, device, with_posf=True)  # the sorted state
         self.perm = torch.empty(n, dtype=torch.int32, device=device)
         self.table = gic.new_cell_table(self.grid, device)
         self.ws = gic.new_workspace(self.grid, n, precision, device)
@@ -72,6 +77,7 @@ class Simulator:
         self.fluid: Optional[DeviceFluid] = None
         self.nb: Optional[gic.Neighbors] = None
         self.fused = fused
+        self.lists_current = False  # A is the last gic_step's result and the lists are those it used
         if verlet_skin is not None:
             self.nb = gic.Neighbors(n, precision, cap=verlet_cap, skin=verlet_skin, device=device)
             gic.gic_neighbors_reset(self.nb)
@@ -89,6 +95,13 @@ class Simulator:
                      dev(v, torch.float32), self.A, stream)
         if self.nb is not None:  # radii may have changed
             gic.gic_neighbors_reset(self.nb, stream)
+        self.lists_current = False
+
+    def load_state(self, src: State):
+        """Copies a state (e.g. a saved initial state) into A; the next
+        gic_step rebuilds the lists."""
+        _copy_state(self.A, src)
+        self.lists_current = False
 
     @classmethod
     def from_problem(cls, prob, precision=GIC_FP32, device="cuda", verlet: bool = True, fused: bool = True,
@@ -118,11 +131,16 @@ class Simulator:
         substep, as the adjoint's recomputation needs)."""
         F = self.fluid
         if self.nb is not None and self.fused and not sort_every:  # sorts only when the lists are rebuilt
-            gic.gic_step(self.grid, self.params, self.A, self.B, self.perm, self.table, self.ws, self.nb, F.u, F.v,
-                         F.w, F.p, F.alpha_f, self.alpha_s if alpha else None,
+            if not self.lists_current:
+                gic.gic_neighbors_reset(self.nb, stream)
+            gic.gic_step(self.grid, self.params, self.A, self.A2, self.B, self.perm, self.table, self.ws, self.nb,
+                         F.u, F.v, F.w, F.p, F.alpha_f, self.alpha_s if alpha else None,
                          self.Fs if transfer else (None, None, None), self.sums if (sums and alpha) else None,
                          stream)
+            self.A, self.A2 = self.A2, self.A
+            self.lists_current = True
             return
+        self.lists_current = False
         gic.gic_sort(self.grid, self.A, self.B, self.perm, self.table, self.ws, stream)
         if self.nb is not None and self.fused:
             self.fused_rest(alpha, transfer, sums, stream)
@@ -137,6 +155,7 @@ class Simulator:
     def fused_rest(self, alpha: bool, transfer: bool, sums: bool, stream=None):
         """Everything after the sort as one gic_substep: B -> A."""
         F = self.fluid
+        self.lists_current = False
         gic.gic_substep(self.grid, self.params, self.B, self.table, self.nb, F.u, F.v, F.w, F.p, F.alpha_f, self.A,
                         None, self.alpha_s if alpha else None,
                         self.Fs if transfer else (None, None, None), self.sums if (sums and alpha) else None, stream)
@@ -144,6 +163,7 @@ class Simulator:
     def contact(self, stream=None):
         """a2 on the sorted state B: Verlet lists when configured, else the
         cell-table walk."""
+        self.lists_current = False
         if self.nb is not None:
             gic.gic_contact_verlet(self.grid, self.params, self.B, self.table, self.nb, self.F_c, stream)
         else:
@@ -164,11 +184,16 @@ class Simulator:
             acc.setdefault(name, []).append((a, b))
 
         if self.nb is not None and self.fused:
-            timed("gic_step", lambda: gic.gic_step(self.grid, self.params, self.A, self.B, self.perm, self.table,
-                                                   self.ws, self.nb, F.u, F.v, F.w, F.p, F.alpha_f,
+            if not self.lists_current:
+                gic.gic_neighbors_reset(self.nb, s)
+            timed("gic_step", lambda: gic.gic_step(self.grid, self.params, self.A, self.A2, self.B, self.perm,
+                                                   self.table, self.ws, self.nb, F.u, F.v, F.w, F.p, F.alpha_f,
                                                    self.alpha_s if alpha else None, self.Fs,
                                                    self.sums if alpha else None, s))
+            self.A, self.A2 = self.A2, self.A
+            self.lists_current = True
             return
+        self.lists_current = False
         timed("gic_sort", lambda: gic.gic_sort(self.grid, self.A, self.B, self.perm, self.table, self.ws, s))
         timed("gic_contact", lambda: self.contact(s))
         timed("gic_g2p_couple", lambda: gic.gic_g2p_couple(self.grid, self.params, self.B, F.u, F.v, F.w, F.p,
@@ -183,14 +208,15 @@ class Simulator:
         for f in self.Fs:
             f.zero_()
 
-    def run(self, K: int, stream=None, alpha_every: bool = False):
+    def run(self, K: int, stream=None, alpha_every: bool = False, sort_every: bool = False):
         """K substeps (one fluid step); F_s accumulates from zero over them
         (Alg. 2); alpha_s and sums are computed at the final positions only
-        (Alg. 1 CalTargetFraction), or after every substep if alpha_every."""
+        (Alg. 1 CalTargetFraction), or after every substep if alpha_every.
+        sort_every: as in substep()."""
         self.zero_transfer()
         for s in range(K):
             last = s == K - 1
-            self.substep(alpha=alpha_every or last, sums=alpha_every or last, stream=stream)
+            self.substep(alpha=alpha_every or last, sums=alpha_every or last, stream=stream, sort_every=sort_every)
 
     # ------------------------------------------------------------ outputs
     def positions(self, state: Optional[State] = None):
@@ -215,6 +241,8 @@ def _copy_state(dst: State, src: State):
     dst.vel.copy_(src.vel)
     if dst.id is not None and src.id is not None:
         dst.id.copy_(src.id)
+    if dst.posf is not None and src.posf is not None:  # a gic_step that keeps its lists reads it
+        dst.posf.copy_(src.posf)
 
 
 class GicWindow(torch.autograd.Function):
@@ -231,12 +259,12 @@ class GicWindow(torch.autograd.Function):
     gic_step (the sort only on list rebuilds).  The window opens with a list
     build, and every checkpoint also keeps the lists as they stand (a new
     copy only after a build), so the recomputation from it repeats the
-    forward pass exactly.  The recomputation keeps, per substep, the state
-    the substep acted on (sorted or in the previous order) and its
-    permutation, and notes which substeps rebuilt the lists; going back, the
+    forward pass exactly.  The recomputation keeps the state before every
+    substep and notes which substeps rebuilt the lists; going back, the
     lists each substep used are restored (from the checkpoint, or by sort +
-    build from the state of the substep that built them) and each substep's
-    adjoint is one gic_substep_adj.
+    build from the state of the substep that built them), and each
+    substep's adjoint is one gic_substep_adj: on the substep's state, or on
+    its sorted copy with the sort's permutation where the substep sorted.
 
     Otherwise forward and recomputation sort every substep, and each
     substep's adjoint re-sorts its state and runs gic_integrate_adj,
@@ -248,13 +276,14 @@ class GicWindow(torch.autograd.Function):
     def forward(ctx, v0, c_drag, mu, sim: "Simulator", init: State, K: int, ckpt: int):
         sim.params.c_drag = float(c_drag)
         sim.params.mu_fric = float(mu)
-        _copy_state(sim.A, init)
+        sim.load_state(init)
         vel = sim.A.vel
         vel[:, :3] = v0.detach().to(vel.dtype)  # init is in original order (id = 0..n-1)
         vel[:, 3] = 0
         stepped = sim.nb is not None and sim.fused
-        if stepped:  # the lists left by earlier calls do not enter the result
+        if stepped:  # the lists left by earlier calls do not enter the result: the first substep builds
             gic.gic_neighbors_reset(sim.nb)
+            sim.lists_current = True
         ckpts, lists = [], []
         for s in range(K):
             if s % ckpt == 0:
@@ -293,27 +322,27 @@ _NB_ARRAYS = ("list", "count", "ref_cell", "ref_pos", "slot")
 
 
 def _lists_snapshot(nb: gic.Neighbors, last: Optional[dict]) -> dict:
-    """The Verlet lists as they stand: the words and, unless a build is
-    pending, the rows and reference entries (`cur` and `at` follow from them
-    at the next check).  Returns `last` again when no build has run since it
-    was taken."""
+    """The Verlet lists as they stand: the flag words (among them the
+    decision for the next gic_step) and, unless a build is pending, the rows
+    and reference entries (`cur` and `at` follow from them at the next
+    check).  The arrays of `last` are shared when no build has run since."""
     flags = nb.flags.clone()
     f = flags.tolist()
     pending = bool(f[1])
-    if last is not None and not pending and not last["pending"] and last["builds"] == f[4]:
-        return last
-    snap = {"flags": flags, "builds": f[4], "pending": pending}
+    snap = {"flags": flags, "builds": f[4], "pending": pending, "arrays": None}
     if not pending:
-        for a in _NB_ARRAYS:
-            snap[a] = getattr(nb, a).clone()
+        if last is not None and last["arrays"] is not None and last["builds"] == f[4]:
+            snap["arrays"] = last["arrays"]
+        else:
+            snap["arrays"] = {a: getattr(nb, a).clone() for a in _NB_ARRAYS}
     return snap
 
 
 def _lists_restore(nb: gic.Neighbors, snap: dict):
     nb.flags.copy_(snap["flags"])
-    if not snap["pending"]:
-        for a in _NB_ARRAYS:
-            getattr(nb, a).copy_(snap[a])
+    if snap["arrays"] is not None:
+        for a, t in snap["arrays"].items():
+            getattr(nb, a).copy_(t)
 
 
 def _backward_stepped(ctx, g_pos, g_vel, g_scalars):
@@ -323,17 +352,24 @@ def _backward_stepped(ctx, g_pos, g_vel, g_scalars):
     g_vel_n = gic.vec4(n, prec, dev)
     log = torch.zeros(ctx.ckpt + 1, dtype=torch.int32, device=dev)
     ends, expected = [], []
+
+    def sort_and_build(st: State):
+        """st sorted into B (perm, cell table) and the lists built from B."""
+        gic.gic_sort(sim.grid, st, sim.B, sim.perm, sim.table, sim.ws)
+        gic.gic_neighbors_reset(nb)
+        gic.gic_contact_verlet(sim.grid, sim.params, sim.B, sim.table, nb, sim.F_c)
+
     for m, (s0, s1) in zip(reversed(range(len(ctx.ckpts))), _segments(ctx.K, ctx.ckpt)):
         L = s1 - s0
-        # recompute the segment, keeping every substep's (sorted) state and permutation
+        # recompute the segment from its checkpoint and lists, keeping the state before every substep
         _copy_state(sim.A, ctx.ckpts[m])
         _lists_restore(nb, ctx.lists[m])
+        sim.lists_current = True
         log[0:1].copy_(nb.flags[4:5])
-        states, perms = [], []
+        states = []
         for k in range(L):
+            states.append(sim.A.clone())
             sim.substep(alpha=False, transfer=False, sums=False)
-            states.append(sim.B.clone())
-            perms.append(sim.perm.clone())
             log[k + 1:k + 2].copy_(nb.flags[4:5])  # list builds so far
         counts = log[:L + 1].tolist()
         built = [counts[k + 1] != counts[k] for k in range(L)]
@@ -342,22 +378,30 @@ def _backward_stepped(ctx, g_pos, g_vel, g_scalars):
         lists_of, count_now = last_build[L - 1], counts[L]
         for k in reversed(range(L)):
             b = last_build[k]
-            if b != lists_of:
+            if b != lists_of and b != k:  # restore the lists substep k walked
                 if b < 0:
                     _lists_restore(nb, ctx.lists[m])
                     count_now = ctx.lists[m]["builds"]
-                else:  # the lists built from states[b]: sort it for its cell table, build
-                    gic.gic_sort(sim.grid, states[b], sim.B, sim.perm, sim.table, sim.ws)
-                    gic.gic_neighbors_reset(nb)
-                    gic.gic_contact_verlet(sim.grid, sim.params, sim.B, sim.table, nb, sim.F_c)
+                else:
+                    sort_and_build(states[b])
                     count_now = 1  # a reset clears the build count
                 lists_of = b
-            gic.gic_substep_adj(sim.grid, sim.params, states[k], perms[k], sim.table, nb, F.u, F.v, F.w, F.p,
-                                F.alpha_f, g_pos, g_vel, None, g_pos_n, g_vel_n, g_scalars[0:1], g_scalars[1:2])
+            if built[k]:  # substep k sorted its state and built the lists from it: the adjoint runs there
+                if lists_of != k:
+                    sort_and_build(states[k])
+                    lists_of, count_now = k, 1
+                else:
+                    gic.gic_sort(sim.grid, states[k], sim.B, sim.perm, sim.table, sim.ws)
+                acted, perm = sim.B, sim.perm
+            else:  # substep k ran on its state as it was, and its result kept the order
+                acted, perm = states[k], None
+            gic.gic_substep_adj(sim.grid, sim.params, acted, perm, sim.table, nb, F.u, F.v, F.w, F.p, F.alpha_f,
+                                g_pos, g_vel, None, g_pos_n, g_vel_n, g_scalars[0:1], g_scalars[1:2])
             g_pos, g_pos_n = g_pos_n, g_pos
             g_vel, g_vel_n = g_vel_n, g_vel
         ends.append(nb.flags[4:5].clone())
         expected.append(count_now)
+    sim.lists_current = False
     # every adjoint walked the lists its forward substep used: no build of its own
     got = torch.cat(ends).tolist()
     if got != expected:
