@@ -41,11 +41,13 @@
  *                    [0, h_c), 32-byte aligned
  *   vel   float[4 n] / double[4 n] = {vx, vy, vz, 0}
  *   id    int32[n] or NULL: original granule id, carried along by gic_sort
- *   posf  float[4 n] or NULL (FP32 path only): the positions again as float
- *         cell fractions {qx/2^30, qy/2^30, qz/2^30, r}.  Derived data: only
- *         gic_sort writes it (into out->posf) and the contact calls read it
- *         (from the sorted state) for their float pre-test; leave it NULL
- *         anywhere else.  16-byte aligned.
+ *   posf  float[4 n] or NULL (FP32 path only): the positions again as float,
+ *         in contact-cell units {cx + qx/2^30, cy + qy/2^30, cz + qz/2^30, r}.
+ *         Derived data: gic_sort writes it (into out->posf), gic_step and
+ *         gic_substep into the next state, and the contact calls read it for
+ *         their float pre-test (with a tolerance of 2^-11 cell; the exact
+ *         integer geometry decides); leave it NULL anywhere else.  16-byte
+ *         aligned.
  * Per-granule vectors (forces, accelerations, gradients) are real[4 n] with
  * the 4th lane unused (real = float for GIC_FP32, double for GIC_FP64).
  * Grid fields are real arrays on the MAC grid, x fastest:
@@ -115,7 +117,7 @@ typedef struct GicGranules {
   void* vel;
   int32_t* id;
   int32_t precision; /* GIC_FP32 or GIC_FP64 */
-  float* posf;       /* optional, GIC_FP32 only: float[4 n] {fx, fy, fz, r}, fx = qx / 2^30 (see below) */
+  float* posf;       /* optional, GIC_FP32 only: float[4 n] {fx, fy, fz, r}, fx = cx + qx / 2^30 (see above) */
 } GicGranules;
 
 /* ------------------------------------------------------------------ sizes */

@@ -203,14 +203,11 @@ __global__ void __launch_bounds__(kTileThreads) k_contact_tile(DGrid G, DParams<
           if (s_off[mid] <= t) lo = mid;
           else hi = mid - 1;
         }
-        // position in units of contact cells relative to the box corner: the three
-        // cells of an x-row are consecutive slots, and no cell offset is needed
+        // position in units of contact cells relative to the box corner (exact
+        // differences of the absolute copies): the three cells of an x-row are
+        // consecutive slots, and no cell offset is needed
         float4 p = __ldg(&posf[s_start[lo] + (t - s_off[lo])]);
-        int lz = (int)(((float)lo + 0.5f) * ibxy);
-        int rem = lo - lz * bx * by;
-        int ly = (int)(((float)rem + 0.5f) * ibx);
-        int lx = rem - ly * bx;
-        s_pf[t] = make_float4((float)lx + p.x, (float)ly + p.y, (float)lz + p.z, p.w);
+        s_pf[t] = make_float4(p.x - (float)bx0, p.y - (float)by0, p.z - (float)bz0, p.w);
       }
     }
     __syncthreads();
@@ -226,10 +223,8 @@ __global__ void __launch_bounds__(kTileThreads) k_contact_tile(DGrid G, DParams<
   if (s_mode == 0) {
     const int lx = cx - bx0, ly = cy - by0, lz = cz - bz0;
     const float4 fi0 = __ldg(&posf[i]);
-    const float xi = (float)lx + fi0.x, yi = (float)ly + fi0.y, zi = (float)lz + fi0.z;
-    const float rci = ri * G.inv_hc_f;
-    // box coordinates reach 2^6 cells: their float rounding (< 1e-5 cell) stays inside this margin
-    const float m2 = 1.0f + 1e-4f;
+    const float xi = fi0.x - (float)bx0, yi = fi0.y - (float)by0, zi = fi0.z - (float)bz0;
+    const float rci = fmaf(ri, G.inv_hc_f, kPosfTol);
     const int xa = max(lx - 1, 0), xb = min(lx + 1, bx - 1);
     // own slot (excluded): own cell's first slot + rank inside the cell
     const int bown = lx + bx * (ly + by * lz);
@@ -247,7 +242,7 @@ __global__ void __launch_bounds__(kTileThreads) k_contact_tile(DGrid G, DParams<
           float rx = fj.x - xi, ry = fj.y - yi, rz = fj.z - zi;
           float d2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
           float Rc = fmaf(fj.w, G.inv_hc_f, rci);
-          if (!(d2 < Rc * Rc * m2) || t == tself) continue;
+          if (!(d2 < Rc * Rc) || t == tself) continue;
           // contact candidate: locate j and its cell offset, then the exact geometry
           int bj = row + xa;
           while (s_off[bj + 1] <= t) ++bj;
@@ -420,8 +415,7 @@ __global__ void __launch_bounds__(256) k_verlet_check(DGrid G, int64_t n, const 
       cp.perm_out[i] = (int32_t)i;
       if constexpr (sizeof(T) == 4) {
         if (cp.posf_out)
-          cp.posf_out[i] = make_float4((float)p.x * 0x1p-30f, (float)p.y * 0x1p-30f, (float)p.z * 0x1p-30f,
-                                       __uint_as_float(p.w));
+          cp.posf_out[i] = posf_of(c, p);
       }
     }
   }

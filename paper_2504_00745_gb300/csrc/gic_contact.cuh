@@ -267,23 +267,21 @@ __device__ __forceinline__ void for_each_cell(const DGrid& G, const uint4* __res
 
 // FP32 candidate loop on the float copy of the positions: per candidate only
 // float adds / FMAs and one compare; the exact integer geometry runs for
-// candidates within 1e-5 of contact.  f(j, ox, oy, oz, geometry).
+// candidates within kPosfTol of contact.  f(j, ox, oy, oz, geometry).
 template <typename F>
 __device__ __forceinline__ void for_each_contact_f(const DGrid& G, const uint4* __restrict__ table, uint32_t epoch,
                                                    int64_t i, int cx, int cy, int cz, const float4& fi,
                                                    const uint4& pi, float ri, const float4* __restrict__ posf,
                                                    const uint4* __restrict__ pos, F&& f) {
-  const float rci = ri * G.inv_hc_f;
-  const float m2 = 1.0f + 1e-5f;
+  const float rci = fmaf(ri, G.inv_hc_f, kPosfTol);
   for_each_cell(G, table, epoch, cx, cy, cz, [&](uint32_t start, uint32_t cnt, int ox, int oy, int oz) {
-    float ax = (float)ox - fi.x, ay = (float)oy - fi.y, az = (float)oz - fi.z;
     for (uint32_t j = start; j < start + cnt; ++j) {
       if ((int64_t)j == i) continue;
       float4 fj = __ldg(&posf[j]);
-      float rx = ax + fj.x, ry = ay + fj.y, rz = az + fj.z;
+      float rx = fj.x - fi.x, ry = fj.y - fi.y, rz = fj.z - fi.z;
       float d2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
       float Rc = fmaf(fj.w, G.inv_hc_f, rci);
-      if (!(d2 < Rc * Rc * m2)) continue;
+      if (!(d2 < Rc * Rc)) continue;
       uint4 pj = __ldg(&pos[j]);
       int Dx, Dy, Dz;
       int_sep(pi, pj, ox, oy, oz, Dx, Dy, Dz);
@@ -402,14 +400,14 @@ __device__ __forceinline__ void verlet_pair(const DGrid& G, const uint4& pi, flo
   uint4 pj;
   float rj;
   float d2, Rs, Rc;
-  if (has_f) {  // float positions in contact cells
+  if (has_f) {  // float positions in contact-cell units
     rj = fj.w;
-    float rx = (float)ox + fj.x - fi.x, ry = (float)oy + fj.y - fi.y, rz = (float)oz + fj.z - fi.z;
+    float rx = fj.x - fi.x, ry = fj.y - fi.y, rz = fj.z - fi.z;
     d2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-    Rc = (ri + rj) * G.inv_hc_f;
-    Rs = (ri + rj + skin) * G.inv_hc_f;
-    near = d2 < Rs * Rs * (1.0f + 1e-4f);
-    touch = d2 < Rc * Rc * (1.0f + 1e-4f);
+    Rc = fmaf(ri + rj, G.inv_hc_f, kPosfTol);
+    Rs = fmaf(ri + rj + skin, G.inv_hc_f, kPosfTol);
+    near = d2 < Rs * Rs;
+    touch = d2 < Rc * Rc;
     if (!touch) return;
     pj = __ldg(&pos[j]);
   } else {  // the exact integer separation, float pre-test
@@ -611,13 +609,29 @@ __device__ __forceinline__ void for_each_list_contact(const DGrid& G, const NbDe
 #pragma unroll
     for (int u = 0; u < 4; ++u)
       jj[u] = k + u < cnt ? (int64_t)(nb.ident ? row[k + u] : nb.cur[row[k + u]]) : -1;
-    int32_t cj[4];
-    float4 fj[4];
+    if (has_f) {  // FP32: the float pre-test needs no partner cell; load it for the pairs that pass
+      float4 fj[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      cj[u] = jj[u] >= 0 ? __ldg(&cell[jj[u]]) : ci;
-      fj[u] = (has_f && jj[u] >= 0) ? __ldg(&posf[jj[u]]) : fi;
+      for (int u = 0; u < 4; ++u) fj[u] = jj[u] >= 0 ? __ldg(&posf[jj[u]]) : fi;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (jj[u] < 0) continue;
+        const float rx = fj[u].x - fi.x, ry = fj[u].y - fi.y, rz = fj[u].z - fi.z;
+        const float Rc = fmaf((float)ri + fj[u].w, G.inv_hc_f, kPosfTol);
+        if (!(fmaf(rx, rx, fmaf(ry, ry, rz * rz)) < Rc * Rc)) continue;
+        const int32_t cj = __ldg(&cell[jj[u]]);
+        const int ox = cell_x(cj) - cx, oy = cell_y(cj) - cy, oz = cell_z(cj) - cz;
+        if (ox < -1 || ox > 1 || oy < -1 || oy > 1 || oz < -1 || oz > 1) continue;
+        bool near, touch;
+        PairGeom<T> g;
+        verlet_pair(G, pi, ri, true, fi, fj[u], pos, jj[u], ox, oy, oz, T(0), near, touch, g);
+        if (touch) f(jj[u], g);
+      }
+      continue;
     }
+    int32_t cj[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) cj[u] = jj[u] >= 0 ? __ldg(&cell[jj[u]]) : ci;
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       if (jj[u] < 0) continue;
@@ -626,7 +640,7 @@ __device__ __forceinline__ void for_each_list_contact(const DGrid& G, const NbDe
       if (ox < -1 || ox > 1 || oy < -1 || oy > 1 || oz < -1 || oz > 1) continue;
       bool near, touch;
       PairGeom<T> g;
-      verlet_pair(G, pi, ri, has_f, fi, fj[u], pos, jj[u], ox, oy, oz, T(0), near, touch, g);
+      verlet_pair(G, pi, ri, false, fi, fi, pos, jj[u], ox, oy, oz, T(0), near, touch, g);
       if (touch) f(jj[u], g);
     }
   }

@@ -88,6 +88,18 @@ __device__ __forceinline__ int cell_z(int32_t c) { return (c >> (2 * kCellBits))
 __device__ __forceinline__ int32_t pack_cell(int x, int y, int z) {
   return x | (y << kCellBits) | (z << (2 * kCellBits));
 }
+
+// The float position copy of an FP32 granule (posf): its position in
+// contact-cell units, c + q / 2^30 per axis, and its radius (metres).  The
+// coordinates are below 1024, so each is off by at most 2^-14 cell and a
+// distance between two copies by less than 2.2e-4 cell: the float pre-tests
+// widen the contact radius by kPosfTol cell and leave the decision to the
+// exact integer geometry.
+constexpr float kPosfTol = 1.0f / 2048.0f;
+__device__ __forceinline__ float4 posf_of(int32_t c, const uint4& p) {
+  return make_float4((float)cell_x(c) + (float)p.x * 0x1p-30f, (float)cell_y(c) + (float)p.y * 0x1p-30f,
+                     (float)cell_z(c) + (float)p.z * 0x1p-30f, __uint_as_float(p.w));
+}
 __device__ __forceinline__ int64_t table_index(const DGrid& G, int x, int y, int z) {
   return 1 + x + (int64_t)G.nc[0] * (y + (int64_t)G.nc[1] * z);
 }

@@ -264,8 +264,7 @@ __global__ void __launch_bounds__(256) k_permute_table(DGrid G, int64_t n, const
   if (S.out_id) S.out_id[k] = S.in_id ? S.in_id[src] : src;
   if constexpr (sizeof(T) == 4) {
     if (S.out_posf)
-      S.out_posf[k] = make_float4((float)p.x * 0x1p-30f, (float)p.y * 0x1p-30f, (float)p.z * 0x1p-30f,
-                                  __uint_as_float(p.w));
+      S.out_posf[k] = posf_of(c, p);
   }
   uint32_t key = keys[k];
   if (k > 0 && keys[k - 1] == key) return;

@@ -76,8 +76,7 @@ __global__ void __launch_bounds__(kSubstepThreads, sizeof(T) == 4 ? 4 : 2) k_sub
     if (id_out && id) id_out[i] = id[i];
     if constexpr (sizeof(T) == 4) {
       if (posf_out)
-        posf_out[i] = make_float4((float)po.x * 0x1p-30f, (float)po.y * 0x1p-30f, (float)po.z * 0x1p-30f,
-                                  __uint_as_float(po.w));
+        posf_out[i] = posf_of(co, po);
     }
     if (fex_out) fex_out[i] = make_vec<T>(fe[0], fe[1], fe[2]);
     // the next call's displacement test, on the positions just written
