@@ -216,8 +216,9 @@ __device__ __forceinline__ void alpha_deposits(const DGrid& G, int32_t cn, uint4
   v[7] = (long long)S - sum7;
 }
 
-// FP32 path of P2G.  One CTA takes 512 consecutive granules of the
-// Morton-sorted state, which occupy a compact block of MAC cells.  When the
+// FP32 path of P2G.  One CTA takes its consecutive granules (512 in the P2G
+// kernel, 256 in the fused substep) of the Morton-sorted state, which occupy
+// a compact block of MAC cells.  When the
 // samples they may touch fit a kP2GTile-entry box, every deposit goes to
 // shared-memory copies of alpha_s and the three F_s grids over that box,
 // held as 32-bit integer limbs (32-bit shared integer atomics run at full
@@ -226,10 +227,12 @@ __device__ __forceinline__ void alpha_deposits(const DGrid& G, int32_t cn, uint4
 // every deposit is a global atomic.
 //   alpha_s: a deposit (< 2^54 units of 2^-53) is split into three 18-bit
 //   limbs, so up to 2^14 deposits per entry add without overflow -- exact.
-//   F_s: a deposit d is rounded to a multiple of u = M 2^-30, M the CTA's
-//   largest |exch f_ex| component, and q = d / u (|q| <= 2^30) is split into
-//   a signed high and an unsigned low 15-bit limb; the limb sums are exact,
-//   so the only rounding besides the float product d is the 2^-30 M grid.
+//   F_s: a deposit d is rounded to a multiple of u = M 2^-b, M the CTA's
+//   largest |exch f_ex| component and b = 30 - ceil(log2(CTA threads)), so
+//   |q| = |d / u| <= 2^b and the at most one deposit per granule and entry
+//   sum to |sum q| <= 2^30 in one 32-bit integer: exact, and the only
+//   rounding besides the float product d is the grid u (2^-22 M for 256
+//   threads, finer than the float sum it replaces).
 // alpha_s stays 64-bit fixed point (exact, order-independent) until
 // k_alpha_finish_f32.
 constexpr int kP2GTile = 1024;
@@ -237,8 +240,7 @@ constexpr int kP2GTile = 1024;
 // Shared-memory copies of alpha_s and the three F_s grids over one CTA's box.
 struct P2GShared {
   uint32_t a[3][kP2GTile];
-  int32_t fh[3][kP2GTile];
-  uint32_t fl[3][kP2GTile];
+  int32_t f[3][kP2GTile];
   int lo[3], hi[3];
   unsigned M;
 };
@@ -267,7 +269,7 @@ struct P2GBox {
   bool tile, ftile;     // deposits go to the shared box (alpha_s; F_s)
   bool do_a, do_f;      // alpha_s / F_s requested
   int b[3], ex, sy, sz, vol;
-  float unit, inv_unit;  // F_s fixed-point unit M 2^-30 and its inverse
+  float unit, inv_unit;  // F_s fixed-point unit M 2^-b and its inverse
 };
 
 __device__ __forceinline__ void p2g_box_init(P2GShared& sh) {
@@ -307,8 +309,9 @@ __device__ __forceinline__ P2GBox p2g_box(P2GShared& sh, const P2GExtent& ext, b
   B.tile = ex > 0 && ey > 0 && ez > 0 && (int64_t)ex * ey * ez <= kP2GTile;
   const float Mc = __uint_as_float(sh.M);
   B.ftile = B.tile && do_f && Mc >= 1e-30f && Mc <= 3.0e38f;
-  B.unit = Mc * 0x1p-30f;
-  B.inv_unit = B.ftile ? 0x1p30f / Mc : 0.f;
+  const int bits = 30 - (32 - __clz((int)blockDim.x - 1));  // 22 for 256 threads, 21 for 512
+  B.unit = ldexpf(Mc, -bits);
+  B.inv_unit = B.ftile ? ldexpf(1.0f, bits) / Mc : 0.f;
   B.vol = B.tile ? ex * ey * ez : 0;
   B.ex = ex;
   B.sy = ex;
@@ -317,10 +320,7 @@ __device__ __forceinline__ P2GBox p2g_box(P2GShared& sh, const P2GExtent& ext, b
     if (do_a) sh.a[0][e] = sh.a[1][e] = sh.a[2][e] = 0u;
     if (B.ftile) {
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        sh.fh[c][e] = 0;
-        sh.fl[c][e] = 0u;
-      }
+      for (int c = 0; c < 3; ++c) sh.f[c][e] = 0;
     }
   }
   if (B.tile) __syncthreads();
@@ -361,8 +361,7 @@ __device__ __forceinline__ void p2g_add_face(P2GShared& sh, const P2GBox& B, con
     for (int k = 0; k < 8; ++k) {
       const int q = __float2int_rn(((k & 1) ? fx1 : fx0) * wyz[k >> 1] * B.inv_unit);
       const int e = e0 + (k & 1) + ((k >> 1) & 1) * B.sy + (k >> 2) * B.sz;
-      atomicAdd(&sh.fh[comp][e], q >> 15);
-      atomicAdd(&sh.fl[comp][e], (uint32_t)(q & 0x7fff));
+      atomicAdd(&sh.f[comp][e], q);
     }
   } else {
     const int nsx = G.nx + (comp == 0), nsy = G.ny + (comp == 1);
@@ -398,7 +397,7 @@ __device__ __forceinline__ void p2g_flush(P2GShared& sh, const P2GBox& B, const 
     if (B.ftile) {
 #pragma unroll
       for (int comp = 0; comp < 3; ++comp) {
-        long long q = (long long)sh.fh[comp][e] * (1ll << 15) + (long long)sh.fl[comp][e];
+        const int q = sh.f[comp][e];
         if (q) atomicAdd(&Fs[comp][sample_index(G.nx + (comp == 0), G.ny + (comp == 1), gx, gy, gz)],
                          (float)q * B.unit);
       }

@@ -100,3 +100,10 @@ def onset_taint(prob, K, eps=2e-10):
         out = oracle.run(prob, K=1, x=x, v=v)
         x, v = out["x"], out["v"]
     return out, taint
+
+
+# The FP32 path's F_s: each deposit is rounded to 2^-22 (2^-21 in the
+# 512-thread P2G kernel) of the largest |exch f_ex| in its CTA, which may be
+# several times the largest F_s entry where granules are sparse; bound
+# relative to max |F_s|.
+FS_TOL_FP32 = 1e-5

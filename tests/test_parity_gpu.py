@@ -16,7 +16,8 @@ import torch
 
 import gic_inputs as gi
 import oracle
-from gpu_util import FP32, FP64, by_id, onset_taint, oracle_inputs, shuffled, sim_for, subset, tol_force
+from gpu_util import (FP32, FP64, FS_TOL_FP32, by_id, onset_taint, oracle_inputs, shuffled, sim_for, subset,
+                      tol_force)
 from paper_2504_00745_gb300 import gic
 from paper_2504_00745_gb300.window import Simulator
 
@@ -230,7 +231,7 @@ def test_p2g_parity(name, prec):
     sums = sim.sums.cpu().numpy()
     assert abs(sums[1] - sums_o[1]) <= 1e-12 * sums_o[1]  # n-term FP64 sums in different orders
     assert abs(sums[0] - sums[1]) <= 1e-12 * sums[1]
-    ftol = 2e-6 if prec == FP32 else 1e-12
+    ftol = FS_TOL_FP32 if prec == FP32 else 1e-12
     for c in range(3):
         fg = sim.Fs[c].cpu().numpy()
         assert np.abs(fg - Fs_o[c]).max() <= ftol * np.abs(Fs_o[c]).max(), (c, np.abs(fg - Fs_o[c]).max(),
@@ -396,7 +397,7 @@ def test_dam_break_full_size_one_substep():
     a_o, Fs_o, sums_o = oracle.p2g(prob.grid, prob.params, xb.cpu().numpy(), xa.cpu().numpy(), r, fex)
     assert np.abs(sim.alpha_s.cpu().numpy() - a_o).max() <= 1e-9
     for c in range(3):
-        assert np.abs(sim.Fs[c].cpu().numpy() - Fs_o[c]).max() <= 2e-6 * np.abs(Fs_o[c]).max()
+        assert np.abs(sim.Fs[c].cpu().numpy() - Fs_o[c]).max() <= FS_TOL_FP32 * np.abs(Fs_o[c]).max()
     assert gic.gic_check_status() == 0
 
 
@@ -515,7 +516,7 @@ def test_full_size_sampled_one_substep(name, prec):
         faces = interior(*dims[c], off)
         got = sim.Fs[c].cpu().numpy()[faces]
         want = Fs_o[c][faces]
-        assert np.abs(got - want).max() <= (2e-6 if prec == FP32 else 1e-12) * np.abs(want).max()
+        assert np.abs(got - want).max() <= (FS_TOL_FP32 if prec == FP32 else 1e-12) * np.abs(want).max()
     assert gic.gic_check_status() == 0
 
 
