@@ -40,21 +40,22 @@ __device__ __forceinline__ GradPLoad<T> gradp_loader(const DGrid& G, const T* p,
 
 // G2P coupling of one granule at (cell, p) with velocity v (Sec. 3.3 Eqs. 5a,
 // 5b; Sec. 5.2 Eq. momentum4): F_fl = c_drag pi r^2 rho_f |u_f - v| (u_f - v)
-// - V grad p and a_f = g - grad p / rho_f.  Returns |u_f - v|.
-template <typename T>
-__device__ __forceinline__ T g2p_granule(const DGrid& G, const DParams<T>& P, const Fields<T>& Fd, int32_t cell,
-                                         const pos_t<T>& pi, const vec_t<T>& vi, T F[3], T a[3]) {
+// - V grad p and a_f = g - grad p / rho_f.  Returns |u_f - v|.  face(comp)
+// and gradp(comp) give the samplers of the face velocities and of the face
+// pressure gradients (global memory or a staged tile: the same values).
+template <typename T, typename Face, typename GradP>
+__device__ __forceinline__ T g2p_granule_with(const DGrid& G, const DParams<T>& P, int32_t cell, const pos_t<T>& pi,
+                                              const vec_t<T>& vi, Face face, GradP gradp, T F[3], T a[3]) {
   int m[3];
   T t[3];
   granule_mac<T>(G, cell, pi, m, t);
-  const T* uvw[3] = {Fd.u, Fd.v, Fd.w};
   T uf[3], gp[3];
   T inv_dx = (T)G.inv_dx;
 #pragma unroll
   for (int comp = 0; comp < 3; ++comp) {
     Stencil3<T> S = make_stencil<T>(G, m, t, comp);
-    uf[comp] = interp<T>(S, face_loader<T>(G, uvw[comp], comp), inv_dx, nullptr);
-    gp[comp] = interp<T>(S, gradp_loader<T>(G, Fd.p, comp), inv_dx, nullptr);
+    uf[comp] = interp<T>(S, face(comp), inv_dx, nullptr);
+    gp[comp] = interp<T>(S, gradp(comp), inv_dx, nullptr);
   }
   T r = radius_of(pi);
   T V = T(4.0 / 3.0 * kPi) * r * r * r;
@@ -74,6 +75,15 @@ __device__ __forceinline__ T g2p_granule(const DGrid& G, const DParams<T>& P, co
     a[2] = P.g[2];
   }
   return sp;
+}
+
+template <typename T>
+__device__ __forceinline__ T g2p_granule(const DGrid& G, const DParams<T>& P, const Fields<T>& Fd, int32_t cell,
+                                         const pos_t<T>& pi, const vec_t<T>& vi, T F[3], T a[3]) {
+  const T* uvw[3] = {Fd.u, Fd.v, Fd.w};
+  return g2p_granule_with<T>(
+      G, P, cell, pi, vi, [&](int comp) { return face_loader<T>(G, uvw[comp], comp); },
+      [&](int comp) { return gradp_loader<T>(G, Fd.p, comp); }, F, a);
 }
 
 // Adjoint of g2p_granule for upstream gradients l (of F_fl) and la (of
@@ -412,6 +422,214 @@ __device__ __forceinline__ void p2g_sums(double* sums, long long v) {
   if (lane_id() == 0 && v != 0) {
     atomicAdd((unsigned long long*)&sums[0], (unsigned long long)v);
     atomicAdd((unsigned long long*)&sums[1], (unsigned long long)v);
+  }
+}
+
+// ---- FP32 fused substep: one CTA tile for G2P staging and P2G ----
+//
+// The CTA's granules (consecutive in Morton order) have MAC cells m; every
+// sample their G2P and F_s stencils touch has indices m - 1 .. m + 1 per
+// axis.  At the start of the substep the CTA reduces that box, stages the
+// face velocities and the face pressure gradients of its samples in shared
+// memory (each computed as the global-memory samplers compute it, so G2P
+// gives the same bits) and zeroes its F_s (and alpha_s) accumulators; F_s is
+// then scattered into the same box (fixed point as in the P2G kernel), and
+// alpha_s, at the new positions, into it where the stencil fits.  A box
+// beyond kSubTile entries falls back to global memory.
+constexpr int kSubTile = 960;  // 46 KB of static shared memory
+constexpr int kSubWarps = 8;  // CTA of 256 threads
+
+struct SubTile {
+  float u[kSubTile], v[kSubTile], w[kSubTile];
+  float gp[3][kSubTile];
+  int32_t f[3][kSubTile];
+  uint32_t a[3][kSubTile];
+  int wlo[3][kSubWarps], whi[3][kSubWarps];
+  unsigned wM[kSubWarps];
+};
+
+struct SubBox {
+  bool tile;
+  int b[3], ex, ey, ez, sy, sz, vol;
+  __device__ __forceinline__ int index(int i, int j, int k) const {
+    return (i - b[0]) + sy * (j - b[1]) + sz * (k - b[2]);
+  }
+  __device__ __forceinline__ bool holds(int i, int j, int k) const {  // the 2x2x2 stencil based at (i, j, k)
+    return i >= b[0] && j >= b[1] && k >= b[2] && i + 1 < b[0] + ex && j + 1 < b[1] + ey && k + 1 < b[2] + ez;
+  }
+};
+
+// Sampler of a staged field: the same values as the global sampler.
+struct TileLoad {
+  const float* s;
+  SubBox B;
+  __device__ __forceinline__ float operator()(int i, int j, int k) const { return s[B.index(i, j, k)]; }
+};
+
+// CTA-wide (every thread calls it): the box of the granules' MAC cells, the
+// staged fields and the zeroed accumulators.  valid: this thread has a
+// granule in contact cell c.
+__device__ __forceinline__ SubBox sub_tile_begin(SubTile& sh, const DGrid& G, const Fields<float>& Fd, bool valid,
+                                                 int32_t c, bool do_a, bool do_f) {
+  const int warp = threadIdx.x >> 5;
+  const int c3[3] = {cell_x(c), cell_y(c), cell_z(c)};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int m = valid ? mac_of(G, c3[a]) : 0;
+    const int l = __reduce_min_sync(0xffffffffu, valid ? m : INT_MAX);
+    const int h = __reduce_max_sync(0xffffffffu, valid ? m : INT_MIN);
+    if (lane_id() == 0) {
+      sh.wlo[a][warp] = l;
+      sh.whi[a][warp] = h;
+    }
+  }
+  __syncthreads();
+  int lo[3], hi[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    lo[a] = INT_MAX;
+    hi[a] = INT_MIN;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      lo[a] = min(lo[a], sh.wlo[a][w]);
+      hi[a] = max(hi[a], sh.whi[a][w]);
+    }
+  }
+  SubBox B;
+  const bool any = lo[0] <= hi[0];  // a CTA without granules has lo > hi
+  B.b[0] = any ? max(lo[0] - 1, 0) : 0;
+  B.b[1] = any ? max(lo[1] - 1, 0) : 0;
+  B.b[2] = any ? max(lo[2] - 1, 0) : 0;
+  B.ex = any ? hi[0] + 1 - B.b[0] + 1 : 1;
+  B.ey = any ? hi[1] + 1 - B.b[1] + 1 : 1;
+  B.ez = any ? hi[2] + 1 - B.b[2] + 1 : 1;
+  B.tile = any && (int64_t)B.ex * B.ey * B.ez <= kSubTile;
+  B.sy = B.ex;
+  B.sz = B.ex * B.ey;
+  B.vol = B.tile ? B.ex * B.ey * B.ez : 0;
+  const float rx = 1.f / (float)B.ex, rxy = 1.f / (float)max(B.sz, 1);
+  for (int e = threadIdx.x; e < B.vol; e += blockDim.x) {
+    // e = lx + ex (ly + ey lz); (e + 1/2) / d stays >= 1/(2 d) from an integer
+    const int lz = (int)(((float)e + 0.5f) * rxy);
+    const int r = e - lz * B.sz;
+    const int ly = (int)(((float)r + 0.5f) * rx);
+    const int lx = r - ly * B.ex;
+    const int i = B.b[0] + lx, j = B.b[1] + ly, k = B.b[2] + lz;
+    const bool cx = i < G.nx, cy = j < G.ny, cz = k < G.nz;  // a cell-centred index
+    const bool fx = i <= G.nx, fy = j <= G.ny, fz = k <= G.nz;  // a face index
+    sh.u[e] = (fx && cy && cz) ? face_loader<float>(G, Fd.u, 0)(i, j, k) : 0.f;
+    sh.v[e] = (cx && fy && cz) ? face_loader<float>(G, Fd.v, 1)(i, j, k) : 0.f;
+    sh.w[e] = (cx && cy && fz) ? face_loader<float>(G, Fd.w, 2)(i, j, k) : 0.f;
+    sh.gp[0][e] = (fx && cy && cz) ? gradp_loader<float>(G, Fd.p, 0)(i, j, k) : 0.f;
+    sh.gp[1][e] = (cx && fy && cz) ? gradp_loader<float>(G, Fd.p, 1)(i, j, k) : 0.f;
+    sh.gp[2][e] = (cx && cy && fz) ? gradp_loader<float>(G, Fd.p, 2)(i, j, k) : 0.f;
+    if (do_f) sh.f[0][e] = sh.f[1][e] = sh.f[2][e] = 0;
+    if (do_a) sh.a[0][e] = sh.a[1][e] = sh.a[2][e] = 0u;
+  }
+  __syncthreads();
+  return B;
+}
+
+// G2P of one granule from the staged tile (B.tile) or global memory.
+__device__ __forceinline__ float sub_g2p(const SubTile& sh, const SubBox& B, const DGrid& G, const DParams<float>& P,
+                                         const Fields<float>& Fd, int32_t c, const uint4& pi, const float4& vi,
+                                         float F[3], float a[3]) {
+  if (!B.tile) return g2p_granule<float>(G, P, Fd, c, pi, vi, F, a);
+  const float* uvw[3] = {sh.u, sh.v, sh.w};
+  return g2p_granule_with<float>(
+      G, P, c, pi, vi, [&](int comp) { return TileLoad{uvw[comp], B}; },
+      [&](int comp) { return TileLoad{sh.gp[comp], B}; }, F, a);
+}
+
+// CTA-wide: the F_s fixed-point unit from the largest |exch f_ex| component
+// of the CTA (M); returns 2^b / M (0 if F_s cannot use the tile).
+__device__ __forceinline__ float sub_fs_scale(SubTile& sh, const SubBox& B, float Mthread, float& unit) {
+  const int warp = threadIdx.x >> 5;
+  const unsigned mb = __reduce_max_sync(0xffffffffu, __float_as_uint(Mthread));  // non-negative floats
+  if (lane_id() == 0) sh.wM[warp] = mb;
+  __syncthreads();
+  unsigned M = 0u;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) M = max(M, sh.wM[w]);
+  const float Mc = __uint_as_float(M);
+  const int bits = 30 - (32 - __clz((int)blockDim.x - 1));  // 22 for 256 threads
+  const bool ok = B.tile && Mc >= 1e-30f && Mc <= 3.0e38f;
+  unit = ldexpf(Mc, -bits);
+  return ok ? ldexpf(1.0f, bits) / Mc : 0.f;
+}
+
+// F_s deposit of one granule on face grid comp (its stencil lies in the box
+// whenever the tile is used; inv_unit = 0: global atomics).
+__device__ __forceinline__ void sub_add_face(SubTile& sh, const SubBox& B, const DGrid& G, float* Fs, int comp,
+                                             const Stencil3<float>& St, float fc, float inv_unit) {
+  const float wx = St.w[0], wy = St.w[1], wz = St.w[2];
+  const float fx0 = (1.f - wx) * fc, fx1 = wx * fc;
+  const float wyz[4] = {(1.f - wy) * (1.f - wz), wy * (1.f - wz), (1.f - wy) * wz, wy * wz};
+  if (inv_unit != 0.f) {
+    const int e0 = B.index(St.i0[0], St.i0[1], St.i0[2]);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int q = __float2int_rn(((k & 1) ? fx1 : fx0) * wyz[k >> 1] * inv_unit);
+      atomicAdd(&sh.f[comp][e0 + (k & 1) + ((k >> 1) & 1) * B.sy + (k >> 2) * B.sz], q);
+    }
+  } else {
+    const int nsx = G.nx + (comp == 0), nsy = G.ny + (comp == 1);
+    float* g0 = Fs + sample_index(nsx, nsy, St.i0[0], St.i0[1], St.i0[2]);
+    const int64_t gy = nsx, gz = (int64_t)nsx * nsy;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const float d = ((k & 1) ? fx1 : fx0) * wyz[k >> 1];
+      if (d != 0.f) atomicAdd(g0 + (k & 1) + ((k >> 1) & 1) * gy + (k >> 2) * gz, d);
+    }
+  }
+}
+
+// alpha_s deposits of one granule at its new position: into the tile when
+// its stencil lies in the box, else straight to global memory (both exact).
+__device__ __forceinline__ void sub_add_alpha(SubTile& sh, const SubBox& B, const DGrid& G, unsigned long long* acc,
+                                              const int ia[3], const long long va[8]) {
+  if (B.tile && B.holds(ia[0], ia[1], ia[2])) {
+    const int e0 = B.index(ia[0], ia[1], ia[2]);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int e = e0 + (k & 1) + ((k >> 1) & 1) * B.sy + (k >> 2) * B.sz;
+      const unsigned long long v = (unsigned long long)va[k];
+      atomicAdd(&sh.a[0][e], (uint32_t)(v & 0x3ffffull));
+      atomicAdd(&sh.a[1][e], (uint32_t)((v >> 18) & 0x3ffffull));
+      atomicAdd(&sh.a[2][e], (uint32_t)(v >> 36));
+    }
+  } else {
+    unsigned long long* g0 = acc + sample_index(G.nx, G.ny, ia[0], ia[1], ia[2]);
+    const int64_t gy = G.nx, gz = (int64_t)G.nx * G.ny;
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if (va[k]) atomicAdd(g0 + (k & 1) + ((k >> 1) & 1) * gy + (k >> 2) * gz, (unsigned long long)va[k]);
+  }
+}
+
+// CTA-wide: the tile's non-zero entries to global memory (one atomic each).
+__device__ __forceinline__ void sub_tile_flush(SubTile& sh, const SubBox& B, const DGrid& G, unsigned long long* acc,
+                                               float* const Fs[3], bool do_a, bool fs_tile, float unit) {
+  if (!B.tile || (!do_a && !fs_tile)) return;
+  __syncthreads();
+  const float rx = 1.f / (float)B.ex, rxy = 1.f / (float)B.sz;
+  for (int e = threadIdx.x; e < B.vol; e += blockDim.x) {
+    const int lz = (int)(((float)e + 0.5f) * rxy);
+    const int r = e - lz * B.sz;
+    const int ly = (int)(((float)r + 0.5f) * rx);
+    const int lx = r - ly * B.ex;
+    const int gx = B.b[0] + lx, gy = B.b[1] + ly, gz = B.b[2] + lz;
+    if (do_a) {  // non-zero only at samples of alpha_s
+      const unsigned long long a = (unsigned long long)sh.a[0][e] + ((unsigned long long)sh.a[1][e] << 18) +
+                                   ((unsigned long long)sh.a[2][e] << 36);
+      if (a) atomicAdd(&acc[sample_index(G.nx, G.ny, gx, gy, gz)], a);
+    }
+    if (fs_tile) {
+#pragma unroll
+      for (int comp = 0; comp < 3; ++comp) {  // non-zero only at samples of that face grid
+        const int q = sh.f[comp][e];
+        if (q) atomicAdd(&Fs[comp][sample_index(G.nx + (comp == 0), G.ny + (comp == 1), gx, gy, gz)],
+                         (float)q * unit);
+      }
+    }
   }
 }
 

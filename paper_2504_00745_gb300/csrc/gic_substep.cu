@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <mutex>
+#include <type_traits>
 
 #include "gic_contact.cuh"
 #include "gic_grid.cuh"
@@ -25,19 +26,21 @@ __global__ void __launch_bounds__(kSubstepThreads, sizeof(T) == 4 ? 4 : 2) k_sub
     vec_t<T>* __restrict__ vel_out, int32_t* __restrict__ id_out, float4* __restrict__ posf_out,
     vec_t<T>* __restrict__ fex_out, double* __restrict__ alpha, T* __restrict__ Fs_u, T* __restrict__ Fs_v,
     T* __restrict__ Fs_w, double* __restrict__ sums, uint32_t* status) {
-  __shared__ P2GShared sh;  // FP32 path only
+  __shared__ std::conditional_t<sizeof(T) == 4, SubTile, int> sh;  // FP32 path only
   const bool rebuild = (nb.flags[kNbRebuild] | nb.flags[kNbSticky]) != 0u;  // uniform over the launch
   const bool do_a = alpha != nullptr, do_f = Fs_u != nullptr;
   const int64_t i = blockIdx.x * (int64_t)kSubstepThreads + threadIdx.x;
   const bool valid = i < n;
-  if constexpr (sizeof(T) == 4) p2g_box_init(sh);
+  const int32_t ci = valid ? cell[i] : 0;
+  // FP32: the CTA's tile (fields staged for G2P, F_s / alpha_s accumulators)
+  SubBox B{};
+  if constexpr (sizeof(T) == 4) B = sub_tile_begin(sh, G, Fd, valid, ci, do_a, do_f);
 
-  int32_t ci = 0, co = 0;
+  int32_t co = 0;
   pos_t<T> pi{}, po{};
   T fe[3] = {T(0), T(0), T(0)};
   bool far = false;
   if (valid) {
-    ci = cell[i];
     pi = pos[i];
     const vec_t<T> vi = vel[i];
     const T ri = radius_of(pi);
@@ -63,7 +66,11 @@ __global__ void __launch_bounds__(kSubstepThreads, sizeof(T) == 4 ? 4 : 2) k_sub
     }
     // a3: G2P coupling
     T Ffl[3], af[3];
-    const T sp = g2p_granule(G, P, Fd, ci, pi, vi, Ffl, af);
+    T sp;
+    if constexpr (sizeof(T) == 4)
+      sp = sub_g2p(sh, B, G, P, Fd, ci, pi, vi, Ffl, af);
+    else
+      sp = g2p_granule(G, P, Fd, ci, pi, vi, Ffl, af);
     if (!isfinite(sp)) flags |= GIC_STATUS_NONFINITE;
     // a4: integrate into the next state
     vec_t<T> vo;
@@ -93,23 +100,23 @@ __global__ void __launch_bounds__(kSubstepThreads, sizeof(T) == 4 ? 4 : 2) k_sub
 
   // a5: P2G
   if constexpr (sizeof(T) == 4) {
-    P2GExtent ext;
-    float fc[3] = {P.exch * fe[0], P.exch * fe[1], P.exch * fe[2]};
-    if (valid) {
-      if (do_a) ext.add_cell(G, co);
-      if (do_f) {
-        ext.add_cell(G, ci);
-        ext.add_force(fc);
+    const float fc[3] = {P.exch * fe[0], P.exch * fe[1], P.exch * fe[2]};
+    float unit = 0.f, inv_unit = 0.f;
+    if (do_f) {  // the CTA's fixed-point unit
+      float Mt = 0.f;
+      if (valid) {
+        const float m = fmaxf(fabsf(fc[0]), fmaxf(fabsf(fc[1]), fabsf(fc[2])));
+        Mt = m <= 3.0e38f ? m : INFINITY;  // NaN or inf: no fixed point for this CTA
       }
+      inv_unit = sub_fs_scale(sh, B, Mt, unit);
     }
-    const P2GBox B = p2g_box(sh, ext, do_a, do_f);
     float* Fs[3] = {Fs_u, Fs_v, Fs_w};
     unsigned long long S = 0;
     if (valid && do_a) {
       int ia[3];
       long long va[8];
       alpha_deposits(G, co, po, ia, va, S);
-      p2g_add_alpha(sh, B, G, (unsigned long long*)alpha, ia, va);
+      sub_add_alpha(sh, B, G, (unsigned long long*)alpha, ia, va);
     }
     if (valid && do_f) {
       int m[3];
@@ -117,9 +124,9 @@ __global__ void __launch_bounds__(kSubstepThreads, sizeof(T) == 4 ? 4 : 2) k_sub
       granule_mac<float>(G, ci, pi, m, t);
 #pragma unroll
       for (int comp = 0; comp < 3; ++comp)
-        p2g_add_face(sh, B, G, Fs[comp], comp, make_stencil<float>(G, m, t, comp), fc[comp]);
+        sub_add_face(sh, B, G, Fs[comp], comp, make_stencil<float>(G, m, t, comp), fc[comp], inv_unit);
     }
-    p2g_flush(sh, B, G, (unsigned long long*)alpha, Fs, kSubstepThreads);
+    sub_tile_flush(sh, B, G, (unsigned long long*)alpha, Fs, do_a, inv_unit != 0.f, unit);
     if (sums) p2g_sums(sums, (long long)S);
   } else {
     // FP64: straight double atomics (alpha_s from V / dx^3 and the tent
