@@ -36,10 +36,10 @@ ALGO_BYTES = {"gic_sort": 88, "gic_contact": 48, "gic_g2p_couple": 65, "gic_inte
               "gic_substep": 72, "gic_step": 72}
 P2G_ALPHA_BYTES = 20
 # DRAM bytes (read + write) of one call of the dominant entry point on a
-# substep that keeps its lists (gic_step: k_verlet_check + k_substep), from
-# an ncu capture of the current kernels on the same workload (ncu flushes
-# the caches before each launch)
-NCU_TRAFFIC = {}
+# substep that keeps its Verlet lists (the gic_step graph: the decision
+# kernel + k_substep), from an ncu capture of the current kernels on the same
+# workload, the graph profiled as one unit (ncu flushes the caches first)
+NCU_TRAFFIC = {("dam_break_1m", "gic_step"): 197.0e6}
 
 
 def algo_bytes(name, K):
@@ -337,8 +337,9 @@ def run_gpu(args, ws, rank, local):
             "vs_baseline": None, "dtype": "f32 (fixed-point positions, f64 alpha_s)", "data": "synthetic",
             "config": {"workload": prob.name, "granules": n, "grid": [prob.grid.nx, prob.grid.ny, prob.grid.nz],
                        "substeps_per_step": K, "dt_sub": prob.params.dt_sub, "precision": "fp32",
-                       "schedule": "one fluid step: K substeps of sort, contact (Verlet lists, skin 0.15 r_max), "
-                                   "G2P couple, integrate, P2G of F_s; alpha_s and sums at the final positions",
+                       "schedule": "one fluid step: K gic_step calls (Morton sort only when the Verlet lists, skin "
+                                   "0.15 r_max, are rebuilt; fused contact, G2P couple, integrate, P2G of F_s); "
+                                   "alpha_s and sums at the final positions",
                        "l2": "flushed between steps (512 MB write), state reset to the initial packing",
                        "wall_s": wall},
             "roofline": roofline, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
