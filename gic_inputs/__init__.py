@@ -761,3 +761,63 @@ def make(name: str, **kw) -> Problem:
         "scale_sweep_16m": scale_sweep,
     }
     return table[name](**kw)
+
+
+# --------------------------------------------------------------------------
+# inputs of the pressure projections that consume alpha_s
+# --------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class ProjectionCase:
+    """Cell-centred alpha_s (FP64) and current fluid fraction alpha_f*
+    (float32), face velocities v* (float32, x fastest), the fluid step and
+    density, and the open sides (-x, +x, -y, +y, -z, +z)."""
+    name: str
+    shape: tuple
+    dx: float
+    alpha_s: np.ndarray
+    alpha_star: np.ndarray
+    u: np.ndarray
+    v: np.ndarray
+    w: np.ndarray
+    dt: float
+    rho_f: float
+    open_sides: tuple
+
+
+def projection_case(seed=31, shape=(21, 18, 25), dx=1.0 / 32, dt=2e-3, rho_f=1000.0, amp=0.5,
+                    open_sides=(0, 0, 0, 0, 0, 1), pack_max=0.85, name="projection_random"):
+    """A sediment-like alpha_s: a smooth bed (a sum of 4 seeded Gaussian bumps
+    over a layer in the lower third) up to pack_max, so that the densest-packing
+    limit is exceeded in places, plus seeded cell noise; alpha_f* = (1 -
+    alpha_s) times a seeded factor in [0.3, 1.8] (beyond the [0.5, 1.5] ratio
+    limit in places); face velocities iid U[-amp, amp], zero on solid walls'
+    normal faces."""
+    nx, ny, nz = shape
+    gen = rng(seed, STREAM_MISC)
+    c = [(np.arange(m) + 0.5) / m for m in (nx, ny, nz)]
+    X, Y, Z = np.meshgrid(c[0], c[1], c[2], indexing="ij")
+    bed = np.clip(1.5 - 4.5 * Z, 0.0, 1.0)
+    for _ in range(4):
+        cx, cy, cz = gen.uniform(0.1, 0.9, 3)
+        s = gen.uniform(0.1, 0.3)
+        bed = bed + 0.6 * np.exp(-((X - cx) ** 2 + (Y - cy) ** 2 + (Z - cz) ** 2) / (2 * s * s))
+    a_s = np.clip(pack_max * bed / bed.max() + gen.uniform(-0.03, 0.03, size=bed.shape), 0.0, pack_max)
+    factor = gen.uniform(0.3, 1.8, size=bed.shape)
+    a_star = (1.0 - a_s) * factor
+    alpha_s = np.ascontiguousarray(np.transpose(a_s, (2, 1, 0))).ravel().astype(np.float64)
+    alpha_star = _flat(a_star)
+    grid = Grid(nx, ny, nz, dx)
+    u = gen.uniform(-amp, amp, size=(nx + 1) * ny * nz).astype(np.float32)
+    vf = gen.uniform(-amp, amp, size=nx * (ny + 1) * nz).astype(np.float32)
+    wf = gen.uniform(-amp, amp, size=nx * ny * (nz + 1)).astype(np.float32)
+    u3 = u.reshape(nz, ny, nx + 1)
+    v3 = vf.reshape(nz, ny + 1, nx)
+    w3 = wf.reshape(nz + 1, ny, nx)
+    for side, (arr, idx) in enumerate(((u3, (slice(None), slice(None), 0)), (u3, (slice(None), slice(None), nx)),
+                                       (v3, (slice(None), 0, slice(None))), (v3, (slice(None), ny, slice(None))),
+                                       (w3, (0,)), (w3, (nz,)))):
+        if not open_sides[side]:
+            arr[idx] = 0
+    return ProjectionCase(name=name, shape=tuple(shape), dx=dx, alpha_s=alpha_s, alpha_star=alpha_star, u=u, v=vf,
+                          w=wf, dt=dt, rho_f=rho_f, open_sides=tuple(open_sides))
