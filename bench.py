@@ -319,6 +319,9 @@ def run_gpu(args, ws, rank, local):
 
     variants = {}
     if not args.no_variants:
+        # the consumer of this window's alpha_s: both projections on the 128^3 grid
+        for tol in (1e-6, 1e-9):
+            variants[f"projection_{prob.name}_tol{tol:g}"] = run_projection(prob, sim, gic, torch, dev, stream, tol)
         variants["fp64_fwd"] = run_fwd(prob, gic.GIC_FP64, gic, torch, dev, stream)
         for prec_name, prec in (("fp32", gic.GIC_FP32), ("fp64", gic.GIC_FP64)):
             variants[f"{prec_name}_adjoint_dam_break"] = run_adjoint(prob, prec, torch, dev)
@@ -485,6 +488,51 @@ def run_fwd(prob, prec, gic, torch, dev, stream, steps=2, warmup=1):
     del sim, init, flush
     torch.cuda.empty_cache()
     return out
+
+
+# algorithmic bytes per cell of one FP32 CG iteration of gic_project:
+# y = A d (read d, alpha_f', write y), the update (read d, y, M^-1, e, r;
+# write e, r) and the new direction (read r, M^-1, d; write d), 4 B each
+PROJ_CG_BYTES = 56
+
+
+def run_projection(prob, sim, gic, torch, dev, stream, tol, reps=3):
+    """gic_project (velocity and density projections, Sec. 5.1) on the
+    workload's grid with alpha_s from the simulator's last window (its final
+    positions), alpha_f* = the workload's fluid fraction field, v* = its face
+    velocities, dt = the fluid step, the top side open.  Time per call (both
+    solves) with CUDA events on `stream`, the solver's counts, and the FP32
+    CG iterations' algorithmic bytes over the whole call's time."""
+    import ctypes as C
+
+    g = prob.grid
+    n = g.nx * g.ny * g.nz
+    grid = gic.GicGrid(g.nx, g.ny, g.nz, 1, float(g.dx), (C.c_double * 3)(0, 0, 0))
+    star = torch.as_tensor(prob.alpha_f, dtype=torch.float32, device=dev)
+    u, v, w = sim.fluid.u, sim.fluid.v, sim.fluid.w
+    p1 = torch.empty(n, dtype=torch.float64, device=dev)
+    p2 = torch.empty_like(p1)
+    vo = [torch.empty_like(f) for f in (u, v, w)]
+    do = [torch.empty_like(f) for f in (u, v, w)]
+    ws = torch.empty(gic.gic_project_workspace_size(grid), dtype=torch.uint8, device=dev)
+    pp = gic.make_proj_params(prob.params.dt_fluid, prob.params.rho_f, (0, 0, 0, 0, 0, 1), tol=tol)
+    times, info = [], None
+    for rep in range(reps + 1):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        info = gic.gic_project(grid, pp, sim.alpha_s, star, u, v, w, p1, p2, vo, do, ws=ws, stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        if rep:
+            times.append(a.elapsed_time(b))
+    ms = statistics.mean(times)
+    iters = int(info.inner[0] + info.inner[1])
+    gbs = PROJ_CG_BYTES * n * iters / (ms / 1000) / 1e9
+    return {"ms_per_call": ms, "cells": n, "tol": tol, "outer": list(info.outer), "inner": list(info.inner),
+            "converged": list(info.converged), "rel_residual": [float(x) for x in info.rel_residual],
+            "cg_algo_bytes_per_cell_iter": PROJ_CG_BYTES, "cg_achieved_gbs_over_call": gbs,
+            "workload": prob.name}
 
 
 def run_profile(args):

@@ -430,6 +430,67 @@ int gic_window_forward_host(const GicGrid* grid, const GicParams* params, int64_
                             int32_t K, double* x_out, double* v_out, double* alpha_s, void* Fs_u, void* Fs_v,
                             void* Fs_w, double* sums2, void* ws, size_t ws_bytes, gic_stream_t stream);
 
+/* ------------------------------------------------------------ projection */
+
+/* The consumer of alpha_s: the velocity and density projections of the
+ * fluid step (Sec. 5.1: Eqs. discret momentum, backward Euler, bring2 and
+ * ppe1 a/b; Eq. position change; the limits stated after it; the face weight
+ * beta_j of the appendix on the Push-Out boundary condition).  On the MAC
+ * grid of `grid` (only nx, ny, nz >= 1 and dx are used):
+ *   alpha_f' = 1 - min(alpha_s, alpha_s_max)                    target fluid fraction
+ *   (dt/rho_f)   div(alpha_f' grad p1) = div(alpha_f' v*)       velocity projection
+ *   (dt^2/rho_f) div(alpha_f' grad p2) = alpha_f' (1 - clamp(alpha_f* / alpha_f', ratio_min, ratio_max))
+ *   v'  = v* - (dt/rho_f) grad p1                               projected face velocities
+ *   dx  = clamp(-(dt^2/rho_f) grad p2, -h, h)                   face displacements of the fluid
+ * grad = face difference / h, div = net face flux / h.  The weight of the
+ * face between two cells is the mean of their alpha_f'; an open side is a
+ * fluid-air interface with p = 0 in the cell beyond and face weight the
+ * inner cell's alpha_f'; a solid side is a wall at rest (no flux, v' = 0 and
+ * dx = 0 on its faces).  At least one side must be open.  The equations are
+ * solved multiplied by alpha_f' (a symmetric positive definite system) by
+ * mixed-precision iterative refinement: FP64 residuals and solution, FP32
+ * Jacobi-preconditioned conjugate gradients for each correction. */
+typedef struct GicProjParams {
+  double dt;                   /* fluid step (s) */
+  double rho_f;                /* fluid density rho_0 */
+  double alpha_s_max;          /* densest-packing limit of alpha_s (0.740 in 3D), in (0, 1) */
+  double ratio_min, ratio_max; /* limits of alpha_f* / alpha_f' (0.5, 1.5), 0 < min <= 1 <= max */
+  double tol;                  /* stop when ||b - A p||_2 <= tol ||b||_2 (FP64), > 0 */
+  double inner_tol;            /* FP32 CG reduction per refinement step (1e-3), in (0, 1) */
+  int32_t max_outer;           /* refinement steps per solve, >= 1 */
+  int32_t max_inner;           /* CG iterations per refinement step, >= 1 */
+  int32_t open[6];             /* sides -x, +x, -y, +y, -z, +z: 1 open (p = 0 beyond), 0 solid wall */
+} GicProjParams;
+
+typedef struct GicProjInfo {
+  int32_t outer[2];            /* refinement steps of the p1 and p2 solves */
+  int32_t inner[2];            /* FP32 CG iterations, summed over the steps */
+  int32_t converged[2];        /* 1 if ||b - A p|| <= tol ||b|| was reached */
+  double rel_residual[2];      /* final ||b - A p||_2 / ||b||_2 (0 when b = 0) */
+} GicProjInfo;
+
+/* Bytes of workspace gic_project needs for this grid. */
+int gic_project_workspace_size(const GicGrid* grid, size_t* bytes);
+
+/* Both projections (see above).  Cell fields nx ny nz, x fastest: alpha_s
+ * (double, e.g. gic_p2g's output), alpha_star = alpha_f* (float, the fluid
+ * fraction before the projection, > 0 where it matters).  Face fields as for
+ * the fluid velocity (float): u, v, w = v* in; u_out, v_out, w_out = v' and
+ * dx_u, dx_v, dx_w = the displacements out (each triple all or none; the
+ * values on solid sides' faces are written 0).  p1, p2 (double, nx ny nz)
+ * are written with the two pressures.  ws: gic_project_workspace_size
+ * bytes, 256-byte aligned.  info (host, may be NULL) receives the solver's
+ * counts.  The call BLOCKS: after each refinement step it reads the residual
+ * on the host (waits on `stream` with a 60 s deadline per wait, then
+ * GIC_ERR_TIMEOUT).  A solve that reaches max_outer without tol returns
+ * GIC_OK with converged = 0; a non-finite residual returns GIC_ERR_INVALID.
+ * Errors: GIC_ERR_INVALID (null pointer, bad parameter, no open side),
+ * GIC_ERR_WORKSPACE, GIC_ERR_ALIGN, GIC_ERR_CUDA, GIC_ERR_TIMEOUT. */
+int gic_project(const GicGrid* grid, const GicProjParams* params, const double* alpha_s, const float* alpha_star,
+                const float* u, const float* v, const float* w, double* p1, double* p2, float* u_out, float* v_out,
+                float* w_out, float* dx_u, float* dx_v, float* dx_w, void* ws, size_t ws_bytes, GicProjInfo* info,
+                gic_stream_t stream);
+
 /* ------------------------------------------------------------ diagnostics */
 
 /* Contact pairs of a sorted state with id set: counts[k] = number of partners

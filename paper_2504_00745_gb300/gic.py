@@ -45,6 +45,17 @@ class GicGranules(C.Structure):
                 ("precision", C.c_int32), ("posf", C.c_void_p)]
 
 
+class GicProjParams(C.Structure):
+    _fields_ = [("dt", C.c_double), ("rho_f", C.c_double), ("alpha_s_max", C.c_double), ("ratio_min", C.c_double),
+                ("ratio_max", C.c_double), ("tol", C.c_double), ("inner_tol", C.c_double), ("max_outer", C.c_int32),
+                ("max_inner", C.c_int32), ("open", C.c_int32 * 6)]
+
+
+class GicProjInfo(C.Structure):
+    _fields_ = [("outer", C.c_int32 * 2), ("inner", C.c_int32 * 2), ("converged", C.c_int32 * 2),
+                ("rel_residual", C.c_double * 2)]
+
+
 class GicNeighbors(C.Structure):
     _fields_ = [("n", C.c_int64), ("cap", C.c_int32), ("skin", C.c_double), ("list", C.c_void_p),
                 ("count", C.c_void_p), ("ref_cell", C.c_void_p), ("ref_pos", C.c_void_p), ("slot", C.c_void_p),
@@ -77,6 +88,8 @@ _SIGS = {
     "gic_contact_verlet_adj": [_P] * 11,
     "gic_substep_adj": [_P] * 19,
     "gic_step": [_P, _P, _P, _P, _P, _P, _P, _P, C.c_size_t, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P],
+    "gic_project_workspace_size": [_P, _P],
+    "gic_project": [_P] * 16 + [C.c_size_t, _P, _P],
 }
 # entry points that exist in include/gic.h but are declared optional here
 # (added later in the library's life) are looked up lazily
@@ -389,6 +402,35 @@ def gic_p2g_adj(grid, params, old: State, new: State, f_ex, g_alpha_s, gFs, g_po
     _check(lib().gic_p2g_adj(C.byref(grid), C.byref(params), C.byref(a), C.byref(b), _ptr(f_ex), _ptr(g_alpha_s),
                              _ptr(gFs[0]), _ptr(gFs[1]), _ptr(gFs[2]), _ptr(g_pos_old), _ptr(g_pos_new),
                              _ptr(g_f_ex), _stream(stream)), "gic_p2g_adj")
+
+
+# ---------------------------------------------------------------- projection
+
+def make_proj_params(dt: float, rho_f: float, open_sides=(0, 0, 0, 0, 0, 1), alpha_s_max: float = 0.740,
+                     ratio_min: float = 0.5, ratio_max: float = 1.5, tol: float = 1e-9, inner_tol: float = 1e-3,
+                     max_outer: int = 12, max_inner: int = 4000) -> GicProjParams:
+    return GicProjParams(float(dt), float(rho_f), float(alpha_s_max), float(ratio_min), float(ratio_max), float(tol),
+                         float(inner_tol), int(max_outer), int(max_inner), (C.c_int32 * 6)(*[int(o) for o in open_sides]))
+
+
+def gic_project_workspace_size(grid: GicGrid) -> int:
+    b = C.c_size_t(0)
+    _check(lib().gic_project_workspace_size(C.byref(grid), C.byref(b)), "gic_project_workspace_size")
+    return int(b.value)
+
+
+def gic_project(grid: GicGrid, params: GicProjParams, alpha_s, alpha_star, u, v, w, p1, p2, vel_out=(None, None, None),
+                disp_out=(None, None, None), ws=None, stream=None) -> GicProjInfo:
+    """Both projections; blocks until they are solved.  Returns the solver's
+    counts (GicProjInfo)."""
+    if ws is None:
+        ws = torch.empty(gic_project_workspace_size(grid), dtype=torch.uint8, device=alpha_s.device)
+    info = GicProjInfo()
+    _check(lib().gic_project(C.byref(grid), C.byref(params), _ptr(alpha_s), _ptr(alpha_star), _ptr(u), _ptr(v),
+                             _ptr(w), _ptr(p1), _ptr(p2), _ptr(vel_out[0]), _ptr(vel_out[1]), _ptr(vel_out[2]),
+                             _ptr(disp_out[0]), _ptr(disp_out[1]), _ptr(disp_out[2]), _ptr(ws), ws.numel(),
+                             C.byref(info), _stream(stream)), "gic_project")
+    return info
 
 
 # ---------------------------------------------------------------- diagnostics

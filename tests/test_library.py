@@ -83,3 +83,36 @@ def test_null_arguments_are_rejected_on_the_host():
     assert L.gic_contact(C.byref(g), C.byref(bad_p), C.byref(empty), C.c_void_p(16), None, None) == 0
     assert L.gic_sort_adj(0, 0, None, None, None, None, None, None) == 0
     assert L.gic_sort_adj(5, 0, None, None, None, None, None, None) == -1
+
+
+def test_projection_validation_on_the_host():
+    """gic_project rejects bad grids, parameters, missing arrays and a short
+    workspace before any device work (fake non-null pointers are never
+    dereferenced on these paths)."""
+    from paper_2504_00745_gb300 import gic
+    L = gic.lib()
+    g = gic.GicGrid(6, 5, 4, 1, 0.1, (C.c_double * 3)(0, 0, 0))
+    one = gic.GicGrid(1, 1, 3, 1, 0.1, (C.c_double * 3)(0, 0, 0))  # a one-cell-wide column is a valid grid
+    a = gic.gic_project_workspace_size(g)
+    assert 0 < a < gic.gic_project_workspace_size(gic.GicGrid(60, 50, 40, 1, 0.1, (C.c_double * 3)(0, 0, 0)))
+    assert gic.gic_project_workspace_size(one) > 0
+    fake = C.c_void_p(1 << 20)
+    arrays = [fake] * 7 + [None] * 6
+
+    def call(grid, pp, arr=arrays, ws=fake, nbytes=a):
+        return L.gic_project(C.byref(grid), C.byref(pp), *arr, ws, nbytes, None, None)
+
+    good = gic.make_proj_params(2e-3, 1000.0)
+    assert call(gic.GicGrid(0, 5, 4, 1, 0.1, (C.c_double * 3)(0, 0, 0)), good) == -1
+    assert call(gic.GicGrid(6, 5, 4, 1, 0.0, (C.c_double * 3)(0, 0, 0)), good) == -1
+    for bad in (gic.make_proj_params(0.0, 1000.0), gic.make_proj_params(2e-3, 1000.0, alpha_s_max=1.0),
+                gic.make_proj_params(2e-3, 1000.0, ratio_min=1.2), gic.make_proj_params(2e-3, 1000.0, tol=0.0),
+                gic.make_proj_params(2e-3, 1000.0, inner_tol=1.0), gic.make_proj_params(2e-3, 1000.0, max_inner=0)):
+        assert call(g, bad) == -1
+    assert call(g, gic.make_proj_params(2e-3, 1000.0, open_sides=(0, 0, 0, 0, 0, 0))) == -1
+    assert "open" in gic.last_error()
+    assert call(g, good, arr=[fake] * 6 + [None] + [None] * 6) == -1  # p2 missing
+    assert call(g, good, arr=[fake] * 7 + [fake, None, None] + [None] * 3) == -1
+    assert "all three" in gic.last_error()
+    assert call(g, good, nbytes=a - 1) == -3
+    assert call(g, good, ws=C.c_void_p((1 << 20) + 64)) == -4
