@@ -14,6 +14,9 @@
 // refinement: the solution p and each residual b - A p are FP64 (one FP64
 // stencil pass per refinement step), and each correction A e = r comes from
 // an FP32 Jacobi-preconditioned conjugate-gradient run to a modest reduction.
+// A CG iteration is two kernels: the new direction fused with y = A d
+// (z-marching tiles), then the vector updates; 16 iterations run as one CUDA
+// graph between host reads of the stop flag.
 // Reductions are deterministic: every block writes a partial sum, and the
 // block that finishes last (an atomic ticket, no waiting) adds the partials
 // in index order and writes the scalar that the next kernels read.
@@ -249,34 +252,122 @@ __global__ void __launch_bounds__(kProjThreads) k_proj_residual(
   }
 }
 
-// CG step 1: y = A d (FP32 operator); d . y into red->dy.  32-bit cell
-// indices (fewer than 2^31 cells); `open` has bit s set for open side s.
-__global__ void __launch_bounds__(kProjThreads, 6) k_cg_apply(PGrid g, unsigned open, const float* __restrict__ ap32,
-                                                              const float* __restrict__ d, float* __restrict__ y,
-                                                              double* __restrict__ P, ProjRed* red) {
+// CG step 1 (with the previous step's new direction): d_new = M^-1 r +
+// beta d_old (beta = 0 on a run's first iteration), y = A d_new (FP32
+// operator) and d_new . y into red->dy.  d_old and d_new are different
+// buffers: neighbouring tiles read d_old while this one writes d_new.
+// A CTA covers a kTX x kTY column tile and marches over lz planes in z: its
+// threads keep the column's d_new and alpha_f' at k-1, k, k+1 in registers
+// and the plane's values at the tile's four sides in shared memory.
+constexpr int kTX = 32, kTY = 8;  // kTX * kTY = kProjThreads
+static_assert(kTX * kTY == kProjThreads, "tile shape");
+
+__global__ void __launch_bounds__(kProjThreads) k_cg_dir_apply(PGrid g, unsigned open, int lz, int tiles_x,
+                                                               int tiles_y, int cur, const float* __restrict__ ap32,
+                                                               const float* __restrict__ r,
+                                                               const float* __restrict__ invd,
+                                                               const float* __restrict__ d_old,
+                                                               float* __restrict__ d_new, float* __restrict__ y,
+                                                               double* __restrict__ P, ProjRed* red) {
+  __shared__ float s_d[kTY + 2][kTX + 2];
+  __shared__ float s_a[kTY + 2][kTX + 2];
   __shared__ double smem[32];
   if (block_flag(&red->done)) return;
-  const unsigned n = (unsigned)g.n, nx = (unsigned)g.nx, ny = (unsigned)g.ny, nz = (unsigned)g.nz;
-  const unsigned nxy = nx * ny;
+  const float be = red->iters == 0 ? 0.f : (float)(red->rz[cur] / red->rz[cur ^ 1]);
+  const int nx = g.nx, ny = g.ny, nz = g.nz;
+  const int b = blockIdx.x;
+  const int bx = b % tiles_x, bt = b / tiles_x, by = bt % tiles_y, bz = bt / tiles_y;
+  const int tx = threadIdx.x % kTX, ty = threadIdx.x / kTX;
+  const int x0 = bx * kTX, y0 = by * kTY;
+  const int i = x0 + tx, j = y0 + ty;
+  const int z0 = bz * lz, z1 = min(z0 + lz, nz);
+  const bool act = i < nx && j < ny;
+  auto at = [&](int ii, int jj, int kk) -> unsigned {
+    return (unsigned)ii + (unsigned)nx * ((unsigned)jj + (unsigned)ny * (unsigned)kk);
+  };
+  auto dn = [&](unsigned c) -> float { return fmaf(be, d_old[c], invd[c] * r[c]); };
+  // this thread's entry of the tile's side ring (80 entries; corners are not needed)
+  int ri = -1, rj = -1, sx = 0, sy = 0;
+  {
+    const int q = threadIdx.x;
+    if (q < kTX) {
+      ri = x0 + q, rj = y0 - 1, sx = q + 1, sy = 0;
+    } else if (q < 2 * kTX) {
+      ri = x0 + q - kTX, rj = y0 + kTY, sx = q - kTX + 1, sy = kTY + 1;
+    } else if (q < 2 * kTX + kTY) {
+      ri = x0 - 1, rj = y0 + q - 2 * kTX, sx = 0, sy = q - 2 * kTX + 1;
+    } else if (q < 2 * kTX + 2 * kTY) {
+      ri = x0 + kTX, rj = y0 + q - 2 * kTX - kTY, sx = kTX + 1, sy = q - 2 * kTX - kTY + 1;
+    }
+  }
+  const bool ring = ri >= 0 && ri < nx && rj >= 0 && rj < ny;
+  float dm = 0.f, dc = 0.f, dp = 0.f, am = 0.f, ac = 0.f, apl = 0.f;
+  if (act) {
+    if (z0 > 0) {
+      const unsigned c = at(i, j, z0 - 1);
+      dm = dn(c);
+      am = ap32[c];
+    }
+    const unsigned c = at(i, j, z0);
+    dc = dn(c);
+    ac = ap32[c];
+  }
   KahanF dyk;
-  for (unsigned c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
-    const unsigned k = c / nxy, rem = c - k * nxy, j = rem / nx, i = rem - j * nx;
-    const float ac = ap32[c], dc = d[c];
-    float acc = 0.f;
-    auto side = [&](bool inside, unsigned nb, unsigned bit) {
-      if (inside)
-        acc += 0.5f * (ac + ap32[nb]) * (dc - d[nb]);
-      else if (open & bit)
+  for (int k = z0; k < z1; ++k) {
+    s_d[ty + 1][tx + 1] = dc;
+    s_a[ty + 1][tx + 1] = ac;
+    if (sx | sy) {  // a ring thread
+      float rd = 0.f, ra = 0.f;
+      if (ring) {
+        const unsigned c = at(ri, rj, k);
+        rd = dn(c);
+        ra = ap32[c];
+      }
+      s_d[sy][sx] = rd;
+      s_a[sy][sx] = ra;
+    }
+    __syncthreads();
+    if (act) {
+      if (k + 1 < nz) {
+        const unsigned c = at(i, j, k + 1);
+        dp = dn(c);
+        apl = ap32[c];
+      }
+      float acc = 0.f;
+      if (i > 0)
+        acc += 0.5f * (ac + s_a[ty + 1][tx]) * (dc - s_d[ty + 1][tx]);
+      else if (open & 1u)
         acc += ac * dc;
-    };
-    side(i > 0, c - 1, 1u);
-    side(i + 1 < nx, c + 1, 2u);
-    side(j > 0, c - nx, 4u);
-    side(j + 1 < ny, c + nx, 8u);
-    side(k > 0, c - nxy, 16u);
-    side(k + 1 < nz, c + nxy, 32u);
-    y[c] = acc;
-    dyk.add(dc * acc);
+      if (i + 1 < nx)
+        acc += 0.5f * (ac + s_a[ty + 1][tx + 2]) * (dc - s_d[ty + 1][tx + 2]);
+      else if (open & 2u)
+        acc += ac * dc;
+      if (j > 0)
+        acc += 0.5f * (ac + s_a[ty][tx + 1]) * (dc - s_d[ty][tx + 1]);
+      else if (open & 4u)
+        acc += ac * dc;
+      if (j + 1 < ny)
+        acc += 0.5f * (ac + s_a[ty + 2][tx + 1]) * (dc - s_d[ty + 2][tx + 1]);
+      else if (open & 8u)
+        acc += ac * dc;
+      if (k > 0)
+        acc += 0.5f * (ac + am) * (dc - dm);
+      else if (open & 16u)
+        acc += ac * dc;
+      if (k + 1 < nz)
+        acc += 0.5f * (ac + apl) * (dc - dp);
+      else if (open & 32u)
+        acc += ac * dc;
+      const unsigned c = at(i, j, k);
+      d_new[c] = dc;
+      y[c] = acc;
+      dyk.add(dc * acc);
+    }
+    __syncthreads();
+    dm = dc;
+    dc = dp;
+    am = ac;
+    ac = apl;
   }
   const double dy = block_sum((double)dyk.s, smem);
   const double vals[1] = {dy};
@@ -285,8 +376,8 @@ __global__ void __launch_bounds__(kProjThreads, 6) k_cg_apply(PGrid g, unsigned 
 }
 
 // CG step 2: alpha = rho / (d . y); e += alpha d; r -= alpha y; the new rho
-// = r . M^-1 r and r . r.  The last block counts the iteration and sets the
-// stop flag when r . r <= rr_stop.
+// = r . M^-1 r and r . r (four cells per thread and step, float4).  The last
+// block counts the iteration and sets the stop flag when r . r <= rr_stop.
 __global__ void __launch_bounds__(kProjThreads) k_cg_update(PGrid g, int cur, const float* __restrict__ d,
                                                             const float* __restrict__ y, const float* __restrict__ invd,
                                                             float* __restrict__ e, float* __restrict__ r,
@@ -300,8 +391,28 @@ __global__ void __launch_bounds__(kProjThreads) k_cg_update(PGrid g, int cur, co
   }
   const float al = (float)(rz / dy);
   KahanF rzk, rrk;
-  const unsigned n = (unsigned)g.n;
-  for (unsigned c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+  const unsigned n = (unsigned)g.n, n4 = n / 4u;
+  const unsigned t0 = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+  for (unsigned q = t0; q < n4; q += stride) {  // arrays are 256-byte aligned
+    const float4 dq = reinterpret_cast<const float4*>(d)[q];
+    const float4 yq = reinterpret_cast<const float4*>(y)[q];
+    const float4 iq = reinterpret_cast<const float4*>(invd)[q];
+    float4 eq = reinterpret_cast<const float4*>(e)[q];
+    float4 rq = reinterpret_cast<const float4*>(r)[q];
+    eq.x = fmaf(al, dq.x, eq.x);
+    eq.y = fmaf(al, dq.y, eq.y);
+    eq.z = fmaf(al, dq.z, eq.z);
+    eq.w = fmaf(al, dq.w, eq.w);
+    rq.x = fmaf(-al, yq.x, rq.x);
+    rq.y = fmaf(-al, yq.y, rq.y);
+    rq.z = fmaf(-al, yq.z, rq.z);
+    rq.w = fmaf(-al, yq.w, rq.w);
+    reinterpret_cast<float4*>(e)[q] = eq;
+    reinterpret_cast<float4*>(r)[q] = rq;
+    rzk.add(rq.x * (iq.x * rq.x) + rq.y * (iq.y * rq.y) + rq.z * (iq.z * rq.z) + rq.w * (iq.w * rq.w));
+    rrk.add(rq.x * rq.x + rq.y * rq.y + rq.z * rq.z + rq.w * rq.w);
+  }
+  for (unsigned c = 4u * n4 + t0; c < n; c += stride) {
     const float dc = d[c];
     e[c] = fmaf(al, dc, e[c]);
     const float rc = fmaf(-al, y[c], r[c]);
@@ -317,17 +428,6 @@ __global__ void __launch_bounds__(kProjThreads) k_cg_update(PGrid g, int cur, co
     red->iters += 1;
     if (!(red->rr > red->rr_stop)) red->done = 1;  // also stops on NaN
   }
-}
-
-// CG step 3: beta = rho_new / rho; d = M^-1 r + beta d.
-__global__ void __launch_bounds__(kProjThreads) k_cg_dir(PGrid g, int cur, const float* __restrict__ r,
-                                                         const float* __restrict__ invd, float* __restrict__ d,
-                                                         const ProjRed* red) {
-  if (block_flag(&red->done)) return;
-  const float be = (float)(red->rz[cur ^ 1] / red->rz[cur]);
-  const unsigned n = (unsigned)g.n;
-  for (unsigned c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x)
-    d[c] = fmaf(be, d[c], invd[c] * r[c]);
 }
 
 // p += e (the FP32 correction into the FP64 solution).
@@ -394,10 +494,31 @@ __global__ void __launch_bounds__(kProjThreads) k_proj_faces(
 // ---- host side ----
 
 struct ProjWs {
-  float *ap32, *invd, *r, *d, *y, *e;
-  double* P;    // 3 nblk partial sums
+  float *ap32, *invd, *r, *d[2], *y, *e;  // d: the CG direction, double-buffered
+  double* P;    // 3 * max(blocks) partial sums
   ProjRed* red;
 };
+
+// Tiles and z-planes per CTA of k_cg_dir_apply: lz halves from 64 until the
+// grid has at least 6 CTAs per SM.
+struct TileGrid {
+  int tiles_x, tiles_y, lz, blocks;
+};
+static TileGrid tile_grid(const PGrid& g) {
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  TileGrid t;
+  t.tiles_x = (g.nx + kTX - 1) / kTX;
+  t.tiles_y = (g.ny + kTY - 1) / kTY;
+  t.lz = 64;
+  for (;;) {
+    const int64_t b = (int64_t)t.tiles_x * t.tiles_y * ((g.nz + t.lz - 1) / t.lz);
+    if (b >= 6 * (int64_t)(sms > 0 ? sms : 152) || t.lz <= 4) break;
+    t.lz /= 2;
+  }
+  t.blocks = (int)((int64_t)t.tiles_x * t.tiles_y * ((g.nz + t.lz - 1) / t.lz));
+  return t;
+}
 
 static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
@@ -412,6 +533,7 @@ static int proj_blocks(int64_t n) {
 // Workspace for n cells and nblk blocks (laid out by the same walk that
 // measures it).
 static size_t proj_layout(int64_t n, int nblk, char* base, ProjWs* W) {
+  // nblk: the most CTAs any kernel with partial sums launches
   size_t off = 0;
   auto take = [&](size_t bytes) {
     char* p = base ? base + off : nullptr;
@@ -422,7 +544,8 @@ static size_t proj_layout(int64_t n, int nblk, char* base, ProjWs* W) {
   w.ap32 = (float*)take(4 * (size_t)n);
   w.invd = (float*)take(4 * (size_t)n);
   w.r = (float*)take(4 * (size_t)n);
-  w.d = (float*)take(4 * (size_t)n);
+  w.d[0] = (float*)take(4 * (size_t)n);
+  w.d[1] = (float*)take(4 * (size_t)n);
   w.y = (float*)take(4 * (size_t)n);
   w.e = (float*)take(4 * (size_t)n);
   w.P = (double*)take(3 * 8 * (size_t)nblk);
@@ -460,7 +583,9 @@ extern "C" int gic_project_workspace_size(const GicGrid* grid, size_t* bytes) {
   int rc = proj_grid(grid, &g);
   if (rc) return rc;
   if (!bytes) return set_error(GIC_ERR_INVALID, "gic_project_workspace_size: bytes is NULL");
-  *bytes = proj_layout(g.n, proj_blocks(g.n), nullptr, nullptr);
+  const TileGrid tg = tile_grid(g);
+  const int nb = proj_blocks(g.n);
+  *bytes = proj_layout(g.n, nb > tg.blocks ? nb : tg.blocks, nullptr, nullptr);
   return GIC_OK;
 }
 
@@ -500,13 +625,15 @@ extern "C" int gic_project(const GicGrid* grid, const GicProjParams* P, const do
     if (P->open[s]) open_bits |= 1u << s;
   }
   const int nblk = proj_blocks(g.n);
-  const size_t need = proj_layout(g.n, nblk, nullptr, nullptr);
+  const TileGrid tg = tile_grid(g);
+  const int pblk = nblk > tg.blocks ? nblk : tg.blocks;  // partial-sum slots
+  const size_t need = proj_layout(g.n, pblk, nullptr, nullptr);
   if (!ws || ws_bytes < need)
     return set_error(GIC_ERR_WORKSPACE, "gic_project: workspace of %zu bytes needed, %zu given", need, ws_bytes);
   if ((uintptr_t)ws % 256) return set_error(GIC_ERR_ALIGN, "gic_project: workspace must be 256-byte aligned");
   cudaStream_t st = (cudaStream_t)stream_;
   ProjWs W;
-  proj_layout(g.n, nblk, (char*)ws, &W);
+  proj_layout(g.n, pblk, (char*)ws, &W);
   uint32_t* status = status_word();
   const double h = grid->dx;
   ProjScales S;
@@ -525,9 +652,9 @@ extern "C" int gic_project(const GicGrid* grid, const GicProjParams* P, const do
     return set_error(GIC_ERR_CUDA, "gic_project: clearing the solver's scalars failed");
   // one CG iteration; all arguments but the parity are fixed for the call
   auto cg_iteration = [&](int cur, cudaStream_t s_) {
-    k_cg_apply<<<nblk, kProjThreads, 0, s_>>>(g, open_bits, W.ap32, W.d, W.y, W.P, W.red);
-    k_cg_update<<<nblk, kProjThreads, 0, s_>>>(g, cur, W.d, W.y, W.invd, W.e, W.r, W.P, W.red);
-    k_cg_dir<<<nblk, kProjThreads, 0, s_>>>(g, cur, W.r, W.invd, W.d, W.red);
+    k_cg_dir_apply<<<tg.blocks, kProjThreads, 0, s_>>>(g, open_bits, tg.lz, tg.tiles_x, tg.tiles_y, cur, W.ap32,
+                                                       W.r, W.invd, W.d[cur], W.d[cur ^ 1], W.y, W.P, W.red);
+    k_cg_update<<<nblk, kProjThreads, 0, s_>>>(g, cur, W.d[cur ^ 1], W.y, W.invd, W.e, W.r, W.P, W.red);
   };
   // kChunk iterations as one CUDA graph (kChunk even: the parities repeat),
   // built when the first CG run needs it
@@ -564,7 +691,7 @@ extern "C" int gic_project(const GicGrid* grid, const GicProjParams* P, const do
       break;
     }
     for (int outer = 0;; ++outer) {
-      k_proj_residual<<<nblk, kProjThreads, 0, st>>>(g, which, S, alpha_s, alpha_star, u, v, w, p, W.invd, W.r, W.d,
+      k_proj_residual<<<nblk, kProjThreads, 0, st>>>(g, which, S, alpha_s, alpha_star, u, v, w, p, W.invd, W.r, W.d[0],
                                                      W.e, P->inner_tol * P->inner_tol, W.P, W.red, status);
       ++launches;
       if ((rc2 = read_red(W.red, &hr, st))) break;
@@ -590,11 +717,11 @@ extern "C" int gic_project(const GicGrid* grid, const GicProjParams* P, const do
             break;
           }
           it += kChunk;
-          launches += 3 * kChunk;
+          launches += 2 * kChunk;
         } else {
           for (; it < P->max_inner; ++it) {
             cg_iteration(it & 1, st);
-            launches += 3;
+            launches += 2;
           }
         }
         cudaError_t le = cudaGetLastError();
