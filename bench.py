@@ -490,10 +490,11 @@ def run_fwd(prob, prec, gic, torch, dev, stream, steps=2, warmup=1):
     return out
 
 
-# algorithmic bytes per cell of one FP32 CG iteration of gic_project:
-# y = A d (read d, alpha_f', write y), the update (read d, y, M^-1, e, r;
-# write e, r) and the new direction (read r, M^-1, d; write d), 4 B each
-PROJ_CG_BYTES = 56
+# algorithmic bytes per cell of one FP32 CG iteration of gic_project, 4 B
+# per value: the new direction fused with y = A d (read r, M^-1, the old
+# direction, alpha_f'; write the direction and y) and the update (read d,
+# y, M^-1, e, r; write e, r)
+PROJ_CG_BYTES = 52
 
 
 def run_projection(prob, sim, gic, torch, dev, stream, tol, reps=3):

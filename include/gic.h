@@ -14,6 +14,8 @@
  *   gic_g2p_couple  drag, buoyancy, fluid acceleration       (Sec. 3.3 Eqs. 5a-5c, Sec. 5.2)
  *   gic_integrate   virtual-mass symplectic Euler            (Sec. 5.2 Eq. sand kine; Alg. 2 MoveParticle)
  *   gic_p2g         alpha_s and exchange momentum to the MAC grid (Sec. 5.1 alpha_s; Sec. 5.2 Exchange Momentum)
+ * and, once per fluid step, gic_project consumes alpha_s: the velocity and
+ * density projections of Sec. 5.1 (Eqs. ppe1 a/b).
  *
  * Conventions shared by every entry point
  * ---------------------------------------
