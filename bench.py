@@ -490,11 +490,13 @@ def run_fwd(prob, prec, gic, torch, dev, stream, steps=2, warmup=1):
     return out
 
 
-# algorithmic bytes per cell of one FP32 CG iteration of gic_project, 4 B
-# per value: the new direction fused with y = A d (read r, M^-1, the old
-# direction, alpha_f'; write the direction and y) and the update (read d,
-# y, M^-1, e, r; write e, r)
-PROJ_CG_BYTES = 52
+# bytes per fine cell of one multigrid-preconditioned CG iteration of
+# gic_project (4 B values, each array read or written once per pass): on the
+# fine level four red-black half sweeps (104), the residual restriction (20),
+# the interpolation (9), rho = r . z (8), the direction fused with y = A d
+# (28) and the updates (24); the coarser levels add about an eighth of the
+# fine level's V-cycle passes (19)
+PROJ_CG_BYTES = 212
 
 
 def run_projection(prob, sim, gic, torch, dev, stream, tol, reps=3):
@@ -502,8 +504,8 @@ def run_projection(prob, sim, gic, torch, dev, stream, tol, reps=3):
     workload's grid with alpha_s from the simulator's last window (its final
     positions), alpha_f* = the workload's fluid fraction field, v* = its face
     velocities, dt = the fluid step, the top side open.  Time per call (both
-    solves) with CUDA events on `stream`, the solver's counts, and the FP32
-    CG iterations' algorithmic bytes over the whole call's time."""
+    solves) with CUDA events on `stream`, the solver's counts, and the CG
+    iterations' bytes over the whole call's time."""
     import ctypes as C
 
     g = prob.grid

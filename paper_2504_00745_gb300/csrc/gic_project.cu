@@ -13,10 +13,9 @@
 // box with one open side).  So the solve is mixed-precision iterative
 // refinement: the solution p and each residual b - A p are FP64 (one FP64
 // stencil pass per refinement step), and each correction A e = r comes from
-// an FP32 Jacobi-preconditioned conjugate-gradient run to a modest reduction.
-// A CG iteration is two kernels: the new direction fused with y = A d
-// (z-marching tiles), then the vector updates; 16 iterations run as one CUDA
-// graph between host reads of the stop flag.
+// an FP32 conjugate-gradient run, preconditioned by a geometric multigrid
+// V-cycle, to a modest reduction.  The CG iterations run as CUDA graphs of a
+// few iterations between host reads of the stop flag.
 // Reductions are deterministic: every block writes a partial sum, and the
 // block that finishes last (an atomic ticket, no waiting) adds the partials
 // in index order and writes the scalar that the next kernels read.
@@ -33,7 +32,7 @@ constexpr int kProjThreads = 256;
 
 struct PGrid {
   int nx, ny, nz;
-  int64_t n;        // cells (< 2^31: cell indices are 32-bit)
+  int64_t n;        // cells (< 2^30: cell and face indices are 32-bit)
   int64_t nxy;      // nx * ny
   int open[6];      // -x, +x, -y, +y, -z, +z
 };
@@ -108,16 +107,6 @@ __device__ __forceinline__ void for_faces(const PGrid& g, int i, int j, int k, i
   }
 }
 
-// A flag read once per block (uniform over the block's threads).
-__device__ __forceinline__ bool block_flag(const int* flag) {
-  __shared__ int f;
-  if (threadIdx.x == 0) f = *(volatile const int*)flag;
-  __syncthreads();
-  const bool r = f != 0;
-  __syncthreads();
-  return r;
-}
-
 // Compensated FP32 sum (Kahan): the CG's per-thread dot-product partials stay
 // off the FP64 pipe, whose rate on GB300 is a small fraction of FP32's.
 struct KahanF {
@@ -143,31 +132,6 @@ __global__ void __launch_bounds__(kProjThreads) k_proj_prep(PGrid g, const doubl
     ap32[c] = (float)target_fraction(alpha_s[c], amax);
 }
 
-// The inverse Jacobi diagonal of the FP32 operator (the preconditioner).
-__global__ void __launch_bounds__(kProjThreads) k_proj_diag(PGrid g, unsigned open, const float* __restrict__ ap32,
-                                                            float* __restrict__ invd) {
-  const unsigned n = (unsigned)g.n, nx = (unsigned)g.nx, ny = (unsigned)g.ny, nz = (unsigned)g.nz;
-  const unsigned nxy = nx * ny;
-  for (unsigned c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
-    const unsigned k = c / nxy, rem = c - k * nxy, j = rem / nx, i = rem - j * nx;
-    const float ac = ap32[c];
-    float diag = 0.f;
-    auto side = [&](bool inside, unsigned nb, unsigned bit) {
-      if (inside)
-        diag += 0.5f * (ac + ap32[nb]);
-      else if (open & bit)
-        diag += ac;
-    };
-    side(i > 0, c - 1, 1u);
-    side(i + 1 < nx, c + 1, 2u);
-    side(j > 0, c - nx, 4u);
-    side(j + 1 < ny, c + nx, 8u);
-    side(k > 0, c - nxy, 16u);
-    side(k + 1 < nz, c + nxy, 32u);
-    invd[c] = diag > 0.f ? 1.f / diag : 0.f;
-  }
-}
-
 struct ProjScales {
   double vel;       // rho h / dt: b1 = vel * (sum of beta v over low faces - over high faces)
   double den;       // -rho h^2 / dt^2: b2 = den * alpha' (1 - clamp(ratio))
@@ -175,16 +139,15 @@ struct ProjScales {
 };
 
 // FP64 residual r = b - A p of system `which` (1: velocity, 2: density);
-// starts the FP32 correction run: r32 = r, d = M^-1 r, e = 0.  Scalars:
-// ||r||^2 (FP64), ||b||^2 and r32 . M^-1 r32 (the CG's first rho).
+// starts the FP32 correction run: r32 = r, e = 0, and arms its stop test.
+// Scalars: ||r||^2 (FP64) and ||b||^2.
 __global__ void __launch_bounds__(kProjThreads) k_proj_residual(
     PGrid g, int which, ProjScales S, const double* __restrict__ alpha_s, const float* __restrict__ alpha_star,
     const float* __restrict__ u, const float* __restrict__ v, const float* __restrict__ w,
-    const double* __restrict__ p, const float* __restrict__ invd, float* __restrict__ r32, float* __restrict__ d32,
-    float* __restrict__ e32, double inner_tol2, double* __restrict__ P, ProjRed* red, uint32_t* status) {
+    const double* __restrict__ p, float* __restrict__ r32, float* __restrict__ e32, double inner_tol2,
+    double* __restrict__ P, ProjRed* red, uint32_t* status) {
   __shared__ double smem[64];
   double rr = 0.0, bb = 0.0;
-  KahanF rzk;
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < g.n; c += (int64_t)gridDim.x * blockDim.x) {
     int i, j, k;
     cell_ijk(g, c, i, j, k);
@@ -231,143 +194,294 @@ __global__ void __launch_bounds__(kProjThreads) k_proj_residual(
     }
     const double r = b - Ap;
     if (!isfinite(r)) raise_status(status, GIC_STATUS_NONFINITE);
-    const float rf = (float)r;
-    const float df = invd[c] * rf;
-    r32[c] = rf;
-    d32[c] = df;
+    r32[c] = (float)r;
     e32[c] = 0.f;
     rr += r * r;
     bb += b * b;
-    rzk.add(rf * df);
   }
   block_sum2(rr, bb, smem);
-  __syncthreads();
-  const double rz = block_sum((double)rzk.s, smem);
-  const double vals[3] = {rr, bb, rz};
-  double* const outs[3] = {&red->rr64, &red->bb, &red->rz[0]};
-  if (reduce_last<3>(vals, P, red, outs) && threadIdx.x == 0) {  // arm the CG run on this residual
+  const double vals[2] = {rr, bb};
+  double* const outs[2] = {&red->rr64, &red->bb};
+  if (reduce_last<2>(vals, P, red, outs) && threadIdx.x == 0) {  // arm the CG run on this residual
     red->rr_stop = inner_tol2 * red->rr64;
     red->done = 0;
     red->iters = 0;
   }
 }
 
-// CG step 1 (with the previous step's new direction): d_new = M^-1 r +
-// beta d_old (beta = 0 on a run's first iteration), y = A d_new (FP32
-// operator) and d_new . y into red->dy.  d_old and d_new are different
-// buffers: neighbouring tiles read d_old while this one writes d_new.
-// A CTA covers a kTX x kTY column tile and marches over lz planes in z: its
-// threads keep the column's d_new and alpha_f' at k-1, k, k+1 in registers
-// and the plane's values at the tile's four sides in shared memory.
-constexpr int kTX = 32, kTY = 8;  // kTX * kTY = kProjThreads
-static_assert(kTX * kTY == kProjThreads, "tile shape");
+// ---- multigrid preconditioner (FP32) ----
+//
+// A level is the operator (A x)_c = sum over c's faces of beta_f (x_c -
+// x_nb) on an nx ny nz cell grid, with x_nb = 0 beyond the boundary: open
+// sides carry their weight, solid sides weight 0, so every level is the same
+// kind of operator.  Level 0 has the face weights of the projection; level
+// l + 1 halves each axis (ceil), a coarse cell covering up to 2 x 2 x 2 fine
+// cells, and its face weights are the sums of the fine face weights across
+// each coarse face: the Galerkin product R A P with P the piecewise-constant
+// interpolation and R = P^T.  The V-cycle smooths with red-black Gauss-Seidel
+// (red then black before the coarse correction, black then red after it, so
+// the preconditioner is symmetric), restricts the residual by summing the
+// children, adds kMgOmega times the interpolated coarse correction (the
+// constant interpolation under-corrects; 1.6 keeps the preconditioner
+// positive definite and halves the CG iterations against 1.0), and solves the
+// coarsest level (every axis <= 4 cells) with one CTA doing a palindromic
+// sequence of Gauss-Seidel sweeps.
+constexpr float kMgOmega = 1.6f;
+constexpr int kMgCoarsePairs = 8;  // (black, red) sweep pairs after the first red sweep on the coarsest level
+constexpr int kMgMaxLevels = 16;
 
-__global__ void __launch_bounds__(kProjThreads) k_cg_dir_apply(PGrid g, unsigned open, int lz, int tiles_x,
-                                                               int tiles_y, int cur, const float* __restrict__ ap32,
-                                                               const float* __restrict__ r,
-                                                               const float* __restrict__ invd,
+struct MgLevel {
+  int nx, ny, nz;
+  float *bx, *by, *bz;  // face weights: (nx+1) ny nz, nx (ny+1) nz, nx ny (nz+1)
+  float* invd;          // 1 / (sum of the cell's six face weights)
+  float *x, *b;         // correction and right-hand side
+};
+
+__device__ __forceinline__ bool stopped(const ProjRed* red) { return *(volatile const int*)&red->done != 0; }
+
+__device__ __forceinline__ void level_ijk(const MgLevel& L, unsigned c, unsigned& i, unsigned& j, unsigned& k) {
+  const unsigned nx = (unsigned)L.nx, nxy = nx * (unsigned)L.ny;
+  k = c / nxy;
+  const unsigned r = c - k * nxy;
+  j = r / nx;
+  i = r - j * nx;
+}
+
+// sum over the cell's interior faces of beta_f x_nb, and the sum of all six
+// face weights
+__device__ __forceinline__ void level_gather(const MgLevel& L, unsigned c, unsigned i, unsigned j, unsigned k,
+                                             const float* __restrict__ x, float& s, float& diag) {
+  const unsigned nx = (unsigned)L.nx, ny = (unsigned)L.ny, nz = (unsigned)L.nz, nxy = nx * ny;
+  const unsigned fx = i + (nx + 1) * (j + ny * k);
+  const unsigned fy = i + nx * (j + (ny + 1) * k);
+  const float wxl = L.bx[fx], wxh = L.bx[fx + 1];
+  const float wyl = L.by[fy], wyh = L.by[fy + nx];
+  const float wzl = L.bz[c], wzh = L.bz[c + nxy];
+  diag = ((wxl + wxh) + (wyl + wyh)) + (wzl + wzh);
+  float t = 0.f;
+  if (i > 0) t = fmaf(wxl, x[c - 1], t);
+  if (i + 1 < nx) t = fmaf(wxh, x[c + 1], t);
+  if (j > 0) t = fmaf(wyl, x[c - nx], t);
+  if (j + 1 < ny) t = fmaf(wyh, x[c + nx], t);
+  if (k > 0) t = fmaf(wzl, x[c - nxy], t);
+  if (k + 1 < nz) t = fmaf(wzh, x[c + nxy], t);
+  s = t;
+}
+
+__device__ __forceinline__ float level_diag(const MgLevel& L, unsigned c, unsigned i, unsigned j, unsigned k) {
+  const unsigned nx = (unsigned)L.nx, ny = (unsigned)L.ny, nxy = nx * ny;
+  const unsigned fx = i + (nx + 1) * (j + ny * k);
+  const unsigned fy = i + nx * (j + (ny + 1) * k);
+  return ((L.bx[fx] + L.bx[fx + 1]) + (L.by[fy] + L.by[fy + nx])) + (L.bz[c] + L.bz[c + nxy]);
+}
+
+// Level-0 face weights from alpha_f' (float): the mean of the two cells, the
+// inner cell's value on an open side, 0 on a solid side.
+__global__ void __launch_bounds__(kProjThreads) k_mg_faces0(MgLevel L, unsigned open, const float* __restrict__ ap) {
+  const unsigned nx = L.nx, ny = L.ny, nz = L.nz;
+  const unsigned nu = (nx + 1) * ny * nz, nv = nx * (ny + 1) * nz, nw = nx * ny * (nz + 1);
+  for (unsigned q = blockIdx.x * blockDim.x + threadIdx.x; q < nu + nv + nw; q += gridDim.x * blockDim.x) {
+    unsigned a, f;
+    if (q < nu) {
+      a = 0, f = q;
+    } else if (q < nu + nv) {
+      a = 1, f = q - nu;
+    } else {
+      a = 2, f = q - nu - nv;
+    }
+    const unsigned sx = nx + (a == 0), sy = ny + (a == 1);
+    const unsigned k = f / (sx * sy), rem = f - k * sx * sy, j = rem / sx, i = rem - j * sx;
+    const unsigned pos = a == 0 ? i : (a == 1 ? j : k);
+    const unsigned m = a == 0 ? nx : (a == 1 ? ny : nz);
+    const unsigned stride = a == 0 ? 1u : (a == 1 ? nx : nx * ny);
+    // the cell above the face (valid when pos < m) and the one below (pos > 0)
+    const unsigned c_hi = i + nx * (j + ny * k), c_lo = c_hi - stride;
+    float wgt;
+    if (pos > 0 && pos < m)
+      wgt = 0.5f * (ap[c_hi] + ap[c_lo]);
+    else if (pos == 0)
+      wgt = (open >> (2 * a)) & 1u ? ap[c_hi] : 0.f;
+    else
+      wgt = (open >> (2 * a + 1)) & 1u ? ap[c_lo] : 0.f;
+    (a == 0 ? L.bx : (a == 1 ? L.by : L.bz))[f] = wgt;
+  }
+}
+
+// Coarse face weights: the sum of the fine face weights across each coarse face.
+__global__ void __launch_bounds__(kProjThreads) k_mg_coarsen(MgLevel F, MgLevel C) {
+  const unsigned cx = C.nx, cy = C.ny, cz = C.nz;
+  const unsigned nu = (cx + 1) * cy * cz, nv = cx * (cy + 1) * cz, nw = cx * cy * (cz + 1);
+  for (unsigned q = blockIdx.x * blockDim.x + threadIdx.x; q < nu + nv + nw; q += gridDim.x * blockDim.x) {
+    unsigned a, f;
+    if (q < nu) {
+      a = 0, f = q;
+    } else if (q < nu + nv) {
+      a = 1, f = q - nu;
+    } else {
+      a = 2, f = q - nu - nv;
+    }
+    const unsigned sx = cx + (a == 0), sy = cy + (a == 1);
+    const unsigned K = f / (sx * sy), rem = f - K * sx * sy, J = rem / sx, I = rem - J * sx;
+    const unsigned fnx = F.nx, fny = F.ny, fnz = F.nz;
+    // the fine face position along axis a, and the 2 x 2 footprint on the other two axes
+    unsigned lo[3] = {2 * I, 2 * J, 2 * K}, hi[3], lim[3] = {fnx, fny, fnz};
+    for (int b = 0; b < 3; ++b) hi[b] = min(lo[b] + 2, lim[b]);
+    lo[a] = min(lo[a], lim[a]);
+    hi[a] = lo[a] + 1;
+    const float* src = a == 0 ? F.bx : (a == 1 ? F.by : F.bz);
+    const unsigned fsx = fnx + (a == 0), fsy = fny + (a == 1);
+    float s = 0.f;
+    for (unsigned k = lo[2]; k < hi[2]; ++k)
+      for (unsigned j = lo[1]; j < hi[1]; ++j)
+        for (unsigned i = lo[0]; i < hi[0]; ++i) s += src[i + fsx * (j + fsy * k)];
+    (a == 0 ? C.bx : (a == 1 ? C.by : C.bz))[f] = s;
+  }
+}
+
+__global__ void __launch_bounds__(kProjThreads) k_mg_diag(MgLevel L) {
+  const unsigned n = (unsigned)L.nx * L.ny * L.nz;
+  for (unsigned c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+    unsigned i, j, k;
+    level_ijk(L, c, i, j, k);
+    const float diag = level_diag(L, c, i, j, k);
+    L.invd[c] = diag > 0.f ? 1.f / diag : 0.f;
+  }
+}
+
+// One Gauss-Seidel half sweep: the cells with (i + j + k) % 2 == color get
+// x_c = (b_c + sum beta_f x_nb) / diag_c.  init: x is taken as 0 (the other
+// color is written 0).
+__global__ void __launch_bounds__(kProjThreads) k_mg_smooth(MgLevel L, unsigned color, int init,
+                                                            const ProjRed* red) {
+  if (stopped(red)) return;
+  const unsigned n = (unsigned)L.nx * L.ny * L.nz;
+  for (unsigned c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+    unsigned i, j, k;
+    level_ijk(L, c, i, j, k);
+    if (((i + j + k) & 1u) != color) {
+      if (init) L.x[c] = 0.f;
+      continue;
+    }
+    float s = 0.f, diag;
+    if (!init) level_gather(L, c, i, j, k, L.x, s, diag);
+    L.x[c] = L.invd[c] * (L.b[c] + s);
+  }
+}
+
+// Coarse right-hand side: the sum of the children's residuals b - A x.
+__global__ void __launch_bounds__(kProjThreads) k_mg_restrict(MgLevel F, MgLevel C, const ProjRed* red) {
+  if (stopped(red)) return;
+  const unsigned n = (unsigned)C.nx * C.ny * C.nz;
+  const unsigned fnx = F.nx, fny = F.ny, fnz = F.nz;
+  for (unsigned q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+    unsigned I, J, K;
+    level_ijk(C, q, I, J, K);
+    float acc = 0.f;
+    for (unsigned k = 2 * K; k < min(2 * K + 2, fnz); ++k)
+      for (unsigned j = 2 * J; j < min(2 * J + 2, fny); ++j)
+        for (unsigned i = 2 * I; i < min(2 * I + 2, fnx); ++i) {
+          const unsigned c = i + fnx * (j + fny * k);
+          float s, diag;
+          level_gather(F, c, i, j, k, F.x, s, diag);
+          acc += F.b[c] - (diag * F.x[c] - s);
+        }
+    C.b[q] = acc;
+  }
+}
+
+// x_fine += kMgOmega x_coarse(parent)
+__global__ void __launch_bounds__(kProjThreads) k_mg_prolong(MgLevel C, MgLevel F, const ProjRed* red) {
+  if (stopped(red)) return;
+  const unsigned n = (unsigned)F.nx * F.ny * F.nz;
+  for (unsigned c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+    unsigned i, j, k;
+    level_ijk(F, c, i, j, k);
+    F.x[c] = fmaf(kMgOmega, C.x[(i >> 1) + (unsigned)C.nx * ((j >> 1) + (unsigned)C.ny * (k >> 1))], F.x[c]);
+  }
+}
+
+// The coarsest level (at most 64 cells) in one CTA: red (from x = 0), then
+// kMgCoarsePairs (black, red) sweep pairs, x held in shared memory.
+constexpr int kMgCoarseMax = 64;
+__global__ void __launch_bounds__(kMgCoarseMax) k_mg_coarsest(MgLevel L, const ProjRed* red) {
+  __shared__ float sx[kMgCoarseMax];
+  if (stopped(red)) return;
+  const unsigned n = (unsigned)L.nx * L.ny * L.nz;
+  const unsigned c = threadIdx.x;
+  unsigned i = 0, j = 0, k = 0;
+  float invd = 0.f, b = 0.f;
+  if (c < n) {
+    level_ijk(L, c, i, j, k);
+    invd = L.invd[c];
+    b = L.b[c];
+  }
+  const unsigned color = (i + j + k) & 1u;
+  sx[c] = (c < n && color == 0u) ? invd * b : 0.f;
+  __syncthreads();
+  for (int p = 0; p < 2 * kMgCoarsePairs; ++p) {
+    const unsigned now = (p & 1) ? 0u : 1u;  // black, red, black, red, ...
+    float v = 0.f;
+    if (c < n && color == now) {
+      float s, diag;
+      level_gather(L, c, i, j, k, sx, s, diag);
+      v = invd * (b + s);
+    }
+    __syncthreads();
+    if (c < n && color == now) sx[c] = v;
+    __syncthreads();
+  }
+  if (c < n) L.x[c] = sx[c];
+}
+
+// ---- conjugate gradients on A e = r with the multigrid preconditioner ----
+
+// rho = r . z (z = M^-1 r from the V-cycle) into red->rz[cur].
+__global__ void __launch_bounds__(kProjThreads) k_cg_dot(int64_t n64, int cur, const float* __restrict__ r,
+                                                         const float* __restrict__ z, double* __restrict__ P,
+                                                         ProjRed* red) {
+  __shared__ double smem[32];
+  if (stopped(red)) return;
+  const unsigned n = (unsigned)n64;
+  KahanF k;
+  for (unsigned c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) k.add(r[c] * z[c]);
+  const double rz = block_sum((double)k.s, smem);
+  const double vals[1] = {rz};
+  double* const outs[1] = {&red->rz[cur]};
+  reduce_last<1>(vals, P, red, outs);
+}
+
+// d_new = z + beta d_old (beta = rho / rho_prev; 0 on a run's first
+// iteration), y = A d_new and d_new . y into red->dy.  d_old and d_new are
+// different buffers: neighbours' d_new is formed from their z and d_old.
+__global__ void __launch_bounds__(kProjThreads) k_cg_dir_apply(MgLevel L, int cur, const float* __restrict__ z,
                                                                const float* __restrict__ d_old,
                                                                float* __restrict__ d_new, float* __restrict__ y,
                                                                double* __restrict__ P, ProjRed* red) {
-  __shared__ float s_d[kTY + 2][kTX + 2];
-  __shared__ float s_a[kTY + 2][kTX + 2];
   __shared__ double smem[32];
-  if (block_flag(&red->done)) return;
+  if (stopped(red)) return;
   const float be = red->iters == 0 ? 0.f : (float)(red->rz[cur] / red->rz[cur ^ 1]);
-  const int nx = g.nx, ny = g.ny, nz = g.nz;
-  const int b = blockIdx.x;
-  const int bx = b % tiles_x, bt = b / tiles_x, by = bt % tiles_y, bz = bt / tiles_y;
-  const int tx = threadIdx.x % kTX, ty = threadIdx.x / kTX;
-  const int x0 = bx * kTX, y0 = by * kTY;
-  const int i = x0 + tx, j = y0 + ty;
-  const int z0 = bz * lz, z1 = min(z0 + lz, nz);
-  const bool act = i < nx && j < ny;
-  auto at = [&](int ii, int jj, int kk) -> unsigned {
-    return (unsigned)ii + (unsigned)nx * ((unsigned)jj + (unsigned)ny * (unsigned)kk);
-  };
-  auto dn = [&](unsigned c) -> float { return fmaf(be, d_old[c], invd[c] * r[c]); };
-  // this thread's entry of the tile's side ring (80 entries; corners are not needed)
-  int ri = -1, rj = -1, sx = 0, sy = 0;
-  {
-    const int q = threadIdx.x;
-    if (q < kTX) {
-      ri = x0 + q, rj = y0 - 1, sx = q + 1, sy = 0;
-    } else if (q < 2 * kTX) {
-      ri = x0 + q - kTX, rj = y0 + kTY, sx = q - kTX + 1, sy = kTY + 1;
-    } else if (q < 2 * kTX + kTY) {
-      ri = x0 - 1, rj = y0 + q - 2 * kTX, sx = 0, sy = q - 2 * kTX + 1;
-    } else if (q < 2 * kTX + 2 * kTY) {
-      ri = x0 + kTX, rj = y0 + q - 2 * kTX - kTY, sx = kTX + 1, sy = q - 2 * kTX - kTY + 1;
-    }
-  }
-  const bool ring = ri >= 0 && ri < nx && rj >= 0 && rj < ny;
-  float dm = 0.f, dc = 0.f, dp = 0.f, am = 0.f, ac = 0.f, apl = 0.f;
-  if (act) {
-    if (z0 > 0) {
-      const unsigned c = at(i, j, z0 - 1);
-      dm = dn(c);
-      am = ap32[c];
-    }
-    const unsigned c = at(i, j, z0);
-    dc = dn(c);
-    ac = ap32[c];
-  }
+  const unsigned nx = L.nx, ny = L.ny, nz = L.nz, nxy = nx * ny, n = nxy * nz;
   KahanF dyk;
-  for (int k = z0; k < z1; ++k) {
-    s_d[ty + 1][tx + 1] = dc;
-    s_a[ty + 1][tx + 1] = ac;
-    if (sx | sy) {  // a ring thread
-      float rd = 0.f, ra = 0.f;
-      if (ring) {
-        const unsigned c = at(ri, rj, k);
-        rd = dn(c);
-        ra = ap32[c];
-      }
-      s_d[sy][sx] = rd;
-      s_a[sy][sx] = ra;
-    }
-    __syncthreads();
-    if (act) {
-      if (k + 1 < nz) {
-        const unsigned c = at(i, j, k + 1);
-        dp = dn(c);
-        apl = ap32[c];
-      }
-      float acc = 0.f;
-      if (i > 0)
-        acc += 0.5f * (ac + s_a[ty + 1][tx]) * (dc - s_d[ty + 1][tx]);
-      else if (open & 1u)
-        acc += ac * dc;
-      if (i + 1 < nx)
-        acc += 0.5f * (ac + s_a[ty + 1][tx + 2]) * (dc - s_d[ty + 1][tx + 2]);
-      else if (open & 2u)
-        acc += ac * dc;
-      if (j > 0)
-        acc += 0.5f * (ac + s_a[ty][tx + 1]) * (dc - s_d[ty][tx + 1]);
-      else if (open & 4u)
-        acc += ac * dc;
-      if (j + 1 < ny)
-        acc += 0.5f * (ac + s_a[ty + 2][tx + 1]) * (dc - s_d[ty + 2][tx + 1]);
-      else if (open & 8u)
-        acc += ac * dc;
-      if (k > 0)
-        acc += 0.5f * (ac + am) * (dc - dm);
-      else if (open & 16u)
-        acc += ac * dc;
-      if (k + 1 < nz)
-        acc += 0.5f * (ac + apl) * (dc - dp);
-      else if (open & 32u)
-        acc += ac * dc;
-      const unsigned c = at(i, j, k);
-      d_new[c] = dc;
-      y[c] = acc;
-      dyk.add(dc * acc);
-    }
-    __syncthreads();
-    dm = dc;
-    dc = dp;
-    am = ac;
-    ac = apl;
+  for (unsigned c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+    unsigned i, j, k;
+    level_ijk(L, c, i, j, k);
+    // beta = 0 takes z alone (the old direction is not read into the sum)
+    auto dn = [&](unsigned q) { return be != 0.f ? fmaf(be, d_old[q], z[q]) : z[q]; };
+    const float dc = dn(c);
+    const unsigned fx = i + (nx + 1) * (j + ny * k);
+    const unsigned fy = i + nx * (j + (ny + 1) * k);
+    const float wxl = L.bx[fx], wxh = L.bx[fx + 1], wyl = L.by[fy], wyh = L.by[fy + nx], wzl = L.bz[c],
+                wzh = L.bz[c + nxy];
+    float acc = (((wxl + wxh) + (wyl + wyh)) + (wzl + wzh)) * dc;
+    if (i > 0) acc = fmaf(-wxl, dn(c - 1), acc);
+    if (i + 1 < nx) acc = fmaf(-wxh, dn(c + 1), acc);
+    if (j > 0) acc = fmaf(-wyl, dn(c - nx), acc);
+    if (j + 1 < ny) acc = fmaf(-wyh, dn(c + nx), acc);
+    if (k > 0) acc = fmaf(-wzl, dn(c - nxy), acc);
+    if (k + 1 < nz) acc = fmaf(-wzh, dn(c + nxy), acc);
+    d_new[c] = dc;
+    y[c] = acc;
+    dyk.add(dc * acc);
   }
   const double dy = block_sum((double)dyk.s, smem);
   const double vals[1] = {dy};
@@ -375,28 +489,27 @@ __global__ void __launch_bounds__(kProjThreads) k_cg_dir_apply(PGrid g, unsigned
   reduce_last<1>(vals, P, red, outs);
 }
 
-// CG step 2: alpha = rho / (d . y); e += alpha d; r -= alpha y; the new rho
-// = r . M^-1 r and r . r (four cells per thread and step, float4).  The last
-// block counts the iteration and sets the stop flag when r . r <= rr_stop.
-__global__ void __launch_bounds__(kProjThreads) k_cg_update(PGrid g, int cur, const float* __restrict__ d,
-                                                            const float* __restrict__ y, const float* __restrict__ invd,
-                                                            float* __restrict__ e, float* __restrict__ r,
-                                                            double* __restrict__ P, ProjRed* red) {
-  __shared__ double smem[64];
-  if (block_flag(&red->done)) return;
+// alpha = rho / (d . y); e += alpha d; r -= alpha y (float4); r . r into
+// red->rr.  The last block counts the iteration and sets the stop flag when
+// r . r <= rr_stop (or on a breakdown).
+__global__ void __launch_bounds__(kProjThreads) k_cg_update(int64_t n64, int cur, const float* __restrict__ d,
+                                                            const float* __restrict__ y, float* __restrict__ e,
+                                                            float* __restrict__ r, double* __restrict__ P,
+                                                            ProjRed* red) {
+  __shared__ double smem[32];
+  if (stopped(red)) return;
   const double dy = red->dy, rz = red->rz[cur];  // the same values in every block
   if (!(dy > 0.0) || !isfinite(rz)) {  // d = 0 (r = 0: converged) or breakdown: stop this run
     if (blockIdx.x == 0 && threadIdx.x == 0) red->done = 1;
     return;
   }
   const float al = (float)(rz / dy);
-  KahanF rzk, rrk;
-  const unsigned n = (unsigned)g.n, n4 = n / 4u;
+  KahanF rrk;
+  const unsigned n = (unsigned)n64, n4 = n / 4u;
   const unsigned t0 = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
   for (unsigned q = t0; q < n4; q += stride) {  // arrays are 256-byte aligned
     const float4 dq = reinterpret_cast<const float4*>(d)[q];
     const float4 yq = reinterpret_cast<const float4*>(y)[q];
-    const float4 iq = reinterpret_cast<const float4*>(invd)[q];
     float4 eq = reinterpret_cast<const float4*>(e)[q];
     float4 rq = reinterpret_cast<const float4*>(r)[q];
     eq.x = fmaf(al, dq.x, eq.x);
@@ -409,22 +522,18 @@ __global__ void __launch_bounds__(kProjThreads) k_cg_update(PGrid g, int cur, co
     rq.w = fmaf(-al, yq.w, rq.w);
     reinterpret_cast<float4*>(e)[q] = eq;
     reinterpret_cast<float4*>(r)[q] = rq;
-    rzk.add(rq.x * (iq.x * rq.x) + rq.y * (iq.y * rq.y) + rq.z * (iq.z * rq.z) + rq.w * (iq.w * rq.w));
     rrk.add(rq.x * rq.x + rq.y * rq.y + rq.z * rq.z + rq.w * rq.w);
   }
   for (unsigned c = 4u * n4 + t0; c < n; c += stride) {
-    const float dc = d[c];
-    e[c] = fmaf(al, dc, e[c]);
+    e[c] = fmaf(al, d[c], e[c]);
     const float rc = fmaf(-al, y[c], r[c]);
     r[c] = rc;
-    rzk.add(rc * (invd[c] * rc));
     rrk.add(rc * rc);
   }
-  double rz_new = (double)rzk.s, rr = (double)rrk.s;
-  block_sum2(rz_new, rr, smem);
-  const double vals[2] = {rz_new, rr};
-  double* const outs[2] = {&red->rz[cur ^ 1], &red->rr};
-  if (reduce_last<2>(vals, P, red, outs) && threadIdx.x == 0) {
+  const double rr = block_sum((double)rrk.s, smem);
+  const double vals[1] = {rr};
+  double* const outs[1] = {&red->rr};
+  if (reduce_last<1>(vals, P, red, outs) && threadIdx.x == 0) {
     red->iters += 1;
     if (!(red->rr > red->rr_stop)) red->done = 1;  // also stops on NaN
   }
@@ -494,31 +603,12 @@ __global__ void __launch_bounds__(kProjThreads) k_proj_faces(
 // ---- host side ----
 
 struct ProjWs {
-  float *ap32, *invd, *r, *d[2], *y, *e;  // d: the CG direction, double-buffered
-  double* P;    // 3 * max(blocks) partial sums
+  float *ap32, *r, *z, *d[2], *y, *e;  // d: the CG direction, double-buffered
+  double* P;                           // 2 * nblk partial sums
   ProjRed* red;
+  MgLevel lev[kMgMaxLevels];
+  int levels;
 };
-
-// Tiles and z-planes per CTA of k_cg_dir_apply: lz halves from 64 until the
-// grid has at least 6 CTAs per SM.
-struct TileGrid {
-  int tiles_x, tiles_y, lz, blocks;
-};
-static TileGrid tile_grid(const PGrid& g) {
-  int dev = 0, sms = 152;
-  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  TileGrid t;
-  t.tiles_x = (g.nx + kTX - 1) / kTX;
-  t.tiles_y = (g.ny + kTY - 1) / kTY;
-  t.lz = 64;
-  for (;;) {
-    const int64_t b = (int64_t)t.tiles_x * t.tiles_y * ((g.nz + t.lz - 1) / t.lz);
-    if (b >= 6 * (int64_t)(sms > 0 ? sms : 152) || t.lz <= 4) break;
-    t.lz /= 2;
-  }
-  t.blocks = (int)((int64_t)t.tiles_x * t.tiles_y * ((g.nz + t.lz - 1) / t.lz));
-  return t;
-}
 
 static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
@@ -530,26 +620,48 @@ static int proj_blocks(int64_t n) {
   return (int)(want < cap ? (want > 0 ? want : 1) : cap);
 }
 
-// Workspace for n cells and nblk blocks (laid out by the same walk that
-// measures it).
-static size_t proj_layout(int64_t n, int nblk, char* base, ProjWs* W) {
-  // nblk: the most CTAs any kernel with partial sums launches
+// Workspace of the call (laid out by the same walk that measures it): the
+// FP32 CG vectors, the partial sums, the scalars and the multigrid levels
+// (halving each axis until every axis has at most 4 cells).
+static size_t proj_layout(const PGrid& g, int nblk, char* base, ProjWs* W) {
   size_t off = 0;
   auto take = [&](size_t bytes) {
     char* p = base ? base + off : nullptr;
     off += align256(bytes);
     return p;
   };
+  const size_t n = (size_t)g.n;
   ProjWs w;
-  w.ap32 = (float*)take(4 * (size_t)n);
-  w.invd = (float*)take(4 * (size_t)n);
-  w.r = (float*)take(4 * (size_t)n);
-  w.d[0] = (float*)take(4 * (size_t)n);
-  w.d[1] = (float*)take(4 * (size_t)n);
-  w.y = (float*)take(4 * (size_t)n);
-  w.e = (float*)take(4 * (size_t)n);
-  w.P = (double*)take(3 * 8 * (size_t)nblk);
+  w.ap32 = (float*)take(4 * n);
+  w.r = (float*)take(4 * n);
+  w.z = (float*)take(4 * n);
+  w.d[0] = (float*)take(4 * n);
+  w.d[1] = (float*)take(4 * n);
+  w.y = (float*)take(4 * n);
+  w.e = (float*)take(4 * n);
+  w.P = (double*)take(2 * 8 * (size_t)nblk);
   w.red = (ProjRed*)take(sizeof(ProjRed));
+  int nx = g.nx, ny = g.ny, nz = g.nz;
+  w.levels = 0;
+  for (;;) {
+    MgLevel& L = w.lev[w.levels];
+    L.nx = nx, L.ny = ny, L.nz = nz;
+    const size_t nl = (size_t)nx * ny * nz;
+    L.bx = (float*)take(4 * (size_t)(nx + 1) * ny * nz);
+    L.by = (float*)take(4 * (size_t)nx * (ny + 1) * nz);
+    L.bz = (float*)take(4 * (size_t)nx * ny * (nz + 1));
+    L.invd = (float*)take(4 * nl);
+    if (w.levels == 0) {
+      L.x = w.z;
+      L.b = w.r;
+    } else {
+      L.x = (float*)take(4 * nl);
+      L.b = (float*)take(4 * nl);
+    }
+    ++w.levels;
+    if ((nx <= 4 && ny <= 4 && nz <= 4) || w.levels == kMgMaxLevels) break;
+    nx = (nx + 1) / 2, ny = (ny + 1) / 2, nz = (nz + 1) / 2;
+  }
   if (W) *W = w;
   return off;
 }
@@ -563,7 +675,7 @@ static int proj_grid(const GicGrid* grid, PGrid* g) {
   g->nz = grid->nz;
   g->nxy = (int64_t)grid->nx * grid->ny;
   g->n = g->nxy * grid->nz;
-  if (g->n >= ((int64_t)1 << 31)) return set_error(GIC_ERR_INVALID, "gic_project: 2^31 cells or more");
+  if (g->n >= ((int64_t)1 << 30)) return set_error(GIC_ERR_INVALID, "gic_project: 2^30 cells or more");
   return GIC_OK;
 }
 
@@ -583,9 +695,7 @@ extern "C" int gic_project_workspace_size(const GicGrid* grid, size_t* bytes) {
   int rc = proj_grid(grid, &g);
   if (rc) return rc;
   if (!bytes) return set_error(GIC_ERR_INVALID, "gic_project_workspace_size: bytes is NULL");
-  const TileGrid tg = tile_grid(g);
-  const int nb = proj_blocks(g.n);
-  *bytes = proj_layout(g.n, nb > tg.blocks ? nb : tg.blocks, nullptr, nullptr);
+  *bytes = proj_layout(g, proj_blocks(g.n), nullptr, nullptr);
   return GIC_OK;
 }
 
@@ -625,15 +735,16 @@ extern "C" int gic_project(const GicGrid* grid, const GicProjParams* P, const do
     if (P->open[s]) open_bits |= 1u << s;
   }
   const int nblk = proj_blocks(g.n);
-  const TileGrid tg = tile_grid(g);
-  const int pblk = nblk > tg.blocks ? nblk : tg.blocks;  // partial-sum slots
-  const size_t need = proj_layout(g.n, pblk, nullptr, nullptr);
+  const size_t need = proj_layout(g, nblk, nullptr, nullptr);
   if (!ws || ws_bytes < need)
     return set_error(GIC_ERR_WORKSPACE, "gic_project: workspace of %zu bytes needed, %zu given", need, ws_bytes);
   if ((uintptr_t)ws % 256) return set_error(GIC_ERR_ALIGN, "gic_project: workspace must be 256-byte aligned");
   cudaStream_t st = (cudaStream_t)stream_;
   ProjWs W;
-  proj_layout(g.n, pblk, (char*)ws, &W);
+  proj_layout(g, nblk, (char*)ws, &W);
+  if (W.levels == kMgMaxLevels && !(W.lev[kMgMaxLevels - 1].nx <= 4 && W.lev[kMgMaxLevels - 1].ny <= 4 &&
+                                    W.lev[kMgMaxLevels - 1].nz <= 4))
+    return set_error(GIC_ERR_INVALID, "gic_project: grid too large for the multigrid hierarchy");
   uint32_t* status = status_word();
   const double h = grid->dx;
   ProjScales S;
@@ -647,18 +758,51 @@ extern "C" int gic_project(const GicGrid* grid, const GicProjParams* P, const do
   ProjRed hr;
   int64_t launches = 0;
   int rc2 = GIC_OK;
+  auto lblocks = [&](const MgLevel& L) { return proj_blocks((int64_t)L.nx * L.ny * L.nz); };
+  auto fblocks = [&](const MgLevel& L) {
+    return proj_blocks((int64_t)(L.nx + 1) * L.ny * L.nz + (int64_t)L.nx * (L.ny + 1) * L.nz +
+                       (int64_t)L.nx * L.ny * (L.nz + 1));
+  };
 
-  if (cudaMemsetAsync(W.red, 0, sizeof(ProjRed), st) != cudaSuccess)
-    return set_error(GIC_ERR_CUDA, "gic_project: clearing the solver's scalars failed");
-  // one CG iteration; all arguments but the parity are fixed for the call
+  if (cudaMemsetAsync(W.red, 0, sizeof(ProjRed), st) != cudaSuccess ||
+      cudaMemsetAsync(W.d[0], 0, sizeof(float) * g.n, st) != cudaSuccess ||
+      cudaMemsetAsync(W.d[1], 0, sizeof(float) * g.n, st) != cudaSuccess)
+    return set_error(GIC_ERR_CUDA, "gic_project: clearing the workspace failed");
+  // the operator's face weights on every level
+  k_proj_prep<<<nblk, kProjThreads, 0, st>>>(g, alpha_s, P->alpha_s_max, W.ap32);
+  k_mg_faces0<<<fblocks(W.lev[0]), kProjThreads, 0, st>>>(W.lev[0], open_bits, W.ap32);
+  k_mg_diag<<<lblocks(W.lev[0]), kProjThreads, 0, st>>>(W.lev[0]);
+  launches += 3;
+  for (int l = 1; l < W.levels; ++l) {
+    k_mg_coarsen<<<fblocks(W.lev[l]), kProjThreads, 0, st>>>(W.lev[l - 1], W.lev[l]);
+    k_mg_diag<<<lblocks(W.lev[l]), kProjThreads, 0, st>>>(W.lev[l]);
+    launches += 2;
+  }
+  // one preconditioned CG iteration: z = V-cycle(r), rho = r . z, the new
+  // direction with y = A d, the updates; all arguments but the parity are
+  // fixed for the call
+  int per_iter = 0;
   auto cg_iteration = [&](int cur, cudaStream_t s_) {
-    k_cg_dir_apply<<<tg.blocks, kProjThreads, 0, s_>>>(g, open_bits, tg.lz, tg.tiles_x, tg.tiles_y, cur, W.ap32,
-                                                       W.r, W.invd, W.d[cur], W.d[cur ^ 1], W.y, W.P, W.red);
-    k_cg_update<<<nblk, kProjThreads, 0, s_>>>(g, cur, W.d[cur ^ 1], W.y, W.invd, W.e, W.r, W.P, W.red);
+    const int top = W.levels - 1;
+    for (int l = 0; l < top; ++l) {
+      k_mg_smooth<<<lblocks(W.lev[l]), kProjThreads, 0, s_>>>(W.lev[l], 0u, 1, W.red);
+      k_mg_smooth<<<lblocks(W.lev[l]), kProjThreads, 0, s_>>>(W.lev[l], 1u, 0, W.red);
+      k_mg_restrict<<<lblocks(W.lev[l + 1]), kProjThreads, 0, s_>>>(W.lev[l], W.lev[l + 1], W.red);
+    }
+    k_mg_coarsest<<<1, kMgCoarseMax, 0, s_>>>(W.lev[top], W.red);
+    for (int l = top - 1; l >= 0; --l) {
+      k_mg_prolong<<<lblocks(W.lev[l]), kProjThreads, 0, s_>>>(W.lev[l + 1], W.lev[l], W.red);
+      k_mg_smooth<<<lblocks(W.lev[l]), kProjThreads, 0, s_>>>(W.lev[l], 1u, 0, W.red);
+      k_mg_smooth<<<lblocks(W.lev[l]), kProjThreads, 0, s_>>>(W.lev[l], 0u, 0, W.red);
+    }
+    k_cg_dot<<<nblk, kProjThreads, 0, s_>>>(g.n, cur, W.r, W.z, W.P, W.red);
+    k_cg_dir_apply<<<nblk, kProjThreads, 0, s_>>>(W.lev[0], cur, W.z, W.d[cur ^ 1], W.d[cur], W.y, W.P, W.red);
+    k_cg_update<<<nblk, kProjThreads, 0, s_>>>(g.n, cur, W.d[cur], W.y, W.e, W.r, W.P, W.red);
+    per_iter = 6 * top + 4;
   };
   // kChunk iterations as one CUDA graph (kChunk even: the parities repeat),
   // built when the first CG run needs it
-  constexpr int kChunk = 16;
+  constexpr int kChunk = 4;
   cudaGraphExec_t chunk = nullptr;
   auto build_chunk = [&]() -> int {
     cudaStream_t cs = nullptr;
@@ -680,9 +824,7 @@ extern "C" int gic_project(const GicGrid* grid, const GicProjParams* P, const do
     }
     return GIC_OK;
   };
-  k_proj_prep<<<nblk, kProjThreads, 0, st>>>(g, alpha_s, P->alpha_s_max, W.ap32);
-  k_proj_diag<<<nblk, kProjThreads, 0, st>>>(g, open_bits, W.ap32, W.invd);
-  launches += 2;
+
   for (int which = 1; which <= 2 && rc2 == GIC_OK; ++which) {
     double* p = which == 1 ? p1 : p2;
     const int sys = which - 1;
@@ -691,8 +833,8 @@ extern "C" int gic_project(const GicGrid* grid, const GicProjParams* P, const do
       break;
     }
     for (int outer = 0;; ++outer) {
-      k_proj_residual<<<nblk, kProjThreads, 0, st>>>(g, which, S, alpha_s, alpha_star, u, v, w, p, W.invd, W.r, W.d[0],
-                                                     W.e, P->inner_tol * P->inner_tol, W.P, W.red, status);
+      k_proj_residual<<<nblk, kProjThreads, 0, st>>>(g, which, S, alpha_s, alpha_star, u, v, w, p, W.r, W.e,
+                                                     P->inner_tol * P->inner_tol, W.P, W.red, status);
       ++launches;
       if ((rc2 = read_red(W.red, &hr, st))) break;
       if (!isfinite(hr.rr64) || !isfinite(hr.bb)) {
@@ -706,8 +848,9 @@ extern "C" int gic_project(const GicGrid* grid, const GicProjParams* P, const do
         break;
       }
       if (outer >= P->max_outer) break;
-      // FP32 CG on A e = r to a reduction of inner_tol (of the FP32 copy's r . r):
-      // graph launches of kChunk iterations, the stop flag read after each
+      // the FP32 preconditioned CG on A e = r to a reduction of inner_tol (of
+      // the FP32 copy's r . r): graph launches of kChunk iterations, the stop
+      // flag read after each
       int it = 0;
       for (;;) {
         if (P->max_inner - it >= kChunk) {
@@ -717,11 +860,11 @@ extern "C" int gic_project(const GicGrid* grid, const GicProjParams* P, const do
             break;
           }
           it += kChunk;
-          launches += 2 * kChunk;
+          launches += (int64_t)per_iter * kChunk;
         } else {
           for (; it < P->max_inner; ++it) {
             cg_iteration(it & 1, st);
-            launches += 2;
+            launches += per_iter;
           }
         }
         cudaError_t le = cudaGetLastError();

@@ -128,7 +128,7 @@ def test_iteration_limits_report_not_converged():
     """A solve cut short by max_outer returns with converged = 0 and the
     residual it reached (larger than tol)."""
     c = gi.projection_case(seed=40, shape=(30, 30, 30))
-    _, info = run_gpu(c, tol=1e-12, max_outer=1, max_inner=5)
+    _, info = run_gpu(c, tol=1e-12, inner_tol=1e-10, max_outer=1, max_inner=5)
     assert info.converged[0] == 0 and info.converged[1] == 0
     assert info.outer[0] == 1 and info.inner[0] == 5
     assert info.rel_residual[0] > 1e-12
