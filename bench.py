@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--profile-substeps", type=int, default=0,
                     help="run this many substeps of the workload once, untimed, and exit (for ncu captures)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"], help="precision of --profile-substeps")
+    ap.add_argument("--profile-projection", action="store_true",
+                    help="with --profile-substeps: then one gic_project call on the window's alpha_s (tol 1e-9)")
     ap.add_argument("--profile-window", action="store_true",
                     help="with --profile-substeps: the differentiable window (forward + backward) instead")
     ap.add_argument("--profile-direct", action="store_true",
@@ -529,7 +531,7 @@ def run_projection(prob, sim, gic, torch, dev, stream, tol, reps=3):
         torch.cuda.synchronize()
         if rep:
             times.append(a.elapsed_time(b))
-    ms = statistics.mean(times)
+    ms = statistics.mean(times) if times else float("nan")
     iters = int(info.inner[0] + info.inner[1])
     gbs = PROJ_CG_BYTES * n * iters / (ms / 1000) / 1e9
     return {"ms_per_call": ms, "cells": n, "tol": tol, "outer": list(info.outer), "inner": list(info.inner),
@@ -562,10 +564,14 @@ def run_profile(args):
         ((x - target) ** 2).sum(dim=1).mean().backward()
     else:
         sim.run(args.profile_substeps, sort_every=args.profile_direct)
+    extra = {}
+    if args.profile_projection:
+        out = run_projection(prob, sim, gic, torch, sim.device, torch.cuda.current_stream(), 1e-9, reps=0)
+        extra = {"projection_outer": out["outer"], "projection_inner": out["inner"]}
     torch.cuda.synchronize()
     st = gic.gic_check_status()
     print(json.dumps({"profile_substeps": args.profile_substeps, "workload": prob.name, "precision": args.precision,
-                      "device_status": st, "launches": gic.launch_count()}))
+                      "device_status": st, "launches": gic.launch_count(), **extra}))
 
 
 def main():
