@@ -223,9 +223,9 @@ __global__ void __launch_bounds__(kProjThreads) k_proj_residual(
 // the preconditioner is symmetric), restricts the residual by summing the
 // children, adds kMgOmega times the interpolated coarse correction (the
 // constant interpolation under-corrects; 1.6 keeps the preconditioner
-// positive definite and halves the CG iterations against 1.0), and solves the
-// coarsest level (every axis <= 4 cells) with one CTA doing a palindromic
-// sequence of Gauss-Seidel sweeps.
+// positive definite and halves the CG iterations against 1.0), and runs the
+// small levels, down to the coarsest (every axis <= 4 cells, solved by a
+// palindromic sequence of Gauss-Seidel sweeps), in one CTA.
 constexpr float kMgOmega = 1.6f;
 constexpr int kMgCoarsePairs = 8;  // (black, red) sweep pairs after the first red sweep on the coarsest level
 constexpr int kMgMaxLevels = 16;
@@ -348,14 +348,16 @@ __global__ void __launch_bounds__(kProjThreads) k_mg_diag(MgLevel L) {
   }
 }
 
+// The V-cycle's passes over the cells t0, t0 + stride, ... of a level: the
+// kernels below run them grid-wide, k_mg_tail within one CTA.
+
 // One Gauss-Seidel half sweep: the cells with (i + j + k) % 2 == color get
 // x_c = (b_c + sum beta_f x_nb) / diag_c.  init: x is taken as 0 (the other
 // color is written 0).
-__global__ void __launch_bounds__(kProjThreads) k_mg_smooth(MgLevel L, unsigned color, int init,
-                                                            const ProjRed* red) {
-  if (stopped(red)) return;
+__device__ __forceinline__ void mg_smooth_range(const MgLevel& L, unsigned color, int init, unsigned t0,
+                                                unsigned stride) {
   const unsigned n = (unsigned)L.nx * L.ny * L.nz;
-  for (unsigned c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+  for (unsigned c = t0; c < n; c += stride) {
     unsigned i, j, k;
     level_ijk(L, c, i, j, k);
     if (((i + j + k) & 1u) != color) {
@@ -369,11 +371,10 @@ __global__ void __launch_bounds__(kProjThreads) k_mg_smooth(MgLevel L, unsigned 
 }
 
 // Coarse right-hand side: the sum of the children's residuals b - A x.
-__global__ void __launch_bounds__(kProjThreads) k_mg_restrict(MgLevel F, MgLevel C, const ProjRed* red) {
-  if (stopped(red)) return;
+__device__ __forceinline__ void mg_restrict_range(const MgLevel& F, const MgLevel& C, unsigned t0, unsigned stride) {
   const unsigned n = (unsigned)C.nx * C.ny * C.nz;
   const unsigned fnx = F.nx, fny = F.ny, fnz = F.nz;
-  for (unsigned q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+  for (unsigned q = t0; q < n; q += stride) {
     unsigned I, J, K;
     level_ijk(C, q, I, J, K);
     float acc = 0.f;
@@ -390,47 +391,70 @@ __global__ void __launch_bounds__(kProjThreads) k_mg_restrict(MgLevel F, MgLevel
 }
 
 // x_fine += kMgOmega x_coarse(parent)
-__global__ void __launch_bounds__(kProjThreads) k_mg_prolong(MgLevel C, MgLevel F, const ProjRed* red) {
-  if (stopped(red)) return;
+__device__ __forceinline__ void mg_prolong_range(const MgLevel& C, const MgLevel& F, unsigned t0, unsigned stride) {
   const unsigned n = (unsigned)F.nx * F.ny * F.nz;
-  for (unsigned c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+  for (unsigned c = t0; c < n; c += stride) {
     unsigned i, j, k;
     level_ijk(F, c, i, j, k);
     F.x[c] = fmaf(kMgOmega, C.x[(i >> 1) + (unsigned)C.nx * ((j >> 1) + (unsigned)C.ny * (k >> 1))], F.x[c]);
   }
 }
 
-// The coarsest level (at most 64 cells) in one CTA: red (from x = 0), then
-// kMgCoarsePairs (black, red) sweep pairs, x held in shared memory.
-constexpr int kMgCoarseMax = 64;
-__global__ void __launch_bounds__(kMgCoarseMax) k_mg_coarsest(MgLevel L, const ProjRed* red) {
-  __shared__ float sx[kMgCoarseMax];
+__global__ void __launch_bounds__(kProjThreads) k_mg_smooth(MgLevel L, unsigned color, int init,
+                                                            const ProjRed* red) {
   if (stopped(red)) return;
-  const unsigned n = (unsigned)L.nx * L.ny * L.nz;
-  const unsigned c = threadIdx.x;
-  unsigned i = 0, j = 0, k = 0;
-  float invd = 0.f, b = 0.f;
-  if (c < n) {
-    level_ijk(L, c, i, j, k);
-    invd = L.invd[c];
-    b = L.b[c];
+  mg_smooth_range(L, color, init, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+
+__global__ void __launch_bounds__(kProjThreads) k_mg_restrict(MgLevel F, MgLevel C, const ProjRed* red) {
+  if (stopped(red)) return;
+  mg_restrict_range(F, C, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+
+__global__ void __launch_bounds__(kProjThreads) k_mg_prolong(MgLevel C, MgLevel F, const ProjRed* red) {
+  if (stopped(red)) return;
+  mg_prolong_range(C, F, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+
+// The levels from `first` (at most kMgTailCells cells) down to the coarsest
+// in one CTA, with a barrier between passes (their launches would cost more
+// than their work): the same passes as the grid-wide V-cycle, and on the
+// coarsest level (every axis <= 4 cells) red from x = 0, then kMgCoarsePairs
+// (black, red) sweep pairs.  Same-color cells do not touch, so a half sweep
+// reads only values no thread of the pass writes.
+constexpr int kMgTailThreads = 1024;
+constexpr int kMgTailCells = 4096;
+struct MgLevels {
+  MgLevel l[kMgMaxLevels];
+};
+
+__global__ void __launch_bounds__(kMgTailThreads) k_mg_tail(MgLevels Ls, int first, int top, const ProjRed* red) {
+  if (stopped(red)) return;
+  const unsigned t0 = threadIdx.x, st = blockDim.x;
+  for (int l = first; l < top; ++l) {
+    mg_smooth_range(Ls.l[l], 0u, 1, t0, st);
+    __syncthreads();
+    mg_smooth_range(Ls.l[l], 1u, 0, t0, st);
+    __syncthreads();
+    mg_restrict_range(Ls.l[l], Ls.l[l + 1], t0, st);
+    __syncthreads();
   }
-  const unsigned color = (i + j + k) & 1u;
-  sx[c] = (c < n && color == 0u) ? invd * b : 0.f;
+  mg_smooth_range(Ls.l[top], 0u, 1, t0, st);
   __syncthreads();
-  for (int p = 0; p < 2 * kMgCoarsePairs; ++p) {
-    const unsigned now = (p & 1) ? 0u : 1u;  // black, red, black, red, ...
-    float v = 0.f;
-    if (c < n && color == now) {
-      float s, diag;
-      level_gather(L, c, i, j, k, sx, s, diag);
-      v = invd * (b + s);
-    }
+  for (int p = 0; p < kMgCoarsePairs; ++p) {
+    mg_smooth_range(Ls.l[top], 1u, 0, t0, st);
     __syncthreads();
-    if (c < n && color == now) sx[c] = v;
+    mg_smooth_range(Ls.l[top], 0u, 0, t0, st);
     __syncthreads();
   }
-  if (c < n) L.x[c] = sx[c];
+  for (int l = top - 1; l >= first; --l) {
+    mg_prolong_range(Ls.l[l + 1], Ls.l[l], t0, st);
+    __syncthreads();
+    mg_smooth_range(Ls.l[l], 1u, 0, t0, st);
+    __syncthreads();
+    mg_smooth_range(Ls.l[l], 0u, 0, t0, st);
+    __syncthreads();
+  }
 }
 
 // ---- conjugate gradients on A e = r with the multigrid preconditioner ----
@@ -459,7 +483,8 @@ __global__ void __launch_bounds__(kProjThreads) k_cg_dir_apply(MgLevel L, int cu
                                                                double* __restrict__ P, ProjRed* red) {
   __shared__ double smem[32];
   if (stopped(red)) return;
-  const float be = red->iters == 0 ? 0.f : (float)(red->rz[cur] / red->rz[cur ^ 1]);
+  // beta in FP32 (a double divide per thread would occupy GB300's slow FP64 pipe)
+  const float be = red->iters == 0 ? 0.f : (float)red->rz[cur] / (float)red->rz[cur ^ 1];
   const unsigned nx = L.nx, ny = L.ny, nz = L.nz, nxy = nx * ny, n = nxy * nz;
   KahanF dyk;
   for (unsigned c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
@@ -503,7 +528,7 @@ __global__ void __launch_bounds__(kProjThreads) k_cg_update(int64_t n64, int cur
     if (blockIdx.x == 0 && threadIdx.x == 0) red->done = 1;
     return;
   }
-  const float al = (float)(rz / dy);
+  const float al = (float)rz / (float)dy;  // FP32, as beta
   KahanF rrk;
   const unsigned n = (unsigned)n64, n4 = n / 4u;
   const unsigned t0 = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
@@ -778,19 +803,24 @@ extern "C" int gic_project(const GicGrid* grid, const GicProjParams* P, const do
     k_mg_diag<<<lblocks(W.lev[l]), kProjThreads, 0, st>>>(W.lev[l]);
     launches += 2;
   }
+  // the levels from `first` on run in one CTA (k_mg_tail)
+  MgLevels levels;
+  for (int l = 0; l < W.levels; ++l) levels.l[l] = W.lev[l];
+  int first = 0;
+  while (first < W.levels - 1 && (int64_t)W.lev[first].nx * W.lev[first].ny * W.lev[first].nz > kMgTailCells) ++first;
   // one preconditioned CG iteration: z = V-cycle(r), rho = r . z, the new
   // direction with y = A d, the updates; all arguments but the parity are
   // fixed for the call
   int per_iter = 0;
   auto cg_iteration = [&](int cur, cudaStream_t s_) {
     const int top = W.levels - 1;
-    for (int l = 0; l < top; ++l) {
+    for (int l = 0; l < first; ++l) {
       k_mg_smooth<<<lblocks(W.lev[l]), kProjThreads, 0, s_>>>(W.lev[l], 0u, 1, W.red);
       k_mg_smooth<<<lblocks(W.lev[l]), kProjThreads, 0, s_>>>(W.lev[l], 1u, 0, W.red);
       k_mg_restrict<<<lblocks(W.lev[l + 1]), kProjThreads, 0, s_>>>(W.lev[l], W.lev[l + 1], W.red);
     }
-    k_mg_coarsest<<<1, kMgCoarseMax, 0, s_>>>(W.lev[top], W.red);
-    for (int l = top - 1; l >= 0; --l) {
+    k_mg_tail<<<1, kMgTailThreads, 0, s_>>>(levels, first, top, W.red);
+    for (int l = first - 1; l >= 0; --l) {
       k_mg_prolong<<<lblocks(W.lev[l]), kProjThreads, 0, s_>>>(W.lev[l + 1], W.lev[l], W.red);
       k_mg_smooth<<<lblocks(W.lev[l]), kProjThreads, 0, s_>>>(W.lev[l], 1u, 0, W.red);
       k_mg_smooth<<<lblocks(W.lev[l]), kProjThreads, 0, s_>>>(W.lev[l], 0u, 0, W.red);
@@ -798,7 +828,7 @@ extern "C" int gic_project(const GicGrid* grid, const GicProjParams* P, const do
     k_cg_dot<<<nblk, kProjThreads, 0, s_>>>(g.n, cur, W.r, W.z, W.P, W.red);
     k_cg_dir_apply<<<nblk, kProjThreads, 0, s_>>>(W.lev[0], cur, W.z, W.d[cur ^ 1], W.d[cur], W.y, W.P, W.red);
     k_cg_update<<<nblk, kProjThreads, 0, s_>>>(g.n, cur, W.d[cur], W.y, W.e, W.r, W.P, W.red);
-    per_iter = 6 * top + 4;
+    per_iter = 6 * first + 4;
   };
   // kChunk iterations as one CUDA graph (kChunk even: the parities repeat),
   // built when the first CG run needs it
