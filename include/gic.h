@@ -451,7 +451,9 @@ int gic_window_forward_host(const GicGrid* grid, const GicParams* params, int64_
  * dx = 0 on its faces).  At least one side must be open.  The equations are
  * solved multiplied by alpha_f' (a symmetric positive definite system) by
  * mixed-precision iterative refinement: FP64 residuals and solution, FP32
- * Jacobi-preconditioned conjugate gradients for each correction. */
+ * conjugate gradients preconditioned by a geometric multigrid V-cycle
+ * (Galerkin face weights, red-black Gauss-Seidel) for each correction.
+ * Grids of 2^30 cells or more are rejected. */
 typedef struct GicProjParams {
   double dt;                   /* fluid step (s) */
   double rho_f;                /* fluid density rho_0 */
