@@ -37,16 +37,6 @@ struct PGrid {
   int open[6];      // -x, +x, -y, +y, -z, +z
 };
 
-__device__ __forceinline__ void cell_ijk(const PGrid& g, int64_t c, int& i, int& j, int& k) {
-  const unsigned cu = (unsigned)c, nxy = (unsigned)g.nxy, nx = (unsigned)g.nx;
-  const unsigned kk = cu / nxy;
-  const unsigned r = cu - kk * nxy;
-  const unsigned jj = r / nx;
-  k = (int)kk;
-  j = (int)jj;
-  i = (int)(r - jj * nx);
-}
-
 // Device scalars of the solver (in the workspace).
 struct ProjRed {
   double dy;       // d . A d
@@ -87,26 +77,6 @@ __device__ __forceinline__ bool reduce_last(const double (&v)[NV], double* __res
   return true;
 }
 
-// Visits the six faces of cell (i, j, k): f(neighbour index or -1, face
-// kind) with kind 0 = interior face, 1 = open side, 2 = solid side.
-template <typename F>
-__device__ __forceinline__ void for_faces(const PGrid& g, int i, int j, int k, int64_t c, F f) {
-  const int idx[3] = {i, j, k};
-  const int n[3] = {g.nx, g.ny, g.nz};
-  const int64_t stride[3] = {1, g.nx, g.nxy};
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    if (idx[a] > 0)
-      f(c - stride[a], 0);
-    else
-      f((int64_t)-1, g.open[2 * a] ? 1 : 2);
-    if (idx[a] < n[a] - 1)
-      f(c + stride[a], 0);
-    else
-      f((int64_t)-1, g.open[2 * a + 1] ? 1 : 2);
-  }
-}
-
 // Compensated FP32 sum (Kahan): the CG's per-thread dot-product partials stay
 // off the FP64 pipe, whose rate on GB300 is a small fraction of FP32's.
 struct KahanF {
@@ -138,56 +108,76 @@ struct ProjScales {
   double rmin, rmax, amax;
 };
 
+// FP64 face weights of the operator (computed once per call, so that each
+// residual pass spends its FP64 work on the stencil itself): the mean
+// alpha_f' of the two cells, the inner cell's on an open side, 0 on a solid
+// side.  Face arrays as the velocity components, x fastest.
+__global__ void __launch_bounds__(kProjThreads) k_proj_faces64(PGrid g, unsigned open, const double* __restrict__ alpha_s,
+                                                               double amax, double* __restrict__ fx,
+                                                               double* __restrict__ fy, double* __restrict__ fz) {
+  const unsigned nx = g.nx, ny = g.ny, nz = g.nz;
+  const unsigned nu = (nx + 1) * ny * nz, nv = nx * (ny + 1) * nz, nw = nx * ny * (nz + 1);
+  for (unsigned q = blockIdx.x * blockDim.x + threadIdx.x; q < nu + nv + nw; q += gridDim.x * blockDim.x) {
+    unsigned a, f;
+    if (q < nu) {
+      a = 0, f = q;
+    } else if (q < nu + nv) {
+      a = 1, f = q - nu;
+    } else {
+      a = 2, f = q - nu - nv;
+    }
+    const unsigned sx = nx + (a == 0), sy = ny + (a == 1);
+    const unsigned k = f / (sx * sy), rem = f - k * sx * sy, j = rem / sx, i = rem - j * sx;
+    const unsigned pos = a == 0 ? i : (a == 1 ? j : k);
+    const unsigned m = a == 0 ? nx : (a == 1 ? ny : nz);
+    const unsigned stride = a == 0 ? 1u : (a == 1 ? nx : nx * ny);
+    // the cell above the face (valid when pos < m) and the one below (pos > 0)
+    const unsigned c_hi = i + nx * (j + ny * k), c_lo = c_hi - stride;
+    double wgt;
+    if (pos > 0 && pos < m)
+      wgt = 0.5 * (target_fraction(alpha_s[c_hi], amax) + target_fraction(alpha_s[c_lo], amax));
+    else if (pos == 0)
+      wgt = (open >> (2 * a)) & 1u ? target_fraction(alpha_s[c_hi], amax) : 0.0;
+    else
+      wgt = (open >> (2 * a + 1)) & 1u ? target_fraction(alpha_s[c_lo], amax) : 0.0;
+    (a == 0 ? fx : (a == 1 ? fy : fz))[f] = wgt;
+  }
+}
+
 // FP64 residual r = b - A p of system `which` (1: velocity, 2: density);
 // starts the FP32 correction run: r32 = r, e = 0, and arms its stop test.
 // Scalars: ||r||^2 (FP64) and ||b||^2.
 __global__ void __launch_bounds__(kProjThreads) k_proj_residual(
     PGrid g, int which, ProjScales S, const double* __restrict__ alpha_s, const float* __restrict__ alpha_star,
     const float* __restrict__ u, const float* __restrict__ v, const float* __restrict__ w,
+    const double* __restrict__ fx, const double* __restrict__ fy, const double* __restrict__ fz,
     const double* __restrict__ p, float* __restrict__ r32, float* __restrict__ e32, double inner_tol2,
     double* __restrict__ P, ProjRed* red, uint32_t* status) {
   __shared__ double smem[64];
   double rr = 0.0, bb = 0.0;
-  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < g.n; c += (int64_t)gridDim.x * blockDim.x) {
-    int i, j, k;
-    cell_ijk(g, c, i, j, k);
-    const double ac = target_fraction(alpha_s[c], S.amax);
+  const unsigned n = (unsigned)g.n, nx = g.nx, ny = g.ny, nz = g.nz, nxy = nx * ny;
+  for (unsigned c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+    const unsigned k = c / nxy, rem = c - k * nxy, j = rem / nx, i = rem - j * nx;
+    const unsigned fu = i + (nx + 1) * (j + ny * k), fv = i + nx * (j + (ny + 1) * k);
+    // the six face weights: low and high x, y, z (0 on solid sides)
+    const double w0 = fx[fu], w1 = fx[fu + 1], w2 = fy[fv], w3 = fy[fv + nx], w4 = fz[c], w5 = fz[c + nxy];
     const double pc = p[c];
+    // (A p)_c as differences (a neighbour beyond an open side is 0)
     double Ap = 0.0;
-    for_faces(g, i, j, k, c, [&](int64_t nb, int kind) {
-      if (kind == 0)
-        Ap += 0.5 * (ac + target_fraction(alpha_s[nb], S.amax)) * (pc - p[nb]);
-      else if (kind == 1)
-        Ap += ac * pc;
-    });
+    Ap = fma(w0, i > 0 ? pc - p[c - 1] : pc, Ap);
+    Ap = fma(w1, i + 1 < nx ? pc - p[c + 1] : pc, Ap);
+    Ap = fma(w2, j > 0 ? pc - p[c - nx] : pc, Ap);
+    Ap = fma(w3, j + 1 < ny ? pc - p[c + nx] : pc, Ap);
+    Ap = fma(w4, k > 0 ? pc - p[c - nxy] : pc, Ap);
+    Ap = fma(w5, k + 1 < nz ? pc - p[c + nxy] : pc, Ap);
     double b;
     if (which == 1) {
       // b1 = (rho h / dt) (sum over low faces - sum over high faces) of beta v*
-      const int64_t nxf = g.nx + 1, nyf = g.ny + 1;
-      const int64_t fu = i + nxf * (j + (int64_t)g.ny * k);
-      const int64_t fv = i + (int64_t)g.nx * (j + nyf * k);
-      const int64_t fw = c;  // w: i + nx (j + ny k) on z-face k
-      const double vlo[3] = {u[fu], v[fv], w[fw]};
-      const double vhi[3] = {u[fu + 1], v[fv + g.nx], w[fw + g.nxy]};
-      const int idx[3] = {i, j, k};
-      const int nn[3] = {g.nx, g.ny, g.nz};
-      const int64_t stride[3] = {1, g.nx, g.nxy};
-      double flux = 0.0;
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        double blo, bhi;
-        if (idx[a] > 0)
-          blo = 0.5 * (ac + target_fraction(alpha_s[c - stride[a]], S.amax));
-        else
-          blo = g.open[2 * a] ? ac : 0.0;
-        if (idx[a] < nn[a] - 1)
-          bhi = 0.5 * (ac + target_fraction(alpha_s[c + stride[a]], S.amax));
-        else
-          bhi = g.open[2 * a + 1] ? ac : 0.0;
-        flux += blo * vlo[a] - bhi * vhi[a];
-      }
+      const double flux = (w0 * (double)u[fu] - w1 * (double)u[fu + 1]) + (w2 * (double)v[fv] - w3 * (double)v[fv + nx]) +
+                          (w4 * (double)w[c] - w5 * (double)w[c + nxy]);
       b = S.vel * flux;
     } else {
+      const double ac = target_fraction(alpha_s[c], S.amax);
       const double q = (double)alpha_star[c] / ac;
       const double ratio = q < S.rmin ? S.rmin : (q > S.rmax ? S.rmax : q);  // NaN stays NaN
       b = S.den * ac * (1.0 - ratio);
@@ -628,6 +618,7 @@ __global__ void __launch_bounds__(kProjThreads) k_proj_faces(
 // ---- host side ----
 
 struct ProjWs {
+  double *fx, *fy, *fz;                // FP64 face weights (the residual's operator)
   float *ap32, *r, *z, *d[2], *y, *e;  // d: the CG direction, double-buffered
   double* P;                           // 2 * nblk partial sums
   ProjRed* red;
@@ -657,6 +648,9 @@ static size_t proj_layout(const PGrid& g, int nblk, char* base, ProjWs* W) {
   };
   const size_t n = (size_t)g.n;
   ProjWs w;
+  w.fx = (double*)take(8 * (size_t)(g.nx + 1) * g.ny * g.nz);
+  w.fy = (double*)take(8 * (size_t)g.nx * (g.ny + 1) * g.nz);
+  w.fz = (double*)take(8 * (size_t)g.nx * g.ny * (g.nz + 1));
   w.ap32 = (float*)take(4 * n);
   w.r = (float*)take(4 * n);
   w.z = (float*)take(4 * n);
@@ -794,10 +788,11 @@ extern "C" int gic_project(const GicGrid* grid, const GicProjParams* P, const do
       cudaMemsetAsync(W.d[1], 0, sizeof(float) * g.n, st) != cudaSuccess)
     return set_error(GIC_ERR_CUDA, "gic_project: clearing the workspace failed");
   // the operator's face weights on every level
+  k_proj_faces64<<<fblocks(W.lev[0]), kProjThreads, 0, st>>>(g, open_bits, alpha_s, P->alpha_s_max, W.fx, W.fy, W.fz);
   k_proj_prep<<<nblk, kProjThreads, 0, st>>>(g, alpha_s, P->alpha_s_max, W.ap32);
   k_mg_faces0<<<fblocks(W.lev[0]), kProjThreads, 0, st>>>(W.lev[0], open_bits, W.ap32);
   k_mg_diag<<<lblocks(W.lev[0]), kProjThreads, 0, st>>>(W.lev[0]);
-  launches += 3;
+  launches += 4;
   for (int l = 1; l < W.levels; ++l) {
     k_mg_coarsen<<<fblocks(W.lev[l]), kProjThreads, 0, st>>>(W.lev[l - 1], W.lev[l]);
     k_mg_diag<<<lblocks(W.lev[l]), kProjThreads, 0, st>>>(W.lev[l]);
@@ -863,8 +858,8 @@ extern "C" int gic_project(const GicGrid* grid, const GicProjParams* P, const do
       break;
     }
     for (int outer = 0;; ++outer) {
-      k_proj_residual<<<nblk, kProjThreads, 0, st>>>(g, which, S, alpha_s, alpha_star, u, v, w, p, W.r, W.e,
-                                                     P->inner_tol * P->inner_tol, W.P, W.red, status);
+      k_proj_residual<<<nblk, kProjThreads, 0, st>>>(g, which, S, alpha_s, alpha_star, u, v, w, W.fx, W.fy, W.fz, p,
+                                                     W.r, W.e, P->inner_tol * P->inner_tol, W.P, W.red, status);
       ++launches;
       if ((rc2 = read_red(W.red, &hr, st))) break;
       if (!isfinite(hr.rr64) || !isfinite(hr.bb)) {
