@@ -22,8 +22,6 @@
 #include <math.h>
 #include <string.h>
 
-#include <vector>
-
 #include "gic_internal.cuh"
 
 namespace gic {

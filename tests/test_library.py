@@ -116,3 +116,5 @@ def test_projection_validation_on_the_host():
     assert "all three" in gic.last_error()
     assert call(g, good, nbytes=a - 1) == -3
     assert call(g, good, ws=C.c_void_p((1 << 20) + 64)) == -4
+    huge = gic.GicGrid(1024, 1024, 1024, 1, 0.1, (C.c_double * 3)(0, 0, 0))  # 2^30 cells: 32-bit indices
+    assert call(huge, good) == -1 and "2^30" in gic.last_error()
