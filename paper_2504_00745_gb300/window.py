@@ -12,7 +12,7 @@ streams only.
 from __future__ import annotations
 
 from dataclasses import dataclass, field
-from typing import List, Optional
+from typing import List, Optional, Tuple
 
 import torch
 
@@ -229,6 +229,66 @@ class Simulator:
 
     def status(self, clear=True) -> int:
         return gic.gic_check_status(clear=clear)
+
+    # ------------------------------------------------------------ checkpoint / resume
+    def save(self, path, step: int = 0, meta: Optional[dict] = None):
+        """Writes the current state (A) to `path` (see save_checkpoint)."""
+        save_checkpoint(path, self.A, step, meta)
+
+    def resume(self, path) -> Tuple[int, dict]:
+        """Loads a state written by save() into A (the next substep rebuilds
+        the Verlet lists); returns (step, meta).  The file must hold a state of
+        this simulator's size and precision."""
+        st, step, meta = load_checkpoint(path, self.device)
+        if st.n != self.n or st.precision != self.precision:
+            raise ValueError(f"checkpoint holds {st.n} granules of precision {st.precision}, "
+                             f"the simulator {self.n} of precision {self.precision}")
+        self.load_state(st)
+        return step, meta
+
+
+# ---------------------------------------------------------------------------
+# checkpoint files
+# ---------------------------------------------------------------------------
+
+CHECKPOINT_FORMAT = "gic-state-1"
+
+
+def save_checkpoint(path, state: State, step: int = 0, meta: Optional[dict] = None):
+    """Writes a granule state to a file with torch.save: the raw arrays in the
+    library's layout (cell, pos, vel, id, posf; moved to the host, bit for
+    bit), the precision, a step counter and a dict of plain metadata (numbers,
+    strings, lists: e.g. the workload's name and parameters), so that a long
+    run can stop and resume exactly."""
+    d = {"format": CHECKPOINT_FORMAT, "precision": int(state.precision), "step": int(step),
+         "meta": dict(meta or {}), "cell": state.cell.detach().cpu(), "pos": state.pos.detach().cpu(),
+         "vel": state.vel.detach().cpu(), "id": None if state.id is None else state.id.detach().cpu(),
+         "posf": None if state.posf is None else state.posf.detach().cpu()}
+    torch.save(d, path)
+
+
+def load_checkpoint(path, device="cuda") -> Tuple[State, int, dict]:
+    """Reads a file written by save_checkpoint: (state on `device`, step,
+    meta).  Raises ValueError for a file of another format or with arrays
+    whose shapes or types do not form a state."""
+    d = torch.load(path, map_location="cpu", weights_only=True)
+    if not isinstance(d, dict) or d.get("format") != CHECKPOINT_FORMAT:
+        raise ValueError(f"{path}: not a {CHECKPOINT_FORMAT} checkpoint")
+    prec = int(d["precision"])
+    if prec not in (GIC_FP32, GIC_FP64):
+        raise ValueError(f"{path}: unknown precision {prec}")
+    cell, pos, vel, ids, posf = d["cell"], d["pos"], d["vel"], d["id"], d["posf"]
+    n = int(cell.shape[0])
+    real = torch.float32 if prec == GIC_FP32 else torch.float64
+    pos_dtype = torch.int32 if prec == GIC_FP32 else torch.float64
+    ok = (cell.dtype == torch.int32 and cell.shape == (n,) and pos.dtype == pos_dtype and tuple(pos.shape) == (n, 4)
+          and vel.dtype == real and tuple(vel.shape) == (n, 4)
+          and (ids is None or (ids.dtype == torch.int32 and tuple(ids.shape) == (n,)))
+          and (posf is None or (prec == GIC_FP32 and posf.dtype == torch.float32 and tuple(posf.shape) == (n, 4))))
+    if not ok:
+        raise ValueError(f"{path}: arrays do not form a granule state of precision {prec}")
+    dev = lambda t: None if t is None else t.to(device).contiguous()
+    return State(dev(cell), dev(pos), dev(vel), dev(ids), prec, dev(posf)), int(d["step"]), dict(d["meta"])
 
 
 # ---------------------------------------------------------------------------
