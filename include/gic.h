@@ -171,9 +171,11 @@ int gic_sort(const GicGrid* grid, const GicGranules* in, GicGranules* out, int32
  *   radix-sort scratch is a static array of about 4.3 MB compiled into the
  *   library: it holds at most gic_sort_static_max_n() granules (262,144);
  *   larger n returns GIC_ERR_INVALID without launching anything.
- *   The array exists once per device that loads the library, until exit.  The
- *   first call on each device looks up its device address (make that first
- *   call before any stream capture).  Every call on a device uses the same
+ *   The array exists once per device that loads the library, until exit.
+ *   Every call looks up the array's device address on the current device
+ *   (no allocation; a cudaDeviceReset in between is harmless); the first
+ *   call on a device also loads the library's kernels there, so make that
+ *   first call before any stream capture.  Every call on a device uses the same
  *   array: calls that can run at the same time on the GPU (different streams
  *   without ordering) race and must be serialised by the caller.  The array
  *   keeps the last call's contents; nothing in it has to start at zero.

@@ -43,7 +43,9 @@
  *    momentum4 is unknown during the sand step and dropped);
  *  - exchange force per granule f = F_p + F_d + m_a (a_f - a_s), scattered at
  *    the substep's starting position, scaled by -dt'/dt;
- *  - walls: the six box planes, infinite mass, at rest, same contact law.
+ *  - walls: the six box planes, infinite mass, at rest, same contact law;
+ *  - a granule that would leave the box is put back on the boundary it
+ *    crossed (and flagged); its velocity is kept.
  */
 #include <math.h>
 #include <stdint.h>
@@ -547,7 +549,12 @@ void or_g2p(const or_grid* G, const or_params* P, int64_t n, const double* x, co
 /* ------------------------------------------------------------------------ */
 
 /* (m + m_a) a = m_a a_f + F_c + F_fl + m g,  m_a = (2/3) pi r^3 rho_f;
- * v' = v + dt a;  x' = x + dt v';  exchange force f = F_fl + m_a (a_f - a). */
+ * v' = v + dt a;  x' = x + dt v';  exchange force f = F_fl + m_a (a_f - a).
+ * A granule whose new position leaves the box is put back on the boundary
+ * it crossed, per axis: onto the lower plane itself, or onto the largest
+ * position below the upper plane that the canonical encoding holds (h_c
+ * 2^-30 inside), and flagged; its velocity is kept.  (The paper has no
+ * rule for this; positions live in the grid's cells, so none lies outside.) */
 void or_integrate(const or_grid* G, const or_params* P, int64_t n, const double* x, const double* v, const double* r,
                   const double* F_c, const double* F_fl, const double* a_f, double* x_new, double* v_new, double* f_ex,
                   uint32_t* status) {
@@ -562,11 +569,17 @@ void or_integrate(const or_grid* G, const or_params* P, int64_t n, const double*
       double acc = (F_c[3 * i + a] + F_fl[3 * i + a] + m * g[a] + ma * a_f[3 * i + a]) / (m + ma);
       double vn = v[3 * i + a] + P->dt * acc;
       double xn = x[3 * i + a] + P->dt * vn;
+      if (!isfinite(vn) || !isfinite(xn)) *status |= OR_NONFINITE;
+      if (xn < lo[a]) {
+        xn = lo[a];
+        *status |= OR_OUT_OF_DOMAIN;
+      } else if (xn >= hi[a]) {
+        xn = hi[a] - G->dx / G->k / 1073741824.0;
+        *status |= OR_OUT_OF_DOMAIN;
+      }
       v_new[3 * i + a] = vn;
       x_new[3 * i + a] = xn;
       f_ex[3 * i + a] = F_fl[3 * i + a] + ma * (a_f[3 * i + a] - acc);
-      if (!(xn >= lo[a] && xn < hi[a])) *status |= OR_OUT_OF_DOMAIN;
-      if (!isfinite(vn) || !isfinite(xn)) *status |= OR_NONFINITE;
     }
   }
 }

@@ -262,18 +262,122 @@ __global__ void __launch_bounds__(kP2GThreads, 2) k_p2g_f32(DGrid G, DParams<flo
   if (sums) p2g_sums(sums, (long long)S);
 }
 
-// In place: 64-bit fixed-point alpha_s -> double; sums[0] and sums[1] (integer
-// totals of the deposits and of V_i / dx^3) -> sum_c alpha_s dx^3, sum_i V_i.
-__global__ void k_alpha_finish_f32(double* __restrict__ a, int64_t m, double dx3, double* __restrict__ sums) {
+// In place: 64-bit fixed-point alpha_s -> double.
+__global__ void k_alpha_finish_f32(double* __restrict__ a, int64_t m) {
   long long* ai = reinterpret_cast<long long*>(a);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
     a[i] = i64_scaled_to_double(ai[i], -53);
-  if (sums && blockIdx.x == 0 && threadIdx.x == 0) {  // both sums were accumulated as 2^-53 integers
-    long long tot = *reinterpret_cast<long long*>(&sums[0]);
-    long long vol = *reinterpret_cast<long long*>(&sums[1]);
-    sums[0] = i64_scaled_to_double(tot, -53) * dx3;
-    sums[1] = i64_scaled_to_double(vol, -53) * dx3;
+}
+
+// ---- FP32 path: exact conservation totals ----
+//
+// Both totals are unsigned 128-bit integers in 2^-53 units: sum_i S_i, added
+// by the scatter into the 16 bytes of sums[0..1] (p2g_sums), and sum_c
+// alpha_s(c), formed here from the cells' integers before they are
+// converted.  Every granule deposits exactly S_i, so the two are equal; each
+// is rounded once to a double and multiplied by dx^3.  The cell total is one
+// cluster of kTotalCtas CTAs: every thread sums its cells in 128 bits, a CTA
+// reduces its threads', and CTA 0 reads the other CTAs' partial totals
+// from their shared memory (distributed shared memory of the cluster), so
+// no global scratch word is needed and the result does not depend on timing.
+struct U128 {
+  unsigned long long lo, hi;
+};
+__device__ __forceinline__ void add128(U128& a, unsigned long long lo, unsigned long long hi) {
+  const unsigned long long l = a.lo + lo;
+  a.hi += hi + (l < a.lo ? 1ull : 0ull);
+  a.lo = l;
+}
+
+// v * 2^e2 rounded to the nearest double (ties to even), v an unsigned 128-bit integer.
+__device__ __forceinline__ double u128_scaled_to_double(U128 v, int e2) {
+  if (v.hi == 0 && v.lo < (1ull << 63)) return i64_scaled_to_double((long long)v.lo, e2);
+  const int msb = v.hi ? 127 - __clzll(v.hi) : 63;
+  const int sh = msb - 52;  // 11 .. 75 low bits are dropped
+  unsigned long long m;     // v >> sh: 53 bits
+  bool above, tie;          // the dropped bits against half a unit of m
+  if (sh < 64) {
+    m = (v.hi << (64 - sh)) | (v.lo >> sh);
+    const unsigned long long rem = v.lo & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+    above = rem > half;
+    tie = rem == half;
+  } else if (sh == 64) {
+    m = v.hi;
+    above = v.lo > (1ull << 63);
+    tie = v.lo == (1ull << 63);
+  } else {
+    m = v.hi >> (sh - 64);
+    const unsigned long long rh = v.hi & ((1ull << (sh - 64)) - 1ull), half = 1ull << (sh - 65);
+    above = rh > half || (rh == half && v.lo != 0);
+    tie = rh == half && v.lo == 0;
   }
+  int e = msb;
+  if (above || (tie && (m & 1ull))) {
+    ++m;
+    if (m == (1ull << 53)) {
+      m >>= 1;
+      ++e;
+    }
+  }
+  const unsigned long long be = (unsigned long long)(e + e2 + 1023);
+  return __longlong_as_double((long long)((be << 52) | (m & ((1ull << 52) - 1ull))));
+}
+
+constexpr int kTotalCtas = 8;  // one portable cluster
+constexpr int kTotalThreads = 1024;
+
+__device__ __forceinline__ unsigned cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// 64-bit load from the shared memory of CTA `rank` of the cluster, at the
+// address that `p` has in this CTA's shared memory
+__device__ __forceinline__ unsigned long long ld_cluster_u64(const void* p, unsigned rank) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  unsigned ra;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rank));
+  unsigned long long v;
+  asm volatile("ld.shared::cluster.u64 %0, [%1];" : "=l"(v) : "r"(ra) : "memory");
+  return v;
+}
+
+__global__ void __cluster_dims__(kTotalCtas, 1, 1) __launch_bounds__(kTotalThreads)
+    k_alpha_total_f32(const unsigned long long* __restrict__ a, int64_t m, double dx3, double* __restrict__ sums) {
+  __shared__ unsigned long long s_lo[kTotalThreads / 32], s_hi[kTotalThreads / 32];
+  __shared__ unsigned long long part[2];
+  U128 t{0ull, 0ull};
+  for (int64_t i = blockIdx.x * (int64_t)kTotalThreads + threadIdx.x; i < m; i += (int64_t)kTotalCtas * kTotalThreads)
+    add128(t, __ldg(&a[i]), 0ull);
+  for (int off = 16; off > 0; off >>= 1) {
+    const unsigned long long lo = __shfl_down_sync(0xffffffffu, t.lo, off);
+    const unsigned long long hi = __shfl_down_sync(0xffffffffu, t.hi, off);
+    add128(t, lo, hi);
+  }
+  if (lane_id() == 0) {
+    s_lo[threadIdx.x >> 5] = t.lo;
+    s_hi[threadIdx.x >> 5] = t.hi;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    U128 c{0ull, 0ull};
+    for (int w = 0; w < kTotalThreads / 32; ++w) add128(c, s_lo[w], s_hi[w]);
+    part[0] = c.lo;
+    part[1] = c.hi;
+  }
+  cluster_sync();  // every CTA's partial total is in its shared memory
+  if (cluster_rank() == 0 && threadIdx.x == 0) {
+    U128 cells{0ull, 0ull};
+    for (unsigned r = 0; r < kTotalCtas; ++r) add128(cells, ld_cluster_u64(&part[0], r), ld_cluster_u64(&part[1], r));
+    const U128 grains{*reinterpret_cast<const unsigned long long*>(&sums[1]),
+                      *reinterpret_cast<const unsigned long long*>(&sums[0])};
+    sums[0] = u128_scaled_to_double(cells, -53) * dx3;
+    sums[1] = u128_scaled_to_double(grains, -53) * dx3;
+  }
+  cluster_sync();  // no CTA leaves while CTA 0 may still read its shared memory
 }
 
 // Adjoint of P2G: G2P-shaped gathers of the grid gradients.
@@ -340,7 +444,12 @@ int alpha_begin(double* alpha_s, int64_t ncell, double* sums2, cudaStream_t stre
 
 int alpha_end(const DGrid& G, int32_t precision, double* alpha_s, int64_t ncell, double* sums2, cudaStream_t stream) {
   if (precision == GIC_FP32) {
-    k_alpha_finish_f32<<<1184, 256, 0, stream>>>(alpha_s, ncell, G.dx * G.dx * G.dx, sums2);
+    if (sums2) {
+      k_alpha_total_f32<<<kTotalCtas, kTotalThreads, 0, stream>>>((const unsigned long long*)alpha_s, ncell,
+                                                                   G.dx * G.dx * G.dx, sums2);
+      count_launches(1);
+    }
+    k_alpha_finish_f32<<<1184, 256, 0, stream>>>(alpha_s, ncell);
     count_launches(1);
   } else if (sums2) {
     k_alpha_sum<<<592, 256, 0, stream>>>(alpha_s, ncell, G.dx * G.dx * G.dx, sums2);
@@ -455,7 +564,12 @@ extern "C" int gic_p2g(const GicGrid* grid, const GicParams* params, const GicGr
   }
   if (alpha_s && old_->precision == GIC_FP32) {
     // the FP32 path accumulated 64-bit fixed point: convert in place
-    k_alpha_finish_f32<<<1184, 256, 0, stream>>>(alpha_s, ncell, G.dx * G.dx * G.dx, sums2);
+    if (sums2) {
+      k_alpha_total_f32<<<kTotalCtas, kTotalThreads, 0, stream>>>((const unsigned long long*)alpha_s, ncell,
+                                                                   G.dx * G.dx * G.dx, sums2);
+      ++launches;
+    }
+    k_alpha_finish_f32<<<1184, 256, 0, stream>>>(alpha_s, ncell);
     ++launches;
   } else if (sums2) {
     k_alpha_sum<<<592, 256, 0, stream>>>(alpha_s, ncell, G.dx * G.dx * G.dx, sums2);

@@ -415,13 +415,18 @@ __device__ __forceinline__ void p2g_flush(P2GShared& sh, const P2GBox& B, const 
   }
 }
 
-// Exact integer warp totals of sum_i V_i / dx^3 into both sums (every granule
-// deposits exactly its S).
+// Exact integer total of sum_i S_i (S_i = V_i / dx^3 in 2^-53 units, the
+// amount every granule deposits) while the scatter runs: a 128-bit unsigned
+// integer held in the 16 bytes of sums[0..1] (low word in sums[1], high word
+// in sums[0]); a warp adds its total (< 2^59) to the low word and carries into
+// the high word when the low word wraps, so the sum is exact and independent
+// of the order of the atomics.  k_alpha_total_f32 turns it into sum_i V_i.
 __device__ __forceinline__ void p2g_sums(double* sums, long long v) {
   for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
   if (lane_id() == 0 && v != 0) {
-    atomicAdd((unsigned long long*)&sums[0], (unsigned long long)v);
-    atomicAdd((unsigned long long*)&sums[1], (unsigned long long)v);
+    const unsigned long long add = (unsigned long long)v;
+    const unsigned long long old = atomicAdd((unsigned long long*)&sums[1], add);
+    if (old + add < old) atomicAdd((unsigned long long*)&sums[0], 1ull);
   }
 }
 

@@ -11,7 +11,6 @@
 // Stability: inside a tile each warp ranks 4 consecutive chunks of 32 keys in
 // order, warps own consecutive sub-ranges and tiles are offset by the counts
 // of earlier tiles, so equal keys keep their input order in every pass.
-#include <mutex>
 
 #include "gic_internal.cuh"
 
@@ -462,27 +461,19 @@ constexpr size_t kStaticSortBytes =
 
 static __device__ __align__(256) unsigned char g_static_sort_scratch[kStaticSortBytes];
 
-namespace {
-std::mutex g_static_mu;
-void* g_static_ptr[64] = {nullptr};
-}  // namespace
-
-// Device address of the static scratch on the current device, looked up once
-// per device (host code may not use the symbol's name as an address).
+// Device address of the static scratch on the current device (host code may
+// not use the symbol's name as an address).  It is looked up on every call
+// rather than cached: a cudaDeviceReset in the same process reloads the
+// module, after which a cached address would point at freed memory.  The
+// lookup allocates nothing; the first one on a device loads the module
+// (lazy loading), which is why that first call must precede any stream
+// capture.
 static int static_scratch(void** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return set_error(GIC_ERR_CUDA, "gic_sort_static: %s", cudaGetErrorString(e));
-  if (dev < 0 || dev >= 64) return set_error(GIC_ERR_INVALID, "gic_sort_static: device index %d unsupported", dev);
-  std::lock_guard<std::mutex> lk(g_static_mu);
-  if (!g_static_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_static_sort_scratch);
-    if (e != cudaSuccess || !p)
-      return set_error(GIC_ERR_CUDA, "gic_sort_static: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
-    g_static_ptr[dev] = p;
-  }
-  *out = g_static_ptr[dev];
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_static_sort_scratch);
+  if (e != cudaSuccess || !p)
+    return set_error(GIC_ERR_CUDA, "gic_sort_static: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+  *out = p;
   return GIC_OK;
 }
 

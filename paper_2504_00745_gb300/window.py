@@ -231,15 +231,24 @@ class Simulator:
         return gic.gic_check_status(clear=clear)
 
     # ------------------------------------------------------------ checkpoint / resume
-    def save(self, path, step: int = 0, meta: Optional[dict] = None):
-        """Writes the current state (A) to `path` (see save_checkpoint)."""
-        save_checkpoint(path, self.A, step, meta)
+    def save(self, path, step: int = 0, meta: Optional[dict] = None, stream=None):
+        """Writes the current state (A) and this simulator's grid to `path`
+        (see save_checkpoint).  The copy to the host waits for `stream` (the
+        stream the substeps ran on; default: torch's current stream) and for
+        torch's current stream, so a save after substeps on a side stream
+        sees their results."""
+        if stream is not None:
+            stream.synchronize()
+        torch.cuda.current_stream(self.device).synchronize()
+        save_checkpoint(path, self.A, step, meta, grid=self.grid_obj)
 
     def resume(self, path) -> Tuple[int, dict]:
         """Loads a state written by save() into A (the next substep rebuilds
         the Verlet lists); returns (step, meta).  The file must hold a state of
-        this simulator's size and precision."""
-        st, step, meta = load_checkpoint(path, self.device)
+        this simulator's size, precision and grid (positions are stored
+        relative to the contact cells of that grid: on another grid they
+        would mean other places)."""
+        st, step, meta = load_checkpoint(path, self.device, grid=self.grid_obj)
         if st.n != self.n or st.precision != self.precision:
             raise ValueError(f"checkpoint holds {st.n} granules of precision {st.precision}, "
                              f"the simulator {self.n} of precision {self.precision}")
@@ -254,26 +263,46 @@ class Simulator:
 CHECKPOINT_FORMAT = "gic-state-1"
 
 
-def save_checkpoint(path, state: State, step: int = 0, meta: Optional[dict] = None):
+def grid_record(grid) -> dict:
+    """The fields of a grid that give a stored state its meaning (positions
+    are contact-cell ids plus offsets in units of h_c = dx / k_contact)."""
+    return {"nx": int(grid.nx), "ny": int(grid.ny), "nz": int(grid.nz), "dx": float(grid.dx),
+            "origin": [float(o) for o in grid.origin], "k_contact": int(grid.k_contact)}
+
+
+def save_checkpoint(path, state: State, step: int = 0, meta: Optional[dict] = None, grid=None):
     """Writes a granule state to a file with torch.save: the raw arrays in the
     library's layout (cell, pos, vel, id, posf; moved to the host, bit for
-    bit), the precision, a step counter and a dict of plain metadata (numbers,
-    strings, lists: e.g. the workload's name and parameters), so that a long
-    run can stop and resume exactly."""
+    bit), the precision, the grid the positions refer to (any object with
+    nx, ny, nz, dx, origin, k_contact; recommended: without it the file can
+    only be loaded without a grid check), a step counter and a dict of plain
+    metadata (numbers, strings, lists: e.g. the workload's name and
+    parameters), so that a long run can stop and resume exactly.  The state
+    is copied with .cpu(), which waits for torch's current stream only: after
+    work on another stream, synchronise that stream first (Simulator.save
+    does)."""
     d = {"format": CHECKPOINT_FORMAT, "precision": int(state.precision), "step": int(step),
+         "grid": None if grid is None else grid_record(grid),
          "meta": dict(meta or {}), "cell": state.cell.detach().cpu(), "pos": state.pos.detach().cpu(),
          "vel": state.vel.detach().cpu(), "id": None if state.id is None else state.id.detach().cpu(),
          "posf": None if state.posf is None else state.posf.detach().cpu()}
     torch.save(d, path)
 
 
-def load_checkpoint(path, device="cuda") -> Tuple[State, int, dict]:
+def load_checkpoint(path, device="cuda", grid=None) -> Tuple[State, int, dict]:
     """Reads a file written by save_checkpoint: (state on `device`, step,
-    meta).  Raises ValueError for a file of another format or with arrays
-    whose shapes or types do not form a state."""
+    meta).  Raises ValueError for a file of another format, with arrays
+    whose shapes or types do not form a state, or -- when `grid` is given --
+    for a file saved on another grid or without a grid record."""
     d = torch.load(path, map_location="cpu", weights_only=True)
     if not isinstance(d, dict) or d.get("format") != CHECKPOINT_FORMAT:
         raise ValueError(f"{path}: not a {CHECKPOINT_FORMAT} checkpoint")
+    if grid is not None:
+        saved = d.get("grid")
+        if saved is None:
+            raise ValueError(f"{path}: the checkpoint records no grid, so its positions cannot be checked")
+        if saved != grid_record(grid):
+            raise ValueError(f"{path}: saved on grid {saved}, not on {grid_record(grid)}")
     prec = int(d["precision"])
     if prec not in (GIC_FP32, GIC_FP64):
         raise ValueError(f"{path}: unknown precision {prec}")

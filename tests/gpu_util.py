@@ -107,3 +107,22 @@ def onset_taint(prob, K, eps=2e-10):
 # several times the largest F_s entry where granules are sparse; bound
 # relative to max |F_s|.
 FS_TOL_FP32 = 1e-5
+
+
+def assert_elementwise(got, want, tol, floor, what=""):
+    """Element by element: |got_i - want_i| <= tol * max(|want_i|, floor).
+
+    `floor` is an absolute scale below which an element is compared to the
+    floor rather than to itself (each test states where its floor comes
+    from).  Reports the worst element on failure."""
+    got = np.asarray(got, dtype=np.float64)
+    want = np.asarray(want, dtype=np.float64)
+    assert got.shape == want.shape, f"{what}: shape {got.shape} != {want.shape}"
+    err = np.abs(got - want)
+    bound = tol * np.maximum(np.abs(want), floor)
+    ratio = err / bound
+    k = int(np.argmax(ratio)) if ratio.size else 0
+    assert ratio.size == 0 or ratio.flat[k] <= 1.0, (
+        f"{what}: element {np.unravel_index(k, got.shape)} got {got.flat[k]:.9e} want {want.flat[k]:.9e} "
+        f"(|err| {err.flat[k]:.3e} > bound {bound.flat[k]:.3e}; floor {floor:.3e})")
+    return float(ratio.max()) if ratio.size else 0.0

@@ -4,7 +4,21 @@ Per kernel: the same upstream gradients on the same state; per window: the
 gradients of L = mean |x_K - target|^2 w.r.t. the initial velocities, c_drag
 and mu from GicWindow (checkpoints every `ckpt` substeps, recompute) against
 oracle.run_adjoint and against central finite differences of the FP64 GPU
-forward.  Tolerance: relative 1e-3 (FP32), 1e-8 (FP64).
+forward.  Every array is compared element by element,
+|g_i - g_o,i| <= tol * max(|g_o,i|, floor), never through a norm:
+
+* kernel adjoints (random upstream gradients): floor = 1e-2 max_k |g_o,k|.
+  An element sums at most a few tens of terms no larger than the largest
+  element; FP32 evaluates each to a few ulps, so an element that cancels to
+  near zero can be off by ~1e-6 of the largest one, which tol * floor
+  (2e-6 of the largest at tol 2e-4) allows and nothing larger;
+* window gradients of L = mean |x_K - target|^2 w.r.t. v0:
+  floor = 10 (2 / N) K dt' eps_x / tol, the change of an element when x_K
+  moves by the position tolerance eps_x of the precision (1e-5 dx FP32,
+  1e-12 dx FP64) with a contact amplification of 10: dL/dv0_i =
+  (2 / N) (x_K,i - target_i) dx_K,i/dv0_i and dx_K/dv0 = K dt' for a free
+  granule.  Scalars (c_drag, mu) are compared relatively, with no floor.
+Tolerance: 1e-3 (FP32), 1e-8 (FP64) for windows.
 """
 import dataclasses
 
@@ -14,7 +28,7 @@ import torch
 
 import gic_inputs as gi
 import oracle
-from gpu_util import FP32, FP64, by_id, oracle_inputs, shuffled, sim_for
+from gpu_util import FP32, FP64, assert_elementwise, by_id, oracle_inputs, shuffled, sim_for
 from paper_2504_00745_gb300 import gic
 from paper_2504_00745_gb300.window import Simulator, window_loss_and_grads
 
@@ -22,10 +36,17 @@ pytestmark = pytest.mark.gpu
 PRECS = [FP32, FP64]
 
 
-def _rel(a, b):
-    a = np.asarray(a, float)
-    b = np.asarray(b, float)
-    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+def _kernel_ok(got, want, tol, what):
+    """A kernel adjoint, element by element (floor 1e-2 of the largest element)."""
+    want = np.asarray(want, float)
+    assert_elementwise(got, want, tol, 1e-2 * np.abs(want).max(), what)
+
+
+def _gv0_ok(got, want, prob, prec, tol, what="g_v0"):
+    """A window's dL/dv0, element by element (floor from the position tolerance)."""
+    eps_x = (1e-5 if prec == FP32 else 1e-12) * prob.grid.dx
+    floor = 10.0 * (2.0 / prob.n) * prob.K * prob.params.dt_sub * eps_x / tol
+    assert_elementwise(got, want, tol, floor, what)
 
 
 def _t4(a, prec):
@@ -52,8 +73,8 @@ def test_contact_adjoint_kernel(name, prec):
     x, v, r = oracle_inputs(prob)
     gx_o, gv_o, gmu_o = oracle.contact_adj(prob.grid, prob.params, x, v, r, lam)
     tol = 2e-4 if prec == FP32 else 1e-9
-    assert _rel(by_id(gpos, sim.B.id)[:, :3], gx_o) < tol
-    assert _rel(by_id(gvel, sim.B.id)[:, :3], gv_o) < tol
+    _kernel_ok(by_id(gpos, sim.B.id)[:, :3], gx_o, tol, "contact g_x")
+    _kernel_ok(by_id(gvel, sim.B.id)[:, :3], gv_o, tol, "contact g_v")
     assert abs(float(gmu.item()) - gmu_o) <= tol * abs(gmu_o)
 
 
@@ -75,8 +96,8 @@ def test_g2p_adjoint_kernel(prec):
     gx_o, gv_o, gc_o = oracle.g2p_adj(prob.grid, prob.params, x, v, r, prob.u, prob.vf, prob.wf, prob.p, prob.alpha_f,
                                       lF, la, lal)
     tol = 1e-5 if prec == FP32 else 1e-11
-    assert _rel(gpos.cpu().numpy()[:, :3], gx_o) < tol
-    assert _rel(gvel.cpu().numpy()[:, :3], gv_o) < tol
+    _kernel_ok(gpos.cpu().numpy()[:, :3], gx_o, tol, "g2p g_x")
+    _kernel_ok(gvel.cpu().numpy()[:, :3], gv_o, tol, "g2p g_v")
     assert abs(float(gc.item()) - gc_o) <= tol * abs(gc_o)
 
 
@@ -91,8 +112,8 @@ def test_integrate_adjoint_kernel(prec):
     torch.cuda.synchronize()
     want = oracle.integrate_adj(prob.grid, prob.params, prob.r.astype(float), gX, gV, gF)
     tol = 1e-6 if prec == FP32 else 1e-13
-    for got, w in zip(outs, want):
-        assert _rel(got.cpu().numpy()[:, :3], w) < tol
+    for k, (got, w) in enumerate(zip(outs, want)):
+        _kernel_ok(got.cpu().numpy()[:, :3], w, tol, f"integrate output {k}")
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -122,9 +143,9 @@ def test_p2g_adjoint_kernel(prec):
     xb, _ = sim.positions(sim.B)
     wo, wn, wf = oracle.p2g_adj(g, prob.params, xa.cpu().numpy(), xb.cpu().numpy(), r, fex, ga, gFs)
     tol = 1e-5 if prec == FP32 else 1e-11
-    assert _rel(gxo.cpu().numpy()[:, :3], wo) < tol
-    assert _rel(gxn.cpu().numpy()[:, :3], wn) < tol
-    assert _rel(gfe.cpu().numpy()[:, :3], wf) < tol
+    _kernel_ok(gxo.cpu().numpy()[:, :3], wo, tol, "p2g g_x_old")
+    _kernel_ok(gxn.cpu().numpy()[:, :3], wn, tol, "p2g g_x_new")
+    _kernel_ok(gfe.cpu().numpy()[:, :3], wf, tol, "p2g g_f_ex")
 
 
 @pytest.mark.parametrize("name", ["dense_block", "random_cloud"])
@@ -155,8 +176,8 @@ def test_substep_adjoint_matches_oracle(name, prec):
                             _t4(gX[ids], prec), _t4(gV[ids], prec), _t4(gFe[ids], prec), gp, gv, gs[0:1], gs[1:2])
         torch.cuda.synchronize()
         assert gic.gic_check_status() == 0
-        assert _rel(by_id(gp, sim.A.id)[:, :3], want_x) < tol
-        assert _rel(by_id(gv, sim.A.id)[:, :3], want_v) < tol
+        _kernel_ok(by_id(gp, sim.A.id)[:, :3], want_x, tol, "substep g_x")
+        _kernel_ok(by_id(gv, sim.A.id)[:, :3], want_v, tol, "substep g_v")
         assert abs(float(gs[0]) - gc_o) <= tol * abs(gc_o)
         assert abs(float(gs[1]) - gmu_o) <= tol * abs(gmu_o)
     assert sim.nb.builds() == 1
@@ -206,12 +227,11 @@ def test_window_gradients_match_oracle_adjoint(kind, ckpt, prec):
     L_o = np.mean(np.sum((out["x"] - prob.target) ** 2, axis=1))
     tol = 1e-3 if prec == FP32 else 1e-8
     assert abs(float(loss) - L_o) <= (1e-6 if prec == FP32 else 1e-12) * L_o
-    assert _rel(gv0.cpu().numpy(), adj["g_v0"]) < tol
-    assert abs(float(gc) - adj["g_c"]) <= tol * abs(adj["g_c"]) + 1e-30
+    _gv0_ok(gv0.cpu().numpy(), adj["g_v0"], prob, prec, tol)
+    assert abs(float(gc) - adj["g_c"]) <= tol * abs(adj["g_c"])
+    assert abs(float(gmu) - adj["g_mu"]) <= tol * abs(adj["g_mu"])
     if kind == "contacts":
-        assert abs(float(gmu) - adj["g_mu"]) <= tol * abs(adj["g_mu"])
-    else:
-        assert abs(float(gmu) - adj["g_mu"]) <= tol * max(abs(adj["g_mu"]), 1e-3 * abs(adj["g_c"]))
+        assert abs(adj["g_mu"]) > 0.0
 
 
 @pytest.mark.parametrize("path", ["rebuild_every_substep", "rebuild_inside_segments", "sorted_every_substep"])
@@ -238,7 +258,7 @@ def test_window_gradient_paths(path, prec):
     out = oracle.run(prob)
     adj = oracle.run_adjoint(prob, 2 * (out["x"] - prob.target) / prob.n)
     tol = 1e-3 if prec == FP32 else 1e-8
-    assert _rel(gv0.cpu().numpy(), adj["g_v0"]) < tol
+    _gv0_ok(gv0.cpu().numpy(), adj["g_v0"], prob, prec, tol)
     assert abs(float(gc) - adj["g_c"]) <= tol * abs(adj["g_c"])
     assert abs(float(gmu) - adj["g_mu"]) <= tol * abs(adj["g_mu"])
 
@@ -275,14 +295,66 @@ def test_window_gradients_match_gpu_fd():
     assert abs(float((gv0.cpu().numpy() * w).sum()) - fd_v) <= 1e-3 * abs(fd_v)
 
 
+def _window_loss_fp64(prob, v=None, P=None, count_contacts=False):
+    """L = mean |x_K - target|^2 from the FP64 GPU forward (v: initial
+    velocities, P: parameters), and with count_contacts the number of contact
+    pairs before each substep (the window's contact signature)."""
+    p = dataclasses.replace(prob, v=(prob.v if v is None else v).astype(np.float32),
+                            params=prob.params if P is None else P)
+    sim = Simulator.from_problem(p, FP64)
+    if v is not None:
+        sim.A.vel[:, :3] = torch.tensor(v, dtype=torch.float64, device="cuda")
+    counts = []
+    partners = torch.zeros(prob.n, dtype=torch.int32, device="cuda")
+    for _ in range(prob.K):
+        if count_contacts:
+            gic.gic_sort(sim.grid, sim.A, sim.B, sim.perm, sim.table, sim.ws)
+            gic.gic_contact_pairs(sim.grid, sim.B, sim.table, counts=partners)
+            counts.append(int(partners.sum().item()) // 2)
+        sim.substep(alpha=False, transfer=False, sums=False)
+    x, _ = sim.positions()
+    return float(((x.cpu().numpy() - prob.target) ** 2).sum(1).mean()), counts
+
+
 @pytest.mark.slow
 def test_differentiable_window_full_size():
     """100,000 granules, 64^3, 50 substeps, checkpoints every 10: FP32 GPU
-    gradients against the FP64 oracle's adjoint."""
+    gradients against the FP64 oracle's adjoint, element by element, and
+    against central finite differences (h = 1e-4 relative) of the FP64 GPU
+    forward on this configuration itself: dL/dv0 . w for a seeded direction
+    w, dL/dc_drag and dL/dmu.  The loose packing (volume fraction 0.3,
+    smallest initial gap 0.01 r) stays contact-free for the whole window in
+    all these runs (asserted: that makes every finite difference
+    contact-stable), so dL/dmu is exactly zero here on both sides; the mu
+    gradient is compared against the oracle and finite differences on the
+    contact windows above."""
     prob = gi.make("diff_window_100k")
     loss, gv0, gc, gmu, _ = window_loss_and_grads(prob, FP32, ckpt=10)
     out = oracle.run(prob)
     adj = oracle.run_adjoint(prob, 2 * (out["x"] - prob.target) / prob.n)
-    assert _rel(gv0.cpu().numpy(), adj["g_v0"]) < 1e-3
+    _gv0_ok(gv0.cpu().numpy(), adj["g_v0"], prob, FP32, 1e-3)
     assert abs(float(gc) - adj["g_c"]) <= 1e-3 * abs(adj["g_c"])
-    assert abs(float(gmu) - adj["g_mu"]) <= 1e-3 * max(abs(adj["g_mu"]), 1e-3 * abs(adj["g_c"]))
+    assert float(gmu) == 0.0 and adj["g_mu"] == 0.0
+    # central differences of the FP64 GPU forward, h = 1e-4 relative
+    P = prob.params
+    L0, c0 = _window_loss_fp64(prob, count_contacts=True)
+    assert abs(L0 - float(loss)) <= 1e-6 * L0
+    hc = 1e-4 * P.c_drag
+    Lp, cp = _window_loss_fp64(prob, P=dataclasses.replace(P, c_drag=P.c_drag + hc), count_contacts=True)
+    Lm, cm = _window_loss_fp64(prob, P=dataclasses.replace(P, c_drag=P.c_drag - hc), count_contacts=True)
+    fd_c = (Lp - Lm) / (2 * hc)
+    assert abs(float(gc) - fd_c) <= 1e-3 * abs(fd_c)
+    hm = 1e-4 * P.mu_fric
+    Lp_mu, _ = _window_loss_fp64(prob, P=dataclasses.replace(P, mu_fric=P.mu_fric + hm))
+    Lm_mu, _ = _window_loss_fp64(prob, P=dataclasses.replace(P, mu_fric=P.mu_fric - hm))
+    assert (Lp_mu - Lm_mu) / (2 * hm) == 0.0
+    rng = np.random.default_rng(7)
+    w = rng.normal(size=(prob.n, 3))
+    v0 = prob.v.astype(np.float64)
+    h = 1e-4 * np.abs(v0).max()
+    Lvp, cvp = _window_loss_fp64(prob, v=v0 + h * w, count_contacts=True)
+    Lvm, cvm = _window_loss_fp64(prob, v=v0 - h * w, count_contacts=True)
+    fd_v = (Lvp - Lvm) / (2 * h)
+    assert abs(float((gv0.cpu().numpy() * w).sum()) - fd_v) <= 1e-3 * abs(fd_v)
+    for counts in (c0, cp, cm, cvp, cvm):
+        assert len(counts) == prob.K and max(counts) == 0

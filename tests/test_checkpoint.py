@@ -67,3 +67,25 @@ def test_foreign_or_inconsistent_files_are_refused(tmp_path):
     torch.save(d, tmp_path / "short.pt")
     with pytest.raises(ValueError, match="do not form"):
         load_checkpoint(tmp_path / "short.pt", device="cpu")
+
+
+def test_grid_is_recorded_and_checked(tmp_path):
+    """Positions are contact-cell ids plus offsets in units of dx / k_contact:
+    a state loaded on another grid would put every granule elsewhere, so a
+    load that names a grid refuses a file from another one (or one that
+    records none)."""
+    from gic_inputs import Grid
+
+    g = Grid(32, 32, 32, 1.0 / 32, k_contact=3)
+    st = random_state(20, GIC_FP32)
+    save_checkpoint(tmp_path / "g.pt", st, grid=g)
+    back, _, _ = load_checkpoint(tmp_path / "g.pt", device="cpu", grid=g)
+    assert torch.equal(back.pos, st.pos)
+    for other in (Grid(32, 32, 32, 1.0 / 32, k_contact=2), Grid(32, 32, 16, 1.0 / 32, k_contact=3),
+                  Grid(32, 32, 32, 1.0 / 64, k_contact=3), Grid(32, 32, 32, 1.0 / 32, origin=(0.5, 0, 0), k_contact=3)):
+        with pytest.raises(ValueError, match="saved on grid"):
+            load_checkpoint(tmp_path / "g.pt", device="cpu", grid=other)
+    save_checkpoint(tmp_path / "nogrid.pt", st)
+    with pytest.raises(ValueError, match="records no grid"):
+        load_checkpoint(tmp_path / "nogrid.pt", device="cpu", grid=g)
+    assert load_checkpoint(tmp_path / "nogrid.pt", device="cpu")[0].n == 20

@@ -183,6 +183,43 @@ def test_coulomb_sliding_on_floor():
     assert abs(out["v"][0, 2]) < 1e-9
 
 
+@pytest.mark.parametrize("kt_over_cn", [1.0, 0.5])
+def test_viscous_tangential_below_the_cap_on_floor(kt_over_cn):
+    """The sub-cap branch of the tangential law (Sec. 3.1: f_t = -k_t v_t on
+    the relative tangential velocity, used while |f_t| < tan(phi) |F_n|),
+    with the reading k_t = kt_over_cn c_n, c_n = 2 zeta sqrt(k_n m_eff) and
+    m_eff = m for a wall.  A granule resting on the floor at the equilibrium
+    overlap m g / k_n, sliding at v0 well under the cap (k_t v0 < mu m g / 5),
+    has v_t = (v_x, 0, 0) exactly (the floor normal is z), so symplectic Euler
+    gives v_x after K substeps = v0 (1 - dt' k_t / m)^K, whatever the small
+    normal motion does.  With the constants below dt' k_t / m = 0.071
+    (kt_over_cn = 1): after 20 substeps the factor is 0.228.  Plausible
+    mistakes all fail by far more than the 1e-9 tolerance: k_t = c_n / 2 gives
+    0.484, k_t = kt_over_cn k_n gives a growing oscillation (dt' k_t / m =
+    1408), m_eff = m / 2 (a granule pair's) gives 0.356, and a dropped dashpot
+    factor 2 in c_n gives 0.484."""
+    r0 = float(np.float32(0.004))  # radii are stored as float32
+    grid = gi.Grid(8, 8, 8, 1.0 / 8, k_contact=1)
+    P = gi.Params(rho_f=0.0, c_drag=0.0, kt_over_cn=kt_over_cn, g=(0.0, 0.0, -9.8), dt_sub=1e-5, dt_fluid=1e-5)
+    m = P.rho_s * 4 / 3 * math.pi * r0 ** 3
+    delta = m * 9.8 / P.k_n
+    cn = 2 * P.zeta * math.sqrt(P.k_n * m)
+    kt = kt_over_cn * cn
+    v0 = 0.2 * P.mu_fric * m * 9.8 / kt
+    x = np.array([[0.5, 0.5, r0 - delta]])
+    v = np.array([[v0, 0.0, 0.0]])
+    K = 20
+    prob = _problem(grid, P, x, v, [r0], _empty_fluid(grid), K)
+    out = oracle.run(prob, K=K, x=x, v=v)
+    want = v0 * (1.0 - P.dt_sub * kt / m) ** K
+    assert abs(out["v"][0, 0] - want) <= 1e-9 * v0
+    assert out["v"][0, 1] == 0.0
+    # the branch really is the viscous one: the speed decays geometrically,
+    # not linearly at mu g (the slip branch of test_coulomb_sliding_on_floor)
+    assert abs(out["v"][0, 0] - (v0 - P.mu_fric * 9.8 * K * P.dt_sub)) > 1e-3 * v0
+    assert out["status"] == 0
+
+
 @pytest.mark.parametrize("c_drag,key", [(0.22, "terminal_velocity_cdrag_0.22"), (5.28, "terminal_velocity_cdrag_5.28")])
 def test_terminal_settling_velocity(c_drag, key):
     """Quadratic drag F_d = c_drag pi r^2 rho_f |dv| dv balancing the buoyant

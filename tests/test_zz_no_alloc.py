@@ -57,6 +57,41 @@ def test_static_sort_matches_workspace_sort_on_consecutive_calls():
     assert gic.gic_check_status() == 0
 
 
+def test_static_sort_allocates_no_device_memory():
+    """What the entry point exists for: once the library is loaded on the
+    device (the first call), further calls -- other sizes, other grids, both
+    precisions -- leave the device's free memory and torch's allocator
+    exactly where they were.  Every input is allocated before the first
+    reading."""
+    cases = [(shuffled(gi.make("dense_block"), seed=4), FP32), (shuffled(gi.make("diff_window_100k"), seed=5), FP32),
+             (subset(shuffled(gi.make("dense_block"), seed=6), 700), FP64)]
+    prepared = []
+    for prob, prec in cases:
+        sim = Simulator.from_problem(prob, prec)
+        table = gic.new_cell_table(sim.grid)
+        prepared.append((sim, table))
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+    def call(sim, table):
+        a, b = sim.A.struct(), sim.B.struct()
+        rc = gic.lib().gic_sort_static(C.byref(sim.grid), C.byref(a), C.byref(b), C.c_void_p(sim.perm.data_ptr()),
+                                       C.c_void_p(table.data_ptr()), stream)
+        assert rc == 0, gic.last_error()
+
+    call(*prepared[0])  # module loading, if this is the first call in the process
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0, reserved0 = torch.cuda.memory_allocated(), torch.cuda.memory_reserved()
+    for _ in range(2):
+        for sim, table in prepared:
+            call(sim, table)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert torch.cuda.memory_allocated() == alloc0 and torch.cuda.memory_reserved() == reserved0
+    assert gic.gic_check_status() == 0
+
+
 def test_static_sort_rejects_more_than_its_capacity():
     nmax = gic.gic_sort_static_max_n()
     assert nmax == 262144
