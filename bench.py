@@ -1,13 +1,15 @@
 """Benchmark of the granule-grid coupling substep on GB300.
 
-One step = one window of K substeps of Alg. 2 (sort, contact, G2P couple,
-integrate, P2G with FP64 volume fraction and conservation sums) over the
-1,000,000-granule dam-break column on a 128^3 grid (100 substeps of 2e-5 s,
-FP32 state with FP64 alpha_s accumulation), starting every step from the same
-seeded initial packing.  The metric is granule-substeps per second.
+One step = one fluid step: a window of K substeps of Alg. 2 (Morton sort on
+Verlet-list rebuilds, fused contact + G2P couple + integrate + P2G of F_s,
+alpha_s and the conservation sums at the final positions) over the largest
+single-GPU workload: the 16,000,000-granule precision and scale sweep on a
+384^3 grid (20 substeps of 1e-5 s, FP32 state with exact fixed-point alpha_s),
+starting every step from the same seeded packing.  The metric is
+granule-substeps per second.
 
 Prints ONE JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
-instead, on a bounded sample of the same workload.
+instead, on all host cores, on bounded sub-boxes of the same workload.
 """
 from __future__ import annotations
 
@@ -21,31 +23,39 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "granule-substeps/s fwd & adjoint, FP32 vs FP64 on 1 GB300; % HBM roofline"
 UNIT = "granule-substeps/s"
-# algorithmic bytes per granule-substep of each step (FP32 path): what the
-# method must move, 12 B per 3-vector, state = 36 B.  P2G scatters F_s from
-# the old positions every substep (cell + pos 20 B, f_ex 12 B) and alpha_s
-# from the new ones once per fluid step (20 B more on the last substep).
-# The fused substep (contact, G2P, integrate, P2G after the sort) reads the
-# sorted state and writes the next one: 36 + 36 B.
+# algorithmic bytes per granule-substep of each entry point (FP32 path):
+# what the method must move, 12 B per 3-vector, state = 36 B.  P2G scatters
+# F_s from the old positions every substep (cell + pos 20 B, f_ex 12 B) and
+# alpha_s from the new ones once per fluid step (20 B more on the last
+# substep).  The fused substep (contact, G2P, integrate, P2G after the sort)
+# is charged the per-unit figure of the hot-path survey for a fused
+# single-pass substep, 90 B: the sorted state in and the next state out
+# (72 B) plus the granule's share of the fluid samples and F_s deposits it
+# touches.  The FP64 path moves twice the floats of every record (2x); the
+# adjoint of the fused substep reads the state and the upstream position and
+# velocity gradients and writes the downstream ones (36 + 32 + 32 = 100 B).
 ALGO_BYTES = {"gic_sort": 88, "gic_contact": 48, "gic_g2p_couple": 65, "gic_integrate": 120, "gic_p2g": 32,
-              "gic_substep": 72, "gic_step": 72}
+              "gic_substep": 90, "gic_step": 90, "gic_substep_adj": 100}
 P2G_ALPHA_BYTES = 20
 # DRAM bytes (read + write) of one call of the dominant entry point on a
 # substep that keeps its Verlet lists (the gic_step graph: the decision
-# kernel + k_substep), from an ncu capture of the current kernels on the same
-# workload, the graph profiled as one unit (ncu flushes the caches first)
+# kernel + k_substep), from an ncu capture of the current kernels (ncu
+# flushes the caches first); per workload
 NCU_TRAFFIC = {("dam_break_1m", "gic_step"): 197.0e6}
 
 
-def algo_bytes(name, K):
+def algo_bytes(name, K, fp64=False):
     """Algorithmic bytes per granule of one call of `name`, averaged over a
-    K-substep window."""
-    return ALGO_BYTES[name] + (P2G_ALPHA_BYTES / K if name in ("gic_p2g", "gic_substep", "gic_step") else 0.0)
+    K-substep window (FP64 path: twice the FP32 figure)."""
+    b = ALGO_BYTES[name] + (P2G_ALPHA_BYTES / K if name in ("gic_p2g", "gic_substep", "gic_step") else 0.0)
+    return 2.0 * b if fp64 else b
 
 
 def parse():
@@ -54,7 +64,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="dam_break_1m")
+    ap.add_argument("--workload", default="scale_sweep_16m")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true", help="skip the FP64 and adjoint variants")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
@@ -170,79 +180,126 @@ class ClockSampler:
 
 # --------------------------------------------------------------------------- CPU oracle sample
 
-def oracle_sample(prob, target_s, K_full):
-    """Time the FP64 oracle on a bounded sample of the workload: the first m
-    granules (the bottom of the column, contacts and walls included) for
-    K_s substeps, sized for about target_s seconds."""
+def crop(prob, start, m):
+    """Granules start .. start + m - 1 of a workload as a problem of its own
+    on the smallest block of the workload's MAC grid that holds them with two
+    cells to spare (same dx, origin moved, fields cut out): the oracle then
+    spends its time on these granules, not on zeroing the full grid."""
     import dataclasses
 
+    import gic_inputs as gi
+
+    g = prob.grid
+    k = g.k_contact
+    cell = prob.cell[start:start + m]
+    mac = cell // k
+    lo = np.maximum(mac.min(0) - 2, 0)
+    hi = np.minimum(mac.max(0) + 3, np.array([g.nx, g.ny, g.nz]))
+    n3 = hi - lo
+    sub = gi.Grid(int(n3[0]), int(n3[1]), int(n3[2]), g.dx,
+                  tuple(float(g.origin[a] + lo[a] * g.dx) for a in range(3)), k)
+
+    def cut(f, ext):  # MAC array with ext extra samples per axis, x fastest
+        a = np.asarray(f).reshape(g.nz + ext[2], g.ny + ext[1], g.nx + ext[0])
+        return np.ascontiguousarray(a[lo[2]:hi[2] + ext[2], lo[1]:hi[1] + ext[1], lo[0]:hi[0] + ext[0]]).ravel()
+
+    return dataclasses.replace(prob, grid=sub, cell=(cell - lo * k).astype(prob.cell.dtype), q=prob.q[start:start + m],
+                               r=prob.r[start:start + m], v=prob.v[start:start + m], u=cut(prob.u, (1, 0, 0)),
+                               vf=cut(prob.vf, (0, 1, 0)), wf=cut(prob.wf, (0, 0, 1)), p=cut(prob.p, (0, 0, 0)),
+                               alpha_f=cut(prob.alpha_f, (0, 0, 0)), target=None)
+
+
+def oracle_rate(prob, target_s, threads):
+    """The FP64 oracle (single-threaded C, as it stands) on `threads` host
+    threads at once, each running its own cropped sub-box of consecutive
+    granules of the workload for the workload's K substeps (the C calls run
+    without the interpreter lock), sized so that each takes about target_s
+    seconds.  Returns (granule-substeps/s over the wall time, sample text)."""
     import oracle
 
-    def sub(m):
-        return dataclasses.replace(prob, cell=prob.cell[:m], q=prob.q[:m], r=prob.r[:m], v=prob.v[:m])
+    K = prob.K
+    m0 = min(prob.n, 4000)
+    t0 = time.perf_counter()
+    oracle.run(crop(prob, 0, m0), K=1)
+    per = (time.perf_counter() - t0) / m0  # seconds per granule-substep, small sample
+    m = int(min(prob.n // max(1, threads), max(1000, target_s / (per * K))))
+    subs = [crop(prob, t * m, m) for t in range(threads)]
+    out = [None] * threads
 
-    # calibrate on a small sample
-    m = min(prob.n, 20000)
+    def work(t):
+        out[t] = oracle.run(subs[t], K=K)["status"]
+
+    ths = [threading.Thread(target=work, args=(t,)) for t in range(threads)]
     t0 = time.perf_counter()
-    oracle.run(sub(m), K=2)
-    per = (time.perf_counter() - t0) / (2 * m)
-    K_s = K_full
-    m = int(min(prob.n, max(1000, target_s / (per * K_s))))
-    if m < 1000:
-        K_s = max(1, int(target_s / (per * 1000)))
-        m = 1000
-    t0 = time.perf_counter()
-    oracle.run(sub(m), K=K_s)
-    dt = time.perf_counter() - t0
-    return {"value": m * K_s / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"first {m} granules of the {prob.n}-granule workload, {K_s} substeps, single-threaded FP64 C",
-            "seconds": dt}
+    for th in ths:
+        th.start()
+    for th in ths:
+        th.join()
+    wall = time.perf_counter() - t0
+    sample = (f"{threads} sub-boxes of {m} consecutive granules of the {prob.n}-granule workload (each on its own "
+              f"block of the MAC grid), {K} substeps each, one FP64 C oracle per host thread")
+    return threads * m * K / wall, sample, wall
+
+
+def oracle_sample(prob, target_s):
+    """cpu_baseline: the oracle on all host cores, and on one."""
+    cores = os.cpu_count() or 1
+    v_all, sample, wall = oracle_rate(prob, target_s, cores)
+    v_one, sample1, wall1 = oracle_rate(prob, target_s / 2, 1)
+    return {"value": v_all, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample, "seconds": wall,
+            "one_core": {"value": v_one, "cores": 1, "sample": sample1, "seconds": wall1}}
 
 
 def run_reference(args, ws, rank):
-    """--impl reference: the oracle is the reference arm (rank 0 only)."""
+    """--impl reference: the oracle is the reference arm (rank 0 only), on
+    all host cores, a bounded sample of the workload per step."""
     if rank != 0:
         return
     import gic_inputs as gi
 
     prob = gi.make(args.workload)
-    import dataclasses
-
-    import oracle
-
-    # bounded sample per step so W + K steps finish within a few minutes
+    cores = os.cpu_count() or 1
     per_step_s = min(20.0, 150.0 / max(1, args.steps + args.warmup))
-    m = min(prob.n, 20000)
-    t0 = time.perf_counter()
-    oracle.run(dataclasses.replace(prob, cell=prob.cell[:m], q=prob.q[:m], r=prob.r[:m], v=prob.v[:m]), K=2)
-    per = (time.perf_counter() - t0) / (2 * m)
-    K_s = prob.K
-    m = int(min(prob.n, max(1000, per_step_s / (per * K_s))))
-    sub = dataclasses.replace(prob, cell=prob.cell[:m], q=prob.q[:m], r=prob.r[:m], v=prob.v[:m])
     for _ in range(args.warmup):
-        oracle.run(sub, K=1)
-    times = []
+        oracle_rate(prob, min(2.0, per_step_s), cores)
+    vals, walls, sample = [], [], ""
     for _ in range(args.steps):
-        t0 = time.perf_counter()
-        oracle.run(sub, K=K_s)
-        times.append(time.perf_counter() - t0)
-    ms = 1000 * statistics.mean(times)
-    value = m * K_s / (ms / 1000)
-    sample = f"first {m} granules of {prob.n}, {K_s} substeps per step, single-threaded FP64 C oracle"
+        v, sample, wall = oracle_rate(prob, per_step_s, cores)
+        vals.append(v)
+        walls.append(wall)
+    value = statistics.mean(vals)
+    ms = 1000 * statistics.mean(walls)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": prob.name, "granules": prob.n, "grid": [prob.grid.nx, prob.grid.ny, prob.grid.nz],
                        "substeps_per_step": prob.K, "sample": sample},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
 # --------------------------------------------------------------------------- GPU arm
 
+def peaks_file():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+def roofline_of(per_call_ms, n, K, fp64, hbm, traffic=None, source="measured"):
+    """HBM roofline of the dominant entry point of a window: its algorithmic
+    bytes per granule x n over its mean call duration."""
+    dom = max(per_call_ms, key=per_call_ms.get)
+    achieved = algo_bytes(dom, K, fp64) * n / (per_call_ms[dom] / 1000.0) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+            "traffic": traffic, "kernel": dom, "peak_source": source, "per_call_ms": per_call_ms,
+            "per_call_frac": {k: algo_bytes(k, K, fp64) * n / (v / 1000.0) / 1e9 / hbm for k, v in per_call_ms.items()},
+            "algo_bytes_per_granule": {k: algo_bytes(k, K, fp64) for k in per_call_ms}}
+
+
 def run_gpu(args, ws, rank, local):
-    import numpy as np
     import torch
 
     import gic_inputs as gi
@@ -257,9 +314,10 @@ def run_gpu(args, ws, rank, local):
     init = sim.A.clone()
     stream = torch.cuda.current_stream()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 512 MB > L2
+    peaks, peak_source = peaks_file()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
 
-    names = list(ALGO_BYTES)
-    ev_acc = {k: [] for k in names}
+    ev_acc = {k: [] for k in ALGO_BYTES}
 
     def one_step(probe=False):
         sim.load_state(init)  # the window's first substep builds the lists
@@ -298,61 +356,136 @@ def run_gpu(args, ws, rank, local):
     value, ms = job_throughput(n * K, ms, ws, dev)
 
     # per-entry-point durations inside the timed region -> roofline of the dominant one
-    per_call = {k: statistics.mean(a.elapsed_time(b) for a, b in ev_acc[k]) for k in names if ev_acc[k]}
-    dom = max(per_call, key=per_call.get)
-    import math
-
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
-    hbm = float(peaks.get("hbm_gbs", 6800.0))
-    achieved = algo_bytes(dom, K) * n / (per_call[dom] / 1000.0) / 1e9
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": NCU_TRAFFIC.get((prob.name, dom)), "kernel": dom,
-                "peak_source": "measured" if peaks else "fallback",
-                "per_call_ms": per_call,
-                "per_call_frac": {k: algo_bytes(k, K) * n / (v / 1000.0) / 1e9 / hbm for k, v in per_call.items()},
-                "algo_bytes_per_granule": {k: algo_bytes(k, K) for k in per_call}}
+    per_call = {k: statistics.mean(a.elapsed_time(b) for a, b in v) for k, v in ev_acc.items() if v}
+    roofline = roofline_of(per_call, n, K, False, hbm, NCU_TRAFFIC.get((prob.name, "gic_step")), peak_source)
 
     # e2e through the C ABI with host buffers (copies inside the timed region)
     e2e = run_e2e(prob, sim, gic, torch, np, dev, stream, max(1, min(args.steps, 3)))
+    # what the exact alpha_s costs: the same state's alpha_s with fixed-point limbs and with FP64 atomics
+    alpha_cost = run_alpha_cost(prob, sim, gic, torch, stream)
 
-    variants = {}
+    variants = {"alpha_s_exact_vs_fp64_atomics": alpha_cost}
+    del sim, init, flush
+    torch.cuda.empty_cache()
     if not args.no_variants:
-        # the consumer of this window's alpha_s: both projections on the 128^3 grid
-        for tol in (1e-6, 1e-9):
-            variants[f"projection_{prob.name}_tol{tol:g}"] = run_projection(prob, sim, gic, torch, dev, stream, tol)
-        variants["fp64_fwd"] = run_fwd(prob, gic.GIC_FP64, gic, torch, dev, stream)
+        variants["fma_rate"] = run_fma_probe(gic, torch, dev, stream)
+        fp64_flops = variants["fma_rate"]["fp64_tflops"]
+        variants[f"fp64_fwd_{prob.name}"] = run_fwd(prob, gic.GIC_FP64, gic, torch, dev, stream, hbm)
+        dam = gi.make("dam_break_1m")
         for prec_name, prec in (("fp32", gic.GIC_FP32), ("fp64", gic.GIC_FP64)):
-            variants[f"{prec_name}_adjoint_dam_break"] = run_adjoint(prob, prec, torch, dev)
-            wprob = gi.make("diff_window_100k")
-            variants[f"{prec_name}_adjoint_diff_window"] = run_adjoint(wprob, prec, torch, dev)
-        del sim, init, flush
+            variants[f"{prec_name}_fwd_dam_break_1m"] = run_fwd(dam, prec, gic, torch, dev, stream, hbm,
+                                                               keep_for_projection=(prec == gic.GIC_FP32))
+        dsim = variants["fp32_fwd_dam_break_1m"].pop("_sim")
+        for tol in (1e-6, 1e-9):
+            variants[f"projection_dam_break_1m_tol{tol:g}"] = run_projection(dam, dsim, gic, torch, dev, stream, tol)
+        del dsim
         torch.cuda.empty_cache()
-        for wname in ("polydisperse_bed_8m", "scale_sweep_16m"):
-            wp = gi.make(wname)
-            for prec_name, prec in (("fp32", gic.GIC_FP32), ("fp64", gic.GIC_FP64)):
-                variants[f"{prec_name}_fwd_{wname}"] = run_fwd(wp, prec, gic, torch, dev, stream)
-            del wp
+        for prec_name, prec in (("fp32", gic.GIC_FP32), ("fp64", gic.GIC_FP64)):
+            variants[f"{prec_name}_adjoint_kernel_dam_break_1m"] = run_adjoint_kernel(dam, prec, gic, torch, dev,
+                                                                                    stream, hbm)
+            variants[f"{prec_name}_adjoint_dam_break_1m"] = run_adjoint(dam, prec, torch, dev)
+            wprob = gi.make("diff_window_100k")
+            variants[f"{prec_name}_adjoint_diff_window_100k"] = run_adjoint(wprob, prec, torch, dev)
+        del dam
+        wp = gi.make("polydisperse_bed_8m")
+        for prec_name, prec in (("fp32", gic.GIC_FP32), ("fp64", gic.GIC_FP64)):
+            variants[f"{prec_name}_fwd_polydisperse_bed_8m"] = run_fwd(wp, prec, gic, torch, dev, stream, hbm,
+                                                                      contacts=(prec == gic.GIC_FP32))
+        del wp
+        for key, v in variants.items():  # the FP64 path against the FP64 pipe: its share of the measured FMA rate
+            if key.startswith("fp64_fwd") and "value" in v:
+                v["fp64_fma_peak_tflops"] = fp64_flops
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32 (fixed-point positions, f64 alpha_s)", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f32 (fixed-point positions, exact f64 alpha_s)", "data": "synthetic",
             "config": {"workload": prob.name, "granules": n, "grid": [prob.grid.nx, prob.grid.ny, prob.grid.nz],
                        "substeps_per_step": K, "dt_sub": prob.params.dt_sub, "precision": "fp32",
                        "schedule": "one fluid step: K gic_step calls (Morton sort only when the Verlet lists, skin "
                                    "0.15 r_max, are rebuilt; fused contact, G2P couple, integrate, P2G of F_s); "
                                    "alpha_s and sums at the final positions",
-                       "l2": "flushed between steps (512 MB write), state reset to the initial packing",
+                       "l2": "flushed between steps (512 MB write); the inputs (16M granules, 1.1 GB of fluid fields) "
+                             "exceed L2 anyway; state reset to the initial packing",
                        "wall_s": wall},
             "roofline": roofline, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
             "device_status": status, "variants": variants}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = oracle_sample(prob, args.cpu_seconds, K)
+        line["cpu_baseline"] = oracle_sample(prob, args.cpu_seconds)
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def run_alpha_cost(prob, sim, gic, torch, stream, reps=5):
+    """alpha_s of the simulator's current FP32 state (after the window): the
+    library's exact path (gic_p2g with alpha_s only: 64-bit fixed-point
+    deposits, integer atomics, the exact totals, the conversion) against
+    the same deposits with plain FP64 atomics (gic_p2g_alpha_atomic64); per
+    call, CUDA events on the stream; and the largest difference."""
+    import ctypes as C
+
+    L = gic.lib()
+    L.gic_p2g_alpha_atomic64.argtypes = [C.c_void_p] * 4
+    L.gic_p2g_alpha_atomic64.restype = C.c_int
+    a64 = torch.empty_like(sim.alpha_s)
+    st = sim.A.struct()
+
+    def exact():
+        gic.gic_p2g(sim.grid, sim.params, sim.A, sim.A, None, sim.alpha_s, (None, None, None), sim.sums, stream)
+
+    def atomic():
+        rc = L.gic_p2g_alpha_atomic64(C.byref(sim.grid), C.byref(st), C.c_void_p(a64.data_ptr()),
+                                      C.c_void_p(stream.cuda_stream))
+        assert rc == 0, gic.last_error()
+
+    out = {}
+    for name, fn in (("exact_fixed_point", exact), ("fp64_atomics", atomic)):
+        fn()
+        times = []
+        for _ in range(reps):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            times.append(a.elapsed_time(b))
+        out[f"{name}_ms"] = statistics.mean(times)
+    out["max_abs_diff"] = float((sim.alpha_s - a64).abs().max().item())
+    out["exact_over_atomics"] = out["exact_fixed_point_ms"] / out["fp64_atomics_ms"]
+    out["workload"] = prob.name
+    out["granules"] = prob.n
+    out["note"] = "exact: order-independent, sum_c alpha_s = sum_i S_i as integers; atomics: order-dependent"
+    return out
+
+
+def run_fma_probe(gic, torch, dev, stream):
+    """FMA rate of this GPU, FP32 and FP64 (gic_probe_fma, CUDA events)."""
+    import ctypes as C
+
+    L = gic.lib()
+    L.gic_probe_fma.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]
+    L.gic_probe_fma.restype = C.c_int
+    blocks = 152 * 8
+    sink = torch.empty(blocks * 256, dtype=torch.float64, device=dev)
+    out = {}
+    for name, prec, iters in (("fp32", gic.GIC_FP32, 8192), ("fp64", gic.GIC_FP64, 512)):
+        fm = C.c_int64(0)
+        times = []
+        for rep in range(4):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            rc = L.gic_probe_fma(prec, blocks, iters, C.c_void_p(sink.data_ptr()), C.byref(fm),
+                                 C.c_void_p(stream.cuda_stream))
+            b.record(stream)
+            assert rc == 0, gic.last_error()
+            torch.cuda.synchronize()
+            if rep:
+                times.append(a.elapsed_time(b))
+        out[f"{name}_tflops"] = 2.0 * fm.value / (min(times) / 1000.0) / 1e12
+        out[f"{name}_ms"] = min(times)
+    out["what"] = "8 independent FMA chains per thread, 1216 CTAs of 256 threads; 2 flops per FMA; best of 3"
+    return out
 
 
 def run_e2e(prob, sim, gic, torch, np, dev, stream, steps):
@@ -442,11 +575,20 @@ def run_adjoint(prob, prec, torch, dev, ckpt=10):
             "dtype": "f32" if prec == 0 else "f64"}
 
 
-def run_fwd(prob, prec, gic, torch, dev, stream, steps=2, warmup=1):
+def contacts_per_granule(sim, gic, torch):
+    """Contact pairs per granule of the simulator's current state (sorted
+    into B for the count), i.e. the contact rate per substep."""
+    counts = torch.zeros(sim.n, dtype=torch.int32, device=sim.device)
+    gic.gic_sort(sim.grid, sim.A, sim.B, sim.perm, sim.table, sim.ws)
+    gic.gic_contact_pairs(sim.grid, sim.B, sim.table, counts=counts)
+    return float(counts.sum().item()) / 2.0 / max(1, sim.n)
+
+
+def run_fwd(prob, prec, gic, torch, dev, stream, hbm, steps=2, warmup=1, keep_for_projection=False, contacts=False):
     """The forward window of a workload on one precision path, `warmup`
     untimed and `steps` timed windows, each from the initial packing after a
     512 MB L2 flush; per-entry-point mean durations from events around each
-    call."""
+    call, and the roofline of the dominant one."""
     from paper_2504_00745_gb300.window import Simulator
 
     sim = Simulator.from_problem(prob, prec, dev)
@@ -456,6 +598,7 @@ def run_fwd(prob, prec, gic, torch, dev, stream, steps=2, warmup=1):
     res = []
     ev_acc = {k: [] for k in ALGO_BYTES}
     gic.gic_check_status(clear=True)
+    c0 = contacts_per_granule(sim, gic, torch) if contacts else None
     for it in range(warmup + steps):
         sim.load_state(init)  # the window's first substep builds the lists
         flush.zero_()
@@ -485,9 +628,56 @@ def run_fwd(prob, prec, gic, torch, dev, stream, steps=2, warmup=1):
     ms = statistics.mean(res)
     per_call = {k: statistics.mean(a.elapsed_time(b) for a, b in v) for k, v in ev_acc.items() if v}
     out = {"value": prob.n * K / (ms / 1000), "unit": UNIT, "ms_per_step": ms, "dtype": "f32" if prec == 0 else "f64",
-           "workload": prob.name, "granules": prob.n, "substeps": K, "steps": steps, "per_call_ms": per_call,
-           "device_status": status}
-    del sim, init, flush
+           "workload": prob.name, "granules": prob.n, "substeps": K, "steps": steps,
+           "roofline": roofline_of(per_call, prob.n, K, prec != 0, hbm), "device_status": status}
+    if contacts:
+        out["contacts_per_granule"] = {"initial": c0, "final": contacts_per_granule(sim, gic, torch)}
+    if keep_for_projection:
+        out["_sim"] = sim
+    else:
+        del sim
+    del init, flush
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_adjoint_kernel(prob, prec, gic, torch, dev, stream, hbm, reps=10):
+    """gic_substep_adj alone (the fused adjoint: integrate, G2P and contact
+    adjoints of one substep over the Verlet lists; with the displacement
+    check it runs first) on the workload's state after one substep, random
+    upstream gradients; mean call time and its roofline."""
+    from paper_2504_00745_gb300.window import Simulator
+
+    sim = Simulator.from_problem(prob, prec, dev)
+    sim.substep(alpha=False, transfer=False, sums=False)  # builds the lists; A is in their order
+    F = sim.fluid
+    g = torch.Generator(device=dev).manual_seed(3)
+    real = torch.float32 if prec == 0 else torch.float64
+    gpo, gvo = (torch.randn((prob.n, 4), generator=g, device=dev, dtype=real) for _ in range(2))
+    gpi, gvi = gic.vec4(prob.n, prec, dev), gic.vec4(prob.n, prec, dev)
+    gs = torch.zeros(2, dtype=torch.float64, device=dev)
+
+    def call():
+        gic.gic_substep_adj(sim.grid, sim.params, sim.A, None, sim.table, sim.nb, F.u, F.v, F.w, F.p, F.alpha_f, gpo,
+                            gvo, None, gpi, gvi, gs[0:1], gs[1:2], stream)
+
+    call()
+    times = []
+    for _ in range(reps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        call()
+        b.record(stream)
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b))
+    builds = sim.nb.builds()
+    status = gic.gic_check_status(clear=True)
+    ms = statistics.mean(times)
+    out = {"value": prob.n / (ms / 1000), "unit": UNIT, "ms_per_call": ms, "dtype": "f32" if prec == 0 else "f64",
+           "workload": prob.name, "granules": prob.n, "list_builds": builds,
+           "roofline": roofline_of({"gic_substep_adj": ms}, prob.n, prob.K, prec != 0, hbm), "device_status": status}
+    del sim
     torch.cuda.empty_cache()
     return out
 

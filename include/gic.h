@@ -520,6 +520,26 @@ int64_t gic_launch_count(void);
 /* Library version string. */
 const char* gic_version(void);
 
+/* ------------------------------------------------------------ measurement aids
+ * (no counterpart in the paper: they exist to measure the path's costs) */
+
+/* FMA rate probe: `blocks` CTAs of 256 threads each run 8 independent FMA
+ * chains of `iters` steps in FP32 (precision GIC_FP32) or FP64 and store one
+ * value per thread into sink (device, blocks * 256 elements of that
+ * precision, 8-byte aligned).  *fmas (host, may be NULL) receives the number
+ * of FMAs the launch performs, so that timing the call on `stream` gives the
+ * GPU's FMA rate.  GIC_ERR_INVALID for an unknown precision, blocks or iters
+ * < 1 or a null sink; GIC_ERR_ALIGN for a misaligned sink. */
+int gic_probe_fma(int32_t precision, int32_t blocks, int32_t iters, void* sink, int64_t* fmas, gic_stream_t stream);
+
+/* alpha_s of an FP32-path state (as gic_p2g computes it at the new
+ * positions, Sec. 5.1) accumulated with plain FP64 atomics instead of the
+ * exact 64-bit fixed point: FP64 tent weights from the fixed-point
+ * positions, order-dependent at the 1e-16 level.  It exists to measure what
+ * the exact accumulation costs; alpha_s (double[nx ny nz], device) is
+ * written.  GIC_ERR_INVALID for an FP64 state or a null alpha_s. */
+int gic_p2g_alpha_atomic64(const GicGrid* grid, const GicGranules* state, double* alpha_s, gic_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -237,6 +237,7 @@ int64_t gic_launch_count(void) { return g_launches.load(); }
 const char* gic_version(void) { return "gic-gb300 0.1 (sm_103a)"; }
 
 int gic_cell_table_size(const GicGrid* grid, size_t* bytes) {
+  GIC_RANGE("gic_cell_table_size");
   DGrid G;
   int rc = make_grid(grid, &G);
   if (rc) return rc;
@@ -247,6 +248,7 @@ int gic_cell_table_size(const GicGrid* grid, size_t* bytes) {
 
 int gic_pack(const GicGrid* grid, int64_t n, const int32_t* cell_xyz, const uint32_t* q, const float* r, const float* v,
              GicGranules* out, gic_stream_t stream) {
+  GIC_RANGE("gic_pack");
   DGrid G;
   int rc = make_grid(grid, &G);
   if (rc) return rc;
@@ -267,6 +269,7 @@ int gic_pack(const GicGrid* grid, int64_t n, const int32_t* cell_xyz, const uint
 }
 
 int gic_unpack(const GicGrid* grid, const GicGranules* in, double* x, double* v, gic_stream_t stream) {
+  GIC_RANGE("gic_unpack");
   DGrid G;
   int rc = make_grid(grid, &G);
   if (rc) return rc;
@@ -286,6 +289,7 @@ int gic_unpack(const GicGrid* grid, const GicGranules* in, double* x, double* v,
 
 int gic_unpack_adj(const GicGrid* grid, const GicGranules* in, const double* gx, const double* gv, void* g_pos,
                    void* g_vel, gic_stream_t stream) {
+  GIC_RANGE("gic_unpack_adj");
   DGrid G;
   int rc = make_grid(grid, &G);
   if (rc) return rc;
@@ -303,6 +307,7 @@ int gic_unpack_adj(const GicGrid* grid, const GicGranules* in, const double* gx,
 }
 
 int gic_check_status(uint32_t* flags, int32_t clear, int32_t timeout_ms, gic_stream_t stream) {
+  GIC_RANGE("gic_check_status");
   if (!flags) return set_error(GIC_ERR_INVALID, "flags is NULL");
   uint32_t* st = status_word();
   if (!st) return set_error(GIC_ERR_CUDA, "status word unavailable");

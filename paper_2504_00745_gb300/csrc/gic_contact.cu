@@ -480,6 +480,7 @@ using namespace gic;
 
 extern "C" int gic_contact(const GicGrid* grid, const GicParams* params, const GicGranules* s, const void* table,
                            void* F_c, gic_stream_t stream) {
+  GIC_RANGE("gic_contact");
   DGrid G;
   int rc = make_grid(grid, &G);
   if (rc) return rc;
@@ -514,6 +515,7 @@ extern "C" int gic_contact(const GicGrid* grid, const GicParams* params, const G
 
 extern "C" int gic_contact_adj(const GicGrid* grid, const GicParams* params, const GicGranules* s, const void* table,
                                const void* gF_c, void* g_pos, void* g_vel, double* g_mu, gic_stream_t stream) {
+  GIC_RANGE("gic_contact_adj");
   DGrid G;
   int rc = make_grid(grid, &G);
   if (rc) return rc;
@@ -543,6 +545,7 @@ extern "C" int gic_contact_adj(const GicGrid* grid, const GicParams* params, con
 
 extern "C" int gic_contact_pairs(const GicGrid* grid, const GicGranules* s, const void* table, int32_t* counts,
                                  int32_t* pairs, int64_t max_pairs, int64_t* n_pairs, gic_stream_t stream) {
+  GIC_RANGE("gic_contact_pairs");
   DGrid G;
   int rc = make_grid(grid, &G);
   if (rc) return rc;
@@ -662,6 +665,7 @@ int verlet_prelude(const DGrid& G, const GicParams* params, const GicGranules* s
 
 extern "C" int gic_contact_verlet(const GicGrid* grid, const GicParams* params, const GicGranules* s,
                                   const void* table, const GicNeighbors* nb, void* F_c, gic_stream_t stream) {
+  GIC_RANGE("gic_contact_verlet");
   DGrid G;
   int rc = make_grid(grid, &G);
   if (rc) return rc;
@@ -688,6 +692,7 @@ extern "C" int gic_contact_verlet(const GicGrid* grid, const GicParams* params, 
 }
 
 extern "C" int gic_neighbors_reset(const GicNeighbors* nb, gic_stream_t stream) {
+  GIC_RANGE("gic_neighbors_reset");
   int rc = check_neighbors(nb, nullptr, "gic_neighbors_reset");
   if (rc) return rc;
   k_neighbors_reset<<<1, 32, 0, stream>>>(nb->flags);
@@ -699,6 +704,7 @@ extern "C" int gic_neighbors_reset(const GicNeighbors* nb, gic_stream_t stream) 
 extern "C" int gic_contact_verlet_adj(const GicGrid* grid, const GicParams* params, const GicGranules* s,
                                       const void* table, const GicNeighbors* nb, void* F_c, const void* gF_c,
                                       void* g_pos, void* g_vel, double* g_mu, gic_stream_t stream) {
+  GIC_RANGE("gic_contact_verlet_adj");
   DGrid G;
   int rc = make_grid(grid, &G);
   if (rc) return rc;

@@ -465,6 +465,7 @@ using namespace gic;
 extern "C" int gic_g2p_couple(const GicGrid* grid, const GicParams* params, const GicGranules* s, const void* u,
                               const void* v, const void* w, const void* p, const void* alpha_f, void* F_fl, void* a_f,
                               void* alpha_f_p, gic_stream_t stream) {
+  GIC_RANGE("gic_g2p_couple");
   DGrid G;
   int rc = make_grid(grid, &G);
   if (rc) return rc;
@@ -496,6 +497,7 @@ extern "C" int gic_g2p_couple_adj(const GicGrid* grid, const GicParams* params, 
                                   const void* v, const void* w, const void* p, const void* alpha_f, const void* gF_fl,
                                   const void* ga_f, const void* galpha_f_p, void* g_pos, void* g_vel,
                                   double* g_cdrag, gic_stream_t stream) {
+  GIC_RANGE("gic_g2p_couple_adj");
   DGrid G;
   int rc = make_grid(grid, &G);
   if (rc) return rc;
@@ -527,6 +529,7 @@ extern "C" int gic_g2p_couple_adj(const GicGrid* grid, const GicParams* params, 
 extern "C" int gic_p2g(const GicGrid* grid, const GicParams* params, const GicGranules* old_, const GicGranules* new_,
                        const void* f_ex, double* alpha_s, void* Fs_u, void* Fs_v, void* Fs_w, double* sums2,
                        gic_stream_t stream) {
+  GIC_RANGE("gic_p2g");
   DGrid G;
   int rc = make_grid(grid, &G);
   if (rc) return rc;
@@ -580,10 +583,37 @@ extern "C" int gic_p2g(const GicGrid* grid, const GicParams* params, const GicGr
   return GIC_OK;
 }
 
+extern "C" int gic_p2g_alpha_atomic64(const GicGrid* grid, const GicGranules* state, double* alpha_s,
+                                      gic_stream_t stream) {
+  GIC_RANGE("gic_p2g_alpha_atomic64");
+  DGrid G;
+  int rc = make_grid(grid, &G);
+  if (rc) return rc;
+  if ((rc = check_granules(state, "gic_p2g_alpha_atomic64"))) return rc;
+  if (state->precision != GIC_FP32)
+    return set_error(GIC_ERR_INVALID, "gic_p2g_alpha_atomic64: the state must be of the FP32 path");
+  if (!alpha_s) return set_error(GIC_ERR_INVALID, "gic_p2g_alpha_atomic64: alpha_s is NULL");
+  const int64_t ncell = (int64_t)G.nx * G.ny * G.nz;
+  k_zero<<<1184, 256, 0, stream>>>(alpha_s, ncell, nullptr);
+  int launches = 1;
+  if (state->n > 0) {
+    DParams<float> P{};
+    k_p2g<float><<<grid_blocks(state->n, 256), 256, 0, stream>>>(G, P, state->n, state->cell,
+                                                                 (const uint4*)state->pos, state->cell,
+                                                                 (const uint4*)state->pos, nullptr, alpha_s, nullptr,
+                                                                 nullptr, nullptr, nullptr);
+    ++launches;
+  }
+  count_launches(launches);
+  GIC_CHECK_LAUNCH("gic_p2g_alpha_atomic64");
+  return GIC_OK;
+}
+
 extern "C" int gic_p2g_adj(const GicGrid* grid, const GicParams* params, const GicGranules* old_,
                            const GicGranules* new_, const void* f_ex, const double* g_alpha_s, const void* gFs_u,
                            const void* gFs_v, const void* gFs_w, void* g_pos_old, void* g_pos_new, void* g_f_ex,
                            gic_stream_t stream) {
+  GIC_RANGE("gic_p2g_adj");
   DGrid G;
   int rc = make_grid(grid, &G);
   if (rc) return rc;

@@ -66,6 +66,7 @@ using namespace gic;
 
 extern "C" int gic_integrate(const GicGrid* grid, const GicParams* params, const GicGranules* in, const void* F_c,
                              const void* F_fl, const void* a_f, GicGranules* out, void* f_ex, gic_stream_t stream) {
+  GIC_RANGE("gic_integrate");
   DGrid G;
   int rc = make_grid(grid, &G);
   if (rc) return rc;
@@ -99,6 +100,7 @@ extern "C" int gic_integrate(const GicGrid* grid, const GicParams* params, const
 extern "C" int gic_integrate_adj(const GicGrid* grid, const GicParams* params, const GicGranules* in,
                                  const void* g_pos_out, const void* g_vel_out, const void* g_f_ex, void* g_pos_in,
                                  void* g_vel_in, void* gF_c, void* gF_fl, void* ga_f, gic_stream_t stream) {
+  GIC_RANGE("gic_integrate_adj");
   DGrid G;
   int rc = make_grid(grid, &G);
   if (rc) return rc;

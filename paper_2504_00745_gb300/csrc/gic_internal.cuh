@@ -9,9 +9,21 @@
 #include <initializer_list>
 #include <cmath>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "gic.h"
 
 namespace gic {
+
+// A named range around an entry point for timeline tools (NVTX; costs a
+// function-pointer test when no tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+#define GIC_RANGE(name) ::gic::NvtxRange gic_nvtx_range_(name)
 
 // ----------------------------------------------------------------- constants
 

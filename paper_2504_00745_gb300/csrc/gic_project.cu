@@ -708,6 +708,7 @@ static int read_red(const ProjRed* dev, ProjRed* host, cudaStream_t st) {
 using namespace gic;
 
 extern "C" int gic_project_workspace_size(const GicGrid* grid, size_t* bytes) {
+  GIC_RANGE("gic_project_workspace_size");
   PGrid g;
   int rc = proj_grid(grid, &g);
   if (rc) return rc;
@@ -720,6 +721,7 @@ extern "C" int gic_project(const GicGrid* grid, const GicProjParams* P, const do
                            const float* u, const float* v, const float* w, double* p1, double* p2, float* u_out,
                            float* v_out, float* w_out, float* dx_u, float* dx_v, float* dx_w, void* ws,
                            size_t ws_bytes, GicProjInfo* info, gic_stream_t stream_) {
+  GIC_RANGE("gic_project");
   PGrid g;
   int rc = proj_grid(grid, &g);
   if (rc) return rc;

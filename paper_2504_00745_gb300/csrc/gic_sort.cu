@@ -335,6 +335,7 @@ static int launch_sort(const DGrid& G, const GicGranules* in, GicGranules* out, 
 using namespace gic;
 
 extern "C" int gic_workspace_size(const GicGrid* grid, int64_t n, int32_t precision, size_t* bytes) {
+  GIC_RANGE("gic_workspace_size");
   DGrid G;
   int rc = make_grid(grid, &G);
   if (rc) return rc;
@@ -347,6 +348,7 @@ extern "C" int gic_workspace_size(const GicGrid* grid, int64_t n, int32_t precis
 
 extern "C" int gic_sort(const GicGrid* grid, const GicGranules* in, GicGranules* out, int32_t* perm, void* cell_table,
                         void* ws, size_t ws_bytes, gic_stream_t stream) {
+  GIC_RANGE("gic_sort");
   DGrid G;
   int rc = make_grid(grid, &G);
   if (rc) return rc;
@@ -415,6 +417,7 @@ __global__ void k_sort_adj(int64_t n, const int32_t* __restrict__ perm, const ve
 
 extern "C" int gic_sort_adj(int64_t n, int32_t precision, const int32_t* perm, const void* g_pos_out,
                             const void* g_vel_out, void* g_pos_in, void* g_vel_in, gic_stream_t stream) {
+  GIC_RANGE("gic_sort_adj");
   if (n < 0) return set_error(GIC_ERR_INVALID, "gic_sort_adj: n < 0");
   if (n == 0) return GIC_OK;
   if (!perm) return set_error(GIC_ERR_INVALID, "gic_sort_adj: perm is NULL");
@@ -483,6 +486,7 @@ extern "C" int64_t gic_sort_static_max_n(void) { return gic::kStaticSortMaxN; }
 
 extern "C" int gic_sort_static(const GicGrid* grid, const GicGranules* in, GicGranules* out, int32_t* perm,
                                void* cell_table, gic_stream_t stream) {
+  GIC_RANGE("gic_sort_static");
   DGrid G;
   int rc = make_grid(grid, &G);
   if (rc) return rc;

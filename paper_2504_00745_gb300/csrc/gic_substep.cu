@@ -311,6 +311,7 @@ extern "C" int gic_substep(const GicGrid* grid, const GicParams* params, const G
                            const void* w, const void* p, const void* alpha_f, GicGranules* next, void* f_ex,
                            double* alpha_s, void* Fs_u, void* Fs_v, void* Fs_w, double* sums2,
                            gic_stream_t stream) {
+  GIC_RANGE("gic_substep");
   DGrid G;
   int rc = make_grid(grid, &G);
   if (rc) return rc;
@@ -498,6 +499,7 @@ extern "C" int gic_step(const GicGrid* grid, const GicParams* params, const GicG
                         const GicNeighbors* nb, const void* u, const void* v, const void* w, const void* p,
                         const void* alpha_f, double* alpha_s, void* Fs_u, void* Fs_v, void* Fs_w, double* sums2,
                         gic_stream_t stream) {
+  GIC_RANGE("gic_step");
   DGrid G;
   int rc = make_grid(grid, &G);
   if (rc) return rc;
@@ -566,6 +568,7 @@ extern "C" int gic_substep_adj(const GicGrid* grid, const GicParams* params, con
                                const void* v, const void* w, const void* p, const void* alpha_f,
                                const void* g_pos_out, const void* g_vel_out, const void* g_f_ex, void* g_pos_in,
                                void* g_vel_in, double* g_cdrag, double* g_mu, gic_stream_t stream) {
+  GIC_RANGE("gic_substep_adj");
   DGrid G;
   int rc = make_grid(grid, &G);
   if (rc) return rc;

@@ -105,6 +105,7 @@ static GicGranules state_at(char* base, int64_t n, int32_t precision) {
 using namespace gic;
 
 extern "C" int gic_window_workspace_size(const GicGrid* grid, int64_t n, int32_t precision, size_t* bytes) {
+  GIC_RANGE("gic_window_workspace_size");
   if (!bytes) return set_error(GIC_ERR_INVALID, "bytes is NULL");
   WindowLayout L;
   int rc = window_layout(grid, n, precision, &L);
@@ -114,6 +115,7 @@ extern "C" int gic_window_workspace_size(const GicGrid* grid, int64_t n, int32_t
 }
 
 extern "C" int gic_window_host_workspace_size(const GicGrid* grid, int64_t n, int32_t precision, size_t* bytes) {
+  GIC_RANGE("gic_window_host_workspace_size");
   if (!bytes) return set_error(GIC_ERR_INVALID, "bytes is NULL");
   WindowLayout L;
   int rc = window_layout(grid, n, precision, &L);
@@ -126,6 +128,7 @@ extern "C" int gic_window_forward(const GicGrid* grid, const GicParams* params, 
                                   const void* u, const void* v, const void* w, const void* p, const void* alpha_f,
                                   double* alpha_s, void* Fs_u, void* Fs_v, void* Fs_w, double* sums2,
                                   void* cell_table, void* ws, size_t ws_bytes, gic_stream_t stream) {
+  GIC_RANGE("gic_window_forward");
   int rc = check_granules(state, "gic_window_forward");
   if (rc) return rc;
   if (K < 0) return set_error(GIC_ERR_INVALID, "gic_window_forward: K < 0");
@@ -219,6 +222,7 @@ extern "C" int gic_window_forward_host(const GicGrid* grid, const GicParams* par
                                        const void* alpha_f, int32_t K, double* x_out, double* v_out,
                                        double* alpha_s, void* Fs_u, void* Fs_v, void* Fs_w, double* sums2, void* ws,
                                        size_t ws_bytes, gic_stream_t stream) {
+  GIC_RANGE("gic_window_forward_host");
   if (n < 0) return set_error(GIC_ERR_INVALID, "gic_window_forward_host: n < 0");
   if (precision != GIC_FP32 && precision != GIC_FP64) return set_error(GIC_ERR_INVALID, "bad precision");
   WindowLayout L;
