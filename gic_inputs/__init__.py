@@ -84,6 +84,11 @@ class Params:
     dt_fluid: float = 1.0e-4
     virtual_mass: int = 1
     walls: int = 1
+    # concentration-gradient / capillary pair force (Sec. 5.4); sigma = 0 leaves it out
+    sigma: float = 0.0           # surface tension coefficient (the paper's scenes: 0.07 N/m)
+    bridge_frac: float = 1.0e-4  # liquid-bridge volume as a fraction of the granule volume (0.01%)
+    moisture: float = 0.0        # water ratio held by every granule
+    moisture_peak: float = 0.3   # moisture ratio where the capillary factor peaks
 
 
 @dataclasses.dataclass
@@ -529,6 +534,28 @@ def dense_block(seed=11, n_side=(8, 8, 8), r0=0.004, nn_factor=1.98, jitter=0.01
     return _finish("dense_block", grid, params, K, x, r, v, u, vf, wf, p, af)
 
 
+def wet_block(seed=12, n_side=(5, 5, 5), r0=0.004, nn_factor=2.02, jitter=0.01, grid_n=32, sigma=0.07, K=10,
+              dt=1e-5, alpha_lo=0.15, alpha_hi=0.45):
+    """Parity case for the capillary pair force: the FCC block of dense_block
+    with its nearest neighbours 2% of r apart (jittered by 1% of r, so most
+    pairs sit in the liquid-bridge range, a few touch), surface tension 0.07
+    N/m, and a fluid fraction that rises linearly in z across the block from
+    alpha_lo to alpha_hi (1 outside it), so that the moisture ratio of the
+    granules varies on both sides of the capillary factor's peak."""
+    prob = dense_block(seed=seed, n_side=n_side, r0=r0, nn_factor=nn_factor, jitter=jitter, grid_n=grid_n, K=K, dt=dt)
+    grid = prob.grid
+    x = prob.positions()
+    lo, hi = x.min(0) - r0, x.max(0) + r0
+    cc = centre_coords(grid)
+    t = np.clip((cc[2] - lo[2]) / (hi[2] - lo[2]), 0.0, 1.0)
+    inside = [(cc[a] >= lo[a]) & (cc[a] <= hi[a]) for a in range(3)]
+    m = inside[0][:, None, None] & inside[1][None, :, None] & inside[2][None, None, :]
+    ramp = np.broadcast_to((alpha_lo + (alpha_hi - alpha_lo) * t)[None, None, :], m.shape)
+    af = _flat(np.where(m, ramp, 1.0))
+    params = dataclasses.replace(prob.params, sigma=sigma)
+    return dataclasses.replace(prob, name="wet_block", params=params, alpha_f=af)
+
+
 def random_cloud(seed=21, n=2000, r0=0.004, grid_n=16, fluid_amp=0.2, K=10, dt=1e-5, phi=0.35):
     """Small random cloud with overlaps: a simple-cubic lattice at volume
     fraction `phi` with uniform jitter of +-0.35 lattice spacings, after which
@@ -756,6 +783,7 @@ def make(name: str, **kw) -> Problem:
         "dam_break_1m": dam_break,
         "diff_window_100k": differentiable_window,
         "dense_block": dense_block,
+        "wet_block": wet_block,
         "random_cloud": random_cloud,
         "polydisperse_bed_8m": polydisperse_bed,
         "scale_sweep_16m": scale_sweep,

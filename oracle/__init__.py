@@ -49,7 +49,8 @@ class OrParams(C.Structure):
     _fields_ = [("rho_s", C.c_double), ("rho_f", C.c_double), ("k_n", C.c_double), ("zeta", C.c_double),
                 ("kt_over_cn", C.c_double), ("mu", C.c_double), ("c_drag", C.c_double), ("gx", C.c_double),
                 ("gy", C.c_double), ("gz", C.c_double), ("dt", C.c_double), ("dt_fluid", C.c_double),
-                ("virtual_mass", C.c_int), ("walls", C.c_int)]
+                ("virtual_mass", C.c_int), ("walls", C.c_int), ("sigma", C.c_double), ("bridge_frac", C.c_double),
+                ("moisture", C.c_double), ("moisture_peak", C.c_double)]
 
 
 _lib = None
@@ -63,6 +64,11 @@ def lib():
         _lib.or_morton.argtypes = [C.c_uint32, C.c_uint32, C.c_uint32]
         _lib.or_cell_table.restype = C.c_int64
         _lib.or_contact_pairs.restype = C.c_int64
+        for fn, args in (("or_gamma", [C.c_double, C.c_double]), ("or_moisture_ratio", [C.c_double, C.c_double]),
+                         ("or_bridge_force", [C.c_double] * 4), ("or_rupture", [C.c_double] * 2)):
+            f = getattr(_lib, fn)
+            f.restype = C.c_double
+            f.argtypes = args
     return _lib
 
 
@@ -80,7 +86,9 @@ def grid_struct(grid) -> OrGrid:
 
 def params_struct(P) -> OrParams:
     return OrParams(P.rho_s, P.rho_f, P.k_n, P.zeta, P.kt_over_cn, P.mu_fric, P.c_drag, P.g[0], P.g[1], P.g[2],
-                    P.dt_sub, P.dt_fluid, int(P.virtual_mass), int(P.walls))
+                    P.dt_sub, P.dt_fluid, int(P.virtual_mass), int(P.walls), float(getattr(P, "sigma", 0.0)),
+                    float(getattr(P, "bridge_frac", 1e-4)), float(getattr(P, "moisture", 0.0)),
+                    float(getattr(P, "moisture_peak", 0.3)))
 
 
 # ---------------------------------------------------------------- encoding
@@ -142,14 +150,44 @@ def contact_pairs(grid, x, r, brute=False):
         cap = m
 
 
-def contact(grid, params, x, v, r, brute=False):
+def _alpha_field(params, alpha_f):
+    if float(getattr(params, "sigma", 0.0)) > 0.0:
+        if alpha_f is None:
+            raise ValueError("the capillary force (sigma > 0) needs the fluid fraction field alpha_f")
+        return _f64(alpha_f)
+    return None
+
+
+def contact(grid, params, x, v, r, brute=False, alpha_f=None):
+    """Pair (contact and, with sigma > 0, capillary) and wall forces; alpha_f:
+    the cell-centred fluid fraction field (needed with sigma > 0)."""
     x, v, r = _f64(x), _f64(v), _f64(r)
+    af = _alpha_field(params, alpha_f)
     n = x.shape[0]
     F = np.empty((n, 3))
     st = C.c_uint32(0)
     lib().or_contact(C.byref(grid_struct(grid)), C.byref(params_struct(params)), C.c_int64(n), _p(x), _p(v), _p(r),
-                     C.c_int(int(brute)), _p(F), C.byref(st))
+                     None if af is None else _p(af), C.c_int(int(brute)), _p(F), C.byref(st))
     return F, st.value
+
+
+def gamma(sr, peak):
+    """Gamma of Sec. 5.4 (the reading's quadratic Bezier curve)."""
+    return lib().or_gamma(float(sr), float(peak))
+
+
+def moisture_ratio(moisture, af):
+    return lib().or_moisture_ratio(float(moisture), float(af))
+
+
+def bridge_force(sigma, R, Vs, s):
+    """F^st of the liquid bridge at separation s (Sec. 5.4)."""
+    return lib().or_bridge_force(float(sigma), float(R), float(Vs), float(s))
+
+
+def rupture(R, Vs):
+    """Rupture distance d_r of a bridge of volume Vs between granules of pair radius R."""
+    return lib().or_rupture(float(R), float(Vs))
 
 
 # ---------------------------------------------------------------- G2P
@@ -237,15 +275,17 @@ def run(prob, K=None, brute=False, x=None, v=None, params=None):
 
 # ---------------------------------------------------------------- adjoints
 
-def contact_adj(grid, params, x, v, r, gF, brute=False):
+def contact_adj(grid, params, x, v, r, gF, brute=False, alpha_f=None):
     """(gx, gv, g_mu) of <gF, contact(x, v)>."""
     x, v, r, gF = map(_f64, (x, v, r, gF))
+    af = _alpha_field(params, alpha_f)
     n = x.shape[0]
     gx = np.zeros((n, 3))
     gv = np.zeros((n, 3))
     gmu = C.c_double(0.0)
     lib().or_contact_adj(C.byref(grid_struct(grid)), C.byref(params_struct(params)), C.c_int64(n), _p(x), _p(v),
-                         _p(r), _p(gF), C.c_int(int(brute)), _p(gx), _p(gv), C.byref(gmu))
+                         _p(r), None if af is None else _p(af), _p(gF), C.c_int(int(brute)), _p(gx), _p(gv),
+                         C.byref(gmu))
     return gx, gv, gmu.value
 
 

@@ -72,6 +72,11 @@ typedef struct {
   double dt;       /* sand substep dt' */
   double dt_fluid; /* fluid step dt (exchange scale dt'/dt) */
   int virtual_mass, walls;
+  /* concentration-gradient / capillary pair force (Sec. 5.4); sigma = 0: off */
+  double sigma;         /* surface tension coefficient */
+  double bridge_frac;   /* liquid-bridge volume V* as a fraction of the granule volume */
+  double moisture;      /* water ratio r_i held by every granule */
+  double moisture_peak; /* where Gamma peaks (the maximum absorption ratio), in [1/4, 3/4] */
 } or_params;
 
 /* ------------------------------------------------------------------------ */
@@ -195,6 +200,95 @@ static int pair_force(const or_params* P, const double xij[3], const double vij[
   return 1;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Concentration-gradient force in its capillary form (Sec. 5.4)            */
+/* ------------------------------------------------------------------------ */
+
+/* Gamma(sr): the moisture factor, zero for a dry (sr = 0) and a saturated
+ * (sr >= 1) neighbourhood, largest (1) at the maximum absorption ratio.  The
+ * paper fits it with a Bezier curve without giving its points; reading:
+ * the quadratic Bezier curve in the (sr, Gamma) plane through (0, 0) and
+ * (1, 0) with middle control point (2 peak - 1/2, 2), whose top, at its
+ * parameter t = 1/2, is (peak, 1).  Along it sr(t) = 2 c t (1 - t) + t^2
+ * (c = 2 peak - 1/2, increasing in t for c in [0, 1]) and Gamma = 4 t (1 - t);
+ * t(sr) is the root in [0, 1] of (1 - 2c) t^2 + 2 c t - sr = 0. */
+double or_gamma(double sr, double peak) {
+  if (!(sr > 0.0) || !(sr < 1.0)) return 0.0;
+  double c = 2.0 * peak - 0.5;
+  double t = sr / (c + sqrt(c * c + (1.0 - 2.0 * c) * sr));
+  return 4.0 * t * (1.0 - t);
+}
+
+/* dGamma/dsr along the same curve (0 outside (0, 1)). */
+static double gamma_slope(double sr, double peak) {
+  if (!(sr > 0.0) || !(sr < 1.0)) return 0.0;
+  double c = 2.0 * peak - 0.5;
+  double t = sr / (c + sqrt(c * c + (1.0 - 2.0 * c) * sr));
+  return 4.0 * (1.0 - 2.0 * t) / (2.0 * (1.0 - 2.0 * c) * t + 2.0 * c);
+}
+
+/* The moisture ratio of Sec. 5.4, sr_i = r_i + alpha_f,i / (1 - alpha_f,i):
+ * the water held by the granule plus the free water around it, per unit of
+ * sand; +inf where there is no sand (alpha_f = 1). */
+double or_moisture_ratio(double moisture, double af) { return af < 1.0 ? moisture + af / (1.0 - af) : INFINITY; }
+
+/* F^st of the liquid bridge at separation s > 0 (Sec. 5.4 with cos theta =
+ * 1): 2 pi sigma R (1 - (1 + 2 V* / (pi R s^2))^(-1/2)), the derivative
+ * dE/ds of the bridge energy E(s) = -2 pi sigma R (-s + sqrt(s^2 + 2 V* /
+ * (pi R))); it tends to 2 pi sigma R as s -> 0 and to 0 as V* -> 0. */
+double or_bridge_force(double sigma, double R, double Vs, double s) {
+  return 2.0 * OR_PI * sigma * R * (1.0 - 1.0 / sqrt(1.0 + 2.0 * Vs / (OR_PI * R * s * s)));
+}
+
+/* dF^st/ds (< 0). */
+static double bridge_slope(double sigma, double R, double Vs, double s) {
+  double b = 2.0 * Vs / (OR_PI * R);
+  double q = 1.0 + b / (s * s);
+  return -2.0 * OR_PI * sigma * R * b / (s * s * s) / (q * sqrt(q));
+}
+
+/* Rupture distance (Willett et al., cited in Sec. 5.4):
+ * d_r = R (v^(1/3) + 0.1 v^(2/3)) with v = V* / R^3.  The paper prints it
+ * without the radius; reading: the dimensionless form of the cited formula
+ * (distances and volume in units of the radius), the only one of consistent
+ * units; for the paper's sizes the two differ by 0.75%. */
+double or_rupture(double R, double Vs) {
+  double v = Vs / (R * R * R);
+  return R * (cbrt(v) + 0.1 * cbrt(v * v));
+}
+
+/* Pair constants of the bridge between radii ri and rj: R = 2 ri rj / (ri + rj)
+ * (the paper's r for equal spheres), V* = bridge_frac (V_i + V_j) / 2. */
+static void bridge_pair(const or_params* P, double ri, double rj, double* R, double* Vs) {
+  *R = 2.0 * ri * rj / (ri + rj);
+  *Vs = P->bridge_frac * 0.5 * (granule_volume(ri) + granule_volume(rj));
+}
+
+/* Capillary force on granule i from j (xij = x_i - x_j), Sec. 5.4:
+ * F = -Gamma((sr_i + sr_j) / 2) F^st(s) xij / |xij| for 0 < s < d_r, with
+ * s = |xij| - r_i - r_j; granules in contact (s <= 0) feel the contact law
+ * instead.  Returns 1 if the force applies. */
+static int capillary_force(const or_params* P, const double xij[3], double ri, double rj, double sri, double srj,
+                           double F[3]) {
+  double d = sqrt(xij[0] * xij[0] + xij[1] * xij[1] + xij[2] * xij[2]);
+  double s = d - (ri + rj);
+  double R, Vs;
+  bridge_pair(P, ri, rj, &R, &Vs);
+  if (!(s > 0.0) || !(s < or_rupture(R, Vs))) return 0;
+  double f = -or_gamma(0.5 * (sri + srj), P->moisture_peak) * or_bridge_force(P->sigma, R, Vs, s);
+  for (int a = 0; a < 3; ++a) F[a] = f * xij[a] / d;
+  return 1;
+}
+
+/* The largest d_r over the radii present (R and V* grow with the radii). */
+static double capillary_reach(const or_params* P, int64_t n, const double* r) {
+  if (!(P->sigma > 0.0)) return 0.0;
+  double rmax = 0.0;
+  for (int64_t i = 0; i < n; ++i) rmax = r[i] > rmax ? r[i] : rmax;
+  if (!(rmax > 0.0)) return 0.0;
+  return or_rupture(rmax, P->bridge_frac * granule_volume(rmax));
+}
+
 /* wall contacts of one granule: the six planes of the box */
 static void wall_forces(const or_grid* G, const or_params* P, const double* x, const double* v, double r, double m,
                         double F[3], uint32_t* status) {
@@ -234,10 +328,10 @@ static void bin_of(const or_bins* B, const double* xi, int bi[3]) {
   }
 }
 
-static void bins_build(or_bins* B, const or_grid* G, int64_t n, const double* x, const double* r) {
+static void bins_build(or_bins* B, const or_grid* G, int64_t n, const double* x, const double* r, double reach) {
   double rmax = 0;
   for (int64_t i = 0; i < n; ++i) rmax = r[i] > rmax ? r[i] : rmax;
-  double hb = 2.0 * rmax;
+  double hb = 2.0 * rmax + reach; /* every pair that interacts lies in adjacent bins */
   if (!(hb > 0)) hb = G->dx;
   double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
   for (int64_t i = 0; i < n; ++i)
@@ -311,7 +405,7 @@ int64_t or_contact_pairs(const or_grid* G, int64_t n, const double* x, const dou
     return m;
   }
   or_bins B;
-  bins_build(&B, G, n, x, r);
+  bins_build(&B, G, n, x, r, 0.0);
   for (int64_t i = 0; i < n; ++i) {
     int bi[3];
     bin_of(&B, x + 3 * i, bi);
@@ -343,30 +437,46 @@ int64_t or_contact_pairs(const or_grid* G, int64_t n, const double* x, const dou
   return m;
 }
 
-/* Contact force on every granule: sum of pair forces over all partners with
- * d < r_i + r_j, plus the walls.  brute != 0 uses the O(N^2) loop. */
+/* Force on granule i from partner j: the contact law while they overlap,
+ * else (with sigma > 0) the capillary force within the rupture distance. */
+static void pair_total(const or_params* P, const double* x, const double* v, const double* r, const double* sr,
+                       int64_t i, int64_t j, double mi, double Fi[3], uint32_t* status) {
+  double xij[3], vij[3], f[3];
+  for (int a = 0; a < 3; ++a) {
+    xij[a] = x[3 * i + a] - x[3 * j + a];
+    vij[a] = v[3 * i + a] - v[3 * j + a];
+  }
+  int c = pair_force(P, xij, vij, r[i], r[j], mi, P->rho_s * granule_volume(r[j]), f);
+  if (c < 0) *status |= OR_COINCIDENT;
+  if (c == 0 && sr) c = capillary_force(P, xij, r[i], r[j], sr[i], sr[j], f);
+  if (c > 0)
+    for (int a = 0; a < 3; ++a) Fi[a] += f[a];
+}
+
+static void moisture_ratios(const or_grid* G, const or_params* P, int64_t n, const double* x, const double* af,
+                            double* sr, double* gsr);
+
+/* Force on every granule from its partners: the contact law over all
+ * partners with d < r_i + r_j and, with sigma > 0, the capillary force
+ * (af: the cell-centred fluid fraction field, interpolated at each granule
+ * as G2P does), plus the walls.  brute != 0 uses the O(N^2) loop. */
 void or_contact(const or_grid* G, const or_params* P, int64_t n, const double* x, const double* v, const double* r,
-                int brute, double* F, uint32_t* status) {
+                const double* af, int brute, double* F, uint32_t* status) {
   or_bins B;
-  if (!brute) bins_build(&B, G, n, x, r);
+  double* sr = NULL;
+  if (P->sigma > 0.0) {
+    sr = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    moisture_ratios(G, P, n, x, af, sr, NULL);
+  }
+  if (!brute) bins_build(&B, G, n, x, r, capillary_reach(P, n, r));
   for (int64_t i = 0; i < n; ++i) {
     double Fi[3] = {0, 0, 0};
     double mi = P->rho_s * granule_volume(r[i]);
     const double* xi = x + 3 * i;
     const double* vi = v + 3 * i;
     if (brute) {
-      for (int64_t j = 0; j < n; ++j) {
-        if (j == i) continue;
-        double xij[3], vij[3], f[3];
-        for (int a = 0; a < 3; ++a) {
-          xij[a] = xi[a] - x[3 * j + a];
-          vij[a] = vi[a] - v[3 * j + a];
-        }
-        int c = pair_force(P, xij, vij, r[i], r[j], mi, P->rho_s * granule_volume(r[j]), f);
-        if (c < 0) *status |= OR_COINCIDENT;
-        if (c > 0)
-          for (int a = 0; a < 3; ++a) Fi[a] += f[a];
-      }
+      for (int64_t j = 0; j < n; ++j)
+        if (j != i) pair_total(P, x, v, r, sr, i, j, mi, Fi, status);
     } else {
       int bi[3];
       bin_of(&B, xi, bi);
@@ -376,24 +486,15 @@ void or_contact(const or_grid* G, const or_params* P, int64_t n, const double* x
             int b[3] = {bi[0] + dx, bi[1] + dy, bi[2] + dz};
             if (b[0] < 0 || b[1] < 0 || b[2] < 0 || b[0] >= B.nb[0] || b[1] >= B.nb[1] || b[2] >= B.nb[2]) continue;
             int64_t lin = b[0] + (int64_t)B.nb[0] * (b[1] + (int64_t)B.nb[1] * b[2]);
-            for (int64_t j = B.head[lin]; j >= 0; j = B.next[j]) {
-              if (j == i) continue;
-              double xij[3], vij[3], f[3];
-              for (int a = 0; a < 3; ++a) {
-                xij[a] = xi[a] - x[3 * j + a];
-                vij[a] = vi[a] - v[3 * j + a];
-              }
-              int c = pair_force(P, xij, vij, r[i], r[j], mi, P->rho_s * granule_volume(r[j]), f);
-              if (c < 0) *status |= OR_COINCIDENT;
-              if (c > 0)
-                for (int a = 0; a < 3; ++a) Fi[a] += f[a];
-            }
+            for (int64_t j = B.head[lin]; j >= 0; j = B.next[j])
+              if (j != i) pair_total(P, x, v, r, sr, i, j, mi, Fi, status);
           }
     }
     if (P->walls) wall_forces(G, P, xi, vi, r[i], mi, Fi, status);
     for (int a = 0; a < 3; ++a) F[3 * i + a] = Fi[a];
   }
   if (!brute) bins_free(&B);
+  free(sr);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -522,6 +623,28 @@ void or_interp_grad_p(const or_grid* G, const double* p, int64_t m, const double
  * F_d = c_drag pi r^2 rho_f |u_f - v| (u_f - v) (Eq. 5b with the drag reading),
  * a_f = dv_f/dt = g - grad p / rho_f (Eq. momentum4 without the F_s term),
  * alpha_f_p = alpha_f interpolated at the granule. */
+static double interp_grad_layout(const or_grid* G, const or_layout* L, const double* f, int gp_comp, const double* p,
+                                 const double* x, double grad[3]);
+
+/* sr_i = r_i + alpha_f,i / (1 - alpha_f,i) at every granule (Sec. 5.4) from the
+ * cell-centred fluid fraction interpolated as G2P does, and (gsr, 3n, may be
+ * NULL) its gradient w.r.t. the granule's position: d sr / d alpha =
+ * 1 / (1 - alpha)^2 times the gradient of the interpolated alpha_f (zero
+ * along an axis where the point is clamped onto an end sample). */
+static void moisture_ratios(const or_grid* G, const or_params* P, int64_t n, const double* x, const double* af,
+                            double* sr, double* gsr) {
+  or_layout Lc = layout_of(G, 3);
+  for (int64_t i = 0; i < n; ++i) {
+    double g[3];
+    double a = interp_grad_layout(G, &Lc, af, -1, NULL, x + 3 * i, g);
+    sr[i] = or_moisture_ratio(P->moisture, a);
+    if (gsr) {
+      double k = a < 1.0 ? 1.0 / ((1.0 - a) * (1.0 - a)) : 0.0;
+      for (int c = 0; c < 3; ++c) gsr[3 * i + c] = k * g[c];
+    }
+  }
+}
+
 void or_g2p(const or_grid* G, const or_params* P, int64_t n, const double* x, const double* v, const double* r,
             const double* u, const double* vf, const double* wf, const double* p, const double* af, double* F_fl,
             double* a_f, double* alpha_f_p) {
@@ -645,7 +768,7 @@ static void substep(const or_grid* G, const or_params* P, const or_fluid* Fd, in
   double* v_new = x_new + 3 * n;
   double* afp = v_new + 3 * n;
   or_g2p(G, P, n, x, v, r, Fd->u, Fd->vf, Fd->wf, Fd->p, Fd->af, F_fl, a_f, afp);
-  or_contact(G, P, n, x, v, r, brute, F_c, status);
+  or_contact(G, P, n, x, v, r, Fd->af, brute, F_c, status);
   or_integrate(G, P, n, x, v, r, F_c, F_fl, a_f, x_new, v_new, f_ex, status);
   or_p2g(G, P, n, x, x_new, r, f_ex, alpha_s, Fs_u, Fs_v, Fs_w, sums);
   memcpy(x, x_new, sizeof(double) * 3 * (size_t)n);
@@ -764,12 +887,48 @@ static int pair_force_jac(const or_params* P, const double x[3], const double v[
   return 1;
 }
 
+/* Jacobians of the capillary force of capillary_force: Jx = dF/dxij and
+ * dsr = dF/d(sr_mean), sr_mean = (sr_i + sr_j) / 2.  F = -Gamma F^st n gives
+ * dF/dx = -Gamma (dF^st/ds n n^T + F^st / d (I - n n^T)) and
+ * dF/dsr_mean = -Gamma' F^st n.  Returns 0 outside 0 < s < d_r. */
+static int capillary_jac(const or_params* P, const double x[3], double ri, double rj, double sri, double srj,
+                         or_m3* Jx, double dsr[3]) {
+  double d = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+  double s = d - (ri + rj);
+  double R, Vs;
+  bridge_pair(P, ri, rj, &R, &Vs);
+  if (!(s > 0.0) || !(s < or_rupture(R, Vs))) return 0;
+  double n[3] = {x[0] / d, x[1] / d, x[2] / d};
+  double srm = 0.5 * (sri + srj);
+  double g = or_gamma(srm, P->moisture_peak);
+  double gp = gamma_slope(srm, P->moisture_peak);
+  double Fs = or_bridge_force(P->sigma, R, Vs, s);
+  double Fp = bridge_slope(P->sigma, R, Vs, s);
+  for (int a = 0; a < 3; ++a) {
+    for (int b = 0; b < 3; ++b)
+      Jx->m[a][b] = -g * (Fp * n[a] * n[b] + Fs / d * ((a == b ? 1.0 : 0.0) - n[a] * n[b]));
+    dsr[a] = -gp * Fs * n[a];
+  }
+  return 1;
+}
+
 /* contact adjoint: gx_i += sum_j Jx_ij^T (l_i - l_j), gv_i likewise,
- * g_mu += sum_i l_i . dF_i/dmu.  Walls: partner gradient zero. */
+ * g_mu += sum_i l_i . dF_i/dmu.  Walls: partner gradient zero.  With the
+ * capillary force (sigma > 0, af = the cell-centred fluid fraction) the pair
+ * force also depends on x_i through sr_i(x_i): gx_i += (1/2) ((l_i - l_j) .
+ * dF/dsr_mean) dsr_i/dx_i; the gather form holds because F_ji = -F_ij as
+ * functions of both positions. */
 void or_contact_adj(const or_grid* G, const or_params* P, int64_t n, const double* x, const double* v,
-                    const double* r, const double* gF, int brute, double* gx, double* gv, double* g_mu) {
+                    const double* r, const double* af, const double* gF, int brute, double* gx, double* gv,
+                    double* g_mu) {
   or_bins B;
-  if (!brute) bins_build(&B, G, n, x, r);
+  double *sr = NULL, *gsr = NULL;
+  if (P->sigma > 0.0) {
+    sr = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    gsr = (double*)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+    moisture_ratios(G, P, n, x, af, sr, gsr);
+  }
+  if (!brute) bins_build(&B, G, n, x, r, capillary_reach(P, n, r));
   double gm = 0.0;
   for (int64_t i = 0; i < n; ++i) {
     double mi = P->rho_s * granule_volume(r[i]);
@@ -810,7 +969,15 @@ void or_contact_adj(const or_grid* G, const or_params* P, int64_t n, const doubl
         lam[a] = li[a] - gF[3 * j + a];
       }
       or_m3 Jx, Jv;
-      if (!pair_force_jac(P, xij, vij, r[i], r[j], mi, P->rho_s * granule_volume(r[j]), &Jx, &Jv, dmu, NULL)) continue;
+      if (!pair_force_jac(P, xij, vij, r[i], r[j], mi, P->rho_s * granule_volume(r[j]), &Jx, &Jv, dmu, NULL)) {
+        double dsr[3];
+        if (sr && isfinite(sr[i]) && isfinite(sr[j]) && capillary_jac(P, xij, r[i], r[j], sr[i], sr[j], &Jx, dsr)) {
+          m3_tmul_add(&Jx, lam, gx + 3 * i);
+          double w = 0.5 * (lam[0] * dsr[0] + lam[1] * dsr[1] + lam[2] * dsr[2]);
+          for (int a = 0; a < 3; ++a) gx[3 * i + a] += w * gsr[3 * i + a];
+        }
+        continue;
+      }
       m3_tmul_add(&Jx, lam, gx + 3 * i);
       m3_tmul_add(&Jv, lam, gv + 3 * i);
       gm += li[0] * dmu[0] + li[1] * dmu[1] + li[2] * dmu[2];
@@ -840,6 +1007,8 @@ void or_contact_adj(const or_grid* G, const or_params* P, int64_t n, const doubl
   }
   *g_mu += gm;
   if (!brute) bins_free(&B);
+  free(sr);
+  free(gsr);
 }
 
 /* value and x-gradient of the interpolation of a sampled field */
@@ -980,9 +1149,14 @@ void or_p2g_adj(const or_grid* G, const or_params* P, int64_t n, const double* x
  * an order-free hash of (i, j, slip) -- used to tell whether a finite-
  * difference pair of runs saw the same contact set. */
 static void contact_signature(const or_grid* G, const or_params* P, int64_t n, const double* x, const double* v,
-                              const double* r, uint64_t sig[3]) {
+                              const double* r, const double* af, uint64_t sig[3]) {
   int64_t m = 0, ms = 0;
   uint64_t h = 0;
+  double* sr = NULL;
+  if (P->sigma > 0.0) { /* capillary pairs (0 < s < d_r) count as a third kind of pair */
+    sr = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    moisture_ratios(G, P, n, x, af, sr, NULL);
+  }
   for (int64_t i = 0; i < n; ++i)
     for (int64_t j = i + 1; j < n; ++j) {
       double xij[3], vij[3], dmu[3];
@@ -993,15 +1167,17 @@ static void contact_signature(const or_grid* G, const or_params* P, int64_t n, c
       or_m3 Jx, Jv;
       int slip = 0;
       if (!pair_force_jac(P, xij, vij, r[i], r[j], P->rho_s * granule_volume(r[i]),
-                          P->rho_s * granule_volume(r[j]), &Jx, &Jv, dmu, &slip))
-        continue;
+                          P->rho_s * granule_volume(r[j]), &Jx, &Jv, dmu, &slip)) {
+        if (!sr || !capillary_jac(P, xij, r[i], r[j], sr[i], sr[j], &Jx, dmu)) continue;
+        slip = 2;
+      }
       ++m;
       ms += slip;
       uint64_t k = (uint64_t)i * 0x9E3779B97F4A7C15ull ^ ((uint64_t)j + 0x632BE59BD9B4E019ull) * 0xBF58476D1CE4E5B9ull;
       k ^= (uint64_t)slip * 0x94D049BB133111EBull;
       h += k * 0xD6E8FEB86659FD93ull;
     }
-  (void)G;
+  free(sr);
   sig[0] += (uint64_t)m;
   sig[1] += (uint64_t)ms;
   sig[2] = sig[2] * 31u + h;
@@ -1031,9 +1207,9 @@ void or_run_adjoint(const or_grid* G, const or_params* P, int64_t n, int K, doub
   for (int s = 0; s < K; ++s) {
     double* xc = xs + n3 * s;
     double* vc = vs + n3 * s;
-    if (sig) contact_signature(G, P, n, xc, vc, r, sig);
+    if (sig) contact_signature(G, P, n, xc, vc, r, af, sig);
     or_g2p(G, P, n, xc, vc, r, u, vf, wf, p, af, Ffl, a_f, afp);
-    or_contact(G, P, n, xc, vc, r, brute, Fc, status);
+    or_contact(G, P, n, xc, vc, r, af, brute, Fc, status);
     or_integrate(G, P, n, xc, vc, r, Fc, Ffl, a_f, xs + n3 * (s + 1), vs + n3 * (s + 1), fex, status);
   }
   memcpy(x, xs + n3 * K, sizeof(double) * 3 * n);
@@ -1056,7 +1232,7 @@ void or_run_adjoint(const or_grid* G, const or_params* P, int64_t n, int K, doub
     double* vc = vs + n3 * s;
     or_integrate_adj(G, P, n, r, gXp, gVp, NULL, gX, gV, gFc, gFfl, gaf);
     or_g2p_adj(G, P, n, xc, vc, r, u, vf, wf, p, af, gFfl, gaf, NULL, gX, gV, g_c);
-    or_contact_adj(G, P, n, xc, vc, r, gFc, brute, gX, gV, g_mu);
+    or_contact_adj(G, P, n, xc, vc, r, af, gFc, brute, gX, gV, g_mu);
     memcpy(gXp, gX, sizeof(double) * 3 * n);
     memcpy(gVp, gV, sizeof(double) * 3 * n);
   }
