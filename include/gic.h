@@ -110,6 +110,17 @@ typedef struct GicParams {
   double dt_fluid;       /* fluid step dt; the exchange force is scaled by dt'/dt */
   int32_t virtual_mass;  /* 1: added mass (2/3) pi r^3 rho_f (Sec. 5.2 Eq. sand kine) */
   int32_t walls;         /* 1: the six box planes are contact partners */
+  /* Concentration-gradient force in its capillary form (Sec. 5.4), between
+   * granules 0 < s < d_r apart: F_ij = -Gamma((sr_i + sr_j) / 2) F^st(s)
+   * (x_i - x_j) / |x_i - x_j|, sr_i = moisture + alpha_f,i / (1 - alpha_f,i)
+   * with alpha_f,i the fluid fraction interpolated at the granule.
+   * sigma = 0 leaves it out.  Only the fused entry points (gic_step,
+   * gic_substep, gic_substep_adj) evaluate it; the separate contact entry
+   * points return GIC_ERR_INVALID when sigma > 0. */
+  double sigma;          /* surface tension coefficient (>= 0) */
+  double bridge_frac;    /* liquid-bridge volume V* as a fraction of the mean volume of the pair (> 0) */
+  double moisture;       /* water ratio r_i held by every granule (>= 0) */
+  double moisture_peak;  /* moisture ratio where Gamma peaks (the maximum absorption ratio), in [1/4, 3/4] */
 } GicParams;
 
 typedef struct GicGranules {

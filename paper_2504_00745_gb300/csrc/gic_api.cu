@@ -4,6 +4,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <chrono>
 #include <mutex>
 #include <thread>
@@ -130,6 +131,33 @@ int make_params(const GicParams* p, DParams<T>* P) {
   P->inv_rho_f = p->rho_f > 0.0 ? (T)(1.0 / p->rho_f) : T(0);
   P->vm = p->virtual_mass ? 1 : 0;
   P->walls = p->walls ? 1 : 0;
+  P->cap = 0;
+  P->sigma = P->frac = P->moist = P->cpk = P->kappa = T(0);
+  if (p->sigma != 0.0) {
+    if (!(p->sigma > 0.0)) return set_error(GIC_ERR_INVALID, "sigma must be >= 0");
+    if (!(p->bridge_frac > 0.0) || !(p->bridge_frac < 1.0))
+      return set_error(GIC_ERR_INVALID, "bridge_frac must lie in (0, 1)");
+    if (!(p->moisture >= 0.0)) return set_error(GIC_ERR_INVALID, "moisture must be >= 0");
+    if (!(p->moisture_peak >= 0.25 && p->moisture_peak <= 0.75))
+      return set_error(GIC_ERR_INVALID, "moisture_peak must lie in [0.25, 0.75]");
+    P->cap = 1;
+    P->sigma = (T)p->sigma;
+    P->frac = (T)p->bridge_frac;
+    P->moist = (T)p->moisture;
+    P->cpk = (T)(2.0 * p->moisture_peak - 0.5);
+    // the largest d_r / (r_i + r_j) over radius ratios rho = r_j / r_i in [1/16, 1]:
+    // R = 2 rho / (1 + rho), V* = frac (2 pi / 3) (1 + rho^3), v = V* / R^3,
+    // d_r = R (v^(1/3) + 0.1 v^(2/3))  (radii in units of r_i)
+    double k = 0.0;
+    for (int t = 0; t <= 4096; ++t) {
+      const double rho = 1.0 / 16.0 + (1.0 - 1.0 / 16.0) * t / 4096.0;
+      const double R = 2.0 * rho / (1.0 + rho);
+      const double v = p->bridge_frac * (2.0 * kPi / 3.0) * (1.0 + rho * rho * rho) / (R * R * R);
+      const double c = std::cbrt(v);
+      k = std::max(k, R * (c + 0.1 * c * c) / (1.0 + rho));
+    }
+    P->kappa = (T)(1.01 * k);
+  }
   return GIC_OK;
 }
 template int make_params<float>(const GicParams*, DParams<float>*);

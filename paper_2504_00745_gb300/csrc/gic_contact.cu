@@ -478,9 +478,20 @@ static int check_table(const void* t) {
 
 using namespace gic;
 
+// The separate contact entry points evaluate the contact law only: the
+// capillary bridges (sigma > 0) need the fluid fraction at both granules,
+// which only the fused entry points receive.
+static int reject_capillary(const GicParams* params, const char* what) {
+  if (params && params->sigma != 0.0)
+    return set_error(GIC_ERR_INVALID,
+                     "%s: the capillary force (sigma > 0) is evaluated by gic_step / gic_substep only", what);
+  return GIC_OK;
+}
+
 extern "C" int gic_contact(const GicGrid* grid, const GicParams* params, const GicGranules* s, const void* table,
                            void* F_c, gic_stream_t stream) {
   GIC_RANGE("gic_contact");
+  if (int rc0 = reject_capillary(params, "gic_contact")) return rc0;
   DGrid G;
   int rc = make_grid(grid, &G);
   if (rc) return rc;
@@ -516,6 +527,7 @@ extern "C" int gic_contact(const GicGrid* grid, const GicParams* params, const G
 extern "C" int gic_contact_adj(const GicGrid* grid, const GicParams* params, const GicGranules* s, const void* table,
                                const void* gF_c, void* g_pos, void* g_vel, double* g_mu, gic_stream_t stream) {
   GIC_RANGE("gic_contact_adj");
+  if (int rc0 = reject_capillary(params, "gic_contact_adj")) return rc0;
   DGrid G;
   int rc = make_grid(grid, &G);
   if (rc) return rc;
@@ -666,6 +678,7 @@ int verlet_prelude(const DGrid& G, const GicParams* params, const GicGranules* s
 extern "C" int gic_contact_verlet(const GicGrid* grid, const GicParams* params, const GicGranules* s,
                                   const void* table, const GicNeighbors* nb, void* F_c, gic_stream_t stream) {
   GIC_RANGE("gic_contact_verlet");
+  if (int rc0 = reject_capillary(params, "gic_contact_verlet")) return rc0;
   DGrid G;
   int rc = make_grid(grid, &G);
   if (rc) return rc;
@@ -705,6 +718,7 @@ extern "C" int gic_contact_verlet_adj(const GicGrid* grid, const GicParams* para
                                       const void* table, const GicNeighbors* nb, void* F_c, const void* gF_c,
                                       void* g_pos, void* g_vel, double* g_mu, gic_stream_t stream) {
   GIC_RANGE("gic_contact_verlet_adj");
+  if (int rc0 = reject_capillary(params, "gic_contact_verlet_adj")) return rc0;
   DGrid G;
   int rc = make_grid(grid, &G);
   if (rc) return rc;

@@ -78,6 +78,11 @@ struct DParams {
   T exch;     // -dt' / dt (exchange scale)
   T inv_rho_f;
   int vm, walls;
+  // capillary pair force (Sec. 5.4); cap = 0: off
+  int cap;
+  T sigma, frac, moist;
+  T cpk;    // 2 moisture_peak - 1/2: the middle control point of Gamma's Bezier curve
+  T kappa;  // d_r of a pair <= kappa (r_i + r_j) for radii within a factor 16: the search reach
 };
 
 int make_grid(const GicGrid* g, DGrid* out);

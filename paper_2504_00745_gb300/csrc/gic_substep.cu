@@ -10,6 +10,7 @@
 #include <mutex>
 #include <type_traits>
 
+#include "gic_capillary.cuh"
 #include "gic_contact.cuh"
 #include "gic_grid.cuh"
 #include "gic_integrate.cuh"
@@ -54,12 +55,26 @@ __global__ void __launch_bounds__(kSubstepThreads, sizeof(T) == 4 ? 4 : 2) k_sub
       const int cx = cell_x(ci), cy = cell_y(ci), cz = cell_z(ci);
       const bool has_f = sizeof(T) == 4 && posf != nullptr;
       const float4 fi = has_f ? __ldg(&posf[i]) : make_float4(0.f, 0.f, 0.f, 0.f);
-      if (rebuild)  // this substep rebuilds the lists: walk the 27 cells
+      if (P.cap) {  // with the capillary bridges (Sec. 5.4): contacts and bridge candidates
+        const T sri = moisture_ratio_at(G, P, Fd.af, ci, pi, (T*)nullptr);
+        auto near = [&](int64_t j, int32_t cj, const pos_t<T>& pj, const PairGeom<T>& g) {
+          if (g.overlap > T(0))
+            add_force(P, g, vi, ldg(&vel[j]), mi, granule_mass(P, radius_of(pj)), F0, F1, F2, coincident);
+          else
+            add_bridge(P, g, ri, radius_of(pj), sri, moisture_ratio_at(G, P, Fd.af, cj, pj, (T*)nullptr), F0, F1,
+                       F2);
+        };
+        if (rebuild)
+          verlet_build_row_near<T>(G, P, nb, table, n, i, cx, cy, cz, ci, pi, ri, skin, id, pos, near);
+        else
+          for_each_list_near<T>(G, P, nb, i, cx, cy, cz, pi, ri, has_f, fi, cell, pos, posf, near);
+      } else if (rebuild) {  // this substep rebuilds the lists: walk the 27 cells
         verlet_build_granule(G, P, nb, table, n, i, cx, cy, cz, ci, pi, ri, mi, vi, has_f, fi, skin, id, pos, posf,
                              vel, F0, F1, F2, coincident);
-      else
+      } else {
         verlet_list_force(G, P, nb, i, cx, cy, cz, ci, pi, ri, mi, vi, has_f, fi, cell, pos, posf, vel, F0, F1, F2,
                           coincident);
+      }
       if (P.walls) add_walls(G, P, pi, ri, mi, vi, cx, cy, cz, F0, F1, F2, status);
       if (coincident) flags |= GIC_STATUS_COINCIDENT;
       if (!isfinite(F0) || !isfinite(F1) || !isfinite(F2)) flags |= GIC_STATUS_NONFINITE;
@@ -200,7 +215,7 @@ __global__ void __launch_bounds__(kSubstepAdjThreads, sizeof(T) == 4 ? 6 : 3) k_
   __shared__ double s_red[64];
   const bool rebuild = (nb.flags[kNbRebuild] | nb.flags[kNbSticky]) != 0u;  // uniform over the launch
   const int64_t i = blockIdx.x * (int64_t)kSubstepAdjThreads + threadIdx.x;
-  double my_gc = 0.0, my_gmu = 0.0;
+  T my_gc = T(0), my_gmu = T(0);
   if (i < n) {
     const int32_t ci = cell[i];
     const pos_t<T> pi = pos[i];
@@ -217,7 +232,7 @@ __global__ void __launch_bounds__(kSubstepAdjThreads, sizeof(T) == 4 ? 6 : 3) k_
     {
       int m[3];
       T t[3], gdv[3];
-      my_gc = (double)g2p_adj_granule<T>(G, P, Fd, ci, pi, vi, o.gFfl, o.gaf, gx, gdv, m, t);
+      my_gc = g2p_adj_granule<T>(G, P, Fd, ci, pi, vi, o.gFfl, o.gaf, gx, gdv, m, t);
 #pragma unroll
       for (int a = 0; a < 3; ++a) gv[a] -= gdv[a];
     }
@@ -237,22 +252,71 @@ __global__ void __launch_bounds__(kSubstepAdjThreads, sizeof(T) == 4 ? 6 : 3) k_
     const int cx = cell_x(ci), cy = cell_y(ci), cz = cell_z(ci);
     const bool has_f = sizeof(T) == 4 && posf != nullptr;
     const float4 fi = has_f ? __ldg(&posf[i]) : make_float4(0.f, 0.f, 0.f, 0.f);
-    if (rebuild)
+    if (P.cap) {  // contacts and capillary bridges; a bridge also depends on x_i through sr_i
+      T gsr[3];
+      const T sri = moisture_ratio_at(G, P, Fd.af, ci, pi, gsr);
+      T wsr = T(0);  // sum over bridges of (lambda_i - lambda_j) . dF/d sr_mean
+      auto near = [&](int64_t j, int32_t cj, const pos_t<T>& pj, const PairGeom<T>& g) {
+        if (g.overlap > T(0)) {
+          pair(j, g);
+          return;
+        }
+        const T rj = radius_of(pj);
+        const IntegrateAdj<T> oj =
+            integrate_adj_granule(P, rj, ldg(&gxo[j]), ldg(&gvo[j]), gfe ? ldg(&gfe[j]) : zero);
+        wsr += add_bridge_adj(P, g, ri, rj, sri, moisture_ratio_at(G, P, Fd.af, cj, pj, (T*)nullptr),
+                              l0 - oj.gFc[0], l1 - oj.gFc[1], l2 - oj.gFc[2], gx[0], gx[1], gx[2]);
+      };
+      if (rebuild)
+        verlet_build_row_near<T>(G, P, nb, table, n, i, cx, cy, cz, ci, pi, ri, skin, id, pos, near);
+      else
+        for_each_list_near<T>(G, P, nb, i, cx, cy, cz, pi, ri, has_f, fi, cell, pos, posf, near);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) gx[a] += T(0.5) * wsr * gsr[a];
+    } else if (rebuild) {
       verlet_build_row<T>(G, nb, table, n, i, cx, cy, cz, ci, pi, ri, has_f, fi, skin, id, pos, posf, pair);
-    else
+    } else {
       for_each_list_contact<T>(G, nb, i, cx, cy, cz, ci, pi, ri, has_f, fi, cell, pos, posf, pair);
+    }
     if (P.walls)
       gm += add_walls_adj(G, P, pi, ri, mi, vi, cx, cy, cz, l0, l1, l2, gx[0], gx[1], gx[2], gv[0], gv[1], gv[2]);
-    my_gmu = (double)gm;
+    my_gmu = gm;
     const int64_t out = perm ? (int64_t)perm[i] : i;
     gxi[out] = make_vec<T>(gx[0], gx[1], gx[2]);
     gvi[out] = make_vec<T>(gv[0], gv[1], gv[2]);
   }
   if (g_cdrag || g_mu) {
-    block_sum2(my_gc, my_gmu, s_red);
-    if (threadIdx.x == 0) {
-      if (g_cdrag) atomicAdd(g_cdrag, my_gc);
-      if (g_mu) atomicAdd(g_mu, my_gmu);
+    if constexpr (sizeof(T) == 4) {
+      // FP32 path: the warp sums in FP32 (the terms are FP32 values), then the
+      // CTA's warps in FP64: the FP64 pipe of this GPU runs at 1/64 of the
+      // FP32 rate, and a per-thread FP64 shuffle tree cost as much as the
+      // rest of the kernel's arithmetic
+      float a = my_gc, b = my_gmu;
+      for (int off = 16; off > 0; off >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, off);
+        b += __shfl_down_sync(0xffffffffu, b, off);
+      }
+      const int w = threadIdx.x >> 5;
+      if (lane_id() == 0) {
+        s_red[w] = (double)a;
+        s_red[32 + w] = (double)b;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double ga = 0.0, gb = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+          ga += s_red[k];
+          gb += s_red[32 + k];
+        }
+        if (g_cdrag) atomicAdd(g_cdrag, ga);
+        if (g_mu) atomicAdd(g_mu, gb);
+      }
+    } else {
+      block_sum2(my_gc, my_gmu, s_red);
+      if (threadIdx.x == 0) {
+        if (g_cdrag) atomicAdd(g_cdrag, my_gc);
+        if (g_mu) atomicAdd(g_mu, my_gmu);
+      }
     }
   }
   verlet_call_done(nb, rebuild);  // its barrier also frees s_red
@@ -312,6 +376,10 @@ extern "C" int gic_substep(const GicGrid* grid, const GicParams* params, const G
                            double* alpha_s, void* Fs_u, void* Fs_v, void* Fs_w, double* sums2,
                            gic_stream_t stream) {
   GIC_RANGE("gic_substep");
+  {  // parameters first, before any device work
+    DParams<double> chk;
+    if (int rc0 = make_params(params, &chk)) return rc0;
+  }
   DGrid G;
   int rc = make_grid(grid, &G);
   if (rc) return rc;
@@ -500,6 +568,10 @@ extern "C" int gic_step(const GicGrid* grid, const GicParams* params, const GicG
                         const void* alpha_f, double* alpha_s, void* Fs_u, void* Fs_v, void* Fs_w, double* sums2,
                         gic_stream_t stream) {
   GIC_RANGE("gic_step");
+  {  // parameters first, before any device work
+    DParams<double> chk;
+    if (int rc0 = make_params(params, &chk)) return rc0;
+  }
   DGrid G;
   int rc = make_grid(grid, &G);
   if (rc) return rc;
@@ -569,6 +641,10 @@ extern "C" int gic_substep_adj(const GicGrid* grid, const GicParams* params, con
                                const void* g_pos_out, const void* g_vel_out, const void* g_f_ex, void* g_pos_in,
                                void* g_vel_in, double* g_cdrag, double* g_mu, gic_stream_t stream) {
   GIC_RANGE("gic_substep_adj");
+  {  // parameters first, before any device work
+    DParams<double> chk;
+    if (int rc0 = make_params(params, &chk)) return rc0;
+  }
   DGrid G;
   int rc = make_grid(grid, &G);
   if (rc) return rc;

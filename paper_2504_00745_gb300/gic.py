@@ -37,7 +37,9 @@ class GicGrid(C.Structure):
 class GicParams(C.Structure):
     _fields_ = [("rho_s", C.c_double), ("rho_f", C.c_double), ("k_n", C.c_double), ("zeta", C.c_double),
                 ("kt_over_cn", C.c_double), ("mu_fric", C.c_double), ("c_drag", C.c_double), ("g", C.c_double * 3),
-                ("dt_sub", C.c_double), ("dt_fluid", C.c_double), ("virtual_mass", C.c_int32), ("walls", C.c_int32)]
+                ("dt_sub", C.c_double), ("dt_fluid", C.c_double), ("virtual_mass", C.c_int32), ("walls", C.c_int32),
+                ("sigma", C.c_double), ("bridge_frac", C.c_double), ("moisture", C.c_double),
+                ("moisture_peak", C.c_double)]
 
 
 class GicGranules(C.Structure):
@@ -159,7 +161,9 @@ def make_grid(g) -> GicGrid:
 
 def make_params(p) -> GicParams:
     return GicParams(p.rho_s, p.rho_f, p.k_n, p.zeta, p.kt_over_cn, p.mu_fric, p.c_drag, (C.c_double * 3)(*p.g),
-                     p.dt_sub, p.dt_fluid, int(p.virtual_mass), int(p.walls))
+                     p.dt_sub, p.dt_fluid, int(p.virtual_mass), int(p.walls), float(getattr(p, "sigma", 0.0)),
+                     float(getattr(p, "bridge_frac", 1e-4)), float(getattr(p, "moisture", 0.0)),
+                     float(getattr(p, "moisture_peak", 0.3)))
 
 
 @dataclass

@@ -443,10 +443,16 @@ def _backward_stepped(ctx, g_pos, g_vel, g_scalars):
     ends, expected = [], []
 
     def sort_and_build(st: State):
-        """st sorted into B (perm, cell table) and the lists built from B."""
+        """st sorted into B (perm, cell table) and the lists built from B
+        (with the capillary force on, by a fused substep into the scratch
+        state A2, whose list build covers the bridge reach)."""
         gic.gic_sort(sim.grid, st, sim.B, sim.perm, sim.table, sim.ws)
         gic.gic_neighbors_reset(nb)
-        gic.gic_contact_verlet(sim.grid, sim.params, sim.B, sim.table, nb, sim.F_c)
+        if sim.params.sigma > 0.0:
+            gic.gic_substep(sim.grid, sim.params, sim.B, sim.table, nb, F.u, F.v, F.w, F.p, F.alpha_f, sim.A2, None,
+                            None, (None, None, None), None)
+        else:
+            gic.gic_contact_verlet(sim.grid, sim.params, sim.B, sim.table, nb, sim.F_c)
 
     for m, (s0, s1) in zip(reversed(range(len(ctx.ckpts))), _segments(ctx.K, ctx.ckpt)):
         L = s1 - s0

@@ -118,3 +118,28 @@ def test_projection_validation_on_the_host():
     assert call(g, good, ws=C.c_void_p((1 << 20) + 64)) == -4
     huge = gic.GicGrid(1024, 1024, 1024, 1, 0.1, (C.c_double * 3)(0, 0, 0))  # 2^30 cells: 32-bit indices
     assert call(huge, good) == -1 and "2^30" in gic.last_error()
+
+
+def test_capillary_parameters_and_scope_on_the_host():
+    """The capillary force (sigma > 0, Sec. 5.4) is evaluated by the fused
+    entry points only: the separate contact entry points refuse it before
+    any device work, and the fused ones validate its parameters (checked
+    here on an empty problem, which enqueues nothing)."""
+    from paper_2504_00745_gb300 import gic
+    L = gic.lib()
+    g = gic.GicGrid(8, 8, 8, 1, 1 / 8, (C.c_double * 3)(0, 0, 0))
+    wet = gic.GicParams(2650, 1000, 1e5, 0.3, 1, 0.5, 0.22, (C.c_double * 3)(0, 0, -9.8), 1e-5, 1e-4, 1, 1,
+                        0.07, 1e-4, 0.0, 0.3)
+    empty = gic.GicGranules(0, None, None, None, None, 0)
+    for name, args in (("gic_contact", (C.byref(g), C.byref(wet), C.byref(empty), C.c_void_p(16), None, None)),
+                       ("gic_contact_verlet", (C.byref(g), C.byref(wet), C.byref(empty), C.c_void_p(16), None, None,
+                                               None))):
+        assert getattr(L, name)(*args) == -1, name
+        assert "capillary" in gic.last_error()
+    # the fused substep validates the capillary parameters
+    bad = gic.GicParams(2650, 1000, 1e5, 0.3, 1, 0.5, 0.22, (C.c_double * 3)(0, 0, -9.8), 1e-5, 1e-4, 1, 1,
+                        0.07, 1e-4, 0.0, 0.9)  # peak outside [1/4, 3/4]
+    nb = gic.GicNeighbors(0, 48, 0.0, *([C.c_void_p(256)] * 8))
+    rc = L.gic_substep(C.byref(g), C.byref(bad), C.byref(empty), C.c_void_p(16), C.byref(nb), *([C.c_void_p(256)] * 5),
+                       C.byref(empty), None, None, None, None, None, None, None)
+    assert rc == -1 and "moisture_peak" in gic.last_error()
