@@ -88,7 +88,9 @@ enum {
   GIC_STATUS_NONFINITE = 4u,     /* a non-finite velocity or force appeared */
   GIC_STATUS_RADIUS = 8u,        /* a radius exceeds h_c / 2: contacts beyond the 27 cells are missed */
   GIC_STATUS_BAD_CELL = 16u,     /* an input cell id lay outside the contact grid */
-  GIC_STATUS_FAST = 32u          /* a granule moved more than one contact cell in a substep */
+  GIC_STATUS_FAST = 32u,         /* a granule moved more than one contact cell in a substep */
+  GIC_STATUS_DEBUG_INDEX = 64u   /* a library built with GIC_DEBUG found an index out of its array; the access
+                                    was skipped (release builds never set it) */
 };
 
 typedef struct GicGrid {

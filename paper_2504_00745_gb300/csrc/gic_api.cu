@@ -78,6 +78,11 @@ int make_grid(const GicGrid* g, DGrid* G) {
   G->ny = g->ny;
   G->nz = g->nz;
   G->k = g->k_contact;
+#ifdef GIC_DEBUG
+  G->dbg = status_word();
+#else
+  G->dbg = nullptr;
+#endif
   for (int a = 0; a < 3; ++a) G->nc[a] = (int)nc[a];
   G->kmul = (uint32_t)(((1u << 20) + (uint32_t)g->k_contact - 1) / (uint32_t)g->k_contact);
   G->dx = g->dx;

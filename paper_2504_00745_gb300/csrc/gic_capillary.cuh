@@ -77,6 +77,8 @@ __device__ __forceinline__ T moisture_ratio_at(const DGrid& G, const DParams<T>&
   L.f = af;
   L.nsx = G.nx;
   L.nsy = G.ny;
+  L.nsz = G.nz;
+  L.dbg = G.dbg;
   T g[3];
   const T a = interp<T>(S, L, (T)G.inv_dx, gsr ? g : nullptr);
   if (!(a < T(1))) {
@@ -165,10 +167,12 @@ __device__ __forceinline__ void for_each_list_near(const DGrid& G, const DParams
                                                    const float4* __restrict__ posf, F&& f) {
   const int32_t s = nb.ident ? (int32_t)i : nb.at[i];
   const int32_t* row = nb.list + (int64_t)s * nb.cap;
-  const int cnt = nb.count[s];
+  int cnt = nb.count[s];
+  if (!GIC_DBG_OK(nb.dbg, cnt >= 0 && cnt <= nb.cap)) cnt = 0;
   const T grow = T(1) + P.kappa;
   for (int k = 0; k < cnt; ++k) {
     const int64_t j = nb.ident ? row[k] : nb.cur[row[k]];
+    if (!GIC_DBG_OK(nb.dbg, j >= 0 && j < nb.n)) continue;
     T rj;
     if constexpr (sizeof(T) == 4) {
       if (has_f) {  // float pre-test on the copies, widened by the bridge reach

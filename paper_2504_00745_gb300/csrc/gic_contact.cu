@@ -605,7 +605,7 @@ NbDev nb_dev(const DGrid& G, const GicNeighbors* nb, bool ident) {
   const double half = 0.5 * nb->skin;
   const double lim = half * G.inv_unit;  // skin / 2 in 2^-30 h_c units
   return NbDev{nb->cap, nb->list, nb->count, nb->ref_cell, nb->ref_pos, nb->slot, nb->cur, nb->at, nb->flags,
-               ident ? 1 : 0, (float)(lim * lim), half * half};
+               ident ? 1 : 0, (float)(lim * lim), half * half, nb->n, G.dbg};
 }
 
 int verlet_view(const DGrid& G, const GicGranules* s, const void* table, const GicNeighbors* nb, const char* what,

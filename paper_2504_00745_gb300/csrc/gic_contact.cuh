@@ -354,6 +354,8 @@ struct NbDev {
   int ident;      // the state is in the order of the last build: slot = index
   float lim2_f;   // (skin / 2)^2 in (2^-30 h_c)^2, FP32 positions
   double lim2_d;  // (skin / 2)^2 in m^2, FP64 positions
+  int64_t n;      // granules (debug builds check partner indices against it)
+  uint32_t* dbg;  // debug builds: the status word the index checks flag
 };
 
 __device__ __forceinline__ float nb_lim2(const NbDev& nb, float) { return nb.lim2_f; }
@@ -603,12 +605,15 @@ __device__ __forceinline__ void for_each_list_contact(const DGrid& G, const NbDe
                                                       const float4* __restrict__ posf, F&& f) {
   const int32_t s = nb.ident ? (int32_t)i : nb.at[i];
   const int32_t* row = nb.list + (int64_t)s * nb.cap;
-  const int cnt = nb.count[s];
+  int cnt = nb.count[s];
+  if (!GIC_DBG_OK(nb.dbg, cnt >= 0 && cnt <= nb.cap)) cnt = 0;
   for (int k = 0; k < cnt; k += 4) {
     int64_t jj[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
+    for (int u = 0; u < 4; ++u) {
       jj[u] = k + u < cnt ? (int64_t)(nb.ident ? row[k + u] : nb.cur[row[k + u]]) : -1;
+      if (jj[u] >= 0 && !GIC_DBG_OK(nb.dbg, jj[u] < nb.n)) jj[u] = -1;
+    }
     if (has_f) {  // FP32: the float pre-test needs no partner cell; load it for the pairs that pass
       float4 fj[4];
 #pragma unroll

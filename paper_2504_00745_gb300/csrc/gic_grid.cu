@@ -2,6 +2,8 @@
 // fluid fraction) and a5 P2G (volume fraction, exchange momentum), with
 // adjoints.  One thread per granule; granules arrive Morton-sorted, so the
 // lanes of a warp read and write the same few MAC cells.
+#include <mutex>
+
 #include "gic_grid.cuh"
 
 namespace gic {
@@ -32,6 +34,8 @@ __global__ void __launch_bounds__(256, 4) k_g2p(DGrid G, DParams<T> P, int64_t n
     L.f = Fd.af;
     L.nsx = G.nx;
     L.nsy = G.ny;
+    L.nsz = G.nz;
+    L.dbg = G.dbg;
     afp[i] = interp<T>(S, L, (T)G.inv_dx, nullptr);
   }
   if (!isfinite(sp)) raise_status(status, GIC_STATUS_NONFINITE);
@@ -64,6 +68,8 @@ __global__ void __launch_bounds__(256) k_g2p_adj(DGrid G, DParams<T> P, int64_t 
       L.f = Fd.af;
       L.nsx = G.nx;
       L.nsy = G.ny;
+      L.nsz = G.nz;
+      L.dbg = G.dbg;
       T gal[3];
       interp<T>(S, L, inv_dx, gal);
       T la_ = galpha[i];
@@ -323,8 +329,9 @@ __device__ __forceinline__ double u128_scaled_to_double(U128 v, int e2) {
   return __longlong_as_double((long long)((be << 52) | (m & ((1ull << 52) - 1ull))));
 }
 
-constexpr int kTotalCtas = 8;  // one portable cluster
+constexpr int kTotalCtas = 16;  // one cluster of 16 CTAs (a non-portable size, enabled per device)
 constexpr int kTotalThreads = 1024;
+constexpr int kTotalUnroll = 4;  // 16-byte loads in flight per thread and pass
 
 __device__ __forceinline__ unsigned cluster_rank() {
   unsigned r;
@@ -345,13 +352,31 @@ __device__ __forceinline__ unsigned long long ld_cluster_u64(const void* p, unsi
   return v;
 }
 
-__global__ void __cluster_dims__(kTotalCtas, 1, 1) __launch_bounds__(kTotalThreads)
-    k_alpha_total_f32(const unsigned long long* __restrict__ a, int64_t m, double dx3, double* __restrict__ sums) {
+__global__ void __launch_bounds__(kTotalThreads)
+    k_alpha_total_f32(const unsigned long long* __restrict__ a, int64_t m, int vec, double dx3,
+                      double* __restrict__ sums) {
   __shared__ unsigned long long s_lo[kTotalThreads / 32], s_hi[kTotalThreads / 32];
   __shared__ unsigned long long part[2];
   U128 t{0ull, 0ull};
-  for (int64_t i = blockIdx.x * (int64_t)kTotalThreads + threadIdx.x; i < m; i += (int64_t)kTotalCtas * kTotalThreads)
-    add128(t, __ldg(&a[i]), 0ull);
+  const int64_t tid = blockIdx.x * (int64_t)kTotalThreads + threadIdx.x;
+  const int64_t S = (int64_t)kTotalCtas * kTotalThreads;
+  if (vec) {  // pairs of cells as 16-byte loads, kTotalUnroll of them in flight
+    const ulonglong2* a2 = reinterpret_cast<const ulonglong2*>(a);
+    const int64_t m2 = m >> 1;
+    for (int64_t p = tid; p < m2; p += kTotalUnroll * S) {
+      ulonglong2 v[kTotalUnroll];
+#pragma unroll
+      for (int u = 0; u < kTotalUnroll; ++u) v[u] = p + u * S < m2 ? __ldg(&a2[p + u * S]) : make_ulonglong2(0ull, 0ull);
+#pragma unroll
+      for (int u = 0; u < kTotalUnroll; ++u) {
+        add128(t, v[u].x, 0ull);
+        add128(t, v[u].y, 0ull);
+      }
+    }
+    if ((m & 1) && tid == 0) add128(t, __ldg(&a[m - 1]), 0ull);
+  } else {
+    for (int64_t i = tid; i < m; i += S) add128(t, __ldg(&a[i]), 0ull);
+  }
   for (int off = 16; off > 0; off >>= 1) {
     const unsigned long long lo = __shfl_down_sync(0xffffffffu, t.lo, off);
     const unsigned long long hi = __shfl_down_sync(0xffffffffu, t.hi, off);
@@ -406,6 +431,8 @@ __global__ void __launch_bounds__(256) k_p2g_adj(DGrid G, DParams<T> P, int64_t 
     L.f = galpha;
     L.nsx = G.nx;
     L.nsy = G.ny;
+    L.nsz = G.nz;
+    L.dbg = G.dbg;
     double g[3];
     interp<double>(S, L, G.inv_dx, g);
     vec_t<T> a = gpos_new[i];
@@ -434,6 +461,44 @@ __global__ void __launch_bounds__(256) k_p2g_adj(DGrid G, DParams<T> P, int64_t 
   }
 }
 
+// The cluster size of k_alpha_total_f32 is beyond the portable 8: allowed
+// once per device, before any capture.
+int alpha_prepare() {
+  static std::mutex mu;
+  static bool done[64] = {false};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return set_error(GIC_ERR_CUDA, "no current device");
+  std::lock_guard<std::mutex> lk(mu);
+  if (!done[dev]) {
+    const cudaError_t e = cudaFuncSetAttribute(k_alpha_total_f32, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return set_error(GIC_ERR_CUDA, "alpha_s totals: %s", cudaGetErrorString(e));
+    done[dev] = true;
+  }
+  return GIC_OK;
+}
+
+static int launch_alpha_total(double* alpha_s, int64_t ncell, double dx3, double* sums2, cudaStream_t stream) {
+  int rc = alpha_prepare();
+  if (rc) return rc;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kTotalCtas, 1, 1);
+  cfg.blockDim = dim3(kTotalThreads, 1, 1);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = kTotalCtas;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  const int vec = ((uintptr_t)alpha_s % 16 == 0) ? 1 : 0;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, k_alpha_total_f32, (const unsigned long long*)alpha_s, ncell, vec,
+                                           dx3, sums2);
+  if (e != cudaSuccess) return set_error(GIC_ERR_CUDA, "alpha_s totals: %s", cudaGetErrorString(e));
+  return GIC_OK;
+}
+
 // alpha_s accumulation around a P2G pass: zero the grid (and sums) before,
 // then convert (FP32 fixed point -> double) or sum (FP64) after.
 int alpha_begin(double* alpha_s, int64_t ncell, double* sums2, cudaStream_t stream) {
@@ -445,8 +510,7 @@ int alpha_begin(double* alpha_s, int64_t ncell, double* sums2, cudaStream_t stre
 int alpha_end(const DGrid& G, int32_t precision, double* alpha_s, int64_t ncell, double* sums2, cudaStream_t stream) {
   if (precision == GIC_FP32) {
     if (sums2) {
-      k_alpha_total_f32<<<kTotalCtas, kTotalThreads, 0, stream>>>((const unsigned long long*)alpha_s, ncell,
-                                                                   G.dx * G.dx * G.dx, sums2);
+      if (int rc = launch_alpha_total(alpha_s, ncell, G.dx * G.dx * G.dx, sums2, stream)) return rc;
       count_launches(1);
     }
     k_alpha_finish_f32<<<1184, 256, 0, stream>>>(alpha_s, ncell);
@@ -568,8 +632,7 @@ extern "C" int gic_p2g(const GicGrid* grid, const GicParams* params, const GicGr
   if (alpha_s && old_->precision == GIC_FP32) {
     // the FP32 path accumulated 64-bit fixed point: convert in place
     if (sums2) {
-      k_alpha_total_f32<<<kTotalCtas, kTotalThreads, 0, stream>>>((const unsigned long long*)alpha_s, ncell,
-                                                                   G.dx * G.dx * G.dx, sums2);
+      if (int rc = launch_alpha_total(alpha_s, ncell, G.dx * G.dx * G.dx, sums2, stream)) return rc;
       ++launches;
     }
     k_alpha_finish_f32<<<1184, 256, 0, stream>>>(alpha_s, ncell);

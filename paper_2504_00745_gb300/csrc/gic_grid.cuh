@@ -23,6 +23,8 @@ __device__ __forceinline__ FieldLoad<T> face_loader(const DGrid& G, const T* f, 
   L.f = f;
   L.nsx = G.nx + (comp == 0);
   L.nsy = G.ny + (comp == 1);
+  L.nsz = G.nz + (comp == 2);
+  L.dbg = G.dbg;
   return L;
 }
 
@@ -35,6 +37,7 @@ __device__ __forceinline__ GradPLoad<T> gradp_loader(const DGrid& G, const T* p,
   L.nz = G.nz;
   L.comp = comp;
   L.inv_dx = (T)G.inv_dx;
+  L.dbg = G.dbg;
   return L;
 }
 
@@ -468,7 +471,12 @@ struct SubBox {
 struct TileLoad {
   const float* s;
   SubBox B;
-  __device__ __forceinline__ float operator()(int i, int j, int k) const { return s[B.index(i, j, k)]; }
+  uint32_t* dbg;
+  __device__ __forceinline__ float operator()(int i, int j, int k) const {
+    const int e = B.index(i, j, k);
+    if (!GIC_DBG_OK(dbg, e >= 0 && e < B.vol)) return 0.f;
+    return s[e];
+  }
 };
 
 // CTA-wide (every thread calls it): the box of the granules' MAC cells, the
@@ -541,8 +549,8 @@ __device__ __forceinline__ float sub_g2p(const SubTile& sh, const SubBox& B, con
   if (!B.tile) return g2p_granule<float>(G, P, Fd, c, pi, vi, F, a);
   const float* uvw[3] = {sh.u, sh.v, sh.w};
   return g2p_granule_with<float>(
-      G, P, c, pi, vi, [&](int comp) { return TileLoad{uvw[comp], B}; },
-      [&](int comp) { return TileLoad{sh.gp[comp], B}; }, F, a);
+      G, P, c, pi, vi, [&](int comp) { return TileLoad{uvw[comp], B, G.dbg}; },
+      [&](int comp) { return TileLoad{sh.gp[comp], B, G.dbg}; }, F, a);
 }
 
 // CTA-wide: the F_s fixed-point unit from the largest |exch f_ex| component
@@ -570,6 +578,7 @@ __device__ __forceinline__ void sub_add_face(SubTile& sh, const SubBox& B, const
   const float wyz[4] = {(1.f - wy) * (1.f - wz), wy * (1.f - wz), (1.f - wy) * wz, wy * wz};
   if (inv_unit != 0.f) {
     const int e0 = B.index(St.i0[0], St.i0[1], St.i0[2]);
+    if (!GIC_DBG_OK(G.dbg, e0 >= 0 && e0 + 1 + B.sy + B.sz < B.vol)) return;
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
       const int q = __float2int_rn(((k & 1) ? fx1 : fx0) * wyz[k >> 1] * inv_unit);
@@ -593,6 +602,7 @@ __device__ __forceinline__ void sub_add_alpha(SubTile& sh, const SubBox& B, cons
                                               const int ia[3], const long long va[8]) {
   if (B.tile && B.holds(ia[0], ia[1], ia[2])) {
     const int e0 = B.index(ia[0], ia[1], ia[2]);
+    if (!GIC_DBG_OK(G.dbg, e0 >= 0 && e0 + 1 + B.sy + B.sz < B.vol)) return;
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
       const int e = e0 + (k & 1) + ((k >> 1) & 1) * B.sy + (k >> 2) * B.sz;
@@ -650,6 +660,8 @@ inline Fields<T> fields(const void* u, const void* v, const void* w, const void*
 }
 
 int alpha_begin(double* alpha_s, int64_t ncell, double* sums2, cudaStream_t stream);
+// one-time per-device set-up of the exact totals' kernel (call before any capture)
+int alpha_prepare();
 int alpha_end(const DGrid& G, int32_t precision, double* alpha_s, int64_t ncell, double* sums2, cudaStream_t stream);
 
 }  // namespace gic

@@ -68,7 +68,22 @@ struct DGrid {
   unsigned long long kinv64;  // ceil(2^64 / k) for k > 1 (fixed-point division by k), 0 for k = 1
   double vol_fx;              // (4/3) pi / dx^3 * 2^53: granule volume fraction in 2^-53 units per r^3
   float vol_fx_hi, vol_fx_lo;  // the same as an unevaluated float pair
+  uint32_t* dbg;               // debug builds: the status word the index checks flag (null otherwise)
 };
+
+// Debug builds (compiled with GIC_DEBUG): device-side checks that an index
+// lies inside its array.  A failed check sets GIC_STATUS_DEBUG_INDEX in the
+// status word and the caller skips the access -- no trap, no assert.
+// Release builds compile the checks away.
+__device__ __forceinline__ bool dbg_fail(uint32_t* dbg) {
+  if (dbg) atomicOr(dbg, (uint32_t)GIC_STATUS_DEBUG_INDEX);
+  return false;
+}
+#ifdef GIC_DEBUG
+#define GIC_DBG_OK(dbg, cond) ((cond) ? true : ::gic::dbg_fail(dbg))
+#else
+#define GIC_DBG_OK(dbg, cond) true
+#endif
 
 template <typename T>
 struct DParams {

@@ -114,8 +114,10 @@ __device__ __forceinline__ T interp(const Stencil3<T>& S, Load load, T inv_dx, T
 template <typename T>
 struct FieldLoad {
   const T* __restrict__ f;
-  int nsx, nsy;
+  int nsx, nsy, nsz;
+  uint32_t* dbg;
   __device__ __forceinline__ T operator()(int i, int j, int k) const {
+    if (!GIC_DBG_OK(dbg, i >= 0 && i < nsx && j >= 0 && j < nsy && k >= 0 && k < nsz)) return T(0);
     return __ldg(&f[sample_index(nsx, nsy, i, j, k)]);
   }
 };
@@ -127,12 +129,15 @@ struct GradPLoad {
   const T* __restrict__ p;
   int nx, ny, nz, comp;
   T inv_dx;
+  uint32_t* dbg;
   __device__ __forceinline__ T operator()(int i, int j, int k) const {
     int idx[3] = {i, j, k};
     const int n[3] = {nx, ny, nz};
     int c = idx[comp];
     c = c < 1 ? 1 : (c > n[comp] - 1 ? n[comp] - 1 : c);
     idx[comp] = c;
+    if (!GIC_DBG_OK(dbg, idx[0] >= 0 && idx[0] < nx && idx[1] >= 0 && idx[1] < ny && idx[2] >= 0 && idx[2] < nz))
+      return T(0);
     T hi = __ldg(&p[sample_index(nx, ny, idx[0], idx[1], idx[2])]);
     idx[comp] = c - 1;
     T lo = __ldg(&p[sample_index(nx, ny, idx[0], idx[1], idx[2])]);

@@ -494,6 +494,7 @@ static int build_step_graph(StepGraph& sg, const DGrid& G, const GicGrid* grid, 
   cudaGraphConditionalHandle h_rebuild, h_keep;
   int launches = 0;
   status_word();  // resolve the device address before capturing
+  if ((rc = alpha_prepare())) return rc;
   if (cudaGraphCreate(&g, 0) != cudaSuccess) return set_error(GIC_ERR_CUDA, "gic_step: cudaGraphCreate failed");
   if (cudaGraphConditionalHandleCreate(&h_rebuild, g, 0, cudaGraphCondAssignDefault) != cudaSuccess ||
       cudaGraphConditionalHandleCreate(&h_keep, g, 0, cudaGraphCondAssignDefault) != cudaSuccess ||

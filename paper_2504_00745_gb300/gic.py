@@ -23,6 +23,7 @@ STATUS_NONFINITE = 4
 STATUS_RADIUS = 8
 STATUS_BAD_CELL = 16
 STATUS_FAST = 32
+STATUS_DEBUG_INDEX = 64  # set only by the GIC_DEBUG build
 
 
 class GicError(RuntimeError):
@@ -98,18 +99,25 @@ _SIGS = {
 _lib = None
 
 
+def _debug_wanted() -> bool:
+    """GIC_LIBRARY=debug in the environment selects the GIC_DEBUG build
+    (device-side index checks) for this process."""
+    return os.environ.get("GIC_LIBRARY", "") == "debug"
+
+
 def lib_path() -> str:
-    return _build.LIB
+    return _build.DEBUG_LIB if _debug_wanted() else _build.LIB
 
 
 def lib():
     """Load libgic.so (building it first when the sources are newer)."""
     global _lib
     if _lib is None:
-        path = _build.LIB
-        if not _build.up_to_date():
+        debug = _debug_wanted()
+        path = _build.DEBUG_LIB if debug else _build.LIB
+        if not _build.up_to_date(debug):
             try:
-                _build.build()
+                _build.build(debug=debug)
             except Exception as e:  # no nvcc or compile error: fail loudly, never fall back
                 raise GicError(f"libgic.so is missing or stale and could not be built: {e}") from e
         if not os.path.exists(path):

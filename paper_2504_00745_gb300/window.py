@@ -374,15 +374,23 @@ class GicWindow(torch.autograd.Function):
             gic.gic_neighbors_reset(sim.nb)
             sim.lists_current = True
         ckpts, lists = [], []
+        log = torch.zeros(K + 1, dtype=torch.int32, device=sim.device) if stepped else None
+        if stepped:
+            log[0:1].copy_(sim.nb.flags[4:5])
         for s in range(K):
             if s % ckpt == 0:
                 ckpts.append(sim.A.clone())
                 if stepped:
-                    lists.append(_lists_snapshot(sim.nb, lists[-1] if lists else None))
+                    lists.append(_lists_snapshot(sim.nb))
             sim.substep(alpha=False, transfer=False, sums=False, sort_every=not stepped)
+            if stepped:
+                log[s + 1:s + 2].copy_(sim.nb.flags[4:5])  # list builds so far (device copy, no wait)
         x, _ = sim.positions()
         ctx.sim, ctx.K, ctx.ckpt, ctx.stepped = sim, K, ckpt, stepped
         ctx.ckpts, ctx.lists = ckpts, lists
+        # the window's build record, read once: the recomputation from each
+        # checkpoint repeats the forward pass exactly, builds included
+        ctx.build_log = log.tolist() if stepped else None
         ctx.final = sim.A.clone()
         return x
 
@@ -410,21 +418,13 @@ def _segments(K: int, ckpt: int):
 _NB_ARRAYS = ("list", "count", "ref_cell", "ref_pos", "slot")
 
 
-def _lists_snapshot(nb: gic.Neighbors, last: Optional[dict]) -> dict:
-    """The Verlet lists as they stand: the flag words (among them the
-    decision for the next gic_step) and, unless a build is pending, the rows
-    and reference entries (`cur` and `at` follow from them at the next
-    check).  The arrays of `last` are shared when no build has run since."""
-    flags = nb.flags.clone()
-    f = flags.tolist()
-    pending = bool(f[1])
-    snap = {"flags": flags, "builds": f[4], "pending": pending, "arrays": None}
-    if not pending:
-        if last is not None and last["arrays"] is not None and last["builds"] == f[4]:
-            snap["arrays"] = last["arrays"]
-        else:
-            snap["arrays"] = {a: getattr(nb, a).clone() for a in _NB_ARRAYS}
-    return snap
+def _lists_snapshot(nb: gic.Neighbors) -> dict:
+    """The Verlet lists as they stand, copied on the device without waiting
+    for them: the flag words (among them the decision for the next gic_step
+    and the build count) and the rows and reference entries (`cur` and `at`
+    follow from them at the next check).  When a build is pending the rows
+    are not used: restoring the flags makes the next call rebuild."""
+    return {"flags": nb.flags.clone(), "arrays": {a: getattr(nb, a).clone() for a in _NB_ARRAYS}}
 
 
 def _lists_restore(nb: gic.Neighbors, snap: dict):
@@ -439,7 +439,6 @@ def _backward_stepped(ctx, g_pos, g_vel, g_scalars):
     n, prec, dev = sim.n, sim.precision, sim.device
     g_pos_n = gic.vec4(n, prec, dev)
     g_vel_n = gic.vec4(n, prec, dev)
-    log = torch.zeros(ctx.ckpt + 1, dtype=torch.int32, device=dev)
     ends, expected = [], []
 
     def sort_and_build(st: State):
@@ -460,13 +459,11 @@ def _backward_stepped(ctx, g_pos, g_vel, g_scalars):
         _copy_state(sim.A, ctx.ckpts[m])
         _lists_restore(nb, ctx.lists[m])
         sim.lists_current = True
-        log[0:1].copy_(nb.flags[4:5])
         states = []
         for k in range(L):
             states.append(sim.A.clone())
             sim.substep(alpha=False, transfer=False, sums=False)
-            log[k + 1:k + 2].copy_(nb.flags[4:5])  # list builds so far
-        counts = log[:L + 1].tolist()
+        counts = ctx.build_log[s0:s1 + 1]  # the forward pass's record: the recomputation repeats it
         built = [counts[k + 1] != counts[k] for k in range(L)]
         # the substep whose build made the lists substep k walked (-1: the checkpoint's)
         last_build = [max([j for j in range(k + 1) if built[j]], default=-1) for k in range(L)]
@@ -476,7 +473,7 @@ def _backward_stepped(ctx, g_pos, g_vel, g_scalars):
             if b != lists_of and b != k:  # restore the lists substep k walked
                 if b < 0:
                     _lists_restore(nb, ctx.lists[m])
-                    count_now = ctx.lists[m]["builds"]
+                    count_now = ctx.build_log[s0]
                 else:
                     sort_and_build(states[b])
                     count_now = 1  # a reset clears the build count

@@ -143,3 +143,16 @@ def test_capillary_parameters_and_scope_on_the_host():
     rc = L.gic_substep(C.byref(g), C.byref(bad), C.byref(empty), C.c_void_p(16), C.byref(nb), *([C.c_void_p(256)] * 5),
                        C.byref(empty), None, None, None, None, None, None, None)
     assert rc == -1 and "moisture_peak" in gic.last_error()
+
+
+def test_debug_build_compiles_and_exports_the_same_symbols():
+    """The GIC_DEBUG variant (device-side index checks that flag
+    GIC_STATUS_DEBUG_INDEX and skip the access) builds for sm_103a and has the
+    release library's interface."""
+    import subprocess
+
+    from paper_2504_00745_gb300 import build as b
+    path = b.build(debug=True)
+    syms = lambda p: {ln.split()[-1] for ln in subprocess.run(["nm", "-D", "--defined-only", p], capture_output=True,
+                                                             text=True).stdout.splitlines() if " T gic_" in ln}
+    assert syms(path) == syms(b.build()) and "gic_step" in syms(path)
