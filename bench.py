@@ -48,7 +48,7 @@ P2G_ALPHA_BYTES = 20
 # substep that keeps its Verlet lists (the gic_step graph: the decision
 # kernel + k_substep), from an ncu capture of the current kernels (ncu
 # flushes the caches first); per workload
-NCU_TRAFFIC = {("dam_break_1m", "gic_step"): 197.0e6}
+NCU_TRAFFIC = {("dam_break_1m", "gic_step"): 197.0e6, ("scale_sweep_16m", "gic_step"): 4.30e9}
 
 
 def algo_bytes(name, K, fp64=False):
@@ -402,7 +402,7 @@ def run_gpu(args, ws, rank, local):
             "config": {"workload": prob.name, "granules": n, "grid": [prob.grid.nx, prob.grid.ny, prob.grid.nz],
                        "substeps_per_step": K, "dt_sub": prob.params.dt_sub, "precision": "fp32",
                        "schedule": "one fluid step: K gic_step calls (Morton sort only when the Verlet lists, skin "
-                                   "0.15 r_max, are rebuilt; fused contact, G2P couple, integrate, P2G of F_s); "
+                                   "0.05 r_max, are rebuilt; fused contact, G2P couple, integrate, P2G of F_s); "
                                    "alpha_s and sums at the final positions",
                        "l2": "flushed between steps (512 MB write); the inputs (16M granules, 1.1 GB of fluid fields) "
                              "exceed L2 anyway; state reset to the initial packing",

@@ -413,7 +413,7 @@ int gic_p2g_adj(const GicGrid* grid, const GicParams* params, const GicGranules*
 int gic_window_workspace_size(const GicGrid* grid, int64_t n, int32_t precision, size_t* bytes);
 
 /* K substeps of Alg. 2 (SandSubstep): per substep gic_step (Verlet lists
- * with skin 0.075 h_c and 64 partners per granule, kept in the workspace; the
+ * with skin 0.025 h_c and 64 partners per granule, kept in the workspace; the
  * sort runs on list rebuilds) when state->id is set, else gic_sort,
  * gic_contact, gic_g2p_couple, gic_integrate and gic_p2g.  `state` is
  * updated in place and ends in the order of the last sort (state->id, if

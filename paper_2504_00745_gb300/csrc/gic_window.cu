@@ -154,7 +154,7 @@ extern "C" int gic_window_forward(const GicGrid* grid, const GicParams* params, 
   void* Ffl = base + L.off_ffl;
   void* af = base + L.off_af;
   void* fex = base + L.off_fex;
-  // Verlet lists (skin 0.15 h_c / 2, an upper bound of 0.15 r_max) when the state carries ids
+  // Verlet lists (skin 0.05 h_c / 2, at least 0.05 r_max since h_c >= 2 r_max) when the state carries ids
   GicNeighbors nb;
   const bool verlet = state->id != nullptr && state->n > 0;
   if (verlet) {
@@ -163,7 +163,7 @@ extern "C" int gic_window_forward(const GicGrid* grid, const GicParams* params, 
     char* q = base + L.off_nb;
     nb.n = state->n;
     nb.cap = kWindowNbCap;
-    nb.skin = 0.075 * grid->dx / grid->k_contact;
+    nb.skin = 0.025 * grid->dx / grid->k_contact;
     nb.list = (int32_t*)q;
     q += al(4 * nn * kWindowNbCap);
     nb.count = (int32_t*)q;
