@@ -47,8 +47,9 @@ P2G_ALPHA_BYTES = 20
 # DRAM bytes (read + write) of one call of the dominant entry point on a
 # substep that keeps its Verlet lists (the gic_step graph: the decision
 # kernel + k_substep), from an ncu capture of the current kernels (ncu
-# flushes the caches first); per workload
-NCU_TRAFFIC = {("dam_break_1m", "gic_step"): 197.0e6, ("scale_sweep_16m", "gic_step"): 4.30e9}
+# flushes the caches first); per workload (None where no capture of the
+# current kernels exists)
+NCU_TRAFFIC = {("scale_sweep_16m", "gic_step"): 2.41e9}
 
 
 def algo_bytes(name, K, fp64=False):

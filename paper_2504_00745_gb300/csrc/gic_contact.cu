@@ -99,66 +99,68 @@ __device__ __forceinline__ void add_pair_force(const DParams<float>& P, const Pa
   }
 }
 
-__global__ void __launch_bounds__(kTileThreads) k_contact_tile(DGrid G, DParams<float> P, int64_t n,
-                                                               const int32_t* __restrict__ cell,
-                                                               const uint4* __restrict__ pos,
-                                                               const float4* __restrict__ posf,
-                                                               const float4* __restrict__ vel,
-                                                               const uint4* __restrict__ table,
-                                                               float4* __restrict__ F, uint32_t* status) {
-  __shared__ int s_lo[3], s_hi[3];
-  __shared__ uint32_t s_start[kTileMaxCells];
-  __shared__ uint32_t s_cnt[kTileMaxCells];
-  __shared__ uint32_t s_off[kTileMaxCells + 1];
-  __shared__ float4 s_pf[kTileMaxGranules];
-  __shared__ uint32_t s_wsum[kTileThreads / 32];
-  __shared__ int s_mode;  // 0: staged, 1: global fallback
+// The CTA's staged neighbourhood in shared memory.
+struct TileShared {
+  int lo[3], hi[3];
+  uint32_t start[kTileMaxCells];
+  uint32_t cnt[kTileMaxCells];
+  uint32_t off[kTileMaxCells + 1];
+  float4 pf[kTileMaxGranules];
+  uint32_t wsum[kTileThreads / 32];
+  int mode;  // 0: staged, 1: global fallback
+};
 
-  const int64_t i = blockIdx.x * (int64_t)kTileThreads + threadIdx.x;
-  const bool valid = i < n;
-  const uint32_t epoch = __ldg(&table[0].x);
-  int cx = 0, cy = 0, cz = 0;
+struct TileBox {
+  int bx0, by0, bz0, bx, by, bz;
+};
+
+// CTA-wide (every thread calls it): the bounding box of the CTA's contact
+// cells with a one-cell halo, clipped to the grid; its table entries (start,
+// count of this epoch), their exclusive scan and the float positions of every
+// granule in the box, relative to the box corner.  sh.mode = 1 when the box or
+// its granules exceed the tile.  valid / ci: this thread's granule and cell.
+__device__ __forceinline__ TileBox tile_stage(TileShared& sh, const DGrid& G, const uint4* __restrict__ table,
+                                              uint32_t epoch, const float4* __restrict__ posf, bool valid,
+                                              int32_t ci) {
   if (threadIdx.x < 3) {
-    s_lo[threadIdx.x] = 1 << 30;
-    s_hi[threadIdx.x] = -1;
+    sh.lo[threadIdx.x] = 1 << 30;
+    sh.hi[threadIdx.x] = -1;
   }
   __syncthreads();
   if (valid) {
-    int32_t ci = cell[i];
-    cx = cell_x(ci);
-    cy = cell_y(ci);
-    cz = cell_z(ci);
-    atomicMin(&s_lo[0], cx);
-    atomicMin(&s_lo[1], cy);
-    atomicMin(&s_lo[2], cz);
-    atomicMax(&s_hi[0], cx);
-    atomicMax(&s_hi[1], cy);
-    atomicMax(&s_hi[2], cz);
+    atomicMin(&sh.lo[0], cell_x(ci));
+    atomicMin(&sh.lo[1], cell_y(ci));
+    atomicMin(&sh.lo[2], cell_z(ci));
+    atomicMax(&sh.hi[0], cell_x(ci));
+    atomicMax(&sh.hi[1], cell_y(ci));
+    atomicMax(&sh.hi[2], cell_z(ci));
   }
   __syncthreads();
-  // bounding box with a one-cell halo, clipped to the grid
-  const int bx0 = max(s_lo[0] - 1, 0), by0 = max(s_lo[1] - 1, 0), bz0 = max(s_lo[2] - 1, 0);
-  const int bx = min(s_hi[0] + 1, G.nc[0] - 1) - bx0 + 1;
-  const int by = min(s_hi[1] + 1, G.nc[1] - 1) - by0 + 1;
-  const int bz = min(s_hi[2] + 1, G.nc[2] - 1) - bz0 + 1;
-  const int ncell = bx * by * bz;
-  if (threadIdx.x == 0) s_mode = (ncell > kTileMaxCells || s_hi[0] < 0) ? 1 : 0;
+  TileBox T;
+  T.bx0 = max(sh.lo[0] - 1, 0);
+  T.by0 = max(sh.lo[1] - 1, 0);
+  T.bz0 = max(sh.lo[2] - 1, 0);
+  T.bx = min(sh.hi[0] + 1, G.nc[0] - 1) - T.bx0 + 1;
+  T.by = min(sh.hi[1] + 1, G.nc[1] - 1) - T.by0 + 1;
+  T.bz = min(sh.hi[2] + 1, G.nc[2] - 1) - T.bz0 + 1;
+  const int ncell = T.bx * T.by * T.bz;
+  if (threadIdx.x == 0) sh.mode = (ncell > kTileMaxCells || sh.hi[0] < 0) ? 1 : 0;
   __syncthreads();
-  if (s_mode == 0) {
+  if (sh.mode == 0) {
     // stage the table entries of the box
     // box index -> coordinates with float reciprocals (exact for these small integers)
-    const float ibx = 1.0f / (float)bx, ibxy = 1.0f / (float)(bx * by);
+    const float ibx = 1.0f / (float)T.bx, ibxy = 1.0f / (float)(T.bx * T.by);
     for (int b = threadIdx.x; b < ncell; b += kTileThreads) {
       int z = (int)(((float)b + 0.5f) * ibxy);
-      int rem = b - z * bx * by;
+      int rem = b - z * T.bx * T.by;
       int y = (int)(((float)rem + 0.5f) * ibx);
-      int x = bx0 + rem - y * bx;
-      y += by0;
-      z += bz0;
+      int x = T.bx0 + rem - y * T.bx;
+      y += T.by0;
+      z += T.bz0;
       uint4 e = __ldg(&table[table_index(G, x, y, z)]);
       bool ok = e.z == epoch;
-      s_start[b] = ok ? e.x : 0u;
-      s_cnt[b] = ok ? e.y : 0u;
+      sh.start[b] = ok ? e.x : 0u;
+      sh.cnt[b] = ok ? e.y : 0u;
     }
     __syncthreads();
     // exclusive scan of the counts (ncell <= 512: 4 per thread)
@@ -169,7 +171,7 @@ __global__ void __launch_bounds__(kTileThreads) k_contact_tile(DGrid G, DParams<
 #pragma unroll
       for (int k = 0; k < per; ++k) {
         int b = threadIdx.x * per + k;
-        loc[k] = b < ncell ? s_cnt[b] : 0u;
+        loc[k] = b < ncell ? sh.cnt[b] : 0u;
         sum += loc[k];
       }
       uint32_t incl = sum;
@@ -177,41 +179,63 @@ __global__ void __launch_bounds__(kTileThreads) k_contact_tile(DGrid G, DParams<
         uint32_t o = __shfl_up_sync(0xffffffffu, incl, off);
         if (lane_id() >= off) incl += o;
       }
-      if (lane_id() == 31) s_wsum[threadIdx.x >> 5] = incl;
+      if (lane_id() == 31) sh.wsum[threadIdx.x >> 5] = incl;
       __syncthreads();
       uint32_t base = 0;
-      for (int w = 0; w < (threadIdx.x >> 5); ++w) base += s_wsum[w];
+      for (int w = 0; w < (threadIdx.x >> 5); ++w) base += sh.wsum[w];
       uint32_t run = base + incl - sum;
 #pragma unroll
       for (int k = 0; k < per; ++k) {
         int b = threadIdx.x * per + k;
-        if (b < kTileMaxCells) s_off[b] = run;
+        if (b < kTileMaxCells) sh.off[b] = run;
         run += loc[k];
       }
-      if (threadIdx.x == kTileThreads - 1) s_off[kTileMaxCells] = run;
+      if (threadIdx.x == kTileThreads - 1) sh.off[kTileMaxCells] = run;
     }
     __syncthreads();
-    const uint32_t total = s_off[kTileMaxCells];
+    const uint32_t total = sh.off[kTileMaxCells];
     if (total > (uint32_t)kTileMaxGranules) {
-      if (threadIdx.x == 0) s_mode = 1;
+      if (threadIdx.x == 0) sh.mode = 1;
     } else {
-      // stage the float positions: slot t belongs to cell b with s_off[b] <= t < s_off[b + 1]
+      // stage the float positions: slot t belongs to cell b with off[b] <= t < off[b + 1]
       for (uint32_t t = threadIdx.x; t < total; t += kTileThreads) {
-        int lo = 0, hi = ncell - 1;  // last b with s_off[b] <= t
+        int lo = 0, hi = ncell - 1;  // last b with off[b] <= t
         while (lo < hi) {
           int mid = (lo + hi + 1) >> 1;
-          if (s_off[mid] <= t) lo = mid;
+          if (sh.off[mid] <= t) lo = mid;
           else hi = mid - 1;
         }
         // position in units of contact cells relative to the box corner (exact
         // differences of the absolute copies): the three cells of an x-row are
         // consecutive slots, and no cell offset is needed
-        float4 p = __ldg(&posf[s_start[lo] + (t - s_off[lo])]);
-        s_pf[t] = make_float4(p.x - (float)bx0, p.y - (float)by0, p.z - (float)bz0, p.w);
+        float4 p = __ldg(&posf[sh.start[lo] + (t - sh.off[lo])]);
+        sh.pf[t] = make_float4(p.x - (float)T.bx0, p.y - (float)T.by0, p.z - (float)T.bz0, p.w);
       }
     }
     __syncthreads();
   }
+  return T;
+}
+
+__global__ void __launch_bounds__(kTileThreads) k_contact_tile(DGrid G, DParams<float> P, int64_t n,
+                                                               const int32_t* __restrict__ cell,
+                                                               const uint4* __restrict__ pos,
+                                                               const float4* __restrict__ posf,
+                                                               const float4* __restrict__ vel,
+                                                               const uint4* __restrict__ table,
+                                                               float4* __restrict__ F, uint32_t* status) {
+  __shared__ TileShared sh;
+  const int64_t i = blockIdx.x * (int64_t)kTileThreads + threadIdx.x;
+  const bool valid = i < n;
+  const uint32_t epoch = __ldg(&table[0].x);
+  const int32_t ci = valid ? cell[i] : 0;
+  const int cx = cell_x(ci), cy = cell_y(ci), cz = cell_z(ci);
+  const TileBox T = tile_stage(sh, G, table, epoch, posf, valid, ci);
+  const int bx0 = T.bx0, by0 = T.by0, bz0 = T.bz0, bx = T.bx, by = T.by, bz = T.bz;
+  uint32_t* const s_start = sh.start;
+  uint32_t* const s_off = sh.off;
+  const float4* const s_pf = sh.pf;
+  const int s_mode = sh.mode;
   if (!valid) return;
   const uint4 pi = pos[i];
   const float4 vi = vel[i];
@@ -285,6 +309,110 @@ __global__ void __launch_bounds__(kTileThreads) k_contact_tile(DGrid G, DParams<
   if (coincident) raise_status(status, GIC_STATUS_COINCIDENT);
   if (!isfinite(F0) || !isfinite(F1) || !isfinite(F2)) raise_status(status, GIC_STATUS_NONFINITE);
   F[i] = make_float4(F0, F1, F2, 0.f);
+}
+
+// The list build of gic_step's rebuilding substep (FP32 path with float
+// copies, contact law only), on the staged neighbourhood: every granule's row
+// -- the partners within r_i + r_j + skin by the float pre-test of
+// verlet_pair, in the order of the 27-cell walk, slot = sorted index -- and its
+// reference entries; no forces (the substep then walks the fresh rows, so the
+// forces and their order are those of a build inside the substep).  The last
+// CTA records the build; if a row overflowed it leaves the rebuild word set,
+// and the substep's own 27-cell walk takes over as before.
+__global__ void __launch_bounds__(kTileThreads) k_verlet_build_tile(DGrid G, int64_t n, const int32_t* __restrict__ cell,
+                                                                    const uint4* __restrict__ pos,
+                                                                    const float4* __restrict__ posf,
+                                                                    const int32_t* __restrict__ id,
+                                                                    const uint4* __restrict__ table, NbDev nb,
+                                                                    float skin) {
+  __shared__ TileShared sh;
+  const bool rebuild = (nb.flags[kNbRebuild] | nb.flags[kNbSticky]) != 0u;  // uniform over the launch
+  const int64_t i = blockIdx.x * (int64_t)kTileThreads + threadIdx.x;
+  const bool valid = i < n;
+  const uint32_t epoch = __ldg(&table[0].x);
+  const int32_t ci = valid ? cell[i] : 0;
+  const int cx = cell_x(ci), cy = cell_y(ci), cz = cell_z(ci);
+  const TileBox T = tile_stage(sh, G, table, epoch, posf, valid, ci);
+  if (valid && rebuild) {
+    const uint4 pi = pos[i];
+    const float ri = __uint_as_float(pi.w);
+    const float4 fi = __ldg(&posf[i]);
+    int32_t* row = nb.list + i * nb.cap;
+    int cnt = 0;
+    bool over = false;
+    auto keep = [&](int64_t j) {
+      if (cnt < nb.cap)
+        row[cnt++] = (int32_t)j;
+      else
+        over = true;
+    };
+    if (sh.mode == 0) {
+      const int lx = cx - T.bx0, ly = cy - T.by0, lz = cz - T.bz0;
+      const float xi = fi.x - (float)T.bx0, yi = fi.y - (float)T.by0, zi = fi.z - (float)T.bz0;
+      const int xa = max(lx - 1, 0), xb = min(lx + 1, T.bx - 1);
+      const int bown = lx + T.bx * (ly + T.by * lz);
+      const uint32_t tself = sh.off[bown] + (uint32_t)(i - (int64_t)sh.start[bown]);
+      for (int oz = -1; oz <= 1; ++oz) {
+        const int z = lz + oz;
+        if (z < 0 || z >= T.bz) continue;
+        for (int oy = -1; oy <= 1; ++oy) {
+          const int y = ly + oy;
+          if (y < 0 || y >= T.by) continue;
+          const int rb = T.bx * (y + T.by * z);
+          const uint32_t t0 = sh.off[rb + xa], t1 = sh.off[rb + xb + 1];
+          int bj = rb + xa;
+          for (uint32_t t = t0; t < t1; ++t) {
+            while (sh.off[bj + 1] <= t) ++bj;  // the cell of slot t (cells of the row in x order)
+            if (t == tself) continue;
+            const float4 fj = sh.pf[t];
+            const float rx = fj.x - xi, ry = fj.y - yi, rz = fj.z - zi;
+            const float d2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+            const float Rs = fmaf(ri + fj.w + skin, G.inv_hc_f, kPosfTol);
+            if (d2 < Rs * Rs) keep((int64_t)sh.start[bj] + (t - sh.off[bj]));
+          }
+        }
+      }
+    } else {
+      for_each_partner(G, table, epoch, i, cx, cy, cz, [&](int64_t j, int, int, int) {
+        const float4 fj = __ldg(&posf[j]);
+        const float rx = fj.x - fi.x, ry = fj.y - fi.y, rz = fj.z - fi.z;
+        const float d2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+        const float Rs = fmaf(ri + fj.w + skin, G.inv_hc_f, kPosfTol);
+        if (d2 < Rs * Rs) keep(j);
+      });
+    }
+    nb.count[i] = cnt;
+    nb.at[i] = (int32_t)i;
+    nb.cur[i] = (int32_t)i;
+    nb.ref_cell[i] = ci;
+    reinterpret_cast<uint4*>(nb.ref_pos)[i] = pi;
+    const int32_t idi = id[i];
+    if (idi >= 0 && (int64_t)idi < n) nb.slot[idi] = (int32_t)i;
+    if (over) atomicOr(&nb.flags[kNbOverflow], 1u);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&nb.flags[kNbCounter], 1u) == gridDim.x - 1) {
+      __threadfence();
+      if (rebuild && atomicExch(&nb.flags[kNbOverflow], 0u) == 0u) {  // a complete build: the substep walks it
+        nb.flags[kNbSticky] = 0u;
+        nb.flags[kNbRebuild] = 0u;
+        nb.flags[kNbBuilds] += 1u;
+      }
+      nb.flags[kNbCounter] = 0u;
+      __threadfence();
+    }
+  }
+}
+
+int launch_build_tile(const DGrid& G, const GicGranules* sorted, const void* table, const NbDev& d, double skin,
+                      cudaStream_t stream) {
+  if (sorted->n == 0) return GIC_OK;
+  k_verlet_build_tile<<<grid_blocks(sorted->n, kTileThreads), kTileThreads, 0, stream>>>(
+      G, sorted->n, sorted->cell, (const uint4*)sorted->pos, (const float4*)sorted->posf, sorted->id,
+      (const uint4*)table, d, (float)skin);
+  return GIC_OK;
 }
 
 // kList: walk the Verlet rows (nb) instead of the 27 cells; the last CTA

@@ -521,6 +521,12 @@ int verlet_view(const DGrid& G, const GicGranules* s, const void* table, const G
 int verlet_check(const DGrid& G, const GicGranules* s, const void* table, const GicNeighbors* nb,
                  cudaStream_t stream, const char* what, NbDev* out, GicGranules* copy_to, int32_t* perm);
 
+// The staged list build of gic_step's rebuilding substep (FP32 path with
+// float copies): rows and reference entries of the sorted state, no forces;
+// records the build unless a row overflowed (see gic_contact.cu).
+int launch_build_tile(const DGrid& G, const GicGranules* sorted, const void* table, const NbDev& d, double skin,
+                      cudaStream_t stream);
+
 // The list build of granule i: walks the 27 cells with the pre-test radius
 // r_i + r_j + skin, writes row i (slot = sorted index) and its reference
 // entries, and hands every partner in contact to f(j, g).

@@ -526,6 +526,10 @@ static int build_step_graph(StepGraph& sg, const DGrid& G, const GicGrid* grid, 
     int uncounted = 0;
     rc = add_branch(g, decide, h_rebuild, cs, [&](cudaStream_t st) {
       int r = sort_gated(grid, state, sorted, perm, cell_table, ws, ws_bytes, nullptr, st);
+      // FP32 with float copies and the contact law alone: the rows are built on
+      // the staged neighbourhood first, and the substep walks them
+      if (r == GIC_OK && state->precision == GIC_FP32 && sorted->posf && params->sigma == 0.0)
+        r = launch_build_tile(G, sorted, cell_table, d, nb->skin, st);
       if (r == GIC_OK)
         r = substep_launch(G, params, sorted, cell_table, nb, d, u, v, w, p, alpha_f, next, nullptr, alpha_s, Fs_u,
                            Fs_v, Fs_w, sums2, st, &uncounted);
