@@ -205,6 +205,10 @@ __device__ __forceinline__ d4 ldg(const d4* p) {
   return r;
 }
 
+// Prefetch of the line holding p into L2 (no register is tied up until the
+// value is loaded).
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
 __device__ __forceinline__ float radius_of(const uint4& p) { return __uint_as_float(p.w); }
 __device__ __forceinline__ double radius_of(const d4& p) { return p.w; }
 

@@ -33,6 +33,20 @@ __global__ void __launch_bounds__(kSubstepThreads, sizeof(T) == 4 ? 4 : 2) k_sub
   const int64_t i = blockIdx.x * (int64_t)kSubstepThreads + threadIdx.x;
   const bool valid = i < n;
   const int32_t ci = valid ? cell[i] : 0;
+  // the granule's own records, prefetched into L2 before the CTA's tile
+  // barriers (the loads themselves come after them; no register is held)
+  if (valid) {
+    prefetch_l2(&pos[i]);
+    prefetch_l2(&vel[i]);
+    if (posf) prefetch_l2(&posf[i]);
+    if (!rebuild) {
+      const int32_t sl = nb.ident ? (int32_t)i : nb.at[i];
+      prefetch_l2(&nb.count[sl]);
+      prefetch_l2(nb.list + (int64_t)sl * nb.cap);
+      prefetch_l2(&nb.ref_cell[sl]);
+      prefetch_l2(reinterpret_cast<const pos_t<T>*>(nb.ref_pos) + sl);
+    }
+  }
   // FP32: the CTA's tile (fields staged for G2P, F_s / alpha_s accumulators)
   SubBox B{};
   if constexpr (sizeof(T) == 4) B = sub_tile_begin(sh, G, Fd, valid, ci, do_a, do_f);
