@@ -149,3 +149,48 @@ def test_bridges_need_the_fused_path():
     sim = Simulator.from_problem(prob, FP32, fused=False)
     with pytest.raises(gic.GicError, match="capillary"):
         sim.run(1)
+
+
+@pytest.mark.slow
+def test_full_size_bridges_one_substep():
+    """The 16M-granule sweep (384^3, FCC neighbours 0.145 r apart before the
+    jitter, so a fraction of the pairs sit inside d_r = 0.075 r) with
+    surface tension 0.07 N/m: one gic_step in the benchmark's launch
+    configuration, wet and dry, and the velocity change the bridges make,
+    per granule, against the oracle's on a 100k-granule box run with a halo
+    wide enough that the box's interior is exact (2 r_max + d_r + 2 dx)."""
+    import math
+
+    base = gi.make("scale_sweep_16m")
+    wet = dataclasses.replace(base, params=dataclasses.replace(base.params, sigma=0.07))
+    got = {}
+    for name, p in (("wet", wet), ("dry", base)):
+        sim = sim_for(p, FP32)
+        sim.run(1)
+        x, v = sim.positions()
+        torch.cuda.synchronize()
+        assert gic.gic_check_status() == 0
+        got[name] = v.cpu().numpy()
+        del sim
+        torch.cuda.empty_cache()
+    x0 = base.positions()
+    r_max = float(base.r.max())
+    d_r = oracle.rupture(r_max, 1e-4 * 4.0 / 3.0 * math.pi * r_max ** 3)
+    halo = 2 * r_max + d_r + 2 * base.grid.dx
+    lo_all, hi_all = x0.min(0), x0.max(0)
+    w = np.sqrt((hi_all[0] - lo_all[0]) * (hi_all[1] - lo_all[1]) * 100_000 / base.n)
+    c = 0.5 * (lo_all[:2] + hi_all[:2])
+    lo = np.array([c[0] - w / 2, c[1] - w / 2, -1.0])
+    hi = np.array([c[0] + w / 2, c[1] + w / 2, 2.0])
+    inside = lambda pad: np.all((x0 >= lo - pad) & (x0 < hi + pad), axis=1)
+    box, core = np.nonzero(inside(halo))[0], np.nonzero(inside(0.0))[0]
+    assert len(core) > 50_000
+    sub = lambda p: dataclasses.replace(p, cell=p.cell[box], q=p.q[box], r=p.r[box], v=p.v[box])
+    ref_w = oracle.run(sub(wet), K=1)
+    ref_d = oracle.run(sub(base), K=1)
+    in_core = np.isin(box, core)
+    dv_o = (ref_w["v"] - ref_d["v"])[in_core]
+    dv_g = (got["wet"] - got["dry"])[box][in_core]
+    scale = np.abs(dv_o).max()
+    assert scale > 0.0 and np.count_nonzero(np.abs(dv_o).max(axis=1) > 0) > 100  # bridges act on many granules
+    assert np.abs(dv_g - dv_o).max() <= 2e-3 * scale
