@@ -76,6 +76,9 @@ def parse():
                     help="with --profile-substeps: then one gic_project call on the window's alpha_s (tol 1e-9)")
     ap.add_argument("--profile-window", action="store_true",
                     help="with --profile-substeps: the differentiable window (forward + backward) instead")
+    ap.add_argument("--profile-granules", type=int, default=0,
+                    help="with --profile-substeps: the workload's generator at this many granules (the same lattice "
+                         "and grid, a thinner bed), for captures that must stay small")
     ap.add_argument("--profile-direct", action="store_true",
                     help="with --profile-substeps: gic_sort + gic_substep every substep (no CUDA graph), so that "
                          "a profiler sees each kernel")
@@ -534,7 +537,8 @@ def run_e2e(prob, sim, gic, torch, np, dev, stream, steps):
     d2h = sum(t.numel() * t.element_size() for t in [o_x, o_v, o_a, *o_fs, o_s])
     sec = statistics.mean(times)
     return {"value": n * K / sec, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-            "ms_per_step": 1000 * sec, "api": "gic_window_forward_host (C ABI, pinned host buffers)"}
+            "ms_per_step": 1000 * sec, "ms_per_call": [1000 * t for t in times],
+            "api": "gic_window_forward_host (C ABI, pinned host buffers)"}
 
 
 def run_adjoint(prob, prec, torch, dev, ckpt=10):
@@ -741,7 +745,7 @@ def run_profile(args):
     from paper_2504_00745_gb300 import gic
     from paper_2504_00745_gb300.window import GicWindow, Simulator
 
-    prob = gi.make(args.workload)
+    prob = gi.make(args.workload, **({"n": args.profile_granules} if args.profile_granules else {}))
     prec = gic.GIC_FP32 if args.precision == "fp32" else gic.GIC_FP64
     sim = Simulator.from_problem(prob, prec)
     if args.profile_window:
@@ -761,7 +765,8 @@ def run_profile(args):
         extra = {"projection_outer": out["outer"], "projection_inner": out["inner"]}
     torch.cuda.synchronize()
     st = gic.gic_check_status()
-    print(json.dumps({"profile_substeps": args.profile_substeps, "workload": prob.name, "precision": args.precision,
+    print(json.dumps({"profile_substeps": args.profile_substeps, "workload": prob.name, "granules": prob.n,
+                      "precision": args.precision,
                       "device_status": st, "launches": gic.launch_count(), **extra}))
 
 

@@ -596,6 +596,48 @@ __device__ __forceinline__ void sub_add_face(SubTile& sh, const SubBox& B, const
   }
 }
 
+// F_s deposits spread over the lanes.  Consecutive sorted granules share
+// stencil samples, and a shared-memory atomic takes one pass per lane on the
+// same address, so granule g's deposits are made by lane g / W of warp g % W
+// (W warps): the lanes of a warp then hold granules W apart, mostly in other
+// cells.  Each thread first parks its granule's inputs (packed MAC cell,
+// in-cell fractions, exchange force) in the alpha_s limbs' space, which a
+// call without alpha_s leaves unused; a CTA barrier separates the two sides.
+// The tile receives the same integer deposits as from the granules' own
+// threads.
+constexpr int kSpreadWords = 7;
+constexpr int kSpreadStride = 256 + 8;  // 256 granules, bank-skewed
+static_assert(kSpreadWords * kSpreadStride <= 3 * kSubTile, "spread inputs exceed the alpha_s limbs");
+__device__ __forceinline__ int spread_slot(int g) { return g + (g >> 5); }
+
+__device__ __forceinline__ void spread_put(SubTile& sh, bool valid, const int m[3], const float t[3],
+                                           const float fc[3]) {
+  float* s = reinterpret_cast<float*>(&sh.a[0][0]);
+  const int k = spread_slot(threadIdx.x);
+  s[k] = __int_as_float(valid ? (m[0] | (m[1] << 10) | (m[2] << 20)) : -1);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    s[(1 + a) * kSpreadStride + k] = t[a];
+    s[(4 + a) * kSpreadStride + k] = fc[a];
+  }
+}
+
+__device__ __forceinline__ void spread_deposit(SubTile& sh, const SubBox& B, const DGrid& G, float* const Fs[3],
+                                               float inv_unit) {
+  const int W = blockDim.x >> 5;
+  const int g = lane_id() * W + (threadIdx.x >> 5);
+  const float* s = reinterpret_cast<const float*>(&sh.a[0][0]);
+  const int k = spread_slot(g);
+  const int pm = __float_as_int(s[k]);
+  if (pm < 0) return;
+  const int m[3] = {pm & 1023, (pm >> 10) & 1023, pm >> 20};
+  const float t[3] = {s[kSpreadStride + k], s[2 * kSpreadStride + k], s[3 * kSpreadStride + k]};
+#pragma unroll
+  for (int comp = 0; comp < 3; ++comp)
+    sub_add_face(sh, B, G, Fs[comp], comp, make_stencil<float>(G, m, t, comp), s[(4 + comp) * kSpreadStride + k],
+                 inv_unit);
+}
+
 // alpha_s deposits of one granule at its new position: into the tile when
 // its stencil lies in the box, else straight to global memory (both exact).
 __device__ __forceinline__ void sub_add_alpha(SubTile& sh, const SubBox& B, const DGrid& G, unsigned long long* acc,

@@ -131,11 +131,18 @@ __global__ void __launch_bounds__(kSubstepThreads, sizeof(T) == 4 ? 4 : 2) k_sub
   if constexpr (sizeof(T) == 4) {
     const float fc[3] = {P.exch * fe[0], P.exch * fe[1], P.exch * fe[2]};
     float unit = 0.f, inv_unit = 0.f;
+    const bool spread = do_f && !do_a && B.tile;  // uniform over the CTA
     if (do_f) {  // the CTA's fixed-point unit
       float Mt = 0.f;
       if (valid) {
         const float m = fmaxf(fabsf(fc[0]), fmaxf(fabsf(fc[1]), fabsf(fc[2])));
         Mt = m <= 3.0e38f ? m : INFINITY;  // NaN or inf: no fixed point for this CTA
+      }
+      if (spread) {  // park the deposit's inputs before the barrier in sub_fs_scale
+        int m[3] = {0, 0, 0};
+        float t[3] = {0.f, 0.f, 0.f};
+        if (valid) granule_mac<float>(G, ci, pi, m, t);
+        spread_put(sh, valid, m, t, fc);
       }
       inv_unit = sub_fs_scale(sh, B, Mt, unit);
     }
@@ -147,7 +154,9 @@ __global__ void __launch_bounds__(kSubstepThreads, sizeof(T) == 4 ? 4 : 2) k_sub
       alpha_deposits(G, co, po, ia, va, S);
       sub_add_alpha(sh, B, G, (unsigned long long*)alpha, ia, va);
     }
-    if (valid && do_f) {
+    if (spread && inv_unit != 0.f) {
+      spread_deposit(sh, B, G, Fs, inv_unit);
+    } else if (valid && do_f) {
       int m[3];
       float t[3];
       granule_mac<float>(G, ci, pi, m, t);
