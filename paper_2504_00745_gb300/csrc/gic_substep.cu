@@ -19,7 +19,11 @@ namespace gic {
 
 constexpr int kSubstepThreads = 256;
 
-template <typename T>
+// kKeep: the kernel of gic_step's list-keeping branch without the capillary
+// force (its lists are valid by the branch's condition, so it carries neither
+// the build nor the bridge code: a smaller instruction footprint); otherwise
+// the general kernel, which reads from the list flags whether it rebuilds.
+template <typename T, bool kKeep>
 __global__ void __launch_bounds__(kSubstepThreads, sizeof(T) == 4 ? 4 : 2) k_substep(
     DGrid G, DParams<T> P, int64_t n, const int32_t* __restrict__ cell, const pos_t<T>* __restrict__ pos,
     const float4* __restrict__ posf, const vec_t<T>* __restrict__ vel, const int32_t* __restrict__ id, NbDev nb,
@@ -28,7 +32,7 @@ __global__ void __launch_bounds__(kSubstepThreads, sizeof(T) == 4 ? 4 : 2) k_sub
     vec_t<T>* __restrict__ fex_out, double* __restrict__ alpha, T* __restrict__ Fs_u, T* __restrict__ Fs_v,
     T* __restrict__ Fs_w, double* __restrict__ sums, uint32_t* status) {
   __shared__ std::conditional_t<sizeof(T) == 4, SubTile, int> sh;  // FP32 path only
-  const bool rebuild = (nb.flags[kNbRebuild] | nb.flags[kNbSticky]) != 0u;  // uniform over the launch
+  const bool rebuild = !kKeep && (nb.flags[kNbRebuild] | nb.flags[kNbSticky]) != 0u;  // uniform over the launch
   const bool do_a = alpha != nullptr, do_f = Fs_u != nullptr;
   const int64_t i = blockIdx.x * (int64_t)kSubstepThreads + threadIdx.x;
   const bool valid = i < n;
@@ -69,7 +73,7 @@ __global__ void __launch_bounds__(kSubstepThreads, sizeof(T) == 4 ? 4 : 2) k_sub
       const int cx = cell_x(ci), cy = cell_y(ci), cz = cell_z(ci);
       const bool has_f = sizeof(T) == 4 && posf != nullptr;
       const float4 fi = has_f ? __ldg(&posf[i]) : make_float4(0.f, 0.f, 0.f, 0.f);
-      if (P.cap) {  // with the capillary bridges (Sec. 5.4): contacts and bridge candidates
+      if (!kKeep && P.cap) {  // with the capillary bridges (Sec. 5.4): contacts and bridge candidates
         const T sri = moisture_ratio_at(G, P, Fd.af, ci, pi, (T*)nullptr);
         auto near = [&](int64_t j, int32_t cj, const pos_t<T>& pj, const PairGeom<T>& g) {
           if (g.overlap > T(0))
@@ -356,7 +360,8 @@ namespace gic {
 static int substep_launch(const DGrid& G, const GicParams* params, const GicGranules* s, const void* cell_table,
                           const GicNeighbors* nb, const NbDev& d, const void* u, const void* v, const void* w,
                           const void* p, const void* alpha_f, GicGranules* next, void* f_ex, double* alpha_s,
-                          void* Fs_u, void* Fs_v, void* Fs_w, double* sums2, cudaStream_t stream, int* launches) {
+                          void* Fs_u, void* Fs_v, void* Fs_w, double* sums2, cudaStream_t stream, int* launches,
+                          bool keep = false) {
   int rc;
   const int64_t ncell = (int64_t)G.nx * G.ny * G.nz;
   if (alpha_s) {
@@ -368,7 +373,8 @@ static int substep_launch(const DGrid& G, const GicParams* params, const GicGran
     if (s->precision == GIC_FP32) {
       DParams<float> P;
       if ((rc = make_params(params, &P))) return rc;
-      k_substep<float><<<blocks, kSubstepThreads, 0, stream>>>(
+      auto kern = keep && !P.cap ? k_substep<float, true> : k_substep<float, false>;
+      kern<<<blocks, kSubstepThreads, 0, stream>>>(
           G, P, s->n, s->cell, (const uint4*)s->pos, (const float4*)s->posf, (const float4*)s->vel, s->id, d,
           (const uint4*)cell_table, (float)nb->skin, fields<float>(u, v, w, p, alpha_f), next->cell,
           (uint4*)next->pos, (float4*)next->vel, next->id, (float4*)next->posf, (float4*)f_ex, alpha_s,
@@ -376,7 +382,8 @@ static int substep_launch(const DGrid& G, const GicParams* params, const GicGran
     } else {
       DParams<double> P;
       if ((rc = make_params(params, &P))) return rc;
-      k_substep<double><<<blocks, kSubstepThreads, 0, stream>>>(
+      auto kern = keep && !P.cap ? k_substep<double, true> : k_substep<double, false>;
+      kern<<<blocks, kSubstepThreads, 0, stream>>>(
           G, P, s->n, s->cell, (const d4*)s->pos, nullptr, (const d4*)s->vel, s->id, d, (const uint4*)cell_table,
           nb->skin, fields<double>(u, v, w, p, alpha_f), next->cell, (d4*)next->pos, (d4*)next->vel, next->id,
           nullptr, (d4*)f_ex, alpha_s, (double*)Fs_u, (double*)Fs_v, (double*)Fs_w, sums2, status_word());
@@ -562,7 +569,7 @@ static int build_step_graph(StepGraph& sg, const DGrid& G, const GicGrid* grid, 
     // 3. the branch that keeps the lists: the substep straight from the state
     rc = add_branch(g, decide, h_keep, cs, [&](cudaStream_t st) {
       return substep_launch(G, params, state, cell_table, nb, d, u, v, w, p, alpha_f, next, nullptr, alpha_s, Fs_u,
-                            Fs_v, Fs_w, sums2, st, &launches);
+                            Fs_v, Fs_w, sums2, st, &launches, true);
     });
     if (rc) break;
     if (cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) {
