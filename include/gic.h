@@ -4,8 +4,9 @@
  * The library implements, as CUDA kernels, the per-substep granule-grid
  * coupling of the Granule-In-Cell (GIC) method (Tang, Zhu, Ni, Chen, "The
  * Granule-In-Cell Method for Simulating Sand-Water Mixtures", ACM TOG 44(6),
- * 2025): Algorithm 2 (SandSubstep) without the capillary / wetting terms,
- * plus a Morton cell sort for the contact neighbour search and a hand-written
+ * 2025): Algorithm 2 (SandSubstep), with the capillary form of the
+ * concentration-gradient force (Sec. 5.4) in the fused entry points, plus a
+ * Morton cell sort for the contact neighbour search and a hand-written
  * adjoint of every step.
  *
  * One substep is
@@ -300,7 +301,8 @@ int gic_substep(const GicGrid* grid, const GicParams* params, const GicGranules*
  *   pointers: buffers must stay allocated while calls with them may come.
  *   Arguments as for gic_sort and gic_substep (state, next and sorted must
  *   carry ids and share no array); errors as for those calls, plus
- *   GIC_ERR_CUDA if a graph cannot be built. */
+ *   GIC_ERR_CUDA if a graph cannot be built.  With sums2 the first 32 bytes
+ *   of ws also hold the exact alpha_s totals while the call runs. */
 int gic_step(const GicGrid* grid, const GicParams* params, const GicGranules* state, GicGranules* next,
              GicGranules* sorted, int32_t* perm, void* cell_table, void* ws, size_t ws_bytes, const GicNeighbors* nb,
              const void* u, const void* v, const void* w, const void* p, const void* alpha_f, double* alpha_s,

@@ -89,11 +89,13 @@ __global__ void __launch_bounds__(256) k_g2p_adj(DGrid G, DParams<T> P, int64_t 
 
 // ------------------------------------------------------------------ P2G
 
-__global__ void k_zero(double* __restrict__ a, int64_t m, double* __restrict__ sums) {
+__global__ void k_zero(double* __restrict__ a, int64_t m, double* __restrict__ sums,
+                       unsigned long long* __restrict__ scratch) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (; i < m; i += stride) a[i] = 0.0;
   if (sums && blockIdx.x == 0 && threadIdx.x < 2) sums[threadIdx.x] = 0.0;
+  if (scratch && blockIdx.x == 0 && threadIdx.x < 4) scratch[threadIdx.x] = 0ull;
 }
 
 __global__ void k_alpha_sum(const double* __restrict__ a, int64_t m, double dx3, double* __restrict__ sums) {
@@ -405,6 +407,69 @@ __global__ void __launch_bounds__(kTotalThreads)
   cluster_sync();  // no CTA leaves while CTA 0 may still read its shared memory
 }
 
+// The same totals in the in-place conversion pass, when the caller lends 32
+// bytes of global scratch (zeroed with the grid): every CTA adds its cells'
+// 128-bit sum into the scratch with two 64-bit atomics (the low word's carry
+// read from its old value), and the CTA that takes the last ticket rounds
+// both totals.  The sum is an integer, so neither the CTAs' order nor the
+// timing changes it, and the cells are read once instead of twice.
+constexpr int kFinishThreads = 256;
+__global__ void __launch_bounds__(kFinishThreads)
+    k_alpha_finish_total_f32(double* __restrict__ a, int64_t m, int vec, double dx3, double* __restrict__ sums,
+                             unsigned long long* __restrict__ scratch) {
+  __shared__ unsigned long long s_lo[kFinishThreads / 32], s_hi[kFinishThreads / 32];
+  U128 t{0ull, 0ull};
+  const int64_t tid = blockIdx.x * (int64_t)kFinishThreads + threadIdx.x;
+  const int64_t S = (int64_t)gridDim.x * kFinishThreads;
+  long long* ai = reinterpret_cast<long long*>(a);
+  if (vec) {  // pairs of cells, 16-byte loads and stores
+    longlong2* a2 = reinterpret_cast<longlong2*>(a);
+    const int64_t m2 = m >> 1;
+    for (int64_t p = tid; p < m2; p += S) {
+      const longlong2 v = a2[p];
+      add128(t, (unsigned long long)v.x, 0ull);
+      add128(t, (unsigned long long)v.y, 0ull);
+      reinterpret_cast<double2*>(a)[p] = make_double2(i64_scaled_to_double(v.x, -53), i64_scaled_to_double(v.y, -53));
+    }
+    if ((m & 1) && tid == 0) {
+      const long long v = ai[m - 1];
+      add128(t, (unsigned long long)v, 0ull);
+      a[m - 1] = i64_scaled_to_double(v, -53);
+    }
+  } else {
+    for (int64_t i = tid; i < m; i += S) {
+      const long long v = ai[i];
+      add128(t, (unsigned long long)v, 0ull);
+      a[i] = i64_scaled_to_double(v, -53);
+    }
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    const unsigned long long lo = __shfl_down_sync(0xffffffffu, t.lo, off);
+    const unsigned long long hi = __shfl_down_sync(0xffffffffu, t.hi, off);
+    add128(t, lo, hi);
+  }
+  if (lane_id() == 0) {
+    s_lo[threadIdx.x >> 5] = t.lo;
+    s_hi[threadIdx.x >> 5] = t.hi;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    U128 c{0ull, 0ull};
+    for (int w = 0; w < kFinishThreads / 32; ++w) add128(c, s_lo[w], s_hi[w]);
+    const unsigned long long old = atomicAdd(&scratch[0], c.lo);
+    atomicAdd(&scratch[1], c.hi + (old + c.lo < old ? 1ull : 0ull));
+    __threadfence();
+    if (atomicAdd(&scratch[2], 1ull) == (unsigned long long)gridDim.x - 1ull) {  // the last CTA
+      __threadfence();
+      const U128 cells{atomicAdd(&scratch[0], 0ull), atomicAdd(&scratch[1], 0ull)};
+      const U128 grains{*reinterpret_cast<const unsigned long long*>(&sums[1]),
+                        *reinterpret_cast<const unsigned long long*>(&sums[0])};
+      sums[0] = u128_scaled_to_double(cells, -53) * dx3;
+      sums[1] = u128_scaled_to_double(grains, -53) * dx3;
+    }
+  }
+}
+
 // Adjoint of P2G: G2P-shaped gathers of the grid gradients.
 template <typename T>
 __global__ void __launch_bounds__(256) k_p2g_adj(DGrid G, DParams<T> P, int64_t n,
@@ -501,14 +566,22 @@ static int launch_alpha_total(double* alpha_s, int64_t ncell, double dx3, double
 
 // alpha_s accumulation around a P2G pass: zero the grid (and sums) before,
 // then convert (FP32 fixed point -> double) or sum (FP64) after.
-int alpha_begin(double* alpha_s, int64_t ncell, double* sums2, cudaStream_t stream) {
-  k_zero<<<1184, 256, 0, stream>>>(alpha_s, ncell, sums2);
+int alpha_begin(double* alpha_s, int64_t ncell, double* sums2, cudaStream_t stream, void* scratch) {
+  k_zero<<<1184, 256, 0, stream>>>(alpha_s, ncell, sums2, sums2 ? (unsigned long long*)scratch : nullptr);
   count_launches(1);
   return GIC_OK;
 }
 
-int alpha_end(const DGrid& G, int32_t precision, double* alpha_s, int64_t ncell, double* sums2, cudaStream_t stream) {
+int alpha_end(const DGrid& G, int32_t precision, double* alpha_s, int64_t ncell, double* sums2, cudaStream_t stream,
+              void* scratch) {
   if (precision == GIC_FP32) {
+    if (sums2 && scratch) {  // the totals inside the conversion pass
+      k_alpha_finish_total_f32<<<1184, kFinishThreads, 0, stream>>>(
+          alpha_s, ncell, ((uintptr_t)alpha_s % 16 == 0) ? 1 : 0, G.dx * G.dx * G.dx, sums2,
+          (unsigned long long*)scratch);
+      count_launches(1);
+      return GIC_OK;
+    }
     if (sums2) {
       if (int rc = launch_alpha_total(alpha_s, ncell, G.dx * G.dx * G.dx, sums2, stream)) return rc;
       count_launches(1);
@@ -610,7 +683,7 @@ extern "C" int gic_p2g(const GicGrid* grid, const GicParams* params, const GicGr
   int64_t ncell = (int64_t)G.nx * G.ny * G.nz;
   int launches = 0;
   if (alpha_s) {
-    k_zero<<<1184, 256, 0, stream>>>(alpha_s, ncell, sums2);
+    k_zero<<<1184, 256, 0, stream>>>(alpha_s, ncell, sums2, nullptr);
     ++launches;
   }
   if (n > 0 && (alpha_s || fs)) {
@@ -657,7 +730,7 @@ extern "C" int gic_p2g_alpha_atomic64(const GicGrid* grid, const GicGranules* st
     return set_error(GIC_ERR_INVALID, "gic_p2g_alpha_atomic64: the state must be of the FP32 path");
   if (!alpha_s) return set_error(GIC_ERR_INVALID, "gic_p2g_alpha_atomic64: alpha_s is NULL");
   const int64_t ncell = (int64_t)G.nx * G.ny * G.nz;
-  k_zero<<<1184, 256, 0, stream>>>(alpha_s, ncell, nullptr);
+  k_zero<<<1184, 256, 0, stream>>>(alpha_s, ncell, nullptr, nullptr);
   int launches = 1;
   if (state->n > 0) {
     DParams<float> P{};

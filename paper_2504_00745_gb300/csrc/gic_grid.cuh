@@ -701,9 +701,13 @@ inline Fields<T> fields(const void* u, const void* v, const void* w, const void*
   return F;
 }
 
-int alpha_begin(double* alpha_s, int64_t ncell, double* sums2, cudaStream_t stream);
+// scratch (optional): 32 bytes of 16-byte aligned global memory the caller
+// lends for the exact totals; with it the totals come out of the conversion
+// pass (one read of the grid), without it from a separate cluster pass.
+int alpha_begin(double* alpha_s, int64_t ncell, double* sums2, cudaStream_t stream, void* scratch = nullptr);
 // one-time per-device set-up of the exact totals' kernel (call before any capture)
 int alpha_prepare();
-int alpha_end(const DGrid& G, int32_t precision, double* alpha_s, int64_t ncell, double* sums2, cudaStream_t stream);
+int alpha_end(const DGrid& G, int32_t precision, double* alpha_s, int64_t ncell, double* sums2, cudaStream_t stream,
+              void* scratch = nullptr);
 
 }  // namespace gic

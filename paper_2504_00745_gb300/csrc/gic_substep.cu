@@ -361,11 +361,11 @@ static int substep_launch(const DGrid& G, const GicParams* params, const GicGran
                           const GicNeighbors* nb, const NbDev& d, const void* u, const void* v, const void* w,
                           const void* p, const void* alpha_f, GicGranules* next, void* f_ex, double* alpha_s,
                           void* Fs_u, void* Fs_v, void* Fs_w, double* sums2, cudaStream_t stream, int* launches,
-                          bool keep = false) {
+                          bool keep = false, void* scratch = nullptr) {
   int rc;
   const int64_t ncell = (int64_t)G.nx * G.ny * G.nz;
   if (alpha_s) {
-    alpha_begin(alpha_s, ncell, sums2, stream);
+    alpha_begin(alpha_s, ncell, sums2, stream, scratch);
     ++*launches;
   }
   if (s->n > 0) {
@@ -392,7 +392,7 @@ static int substep_launch(const DGrid& G, const GicParams* params, const GicGran
     ++*launches;
   }
   if (alpha_s) {
-    alpha_end(G, s->precision, alpha_s, ncell, sums2, stream);
+    alpha_end(G, s->precision, alpha_s, ncell, sums2, stream, scratch);
     ++*launches;
   }
   return GIC_OK;
@@ -562,14 +562,14 @@ static int build_step_graph(StepGraph& sg, const DGrid& G, const GicGrid* grid, 
         r = launch_build_tile(G, sorted, cell_table, d, nb->skin, st);
       if (r == GIC_OK)
         r = substep_launch(G, params, sorted, cell_table, nb, d, u, v, w, p, alpha_f, next, nullptr, alpha_s, Fs_u,
-                           Fs_v, Fs_w, sums2, st, &uncounted);
+                           Fs_v, Fs_w, sums2, st, &uncounted, false, ws);
       return r;
     });
     if (rc) break;
     // 3. the branch that keeps the lists: the substep straight from the state
     rc = add_branch(g, decide, h_keep, cs, [&](cudaStream_t st) {
       return substep_launch(G, params, state, cell_table, nb, d, u, v, w, p, alpha_f, next, nullptr, alpha_s, Fs_u,
-                            Fs_v, Fs_w, sums2, st, &launches, true);
+                            Fs_v, Fs_w, sums2, st, &launches, true, ws);
     });
     if (rc) break;
     if (cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) {
