@@ -80,7 +80,7 @@ __device__ __forceinline__ T moisture_ratio_at(const DGrid& G, const DParams<T>&
   L.nsz = G.nz;
   L.dbg = G.dbg;
   T g[3];
-  const T a = interp<T>(S, L, (T)G.inv_dx, gsr ? g : nullptr);
+  const T a = interp<T>(S, L, grid_inv_dx<T>(G), gsr ? g : nullptr);
   if (!(a < T(1))) {
     if (gsr) gsr[0] = gsr[1] = gsr[2] = T(0);
     return T(INFINITY);

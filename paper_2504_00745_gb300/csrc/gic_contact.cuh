@@ -195,12 +195,15 @@ __device__ __forceinline__ bool wall_geom(const DGrid& G, const uint4& p, int a,
   float Ph = r * G.s_hi;
   float Pl = fmaf(r, G.s_hi, -Ph) + r * G.s_lo;
   float ov;
-  if (Ph >= 16777216.0f)
-    ov = (float)((long long)Ph - gq) + Pl;  // Ph is an integer here
+  // gq <= 2^30; 32-bit conversions where the values fit (the 64-bit ones run on the FP64 pipe)
+  if (Ph >= 2147483648.0f)
+    ov = (float)((long long)Ph - gq) + Pl;
+  else if (Ph >= 16777216.0f)
+    ov = (float)((int)Ph - (int)gq) + Pl;  // Ph is an integer here
   else
-    ov = (Ph - (float)gq) + Pl;
+    ov = (Ph - (float)(int)gq) + Pl;
   if (!(ov > 0.0f)) return false;
-  gap = (float)gq * G.unit_f;
+  gap = (float)(int)gq * G.unit_f;
   overlap = ov * G.unit_f;
   return true;
 }

@@ -36,7 +36,7 @@ __device__ __forceinline__ GradPLoad<T> gradp_loader(const DGrid& G, const T* p,
   L.ny = G.ny;
   L.nz = G.nz;
   L.comp = comp;
-  L.inv_dx = (T)G.inv_dx;
+  L.inv_dx = grid_inv_dx<T>(G);
   L.dbg = G.dbg;
   return L;
 }
@@ -53,7 +53,7 @@ __device__ __forceinline__ T g2p_granule_with(const DGrid& G, const DParams<T>& 
   T t[3];
   granule_mac<T>(G, cell, pi, m, t);
   T uf[3], gp[3];
-  T inv_dx = (T)G.inv_dx;
+  T inv_dx = grid_inv_dx<T>(G);
 #pragma unroll
   for (int comp = 0; comp < 3; ++comp) {
     Stencil3<T> S = make_stencil<T>(G, m, t, comp);
@@ -100,7 +100,7 @@ __device__ __forceinline__ T g2p_adj_granule(const DGrid& G, const DParams<T>& P
   granule_mac<T>(G, cell, pi, m, t);
   const T* uvw[3] = {Fd.u, Fd.v, Fd.w};
   T uf[3], gu[3][3], ggp[3][3];
-  const T inv_dx = (T)G.inv_dx;
+  const T inv_dx = grid_inv_dx<T>(G);
 #pragma unroll
   for (int comp = 0; comp < 3; ++comp) {
     Stencil3<T> S = make_stencil<T>(G, m, t, comp);

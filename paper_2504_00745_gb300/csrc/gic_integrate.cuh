@@ -26,7 +26,9 @@ __device__ __forceinline__ void advance_axis(const DGrid& G, float dt, float v, 
   float inc_f = dt * v * G.inv_unit_f;
   // clamp far beyond one cell so the integer conversion is defined
   inc_f = fminf(fmaxf(inc_f, -0x1p40f), 0x1p40f);
-  long long inc = __float2ll_rn(inc_f);
+  // the same rounding either way; the 64-bit conversion runs on the FP64
+  // pipe, so it is kept for moves of a cell or more (flagged as fast)
+  long long inc = fabsf(inc_f) < 0x1p30f ? (long long)__float2int_rn(inc_f) : __float2ll_rn(inc_f);
   long long s = (long long)q + inc;
   long long shift = s >> kFracBits;  // floor division by 2^30
   q_out = (uint32_t)(s & (long long)kFracMask);

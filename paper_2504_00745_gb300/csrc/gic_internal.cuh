@@ -71,6 +71,20 @@ struct DGrid {
   uint32_t* dbg;               // debug builds: the status word the index checks flag (null otherwise)
 };
 
+// The grid's h_c and 1 / dx in each precision: the FP32 path reads the float
+// copies (a double-to-float conversion runs on the FP64 pipe, a small
+// fraction of the FP32 rate on this GPU).
+template <typename T>
+__device__ __forceinline__ T grid_inv_dx(const DGrid& G) {
+  if constexpr (sizeof(T) == 4) return G.inv_dx_f;
+  else return G.inv_dx;
+}
+template <typename T>
+__device__ __forceinline__ T grid_hc(const DGrid& G) {
+  if constexpr (sizeof(T) == 4) return G.hc_f;
+  else return G.hc;
+}
+
 // Debug builds (compiled with GIC_DEBUG): device-side checks that an index
 // lies inside its array.  A failed check sets GIC_STATUS_DEBUG_INDEX in the
 // status word and the caller skips the access -- no trap, no assert.

@@ -45,8 +45,7 @@ __global__ void __launch_bounds__(kSubstepThreads, sizeof(T) == 4 ? 4 : 2) k_sub
     if (posf) prefetch_l2(&posf[i]);
     if (!rebuild) {
       const int32_t sl = nb.ident ? (int32_t)i : nb.at[i];
-      prefetch_l2(&nb.count[sl]);
-      prefetch_l2(nb.list + (int64_t)sl * nb.cap);
+      prefetch_l2(&nb.count[sl]);  // (not the row: a whole line for a few entries)
       prefetch_l2(&nb.ref_cell[sl]);
       prefetch_l2(reinterpret_cast<const pos_t<T>*>(nb.ref_pos) + sl);
     }
@@ -65,7 +64,7 @@ __global__ void __launch_bounds__(kSubstepThreads, sizeof(T) == 4 ? 4 : 2) k_sub
     const T ri = radius_of(pi);
     const T mi = granule_mass(P, ri);
     uint32_t flags = 0;
-    if (T(2) * ri > (T)G.hc) flags |= GIC_STATUS_RADIUS;
+    if (T(2) * ri > grid_hc<T>(G)) flags |= GIC_STATUS_RADIUS;
     // a2: contact
     T F0 = 0, F1 = 0, F2 = 0;
     bool coincident = false;
