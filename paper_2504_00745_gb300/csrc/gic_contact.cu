@@ -107,7 +107,8 @@ struct TileShared {
   uint32_t off[kTileMaxCells + 1];
   float4 pf[kTileMaxGranules];
   uint32_t wsum[kTileThreads / 32];
-  int mode;  // 0: staged, 1: global fallback
+  int mode;             // 0: staged, 1: global fallback
+  unsigned rmax_bits;   // the largest staged radius (float bits)
 };
 
 struct TileBox {
@@ -126,6 +127,7 @@ __device__ __forceinline__ TileBox tile_stage(TileShared& sh, const DGrid& G, co
     sh.lo[threadIdx.x] = 1 << 30;
     sh.hi[threadIdx.x] = -1;
   }
+  if (threadIdx.x == 0) sh.rmax_bits = 0u;
   __syncthreads();
   if (valid) {
     atomicMin(&sh.lo[0], cell_x(ci));
@@ -198,6 +200,7 @@ __device__ __forceinline__ TileBox tile_stage(TileShared& sh, const DGrid& G, co
       if (threadIdx.x == 0) sh.mode = 1;
     } else {
       // stage the float positions: slot t belongs to cell b with off[b] <= t < off[b + 1]
+      float rmax = 0.f;
       for (uint32_t t = threadIdx.x; t < total; t += kTileThreads) {
         int lo = 0, hi = ncell - 1;  // last b with off[b] <= t
         while (lo < hi) {
@@ -210,7 +213,10 @@ __device__ __forceinline__ TileBox tile_stage(TileShared& sh, const DGrid& G, co
         // consecutive slots, and no cell offset is needed
         float4 p = __ldg(&posf[sh.start[lo] + (t - sh.off[lo])]);
         sh.pf[t] = make_float4(p.x - (float)T.bx0, p.y - (float)T.by0, p.z - (float)T.bz0, p.w);
+        rmax = fmaxf(rmax, p.w);
       }
+      const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(rmax));  // radii >= 0
+      if (lane_id() == 0) atomicMax(&sh.rmax_bits, m);
     }
     __syncthreads();
   }
@@ -349,26 +355,40 @@ __global__ void __launch_bounds__(kTileThreads) k_verlet_build_tile(DGrid G, int
     if (sh.mode == 0) {
       const int lx = cx - T.bx0, ly = cy - T.by0, lz = cz - T.bz0;
       const float xi = fi.x - (float)T.bx0, yi = fi.y - (float)T.by0, zi = fi.z - (float)T.bz0;
-      const int xa = max(lx - 1, 0), xb = min(lx + 1, T.bx - 1);
       const int bown = lx + T.bx * (ly + T.by * lz);
       const uint32_t tself = sh.off[bown] + (uint32_t)(i - (int64_t)sh.start[bown]);
+      // Cells farther than the largest pre-test radius of any staged partner
+      // (plus a margin past the float rounding of d2) hold no partner: whole
+      // rows (oy, oz) and the end cells of a row are skipped.  A staged copy
+      // lies in its closed cell, so its distance is at least the cell's.
+      const float Rmax = fmaf(ri + __uint_as_float(sh.rmax_bits) + skin, G.inv_hc_f, kPosfTol) + 1e-3f;
+      const float R2 = Rmax * Rmax;
+      const float dxl = xi - (float)lx, dxh = (float)(lx + 1) - xi;  // to the own cell's x faces
       for (int oz = -1; oz <= 1; ++oz) {
         const int z = lz + oz;
         if (z < 0 || z >= T.bz) continue;
+        const float dz = oz < 0 ? zi - (float)lz : (oz > 0 ? (float)(lz + 1) - zi : 0.f);
         for (int oy = -1; oy <= 1; ++oy) {
           const int y = ly + oy;
           if (y < 0 || y >= T.by) continue;
+          const float dy = oy < 0 ? yi - (float)ly : (oy > 0 ? (float)(ly + 1) - yi : 0.f);
+          const float dyz = fmaf(dy, dy, dz * dz);
+          if (dyz >= R2) continue;
+          const int xa = (lx > 0 && fmaf(dxl, dxl, dyz) < R2) ? lx - 1 : lx;
+          const int xb = (lx + 1 < T.bx && fmaf(dxh, dxh, dyz) < R2) ? lx + 1 : lx;
           const int rb = T.bx * (y + T.by * z);
           const uint32_t t0 = sh.off[rb + xa], t1 = sh.off[rb + xb + 1];
-          int bj = rb + xa;
           for (uint32_t t = t0; t < t1; ++t) {
-            while (sh.off[bj + 1] <= t) ++bj;  // the cell of slot t (cells of the row in x order)
             if (t == tself) continue;
             const float4 fj = sh.pf[t];
             const float rx = fj.x - xi, ry = fj.y - yi, rz = fj.z - zi;
             const float d2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
             const float Rs = fmaf(ri + fj.w + skin, G.inv_hc_f, kPosfTol);
-            if (d2 < Rs * Rs) keep((int64_t)sh.start[bj] + (t - sh.off[bj]));
+            if (d2 < Rs * Rs) {
+              int bj = rb + xa;
+              while (sh.off[bj + 1] <= t) ++bj;  // the cell of slot t (cells of the row in x order)
+              keep((int64_t)sh.start[bj] + (t - sh.off[bj]));
+            }
           }
         }
       }
