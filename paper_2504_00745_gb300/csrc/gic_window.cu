@@ -4,6 +4,7 @@
 // (gic_window_forward_host).  All scratch comes from the caller's workspace.
 #include <string.h>
 
+#include "gic_contact.cuh"
 #include "gic_internal.cuh"
 
 namespace gic {
@@ -85,6 +86,34 @@ static int window_layout(const GicGrid* grid, int64_t n, int32_t precision, Wind
   return GIC_OK;
 }
 
+// The window's Verlet lists in the workspace.
+static GicNeighbors window_lists(const GicGrid* grid, char* base, const WindowLayout& L, int64_t n,
+                                 int32_t precision) {
+  GicNeighbors nb;
+  size_t nn = (size_t)n;
+  size_t real = precision == GIC_FP32 ? 4 : 8;
+  char* q = base + L.off_nb;
+  nb.n = n;
+  nb.cap = kWindowNbCap;
+  nb.skin = 0.025 * grid->dx / grid->k_contact;
+  nb.list = (int32_t*)q;
+  q += al(4 * nn * kWindowNbCap);
+  nb.count = (int32_t*)q;
+  q += al(4 * nn);
+  nb.ref_cell = (int32_t*)q;
+  q += al(4 * nn);
+  nb.ref_pos = q;
+  q += al(4 * real * nn);
+  nb.slot = (int32_t*)q;
+  q += al(4 * nn);
+  nb.cur = (int32_t*)q;
+  q += al(4 * nn);
+  nb.at = (int32_t*)q;
+  q += al(4 * nn);
+  nb.flags = (uint32_t*)q;
+  return nb;
+}
+
 static GicGranules state_at(char* base, int64_t n, int32_t precision) {
   size_t real = precision == GIC_FP32 ? 4 : 8;
   size_t nn = (size_t)(n > 0 ? n : 1);
@@ -98,6 +127,80 @@ static GicGranules state_at(char* base, int64_t n, int32_t precision) {
   s.precision = precision;
   s.posf = nullptr;
   return s;
+}
+
+// The window's three states in the workspace: S[0] sorted, S[1] and S[2]
+// the states gic_step alternates between.
+static void window_states(char* base, const WindowLayout& L, int64_t n, int32_t precision, bool with_id,
+                          GicGranules S[3]) {
+  for (int k = 0; k < 3; ++k) {
+    S[k] = state_at(base + L.off_state_b + k * L.state_bytes, n, precision);
+    if (!with_id) S[k].id = nullptr;
+    if (precision == GIC_FP32) {
+      size_t nn = (size_t)(n > 0 ? n : 1);
+      S[k].posf = (float*)(base + L.off_state_b + k * L.state_bytes + al(4 * nn) + 2 * al(16 * nn) + al(4 * nn));
+    }
+  }
+}
+
+// A second stream and the two events that fork it from and join it to the
+// caller's stream, released on every return.
+struct SideStream {
+  cudaStream_t s = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+  int open(const char* what) {
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      return set_error(GIC_ERR_CUDA, "%s: side stream set-up failed", what);
+    }
+    return GIC_OK;
+  }
+  ~SideStream() {
+    if (join) cudaEventDestroy(join);
+    if (fork) cudaEventDestroy(fork);
+    if (s) cudaStreamDestroy(s);  // returns at once; the stream's work still completes
+  }
+};
+
+// The window of gic_window_forward_host with the first substep's sort and
+// list build done before the fluid fields are needed: A is sorted into S[0],
+// the rows of S[0] are built on the staged neighbourhood (FP32, contact law
+// alone), the stream waits for `fields`, and the K gic_step calls start from
+// S[0] with the lists already current (a build that overflows leaves the
+// rebuild flag set, and the first call rebuilds as usual).  The same kernels
+// in the same order as gic_window_forward: the same results.
+static int window_prebuilt(const GicGrid* grid, const GicParams* params, const WindowLayout& L, char* base,
+                           const GicGranules* A, int32_t K, cudaEvent_t fields, const void* u, const void* v,
+                           const void* w, const void* p, const void* alpha_f, double* alpha_s, void* Fs_u,
+                           void* Fs_v, void* Fs_w, double* sums2, void* table, cudaStream_t st,
+                           const GicGranules** result) {
+  int rc;
+  GicGranules S[3];
+  window_states(base, L, A->n, A->precision, true, S);
+  int32_t* perm = (int32_t*)(base + L.off_perm);
+  GicNeighbors nb = window_lists(grid, base, L, A->n, A->precision);
+  const gic_stream_t stream = (gic_stream_t)st;
+  if ((rc = gic_neighbors_reset(&nb, stream))) return rc;
+  if ((rc = gic_sort(grid, A, &S[0], perm, table, base + L.off_sort, L.sort_ws, stream))) return rc;
+  DGrid G;
+  if ((rc = make_grid(grid, &G))) return rc;
+  if ((rc = launch_build_tile(G, &S[0], table, nb_dev(G, &nb, true), nb.skin, st))) return rc;
+  if (cudaStreamWaitEvent(st, fields, 0) != cudaSuccess)
+    return set_error(GIC_ERR_CUDA, "gic_window_forward_host: stream wait failed");
+  const GicGranules* cur = &S[0];
+  for (int s = 0; s < K; ++s) {
+    const bool last = s == K - 1;
+    GicGranules* nxt = cur == &S[1] ? &S[2] : &S[1];
+    GicGranules* srt = cur == &S[0] ? &S[2] : &S[0];  // shares no array with cur or nxt
+    if ((rc = gic_step(grid, params, cur, nxt, srt, perm, table, base + L.off_sort, L.sort_ws, &nb, u, v, w, p,
+                       alpha_f, last ? alpha_s : nullptr, Fs_u, Fs_v, Fs_w, last ? sums2 : nullptr, stream)))
+      return rc;
+    cur = nxt;
+  }
+  *result = cur;
+  return GIC_OK;
 }
 
 }  // namespace gic
@@ -140,14 +243,7 @@ extern "C" int gic_window_forward(const GicGrid* grid, const GicParams* params, 
   if ((uintptr_t)ws % 256) return set_error(GIC_ERR_ALIGN, "gic_window_forward: workspace must be 256-byte aligned");
   char* base = (char*)ws;
   GicGranules S[3];  // S[0] sorted, S[1] and S[2] the states gic_step alternates between
-  for (int k = 0; k < 3; ++k) {
-    S[k] = state_at(base + L.off_state_b + k * L.state_bytes, state->n, state->precision);
-    if (!state->id) S[k].id = nullptr;
-    if (state->precision == GIC_FP32) {
-      size_t nn = (size_t)(state->n > 0 ? state->n : 1);
-      S[k].posf = (float*)(base + L.off_state_b + k * L.state_bytes + al(4 * nn) + 2 * al(16 * nn) + al(4 * nn));
-    }
-  }
+  window_states(base, L, state->n, state->precision, state->id != nullptr, S);
   GicGranules& B = S[0];
   int32_t* perm = (int32_t*)(base + L.off_perm);
   void* Fc = base + L.off_fc;
@@ -158,27 +254,7 @@ extern "C" int gic_window_forward(const GicGrid* grid, const GicParams* params, 
   GicNeighbors nb;
   const bool verlet = state->id != nullptr && state->n > 0;
   if (verlet) {
-    size_t nn = (size_t)state->n;
-    size_t real = state->precision == GIC_FP32 ? 4 : 8;
-    char* q = base + L.off_nb;
-    nb.n = state->n;
-    nb.cap = kWindowNbCap;
-    nb.skin = 0.025 * grid->dx / grid->k_contact;
-    nb.list = (int32_t*)q;
-    q += al(4 * nn * kWindowNbCap);
-    nb.count = (int32_t*)q;
-    q += al(4 * nn);
-    nb.ref_cell = (int32_t*)q;
-    q += al(4 * nn);
-    nb.ref_pos = q;
-    q += al(4 * real * nn);
-    nb.slot = (int32_t*)q;
-    q += al(4 * nn);
-    nb.cur = (int32_t*)q;
-    q += al(4 * nn);
-    nb.at = (int32_t*)q;
-    q += al(4 * nn);
-    nb.flags = (uint32_t*)q;
+    nb = window_lists(grid, base, L, state->n, state->precision);
     if ((rc = gic_neighbors_reset(&nb, stream))) return rc;
   }
   // alpha_s once, at the final positions (Alg. 1 CalTargetFraction); F_s every substep (Alg. 2)
@@ -258,6 +334,13 @@ extern "C" int gic_window_forward_host(const GicGrid* grid, const GicParams* par
     cudaError_t e_ = (call);                                                                       \
     if (e_ != cudaSuccess) return set_error(GIC_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
   } while (0)
+  // FP32 with the contact law alone: the granules go first, and their sort and
+  // list build run while the fluid fields are copied on a second stream (the
+  // first substep waits for them); otherwise everything in stream order
+  const bool overlap = precision == GIC_FP32 && n > 0 && K > 0 && params && params->sigma == 0.0;
+  SideStream side;
+  if (overlap && (rc = side.open("gic_window_forward_host"))) return rc;
+  cudaStream_t sf = overlap ? side.s : st;  // the fields' stream
   // inputs: host -> device (one copy per array)
   if (n > 0) {
     GIC_CU(cudaMemcpyAsync(base + L.off_cxyz, cell_xyz, 12 * (size_t)n, cudaMemcpyHostToDevice, st));
@@ -265,22 +348,33 @@ extern "C" int gic_window_forward_host(const GicGrid* grid, const GicParams* par
     GIC_CU(cudaMemcpyAsync(base + L.off_r, r, 4 * (size_t)n, cudaMemcpyHostToDevice, st));
     GIC_CU(cudaMemcpyAsync(base + L.off_v, v, 12 * (size_t)n, cudaMemcpyHostToDevice, st));
   }
-  GIC_CU(cudaMemcpyAsync(fu, u_f, real * L.n_fields_u, cudaMemcpyHostToDevice, st));
-  GIC_CU(cudaMemcpyAsync(fv, v_f, real * L.n_fields_v, cudaMemcpyHostToDevice, st));
-  GIC_CU(cudaMemcpyAsync(fw, w_f, real * L.n_fields_w, cudaMemcpyHostToDevice, st));
-  GIC_CU(cudaMemcpyAsync(fp, p_f, real * L.n_cells, cudaMemcpyHostToDevice, st));
-  GIC_CU(cudaMemcpyAsync(fa, alpha_f, real * L.n_cells, cudaMemcpyHostToDevice, st));
+  if (overlap) {  // the fields' stream starts after everything on st so far (earlier calls included)
+    GIC_CU(cudaEventRecord(side.fork, st));
+    GIC_CU(cudaStreamWaitEvent(sf, side.fork, 0));
+  }
+  GIC_CU(cudaMemcpyAsync(fu, u_f, real * L.n_fields_u, cudaMemcpyHostToDevice, sf));
+  GIC_CU(cudaMemcpyAsync(fv, v_f, real * L.n_fields_v, cudaMemcpyHostToDevice, sf));
+  GIC_CU(cudaMemcpyAsync(fw, w_f, real * L.n_fields_w, cudaMemcpyHostToDevice, sf));
+  GIC_CU(cudaMemcpyAsync(fp, p_f, real * L.n_cells, cudaMemcpyHostToDevice, sf));
+  GIC_CU(cudaMemcpyAsync(fa, alpha_f, real * L.n_cells, cudaMemcpyHostToDevice, sf));
+  GIC_CU(cudaMemsetAsync(su, 0, real * L.n_fields_u, sf));
+  GIC_CU(cudaMemsetAsync(sv, 0, real * L.n_fields_v, sf));
+  GIC_CU(cudaMemsetAsync(sw, 0, real * L.n_fields_w, sf));
+  if (overlap) GIC_CU(cudaEventRecord(side.join, sf));
   GIC_CU(cudaMemsetAsync(table, 0, table_bytes, st));
-  GIC_CU(cudaMemsetAsync(su, 0, real * L.n_fields_u, st));
-  GIC_CU(cudaMemsetAsync(sv, 0, real * L.n_fields_v, st));
-  GIC_CU(cudaMemsetAsync(sw, 0, real * L.n_fields_w, st));
   if ((rc = gic_pack(grid, n, (const int32_t*)(base + L.off_cxyz), (const uint32_t*)(base + L.off_q),
                      (const float*)(base + L.off_r), (const float*)(base + L.off_v), &A, stream)))
     return rc;
-  if ((rc = gic_window_forward(grid, params, &A, K, fu, fv, fw, fp, fa, d_alpha, su, sv, sw, d_sums, table,
-                               base + L.off_sort, L.total, stream)))
+  const GicGranules* result = &A;
+  if (overlap) {
+    if ((rc = window_prebuilt(grid, params, L, base, &A, K, side.join, fu, fv, fw, fp, fa, d_alpha, su, sv, sw,
+                              d_sums, table, st, &result)))
+      return rc;
+  } else if ((rc = gic_window_forward(grid, params, &A, K, fu, fv, fw, fp, fa, d_alpha, su, sv, sw, d_sums, table,
+                                      base + L.off_sort, L.total, stream))) {
     return rc;
-  if ((rc = gic_unpack(grid, &A, d_x, d_v, stream))) return rc;
+  }
+  if ((rc = gic_unpack(grid, result, d_x, d_v, stream))) return rc;
   // outputs: device -> host
   if (n > 0) {
     if (x_out) GIC_CU(cudaMemcpyAsync(x_out, d_x, 24 * (size_t)n, cudaMemcpyDeviceToHost, st));
