@@ -35,8 +35,8 @@ UNIT = "granule-substeps/s"
 # F_s from the old positions every substep (cell + pos 20 B, f_ex 12 B) and
 # alpha_s from the new ones once per fluid step (20 B more on the last
 # substep).  The fused substep (contact, G2P, integrate, P2G after the sort)
-# is charged the per-unit figure of the hot-path survey for a fused
-# single-pass substep, 90 B: the sorted state in and the next state out
+# is charged 90 B, the per-unit figure for a fused single-pass substep:
+# the sorted state in and the next state out
 # (72 B) plus the granule's share of the fluid samples and F_s deposits it
 # touches.  The FP64 path moves twice the floats of every record (2x); the
 # adjoint of the fused substep reads the state and the upstream position and
