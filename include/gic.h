@@ -441,6 +441,9 @@ int gic_window_host_workspace_size(const GicGrid* grid, int64_t n, int32_t preci
  * the final positions / velocities (double[3n] each, original order),
  * alpha_s (double), F_s (real, accumulated from zero) and sums2 (any output
  * may be NULL).  Host buffers should be pinned for asynchronous copies.
+ * FP32 with sigma = 0: the fluid fields are copied on a second stream of the
+ * library's own (created and released by the call, joined to `stream` with
+ * events) while the granules are sorted and the first substep's lists built.
  * Blocks until the results are on the host (deadline 10 minutes, then
  * GIC_ERR_TIMEOUT). */
 int gic_window_forward_host(const GicGrid* grid, const GicParams* params, int64_t n, int32_t precision,
