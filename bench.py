@@ -81,6 +81,9 @@ def parse():
     ap.add_argument("--profile-granules", type=int, default=0,
                     help="with --profile-substeps: the workload's generator at this many granules (the same lattice "
                          "and grid, a thinner bed), for captures that must stay small")
+    ap.add_argument("--profile-build", action="store_true",
+                    help="with --profile-substeps: instead of substeps, that many list builds of the sorted state "
+                         "(gic_sort + gic_neighbors_build), for a capture of the staged build")
     ap.add_argument("--profile-direct", action="store_true",
                     help="with --profile-substeps: gic_sort + gic_substep every substep (no CUDA graph), so that "
                          "a profiler sees each kernel")
@@ -763,6 +766,11 @@ def run_profile(args):
         mu = torch.tensor(float(prob.params.mu_fric), dtype=torch.float64, device=sim.device, requires_grad=True)
         x = GicWindow.apply(v0, c, mu, sim, sim.A.clone(), args.profile_substeps, 10)
         ((x - target) ** 2).sum(dim=1).mean().backward()
+    elif args.profile_build:
+        for _ in range(args.profile_substeps):
+            gic.gic_sort(sim.grid, sim.A, sim.B, sim.perm, sim.table, sim.ws)
+            gic.gic_neighbors_reset(sim.nb)
+            gic.gic_neighbors_build(sim.grid, sim.B, sim.table, sim.nb)
     else:
         sim.run(args.profile_substeps, sort_every=args.profile_direct)
     extra = {}

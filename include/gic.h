@@ -312,6 +312,21 @@ int gic_step(const GicGrid* grid, const GicParams* params, const GicGranules* st
  * (flags = {0, 1, 0, 0, 0, ...}). */
 int gic_neighbors_reset(const GicNeighbors* nb, gic_stream_t stream);
 
+/* Build the Verlet lists of a sorted state without computing forces (the
+ * neighbour search of Sec. 3.1, stored as the lists above): every slot gets
+ * the partners within r_i + r_j + skin, in the order a rebuilding
+ * gic_contact_verlet / gic_substep / gic_step would store them, from a
+ * per-CTA staged neighbourhood (the cell-table box and the float positions of
+ * every granule in it, in shared memory).  `sorted` and `cell_table` are the
+ * output of gic_sort (FP32 with posf and ids); slots are its sorted indices,
+ * so gic_step may start from `sorted` with these lists.  The build is recorded
+ * (flags[4] += 1, rebuild request cleared) unless a row would exceed cap, in
+ * which case the request stays set and the next call rebuilds.  One or two
+ * launches, no host sync.  Errors: GIC_ERR_INVALID for FP64, a missing posf
+ * or id array, or sizes that differ. */
+int gic_neighbors_build(const GicGrid* grid, const GicGranules* sorted, const void* cell_table,
+                        const GicNeighbors* nb, gic_stream_t stream);
+
 /* a3: trilinear G2P of u, v, w, grad p (face differences of p) and alpha_f:
  *   F_fl = c_drag pi r^2 rho_f |u_f - v| (u_f - v) - (4/3) pi r^3 grad p
  *   a_f  = g - grad p / rho_f   (dv_f/dt of Sec. 5.2 Eq. momentum4 without the

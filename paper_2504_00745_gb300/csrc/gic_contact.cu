@@ -862,6 +862,32 @@ extern "C" int gic_neighbors_reset(const GicNeighbors* nb, gic_stream_t stream) 
   return GIC_OK;
 }
 
+namespace gic {
+// A rebuild request (the sticky word's bit 0): the build kernel reads it and
+// clears it after a complete build; after an overflow it stays, and the next
+// call on these lists rebuilds.
+__global__ void k_request_build(uint32_t* flags) { flags[kNbSticky] |= 1u; }
+}  // namespace gic
+
+extern "C" int gic_neighbors_build(const GicGrid* grid, const GicGranules* sorted, const void* cell_table,
+                                   const GicNeighbors* nb, gic_stream_t stream) {
+  GIC_RANGE("gic_neighbors_build");
+  DGrid G;
+  int rc = make_grid(grid, &G);
+  if (rc) return rc;
+  if ((rc = check_granules(sorted, "gic_neighbors_build", true))) return rc;
+  if (sorted->precision != GIC_FP32 || !sorted->posf)
+    return set_error(GIC_ERR_INVALID, "gic_neighbors_build: the staged build needs an FP32 state with posf");
+  NbDev d;
+  if ((rc = verlet_view(G, sorted, cell_table, nb, "gic_neighbors_build", true, &d))) return rc;
+  if (sorted->n == 0) return GIC_OK;
+  k_request_build<<<1, 1, 0, (cudaStream_t)stream>>>(nb->flags);
+  if ((rc = launch_build_tile(G, sorted, cell_table, d, nb->skin, (cudaStream_t)stream))) return rc;
+  count_launches(2);
+  GIC_CHECK_LAUNCH("gic_neighbors_build");
+  return GIC_OK;
+}
+
 extern "C" int gic_contact_verlet_adj(const GicGrid* grid, const GicParams* params, const GicGranules* s,
                                       const void* table, const GicNeighbors* nb, void* F_c, const void* gF_c,
                                       void* g_pos, void* g_vel, double* g_mu, gic_stream_t stream) {

@@ -4,7 +4,6 @@
 // (gic_window_forward_host).  All scratch comes from the caller's workspace.
 #include <string.h>
 
-#include "gic_contact.cuh"
 #include "gic_internal.cuh"
 
 namespace gic {
@@ -184,9 +183,7 @@ static int window_prebuilt(const GicGrid* grid, const GicParams* params, const W
   const gic_stream_t stream = (gic_stream_t)st;
   if ((rc = gic_neighbors_reset(&nb, stream))) return rc;
   if ((rc = gic_sort(grid, A, &S[0], perm, table, base + L.off_sort, L.sort_ws, stream))) return rc;
-  DGrid G;
-  if ((rc = make_grid(grid, &G))) return rc;
-  if ((rc = launch_build_tile(G, &S[0], table, nb_dev(G, &nb, true), nb.skin, st))) return rc;
+  if ((rc = gic_neighbors_build(grid, &S[0], table, &nb, stream))) return rc;
   if (cudaStreamWaitEvent(st, fields, 0) != cudaSuccess)
     return set_error(GIC_ERR_CUDA, "gic_window_forward_host: stream wait failed");
   const GicGranules* cur = &S[0];

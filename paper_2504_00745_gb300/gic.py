@@ -356,6 +356,13 @@ def gic_neighbors_reset(nb: Neighbors, stream=None):
     _check(lib().gic_neighbors_reset(C.byref(b), _stream(stream)), "gic_neighbors_reset")
 
 
+def gic_neighbors_build(grid: GicGrid, sorted_: State, cell_table, nb: Neighbors, stream=None):
+    b = nb.struct()
+    s = sorted_.struct()
+    _check(lib().gic_neighbors_build(C.byref(grid), C.byref(s), _ptr(cell_table), C.byref(b), _stream(stream)),
+           "gic_neighbors_build")
+
+
 def gic_g2p_couple(grid: GicGrid, params: GicParams, st: State, u, v, w, p, alpha_f, F_fl, a_f, alpha_f_p=None,
                    stream=None):
     s = st.struct()

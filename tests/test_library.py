@@ -83,6 +83,14 @@ def test_null_arguments_are_rejected_on_the_host():
     assert L.gic_contact(C.byref(g), C.byref(bad_p), C.byref(empty), C.c_void_p(16), None, None) == 0
     assert L.gic_sort_adj(0, 0, None, None, None, None, None, None) == 0
     assert L.gic_sort_adj(5, 0, None, None, None, None, None, None) == -1
+    # the staged list build wants an FP32 sorted state with ids and float copies
+    fake = C.c_void_p(256)  # never dereferenced: the checks come first
+    s64 = gic.GicGranules(10, fake, fake, fake, fake, 1, None)
+    assert L.gic_neighbors_build(C.byref(g), C.byref(s64), fake, None, None) == -1
+    assert "FP32" in gic.last_error()
+    s32 = gic.GicGranules(10, fake, fake, fake, fake, 0, None)
+    assert L.gic_neighbors_build(C.byref(g), C.byref(s32), fake, None, None) == -1
+    assert L.gic_neighbors_build(C.byref(g), C.byref(s), fake, None, None) == -1  # no arrays
 
 
 def test_projection_validation_on_the_host():

@@ -257,3 +257,33 @@ def test_staged_build_gives_the_substeps_own_rows(name):
     xa, va = a.positions()
     xb, vb = b.positions()
     assert np.array_equal(xa.cpu().numpy(), xb.cpu().numpy()) and np.array_equal(va.cpu().numpy(), vb.cpu().numpy())
+
+
+@pytest.mark.parametrize("name", ["dense_block", "random_cloud"])
+def test_neighbors_build_gives_the_rebuilding_substeps_rows(name):
+    """gic_neighbors_build on a sorted state writes the rows, counts and
+    reference entries that the build inside the fused substep writes for the
+    same sorted state (gic_substep after gic_sort), bit for bit, and records
+    one build; an FP64 state is refused."""
+    prob = shuffled(gi.make(name))
+    a = Simulator.from_problem(prob, FP32)
+    gic.gic_sort(a.grid, a.A, a.B, a.perm, a.table, a.ws)
+    gic.gic_neighbors_reset(a.nb)
+    gic.gic_neighbors_build(a.grid, a.B, a.table, a.nb)
+    b = Simulator.from_problem(prob, FP32)
+    gic.gic_sort(b.grid, b.A, b.B, b.perm, b.table, b.ws)
+    b.fused_rest(alpha=False, transfer=False, sums=False)  # gic_substep: the build inside the substep
+    torch.cuda.synchronize()
+    assert gic.gic_check_status() == 0
+    assert a.nb.builds() == 1 and b.nb.builds() == 1
+    cnt = a.nb.count.cpu().numpy()
+    assert np.array_equal(cnt, b.nb.count.cpu().numpy())
+    la, lb = a.nb.list.view(prob.n, -1).cpu().numpy(), b.nb.list.view(prob.n, -1).cpu().numpy()
+    for k in range(prob.n):
+        assert np.array_equal(la[k, :cnt[k]], lb[k, :cnt[k]])
+    assert np.array_equal(a.nb.ref_cell.cpu().numpy(), b.nb.ref_cell.cpu().numpy())
+    assert np.array_equal(a.nb.ref_pos.cpu().numpy(), b.nb.ref_pos.cpu().numpy())
+    c = Simulator.from_problem(prob, FP64)
+    gic.gic_sort(c.grid, c.A, c.B, c.perm, c.table, c.ws)
+    with pytest.raises(gic.GicError, match="FP32"):
+        gic.gic_neighbors_build(c.grid, c.B, c.table, c.nb)
