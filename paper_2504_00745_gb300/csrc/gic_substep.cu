@@ -18,6 +18,8 @@
 namespace gic {
 
 constexpr int kSubstepThreads = 256;
+static_assert(kSubstepThreads == 32 * kSubWarps && kSubstepThreads + kSubstepThreads / 32 <= kSpreadStride,
+              "the shared tile's warp arrays and the spread deposits are sized for CTAs of 256 threads");
 
 // kKeep: the kernel of gic_step's list-keeping branch without the capillary
 // force (its lists are valid by the branch's condition, so it carries neither

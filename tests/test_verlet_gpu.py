@@ -287,3 +287,32 @@ def test_neighbors_build_gives_the_rebuilding_substeps_rows(name):
     gic.gic_sort(c.grid, c.A, c.B, c.perm, c.table, c.ws)
     with pytest.raises(gic.GicError, match="FP32"):
         gic.gic_neighbors_build(c.grid, c.B, c.table, c.nb)
+
+
+def test_neighbors_build_overflow_leaves_the_rebuild_to_the_next_call():
+    """A list build whose rows would exceed cap records no build and keeps
+    the rebuild request: a gic_step that then starts from the sorted state
+    rebuilds (in its own 27-cell walk) and gives the same state as a
+    simulator whose first gic_step built the lists itself."""
+    prob = shuffled(gi.make("dense_block"))
+    K = 5
+    sims = []
+    for prebuilt in (True, False):
+        sim = Simulator(prob.grid, prob.params, prob.n, FP32, verlet_skin=0.15 * float(prob.r.max()), verlet_cap=2)
+        sim.set_fluid(prob.u, prob.vf, prob.wf, prob.p, prob.alpha_f)
+        sim.set_state(prob.cell, prob.q, prob.r, prob.v)
+        if prebuilt:
+            gic.gic_sort(sim.grid, sim.A, sim.B, sim.perm, sim.table, sim.ws)
+            gic.gic_neighbors_reset(sim.nb)
+            gic.gic_neighbors_build(sim.grid, sim.B, sim.table, sim.nb)
+            torch.cuda.synchronize()
+            assert sim.nb.builds() == 0 and (int(sim.nb.flags[1].item()) & 1)  # overflowed: still requested
+            sim.A, sim.B = sim.B, sim.A  # start from the sorted state with these lists
+            sim.lists_current = True
+        sim.run(K)
+        torch.cuda.synchronize()
+        assert gic.gic_check_status() == 0
+        sims.append(sim)
+    xa, va = sims[0].positions()
+    xb, vb = sims[1].positions()
+    assert np.array_equal(xa.cpu().numpy(), xb.cpu().numpy()) and np.array_equal(va.cpu().numpy(), vb.cpu().numpy())
