@@ -152,17 +152,29 @@ __device__ __forceinline__ TileBox tile_stage(TileShared& sh, const DGrid& G, co
     // stage the table entries of the box
     // box index -> coordinates with float reciprocals (exact for these small integers)
     const float ibx = 1.0f / (float)T.bx, ibxy = 1.0f / (float)(T.bx * T.by);
-    for (int b = threadIdx.x; b < ncell; b += kTileThreads) {
-      int z = (int)(((float)b + 0.5f) * ibxy);
-      int rem = b - z * T.bx * T.by;
-      int y = (int)(((float)rem + 0.5f) * ibx);
-      int x = T.bx0 + rem - y * T.bx;
-      y += T.by0;
-      z += T.bz0;
-      uint4 e = __ldg(&table[table_index(G, x, y, z)]);
-      bool ok = e.z == epoch;
-      sh.start[b] = ok ? e.x : 0u;
-      sh.cnt[b] = ok ? e.y : 0u;
+    constexpr int kU = 4;  // loads in flight per thread
+    for (int b0 = threadIdx.x; b0 < ncell; b0 += kU * kTileThreads) {
+      uint4 e[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int b = b0 + u * kTileThreads;
+        if (b >= ncell) break;
+        int z = (int)(((float)b + 0.5f) * ibxy);
+        int rem = b - z * T.bx * T.by;
+        int y = (int)(((float)rem + 0.5f) * ibx);
+        int x = T.bx0 + rem - y * T.bx;
+        y += T.by0;
+        z += T.bz0;
+        e[u] = __ldg(&table[table_index(G, x, y, z)]);
+      }
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int b = b0 + u * kTileThreads;
+        if (b >= ncell) break;
+        const bool ok = e[u].z == epoch;
+        sh.start[b] = ok ? e[u].x : 0u;
+        sh.cnt[b] = ok ? e[u].y : 0u;
+      }
     }
     __syncthreads();
     // exclusive scan of the counts (ncell <= 512: 4 per thread)
@@ -201,19 +213,31 @@ __device__ __forceinline__ TileBox tile_stage(TileShared& sh, const DGrid& G, co
     } else {
       // stage the float positions: slot t belongs to cell b with off[b] <= t < off[b + 1]
       float rmax = 0.f;
-      for (uint32_t t = threadIdx.x; t < total; t += kTileThreads) {
-        int lo = 0, hi = ncell - 1;  // last b with off[b] <= t
-        while (lo < hi) {
-          int mid = (lo + hi + 1) >> 1;
-          if (sh.off[mid] <= t) lo = mid;
-          else hi = mid - 1;
+      for (uint32_t t0 = threadIdx.x; t0 < total; t0 += kU * kTileThreads) {
+        float4 pv[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+          const uint32_t t = t0 + u * kTileThreads;
+          if (t >= total) break;
+          int lo = 0, hi = ncell - 1;  // last b with off[b] <= t
+          while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (sh.off[mid] <= t) lo = mid;
+            else hi = mid - 1;
+          }
+          pv[u] = __ldg(&posf[sh.start[lo] + (t - sh.off[lo])]);
         }
-        // position in units of contact cells relative to the box corner (exact
-        // differences of the absolute copies): the three cells of an x-row are
-        // consecutive slots, and no cell offset is needed
-        float4 p = __ldg(&posf[sh.start[lo] + (t - sh.off[lo])]);
-        sh.pf[t] = make_float4(p.x - (float)T.bx0, p.y - (float)T.by0, p.z - (float)T.bz0, p.w);
-        rmax = fmaxf(rmax, p.w);
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+          const uint32_t t = t0 + u * kTileThreads;
+          if (t >= total) break;
+          // position in units of contact cells relative to the box corner (exact
+          // differences of the absolute copies): the three cells of an x-row are
+          // consecutive slots, and no cell offset is needed
+          const float4 p = pv[u];
+          sh.pf[t] = make_float4(p.x - (float)T.bx0, p.y - (float)T.by0, p.z - (float)T.bz0, p.w);
+          rmax = fmaxf(rmax, p.w);
+        }
       }
       const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(rmax));  // radii >= 0
       if (lane_id() == 0) atomicMax(&sh.rmax_bits, m);
