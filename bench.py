@@ -544,10 +544,37 @@ def run_e2e(prob, sim, gic, torch, np, dev, stream, steps):
     # the median call: the copies run over the host's memory, which other jobs on the machine share, and single
     # calls have taken 2-3x the others (every call is listed)
     sec = statistics.median(times)
+    link = host_link_rates(torch, o_a, dev, stream)
+    io_ms = 1e-6 * (h2d / link["h2d_gbs"] + d2h / link["d2h_gbs"])
+    link["io_ms_at_link_rate"] = io_ms
+    link["what"] = ("one pinned-host <-> device copy of %d MB on the call's stream, best of 3, after the timed calls; "
+                    "io_ms_at_link_rate = h2d bytes / h2d rate + d2h bytes / d2h rate" % (o_a.numel() * 8 >> 20))
     return {"value": n * K / sec, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
             "ms_per_step": 1000 * sec, "ms_per_call": [1000 * t for t in times],
             "ms_mean": 1000 * statistics.mean(times), "statistic": "median of the timed calls",
-            "api": "gic_window_forward_host (C ABI, pinned host buffers)"}
+            "api": "gic_window_forward_host (C ABI, pinned host buffers)", "host_link": link}
+
+
+def host_link_rates(torch, h, dev, stream):
+    """Copy rate of the host link in each direction (GB/s): `h` (pinned) to a
+    device buffer and back, timed with CUDA events on `stream`."""
+    d = torch.empty(h.shape, dtype=h.dtype, device=dev)
+    nbytes = h.numel() * h.element_size()
+    out = {}
+    with torch.cuda.stream(stream):
+        for name, dst, src in (("h2d_gbs", d, h), ("d2h_gbs", h, d)):
+            best = float("inf")
+            for _ in range(3):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                a.record(stream)
+                dst.copy_(src, non_blocking=True)
+                b.record(stream)
+                b.synchronize()
+                best = min(best, a.elapsed_time(b))
+            out[name] = nbytes / (best * 1e6)
+    del d
+    return out
 
 
 def run_adjoint(prob, prec, torch, dev, ckpt=10):
