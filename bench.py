@@ -51,7 +51,7 @@ P2G_ALPHA_BYTES = 20
 # GB), from a graph-level ncu capture of the current kernels (ncu flushes the
 # caches first); per workload (None where no capture of the current kernels
 # exists)
-NCU_TRAFFIC = {("scale_sweep_16m", "gic_step"): (7.08e9 + 18 * 2.40e9 + 3.76e9) / 20}
+NCU_TRAFFIC = {("scale_sweep_16m", "gic_step"): (7.077e9 + 18 * 2.403e9 + 3.760e9) / 20}
 
 
 def algo_bytes(name, K, fp64=False):

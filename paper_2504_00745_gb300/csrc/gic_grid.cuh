@@ -542,11 +542,31 @@ __device__ __forceinline__ SubBox sub_tile_begin(SubTile& sh, const DGrid& G, co
   return B;
 }
 
+// G2P of one granule from global memory, out of line: the path of a CTA whose
+// box exceeds the tile, kept out of the fused kernel's instruction stream.
+struct G2POut {
+  float F[3], a[3], sp;
+};
+static __device__ __noinline__ G2POut g2p_global_f32(const DGrid G, const DParams<float> P, const Fields<float> Fd,
+                                                     int32_t c, uint4 pi, float4 vi) {
+  G2POut o;
+  o.sp = g2p_granule<float>(G, P, Fd, c, pi, vi, o.F, o.a);
+  return o;
+}
+
 // G2P of one granule from the staged tile (B.tile) or global memory.
 __device__ __forceinline__ float sub_g2p(const SubTile& sh, const SubBox& B, const DGrid& G, const DParams<float>& P,
                                          const Fields<float>& Fd, int32_t c, const uint4& pi, const float4& vi,
                                          float F[3], float a[3]) {
-  if (!B.tile) return g2p_granule<float>(G, P, Fd, c, pi, vi, F, a);
+  if (!B.tile) {
+    const G2POut o = g2p_global_f32(G, P, Fd, c, pi, vi);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      F[d] = o.F[d];
+      a[d] = o.a[d];
+    }
+    return o.sp;
+  }
   const float* uvw[3] = {sh.u, sh.v, sh.w};
   return g2p_granule_with<float>(
       G, P, c, pi, vi, [&](int comp) { return TileLoad{uvw[comp], B, G.dbg}; },

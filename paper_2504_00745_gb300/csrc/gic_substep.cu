@@ -25,7 +25,8 @@ static_assert(kSubstepThreads == 32 * kSubWarps && kSubstepThreads + kSubstepThr
 // force (its lists are valid by the branch's condition, so it carries neither
 // the build nor the bridge code: a smaller instruction footprint); otherwise
 // the general kernel, which reads from the list flags whether it rebuilds.
-template <typename T, bool kKeep>
+// kNoAlpha: a call without alpha_s (the kernel then carries none of its code).
+template <typename T, bool kKeep, bool kNoAlpha = false>
 __global__ void __launch_bounds__(kSubstepThreads, sizeof(T) == 4 ? 4 : 2) k_substep(
     DGrid G, DParams<T> P, int64_t n, const int32_t* __restrict__ cell, const pos_t<T>* __restrict__ pos,
     const float4* __restrict__ posf, const vec_t<T>* __restrict__ vel, const int32_t* __restrict__ id, NbDev nb,
@@ -35,7 +36,7 @@ __global__ void __launch_bounds__(kSubstepThreads, sizeof(T) == 4 ? 4 : 2) k_sub
     T* __restrict__ Fs_w, double* __restrict__ sums, uint32_t* status) {
   __shared__ std::conditional_t<sizeof(T) == 4, SubTile, int> sh;  // FP32 path only
   const bool rebuild = !kKeep && (nb.flags[kNbRebuild] | nb.flags[kNbSticky]) != 0u;  // uniform over the launch
-  const bool do_a = alpha != nullptr, do_f = Fs_u != nullptr;
+  const bool do_a = !kNoAlpha && alpha != nullptr, do_f = Fs_u != nullptr;
   const int64_t i = blockIdx.x * (int64_t)kSubstepThreads + threadIdx.x;
   const bool valid = i < n;
   const int32_t ci = valid ? cell[i] : 0;
@@ -374,7 +375,9 @@ static int substep_launch(const DGrid& G, const GicParams* params, const GicGran
     if (s->precision == GIC_FP32) {
       DParams<float> P;
       if ((rc = make_params(params, &P))) return rc;
-      auto kern = keep && !P.cap ? k_substep<float, true> : k_substep<float, false>;
+      auto kern = !(keep && !P.cap) ? k_substep<float, false>
+                  : alpha_s             ? k_substep<float, true>
+                                        : k_substep<float, true, true>;
       kern<<<blocks, kSubstepThreads, 0, stream>>>(
           G, P, s->n, s->cell, (const uint4*)s->pos, (const float4*)s->posf, (const float4*)s->vel, s->id, d,
           (const uint4*)cell_table, (float)nb->skin, fields<float>(u, v, w, p, alpha_f), next->cell,
