@@ -478,6 +478,65 @@ __device__ __forceinline__ void add_walls(const DGrid& G, const DParams<T>& P, c
   }
 }
 
+// FP32 wall forces out of line: granule i's force with the walls of the set
+// bits of `ends` (bit 2a + side: the granule's cell is that end cell of axis
+// a) added in the order of add_walls, so the sums are the same bits.  Only
+// the few granules in an end cell make the call; the grid and contact
+// constants come as scalars.
+struct WallSum {
+  float F0, F1, F2;
+  bool ok;
+};
+static __device__ __noinline__ WallSum walls_f32(float s_hi, float s_lo, float unit_f, float k_n, float zeta,
+                                                 float kt_over_cn, float mu, uint4 pi, float ri, float mi, float4 vi,
+                                                 unsigned ends, float F0, float F1, float F2) {
+  DGrid G;
+  G.s_hi = s_hi;
+  G.s_lo = s_lo;
+  G.unit_f = unit_f;
+  DParams<float> P;
+  P.k_n = k_n;
+  P.zeta = zeta;
+  P.kt_over_cn = kt_over_cn;
+  P.mu = mu;
+  WallSum R{F0, F1, F2, true};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      if (!(ends >> (2 * a + side) & 1u)) continue;
+      float gap, ov;
+      if (!wall_geom(G, pi, a, side, ri, gap, ov)) continue;
+      float x[3] = {0.f, 0.f, 0.f};
+      x[a] = side == 0 ? gap : -gap;
+      float f0, f1, f2;
+      if (pair_force(P, x[0], x[1], x[2], gap, ov, vi.x, vi.y, vi.z, mi, f0, f1, f2)) {
+        R.F0 += f0;
+        R.F1 += f1;
+        R.F2 += f2;
+      } else {
+        R.ok = false;
+      }
+    }
+  }
+  return R;
+}
+
+__device__ __forceinline__ void add_walls_f32(const DGrid& G, const DParams<float>& P, const uint4& pi, float ri,
+                                              float mi, const float4& vi, int cx, int cy, int cz, float& F0, float& F1,
+                                              float& F2, uint32_t* status) {
+  const unsigned ends = (unsigned)(cx == 0) | (unsigned)(cx == G.nc[0] - 1) << 1 | (unsigned)(cy == 0) << 2 |
+                        (unsigned)(cy == G.nc[1] - 1) << 3 | (unsigned)(cz == 0) << 4 |
+                        (unsigned)(cz == G.nc[2] - 1) << 5;
+  if (!ends) return;
+  const WallSum R = walls_f32(G.s_hi, G.s_lo, G.unit_f, P.k_n, P.zeta, P.kt_over_cn, P.mu, pi, ri, mi, vi, ends, F0,
+                              F1, F2);
+  F0 = R.F0;
+  F1 = R.F1;
+  F2 = R.F2;
+  if (!R.ok) raise_status(status, GIC_STATUS_OUT_OF_DOMAIN);
+}
+
 // The walls' part of the contact adjoint of granule i (upstream l = its own
 // force gradient): adds to gx, gv and returns the mu part.  A wall vector
 // depends on x_i only through its axis-a component.

@@ -591,29 +591,51 @@ __device__ __forceinline__ float sub_fs_scale(SubTile& sh, const SubBox& B, floa
 
 // F_s deposit of one granule on face grid comp (its stencil lies in the box
 // whenever the tile is used; inv_unit = 0: global atomics).
-__device__ __forceinline__ void sub_add_face(SubTile& sh, const SubBox& B, const DGrid& G, float* Fs, int comp,
-                                             const Stencil3<float>& St, float fc, float inv_unit) {
+// F_s deposit of one granule on face grid comp straight to global memory
+// (float atomics).
+__device__ __forceinline__ void add_face_global(const DGrid& G, float* Fs, int comp, const Stencil3<float>& St,
+                                                float fc) {
   const float wx = St.w[0], wy = St.w[1], wz = St.w[2];
   const float fx0 = (1.f - wx) * fc, fx1 = wx * fc;
   const float wyz[4] = {(1.f - wy) * (1.f - wz), wy * (1.f - wz), (1.f - wy) * wz, wy * wz};
-  if (inv_unit != 0.f) {
-    const int e0 = B.index(St.i0[0], St.i0[1], St.i0[2]);
-    if (!GIC_DBG_OK(G.dbg, e0 >= 0 && e0 + 1 + B.sy + B.sz < B.vol)) return;
+  const int nsx = G.nx + (comp == 0), nsy = G.ny + (comp == 1);
+  float* g0 = Fs + sample_index(nsx, nsy, St.i0[0], St.i0[1], St.i0[2]);
+  const int64_t gy = nsx, gz = (int64_t)nsx * nsy;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const int q = __float2int_rn(((k & 1) ? fx1 : fx0) * wyz[k >> 1] * inv_unit);
-      atomicAdd(&sh.f[comp][e0 + (k & 1) + ((k >> 1) & 1) * B.sy + (k >> 2) * B.sz], q);
-    }
-  } else {
-    const int nsx = G.nx + (comp == 0), nsy = G.ny + (comp == 1);
-    float* g0 = Fs + sample_index(nsx, nsy, St.i0[0], St.i0[1], St.i0[2]);
-    const int64_t gy = nsx, gz = (int64_t)nsx * nsy;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const float d = ((k & 1) ? fx1 : fx0) * wyz[k >> 1];
-      if (d != 0.f) atomicAdd(g0 + (k & 1) + ((k >> 1) & 1) * gy + (k >> 2) * gz, d);
-    }
+  for (int k = 0; k < 8; ++k) {
+    const float d = ((k & 1) ? fx1 : fx0) * wyz[k >> 1];
+    if (d != 0.f) atomicAdd(g0 + (k & 1) + ((k >> 1) & 1) * gy + (k >> 2) * gz, d);
   }
+}
+
+__device__ __forceinline__ void sub_add_face(SubTile& sh, const SubBox& B, const DGrid& G, float* Fs, int comp,
+                                             const Stencil3<float>& St, float fc, float inv_unit) {
+  if (inv_unit == 0.f) {
+    add_face_global(G, Fs, comp, St, fc);
+    return;
+  }
+  const float wx = St.w[0], wy = St.w[1], wz = St.w[2];
+  const float fx0 = (1.f - wx) * fc, fx1 = wx * fc;
+  const float wyz[4] = {(1.f - wy) * (1.f - wz), wy * (1.f - wz), (1.f - wy) * wz, wy * wz};
+  const int e0 = B.index(St.i0[0], St.i0[1], St.i0[2]);
+  if (!GIC_DBG_OK(G.dbg, e0 >= 0 && e0 + 1 + B.sy + B.sz < B.vol)) return;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int q = __float2int_rn(((k & 1) ? fx1 : fx0) * wyz[k >> 1] * inv_unit);
+    atomicAdd(&sh.f[comp][e0 + (k & 1) + ((k >> 1) & 1) * B.sy + (k >> 2) * B.sz], q);
+  }
+}
+
+// F_s deposits of one granule straight to global memory, out of line: in a
+// call without alpha_s, the path of a CTA whose F_s cannot use the tile.
+static __device__ __noinline__ void fs_deposit_global(const DGrid G, float* Fs_u, float* Fs_v, float* Fs_w, int32_t c,
+                                                      uint4 pi, float fc0, float fc1, float fc2) {
+  int m[3];
+  float t[3];
+  granule_mac<float>(G, c, pi, m, t);
+  add_face_global(G, Fs_u, 0, make_stencil<float>(G, m, t, 0), fc0);
+  add_face_global(G, Fs_v, 1, make_stencil<float>(G, m, t, 1), fc1);
+  add_face_global(G, Fs_w, 2, make_stencil<float>(G, m, t, 2), fc2);
 }
 
 // F_s deposits spread over the lanes.  Consecutive sorted granules share

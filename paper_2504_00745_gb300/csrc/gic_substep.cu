@@ -95,7 +95,12 @@ __global__ void __launch_bounds__(kSubstepThreads, sizeof(T) == 4 ? 4 : 2) k_sub
         verlet_list_force(G, P, nb, i, cx, cy, cz, ci, pi, ri, mi, vi, has_f, fi, cell, pos, posf, vel, F0, F1, F2,
                           coincident);
       }
-      if (P.walls) add_walls(G, P, pi, ri, mi, vi, cx, cy, cz, F0, F1, F2, status);
+      if (P.walls) {
+        if constexpr (sizeof(T) == 4)
+          add_walls_f32(G, P, pi, ri, mi, vi, cx, cy, cz, F0, F1, F2, status);
+        else
+          add_walls(G, P, pi, ri, mi, vi, cx, cy, cz, F0, F1, F2, status);
+      }
       if (coincident) flags |= GIC_STATUS_COINCIDENT;
       if (!isfinite(F0) || !isfinite(F1) || !isfinite(F2)) flags |= GIC_STATUS_NONFINITE;
     }
@@ -162,6 +167,8 @@ __global__ void __launch_bounds__(kSubstepThreads, sizeof(T) == 4 ? 4 : 2) k_sub
     }
     if (spread && inv_unit != 0.f) {
       spread_deposit(sh, B, G, Fs, inv_unit);
+    } else if (kNoAlpha && valid && do_f) {  // inv_unit == 0 here: no tile for F_s
+      fs_deposit_global(G, Fs_u, Fs_v, Fs_w, ci, pi, fc[0], fc[1], fc[2]);
     } else if (valid && do_f) {
       int m[3];
       float t[3];
