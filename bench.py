@@ -46,12 +46,12 @@ ALGO_BYTES = {"gic_sort": 88, "gic_contact": 48, "gic_g2p_couple": 65, "gic_inte
 P2G_ALPHA_BYTES = 20
 # DRAM bytes (read + write) of one call of the dominant entry point, averaged
 # over the window's calls as the duration is: on the sweep 1 call that sorts
-# and rebuilds the lists (7.08 GB), 18 that keep them (2.40 GB each: the
+# and rebuilds the lists (7.08 GB), 18 that keep them (2.41 GB each: the
 # decision kernel + k_substep) and the last, which also forms alpha_s (3.76
 # GB), from a graph-level ncu capture of the current kernels (ncu flushes the
 # caches first); per workload (None where no capture of the current kernels
 # exists)
-NCU_TRAFFIC = {("scale_sweep_16m", "gic_step"): (7.077e9 + 18 * 2.403e9 + 3.760e9) / 20}
+NCU_TRAFFIC = {("scale_sweep_16m", "gic_step"): (7.077e9 + 18 * 2.409e9 + 3.760e9) / 20}
 
 
 def algo_bytes(name, K, fp64=False):
