@@ -490,11 +490,11 @@ struct WallSum {
 static __device__ __noinline__ WallSum walls_f32(float s_hi, float s_lo, float unit_f, float k_n, float zeta,
                                                  float kt_over_cn, float mu, uint4 pi, float ri, float mi, float4 vi,
                                                  unsigned ends, float F0, float F1, float F2) {
-  DGrid G;
+  DGrid G{};  // only the constants the wall law reads are set
   G.s_hi = s_hi;
   G.s_lo = s_lo;
   G.unit_f = unit_f;
-  DParams<float> P;
+  DParams<float> P{};
   P.k_n = k_n;
   P.zeta = zeta;
   P.kt_over_cn = kt_over_cn;
