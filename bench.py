@@ -250,13 +250,69 @@ def oracle_rate(prob, target_s, threads):
     return threads * m * K / wall, sample, wall
 
 
-def oracle_sample(prob, target_s):
-    """cpu_baseline: the oracle on all host cores, and on one."""
+def oracle_sample(prob, target_s, others=None):
+    """cpu_baseline: the oracle on all host cores, and on one; with `others`
+    (problems by workload name), also on the other configurations."""
     cores = os.cpu_count() or 1
     v_all, sample, wall = oracle_rate(prob, target_s, cores)
     v_one, sample1, wall1 = oracle_rate(prob, target_s / 2, 1)
-    return {"value": v_all, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample, "seconds": wall,
-            "one_core": {"value": v_one, "cores": 1, "sample": sample1, "seconds": wall1}}
+    out = {"value": v_all, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample, "seconds": wall,
+           "one_core": {"value": v_one, "cores": 1, "sample": sample1, "seconds": wall1}}
+    if others is not None:
+        out["configs"] = oracle_configs(others, cores)
+    return out
+
+
+# the oracle on the other configurations: (workload, granules timed; None = all)
+ORACLE_CONFIGS = (("plain_fp64_8k", None), ("diff_window_100k", None), ("dam_break_1m", 100_000),
+                  ("polydisperse_bed_8m", 50_000))
+
+
+def oracle_split_rate(prob, m, threads):
+    """The oracle on the first m granules of a workload (in the generator's
+    order), split into `threads` runs of consecutive granules, each on its own
+    block of the MAC grid on its own host thread, for the workload's K
+    substeps.  Returns (granule-substeps/s over the wall time, wall seconds)."""
+    import oracle
+
+    K = prob.K
+    chunk = -(-m // threads)
+    subs = [crop(prob, t * chunk, min(chunk, m - t * chunk)) for t in range(threads) if t * chunk < m]
+
+    def work(sub):
+        oracle.run(sub, K=K)
+
+    ths = [threading.Thread(target=work, args=(sub,)) for sub in subs]
+    t0 = time.perf_counter()
+    for th in ths:
+        th.start()
+    for th in ths:
+        th.join()
+    wall = time.perf_counter() - t0
+    return m * K / wall, wall
+
+
+def oracle_configs(problems, cores):
+    """The oracle's rate on each configuration of ORACLE_CONFIGS: the whole
+    problem (or its first granules, a block of consecutive ones) on one core,
+    and the same granules split over all cores (the runs then miss the
+    contacts across their cuts: a timing, not a result)."""
+    import gic_inputs as gi
+
+    out = {}
+    for name, m in ORACLE_CONFIGS:
+        try:
+            prob = problems[name] if name in problems else gi.make(name)
+            mm = prob.n if m is None else min(m, prob.n)
+            one, w1 = oracle_split_rate(prob, mm, 1)
+            allc, wa = oracle_split_rate(prob, mm, cores)
+            out[name] = {"granules": mm, "of": prob.n, "substeps": prob.K, "one_core": one, "one_core_s": w1,
+                         "all_cores": allc, "all_cores_s": wa, "cores": cores,
+                         "sample": "the whole problem" if mm == prob.n else
+                         f"the first {mm} granules (consecutive in the generator's order) on their block of the grid"}
+        except Exception as e:  # a timing leg: never the benchmark line's failure
+            out[name] = {"error": f"{type(e).__name__}: {e}"}
+    return out
 
 
 def run_reference(args, ws, rank):
@@ -374,6 +430,7 @@ def run_gpu(args, ws, rank, local):
     alpha_cost = run_alpha_cost(prob, sim, gic, torch, stream)
 
     variants = {"alpha_s_exact_vs_fp64_atomics": alpha_cost}
+    oracle_probs = {}  # the other configurations' problems, for the oracle's timings after the GPU work
     del sim, init, flush
     torch.cuda.empty_cache()
     if not args.no_variants:
@@ -381,6 +438,7 @@ def run_gpu(args, ws, rank, local):
         fp64_flops = variants["fma_rate"]["fp64_tflops"]
         variants[f"fp64_fwd_{prob.name}"] = run_fwd(prob, gic.GIC_FP64, gic, torch, dev, stream, hbm)
         dam = gi.make("dam_break_1m")
+        oracle_probs["dam_break_1m"] = dam
         for prec_name, prec in (("fp32", gic.GIC_FP32), ("fp64", gic.GIC_FP64)):
             variants[f"{prec_name}_fwd_dam_break_1m"] = run_fwd(dam, prec, gic, torch, dev, stream, hbm,
                                                                keep_for_projection=(prec == gic.GIC_FP32))
@@ -393,10 +451,10 @@ def run_gpu(args, ws, rank, local):
             variants[f"{prec_name}_adjoint_kernel_dam_break_1m"] = run_adjoint_kernel(dam, prec, gic, torch, dev,
                                                                                     stream, hbm)
             variants[f"{prec_name}_adjoint_dam_break_1m"] = run_adjoint(dam, prec, torch, dev)
-            wprob = gi.make("diff_window_100k")
+            wprob = oracle_probs["diff_window_100k"] = gi.make("diff_window_100k")
             variants[f"{prec_name}_adjoint_diff_window_100k"] = run_adjoint(wprob, prec, torch, dev)
         del dam
-        wp = gi.make("polydisperse_bed_8m")
+        wp = oracle_probs["polydisperse_bed_8m"] = gi.make("polydisperse_bed_8m")
         for prec_name, prec in (("fp32", gic.GIC_FP32), ("fp64", gic.GIC_FP64)):
             variants[f"{prec_name}_fwd_polydisperse_bed_8m"] = run_fwd(wp, prec, gic, torch, dev, stream, hbm,
                                                                       contacts=(prec == gic.GIC_FP32))
@@ -419,7 +477,7 @@ def run_gpu(args, ws, rank, local):
             "roofline": roofline, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
             "device_status": status, "variants": variants}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = oracle_sample(prob, args.cpu_seconds)
+        line["cpu_baseline"] = oracle_sample(prob, args.cpu_seconds, None if args.no_variants else oracle_probs)
     if rank == 0:
         print(json.dumps(line), flush=True)
 

@@ -40,3 +40,16 @@ def test_window_traffic_lies_between_its_calls():
     t = bench.NCU_TRAFFIC[("scale_sweep_16m", "gic_step")]
     assert 2.4e9 < t < 7.1e9
     assert t < 3.0e9  # 18 of the 20 calls keep the lists
+
+
+def test_oracle_configs_time_each_configuration_and_never_raise(monkeypatch):
+    import bench
+
+    monkeypatch.setattr(bench, "ORACLE_CONFIGS", (("plain_fp64_8k", None), ("plain_fp64_8k", 2000),
+                                                  ("no_such_workload", None)))
+    r = bench.oracle_configs({}, 2)
+    whole = r["plain_fp64_8k"]  # the later entry of the same name: its first 2000 granules
+    assert whole["granules"] == 2000 and whole["of"] == 8000 and whole["substeps"] == 10
+    assert whole["one_core"] > 0 and whole["all_cores"] > 0 and whole["cores"] == 2
+    assert "first 2000 granules" in whole["sample"]
+    assert "error" in r["no_such_workload"]  # a failed leg is reported, not raised
